@@ -1,0 +1,205 @@
+"""IMEX timesteppers, their tangents and their exact discrete adjoints (oracle).
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
+
+Notation follows Supplementary A.4 of arXiv 2506.14792: the IVP is
+``M dX/dt + L X = F(X)``.  A problem object supplies, on complex coefficient
+vectors (the real inner product is ``<a, b> = Re sum conj(a) b``):
+
+* ``M(X)``, ``L(X)``, ``F(X)``            -- maps from variable space to equation space
+* ``Mt(Y)``, ``Lt(Y)``                    -- their adjoints (equation -> variable space)
+* ``F_jvp(X, dX)``, ``F_vjp(X, Y)``       -- Jacobian-vector / vector-Jacobian products of F
+* ``solve(a, b, R)``                      -- X with (a M + b L) X = R
+* ``solve_t(a, b, R)``                    -- Y with (a M + b L)^dagger Y = R
+* ``project(X)``                          -- orthogonal projection onto the admissible
+                                             (Hermitian-consistent) coefficients, applied
+                                             after every solve; it is self-adjoint.
+
+Scheme constants are the published methods the paper cites for its
+timesteppers (Wang & Ruuth 2008 SBDF; Ascher, Ruuth & Spiteri 1997 ARS(2,2,2)).
+"""
+import math
+
+import numpy as np
+
+
+def inner(a, b):
+    """Real inner product over the stored real numbers of two coefficient vectors."""
+    return float(np.real(np.vdot(a, b)))
+
+
+# --------------------------------------------------------------------------------------
+# Scheme constants
+# --------------------------------------------------------------------------------------
+
+def sbdf_coeffs(n, order, dt):
+    """Coefficients (a[0..s], b[0..s], c[0..s]) of step n (n >= 1) of SBDF<order>.
+
+    Eq. imex: (a0 M + b0 L) X_n = sum_{i=1..s} [c_i F(X_{n-i}) - (a_i M + b_i L) X_{n-i}].
+    The scheme falls back to a lower order while fewer than ``order`` past steps
+    exist (the paper: "revert to lower order multistep IMEX schemes for early
+    iterations").  c[0] is unused and set to 0.
+    """
+    s = min(n, order)
+    if s == 1:  # backward/forward Euler
+        return (np.array([1.0 / dt, -1.0 / dt]), np.array([1.0, 0.0]), np.array([0.0, 1.0]))
+    if s == 2:  # SBDF2 with constant dt
+        return (np.array([1.5 / dt, -2.0 / dt, 0.5 / dt]), np.array([1.0, 0.0, 0.0]),
+                np.array([0.0, 2.0, -1.0]))
+    raise ValueError("only SBDF1 / SBDF2 are defined here")
+
+
+RK222_GAMMA = 1.0 - 1.0 / math.sqrt(2.0)
+RK222_DELTA = 1.0 - 1.0 / (2.0 * RK222_GAMMA)
+
+
+def rk222_tableaux():
+    """ARS(2,2,2): explicit tableau A[i][j] and implicit tableau H[i][j] (i, j = 0..2)."""
+    g, d = RK222_GAMMA, RK222_DELTA
+    A = np.array([[0.0, 0.0, 0.0], [g, 0.0, 0.0], [d, 1.0 - d, 0.0]])
+    H = np.array([[0.0, 0.0, 0.0], [0.0, g, 0.0], [0.0, 1.0 - g, g]])
+    return A, H
+
+
+# --------------------------------------------------------------------------------------
+# Multistep IMEX (eq. imex and eq. IMEX_adjoint)
+# --------------------------------------------------------------------------------------
+
+def multistep_forward(prob, X0, nsteps, dt, order=2):
+    """Forward trajectory [X_0, X_1, ..., X_N] of eq. imex."""
+    X = [X0]
+    Fs = [prob.F(X0)]
+    for n in range(1, nsteps + 1):
+        a, b, c = sbdf_coeffs(n, order, dt)
+        s = len(a) - 1
+        R = 0
+        for i in range(1, s + 1):
+            Xi = X[n - i]
+            R = R + c[i] * Fs[n - i] - (a[i] * prob.M(Xi) + b[i] * prob.L(Xi))
+        Xn = prob.project(prob.solve(a[0], b[0], R))
+        X.append(Xn)
+        Fs.append(prob.F(Xn))
+    return X
+
+
+def multistep_tangent(prob, X, dX0, dt, order=2):
+    """Tangent (JVP) trajectory [dX_0, ..., dX_N] along the primal trajectory X."""
+    nsteps = len(X) - 1
+    dX = [dX0]
+    for n in range(1, nsteps + 1):
+        a, b, c = sbdf_coeffs(n, order, dt)
+        s = len(a) - 1
+        R = 0
+        for i in range(1, s + 1):
+            Xi, dXi = X[n - i], dX[n - i]
+            R = R + c[i] * prob.F_jvp(Xi, dXi) - (a[i] * prob.M(dXi) + b[i] * prob.L(dXi))
+        dX.append(prob.project(prob.solve(a[0], b[0], R)))
+    return dX
+
+
+def multistep_adjoint(prob, X, dJ, dt, order=2):
+    """Gradient dJ/dX_0 by eq. IMEX_adjoint run backward over the trajectory X.
+
+    ``dJ(n)`` returns the explicit partial dJ/dX_n (or None).  The adjoint solve
+    at step n carries the source dJ/dX_n on its right-hand side wherever the
+    objective touches X_n, and the initial condition's cotangent is the
+    right-hand side of eq. IMEX_adjoint at n = 0 with no solve (X_0 is an input).
+    Superscripts follow the equation: the coefficients of step n+i multiply Y_{n+i}.
+    """
+    nsteps = len(X) - 1
+    Y = [None] * (nsteps + 1)
+    coeffs = [None] + [sbdf_coeffs(n, order, dt) for n in range(1, nsteps + 1)]
+    for n in range(nsteps, -1, -1):
+        lam = dJ(n)
+        lam = 0 if lam is None else lam
+        for i in range(1, order + 1):
+            m = n + i
+            if m > nsteps:
+                continue
+            a, b, c = coeffs[m]
+            if i > len(a) - 1:
+                continue
+            Ym = Y[m]
+            lam = lam + c[i] * prob.F_vjp(X[n], Ym) - (a[i] * prob.Mt(Ym) + b[i] * prob.Lt(Ym))
+        if n == 0:
+            return lam
+        a, b, _ = coeffs[n]
+        Y[n] = prob.solve_t(a[0], b[0], prob.project(lam))
+
+
+# --------------------------------------------------------------------------------------
+# Runge-Kutta IMEX (Supplementary A.4, RK stage equation and its adjoint)
+# --------------------------------------------------------------------------------------
+
+def rk_step(prob, Xn, dt, A, H):
+    """One RK IMEX step; returns the list of stage values [X_{n,0}, ..., X_{n,s}]."""
+    s = A.shape[0] - 1
+    stages = [Xn]
+    Fst = [prob.F(Xn)]
+    MX0 = prob.M(Xn)
+    for i in range(1, s + 1):
+        R = MX0
+        for j in range(i):
+            R = R + dt * (A[i, j] * Fst[j] - H[i, j] * prob.L(stages[j]))
+        Xi = prob.project(prob.solve(1.0, dt * H[i, i], R))
+        stages.append(Xi)
+        if i < s:
+            Fst.append(prob.F(Xi))
+    return stages
+
+
+def rk_forward(prob, X0, nsteps, dt, A, H):
+    """Forward trajectory; returns (states [X_0..X_N], stages per step)."""
+    X = [X0]
+    stages = []
+    for _ in range(nsteps):
+        st = rk_step(prob, X[-1], dt, A, H)
+        stages.append(st)
+        X.append(st[-1])
+    return X, stages
+
+
+def rk_tangent(prob, stages, dX0, dt, A, H):
+    """Tangent trajectory [dX_0, ..., dX_N] along recorded RK stages."""
+    s = A.shape[0] - 1
+    dX = [dX0]
+    for st in stages:
+        dst = [dX[-1]]
+        MdX0 = prob.M(dX[-1])
+        for i in range(1, s + 1):
+            R = MdX0
+            for j in range(i):
+                R = R + dt * (A[i, j] * prob.F_jvp(st[j], dst[j]) - H[i, j] * prob.L(dst[j]))
+            dst.append(prob.project(prob.solve(1.0, dt * H[i, i], R)))
+        dX.append(dst[-1])
+    return dX
+
+
+def rk_adjoint(prob, stages, dJ, dt, A, H):
+    """Gradient dJ/dX_0 by the RK IMEX adjoint run backward over recorded stages.
+
+    ``Ybar`` is the total cotangent of the step's output X_{n+1} (the paper's
+    Y_{n+1,0}); Y[i] are the stage cotangents solving
+    (M + dt H_ii L)^dagger Y_{n,i} = Ybar (i = s) or
+    sum_{j>i} dt (A_ji dF/dX_{n,i} - H_ji L)^dagger Y_{n,j} (0 < i < s), and the
+    cotangent of X_n is sum_j (M^dagger + dt [A_j0 dF/dX_{n,0} - H_j0 L]^dagger) Y_{n,j}.
+    """
+    s = A.shape[0] - 1
+    nsteps = len(stages)
+    Ybar = dJ(nsteps)
+    Ybar = 0 * stages[-1][-1] if Ybar is None else Ybar
+    for n in range(nsteps - 1, -1, -1):
+        st = stages[n]
+        Y = [None] * (s + 1)
+        Y[s] = prob.solve_t(1.0, dt * H[s, s], prob.project(Ybar))
+        for i in range(s - 1, 0, -1):
+            rhs = 0
+            for j in range(i + 1, s + 1):
+                rhs = rhs + dt * (A[j, i] * prob.F_vjp(st[i], Y[j]) - H[j, i] * prob.Lt(Y[j]))
+            Y[i] = prob.solve_t(1.0, dt * H[i, i], prob.project(rhs))
+        lam = 0
+        for j in range(1, s + 1):
+            lam = lam + prob.Mt(Y[j]) + dt * (A[j, 0] * prob.F_vjp(st[0], Y[j]) - H[j, 0] * prob.Lt(Y[j]))
+        src = dJ(n)
+        Ybar = lam if src is None else lam + src
+    return Ybar

@@ -1,0 +1,36 @@
+"""Seeded synthetic inputs shared by the CUDA path, the oracle and the benchmark.
+
+This module holds input recipes only (random draws, spectral envelopes and
+normalisations of the draws); none of the method's arithmetic (transforms,
+nonlinear terms, solves, timestepping) lives here.  Every generator is
+deterministic in its seed (numpy PCG64).
+"""
+import numpy as np
+
+
+def burgers_ic(N, batch=1, seed=1, nmodes=16, length=2.0 * np.pi):
+    """Half-spectrum coefficients (batch, N//2) complex of
+    u0(x) = sum_{k=1..16} k^-2 (a_k cos kx + b_k sin kx), a_k, b_k ~ N(0,1),
+    scaled so that max_x |u0| = 1 (maximum taken on a 1024-point sample grid).
+    """
+    K = N // 2
+    rng = np.random.default_rng(seed)
+    ab = rng.standard_normal((batch, nmodes, 2))
+    k = np.arange(1, nmodes + 1)
+    c = np.zeros((batch, K), dtype=np.complex128)
+    c[:, 1:nmodes + 1] = (ab[:, :, 0] - 1j * ab[:, :, 1]) * (0.5 / k ** 2)
+    xs = np.arange(1024) * (2.0 * np.pi / 1024)
+    cosm = np.cos(np.outer(k, xs))
+    sinm = np.sin(np.outer(k, xs))
+    for s in range(0, batch, 2048):
+        a = ab[s:s + 2048, :, 0] / k ** 2
+        b = ab[s:s + 2048, :, 1] / k ** 2
+        u = a @ cosm + b @ sinm
+        c[s:s + 2048] /= np.max(np.abs(u), axis=1)[:, None]
+    return c
+
+
+def random_coeffs(shape, seed, scale=1.0):
+    """Complex N(0, scale^2) coefficients (used for test directions and cotangents)."""
+    rng = np.random.default_rng(seed)
+    return scale * (rng.standard_normal(shape) + 1j * rng.standard_normal(shape))
