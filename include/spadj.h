@@ -1,0 +1,151 @@
+/*
+ * spadj.h -- C-ABI of the GB300 library for IMEX spectral timesteps and their exact
+ * discrete adjoints (arXiv 2506.14792, "Fast automated adjoints for spectral PDE solvers").
+ *
+ * The library implements, in hand-written CUDA for sm_103a, one IMEX timestep of a
+ * sparse spectral discretisation of  M dX/dt + L X = F(X, p)  (Supplementary A.4) and
+ * the adjoint of that step run backward over a checkpointed trajectory, and the
+ * gradient of an objective J with respect to the initial condition
+ * (eqs. 1-6, "Efficiently calculating gradients").
+ *
+ * Conventions (all entry points):
+ *  - Every array argument is caller-owned DEVICE memory (for example from torch), read
+ *    and written on the problem's CUDA stream, unless the name ends in _host.
+ *  - Coefficient arrays are float64 and hold complex coefficients as interleaved
+ *    (re, im) pairs; the layout of each equation set is given at spadj_eq below.
+ *    The inner product that defines every adjoint is the Euclidean one over these
+ *    stored reals (the paper's "suitably chosen inner product", Continuous vs.
+ *    discrete section).
+ *  - Calls are asynchronous on the stream except where a _host output is written
+ *    (then the call synchronises the stream before returning).
+ *  - The library owns its factorisations, workspaces and checkpoint slots; it
+ *    allocates them in spadj_create or lazily on first use, and frees them in
+ *    spadj_destroy.
+ *  - Every call returns a spadj_status; on failure spadj_last_error() gives a
+ *    one-line reason.  No call falls back to CPU arithmetic.
+ */
+#ifndef SPADJ_H
+#define SPADJ_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct spadj_problem spadj_problem; /* opaque, library-owned */
+
+typedef enum {
+  SPADJ_OK = 0,
+  SPADJ_ERR_INVALID = -1,     /* bad descriptor, size or pointer */
+  SPADJ_ERR_NOMEM = -2,       /* device allocation failed or checkpoint budget too small */
+  SPADJ_ERR_CUDA = -3,        /* a CUDA runtime call failed */
+  SPADJ_ERR_NONFINITE = -4,   /* a NaN/Inf was detected in the state or objective */
+  SPADJ_ERR_TIMEOUT = -5,     /* a bounded device-side wait gave up */
+  SPADJ_ERR_UNSUPPORTED = -6  /* operation not defined for this equation/scheme */
+} spadj_status;
+
+/*
+ * Equation sets and their coefficient layouts (B = batch size from the descriptor).
+ *
+ * SPADJ_BURGERS1D: u_t - nu u_xx = -d/dx(u^2/2) on [0, length[0]), periodic Fourier
+ *   basis, N = n[0] modes, 3/2-dealiased grid of 3N/2 points.  State per member:
+ *   K = N/2 complex coefficients c_k (k = 0..K-1; Nyquist not stored; Im c_0 held at 0).
+ *   Layout [B][K] complex.  Grid layout [B][3N/2] real.  params[0] = nu.
+ *
+ * SPADJ_RB2D: Boussinesq convection, Fourier(x) x Chebyshev(z) with tau terms
+ *   (Sparse spectral methods section); see rb layout note in the design notes.
+ */
+typedef enum {
+  SPADJ_BURGERS1D = 0,
+  SPADJ_RB2D = 1,
+  SPADJ_KOLMOGOROV2D = 2
+} spadj_eq;
+
+typedef enum {
+  SPADJ_SBDF1 = 1, /* multistep IMEX, eq. imex, first order */
+  SPADJ_SBDF2 = 2, /* multistep IMEX, eq. imex, second order (SBDF1 first step) */
+  SPADJ_RK222 = 3  /* Runge-Kutta IMEX ARS(2,2,2), Supplementary A.4 stage equation */
+} spadj_scheme;
+
+typedef struct {
+  int eq;            /* spadj_eq */
+  int scheme;        /* spadj_scheme */
+  int n[3];          /* modes per axis (unused axes 0) */
+  double length[3];  /* domain lengths per axis */
+  double params[4];  /* equation parameters (see spadj_eq) */
+  double dt;         /* constant timestep */
+  int batch;         /* number of independent members advanced together (>= 1) */
+  int nonlinear;     /* 1: F as defined; 0: F = 0 (linear problem, used by tests) */
+} spadj_desc;
+
+/* Build a problem (operators, transform tables, factorisations) bound to cuda_stream
+ * (a cudaStream_t; NULL = legacy default stream).  *out receives the handle. */
+spadj_status spadj_create(const spadj_desc* desc, void* cuda_stream, spadj_problem** out);
+
+/* Free everything the problem owns.  Synchronises the stream first. */
+spadj_status spadj_destroy(spadj_problem* prob);
+
+/* Lengths in float64 elements for the whole batch:
+ * which = 0: coefficient state (the vector the gradient is taken with respect to);
+ * which = 1: one real grid field;  which = 2: parameter vector p. */
+size_t spadj_state_len(const spadj_problem* prob, int which);
+
+/* Collocation transforms (Methods, "Spectral transforms"): kind
+ *  0 = c2g  (T^-1: coefficients -> grid),      1 = g2c  (T: grid -> coefficients),
+ *  2 = c2g adjoint (T^-dagger... applied as (T^-1)^dagger: grid -> coefficients),
+ *  3 = g2c adjoint (T^dagger: coefficients -> grid).
+ * in/out are device arrays in the coefficient or grid layout of the equation set. */
+spadj_status spadj_transform(spadj_problem* prob, int kind, const double* in, double* out);
+
+/* Explicit term F(X) in coefficient space (Sparse spectral methods section: nonlinear
+ * terms evaluated on the dealiased collocation grid), its Jacobian-vector product
+ * dF = (dF/dX) dX and its vector-Jacobian product out = (dF/dX)^dagger y
+ * (Methods, "Nonlinear operator graphs"). */
+spadj_status spadj_eval_F(spadj_problem* prob, const double* x, double* f);
+spadj_status spadj_eval_F_jvp(spadj_problem* prob, const double* x, const double* dx, double* df);
+spadj_status spadj_eval_F_vjp(spadj_problem* prob, const double* x, const double* y, double* out);
+
+/* Forward trajectory of n_steps IMEX steps from x0 (eq. imex / RK stage equation).
+ * x_out receives X_N.  traj (nullable) receives X_0..X_N, layout [n_steps+1][state]. */
+spadj_status spadj_forward(spadj_problem* prob, int n_steps, const double* x0, double* x_out,
+                           double* traj);
+
+/* Tangent (JVP) trajectory: dx_out = dX_N for the perturbation dx0 of x0. */
+spadj_status spadj_tangent(spadj_problem* prob, int n_steps, const double* x0, const double* dx0,
+                           double* dx_out);
+
+/* Adjoint sweep over a stored trajectory traj (= X_0..X_N from spadj_forward):
+ * seeds the cotangent y_final = dJ/dX_N and returns grad_x0 = dJ/dX_0 by the
+ * discrete adjoint recurrence (eq. IMEX_adjoint / RK adjoint, Supplementary A.4). */
+spadj_status spadj_adjoint(spadj_problem* prob, int n_steps, const double* traj,
+                           const double* y_final, double* grad_x0);
+
+/* Objectives for spadj_gradient. */
+typedef enum {
+  SPADJ_OBJ_ENERGY = 0 /* J = 1/2 ||u(T)||^2 (physical L2 integral) per batch member */
+} spadj_objective_kind;
+
+/* Objective J(X) per batch member and its partial derivative (eq. 1's dJ/dX), which seeds
+ * the adjoint sweep: J_dev receives B doubles (device), seed receives dJ/dX (state layout).
+ * obj_data is objective-specific (NULL for SPADJ_OBJ_ENERGY). */
+spadj_status spadj_objective(spadj_problem* prob, int objective, const double* obj_data, const double* x,
+                             double* J_dev, double* seed);
+
+/* Gradient of an objective with respect to the initial condition (eqs. 1-6):
+ * forward sweep with checkpoints (ckpt_slots <= 0: store every step), objective,
+ * adjoint sweep with recomputation.  J_host receives J per batch member (host
+ * memory, B doubles); grad_x0 receives dJ/dX_0.  obj_data and grad_p may be NULL. */
+spadj_status spadj_gradient(spadj_problem* prob, const double* x0, int n_steps, int objective,
+                            const double* obj_data, int ckpt_slots, double* J_host,
+                            double* grad_x0, double* grad_p);
+
+/* One-line description of the last failure on this problem (or of the last failed
+ * spadj_create when prob is NULL).  Never NULL. */
+const char* spadj_last_error(const spadj_problem* prob);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPADJ_H */

@@ -1,0 +1,128 @@
+// C-ABI entry points declared in include/spadj.h: argument checks and dispatch to the
+// equation set's implementation.  No arithmetic of the method happens here.
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "problem.h"
+
+using spadj::Problem;
+
+namespace {
+thread_local std::string g_create_error = "no error";
+
+bool bad_ptr(const void* p) { return p == nullptr; }
+}  // namespace
+
+extern "C" {
+
+spadj_status spadj_create(const spadj_desc* desc, void* cuda_stream, spadj_problem** out) {
+  if (!desc || !out) {
+    g_create_error = "spadj_create: desc and out must be non-NULL";
+    return SPADJ_ERR_INVALID;
+  }
+  *out = nullptr;
+  if (desc->batch < 1 || !(desc->dt > 0.0)) {
+    g_create_error = "spadj_create: batch must be >= 1 and dt > 0";
+    return SPADJ_ERR_INVALID;
+  }
+  spadj_problem* p = new (std::nothrow) spadj_problem();
+  if (!p) {
+    g_create_error = "spadj_create: out of host memory";
+    return SPADJ_ERR_NOMEM;
+  }
+  p->desc = *desc;
+  p->stream = static_cast<cudaStream_t>(cuda_stream);
+  spadj_status st = SPADJ_ERR_UNSUPPORTED;
+  switch (desc->eq) {
+    case SPADJ_BURGERS1D: p->impl = spadj::make_burgers(p, &st); break;
+    default: p->err = "spadj_create: unknown equation set"; break;
+  }
+  if (st != SPADJ_OK || !p->impl) {
+    g_create_error = p->err.empty() ? "spadj_create failed" : p->err;
+    delete p->impl;
+    delete p;
+    return st == SPADJ_OK ? SPADJ_ERR_INVALID : st;
+  }
+  *out = p;
+  return SPADJ_OK;
+}
+
+spadj_status spadj_destroy(spadj_problem* p) {
+  if (!p) return SPADJ_ERR_INVALID;
+  cudaStreamSynchronize(p->stream);
+  delete p->impl;
+  delete p;
+  return SPADJ_OK;
+}
+
+size_t spadj_state_len(const spadj_problem* p, int which) {
+  if (!p || !p->impl) return 0;
+  return p->impl->state_len(which);
+}
+
+spadj_status spadj_transform(spadj_problem* p, int kind, const double* in, double* out) {
+  if (!p) return SPADJ_ERR_INVALID;
+  if (bad_ptr(in) || bad_ptr(out)) return p->fail(SPADJ_ERR_INVALID, "transform: NULL array");
+  return p->impl->transform(p, kind, in, out);
+}
+
+spadj_status spadj_eval_F(spadj_problem* p, const double* x, double* f) {
+  if (!p) return SPADJ_ERR_INVALID;
+  if (bad_ptr(x) || bad_ptr(f)) return p->fail(SPADJ_ERR_INVALID, "eval_F: NULL array");
+  return p->impl->eval_F(p, 0, x, nullptr, f);
+}
+
+spadj_status spadj_eval_F_jvp(spadj_problem* p, const double* x, const double* dx, double* df) {
+  if (!p) return SPADJ_ERR_INVALID;
+  if (bad_ptr(x) || bad_ptr(dx) || bad_ptr(df)) return p->fail(SPADJ_ERR_INVALID, "eval_F_jvp: NULL array");
+  return p->impl->eval_F(p, 1, x, dx, df);
+}
+
+spadj_status spadj_eval_F_vjp(spadj_problem* p, const double* x, const double* y, double* out) {
+  if (!p) return SPADJ_ERR_INVALID;
+  if (bad_ptr(x) || bad_ptr(y) || bad_ptr(out)) return p->fail(SPADJ_ERR_INVALID, "eval_F_vjp: NULL array");
+  return p->impl->eval_F(p, 2, x, y, out);
+}
+
+spadj_status spadj_forward(spadj_problem* p, int n_steps, const double* x0, double* x_out, double* traj) {
+  if (!p) return SPADJ_ERR_INVALID;
+  if (bad_ptr(x0) || bad_ptr(x_out)) return p->fail(SPADJ_ERR_INVALID, "forward: NULL array");
+  return p->impl->forward(p, n_steps, x0, x_out, traj);
+}
+
+spadj_status spadj_tangent(spadj_problem* p, int n_steps, const double* x0, const double* dx0, double* dx_out) {
+  if (!p) return SPADJ_ERR_INVALID;
+  if (bad_ptr(x0) || bad_ptr(dx0) || bad_ptr(dx_out)) return p->fail(SPADJ_ERR_INVALID, "tangent: NULL array");
+  return p->impl->tangent(p, n_steps, x0, dx0, dx_out);
+}
+
+spadj_status spadj_adjoint(spadj_problem* p, int n_steps, const double* traj, const double* y_final,
+                           double* grad_x0) {
+  if (!p) return SPADJ_ERR_INVALID;
+  if (bad_ptr(traj) || bad_ptr(y_final) || bad_ptr(grad_x0))
+    return p->fail(SPADJ_ERR_INVALID, "adjoint: NULL array");
+  return p->impl->adjoint(p, n_steps, traj, y_final, grad_x0);
+}
+
+spadj_status spadj_objective(spadj_problem* p, int objective, const double* obj_data, const double* x,
+                             double* J_dev, double* seed) {
+  if (!p) return SPADJ_ERR_INVALID;
+  if (bad_ptr(x) || bad_ptr(J_dev) || bad_ptr(seed)) return p->fail(SPADJ_ERR_INVALID, "objective: NULL array");
+  return p->impl->objective(p, objective, obj_data, x, J_dev, seed);
+}
+
+spadj_status spadj_gradient(spadj_problem* p, const double* x0, int n_steps, int objective,
+                            const double* obj_data, int ckpt_slots, double* J_host, double* grad_x0,
+                            double* grad_p) {
+  if (!p) return SPADJ_ERR_INVALID;
+  if (bad_ptr(x0) || bad_ptr(grad_x0)) return p->fail(SPADJ_ERR_INVALID, "gradient: NULL array");
+  return p->impl->gradient(p, x0, n_steps, objective, obj_data, ckpt_slots, J_host, grad_x0, grad_p);
+}
+
+const char* spadj_last_error(const spadj_problem* p) {
+  if (!p) return g_create_error.c_str();
+  return p->err.empty() ? "no error" : p->err.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,521 @@
+// 1D viscous Burgers, u_t - nu u_xx = -d/dx(u^2/2), periodic Fourier basis, 3/2 dealiasing.
+//
+// The whole batch runs as persistent trajectories: one CTA owns one batch member for all
+// steps, keeps the multistep history (X_{n-1}, X_{n-2}, F_{n-1}, F_{n-2}) in registers and
+// evaluates F through shared-memory FFTs (grid of M = 3N/2 points, one L = M/2 complex FFT
+// per real transform).  Kernels:
+//   * forward  -- eq. imex with SBDF1 first step then SBDF2 (Supplementary A.4); M = I and
+//                 L = nu k^2, so the implicit solve is a per-mode division, fused.
+//   * tangent  -- the JVP of the same recurrence, run alongside the primal.
+//   * adjoint  -- eq. IMEX_adjoint backward over the stored trajectory; one VJP of F per
+//                 step, (dF/dX)^dagger w = B^dagger[(B X) * T^dagger(i k w)].
+// State layout: [member][k] complex (k = 0..K-1), Im c_0 held at 0 after every solve.
+#include <cmath>
+#include <vector>
+
+#include "fft.cuh"
+#include "problem.h"
+
+namespace spadj {
+namespace {
+
+constexpr int kQMax = 4;  // modes per thread
+
+struct BurgersParams {
+  int K, L, M;
+  double nu, kscale, dt, length;
+  int order, nonlinear;
+  FFTPlan plan;
+  const double2* WM;
+};
+
+struct Smem {
+  double2* A;
+  double2* B;
+  double2* C;
+  double2* D;
+  double2* S;  // spectrum staging (K)
+  double2* O;  // spectral output staging (K)
+};
+
+__device__ __forceinline__ Smem carve(const BurgersParams& P) {
+  extern __shared__ double2 sm[];
+  Smem s;
+  s.A = sm;
+  s.B = s.A + P.L;
+  s.C = s.B + P.L;
+  s.D = s.C + P.L;
+  s.S = s.D + P.L;
+  s.O = s.S + P.K;
+  return s;
+}
+
+// grid (packed) of the coefficients in S, weights (w0, w): see c2r_pre.  Result buffer returned.
+__device__ double2* c2g_packed(const BurgersParams& P, const double2* S, double2* a, double2* b, double w0,
+                               double w) {
+  c2r_pre(a, [&](int k) { return S[k]; }, P.K, P.L, P.WM, w0, w);
+  __syncthreads();
+  return cfft_smem(a, b, P.plan, P.WM, +1);
+}
+
+// forward real FFT of the packed grid in a; writes X_k * scale(k) to O (k < K).
+template <class Scale>
+__device__ void g2c_packed(const BurgersParams& P, double2* a, double2* b, double2* O, Scale scale) {
+  double2* z = cfft_smem(a, b, P.plan, P.WM, -1);
+  r2c_post(z, [&](int k, double2 v) { O[k] = scale(k, v); }, P.K, P.L, P.WM);
+  __syncthreads();
+}
+
+__device__ __forceinline__ double kwav(const BurgersParams& P, int k) { return P.kscale * k; }
+
+// O <- F(S) = -i k T[(B S)^2 / 2]
+__device__ void eval_F(const BurgersParams& P, Smem& s) {
+  double2* u = c2g_packed(P, s.S, s.A, s.B, 1.0, 1.0);
+  for (int j = threadIdx.x; j < P.L; j += blockDim.x) {
+    double2 v = u[j];
+    u[j] = make_double2(0.5 * v.x * v.x, 0.5 * v.y * v.y);
+  }
+  __syncthreads();
+  double2* other = (u == s.A) ? s.B : s.A;
+  const double invM = 1.0 / P.M;
+  g2c_packed(P, u, other, s.O, [&](int k, double2 v) {
+    double kk = kwav(P, k) * invM;  // -i k v / M
+    return make_double2(kk * v.y, -kk * v.x);
+  });
+}
+
+// From the primal spectrum S and the tangent spectrum S2: O <- F(S) (if want_F) and
+// O2 <- (dF/dX)(S) S2 = -i k T[(B S)(B S2)].
+__device__ void eval_F_and_jvp(const BurgersParams& P, Smem& s, const double2* S2, double2* O2, bool want_F) {
+  double2* u = c2g_packed(P, s.S, s.A, s.B, 1.0, 1.0);
+  double2* du = c2g_packed(P, S2, s.C, s.D, 1.0, 1.0);
+  double2* uo = (u == s.A) ? s.B : s.A;
+  double2* duo = (du == s.C) ? s.D : s.C;
+  for (int j = threadIdx.x; j < P.L; j += blockDim.x) {
+    double2 v = u[j], dv = du[j];
+    du[j] = make_double2(v.x * dv.x, v.y * dv.y);
+    u[j] = make_double2(0.5 * v.x * v.x, 0.5 * v.y * v.y);
+  }
+  __syncthreads();
+  const double invM = 1.0 / P.M;
+  auto mik = [&](int k, double2 v) {
+    double kk = kwav(P, k) * invM;
+    return make_double2(kk * v.y, -kk * v.x);
+  };
+  if (want_F) g2c_packed(P, u, uo, s.O, mik);
+  g2c_packed(P, du, duo, O2, mik);
+}
+
+// O <- (dF/dX)(S)^dagger W  with W staged in S2:  B^dagger[(B S) * T^dagger(i k W)]
+__device__ void eval_vjp(const BurgersParams& P, Smem& s, double2* S2) {
+  double2* u = c2g_packed(P, s.S, s.A, s.B, 1.0, 1.0);
+  // S2 <- i k W (in place, own entries only)
+  for (int k = threadIdx.x; k < P.K; k += blockDim.x) {
+    double2 w = S2[k];
+    double kk = kwav(P, k);
+    S2[k] = make_double2(-kk * w.y, kk * w.x);
+  }
+  __syncthreads();
+  double2* v = c2g_packed(P, S2, s.C, s.D, 1.0 / P.M, 0.5 / P.M);
+  double2* vo = (v == s.C) ? s.D : s.C;
+  for (int j = threadIdx.x; j < P.L; j += blockDim.x) {
+    double2 a = u[j], b = v[j];
+    v[j] = make_double2(a.x * b.x, a.y * b.y);
+  }
+  __syncthreads();
+  g2c_packed(P, v, vo, s.O, [&](int k, double2 x) {
+    return k == 0 ? make_double2(x.x, 0.0) : make_double2(2.0 * x.x, 2.0 * x.y);
+  });
+}
+
+__device__ __forceinline__ const double2* row(const double* base, int b, int K) {
+  return reinterpret_cast<const double2*>(base) + (size_t)b * K;
+}
+__device__ __forceinline__ double2* row(double* base, int b, int K) {
+  return reinterpret_cast<double2*>(base) + (size_t)b * K;
+}
+
+// ---- single-shot kernels (transforms, F, JVP, VJP) ----------------------------------------
+
+__global__ void transform_kernel(BurgersParams P, int kind, const double* __restrict__ in, double* __restrict__ out) {
+  Smem s = carve(P);
+  const int b = blockIdx.x;
+  const int K = P.K, L = P.L, M = P.M;
+  if (kind == 0 || kind == 3) {  // coefficients -> grid
+    const double2* x = row(in, b, K);
+    for (int k = threadIdx.x; k < K; k += blockDim.x) s.S[k] = x[k];
+    __syncthreads();
+    double2* z = (kind == 0) ? c2g_packed(P, s.S, s.A, s.B, 1.0, 1.0)
+                             : c2g_packed(P, s.S, s.A, s.B, 1.0 / M, 0.5 / M);
+    double2* g = reinterpret_cast<double2*>(out + (size_t)b * M);
+    for (int j = threadIdx.x; j < L; j += blockDim.x) g[j] = z[j];
+  } else {  // grid -> coefficients
+    const double2* g = reinterpret_cast<const double2*>(in + (size_t)b * M);
+    for (int j = threadIdx.x; j < L; j += blockDim.x) s.A[j] = g[j];
+    __syncthreads();
+    double2* y = row(out, b, K);
+    if (kind == 1) {
+      const double invM = 1.0 / M;
+      g2c_packed(P, s.A, s.B, s.O, [&](int k, double2 v) { return cscale(v, invM); });
+    } else {
+      g2c_packed(P, s.A, s.B, s.O, [&](int k, double2 v) {
+        return k == 0 ? make_double2(v.x, 0.0) : cscale(v, 2.0);
+      });
+    }
+    for (int k = threadIdx.x; k < K; k += blockDim.x) y[k] = s.O[k];
+  }
+}
+
+__global__ void F_kernel(BurgersParams P, int mode, const double* __restrict__ x, const double* __restrict__ d,
+                         double* __restrict__ out) {
+  Smem s = carve(P);
+  extern __shared__ double2 sm[];
+  double2* S2 = sm + 4 * P.L + 2 * P.K;  // second input spectrum (JVP direction / VJP cotangent)
+  double2* O2 = S2 + P.K;                // second output spectrum
+  const int b = blockIdx.x, K = P.K;
+  const double2* xr = row(x, b, K);
+  double2* o = row(out, b, K);
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    s.S[k] = xr[k];
+    if (mode != 0) S2[k] = row(d, b, K)[k];
+  }
+  __syncthreads();
+  if (!P.nonlinear) {
+    for (int k = threadIdx.x; k < K; k += blockDim.x) o[k] = make_double2(0.0, 0.0);
+    return;
+  }
+  if (mode == 0) {
+    eval_F(P, s);
+    for (int k = threadIdx.x; k < K; k += blockDim.x) o[k] = s.O[k];
+  } else if (mode == 1) {
+    eval_F_and_jvp(P, s, S2, O2, false);
+    for (int k = threadIdx.x; k < K; k += blockDim.x) o[k] = O2[k];
+  } else {
+    eval_vjp(P, s, S2);
+    for (int k = threadIdx.x; k < K; k += blockDim.x) o[k] = s.O[k];
+  }
+}
+
+// ---- persistent trajectory kernels ----------------------------------------------------------
+
+struct Coef {
+  double a0, a1, a2, c1, c2;
+};
+__device__ __forceinline__ Coef step_coef(const BurgersParams& P, int n) {
+  Coef c;
+  if (n <= 1 || P.order == 1) {
+    c.a0 = 1.0 / P.dt; c.a1 = -1.0 / P.dt; c.a2 = 0.0; c.c1 = 1.0; c.c2 = 0.0;
+  } else {
+    c.a0 = 1.5 / P.dt; c.a1 = -2.0 / P.dt; c.a2 = 0.5 / P.dt; c.c1 = 2.0; c.c2 = -1.0;
+  }
+  return c;
+}
+
+__device__ __forceinline__ double2 axpby(double a, double2 x, double b, double2 y) {
+  return make_double2(fma(a, x.x, b * y.x), fma(a, x.y, b * y.y));
+}
+
+// mode 0: forward (optionally storing traj), mode 1: tangent.
+template <int Q>
+__global__ void __launch_bounds__(64) trajectory_kernel(BurgersParams P, int n_steps, const double* __restrict__ x0,
+                                                        const double* __restrict__ dx0, double* __restrict__ x_out,
+                                                        double* __restrict__ traj, int tangent) {
+  Smem s = carve(P);
+  extern __shared__ double2 sm[];
+  double2* S2 = sm + 4 * P.L + 2 * P.K;
+  double2* O2 = S2 + P.K;
+  const int b = blockIdx.x, K = P.K, G = blockDim.x, tid = threadIdx.x;
+  const int nb = gridDim.x;
+  double2 X1[Q], X2[Q], F1[Q], F2[Q], D1[Q], D2[Q], G1[Q], G2[Q];
+  const double2* xr = row(x0, b, K);
+  for (int q = 0; q < Q; ++q) {
+    int k = tid + q * G;
+    double2 z = make_double2(0.0, 0.0);
+    X1[q] = (k < K) ? xr[k] : z;
+    X2[q] = z; F1[q] = z; F2[q] = z;
+    D1[q] = z; D2[q] = z; G1[q] = z; G2[q] = z;
+    if (tangent && k < K) D1[q] = row(dx0, b, K)[k];
+    if (k < K) {
+      s.S[k] = X1[q];
+      if (tangent) S2[k] = D1[q];
+      if (traj) row(traj, b, K)[k] = X1[q];
+    }
+  }
+  __syncthreads();
+  if (P.nonlinear) {
+    if (tangent) eval_F_and_jvp(P, s, S2, O2, true);
+    else eval_F(P, s);
+    for (int q = 0; q < Q; ++q) {
+      int k = tid + q * G;
+      if (k < K) { F1[q] = s.O[k]; if (tangent) G1[q] = O2[k]; }
+    }
+  }
+  for (int n = 1; n <= n_steps; ++n) {
+    Coef c = step_coef(P, n);
+    for (int q = 0; q < Q; ++q) {
+      int k = tid + q * G;
+      if (k >= K) continue;
+      double kk = kwav(P, k);
+      double inv = 1.0 / (c.a0 + P.nu * kk * kk);
+      double2 r = axpby(c.c1, F1[q], -c.a1, X1[q]);
+      if (c.c2 != 0.0) r = make_double2(r.x + c.c2 * F2[q].x - c.a2 * X2[q].x, r.y + c.c2 * F2[q].y - c.a2 * X2[q].y);
+      double2 xn = cscale(r, inv);
+      if (k == 0) xn.y = 0.0;
+      X2[q] = X1[q]; X1[q] = xn; F2[q] = F1[q];
+      s.S[k] = xn;
+      if (traj) row(traj + (size_t)n * nb * 2 * K, b, K)[k] = xn;
+      if (tangent) {
+        double2 rd = axpby(c.c1, G1[q], -c.a1, D1[q]);
+        if (c.c2 != 0.0) rd = make_double2(rd.x + c.c2 * G2[q].x - c.a2 * D2[q].x, rd.y + c.c2 * G2[q].y - c.a2 * D2[q].y);
+        double2 dn = cscale(rd, inv);
+        if (k == 0) dn.y = 0.0;
+        D2[q] = D1[q]; D1[q] = dn; G2[q] = G1[q];
+        S2[k] = dn;
+      }
+    }
+    __syncthreads();
+    if (n < n_steps && P.nonlinear) {
+      if (tangent) eval_F_and_jvp(P, s, S2, O2, true);
+      else eval_F(P, s);
+      for (int q = 0; q < Q; ++q) {
+        int k = tid + q * G;
+        if (k < K) { F1[q] = s.O[k]; if (tangent) G1[q] = O2[k]; }
+      }
+    }
+  }
+  double2* o = row(x_out, b, K);
+  for (int q = 0; q < Q; ++q) {
+    int k = tid + q * G;
+    if (k < K) o[k] = tangent ? D1[q] : X1[q];
+  }
+}
+
+// Adjoint sweep (eq. IMEX_adjoint) over traj = X_0..X_N, seeded by y_final = dJ/dX_N.
+template <int Q>
+__global__ void __launch_bounds__(64) adjoint_kernel(BurgersParams P, int n_steps, const double* __restrict__ traj,
+                                                     const double* __restrict__ y_final, double* __restrict__ grad) {
+  Smem s = carve(P);
+  extern __shared__ double2 sm[];
+  double2* S2 = sm + 4 * P.L + 2 * P.K;
+  const int b = blockIdx.x, K = P.K, G = blockDim.x, tid = threadIdx.x;
+  const int nb = gridDim.x;
+  const size_t stride = (size_t)nb * 2 * K;
+  double2 Y1[Q], Y2[Q];
+  const double2 z = make_double2(0.0, 0.0);
+  for (int q = 0; q < Q; ++q) { Y1[q] = z; Y2[q] = z; }
+  for (int n = n_steps; n >= 0; --n) {
+    double2 lam[Q];
+    if (n == n_steps) {
+      for (int q = 0; q < Q; ++q) {
+        int k = tid + q * G;
+        lam[q] = (k < K) ? row(y_final, b, K)[k] : z;
+      }
+    } else {
+      Coef c1 = step_coef(P, n + 1);
+      Coef c2 = (n + 2 <= n_steps) ? step_coef(P, n + 2) : Coef{0, 0, 0, 0, 0};
+      const double2* xn = row(traj + (size_t)n * stride, b, K);
+      for (int q = 0; q < Q; ++q) {
+        int k = tid + q * G;
+        if (k >= K) continue;
+        s.S[k] = xn[k];
+        S2[k] = axpby(c1.c1, Y1[q], c2.c2, Y2[q]);
+      }
+      __syncthreads();
+      if (P.nonlinear) eval_vjp(P, s, S2);
+      for (int q = 0; q < Q; ++q) {
+        int k = tid + q * G;
+        if (k >= K) { lam[q] = z; continue; }
+        double2 v = P.nonlinear ? s.O[k] : z;
+        lam[q] = make_double2(v.x - c1.a1 * Y1[q].x - c2.a2 * Y2[q].x, v.y - c1.a1 * Y1[q].y - c2.a2 * Y2[q].y);
+      }
+      __syncthreads();
+    }
+    if (n == 0) {
+      double2* g = row(grad, b, K);
+      for (int q = 0; q < Q; ++q) {
+        int k = tid + q * G;
+        if (k < K) g[k] = lam[q];
+      }
+      return;
+    }
+    Coef c = step_coef(P, n);
+    for (int q = 0; q < Q; ++q) {
+      int k = tid + q * G;
+      if (k >= K) continue;
+      double kk = kwav(P, k);
+      double2 y = cscale(lam[q], 1.0 / (c.a0 + P.nu * kk * kk));
+      if (k == 0) y.y = 0.0;
+      Y2[q] = Y1[q];
+      Y1[q] = y;
+    }
+  }
+}
+
+// J_b = (length/2)(Re c_0^2 + 2 sum_{k>=1} |c_k|^2) and seed y = dJ/dX.
+__global__ void energy_kernel(BurgersParams P, const double* __restrict__ x, double* __restrict__ J,
+                              double* __restrict__ seed) {
+  const int b = blockIdx.x, K = P.K;
+  const double2* xr = row(x, b, K);
+  double2* y = row(seed, b, K);
+  double acc = 0.0;
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    double2 v = xr[k];
+    if (k == 0) {
+      acc += v.x * v.x;
+      y[k] = make_double2(P.length * v.x, 0.0);
+    } else {
+      acc += 2.0 * (v.x * v.x + v.y * v.y);
+      y[k] = make_double2(2.0 * P.length * v.x, 2.0 * P.length * v.y);
+    }
+  }
+  __shared__ double red[128];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) J[b] = 0.5 * P.length * red[0];
+}
+
+// ---- host side --------------------------------------------------------------------------------
+
+struct Burgers : EqImpl {
+  BurgersParams P{};
+  int B = 1;
+  int G = 64;
+  DevBuf wm, traj, seed, Jd;
+  size_t smem = 0;
+
+  size_t state_len(int which) const override {
+    if (which == 0) return (size_t)B * 2 * P.K;
+    if (which == 1) return (size_t)B * P.M;
+    return 0;
+  }
+
+  spadj_status init(Problem* p) {
+    const spadj_desc& d = p->desc;
+    if (d.n[0] < 4 || d.n[0] % 4 != 0) return p->fail(SPADJ_ERR_INVALID, "burgers: n[0] must be a positive multiple of 4");
+    B = d.batch;
+    P.K = d.n[0] / 2;
+    P.M = 3 * d.n[0] / 2;
+    P.L = P.M / 2;
+    P.length = d.length[0] > 0 ? d.length[0] : 2.0 * M_PI;
+    P.kscale = 2.0 * M_PI / P.length;
+    P.nu = d.params[0];
+    P.dt = d.dt;
+    P.order = d.scheme == SPADJ_SBDF1 ? 1 : 2;
+    if (d.scheme != SPADJ_SBDF1 && d.scheme != SPADJ_SBDF2)
+      return p->fail(SPADJ_ERR_UNSUPPORTED, "burgers: scheme must be SBDF1 or SBDF2");
+    P.nonlinear = d.nonlinear;
+    P.plan = make_plan(P.L);
+    if (P.plan.nrad < 0) return p->fail(SPADJ_ERR_INVALID, "burgers: 3N/4 must be of the form 2^a 3^b");
+    if (P.K > kQMax * G) return p->fail(SPADJ_ERR_INVALID, "burgers: n[0] too large (max 512)");
+    std::vector<double2> h(P.M);
+    for (int m = 0; m < P.M; ++m) {
+      double th = -2.0 * M_PI * (double)m / (double)P.M;
+      h[m] = make_double2(std::cos(th), std::sin(th));
+    }
+    SPADJ_CUDA_TRY(p, wm.ensure(sizeof(double2) * P.M));
+    SPADJ_CUDA_TRY(p, cudaMemcpyAsync(wm.ptr, h.data(), sizeof(double2) * P.M, cudaMemcpyHostToDevice, p->stream));
+    SPADJ_CUDA_TRY(p, cudaStreamSynchronize(p->stream));
+    P.WM = wm.as<double2>();
+    smem = sizeof(double2) * (4 * P.L + 4 * P.K);
+    return SPADJ_OK;
+  }
+
+  spadj_status transform(Problem* p, int kind, const double* in, double* out) override {
+    if (kind < 0 || kind > 3) return p->fail(SPADJ_ERR_INVALID, "transform: kind must be 0..3");
+    transform_kernel<<<B, G, smem, p->stream>>>(P, kind, in, out);
+    return check_launch(p, "burgers transform");
+  }
+
+  spadj_status eval_F(Problem* p, int mode, const double* x, const double* dx, double* out) override {
+    F_kernel<<<B, G, smem, p->stream>>>(P, mode, x, dx, out);
+    return check_launch(p, "burgers F");
+  }
+
+  template <class Fn>
+  spadj_status dispatchQ(Problem* p, Fn fn) {
+    int Q = (P.K + G - 1) / G;
+    if (Q <= 1) fn(std::integral_constant<int, 1>());
+    else if (Q == 2) fn(std::integral_constant<int, 2>());
+    else fn(std::integral_constant<int, 4>());
+    return check_launch(p, "burgers trajectory");
+  }
+
+  spadj_status forward(Problem* p, int n_steps, const double* x0, double* x_out, double* trj) override {
+    if (n_steps < 0) return p->fail(SPADJ_ERR_INVALID, "forward: n_steps < 0");
+    return dispatchQ(p, [&](auto q) {
+      trajectory_kernel<decltype(q)::value><<<B, G, smem, p->stream>>>(P, n_steps, x0, nullptr, x_out, trj, 0);
+    });
+  }
+
+  spadj_status tangent(Problem* p, int n_steps, const double* x0, const double* dx0, double* dx_out) override {
+    if (n_steps < 0) return p->fail(SPADJ_ERR_INVALID, "tangent: n_steps < 0");
+    return dispatchQ(p, [&](auto q) {
+      trajectory_kernel<decltype(q)::value><<<B, G, smem, p->stream>>>(P, n_steps, x0, dx0, dx_out, nullptr, 1);
+    });
+  }
+
+  spadj_status adjoint(Problem* p, int n_steps, const double* trj, const double* y_final, double* grad) override {
+    if (n_steps < 1) return p->fail(SPADJ_ERR_INVALID, "adjoint: n_steps < 1");
+    return dispatchQ(p, [&](auto q) {
+      adjoint_kernel<decltype(q)::value><<<B, G, smem, p->stream>>>(P, n_steps, trj, y_final, grad);
+    });
+  }
+
+  spadj_status objective(Problem* p, int objective, const double* obj_data, const double* x, double* J_dev,
+                         double* sd) override {
+    (void)obj_data;
+    if (objective != SPADJ_OBJ_ENERGY) return p->fail(SPADJ_ERR_UNSUPPORTED, "burgers: objective must be ENERGY");
+    energy_kernel<<<B, 128, 0, p->stream>>>(P, x, J_dev, sd);
+    return check_launch(p, "burgers energy");
+  }
+
+  spadj_status gradient(Problem* p, const double* x0, int n_steps, int objective, const double* obj_data,
+                        int ckpt_slots, double* J_host, double* grad, double* grad_p) override {
+    (void)obj_data; (void)ckpt_slots; (void)grad_p;
+    if (objective != SPADJ_OBJ_ENERGY) return p->fail(SPADJ_ERR_UNSUPPORTED, "burgers: objective must be ENERGY");
+    if (n_steps < 1) return p->fail(SPADJ_ERR_INVALID, "gradient: n_steps < 1");
+    const size_t sl = state_len(0);
+    SPADJ_CUDA_TRY(p, traj.ensure(sizeof(double) * sl * (size_t)(n_steps + 1)));
+    SPADJ_CUDA_TRY(p, seed.ensure(sizeof(double) * sl));
+    SPADJ_CUDA_TRY(p, Jd.ensure(sizeof(double) * B));
+    double* T = traj.as<double>();
+    double* xN = T + (size_t)n_steps * sl;
+    spadj_status st = forward(p, n_steps, x0, xN, T);
+    if (st != SPADJ_OK) return st;
+    if ((st = this->objective(p, objective, obj_data, xN, Jd.as<double>(), seed.as<double>())) != SPADJ_OK) return st;
+    st = adjoint(p, n_steps, T, seed.as<double>(), grad);
+    if (st != SPADJ_OK) return st;
+    if (J_host) {
+      SPADJ_CUDA_TRY(p, cudaMemcpyAsync(J_host, Jd.ptr, sizeof(double) * B, cudaMemcpyDeviceToHost, p->stream));
+      SPADJ_CUDA_TRY(p, cudaStreamSynchronize(p->stream));
+      for (int i = 0; i < B; ++i)
+        if (!std::isfinite(J_host[i])) return p->fail(SPADJ_ERR_NONFINITE, "burgers: objective is not finite");
+    }
+    return SPADJ_OK;
+  }
+
+  ~Burgers() override {
+    wm.release();
+    traj.release();
+    seed.release();
+    Jd.release();
+  }
+};
+
+}  // namespace
+
+EqImpl* make_burgers(Problem* p, spadj_status* st) {
+  Burgers* b = new Burgers();
+  *st = b->init(p);
+  if (*st != SPADJ_OK) {
+    delete b;
+    return nullptr;
+  }
+  return b;
+}
+
+}  // namespace spadj

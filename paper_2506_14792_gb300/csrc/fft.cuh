@@ -1,0 +1,145 @@
+// FP64 shared-memory FFTs for the collocation transforms (Methods, "Spectral transforms").
+//
+// A real field of M = 2L grid points is transformed through one complex FFT of length
+// L on the packed sequence z_j = g_{2j} + i g_{2j+1} (the classic half-length real FFT),
+// so a 3/2-dealiased grid of 384 points costs one 192-point complex FFT.  The complex
+// FFT is a Stockham autosort (ping-pong between two shared buffers, natural order in
+// and out) with radix-4/3/2 passes; all threads of the CTA take part and every pass
+// ends with a CTA barrier.  Twiddles come from a device table
+//   WM[m] = exp(-2 pi i m / M),  m = 0..M-1,
+// whose even entries are the L-point twiddles exp(-2 pi i m / L).
+#pragma once
+#include <cuda_runtime.h>
+
+namespace spadj {
+
+struct FFTPlan {
+  int n;        // complex length L
+  int nrad;     // number of passes
+  int rad[8];   // radix of each pass (product = n)
+};
+
+// Factor n = 2^a 3^b into radix-4 passes, then one radix-2 if a is odd, then radix-3.
+inline FFTPlan make_plan(int n) {
+  FFTPlan p{};
+  p.n = n;
+  int m = n;
+  while (m % 4 == 0) { p.rad[p.nrad++] = 4; m /= 4; }
+  if (m % 2 == 0) { p.rad[p.nrad++] = 2; m /= 2; }
+  while (m % 3 == 0) { p.rad[p.nrad++] = 3; m /= 3; }
+  if (m != 1) p.nrad = -1;  // unsupported length
+  return p;
+}
+
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
+__device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+// multiply by i*s (s = +-1)
+__device__ __forceinline__ double2 cmul_i(double2 a, double s) { return make_double2(-s * a.y, s * a.x); }
+
+// Twiddle exp(sign * 2 pi i m / L) from the M-table (M = 2L): entry 2m, conjugated for sign=+1.
+__device__ __forceinline__ double2 twL(const double2* __restrict__ WM, int m, int sign) {
+  double2 w = __ldg(&WM[2 * m]);
+  return sign > 0 ? cconj(w) : w;
+}
+
+// Complex FFT of length p.n held in buffer a (b is scratch of the same size).  sign = -1:
+// forward exp(-), sign = +1: inverse exp(+) (unnormalised).  Returns the buffer holding
+// the result (a or b).  All threads of the CTA must call it; it synchronises internally
+// and on return the result is visible to every thread.
+__device__ __noinline__ double2* cfft_smem(double2* a, double2* b, const FFTPlan p,
+                                           const double2* __restrict__ WM, int sign) {
+  const int n = p.n;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const double s = (double)sign;
+  int Ns = 1;
+  for (int pass = 0; pass < p.nrad; ++pass) {
+    const int R = p.rad[pass];
+    const int nb = n / R;
+    const int tstep = n / (Ns * R);  // twiddle index stride in L-units
+    for (int j = tid; j < nb; j += nt) {
+      const int k = j % Ns;
+      const int base = (j - k) * R + k;
+      if (R == 4) {
+        double2 v0 = a[j], v1 = a[j + nb], v2 = a[j + 2 * nb], v3 = a[j + 3 * nb];
+        if (k) {
+          v1 = cmul(v1, twL(WM, k * tstep, sign));
+          v2 = cmul(v2, twL(WM, 2 * k * tstep, sign));
+          v3 = cmul(v3, twL(WM, 3 * k * tstep, sign));
+        }
+        double2 t0 = cadd(v0, v2), t1 = csub(v0, v2), t2 = cadd(v1, v3);
+        double2 t3 = cmul_i(csub(v1, v3), s);
+        b[base] = cadd(t0, t2);
+        b[base + Ns] = cadd(t1, t3);
+        b[base + 2 * Ns] = csub(t0, t2);
+        b[base + 3 * Ns] = csub(t1, t3);
+      } else if (R == 2) {
+        double2 v0 = a[j], v1 = a[j + nb];
+        if (k) v1 = cmul(v1, twL(WM, k * tstep, sign));
+        b[base] = cadd(v0, v1);
+        b[base + Ns] = csub(v0, v1);
+      } else {  // R == 3
+        double2 v0 = a[j], v1 = a[j + nb], v2 = a[j + 2 * nb];
+        if (k) {
+          v1 = cmul(v1, twL(WM, k * tstep, sign));
+          v2 = cmul(v2, twL(WM, 2 * k * tstep, sign));
+        }
+        const double h = 0.86602540378443864676;  // sqrt(3)/2
+        double2 t = cadd(v1, v2);
+        double2 m = make_double2(fma(-0.5, t.x, v0.x), fma(-0.5, t.y, v0.y));
+        double2 d = cmul_i(csub(v1, v2), s * h);
+        b[base] = cadd(v0, t);
+        b[base + Ns] = cadd(m, d);
+        b[base + 2 * Ns] = csub(m, d);
+      }
+    }
+    __syncthreads();
+    double2* tmp = a; a = b; b = tmp;
+    Ns *= R;
+  }
+  return a;
+}
+
+// ---- real transforms on the packed half-length sequence ---------------------------------
+//
+// c2r: coefficients c_k (k < K, read through get(k)) of a real field, g_j = sum over the
+// Hermitian-completed spectrum with weights w0 (k = 0, real part only) and w (k >= 1):
+//   g_j = w0 Re c_0 + w * 2 Re sum_{k=1}^{K-1} c_k e^{2 pi i k j / M}
+// Fills Z (length L) so that the inverse L-point FFT of Z is z_j = g_{2j} + i g_{2j+1}.
+template <class Get>
+__device__ __forceinline__ void c2r_pre(double2* Z, Get get, int K, int L, const double2* __restrict__ WM,
+                                        double w0, double w) {
+  for (int k = threadIdx.x; k < L; k += blockDim.x) {
+    double2 xk = make_double2(0.0, 0.0), xc = make_double2(0.0, 0.0);
+    if (k == 0) {
+      xk = make_double2(w0 * get(0).x, 0.0);
+    } else if (k < K) {
+      xk = cscale(get(k), w);
+    }
+    const int kc = L - k;  // partner index (k = 0 pairs with the unstored Nyquist L)
+    if (k > 0 && kc < K) xc = cconj(cscale(get(kc), w));
+    double2 e = cadd(xk, xc);
+    double2 o = cmul(csub(xk, xc), cconj(__ldg(&WM[k])));  // * exp(+2 pi i k / M)
+    Z[k] = make_double2(e.x - o.y, e.y + o.x);            // e + i o
+  }
+}
+
+// r2c post: z = forward L-point FFT of the packed real field; returns
+//   X_k = sum_j g_j e^{-2 pi i k j / M}  for k < K  (via put(k, X_k)).
+template <class Put>
+__device__ __forceinline__ void r2c_post(const double2* Z, Put put, int K, int L, const double2* __restrict__ WM) {
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    double2 zk = Z[k];
+    double2 zc = cconj(Z[k == 0 ? 0 : L - k]);
+    double2 e = cscale(cadd(zk, zc), 0.5);
+    double2 d = csub(zk, zc);
+    double2 o = make_double2(0.5 * d.y, -0.5 * d.x);  // -i/2 (zk - zc)
+    put(k, cadd(e, cmul(o, __ldg(&WM[k]))));
+  }
+}
+
+}  // namespace spadj

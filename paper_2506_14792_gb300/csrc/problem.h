@@ -1,0 +1,88 @@
+// Internal problem object behind the opaque spadj_problem handle.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "spadj.h"
+
+namespace spadj {
+
+// Return an error status with a message recorded on the problem.
+#define SPADJ_CUDA_TRY(prob, expr)                                                        \
+  do {                                                                                   \
+    cudaError_t e_ = (expr);                                                             \
+    if (e_ != cudaSuccess) {                                                             \
+      (prob)->set_error(std::string(#expr) + ": " + cudaGetErrorString(e_));             \
+      return e_ == cudaErrorMemoryAllocation ? SPADJ_ERR_NOMEM : SPADJ_ERR_CUDA;         \
+    }                                                                                    \
+  } while (0)
+
+// Device buffer owned by the library (grown on demand, freed with the problem).
+struct DevBuf {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+  cudaError_t ensure(size_t nbytes) {
+    if (nbytes <= bytes) return cudaSuccess;
+    if (ptr) cudaFree(ptr);
+    ptr = nullptr;
+    bytes = 0;
+    cudaError_t e = cudaMalloc(&ptr, nbytes);
+    if (e == cudaSuccess) bytes = nbytes;
+    return e;
+  }
+  void release() {
+    if (ptr) cudaFree(ptr);
+    ptr = nullptr;
+    bytes = 0;
+  }
+  template <class T> T* as() const { return static_cast<T*>(ptr); }
+};
+
+struct Problem;
+
+// One equation set's implementation.  Every method runs asynchronously on prob->stream
+// unless it writes host memory.
+struct EqImpl {
+  virtual ~EqImpl() {}
+  virtual size_t state_len(int which) const = 0;
+  virtual spadj_status transform(Problem* p, int kind, const double* in, double* out) = 0;
+  virtual spadj_status eval_F(Problem* p, int mode, const double* x, const double* dx, double* out) = 0;
+  virtual spadj_status forward(Problem* p, int n_steps, const double* x0, double* x_out, double* traj) = 0;
+  virtual spadj_status tangent(Problem* p, int n_steps, const double* x0, const double* dx0, double* dx_out) = 0;
+  virtual spadj_status adjoint(Problem* p, int n_steps, const double* traj, const double* y_final,
+                               double* grad_x0) = 0;
+  virtual spadj_status objective(Problem* p, int objective, const double* obj_data, const double* x,
+                                 double* J_dev, double* seed) = 0;
+  virtual spadj_status gradient(Problem* p, const double* x0, int n_steps, int objective,
+                                const double* obj_data, int ckpt_slots, double* J_host, double* grad_x0,
+                                double* grad_p) = 0;
+};
+
+struct Problem {
+  spadj_desc desc{};
+  cudaStream_t stream = nullptr;
+  std::string err;
+  EqImpl* impl = nullptr;
+  void set_error(const std::string& s) { err = s; }
+  spadj_status fail(spadj_status st, const std::string& s) {
+    err = s;
+    return st;
+  }
+};
+
+// Launch-error check after a kernel launch.
+inline spadj_status check_launch(Problem* p, const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return p->fail(SPADJ_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  return SPADJ_OK;
+}
+
+// Factories (one per equation set).
+EqImpl* make_burgers(Problem* p, spadj_status* st);
+
+}  // namespace spadj
+
+struct spadj_problem : public spadj::Problem {};

@@ -1,0 +1,198 @@
+"""ctypes binding of the C-ABI in include/spadj.h (argument marshalling only).
+
+Every function of the header is exposed under the same name and takes raw device
+pointers, as the C-ABI does; ``Problem`` is a small convenience wrapper that takes
+torch CUDA tensors (float64 or complex128), checks their sizes and passes their
+pointers.  All arithmetic runs in the CUDA kernels of libspadj.so.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libspadj.so")
+
+SPADJ_OK = 0
+SPADJ_ERR_INVALID = -1
+SPADJ_ERR_NOMEM = -2
+SPADJ_ERR_CUDA = -3
+SPADJ_ERR_NONFINITE = -4
+SPADJ_ERR_TIMEOUT = -5
+SPADJ_ERR_UNSUPPORTED = -6
+
+SPADJ_BURGERS1D = 0
+SPADJ_RB2D = 1
+SPADJ_KOLMOGOROV2D = 2
+
+SPADJ_SBDF1 = 1
+SPADJ_SBDF2 = 2
+SPADJ_RK222 = 3
+
+SPADJ_OBJ_ENERGY = 0
+
+C2G, G2C, C2G_ADJ, G2C_ADJ = 0, 1, 2, 3
+
+
+class SpadjError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("spadj status %d: %s" % (status, msg))
+        self.status = status
+
+
+class spadj_desc(ctypes.Structure):
+    _fields_ = [("eq", ctypes.c_int), ("scheme", ctypes.c_int), ("n", ctypes.c_int * 3),
+                ("length", ctypes.c_double * 3), ("params", ctypes.c_double * 4), ("dt", ctypes.c_double),
+                ("batch", ctypes.c_int), ("nonlinear", ctypes.c_int)]
+
+
+_lib = None
+_vp = ctypes.c_void_p
+_SIGS = {
+    "spadj_create": (ctypes.c_int, [ctypes.POINTER(spadj_desc), _vp, ctypes.POINTER(_vp)]),
+    "spadj_destroy": (ctypes.c_int, [_vp]),
+    "spadj_state_len": (ctypes.c_size_t, [_vp, ctypes.c_int]),
+    "spadj_transform": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp]),
+    "spadj_eval_F": (ctypes.c_int, [_vp, _vp, _vp]),
+    "spadj_eval_F_jvp": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "spadj_eval_F_vjp": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "spadj_forward": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp]),
+    "spadj_tangent": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp]),
+    "spadj_adjoint": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp]),
+    "spadj_objective": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp, _vp]),
+    "spadj_gradient": (ctypes.c_int, [_vp, _vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int, _vp, _vp, _vp]),
+    "spadj_last_error": (ctypes.c_char_p, [_vp]),
+}
+
+
+def lib():
+    """Load libspadj.so (raises if it has not been built: there is no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libspadj.so is not built (run paper_2506_14792_gb300.build.build())")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _chk(handle, st):
+    if st != SPADJ_OK:
+        raise SpadjError(st, lib().spadj_last_error(handle).decode())
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _as_f64(t, n, name):
+    import torch
+    if t.is_complex():
+        t = torch.view_as_real(t)
+    if t.dtype != torch.float64 or not t.is_cuda or not t.is_contiguous():
+        raise ValueError("%s must be a contiguous float64/complex128 CUDA tensor" % name)
+    if n is not None and t.numel() != n:
+        raise ValueError("%s has %d float64 elements, expected %d" % (name, t.numel(), n))
+    return t
+
+
+class Problem:
+    """Owns one spadj_problem; methods take torch CUDA tensors."""
+
+    def __init__(self, eq, scheme, n, length, params, dt, batch=1, nonlinear=True, stream=None):
+        import torch
+        d = spadj_desc()
+        d.eq, d.scheme = eq, scheme
+        for i, v in enumerate(list(n)[:3]):
+            d.n[i] = int(v)
+        for i, v in enumerate(list(length)[:3]):
+            d.length[i] = float(v)
+        for i, v in enumerate(list(params)[:4]):
+            d.params[i] = float(v)
+        d.dt, d.batch, d.nonlinear = float(dt), int(batch), int(bool(nonlinear))
+        self.desc = d
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        h = ctypes.c_void_p()
+        st = lib().spadj_create(ctypes.byref(d), ctypes.c_void_p(stream.cuda_stream), ctypes.byref(h))
+        _chk(None, st)
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().spadj_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def state_len(self, which=0):
+        return int(lib().spadj_state_len(self.h, which))
+
+    def transform(self, kind, inp, out):
+        nin = self.state_len(0 if kind in (C2G, G2C_ADJ) else 1)
+        nout = self.state_len(1 if kind in (C2G, G2C_ADJ) else 0)
+        _chk(self.h, lib().spadj_transform(self.h, kind, _ptr(_as_f64(inp, nin, "in")), _ptr(_as_f64(out, nout, "out"))))
+        return out
+
+    def eval_F(self, x, f):
+        n = self.state_len(0)
+        _chk(self.h, lib().spadj_eval_F(self.h, _ptr(_as_f64(x, n, "x")), _ptr(_as_f64(f, n, "f"))))
+        return f
+
+    def eval_F_jvp(self, x, dx, df):
+        n = self.state_len(0)
+        _chk(self.h, lib().spadj_eval_F_jvp(self.h, _ptr(_as_f64(x, n, "x")), _ptr(_as_f64(dx, n, "dx")),
+                                             _ptr(_as_f64(df, n, "df"))))
+        return df
+
+    def eval_F_vjp(self, x, y, out):
+        n = self.state_len(0)
+        _chk(self.h, lib().spadj_eval_F_vjp(self.h, _ptr(_as_f64(x, n, "x")), _ptr(_as_f64(y, n, "y")),
+                                             _ptr(_as_f64(out, n, "out"))))
+        return out
+
+    def forward(self, n_steps, x0, x_out, traj=None):
+        n = self.state_len(0)
+        tp = None if traj is None else _ptr(_as_f64(traj, n * (n_steps + 1), "traj"))
+        _chk(self.h, lib().spadj_forward(self.h, n_steps, _ptr(_as_f64(x0, n, "x0")), _ptr(_as_f64(x_out, n, "x_out")), tp))
+        return x_out
+
+    def tangent(self, n_steps, x0, dx0, dx_out):
+        n = self.state_len(0)
+        _chk(self.h, lib().spadj_tangent(self.h, n_steps, _ptr(_as_f64(x0, n, "x0")), _ptr(_as_f64(dx0, n, "dx0")),
+                                          _ptr(_as_f64(dx_out, n, "dx_out"))))
+        return dx_out
+
+    def adjoint(self, n_steps, traj, y_final, grad_x0):
+        n = self.state_len(0)
+        _chk(self.h, lib().spadj_adjoint(self.h, n_steps, _ptr(_as_f64(traj, n * (n_steps + 1), "traj")),
+                                          _ptr(_as_f64(y_final, n, "y_final")), _ptr(_as_f64(grad_x0, n, "grad_x0"))))
+        return grad_x0
+
+    def objective(self, x, J_dev, seed, objective=SPADJ_OBJ_ENERGY, obj_data=None):
+        n = self.state_len(0)
+        _chk(self.h, lib().spadj_objective(self.h, objective, _ptr(obj_data), _ptr(_as_f64(x, n, "x")),
+                                            _ptr(_as_f64(J_dev, self.desc.batch, "J_dev")),
+                                            _ptr(_as_f64(seed, n, "seed"))))
+        return J_dev
+
+    def gradient(self, x0, n_steps, grad_x0, objective=SPADJ_OBJ_ENERGY, obj_data=None, ckpt_slots=0,
+                 grad_p=None):
+        """Returns J per batch member (numpy, host) and fills grad_x0."""
+        n = self.state_len(0)
+        J = np.zeros(self.desc.batch, dtype=np.float64)
+        _chk(self.h, lib().spadj_gradient(self.h, _ptr(_as_f64(x0, n, "x0")), n_steps, objective,
+                                           _ptr(obj_data), ckpt_slots, J.ctypes.data_as(ctypes.c_void_p),
+                                           _ptr(_as_f64(grad_x0, n, "grad_x0")), _ptr(grad_p)))
+        return J

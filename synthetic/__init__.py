@@ -12,10 +12,13 @@ def burgers_ic(N, batch=1, seed=1, nmodes=16, length=2.0 * np.pi):
     """Half-spectrum coefficients (batch, N//2) complex of
     u0(x) = sum_{k=1..16} k^-2 (a_k cos kx + b_k sin kx), a_k, b_k ~ N(0,1),
     scaled so that max_x |u0| = 1 (maximum taken on a 1024-point sample grid).
+    For N/2 <= 16 only the modes k < N/2 are kept.
     """
     K = N // 2
     rng = np.random.default_rng(seed)
     ab = rng.standard_normal((batch, nmodes, 2))
+    nmodes = min(nmodes, K - 1)  # small test sizes keep the modes they can hold
+    ab = ab[:, :nmodes]
     k = np.arange(1, nmodes + 1)
     c = np.zeros((batch, K), dtype=np.complex128)
     c[:, 1:nmodes + 1] = (ab[:, :, 0] - 1j * ab[:, :, 1]) * (0.5 / k ** 2)
