@@ -37,3 +37,22 @@ def random_coeffs(shape, seed, scale=1.0):
     """Complex N(0, scale^2) coefficients (used for test directions and cotangents)."""
     rng = np.random.default_rng(seed)
     return scale * (rng.standard_normal(shape) + 1j * rng.standard_normal(shape))
+
+
+def rb_ic(Nx, Nz, seed=2, amp=1e-3):
+    """Rayleigh-Benard initial state (3, Nx/2, Nz) complex: u = w = 0 and a temperature
+    perturbation theta = amp * sum a_{m,n} phi_n(z) e^{i kx_m x} with N(0,1) draws a_{m,n},
+    phi_n = T_{n+2} - T_n (vanishing at both walls), a (1 + n)^-2 (1 + m)^-1 envelope and
+    Hermitian-consistent mean pencil (real coefficients at m = 0)."""
+    K = Nx // 2
+    rng = np.random.default_rng(seed)
+    a = rng.standard_normal((K, Nz - 2)) + 1j * rng.standard_normal((K, Nz - 2))
+    a[0] = a[0].real
+    env = 1.0 / ((1.0 + np.arange(Nz - 2))[None, :] ** 2 * (1.0 + np.arange(K))[:, None])
+    a *= env
+    th = np.zeros((K, Nz), dtype=np.complex128)
+    th[:, 2:] += a
+    th[:, :Nz - 2] -= a
+    s = np.zeros((3, K, Nz), dtype=np.complex128)
+    s[2] = amp * th
+    return s
