@@ -53,8 +53,15 @@ typedef enum {
  *   K = N/2 complex coefficients c_k (k = 0..K-1; Nyquist not stored; Im c_0 held at 0).
  *   Layout [B][K] complex.  Grid layout [B][3N/2] real.  params[0] = nu.
  *
- * SPADJ_RB2D: Boussinesq convection, Fourier(x) x Chebyshev(z) with tau terms
- *   (Sparse spectral methods section); see rb layout note in the design notes.
+ * SPADJ_RB2D: Boussinesq convection in free-fall units, buoyancy b = 1 - z + theta,
+ *   x in [0, length[0]) periodic Fourier (Nx = n[0] modes), z in [0, 1] Chebyshev-T
+ *   (N = n[1] modes) with tau terms; equations projected on the ultraspherical C^(2)
+ *   (momentum, temperature) and C^(1) (continuity) bases, no-slip, fixed temperature
+ *   (Sparse spectral methods section).  params[0] = Ra, params[1] = Pr (nu = (Ra/Pr)^-1/2,
+ *   kappa = (Ra Pr)^-1/2).  Scheme RK222.  State: u, w, theta coefficients, layout
+ *   [3][Nx/2][N] complex (x-mode m = 0..Nx/2-1, Nyquist not stored; the m = 0 pencil is
+ *   held real).  Grid layout [3N/2][3Nx/2] real (Gauss-Chebyshev z rows, uniform x).
+ *   Pressure and tau variables are internal to the stage solves.
  */
 typedef enum {
   SPADJ_BURGERS1D = 0,
@@ -88,7 +95,8 @@ spadj_status spadj_destroy(spadj_problem* prob);
 
 /* Lengths in float64 elements for the whole batch:
  * which = 0: coefficient state (the vector the gradient is taken with respect to);
- * which = 1: one real grid field;  which = 2: parameter vector p. */
+ * which = 1: one real grid field;  which = 2: parameter vector p;
+ * which = 3: one scalar coefficient field (the input/output of spadj_transform). */
 size_t spadj_state_len(const spadj_problem* prob, int which);
 
 /* Collocation transforms (Methods, "Spectral transforms"): kind
@@ -105,6 +113,19 @@ spadj_status spadj_transform(spadj_problem* prob, int kind, const double* in, do
 spadj_status spadj_eval_F(spadj_problem* prob, const double* x, double* f);
 spadj_status spadj_eval_F_jvp(spadj_problem* prob, const double* x, const double* dx, double* df);
 spadj_status spadj_eval_F_vjp(spadj_problem* prob, const double* x, const double* y, double* out);
+
+/* Stage solve of the sparse pencil systems (Methods, "Linear system solves"), defined for
+ * SPADJ_RB2D: x = prognostic part of (M + dt*gamma*L)^-1 [S1S0 v; 0] per x-mode pencil,
+ * v and x in the state layout (T coefficients).  transpose = 1 applies the adjoint map
+ * (Hermitian transpose, reusing the same factorisation).  SPADJ_ERR_UNSUPPORTED otherwise. */
+spadj_status spadj_solve(spadj_problem* prob, int transpose, const double* v, double* x);
+
+/* Binomial checkpoint schedule used by spadj_gradient (host only, no GPU needed): for
+ * n_steps steps and `slots` state slots (slot 0 = initial state) writes n_ops actions of
+ * 4 ints (type, a, b, slot) to ops (host) if ops != NULL and max_ops suffices.  Types:
+ * 0 advance a->b, 1 store state a in slot, 2 restore state a from slot, 3 adjoint of step a
+ * (state X_a current), 4 free slot, 5 evaluate the objective at state a. */
+spadj_status spadj_checkpoint_schedule(int n_steps, int slots, int* ops, int max_ops, int* n_ops);
 
 /* Forward trajectory of n_steps IMEX steps from x0 (eq. imex / RK stage equation).
  * x_out receives X_N.  traj (nullable) receives X_0..X_N, layout [n_steps+1][state]. */

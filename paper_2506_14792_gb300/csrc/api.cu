@@ -3,8 +3,10 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "problem.h"
+#include "revolve.h"
 
 using spadj::Problem;
 
@@ -36,6 +38,7 @@ spadj_status spadj_create(const spadj_desc* desc, void* cuda_stream, spadj_probl
   spadj_status st = SPADJ_ERR_UNSUPPORTED;
   switch (desc->eq) {
     case SPADJ_BURGERS1D: p->impl = spadj::make_burgers(p, &st); break;
+    case SPADJ_RB2D: p->impl = spadj::make_rb(p, &st); break;
     default: p->err = "spadj_create: unknown equation set"; break;
   }
   if (st != SPADJ_OK || !p->impl) {
@@ -83,6 +86,34 @@ spadj_status spadj_eval_F_vjp(spadj_problem* p, const double* x, const double* y
   if (!p) return SPADJ_ERR_INVALID;
   if (bad_ptr(x) || bad_ptr(y) || bad_ptr(out)) return p->fail(SPADJ_ERR_INVALID, "eval_F_vjp: NULL array");
   return p->impl->eval_F(p, 2, x, y, out);
+}
+
+spadj_status spadj_solve(spadj_problem* p, int transpose, const double* v, double* x) {
+  if (!p) return SPADJ_ERR_INVALID;
+  if (bad_ptr(v) || bad_ptr(x)) return p->fail(SPADJ_ERR_INVALID, "solve: NULL array");
+  return spadj::rb_pencil_solve(p->impl, p, transpose, v, x);
+}
+
+spadj_status spadj_checkpoint_schedule(int n_steps, int slots, int* ops, int max_ops, int* n_ops) {
+  if (n_steps < 1 || slots < 1 || !n_ops) {
+    g_create_error = "checkpoint_schedule: need n_steps >= 1, slots >= 1, n_ops != NULL";
+    return SPADJ_ERR_INVALID;
+  }
+  spadj::CkptPlanner planner;
+  std::vector<spadj::CkptOp> plan = planner.plan(n_steps, slots > n_steps + 1 ? n_steps + 1 : slots);
+  *n_ops = (int)plan.size();
+  if (!ops) return SPADJ_OK;
+  if ((int)plan.size() > max_ops) {
+    g_create_error = "checkpoint_schedule: max_ops too small";
+    return SPADJ_ERR_INVALID;
+  }
+  for (size_t i = 0; i < plan.size(); ++i) {
+    ops[4 * i + 0] = plan[i].type;
+    ops[4 * i + 1] = plan[i].a;
+    ops[4 * i + 2] = plan[i].b;
+    ops[4 * i + 3] = plan[i].slot;
+  }
+  return SPADJ_OK;
 }
 
 spadj_status spadj_forward(spadj_problem* p, int n_steps, const double* x0, double* x_out, double* traj) {

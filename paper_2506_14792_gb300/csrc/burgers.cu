@@ -390,6 +390,7 @@ struct Burgers : EqImpl {
   size_t state_len(int which) const override {
     if (which == 0) return (size_t)B * 2 * P.K;
     if (which == 1) return (size_t)B * P.M;
+    if (which == 3) return (size_t)B * 2 * P.K;
     return 0;
   }
 

@@ -51,7 +51,7 @@ __device__ __forceinline__ double2 twL(const double2* __restrict__ WM, int m, in
 // forward exp(-), sign = +1: inverse exp(+) (unnormalised).  Returns the buffer holding
 // the result (a or b).  All threads of the CTA must call it; it synchronises internally
 // and on return the result is visible to every thread.
-__device__ __noinline__ double2* cfft_smem(double2* a, double2* b, const FFTPlan p,
+static __device__ __noinline__ double2* cfft_smem(double2* a, double2* b, const FFTPlan p,
                                            const double2* __restrict__ WM, int sign) {
   const int n = p.n;
   const int tid = threadIdx.x, nt = blockDim.x;

@@ -82,6 +82,8 @@ inline spadj_status check_launch(Problem* p, const char* what) {
 
 // Factories (one per equation set).
 EqImpl* make_burgers(Problem* p, spadj_status* st);
+EqImpl* make_rb(Problem* p, spadj_status* st);
+spadj_status rb_pencil_solve(EqImpl* impl, Problem* p, int transpose, const double* v, double* x);
 
 }  // namespace spadj
 

@@ -1,0 +1,593 @@
+// 2D Rayleigh-Benard convection: RK222 IMEX forward step, tangent step and exact discrete
+// adjoint step on the GPU, with binomial checkpointing for the gradient.
+//
+// Per RK222 step (ARS(2,2,2), Supplementary A.4, both stages share M + dt*gamma*L):
+//   f0 = F(x0);  v1 = x0 + dt A10 f0;                      x1 = Phi v1
+//   f1 = F(x1);  v2 = (1-c) x0 + dt(A20 - c A10) f0 + dt A21 f1 + c x1;   x2 = Phi v2
+// where every quantity is in Chebyshev-T space, Phi is the per-pencil prognostic stage
+// solution operator (rb_setup.cpp) and c = H21/gamma: the stage-2 term -dt H21 L X1 equals
+// -(H21/gamma)(R1 - M X1) because X1 solves (M + dt gamma L) X1 = R1, and R1 - M X1 =
+// S1S0 (v1 - x1).  The adjoint step is the exact reverse of this sequence (it equals the
+// paper's RK IMEX adjoint recurrence; the parity tests check it against the oracle's
+// implementation of that recurrence), the tangent its forward derivative.
+// F is evaluated pseudospectrally: z transforms (Chebyshev matrices with reflection
+// folding), x FFTs, grid products, back to T space (Sparse spectral methods section).
+#include <cmath>
+#include <vector>
+
+#include "problem.h"
+#include "rb_kernels.cuh"
+#include "rb_setup.h"
+#include "revolve.h"
+
+namespace spadj {
+namespace {
+
+using namespace rbk;
+
+struct RB : EqImpl {
+  // sizes and parameters
+  int Nx = 0, Kx = 0, N = 0, Mx = 0, Mz = 0, L = 0;
+  double Lx = 4.0, nu = 0, kappa = 0, dt = 0, Ra = 0, Pr = 1;
+  double A10, A20, A21, H21, gam, cc;
+  int nonlinear = 1;
+  size_t ns = 0;    // complex entries of one state [3][Kx][N]
+  size_t nmix = 0;  // complex entries of one mixed array [Mz][Kx]
+  size_t npts = 0;  // grid points Mz*Mx
+  XParams xp{};
+  // device constants
+  DevBuf wm, czE, cdzE, gzF, gzTE, czTF, cdzTF, gmat, phi;
+  // device work buffers
+  DevBuf Z, G0, G1, dG, Gb, Fg, Y, f0, f1, df0, df1, x1, dx1, vb2, vb1, xb1, tmpx, tmpy, ybar, ybar2, cur, nxt,
+      partial, Jdev, seedbuf, slots, traj_tmp;
+  size_t zsmem = 0, xsmem = 0, ssmem = 0;
+
+  size_t state_len(int which) const override {
+    if (which == 0) return 2 * ns;
+    if (which == 1) return npts;
+    if (which == 3) return (size_t)2 * Kx * N;
+    return 0;
+  }
+
+  double2* st(DevBuf& b, int f = 0) { return b.as<double2>() + (size_t)f * Kx * N; }
+  double2* mix(DevBuf& b, int i) { return b.as<double2>() + (size_t)i * nmix; }
+  double* grid(DevBuf& b, int i) { return b.as<double>() + (size_t)i * npts; }
+
+  spadj_status init(Problem* p) {
+    const spadj_desc& d = p->desc;
+    Nx = d.n[0];
+    N = d.n[1];
+    if (Nx < 4 || Nx % 4 != 0 || N < 8 || N % 4 != 0)
+      return p->fail(SPADJ_ERR_INVALID, "rb: n[0] must be a multiple of 4 (>= 4) and n[1] a multiple of 4 (>= 8)");
+    if (d.scheme != SPADJ_RK222) return p->fail(SPADJ_ERR_UNSUPPORTED, "rb: scheme must be RK222");
+    if (d.batch != 1) return p->fail(SPADJ_ERR_UNSUPPORTED, "rb: batch must be 1 (one problem per handle)");
+    Kx = Nx / 2;
+    Mx = 3 * Nx / 2;
+    Mz = 3 * N / 2;
+    L = Mx / 2;
+    if (Mz % 2 != 0) return p->fail(SPADJ_ERR_INVALID, "rb: 3*n[1]/2 must be even");
+    Lx = d.length[0] > 0 ? d.length[0] : 4.0;
+    Ra = d.params[0];
+    Pr = d.params[1] > 0 ? d.params[1] : 1.0;
+    if (!(Ra > 0)) return p->fail(SPADJ_ERR_INVALID, "rb: params[0] (Rayleigh number) must be > 0");
+    nu = std::pow(Ra / Pr, -0.5);
+    kappa = std::pow(Ra * Pr, -0.5);
+    dt = d.dt;
+    nonlinear = d.nonlinear;
+    gam = 1.0 - 1.0 / std::sqrt(2.0);
+    const double del = 1.0 - 1.0 / (2.0 * gam);
+    A10 = gam; A20 = del; A21 = 1.0 - del; H21 = 1.0 - gam;
+    cc = H21 / gam;
+    ns = (size_t)3 * Kx * N;
+    nmix = (size_t)Mz * Kx;
+    npts = (size_t)Mz * Mx;
+    xp.Kx = Kx; xp.Mx = Mx; xp.L = L; xp.kscale = 2.0 * M_PI / Lx;
+    xp.plan = make_plan(L);
+    if (xp.plan.nrad < 0) return p->fail(SPADJ_ERR_INVALID, "rb: 3*n[0]/4 must be of the form 2^a 3^b");
+
+    // host operators and solution operators
+    rbhost::Operators o = rbhost::build_operators(N, Mz);
+    std::vector<double> ph;
+    std::string err;
+    if (!rbhost::build_phi(o, Kx, Lx, nu, kappa, dt * gam, ph, &err)) return p->fail(SPADJ_ERR_INVALID, err);
+    // split Phi' (3N x 3N per pencil) into its two reflection-parity blocks
+    const int Nh = N / 2, H = 3 * Nh, np = 3 * N;
+    std::vector<double> pb((size_t)Kx * 2 * H * H);
+    auto cls_idx = [&](int cls, int c) {  // class-local index -> global prognostic index
+      const int f = c / Nh, h = c % Nh;
+      const int n = 2 * h + ((f == 0) ? cls : 1 - cls);
+      return f * N + n;
+    };
+    for (int m = 0; m < Kx; ++m)
+      for (int cls = 0; cls < 2; ++cls)
+        for (int r = 0; r < H; ++r)
+          for (int c = 0; c < H; ++c)
+            pb[(((size_t)m * 2 + cls) * H + r) * H + c] = ph[(size_t)m * np * np + (size_t)cls_idx(cls, r) * np + cls_idx(cls, c)];
+    // half matrices for the reflection-folded z transforms
+    const int Mh = Mz / 2;
+    std::vector<double> hczE((size_t)Mh * N), hcdzE((size_t)Mh * N), hgzF((size_t)N * Mh), hgzTE((size_t)Mh * N),
+        hczTF((size_t)N * Mh), hcdzTF((size_t)N * Mh);
+    for (int j = 0; j < Mh; ++j)
+      for (int n = 0; n < N; ++n) {
+        hczE[(size_t)j * N + n] = o.Cz[(size_t)j * N + n];
+        hcdzE[(size_t)j * N + n] = o.Cdz[(size_t)j * N + n];
+        hgzTE[(size_t)j * N + n] = o.Gz[(size_t)n * Mz + j];
+        hgzF[(size_t)n * Mh + j] = o.Gz[(size_t)n * Mz + j];
+        hczTF[(size_t)n * Mh + j] = o.Cz[(size_t)j * N + n];
+        hcdzTF[(size_t)n * Mh + j] = o.Cdz[(size_t)j * N + n];
+      }
+    std::vector<double2> hwm(Mx);
+    for (int m = 0; m < Mx; ++m) {
+      const double th = -2.0 * M_PI * (double)m / (double)Mx;
+      hwm[m] = make_double2(std::cos(th), std::sin(th));
+    }
+    auto up = [&](DevBuf& b, const void* h, size_t bytes) -> cudaError_t {
+      cudaError_t e = b.ensure(bytes);
+      if (e != cudaSuccess) return e;
+      return cudaMemcpyAsync(b.ptr, h, bytes, cudaMemcpyHostToDevice, p->stream);
+    };
+    SPADJ_CUDA_TRY(p, up(wm, hwm.data(), sizeof(double2) * Mx));
+    SPADJ_CUDA_TRY(p, up(czE, hczE.data(), sizeof(double) * hczE.size()));
+    SPADJ_CUDA_TRY(p, up(cdzE, hcdzE.data(), sizeof(double) * hcdzE.size()));
+    SPADJ_CUDA_TRY(p, up(gzF, hgzF.data(), sizeof(double) * hgzF.size()));
+    SPADJ_CUDA_TRY(p, up(gzTE, hgzTE.data(), sizeof(double) * hgzTE.size()));
+    SPADJ_CUDA_TRY(p, up(czTF, hczTF.data(), sizeof(double) * hczTF.size()));
+    SPADJ_CUDA_TRY(p, up(cdzTF, hcdzTF.data(), sizeof(double) * hcdzTF.size()));
+    SPADJ_CUDA_TRY(p, up(gmat, o.G.data(), sizeof(double) * o.G.size()));
+    SPADJ_CUDA_TRY(p, up(phi, pb.data(), sizeof(double) * pb.size()));
+    SPADJ_CUDA_TRY(p, cudaStreamSynchronize(p->stream));
+    xp.WM = wm.as<double2>();
+    // work buffers
+    const size_t sb = sizeof(double2) * ns, mb = sizeof(double2) * nmix, gb = sizeof(double) * npts;
+    SPADJ_CUDA_TRY(p, Z.ensure(6 * mb));
+    SPADJ_CUDA_TRY(p, Y.ensure(6 * mb));
+    SPADJ_CUDA_TRY(p, G0.ensure(8 * gb));
+    SPADJ_CUDA_TRY(p, G1.ensure(8 * gb));
+    SPADJ_CUDA_TRY(p, dG.ensure(8 * gb));
+    SPADJ_CUDA_TRY(p, Gb.ensure(8 * gb));
+    SPADJ_CUDA_TRY(p, Fg.ensure(3 * gb));
+    for (DevBuf* b : {&f0, &f1, &df0, &df1, &x1, &dx1, &vb2, &vb1, &xb1, &tmpx, &tmpy, &ybar, &ybar2, &cur, &nxt, &seedbuf})
+      SPADJ_CUDA_TRY(p, b->ensure(sb));
+    SPADJ_CUDA_TRY(p, partial.ensure(sizeof(double) * Kx));
+    SPADJ_CUDA_TRY(p, Jdev.ensure(sizeof(double)));
+    zsmem = (size_t)2 * 2 * (size_t)std::max(N, Mz / 2) * kTM * sizeof(double2);
+    xsmem = sizeof(double2) * (4 * L + Kx);
+    ssmem = sizeof(double) * (size_t)H * kSolveRows + sizeof(double2) * (H + 4 * kSolveRows);
+    return SPADJ_OK;
+  }
+
+  // ---- building blocks -----------------------------------------------------------------------
+  spadj_status launch_z(Problem* p, ZJobs& js) {
+    js.ncols = Kx;
+    dim3 grid((Kx + kTM - 1) / kTM, js.n);
+    zmm_kernel<<<grid, 128, zsmem, p->stream>>>(js);
+    return check_launch(p, "rb zmm");
+  }
+  spadj_status launch_x(Problem* p, XJobs& js) {
+    dim3 grid(Mz, js.n);
+    xfft_kernel<<<grid, 64, xsmem, p->stream>>>(js, xp);
+    return check_launch(p, "rb xfft");
+  }
+  ZJob zexpand(const double2* in, const double* mat, int deriv, double2* out) {
+    ZJob j{};
+    j.in[0] = in; j.mat[0] = mat; j.alpha[0] = 1.0; j.deriv[0] = deriv; j.nterm = 1;
+    j.out = out; j.I = Mz; j.K = N; j.ik = 1; j.im = N; j.oi = Kx; j.om = 1;
+    return j;
+  }
+  ZJob zfold(const double2* in, const double* mat, int deriv, double2* out) {
+    ZJob j{};
+    j.in[0] = in; j.mat[0] = mat; j.alpha[0] = 1.0; j.deriv[0] = deriv; j.nterm = 1;
+    j.out = out; j.I = N; j.K = Mz; j.ik = Kx; j.im = 1; j.oi = 1; j.om = N;
+    return j;
+  }
+  XJob xc2r(const double2* in, int cmul, double w0, double w, double* out) {
+    XJob j{};
+    j.dir = 0; j.cin = in; j.cmul = cmul; j.w0 = w0; j.w = w; j.rout = out;
+    return j;
+  }
+  XJob xr2c(const double* in0, int mul0, const double* in1, int mul1, double s0, double s, double2* out) {
+    XJob j{};
+    j.dir = 1; j.rin[0] = in0; j.rmul[0] = mul0; j.nr = 1;
+    if (in1) { j.rin[1] = in1; j.rmul[1] = mul1; j.nr = 2; }
+    j.s0 = s0; j.s = s; j.cout = out;
+    return j;
+  }
+
+  // grid fields u, ux, uz, w, wx, wz, tx, tz of the state x (T space) into G
+  spadj_status c2g_fields(Problem* p, const double2* x, DevBuf& G) {
+    ZJobs zj{};
+    zj.expand = 1;
+    const double2* u = x;
+    const double2* w = x + (size_t)Kx * N;
+    const double2* t = x + (size_t)2 * Kx * N;
+    zj.j[0] = zexpand(u, czE.as<double>(), 0, mix(Z, 0));
+    zj.j[1] = zexpand(u, cdzE.as<double>(), 1, mix(Z, 1));
+    zj.j[2] = zexpand(w, czE.as<double>(), 0, mix(Z, 2));
+    zj.j[3] = zexpand(w, cdzE.as<double>(), 1, mix(Z, 3));
+    zj.j[4] = zexpand(t, czE.as<double>(), 0, mix(Z, 4));
+    zj.j[5] = zexpand(t, cdzE.as<double>(), 1, mix(Z, 5));
+    zj.n = 6;
+    spadj_status s = launch_z(p, zj);
+    if (s != SPADJ_OK) return s;
+    XJobs xj{};
+    xj.j[0] = xc2r(mix(Z, 0), 0, 1.0, 1.0, grid(G, 0));
+    xj.j[1] = xc2r(mix(Z, 0), 1, 1.0, 1.0, grid(G, 1));
+    xj.j[2] = xc2r(mix(Z, 1), 0, 1.0, 1.0, grid(G, 2));
+    xj.j[3] = xc2r(mix(Z, 2), 0, 1.0, 1.0, grid(G, 3));
+    xj.j[4] = xc2r(mix(Z, 2), 1, 1.0, 1.0, grid(G, 4));
+    xj.j[5] = xc2r(mix(Z, 3), 0, 1.0, 1.0, grid(G, 5));
+    xj.j[6] = xc2r(mix(Z, 4), 1, 1.0, 1.0, grid(G, 6));
+    xj.j[7] = xc2r(mix(Z, 5), 0, 1.0, 1.0, grid(G, 7));
+    xj.n = 8;
+    return launch_x(p, xj);
+  }
+
+  // three grid fields Fg -> T-space state f (g2c: 1/Mx r2c, then Gz)
+  spadj_status g2c3(Problem* p, double2* f) {
+    XJobs xj{};
+    for (int q = 0; q < 3; ++q) xj.j[q] = xr2c(grid(Fg, q), 0, nullptr, 0, 1.0 / Mx, 1.0 / Mx, mix(Y, q));
+    xj.n = 3;
+    spadj_status s = launch_x(p, xj);
+    if (s != SPADJ_OK) return s;
+    ZJobs zj{};
+    zj.expand = 0;
+    for (int q = 0; q < 3; ++q) zj.j[q] = zfold(mix(Y, q), gzF.as<double>(), 0, f + (size_t)q * Kx * N);
+    zj.n = 3;
+    return launch_z(p, zj);
+  }
+
+  int prod_grid() const { return (int)std::min<size_t>((npts + 255) / 256, 1024); }
+
+  // f = F(x) in T space; grid fields of x left in G
+  spadj_status evalF(Problem* p, const double2* x, double2* f, DevBuf& G) {
+    spadj_status s = c2g_fields(p, x, G);
+    if (s != SPADJ_OK) return s;
+    if (!nonlinear) {
+      cudaMemsetAsync(f, 0, sizeof(double2) * ns, p->stream);
+      return check_launch(p, "rb zero F");
+    }
+    prod_fwd_kernel<<<prod_grid(), 256, 0, p->stream>>>(G.as<double>(), Fg.as<double>(), (int)npts);
+    if ((s = check_launch(p, "rb prod")) != SPADJ_OK) return s;
+    return g2c3(p, f);
+  }
+
+  // df = (dF/dx)(x) dx, with the grid fields of x already in G
+  spadj_status evalJvp(Problem* p, DevBuf& G, const double2* dx, double2* df) {
+    if (!nonlinear) {
+      cudaMemsetAsync(df, 0, sizeof(double2) * ns, p->stream);
+      return check_launch(p, "rb zero dF");
+    }
+    spadj_status s = c2g_fields(p, dx, dG);
+    if (s != SPADJ_OK) return s;
+    prod_jvp_kernel<<<prod_grid(), 256, 0, p->stream>>>(G.as<double>(), dG.as<double>(), Fg.as<double>(), (int)npts);
+    if ((s = check_launch(p, "rb prod jvp")) != SPADJ_OK) return s;
+    return g2c3(p, df);
+  }
+
+  // out = sum_a beta_a add_a + (dF/dx)(x)^dagger (sum_t alpha_t fb_t), grid fields of x in G.
+  spadj_status evalVjp(Problem* p, DevBuf& G, int nfb, const double2* const* fb, const double* alpha, int nadd,
+                       const double2* const* add, const double* beta, double2* out) {
+    spadj_status s;
+    if (nonlinear) {
+      // T^dagger: Gz^T (expand) then c2r with weights 1/Mx, 1/(2Mx)
+      ZJobs zj{};
+      zj.expand = 1;
+      for (int q = 0; q < 3; ++q) {
+        ZJob j{};
+        for (int t = 0; t < nfb; ++t) {
+          j.in[t] = fb[t] + (size_t)q * Kx * N;
+          j.mat[t] = gzTE.as<double>();
+          j.alpha[t] = alpha[t];
+          j.deriv[t] = 0;
+        }
+        j.nterm = nfb;
+        j.out = mix(Z, q); j.I = Mz; j.K = N; j.ik = 1; j.im = N; j.oi = Kx; j.om = 1;
+        zj.j[q] = j;
+      }
+      zj.n = 3;
+      if ((s = launch_z(p, zj)) != SPADJ_OK) return s;
+      XJobs xj{};
+      for (int q = 0; q < 3; ++q) xj.j[q] = xc2r(mix(Z, q), 0, 1.0 / Mx, 0.5 / Mx, grid(Fg, q));
+      xj.n = 3;
+      if ((s = launch_x(p, xj)) != SPADJ_OK) return s;
+      prod_vjp_kernel<<<prod_grid(), 256, 0, p->stream>>>(G.as<double>(), Fg.as<double>(), Gb.as<double>(), (int)npts);
+      if ((s = check_launch(p, "rb prod vjp")) != SPADJ_OK) return s;
+      // (T^-1)^dagger in x: r2c with factor 2 on k >= 1, x-derivative adjoint -ik
+      XJobs xb{};
+      xb.j[0] = xr2c(grid(Gb, 0), 0, grid(Gb, 1), 2, 1.0, 2.0, mix(Y, 0));  // a_u
+      xb.j[1] = xr2c(grid(Gb, 2), 0, nullptr, 0, 1.0, 2.0, mix(Y, 1));      // b_u
+      xb.j[2] = xr2c(grid(Gb, 3), 0, grid(Gb, 4), 2, 1.0, 2.0, mix(Y, 2));  // a_w
+      xb.j[3] = xr2c(grid(Gb, 5), 0, nullptr, 0, 1.0, 2.0, mix(Y, 3));      // b_w
+      xb.j[4] = xr2c(grid(Gb, 6), 2, nullptr, 0, 1.0, 2.0, mix(Y, 4));      // a_t
+      xb.j[5] = xr2c(grid(Gb, 7), 0, nullptr, 0, 1.0, 2.0, mix(Y, 5));      // b_t
+      xb.n = 6;
+      if ((s = launch_x(p, xb)) != SPADJ_OK) return s;
+    }
+    // z part: out_q = Cz^T a_q + C'z^T b_q (+ addends)
+    ZJobs zf{};
+    zf.expand = 0;
+    for (int q = 0; q < 3; ++q) {
+      ZJob j{};
+      if (nonlinear) {
+        j.in[0] = mix(Y, 2 * q); j.mat[0] = czTF.as<double>(); j.alpha[0] = 1.0; j.deriv[0] = 0;
+        j.in[1] = mix(Y, 2 * q + 1); j.mat[1] = cdzTF.as<double>(); j.alpha[1] = 1.0; j.deriv[1] = 1;
+        j.nterm = 2;
+      } else {
+        j.in[0] = mix(Y, 0); j.mat[0] = czTF.as<double>(); j.alpha[0] = 0.0; j.nterm = 1;
+      }
+      for (int a = 0; a < nadd; ++a) { j.add[a] = add[a] + (size_t)q * Kx * N; j.beta[a] = beta[a]; }
+      j.nadd = nadd;
+      j.out = out + (size_t)q * Kx * N; j.I = N; j.K = Mz; j.ik = Kx; j.im = 1; j.oi = 1; j.om = N;
+      zf.j[q] = j;
+    }
+    zf.n = 3;
+    if (!nonlinear) {
+      // alpha = 0 term reads a mixed buffer that must be finite
+      cudaMemsetAsync(Y.ptr, 0, sizeof(double2) * nmix, p->stream);
+    }
+    return launch_z(p, zf);
+  }
+
+  spadj_status solve(Problem* p, int transpose, int nin, const double2* const* in, const double* a, double2* out) {
+    SolveArgs S{};
+    for (int t = 0; t < nin; ++t) { S.in[t] = in[t]; S.a[t] = a[t]; }
+    S.nin = nin; S.out = out; S.transpose = transpose; S.phi = phi.as<double>(); S.Kx = Kx; S.N = N;
+    const int H = 3 * N / 2;
+    dim3 grid(Kx, 2, (H + kSolveRows - 1) / kSolveRows);
+    solve_kernel<<<grid, 128, ssmem, p->stream>>>(S);
+    return check_launch(p, "rb solve");
+  }
+
+  // ---- RK222 steps ---------------------------------------------------------------------------
+  spadj_status step_fwd(Problem* p, const double2* x0, double2* x2) {
+    spadj_status s;
+    if ((s = evalF(p, x0, st(f0), G0)) != SPADJ_OK) return s;
+    { const double2* in[2] = {x0, st(f0)}; double a[2] = {1.0, dt * A10};
+      if ((s = solve(p, 0, 2, in, a, st(x1))) != SPADJ_OK) return s; }
+    if ((s = evalF(p, st(x1), st(f1), G1)) != SPADJ_OK) return s;
+    const double2* in[4] = {x0, st(f0), st(f1), st(x1)};
+    double a[4] = {1.0 - cc, dt * (A20 - cc * A10), dt * A21, cc};
+    return solve(p, 0, 4, in, a, x2);
+  }
+
+  spadj_status step_tan(Problem* p, const double2* x0, const double2* dx0, double2* x2, double2* dx2) {
+    spadj_status s;
+    if ((s = evalF(p, x0, st(f0), G0)) != SPADJ_OK) return s;
+    if ((s = evalJvp(p, G0, dx0, st(df0))) != SPADJ_OK) return s;
+    { const double2* in[2] = {x0, st(f0)}; double a[2] = {1.0, dt * A10};
+      if ((s = solve(p, 0, 2, in, a, st(x1))) != SPADJ_OK) return s; }
+    { const double2* in[2] = {dx0, st(df0)}; double a[2] = {1.0, dt * A10};
+      if ((s = solve(p, 0, 2, in, a, st(dx1))) != SPADJ_OK) return s; }
+    if ((s = evalF(p, st(x1), st(f1), G1)) != SPADJ_OK) return s;
+    if ((s = evalJvp(p, G1, st(dx1), st(df1))) != SPADJ_OK) return s;
+    double a[4] = {1.0 - cc, dt * (A20 - cc * A10), dt * A21, cc};
+    { const double2* in[4] = {x0, st(f0), st(f1), st(x1)};
+      if ((s = solve(p, 0, 4, in, a, x2)) != SPADJ_OK) return s; }
+    const double2* in[4] = {dx0, st(df0), st(df1), st(dx1)};
+    return solve(p, 0, 4, in, a, dx2);
+  }
+
+  // xb0 = cotangent of X_n from xb2 = cotangent of X_{n+1}, primal x0 = X_n.
+  spadj_status step_adj(Problem* p, const double2* x0, const double2* xb2, double2* xb0) {
+    spadj_status s;
+    if ((s = evalF(p, x0, st(f0), G0)) != SPADJ_OK) return s;
+    { const double2* in[2] = {x0, st(f0)}; double a[2] = {1.0, dt * A10};
+      if ((s = solve(p, 0, 2, in, a, st(x1))) != SPADJ_OK) return s; }
+    if (nonlinear && (s = c2g_fields(p, st(x1), G1)) != SPADJ_OK) return s;
+    { const double2* in[1] = {xb2}; double a[1] = {1.0};
+      if ((s = solve(p, 1, 1, in, a, st(vb2))) != SPADJ_OK) return s; }
+    // xb1 = c vb2 + (dF/dx1)^dagger (dt A21 vb2)
+    { const double2* fb[1] = {st(vb2)}; double al[1] = {dt * A21};
+      const double2* ad[1] = {st(vb2)}; double be[1] = {cc};
+      if ((s = evalVjp(p, G1, 1, fb, al, 1, ad, be, st(xb1))) != SPADJ_OK) return s; }
+    { const double2* in[1] = {st(xb1)}; double a[1] = {1.0};
+      if ((s = solve(p, 1, 1, in, a, st(vb1))) != SPADJ_OK) return s; }
+    // xb0 = (1-c) vb2 + vb1 + (dF/dx0)^dagger (dt(A20 - c A10) vb2 + dt A10 vb1)
+    const double2* fb[2] = {st(vb2), st(vb1)};
+    double al[2] = {dt * (A20 - cc * A10), dt * A10};
+    const double2* ad[2] = {st(vb2), st(vb1)};
+    double be[2] = {1.0 - cc, 1.0};
+    return evalVjp(p, G0, 2, fb, al, 2, ad, be, xb0);
+  }
+
+  // ---- C-ABI operations ----------------------------------------------------------------------
+  spadj_status transform(Problem* p, int kind, const double* in, double* out) override {
+    // one scalar field: coefficients [Kx][N] <-> grid [Mz][Mx]
+    const double2* ci = reinterpret_cast<const double2*>(in);
+    double2* co = reinterpret_cast<double2*>(out);
+    spadj_status s;
+    if (kind == 0 || kind == 3) {
+      ZJobs zj{};
+      zj.expand = 1;
+      zj.j[0] = zexpand(ci, kind == 0 ? czE.as<double>() : gzTE.as<double>(), 0, mix(Z, 0));
+      zj.n = 1;
+      if ((s = launch_z(p, zj)) != SPADJ_OK) return s;
+      XJobs xj{};
+      xj.j[0] = kind == 0 ? xc2r(mix(Z, 0), 0, 1.0, 1.0, out) : xc2r(mix(Z, 0), 0, 1.0 / Mx, 0.5 / Mx, out);
+      xj.n = 1;
+      return launch_x(p, xj);
+    }
+    if (kind == 1 || kind == 2) {
+      XJobs xj{};
+      xj.j[0] = kind == 1 ? xr2c(in, 0, nullptr, 0, 1.0 / Mx, 1.0 / Mx, mix(Y, 0))
+                          : xr2c(in, 0, nullptr, 0, 1.0, 2.0, mix(Y, 0));
+      xj.n = 1;
+      if ((s = launch_x(p, xj)) != SPADJ_OK) return s;
+      ZJobs zj{};
+      zj.expand = 0;
+      zj.j[0] = zfold(mix(Y, 0), kind == 1 ? gzF.as<double>() : czTF.as<double>(), 0, co);
+      zj.n = 1;
+      return launch_z(p, zj);
+    }
+    return p->fail(SPADJ_ERR_INVALID, "transform: kind must be 0..3");
+  }
+
+  spadj_status eval_F(Problem* p, int mode, const double* x, const double* dx, double* out) override {
+    const double2* xc = reinterpret_cast<const double2*>(x);
+    const double2* dc = reinterpret_cast<const double2*>(dx);
+    double2* oc = reinterpret_cast<double2*>(out);
+    spadj_status s;
+    if (mode == 0) return evalF(p, xc, oc, G0);
+    if ((s = c2g_fields(p, xc, G0)) != SPADJ_OK) return s;
+    if (mode == 1) return evalJvp(p, G0, dc, oc);
+    const double2* fb[1] = {dc};
+    double al[1] = {1.0};
+    return evalVjp(p, G0, 1, fb, al, 0, nullptr, nullptr, oc);
+  }
+
+  spadj_status pencil_solve(Problem* p, int transpose, const double* v, double* x) {
+    const double2* in[1] = {reinterpret_cast<const double2*>(v)};
+    double a[1] = {1.0};
+    return solve(p, transpose, 1, in, a, reinterpret_cast<double2*>(x));
+  }
+
+  spadj_status forward(Problem* p, int n_steps, const double* x0, double* x_out, double* traj) override {
+    if (n_steps < 0) return p->fail(SPADJ_ERR_INVALID, "forward: n_steps < 0");
+    const size_t sb = sizeof(double2) * ns;
+    SPADJ_CUDA_TRY(p, cudaMemcpyAsync(cur.ptr, x0, sb, cudaMemcpyDeviceToDevice, p->stream));
+    if (traj) SPADJ_CUDA_TRY(p, cudaMemcpyAsync(traj, x0, sb, cudaMemcpyDeviceToDevice, p->stream));
+    for (int n = 0; n < n_steps; ++n) {
+      spadj_status s = step_fwd(p, cur.as<double2>(), nxt.as<double2>());
+      if (s != SPADJ_OK) return s;
+      std::swap(cur, nxt);
+      if (traj)
+        SPADJ_CUDA_TRY(p, cudaMemcpyAsync(traj + (size_t)(n + 1) * 2 * ns, cur.ptr, sb, cudaMemcpyDeviceToDevice, p->stream));
+    }
+    SPADJ_CUDA_TRY(p, cudaMemcpyAsync(x_out, cur.ptr, sb, cudaMemcpyDeviceToDevice, p->stream));
+    return SPADJ_OK;
+  }
+
+  spadj_status tangent(Problem* p, int n_steps, const double* x0, const double* dx0, double* dx_out) override {
+    if (n_steps < 0) return p->fail(SPADJ_ERR_INVALID, "tangent: n_steps < 0");
+    const size_t sb = sizeof(double2) * ns;
+    SPADJ_CUDA_TRY(p, cudaMemcpyAsync(cur.ptr, x0, sb, cudaMemcpyDeviceToDevice, p->stream));
+    SPADJ_CUDA_TRY(p, cudaMemcpyAsync(tmpx.ptr, dx0, sb, cudaMemcpyDeviceToDevice, p->stream));
+    for (int n = 0; n < n_steps; ++n) {
+      spadj_status s = step_tan(p, cur.as<double2>(), tmpx.as<double2>(), nxt.as<double2>(), tmpy.as<double2>());
+      if (s != SPADJ_OK) return s;
+      std::swap(cur, nxt);
+      std::swap(tmpx, tmpy);
+    }
+    SPADJ_CUDA_TRY(p, cudaMemcpyAsync(dx_out, tmpx.ptr, sb, cudaMemcpyDeviceToDevice, p->stream));
+    return SPADJ_OK;
+  }
+
+  spadj_status adjoint(Problem* p, int n_steps, const double* traj, const double* y_final, double* grad) override {
+    if (n_steps < 1) return p->fail(SPADJ_ERR_INVALID, "adjoint: n_steps < 1");
+    const size_t sb = sizeof(double2) * ns;
+    SPADJ_CUDA_TRY(p, cudaMemcpyAsync(ybar.ptr, y_final, sb, cudaMemcpyDeviceToDevice, p->stream));
+    for (int n = n_steps - 1; n >= 0; --n) {
+      const double2* xn = reinterpret_cast<const double2*>(traj) + (size_t)n * ns;
+      spadj_status s = step_adj(p, xn, ybar.as<double2>(), ybar2.as<double2>());
+      if (s != SPADJ_OK) return s;
+      std::swap(ybar, ybar2);
+    }
+    SPADJ_CUDA_TRY(p, cudaMemcpyAsync(grad, ybar.ptr, sb, cudaMemcpyDeviceToDevice, p->stream));
+    return SPADJ_OK;
+  }
+
+  spadj_status objective(Problem* p, int objective, const double* obj_data, const double* x, double* J_dev,
+                         double* sd) override {
+    (void)obj_data;
+    if (objective != SPADJ_OBJ_ENERGY) return p->fail(SPADJ_ERR_UNSUPPORTED, "rb: objective must be ENERGY");
+    energy_kernel<<<Kx, 128, 0, p->stream>>>(reinterpret_cast<const double2*>(x), gmat.as<double>(), Lx, Kx, N,
+                                             partial.as<double>(), reinterpret_cast<double2*>(sd));
+    spadj_status s = check_launch(p, "rb energy");
+    if (s != SPADJ_OK) return s;
+    sum_kernel<<<1, 128, 0, p->stream>>>(partial.as<double>(), Kx, J_dev);
+    return check_launch(p, "rb sum");
+  }
+
+  int last_recompute = 0;
+
+  spadj_status gradient(Problem* p, const double* x0, int n_steps, int objective_kind, const double* obj_data,
+                        int ckpt_slots, double* J_host, double* grad, double* grad_p) override {
+    (void)grad_p;
+    if (n_steps < 1) return p->fail(SPADJ_ERR_INVALID, "gradient: n_steps < 1");
+    if (objective_kind != SPADJ_OBJ_ENERGY) return p->fail(SPADJ_ERR_UNSUPPORTED, "rb: objective must be ENERGY");
+    int S = (ckpt_slots <= 0 || ckpt_slots > n_steps + 1) ? n_steps + 1 : ckpt_slots;
+    const size_t sb = sizeof(double2) * ns;
+    SPADJ_CUDA_TRY(p, slots.ensure(sb * (size_t)S));
+    CkptPlanner planner;
+    std::vector<CkptOp> ops = planner.plan(n_steps, S);
+    SPADJ_CUDA_TRY(p, cudaMemcpyAsync(cur.ptr, x0, sb, cudaMemcpyDeviceToDevice, p->stream));
+    int cur_step = 0;
+    int recompute = 0;
+    bool have_seed = false;
+    auto slot_ptr = [&](int sl) { return slots.as<char>() + (size_t)sl * sb; };
+    for (const CkptOp& op : ops) {
+      spadj_status s = SPADJ_OK;
+      switch (op.type) {
+        case CK_STORE:
+          SPADJ_CUDA_TRY(p, cudaMemcpyAsync(slot_ptr(op.slot), cur.ptr, sb, cudaMemcpyDeviceToDevice, p->stream));
+          break;
+        case CK_RESTORE:
+          if (cur_step != op.a) {
+            SPADJ_CUDA_TRY(p, cudaMemcpyAsync(cur.ptr, slot_ptr(op.slot), sb, cudaMemcpyDeviceToDevice, p->stream));
+            cur_step = op.a;
+          }
+          break;
+        case CK_ADVANCE:
+          for (int k = op.a; k < op.b; ++k) {
+            if ((s = step_fwd(p, cur.as<double2>(), nxt.as<double2>())) != SPADJ_OK) return s;
+            std::swap(cur, nxt);
+            ++recompute;
+          }
+          cur_step = op.b;
+          break;
+        case CK_OBJECTIVE:
+          if ((s = objective(p, objective_kind, obj_data, cur.as<double>(), Jdev.as<double>(), ybar.as<double>())) != SPADJ_OK)
+            return s;
+          have_seed = true;
+          break;
+        case CK_ADJOINT:
+          if (!have_seed) return p->fail(SPADJ_ERR_INVALID, "gradient: schedule reached an adjoint step before the objective");
+          if ((s = step_adj(p, cur.as<double2>(), ybar.as<double2>(), ybar2.as<double2>())) != SPADJ_OK) return s;
+          std::swap(ybar, ybar2);
+          break;
+        default:
+          break;
+      }
+    }
+    last_recompute = recompute;
+    SPADJ_CUDA_TRY(p, cudaMemcpyAsync(grad, ybar.ptr, sb, cudaMemcpyDeviceToDevice, p->stream));
+    if (J_host) {
+      SPADJ_CUDA_TRY(p, cudaMemcpyAsync(J_host, Jdev.ptr, sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+      SPADJ_CUDA_TRY(p, cudaStreamSynchronize(p->stream));
+      if (!std::isfinite(J_host[0])) return p->fail(SPADJ_ERR_NONFINITE, "rb: objective is not finite");
+    }
+    return SPADJ_OK;
+  }
+
+  ~RB() override {
+    for (DevBuf* b : {&wm, &czE, &cdzE, &gzF, &gzTE, &czTF, &cdzTF, &gmat, &phi, &Z, &G0, &G1, &dG, &Gb, &Fg, &Y, &f0,
+                      &f1, &df0, &df1, &x1, &dx1, &vb2, &vb1, &xb1, &tmpx, &tmpy, &ybar, &ybar2, &cur, &nxt, &partial,
+                      &Jdev, &seedbuf, &slots, &traj_tmp})
+      b->release();
+  }
+};
+
+}  // namespace
+
+EqImpl* make_rb(Problem* p, spadj_status* st) {
+  RB* r = new RB();
+  *st = r->init(p);
+  if (*st != SPADJ_OK) {
+    delete r;
+    return nullptr;
+  }
+  return r;
+}
+
+spadj_status rb_pencil_solve(EqImpl* impl, Problem* p, int transpose, const double* v, double* x) {
+  RB* r = dynamic_cast<RB*>(impl);
+  if (!r) return p->fail(SPADJ_ERR_UNSUPPORTED, "solve: only defined for the Rayleigh-Benard pencils");
+  return r->pencil_solve(p, transpose, v, x);
+}
+
+int rb_last_recompute(EqImpl* impl) {
+  RB* r = dynamic_cast<RB*>(impl);
+  return r ? r->last_recompute : -1;
+}
+
+}  // namespace spadj

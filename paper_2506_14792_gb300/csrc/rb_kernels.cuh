@@ -1,0 +1,427 @@
+// Device kernels of the Rayleigh-Benard path (Fourier x x Chebyshev z, FP64).
+//
+// Layouts (Kx = Nx/2 x-modes, N Chebyshev modes, Mx x Mz dealiased grid):
+//   coefficients  [field][Kx][N]   complex (one pencil contiguous)
+//   mixed         [Mz][Kx]         complex (z on the grid, x in spectral space)
+//   grid          [Mz][Mx]         real
+// The z transforms are small dense real matrices applied to complex columns; they use
+// the reflection symmetry of the Gauss grid (xi_{Mz-1-j} = -xi_j, T_n(-xi) = (-1)^n T_n(xi))
+// so every output pair (j, Mz-1-j) costs one half-length dot product ("expand"), and
+// every grid-to-coefficient reduction runs over Mz/2 folded samples ("fold").
+#pragma once
+#include "fft.cuh"
+
+namespace spadj {
+namespace rbk {
+
+constexpr int kZMaxJobs = 9;
+constexpr int kXMaxJobs = 12;
+
+// One z-transform job: out = sum_t alpha_t * mat_t * in_t (+ sum_a beta_a * add_a).
+//   expand: K = N coefficients -> I = Mz grid rows; mat_t is (Mz/2) x N (rows j < Mz/2)
+//   fold:   K = Mz grid rows -> I = N coefficients; mat_t is N x (Mz/2) (columns j < Mz/2)
+// deriv_t = 1 when mat_t has the reflection parity of a z-derivative (-(-1)^n).
+struct ZJob {
+  const double2* in[2];
+  const double* mat[2];
+  double alpha[2];
+  int deriv[2];
+  int nterm;
+  const double2* add[2];
+  double beta[2];
+  int nadd;
+  double2* out;
+  int I, K;
+  int ik, im;  // in(k, m) = in[k*ik + m*im]
+  int oi, om;  // out(i, m) = out[i*oi + m*om]
+};
+struct ZJobs {
+  ZJob j[kZMaxJobs];
+  int n;
+  int ncols;  // Kx
+  int expand; // 1: expand, 0: fold
+};
+
+constexpr int kTM = 4;  // columns per CTA
+
+__global__ void __launch_bounds__(128) zmm_kernel(const __grid_constant__ ZJobs js) {
+  const ZJob& J = js.j[blockIdx.y];
+  const int m0 = blockIdx.x * kTM;
+  const int ncols = js.ncols;
+  extern __shared__ double2 sb[];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int K = J.K, I = J.I;
+  const int Kh = js.expand ? K : K / 2;  // staged rows per term
+  // stage inputs: expand -> raw coefficient columns; fold -> (s, d) = f_j +- f_{Mz-1-j}
+  for (int t = 0; t < J.nterm; ++t) {
+    double2* s = sb + (size_t)t * 2 * Kh * kTM;
+    const double2* src = J.in[t];
+    const bool kfast = (J.ik == 1);
+    for (int idx = tid; idx < Kh * kTM; idx += nt) {
+      int k, mm;
+      if (kfast) { k = idx % Kh; mm = idx / Kh; } else { mm = idx % kTM; k = idx / kTM; }
+      const int m = m0 + mm;
+      double2 v = make_double2(0.0, 0.0), v2 = make_double2(0.0, 0.0);
+      if (m < ncols) {
+        v = src[(size_t)k * J.ik + (size_t)m * J.im];
+        if (!js.expand) v2 = src[(size_t)(K - 1 - k) * J.ik + (size_t)m * J.im];
+      }
+      if (js.expand) {
+        s[k * kTM + mm] = v;
+      } else {
+        s[k * kTM + mm] = make_double2(v.x + v2.x, v.y + v2.y);             // s_j
+        s[(Kh + k) * kTM + mm] = make_double2(v.x - v2.x, v.y - v2.y);      // d_j
+      }
+    }
+  }
+  __syncthreads();
+  const int mm = tid % kTM;
+  const int ig = tid / kTM, ng = nt / kTM;
+  const int m = m0 + mm;
+  if (js.expand) {
+    const int Ih = I / 2;
+    for (int i = ig; i < Ih; i += ng) {
+      double2 lo = make_double2(0.0, 0.0), hi = make_double2(0.0, 0.0);
+      for (int t = 0; t < J.nterm; ++t) {
+        const double* a = J.mat[t] + (size_t)i * K;
+        const double2* s = sb + (size_t)t * 2 * Kh * kTM + mm;
+        double2 E = make_double2(0.0, 0.0), O = make_double2(0.0, 0.0);
+        int k = 0;
+        for (; k + 1 < K; k += 2) {
+          const double ae = __ldg(a + k), ao = __ldg(a + k + 1);
+          const double2 ve = s[k * kTM], vo = s[(k + 1) * kTM];
+          E.x = fma(ae, ve.x, E.x); E.y = fma(ae, ve.y, E.y);
+          O.x = fma(ao, vo.x, O.x); O.y = fma(ao, vo.y, O.y);
+        }
+        if (k < K) {
+          const double ae = __ldg(a + k);
+          const double2 ve = s[k * kTM];
+          E.x = fma(ae, ve.x, E.x); E.y = fma(ae, ve.y, E.y);
+        }
+        const double al = J.alpha[t];
+        // out_j = E + O ; out_{Mz-1-j} = E - O (parity (-1)^n) or -E + O (derivative parity)
+        const double se = J.deriv[t] ? -1.0 : 1.0;
+        lo.x = fma(al, E.x + O.x, lo.x); lo.y = fma(al, E.y + O.y, lo.y);
+        hi.x = fma(al, se * (E.x - O.x), hi.x); hi.y = fma(al, se * (E.y - O.y), hi.y);
+      }
+      if (m < ncols) {
+        const size_t o1 = (size_t)i * J.oi + (size_t)m * J.om;
+        const size_t o2 = (size_t)(I - 1 - i) * J.oi + (size_t)m * J.om;
+        for (int a = 0; a < J.nadd; ++a) {
+          const double2 p = J.add[a][o1], q = J.add[a][o2];
+          lo.x = fma(J.beta[a], p.x, lo.x); lo.y = fma(J.beta[a], p.y, lo.y);
+          hi.x = fma(J.beta[a], q.x, hi.x); hi.y = fma(J.beta[a], q.y, hi.y);
+        }
+        J.out[o1] = lo;
+        J.out[o2] = hi;
+      }
+    }
+  } else {
+    const int Kf = K / 2;
+    for (int i = ig; i < I; i += ng) {
+      double2 acc = make_double2(0.0, 0.0);
+      for (int t = 0; t < J.nterm; ++t) {
+        const double* a = J.mat[t] + (size_t)i * Kf;
+        // even i pairs with s for parity (-1)^n, with d for derivative parity
+        const bool use_s = ((i & 1) == 0) != (J.deriv[t] != 0);
+        const double2* s = sb + (size_t)t * 2 * Kh * kTM + (use_s ? 0 : Kh * kTM) + mm;
+        double2 v = make_double2(0.0, 0.0);
+        for (int k = 0; k < Kf; ++k) {
+          const double av = __ldg(a + k);
+          const double2 x = s[k * kTM];
+          v.x = fma(av, x.x, v.x); v.y = fma(av, x.y, v.y);
+        }
+        acc.x = fma(J.alpha[t], v.x, acc.x); acc.y = fma(J.alpha[t], v.y, acc.y);
+      }
+      if (m < ncols) {
+        const size_t o = (size_t)i * J.oi + (size_t)m * J.om;
+        for (int a = 0; a < J.nadd; ++a) {
+          const double2 p = J.add[a][o];
+          acc.x = fma(J.beta[a], p.x, acc.x); acc.y = fma(J.beta[a], p.y, acc.y);
+        }
+        J.out[o] = acc;
+      }
+    }
+  }
+}
+
+// One x-transform job over all Mz rows.
+//   dir 0 (c2r): grid row j = sum over the Hermitian spectrum of mult(k) * cin[j][k]
+//                with weights (w0 on k = 0, w on k >= 1), mult = 1 or i*k.
+//   dir 1 (r2c): cout[j][k] = sum_t mult_t(k) * scale(k) * FFT(rin_t row j)[k], k < Kx,
+//                mult = 1 or -i*k, scale = s0 (k = 0) or s (k >= 1).
+struct XJob {
+  int dir;
+  const double2* cin;
+  int cmul;
+  double w0, w;
+  double* rout;
+  const double* rin[2];
+  int rmul[2];
+  int nr;
+  double s0, s;
+  double2* cout;
+};
+struct XJobs {
+  XJob j[kXMaxJobs];
+  int n;
+};
+
+struct XParams {
+  int Kx, Mx, L;
+  double kscale;
+  FFTPlan plan;
+  const double2* WM;
+};
+
+__global__ void __launch_bounds__(64) xfft_kernel(const __grid_constant__ XJobs js, XParams P) {
+  const XJob& J = js.j[blockIdx.y];
+  const int row = blockIdx.x;
+  const int L = P.L, Kx = P.Kx, Mx = P.Mx;
+  extern __shared__ double2 sx[];
+  double2* A = sx;
+  double2* B = A + L;
+  double2* C = B + L;
+  double2* D = C + L;
+  double2* S = D + L;  // Kx
+  if (J.dir == 0) {
+    const double2* src = J.cin + (size_t)row * Kx;
+    for (int k = threadIdx.x; k < Kx; k += blockDim.x) {
+      double2 v = src[k];
+      if (J.cmul == 1) {  // i k v
+        const double kk = P.kscale * k;
+        v = make_double2(-kk * v.y, kk * v.x);
+      }
+      S[k] = v;
+    }
+    __syncthreads();
+    c2r_pre(A, [&](int k) { return S[k]; }, Kx, L, P.WM, J.w0, J.w);
+    __syncthreads();
+    double2* z = cfft_smem(A, B, P.plan, P.WM, +1);
+    double2* g = reinterpret_cast<double2*>(J.rout + (size_t)row * Mx);
+    for (int j = threadIdx.x; j < L; j += blockDim.x) g[j] = z[j];
+  } else {
+    for (int t = 0; t < J.nr; ++t) {
+      double2* a = (t == 0) ? A : C;
+      const double2* g = reinterpret_cast<const double2*>(J.rin[t] + (size_t)row * Mx);
+      for (int j = threadIdx.x; j < L; j += blockDim.x) a[j] = g[j];
+    }
+    __syncthreads();
+    double2* z0 = cfft_smem(A, B, P.plan, P.WM, -1);
+    double2* z1 = nullptr;
+    if (J.nr > 1) z1 = cfft_smem(C, D, P.plan, P.WM, -1);
+    double2* dst = J.cout + (size_t)row * Kx;
+    // r2c post-processing for each input, combined
+    for (int k = threadIdx.x; k < Kx; k += blockDim.x) {
+      double2 acc = make_double2(0.0, 0.0);
+      for (int t = 0; t < J.nr; ++t) {
+        const double2* Z = (t == 0) ? z0 : z1;
+        double2 zk = Z[k];
+        double2 zc = cconj(Z[k == 0 ? 0 : L - k]);
+        double2 e = cscale(cadd(zk, zc), 0.5);
+        double2 d = csub(zk, zc);
+        double2 o = make_double2(0.5 * d.y, -0.5 * d.x);
+        double2 X = cadd(e, cmul(o, __ldg(&P.WM[k])));
+        if (J.rmul[t] == 2) {  // -i k X
+          const double kk = P.kscale * k;
+          X = make_double2(kk * X.y, -kk * X.x);
+        }
+        acc = cadd(acc, X);
+      }
+      const double sc = (k == 0) ? J.s0 : J.s;
+      double2 r = cscale(acc, sc);
+      if (k == 0) r.y = 0.0;
+      dst[k] = r;
+    }
+  }
+}
+
+// Grid-point products.  Slots of the primal/tangent grid arrays: 0 u, 1 ux, 2 uz,
+// 3 w, 4 wx, 5 wz, 6 tx, 7 tz; outputs F: 0 F_u, 1 F_w, 2 F_t.
+__global__ void prod_fwd_kernel(const double* __restrict__ G, double* __restrict__ F, int npts) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < npts; i += gridDim.x * blockDim.x) {
+    const double u = G[0 * (size_t)npts + i], ux = G[1 * (size_t)npts + i], uz = G[2 * (size_t)npts + i];
+    const double w = G[3 * (size_t)npts + i], wx = G[4 * (size_t)npts + i], wz = G[5 * (size_t)npts + i];
+    const double tx = G[6 * (size_t)npts + i], tz = G[7 * (size_t)npts + i];
+    F[0 * (size_t)npts + i] = -fma(u, ux, w * uz);
+    F[1 * (size_t)npts + i] = -fma(u, wx, w * wz);
+    F[2 * (size_t)npts + i] = -fma(u, tx, w * tz);
+  }
+}
+
+__global__ void prod_jvp_kernel(const double* __restrict__ G, const double* __restrict__ dG, double* __restrict__ F,
+                                int npts) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < npts; i += gridDim.x * blockDim.x) {
+    double g[8], d[8];
+#pragma unroll
+    for (int s = 0; s < 8; ++s) { g[s] = G[s * (size_t)npts + i]; d[s] = dG[s * (size_t)npts + i]; }
+    F[0 * (size_t)npts + i] = -(d[0] * g[1] + g[0] * d[1] + d[3] * g[2] + g[3] * d[2]);
+    F[1 * (size_t)npts + i] = -(d[0] * g[4] + g[0] * d[4] + d[3] * g[5] + g[3] * d[5]);
+    F[2 * (size_t)npts + i] = -(d[0] * g[6] + g[0] * d[6] + d[3] * g[7] + g[3] * d[7]);
+  }
+}
+
+// Reverse of prod_fwd: from grid cotangents (gu, gw, gt) of (F_u, F_w, F_t) produce the
+// cotangents of the 8 grid fields.
+__global__ void prod_vjp_kernel(const double* __restrict__ G, const double* __restrict__ gF, double* __restrict__ Gb,
+                                int npts) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < npts; i += gridDim.x * blockDim.x) {
+    const double u = G[0 * (size_t)npts + i], ux = G[1 * (size_t)npts + i], uz = G[2 * (size_t)npts + i];
+    const double w = G[3 * (size_t)npts + i], wx = G[4 * (size_t)npts + i], wz = G[5 * (size_t)npts + i];
+    const double tx = G[6 * (size_t)npts + i], tz = G[7 * (size_t)npts + i];
+    const double gu = gF[0 * (size_t)npts + i], gw = gF[1 * (size_t)npts + i], gt = gF[2 * (size_t)npts + i];
+    Gb[0 * (size_t)npts + i] = -(gu * ux + gw * wx + gt * tx);
+    Gb[1 * (size_t)npts + i] = -gu * u;
+    Gb[2 * (size_t)npts + i] = -gu * w;
+    Gb[3 * (size_t)npts + i] = -(gu * uz + gw * wz + gt * tz);
+    Gb[4 * (size_t)npts + i] = -gw * u;
+    Gb[5 * (size_t)npts + i] = -gw * w;
+    Gb[6 * (size_t)npts + i] = -gt * u;
+    Gb[7 * (size_t)npts + i] = -gt * w;
+  }
+}
+
+// Stage solve x = Phi v per pencil and parity class (or the adjoint v = Phi^H x), with the
+// right-hand side formed on the fly as v = sum_t a_t in_t.  Phi = Dc Phi' Dr with real
+// Phi' stored per pencil as two (3N/2)^2 parity blocks; Dr, Dc^H and the projection of the
+// mean pencil onto real coefficients are applied on load and store.
+struct SolveArgs {
+  const double2* in[4];
+  double a[4];
+  int nin;
+  double2* out;
+  int transpose;
+  const double* phi;  // [Kx][2][H][H], H = 3N/2
+  int Kx, N;
+};
+
+constexpr int kSolveRows = 32;  // output rows per CTA (4 warps split the reduction in quarters)
+
+__global__ void __launch_bounds__(128) solve_kernel(const __grid_constant__ SolveArgs S) {
+  const int m = blockIdx.x, cls = blockIdx.y, r0 = blockIdx.z * kSolveRows;
+  const int N = S.N, Nh = N / 2, H = 3 * Nh, Kx = S.Kx;
+  extern __shared__ double sphi[];      // [H][kSolveRows] block of Phi' (or its transpose)
+  double2* v = reinterpret_cast<double2*>(sphi + (size_t)H * kSolveRows);  // [H]
+  const double* blk = S.phi + ((size_t)m * 2 + cls) * H * H;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  // class index c -> (field f, mode n)
+  for (int c = tid; c < H; c += nt) {
+    const int f = c / Nh, h = c % Nh;
+    const int n = 2 * h + ((f == 0) ? cls : 1 - cls);
+    const size_t off = ((size_t)f * Kx + m) * N + n;
+    double2 x = make_double2(0.0, 0.0);
+    for (int t = 0; t < S.nin; ++t) {
+      const double2 y = S.in[t][off];
+      x.x = fma(S.a[t], y.x, x.x);
+      x.y = fma(S.a[t], y.y, x.y);
+    }
+    if (S.transpose && m == 0) x.y = 0.0;          // projection (self-adjoint)
+    if (f == 0) x = make_double2(x.y, -x.x);        // times -i (Dr, or Dc^H)
+    v[c] = x;
+  }
+  // stage rows r0..r0+R of Phi' (forward) or columns r0..r0+R (adjoint) as [k][r]
+  const int R = min(kSolveRows, H - r0);
+  for (int idx = tid; idx < H * kSolveRows; idx += nt) {
+    int k, r;
+    double val = 0.0;
+    if (S.transpose) {  // need Phi'[k][r0 + r]: coalesced over r
+      k = idx / kSolveRows; r = idx % kSolveRows;
+      if (r < R) val = blk[(size_t)k * H + r0 + r];
+    } else {            // need Phi'[r0 + r][k]: coalesced over k
+      r = idx / H; k = idx % H;
+      if (r < R) val = blk[(size_t)(r0 + r) * H + k];
+    }
+    sphi[k * kSolveRows + r] = val;
+  }
+  __syncthreads();
+  // thread (r, q): partial dot product over the q-th quarter of the columns
+  double2* red = v + H;  // [4][kSolveRows]
+  {
+    const int r = tid % kSolveRows, q = tid / kSolveRows;
+    const int kq = (H + 3) / 4;
+    const int k0 = q * kq, k1 = min(H, k0 + kq);
+    double2 acc = make_double2(0.0, 0.0);
+    for (int k = k0; k < k1; ++k) {
+      const double p = sphi[k * kSolveRows + r];
+      const double2 x = v[k];
+      acc.x = fma(p, x.x, acc.x);
+      acc.y = fma(p, x.y, acc.y);
+    }
+    red[q * kSolveRows + r] = acc;
+  }
+  __syncthreads();
+  for (int r = tid; r < R; r += nt) {
+    double2 acc = red[r];
+    for (int q = 1; q < 4; ++q) acc = cadd(acc, red[q * kSolveRows + r]);
+    const int c = r0 + r;
+    const int f = c / Nh, h = c % Nh;
+    const int n = 2 * h + ((f == 0) ? cls : 1 - cls);
+    if (f == 0) acc = make_double2(-acc.y, acc.x);  // times i (Dc, or Dr^H)
+    if (!S.transpose && m == 0) acc.y = 0.0;        // projection onto real mean pencil
+    S.out[((size_t)f * Kx + m) * N + n] = acc;
+  }
+}
+
+// Kinetic energy J = (Lx/2) sum_{u,w} sum_m w_m c_m^H G c_m and its gradient
+// seed = Lx w_m G c_m (w_0 = 1, w_m = 2; real part only on the mean pencil).
+__global__ void energy_kernel(const double2* __restrict__ x, const double* __restrict__ G, double Lx, int Kx, int N,
+                              double* __restrict__ partial, double2* __restrict__ seed) {
+  const int m = blockIdx.x;
+  const double wm = (m == 0) ? 1.0 : 2.0;
+  double acc = 0.0;
+  for (int idx = threadIdx.x; idx < 3 * N; idx += blockDim.x) {
+    const int f = idx / N, i = idx % N;
+    const size_t base = ((size_t)f * Kx + m) * N;
+    double2 g = make_double2(0.0, 0.0);
+    if (f < 2) {
+      for (int k = 0; k < N; ++k) {
+        double2 c = x[base + k];
+        if (m == 0) c.y = 0.0;
+        const double gv = __ldg(&G[i * N + k]);
+        g.x = fma(gv, c.x, g.x);
+        g.y = fma(gv, c.y, g.y);
+      }
+      double2 ci = x[base + i];
+      if (m == 0) ci.y = 0.0;
+      acc += ci.x * g.x + ci.y * g.y;
+    }
+    seed[base + i] = make_double2(Lx * wm * g.x, Lx * wm * g.y);
+  }
+  __shared__ double red[128];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[m] = 0.5 * Lx * wm * red[0];
+}
+
+__global__ void sum_kernel(const double* __restrict__ partial, int n, double* __restrict__ out) {
+  __shared__ double red[128];
+  double a = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) a += partial[i];
+  red[threadIdx.x] = a;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[0] = red[0];
+}
+
+// y = sum_t a_t x_t over n complex entries (state combinations).
+__global__ void axpy_kernel(double2* __restrict__ y, const double2* __restrict__ x0, double a0,
+                            const double2* __restrict__ x1, double a1, const double2* __restrict__ x2, double a2,
+                            size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    double2 v = x0[i];
+    double2 r = make_double2(a0 * v.x, a0 * v.y);
+    if (x1) { v = x1[i]; r.x = fma(a1, v.x, r.x); r.y = fma(a1, v.y, r.y); }
+    if (x2) { v = x2[i]; r.x = fma(a2, v.x, r.x); r.y = fma(a2, v.y, r.y); }
+    y[i] = r;
+  }
+}
+
+}  // namespace rbk
+}  // namespace spadj

@@ -56,6 +56,8 @@ _SIGS = {
     "spadj_eval_F": (ctypes.c_int, [_vp, _vp, _vp]),
     "spadj_eval_F_jvp": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "spadj_eval_F_vjp": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "spadj_solve": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp]),
+    "spadj_checkpoint_schedule": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "spadj_forward": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp]),
     "spadj_tangent": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp]),
     "spadj_adjoint": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp]),
@@ -102,6 +104,18 @@ def _as_f64(t, n, name):
     return t
 
 
+def checkpoint_schedule(n_steps, slots):
+    """Host-side binomial checkpoint schedule: list of (type, a, b, slot) actions."""
+    n = ctypes.c_int()
+    _chk(None, lib().spadj_checkpoint_schedule(n_steps, slots, None, 0, ctypes.byref(n)))
+    buf = (ctypes.c_int * (4 * n.value))()
+    _chk(None, lib().spadj_checkpoint_schedule(n_steps, slots, buf, n.value, ctypes.byref(n)))
+    return [tuple(buf[4 * i:4 * i + 4]) for i in range(n.value)]
+
+
+CK_ADVANCE, CK_STORE, CK_RESTORE, CK_ADJOINT, CK_FREE, CK_OBJECTIVE = range(6)
+
+
 class Problem:
     """Owns one spadj_problem; methods take torch CUDA tensors."""
 
@@ -140,8 +154,8 @@ class Problem:
         return int(lib().spadj_state_len(self.h, which))
 
     def transform(self, kind, inp, out):
-        nin = self.state_len(0 if kind in (C2G, G2C_ADJ) else 1)
-        nout = self.state_len(1 if kind in (C2G, G2C_ADJ) else 0)
+        nin = self.state_len(3 if kind in (C2G, G2C_ADJ) else 1)
+        nout = self.state_len(1 if kind in (C2G, G2C_ADJ) else 3)
         _chk(self.h, lib().spadj_transform(self.h, kind, _ptr(_as_f64(inp, nin, "in")), _ptr(_as_f64(out, nout, "out"))))
         return out
 
@@ -161,6 +175,11 @@ class Problem:
         _chk(self.h, lib().spadj_eval_F_vjp(self.h, _ptr(_as_f64(x, n, "x")), _ptr(_as_f64(y, n, "y")),
                                              _ptr(_as_f64(out, n, "out"))))
         return out
+
+    def solve(self, v, x, transpose=False):
+        n = self.state_len(0)
+        _chk(self.h, lib().spadj_solve(self.h, int(bool(transpose)), _ptr(_as_f64(v, n, "v")), _ptr(_as_f64(x, n, "x"))))
+        return x
 
     def forward(self, n_steps, x0, x_out, traj=None):
         n = self.state_len(0)

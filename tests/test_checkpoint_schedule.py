@@ -1,0 +1,73 @@
+"""Host-side check of the binomial checkpoint schedule (no GPU): simulating the actions
+must reverse every step exactly once in order N-1..0 with the right state current,
+evaluate the objective once at X_N before the first adjoint step, never use more slots
+than given, and recompute at most t forward sweeps with t minimal for
+C(s + t, s) >= N (Griewank-Walther binomial bound)."""
+from math import comb
+
+import pytest
+
+from paper_2506_14792_gb300 import build, spadj
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if build.stale():
+        build.build()
+
+
+def simulate(n, slots):
+    ops = spadj.checkpoint_schedule(n, slots)
+    store = {}
+    cur = 0
+    adjoint_order = []
+    advances = 0
+    objective_at = None
+    for typ, a, b, sl in ops:
+        if typ == spadj.CK_STORE:
+            assert cur == a
+            assert 0 <= sl < min(slots, n + 1)
+            assert sl not in store
+            store[sl] = a
+        elif typ == spadj.CK_RESTORE:
+            assert store.get(sl) == a
+            cur = a
+        elif typ == spadj.CK_ADVANCE:
+            assert cur == a and b > a
+            advances += b - a
+            cur = b
+        elif typ == spadj.CK_OBJECTIVE:
+            assert cur == n and objective_at is None and not adjoint_order
+            objective_at = a
+        elif typ == spadj.CK_ADJOINT:
+            assert cur == a and objective_at == n
+            adjoint_order.append(a)
+        elif typ == spadj.CK_FREE:
+            assert store.get(sl) == a
+            del store[sl]
+    assert adjoint_order == list(range(n - 1, -1, -1))
+    return advances
+
+
+@pytest.mark.parametrize("n", [1, 2, 7, 30, 200, 2000])
+@pytest.mark.parametrize("slots", [1, 2, 3, 16, 64, 100000])
+def test_schedule_valid_and_binomial(n, slots):
+    if n >= 2000 and slots <= 2:
+        pytest.skip("quadratic schedule, covered at smaller n")
+    adv = simulate(n, slots)
+    s = min(slots, n + 1) - 1
+    if s >= n:
+        assert adv == n  # store-all: one forward sweep
+        return
+    if s == 0:
+        assert adv == n * (n + 1) // 2
+        return
+    t = 1
+    while comb(s + t, s) < n:
+        t += 1
+    assert adv <= t * n + n
+
+
+def test_rejects_bad_arguments():
+    with pytest.raises(spadj.SpadjError):
+        spadj.checkpoint_schedule(0, 4)
