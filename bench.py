@@ -18,7 +18,11 @@ import subprocess
 import sys
 import time
 
-import numpy as np
+# the CPU oracle baseline is reported per core: keep numpy's BLAS single-threaded
+for _v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import numpy as np  # noqa: E402
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
@@ -28,6 +32,11 @@ import synthetic  # noqa: E402
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # FP64 peak: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.07 GHz (nominal GB300 FP64 1.25 TFLOP/s).
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
+
+
+# DRAM traffic (bytes per launch) of the dominant kernel from an ncu capture, keyed by
+# (workload, kernel class); None until measured for the current kernels.
+TRAFFIC = {}
 
 
 def fp64_flops_real_fft(M):
@@ -59,12 +68,6 @@ class Burgers:
     def units_per_step(self):
         return self.B * self.dof * self.nsteps
 
-    # algorithmic FP64 flops per member per step: 2 real FFTs forward, 3 adjoint (+ pointwise)
-    def kernel_flops(self):
-        f = fp64_flops_real_fft(self.M)
-        fwd = self.B * self.nsteps * (2 * f + self.M + 10 * self.K)
-        adj = self.B * self.nsteps * (3 * f + 2 * self.M + 12 * self.K)
-        return {"forward": fwd, "adjoint": adj}
 
     def setup(self, device):
         import torch
@@ -84,21 +87,14 @@ class Burgers:
         self.grad_pin = torch.empty((self.B, self.K), dtype=torch.complex128).pin_memory()
         self.x0_dev2 = torch.empty_like(self.x0)
 
-    def launches_per_step(self):
-        return 3
 
-    def step(self, ev):
-        """Device-resident step; ev = list of 4 events recorded between the kernels."""
-        ev[0].record()
+    flush_l2 = False
+
+    def step(self, ev=None):
+        """Device-resident step: forward (trajectory stored), objective, adjoint sweep."""
         self.p.forward(self.nsteps, self.x0, self.xN, self.traj)
-        ev[1].record()
         self.p.objective(self.xN, self.J, self.seedv)
-        ev[2].record()
         self.p.adjoint(self.nsteps, self.traj, self.seedv, self.grad)
-        ev[3].record()
-
-    def kernel_names(self):
-        return ["forward", "objective", "adjoint"]
 
     def e2e_step(self):
         """Public API call with host buffers: pinned H2D of x0, spadj_gradient (J to host), D2H of grad."""
@@ -122,8 +118,74 @@ class Burgers:
         return Bs * self.dof * self.nsteps / el, "%d members x %d steps (gradient, numpy FP64)" % (Bs, self.nsteps), el
 
 
-WORKLOADS = {"burgers": Burgers}
-DEFAULT_WORKLOAD = "burgers"
+class RayleighBenard:
+    """2D Rayleigh-Benard, Fourier(x) 256 x Chebyshev(z) 64 tau, Ra=1e6, Pr=1, no-slip,
+    RK222 dt=1e-3, 2000 steps, kinetic energy at T, binomial checkpointing (64 slots)."""
+    name = "rayleigh_benard2d_256x64_Ra1e6_rk222_2000steps"
+
+    def __init__(self, Nx=256, Nz=64, Ra=1e6, Pr=1.0, dt=1e-3, nsteps=2000, slots=64, seed=2, amp=1e-3):
+        self.Nx, self.Nz, self.Ra, self.Pr, self.dt, self.nsteps = Nx, Nz, Ra, Pr, dt, nsteps
+        self.slots, self.seed, self.amp = slots, seed, amp
+        self.dof = 3 * Nx * Nz
+        self.B = 1
+        self.flush_l2 = True
+
+    def config(self):
+        return {"workload": self.name, "Nx": self.Nx, "Nz": self.Nz, "Ra": self.Ra, "Pr": self.Pr, "dt": self.dt,
+                "steps": self.nsteps, "scheme": "RK222 (ARS222)", "objective": "kinetic energy at T",
+                "checkpoint_slots": self.slots, "dof": self.dof,
+                "l2": "L2 flushed between timed iterations (256 MB write); working set ~60 MB fits L2"}
+
+    def units_per_step(self):
+        return self.dof * self.nsteps
+
+    def setup(self, device):
+        import torch
+        from paper_2506_14792_gb300 import spadj
+        self.torch = torch
+        self.p = spadj.Problem(spadj.SPADJ_RB2D, spadj.SPADJ_RK222, [self.Nx, self.Nz], [4.0], [self.Ra, self.Pr],
+                               self.dt)
+        self.s0 = synthetic.rb_ic(self.Nx, self.Nz, seed=self.seed, amp=self.amp)
+        shape = (3, self.Nx // 2, self.Nz)
+        self.x0 = torch.from_numpy(self.s0).to(device)
+        self.grad = torch.empty(shape, dtype=torch.complex128, device=device)
+        self.x0_pin = torch.from_numpy(self.s0).pin_memory()
+        self.grad_pin = torch.empty(shape, dtype=torch.complex128).pin_memory()
+        self.x0_dev2 = torch.empty_like(self.x0)
+        self.launches = None
+
+    def step(self, ev=None):
+        self.p.gradient(self.x0, self.nsteps, self.grad, ckpt_slots=self.slots, want_J=False)
+
+    def e2e_step(self):
+        self.x0_dev2.copy_(self.x0_pin, non_blocking=True)
+        J = self.p.gradient(self.x0_dev2, self.nsteps, self.grad, ckpt_slots=self.slots)
+        self.grad_pin.copy_(self.grad, non_blocking=True)
+        return J
+
+    def e2e_bytes(self):
+        n = self.s0.nbytes
+        return n, n + 8
+
+    def cpu_sample(self, nsteps=6):
+        """Oracle gradient (store-all) over the first `nsteps` steps of the same workload."""
+        from oracle import rayleigh_benard as orb
+        if not hasattr(self, "_oracle"):
+            self._oracle = orb.RayleighBenard(self.Nx, self.Nz, self.Ra, self.Pr)
+            orb.gradient(self._oracle, self._oracle.pencils(synthetic.rb_ic(self.Nx, self.Nz, seed=self.seed,
+                                                                                amp=self.amp)), 1, self.dt)
+        o = self._oracle
+        X0 = o.pencils(synthetic.rb_ic(self.Nx, self.Nz, seed=self.seed, amp=self.amp))
+        t = time.perf_counter()
+        orb.gradient(o, X0, nsteps, self.dt)
+        el = time.perf_counter() - t
+        return (self.dof * nsteps / el,
+                "%d of %d steps of the same gradient (forward+adjoint, store-all, numpy/scipy FP64, "
+                "factorisations cached)" % (nsteps, self.nsteps), el)
+
+
+WORKLOADS = {"burgers": Burgers, "rb": RayleighBenard}
+DEFAULT_WORKLOAD = "rb"
 
 
 # ---------------------------------------------------------------------------------------
@@ -185,7 +247,7 @@ def run_reference(args, wl):
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
-    cores = int(os.environ.get("OMP_NUM_THREADS", "1"))
+    cores = int(os.environ.get("OPENBLAS_NUM_THREADS", "1"))
     for _ in range(args.warmup):
         wl.cpu_sample()
     vals, secs = [], []
@@ -214,7 +276,7 @@ def run_gpu(args, wl):
     dev = torch.device("cuda", local)
     wl.setup(dev)
     stream = torch.cuda.current_stream()
-    names = wl.kernel_names()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev) if wl.flush_l2 else None
 
     def barrier():
         torch.cuda.synchronize()
@@ -223,25 +285,34 @@ def run_gpu(args, wl):
             dist.barrier()
             torch.cuda.synchronize()
 
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(len(names) + 1)] for _ in range(args.steps)]
-    warm = [torch.cuda.Event(enable_timing=True) for _ in range(len(names) + 1)]
     for _ in range(args.warmup):
-        wl.step(warm)
+        wl.step()
     barrier()
     clk = ClockSampler(local)
     clk.start()
     time.sleep(0.3)
-    t0 = torch.cuda.Event(enable_timing=True)
-    t1 = torch.cuda.Event(enable_timing=True)
-    t0.record(stream)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    barrier()
     for i in range(args.steps):
-        wl.step(evs[i])
-    t1.record(stream)
+        if flush is not None:
+            flush.fill_(float(i))  # write 256 MB (> L2) between timed iterations, outside the events
+        starts[i].record(stream)
+        wl.step()
+        ends[i].record(stream)
     barrier()
     clocks = clk.stop()
-    ms = t0.elapsed_time(t1)
-    per_kernel = {nm: float(np.mean([evs[i][j].elapsed_time(evs[i][j + 1]) for i in range(args.steps)]))
-                  for j, nm in enumerate(names)}
+    ms = float(sum(starts[i].elapsed_time(ends[i]) for i in range(args.steps)))
+    # per-kernel breakdown: one more step of the same workload with the library bracketing each
+    # of its launches by CUDA events on this stream (kept out of the timed region: the events
+    # add host work between launches)
+    wl.p.timing(True)
+    if flush is not None:
+        flush.fill_(-1.0)
+    wl.step()
+    barrier()
+    rep = wl.p.timing_report()
+    wl.p.timing(False)
     if ws > 1:
         import torch.distributed as dist
         t = torch.tensor([ms], device=dev)
@@ -269,25 +340,30 @@ def run_gpu(args, wl):
         e2e_ms = float(t.item())
     bi, bo = wl.e2e_bytes()
 
-    # roofline of the dominant kernel (FP64 ALU bound)
-    flops = wl.kernel_flops()
-    dom = max(flops, key=lambda k: per_kernel.get(k, 0.0))
-    achieved = flops[dom] / (per_kernel[dom] / 1e3) / 1e9
+    # roofline of the dominant kernel class (FP64 ALU bound on GB300)
+    dom = max(rep, key=lambda k: rep[k][0])
+    dms, dfl, dn = rep[dom]
+    achieved = dfl / (dms / 1e3) / 1e9
+    per_kernel = {k: {"ms_total": v[0], "launches": v[2], "share": v[0] / sum(x[0] for x in rep.values()),
+                      "gflops": v[1] / (v[0] / 1e3) / 1e9 if v[0] > 0 else None} for k, v in rep.items()}
     roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
-            "frac": achieved / FP64_PEAK_GFLOPS, "traffic": wl.traffic(dom) if hasattr(wl, "traffic") else None,
-            "per_kernel_ms": per_kernel,
-            "peak_note": "FP64 FMA peak 152 SM x 2 DFMA/clk x 2.07 GHz (nominal 1.25 TFLOP/s)"}
+            "frac": achieved / FP64_PEAK_GFLOPS, "traffic": TRAFFIC.get((wl.name, dom)),
+            "avg_launch_us": 1e3 * dms / dn, "flops_per_launch": dfl / dn, "per_kernel": per_kernel,
+            "peak_note": "FP64 FMA peak 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s); "
+                         "no tensor-core FP64 path (GB300 FP64 tensor rate is the same)"}
+    launches = int(sum(v[2] for v in rep.values())) * args.steps
     if rank != 0:
         return 0
     cpu = None
     if ws == 1 and not args.no_cpu:
         v, sample, el = wl.cpu_sample()
-        cpu = {"value": v, "unit": "dof*steps/s", "cores": 1, "kind": "oracle", "sample": sample}
+        cpu = {"value": v, "unit": "dof*steps/s", "cores": int(os.environ.get("OPENBLAS_NUM_THREADS", "1")),
+               "kind": "oracle", "sample": sample}
     line = {"metric": "forward+adjoint gradient dof*steps/s at 1e-10 rel vs FP64 oracle", "value": value,
             "unit": "dof*steps/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64", "data": "synthetic", "config": dict(wl.config(), parallelism="dp%d" % ws),
-            "gpu_launches": wl.launches_per_step() * args.steps,
+            "dtype": "f64", "data": "synthetic", "config": dict(wl.config(), parallelism="replicas%d" % ws),
+            "gpu_launches": launches,
             "e2e": {"value": units / (e2e_ms / 1e3), "unit": "dof*steps/s", "h2d_bytes_per_step": bi,
                     "d2h_bytes_per_step": bo},
             "roofline": roof, "cpu_baseline": cpu, "clocks": clocks}
@@ -303,8 +379,11 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
+    ap.add_argument("--nsteps", type=int, default=None, help="override the workload's time steps (profiling runs)")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]()
+    if args.nsteps is not None:
+        wl.nsteps = args.nsteps
     if args.impl == "reference":
         return run_reference(args, wl)
     return run_gpu(args, wl)

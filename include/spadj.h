@@ -161,6 +161,16 @@ spadj_status spadj_gradient(spadj_problem* prob, const double* x0, int n_steps, 
                             const double* obj_data, int ckpt_slots, double* J_host,
                             double* grad_x0, double* grad_p);
 
+/* Measurement support (not part of the method): when enabled, every kernel the library
+ * launches on the problem's stream is bracketed by CUDA events; spadj_timing_report
+ * returns, per kernel class, the summed device time (ms), the summed algorithmic FP64
+ * flop count and the number of launches since timing was (re)enabled.  Classes:
+ * 0 z (Chebyshev) transforms, 1 x (Fourier) FFTs, 2 grid-point products, 3 pencil solves,
+ * 4 objective, 5 fused persistent trajectory kernels.  spadj_timing synchronises the
+ * stream and resets the counters. */
+spadj_status spadj_timing(spadj_problem* prob, int enable);
+spadj_status spadj_timing_report(spadj_problem* prob, int kernel_class, double* ms, double* flops, long* launches);
+
 /* One-line description of the last failure on this problem (or of the last failed
  * spadj_create when prob is NULL).  Never NULL. */
 const char* spadj_last_error(const spadj_problem* prob);

@@ -151,6 +151,25 @@ spadj_status spadj_gradient(spadj_problem* p, const double* x0, int n_steps, int
   return p->impl->gradient(p, x0, n_steps, objective, obj_data, ckpt_slots, J_host, grad_x0, grad_p);
 }
 
+spadj_status spadj_timing(spadj_problem* p, int enable) {
+  if (!p) return SPADJ_ERR_INVALID;
+  SPADJ_CUDA_TRY(p, cudaStreamSynchronize(p->stream));
+  p->timing.reset();
+  p->timing.enabled = enable != 0;
+  return SPADJ_OK;
+}
+
+spadj_status spadj_timing_report(spadj_problem* p, int kernel_class, double* ms, double* flops, long* launches) {
+  if (!p) return SPADJ_ERR_INVALID;
+  if (kernel_class < 0 || kernel_class >= spadj::KC_COUNT || !ms || !flops || !launches)
+    return p->fail(SPADJ_ERR_INVALID, "timing_report: bad kernel class or NULL output");
+  p->timing.collect();
+  *ms = p->timing.ms[kernel_class];
+  *flops = p->timing.flops[kernel_class];
+  *launches = p->timing.launches[kernel_class];
+  return SPADJ_OK;
+}
+
 const char* spadj_last_error(const spadj_problem* p) {
   if (!p) return g_create_error.c_str();
   return p->err.empty() ? "no error" : p->err.c_str();

@@ -445,11 +445,18 @@ struct Burgers : EqImpl {
     return check_launch(p, "burgers trajectory");
   }
 
+  // algorithmic FP64 flops per member-step: real FFTs of M points (2.5 M log2 M each) plus
+  // the pointwise product and the per-mode combine.
+  double fft_flops() const { return 2.5 * P.M * std::log2((double)P.M); }
+
   spadj_status forward(Problem* p, int n_steps, const double* x0, double* x_out, double* trj) override {
     if (n_steps < 0) return p->fail(SPADJ_ERR_INVALID, "forward: n_steps < 0");
-    return dispatchQ(p, [&](auto q) {
+    cudaEvent_t t = p->tic();
+    spadj_status s = dispatchQ(p, [&](auto q) {
       trajectory_kernel<decltype(q)::value><<<B, G, smem, p->stream>>>(P, n_steps, x0, nullptr, x_out, trj, 0);
     });
+    p->toc(t, KC_FUSED, (double)B * n_steps * (2 * fft_flops() + P.M + 10.0 * P.K));
+    return s;
   }
 
   spadj_status tangent(Problem* p, int n_steps, const double* x0, const double* dx0, double* dx_out) override {
@@ -461,9 +468,12 @@ struct Burgers : EqImpl {
 
   spadj_status adjoint(Problem* p, int n_steps, const double* trj, const double* y_final, double* grad) override {
     if (n_steps < 1) return p->fail(SPADJ_ERR_INVALID, "adjoint: n_steps < 1");
-    return dispatchQ(p, [&](auto q) {
+    cudaEvent_t t = p->tic();
+    spadj_status s = dispatchQ(p, [&](auto q) {
       adjoint_kernel<decltype(q)::value><<<B, G, smem, p->stream>>>(P, n_steps, trj, y_final, grad);
     });
+    p->toc(t, KC_FUSED, (double)B * n_steps * (3 * fft_flops() + 2.0 * P.M + 12.0 * P.K));
+    return s;
   }
 
   spadj_status objective(Problem* p, int objective, const double* obj_data, const double* x, double* J_dev,

@@ -61,11 +61,66 @@ struct EqImpl {
                                 double* grad_p) = 0;
 };
 
+// Optional per-kernel-class timing: CUDA events recorded on the problem's stream around
+// every launch of the library, with the algorithmic FP64 flop count of that launch.
+enum KernelClass { KC_ZTRANSFORM = 0, KC_XFFT = 1, KC_POINTWISE = 2, KC_SOLVE = 3, KC_OBJECTIVE = 4, KC_FUSED = 5,
+                   KC_COUNT = 6 };
+
+struct Timing {
+  bool enabled = false;
+  struct Rec { int kc; cudaEvent_t a, b; double flops; };
+  std::vector<Rec> pending;
+  std::vector<cudaEvent_t> pool;
+  double ms[KC_COUNT] = {0}, flops[KC_COUNT] = {0};
+  long launches[KC_COUNT] = {0};
+  cudaEvent_t get() {
+    if (!pool.empty()) { cudaEvent_t e = pool.back(); pool.pop_back(); return e; }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+  }
+  void reset() {
+    collect();
+    for (int i = 0; i < KC_COUNT; ++i) { ms[i] = 0; flops[i] = 0; launches[i] = 0; }
+  }
+  void collect() {
+    for (Rec& r : pending) {
+      cudaEventSynchronize(r.b);
+      float t = 0.f;
+      cudaEventElapsedTime(&t, r.a, r.b);
+      ms[r.kc] += t;
+      flops[r.kc] += r.flops;
+      launches[r.kc] += 1;
+      pool.push_back(r.a);
+      pool.push_back(r.b);
+    }
+    pending.clear();
+  }
+  ~Timing() {
+    collect();
+    for (cudaEvent_t e : pool) cudaEventDestroy(e);
+  }
+};
+
 struct Problem {
   spadj_desc desc{};
   cudaStream_t stream = nullptr;
   std::string err;
   EqImpl* impl = nullptr;
+  Timing timing;
+  cudaEvent_t tic() {
+    if (!timing.enabled) return nullptr;
+    cudaEvent_t e = timing.get();
+    cudaEventRecord(e, stream);
+    return e;
+  }
+  void toc(cudaEvent_t a, int kc, double flops) {
+    if (!a) return;
+    cudaEvent_t b = timing.get();
+    cudaEventRecord(b, stream);
+    timing.pending.push_back({kc, a, b, flops});
+    if (timing.pending.size() > 4096) timing.collect();
+  }
   void set_error(const std::string& s) { err = s; }
   spadj_status fail(spadj_status st, const std::string& s) {
     err = s;

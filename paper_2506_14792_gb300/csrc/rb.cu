@@ -157,15 +157,31 @@ struct RB : EqImpl {
   }
 
   // ---- building blocks -----------------------------------------------------------------------
+  // algorithmic FP64 flops: folded z transform = 4 flops per real-matrix x complex MAC over
+  // Kx columns and N x Mz/2 entries per term; real FFT of Mx points = 2.5 Mx log2 Mx.
+  double zflops(const ZJobs& js) const {
+    double f = 0;
+    for (int i = 0; i < js.n; ++i) f += 4.0 * Kx * N * (Mz / 2) * js.j[i].nterm;
+    return f;
+  }
+  double xflops(const XJobs& js) const {
+    double f = 0, one = 2.5 * Mx * std::log2((double)Mx) * Mz;
+    for (int i = 0; i < js.n; ++i) f += one * (js.j[i].dir == 0 ? 1 : js.j[i].nr);
+    return f;
+  }
   spadj_status launch_z(Problem* p, ZJobs& js) {
     js.ncols = Kx;
     dim3 grid((Kx + kTM - 1) / kTM, js.n);
+    cudaEvent_t t = p->tic();
     zmm_kernel<<<grid, 128, zsmem, p->stream>>>(js);
+    p->toc(t, KC_ZTRANSFORM, zflops(js));
     return check_launch(p, "rb zmm");
   }
   spadj_status launch_x(Problem* p, XJobs& js) {
     dim3 grid(Mz, js.n);
+    cudaEvent_t t = p->tic();
     xfft_kernel<<<grid, 64, xsmem, p->stream>>>(js, xp);
+    p->toc(t, KC_XFFT, xflops(js));
     return check_launch(p, "rb xfft");
   }
   ZJob zexpand(const double2* in, const double* mat, int deriv, double2* out) {
@@ -246,7 +262,9 @@ struct RB : EqImpl {
       cudaMemsetAsync(f, 0, sizeof(double2) * ns, p->stream);
       return check_launch(p, "rb zero F");
     }
+    cudaEvent_t tp = p->tic();
     prod_fwd_kernel<<<prod_grid(), 256, 0, p->stream>>>(G.as<double>(), Fg.as<double>(), (int)npts);
+    p->toc(tp, KC_POINTWISE, 12.0 * npts);
     if ((s = check_launch(p, "rb prod")) != SPADJ_OK) return s;
     return g2c3(p, f);
   }
@@ -259,7 +277,9 @@ struct RB : EqImpl {
     }
     spadj_status s = c2g_fields(p, dx, dG);
     if (s != SPADJ_OK) return s;
+    cudaEvent_t tp = p->tic();
     prod_jvp_kernel<<<prod_grid(), 256, 0, p->stream>>>(G.as<double>(), dG.as<double>(), Fg.as<double>(), (int)npts);
+    p->toc(tp, KC_POINTWISE, 24.0 * npts);
     if ((s = check_launch(p, "rb prod jvp")) != SPADJ_OK) return s;
     return g2c3(p, df);
   }
@@ -290,7 +310,9 @@ struct RB : EqImpl {
       for (int q = 0; q < 3; ++q) xj.j[q] = xc2r(mix(Z, q), 0, 1.0 / Mx, 0.5 / Mx, grid(Fg, q));
       xj.n = 3;
       if ((s = launch_x(p, xj)) != SPADJ_OK) return s;
+      cudaEvent_t tp = p->tic();
       prod_vjp_kernel<<<prod_grid(), 256, 0, p->stream>>>(G.as<double>(), Fg.as<double>(), Gb.as<double>(), (int)npts);
+      p->toc(tp, KC_POINTWISE, 24.0 * npts);
       if ((s = check_launch(p, "rb prod vjp")) != SPADJ_OK) return s;
       // (T^-1)^dagger in x: r2c with factor 2 on k >= 1, x-derivative adjoint -ik
       XJobs xb{};
@@ -334,7 +356,10 @@ struct RB : EqImpl {
     S.nin = nin; S.out = out; S.transpose = transpose; S.phi = phi.as<double>(); S.Kx = Kx; S.N = N;
     const int H = 3 * N / 2;
     dim3 grid(Kx, 2, (H + kSolveRows - 1) / kSolveRows);
+    cudaEvent_t t = p->tic();
     solve_kernel<<<grid, 128, ssmem, p->stream>>>(S);
+    // two real H x H matvecs per pencil, each on two right-hand sides (re, im)
+    p->toc(t, KC_SOLVE, 2.0 * Kx * 2.0 * H * H * 2.0);
     return check_launch(p, "rb solve");
   }
 
@@ -490,8 +515,10 @@ struct RB : EqImpl {
                          double* sd) override {
     (void)obj_data;
     if (objective != SPADJ_OBJ_ENERGY) return p->fail(SPADJ_ERR_UNSUPPORTED, "rb: objective must be ENERGY");
+    cudaEvent_t t = p->tic();
     energy_kernel<<<Kx, 128, 0, p->stream>>>(reinterpret_cast<const double2*>(x), gmat.as<double>(), Lx, Kx, N,
                                              partial.as<double>(), reinterpret_cast<double2*>(sd));
+    p->toc(t, KC_OBJECTIVE, 8.0 * Kx * 2 * N * N);
     spadj_status s = check_launch(p, "rb energy");
     if (s != SPADJ_OK) return s;
     sum_kernel<<<1, 128, 0, p->stream>>>(partial.as<double>(), Kx, J_dev);

@@ -63,6 +63,9 @@ _SIGS = {
     "spadj_adjoint": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp]),
     "spadj_objective": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp, _vp]),
     "spadj_gradient": (ctypes.c_int, [_vp, _vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int, _vp, _vp, _vp]),
+    "spadj_timing": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "spadj_timing_report": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                            ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_long)]),
     "spadj_last_error": (ctypes.c_char_p, [_vp]),
 }
 
@@ -207,11 +210,28 @@ class Problem:
         return J_dev
 
     def gradient(self, x0, n_steps, grad_x0, objective=SPADJ_OBJ_ENERGY, obj_data=None, ckpt_slots=0,
-                 grad_p=None):
-        """Returns J per batch member (numpy, host) and fills grad_x0."""
+                 grad_p=None, want_J=True):
+        """Fills grad_x0; returns J per batch member (numpy, host) or None when want_J is False
+        (then the call stays asynchronous on the stream)."""
         n = self.state_len(0)
-        J = np.zeros(self.desc.batch, dtype=np.float64)
+        J = np.zeros(self.desc.batch, dtype=np.float64) if want_J else None
+        jp = J.ctypes.data_as(ctypes.c_void_p) if want_J else None
         _chk(self.h, lib().spadj_gradient(self.h, _ptr(_as_f64(x0, n, "x0")), n_steps, objective,
-                                           _ptr(obj_data), ckpt_slots, J.ctypes.data_as(ctypes.c_void_p),
+                                           _ptr(obj_data), ckpt_slots, jp,
                                            _ptr(_as_f64(grad_x0, n, "grad_x0")), _ptr(grad_p)))
         return J
+
+    KERNEL_CLASSES = ("z_transform", "x_fft", "pointwise", "pencil_solve", "objective", "fused_trajectory")
+
+    def timing(self, enable=True):
+        _chk(self.h, lib().spadj_timing(self.h, int(bool(enable))))
+
+    def timing_report(self):
+        """{class: (ms, flops, launches)} since timing was enabled."""
+        out = {}
+        for k, name in enumerate(self.KERNEL_CLASSES):
+            ms, fl, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_long()
+            _chk(self.h, lib().spadj_timing_report(self.h, k, ctypes.byref(ms), ctypes.byref(fl), ctypes.byref(n)))
+            if n.value:
+                out[name] = (ms.value, fl.value, n.value)
+        return out
