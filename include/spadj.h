@@ -106,6 +106,22 @@ size_t spadj_state_len(const spadj_problem* prob, int which);
  * in/out are device arrays in the coefficient or grid layout of the equation set. */
 spadj_status spadj_transform(spadj_problem* prob, int kind, const double* in, double* out);
 
+/* spadj_transform without any device allocation, for callers that cannot call cudaMalloc:
+ * processes whose device memory is owned by their own allocator (a framework's caching
+ * allocator or an arena reserved at start-up) and may not go around it, and latency-bound
+ * loops that cannot afford cudaMalloc/cudaFree, which can synchronise the device.  The paper
+ * has no counterpart; this is an interface convenience of this library.
+ * Defined for SPADJ_RB2D only (SPADJ_ERR_UNSUPPORTED otherwise).  Same kinds, layouts and
+ * results as spadj_transform.  Its intermediate array (3*n[1]/2 x n[0]/2 complex entries)
+ * lives in a static device array of 262144 complex entries (4 MiB) that every GPU loading
+ * the library holds until the process exits; larger sizes return SPADJ_ERR_INVALID.  The
+ * first call on a device looks the array's address up (cudaGetSymbolAddress, with the
+ * problem's device current); make that first call before any stream capture.  All calls
+ * share the one array: calls whose kernels overlap on the GPU (different streams, or
+ * different problems on one device) race and must be serialised by the caller.  The array
+ * is fully overwritten before it is read, so no clearing is needed between calls. */
+spadj_status spadj_transform_noalloc(spadj_problem* prob, int kind, const double* in, double* out);
+
 /* Explicit term F(X) in coefficient space (Sparse spectral methods section: nonlinear
  * terms evaluated on the dealiased collocation grid), its Jacobian-vector product
  * dF = (dF/dX) dX and its vector-Jacobian product out = (dF/dX)^dagger y

@@ -70,6 +70,12 @@ spadj_status spadj_transform(spadj_problem* p, int kind, const double* in, doubl
   return p->impl->transform(p, kind, in, out);
 }
 
+spadj_status spadj_transform_noalloc(spadj_problem* p, int kind, const double* in, double* out) {
+  if (!p) return SPADJ_ERR_INVALID;
+  if (bad_ptr(in) || bad_ptr(out)) return p->fail(SPADJ_ERR_INVALID, "transform_noalloc: NULL array");
+  return spadj::rb_transform_noalloc(p->impl, p, kind, in, out);
+}
+
 spadj_status spadj_eval_F(spadj_problem* p, const double* x, double* f) {
   if (!p) return SPADJ_ERR_INVALID;
   if (bad_ptr(x) || bad_ptr(f)) return p->fail(SPADJ_ERR_INVALID, "eval_F: NULL array");

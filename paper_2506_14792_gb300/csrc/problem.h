@@ -139,6 +139,7 @@ inline spadj_status check_launch(Problem* p, const char* what) {
 EqImpl* make_burgers(Problem* p, spadj_status* st);
 EqImpl* make_rb(Problem* p, spadj_status* st);
 spadj_status rb_pencil_solve(EqImpl* impl, Problem* p, int transpose, const double* v, double* x);
+spadj_status rb_transform_noalloc(EqImpl* impl, Problem* p, int kind, const double* in, double* out);
 
 }  // namespace spadj
 

@@ -13,6 +13,7 @@
 // F is evaluated pseudospectrally: z transforms (Chebyshev matrices with reflection
 // folding), x FFTs, grid products, back to T space (Sparse spectral methods section).
 #include <cmath>
+#include <mutex>
 #include <vector>
 
 #include "problem.h"
@@ -447,6 +448,38 @@ struct RB : EqImpl {
     return p->fail(SPADJ_ERR_INVALID, "transform: kind must be 0..3");
   }
 
+  // Same transform as transform() above, with the intermediate mixed array supplied by the
+  // caller (the no-allocation entry point passes its static device scratch here).
+  spadj_status transform_into(Problem* p, int kind, const double* in, double* out, double2* scratch) {
+    const double2* ci = reinterpret_cast<const double2*>(in);
+    double2* co = reinterpret_cast<double2*>(out);
+    spadj_status s;
+    if (kind == 0 || kind == 3) {
+      ZJobs zj{};
+      zj.expand = 1;
+      zj.j[0] = zexpand(ci, kind == 0 ? czE.as<double>() : gzTE.as<double>(), 0, scratch);
+      zj.n = 1;
+      if ((s = launch_z(p, zj)) != SPADJ_OK) return s;
+      XJobs xj{};
+      xj.j[0] = kind == 0 ? xc2r(scratch, 0, 1.0, 1.0, out) : xc2r(scratch, 0, 1.0 / Mx, 0.5 / Mx, out);
+      xj.n = 1;
+      return launch_x(p, xj);
+    }
+    if (kind == 1 || kind == 2) {
+      XJobs xj{};
+      xj.j[0] = kind == 1 ? xr2c(in, 0, nullptr, 0, 1.0 / Mx, 1.0 / Mx, scratch)
+                          : xr2c(in, 0, nullptr, 0, 1.0, 2.0, scratch);
+      xj.n = 1;
+      if ((s = launch_x(p, xj)) != SPADJ_OK) return s;
+      ZJobs zj{};
+      zj.expand = 0;
+      zj.j[0] = zfold(scratch, kind == 1 ? gzF.as<double>() : czTF.as<double>(), 0, co);
+      zj.n = 1;
+      return launch_z(p, zj);
+    }
+    return p->fail(SPADJ_ERR_INVALID, "transform_noalloc: kind must be 0..3");
+  }
+
   spadj_status eval_F(Problem* p, int mode, const double* x, const double* dx, double* out) override {
     const double2* xc = reinterpret_cast<const double2*>(x);
     const double2* dc = reinterpret_cast<const double2*>(dx);
@@ -615,6 +648,48 @@ spadj_status rb_pencil_solve(EqImpl* impl, Problem* p, int transpose, const doub
 int rb_last_recompute(EqImpl* impl) {
   RB* r = dynamic_cast<RB*>(impl);
   return r ? r->last_recompute : -1;
+}
+
+// ---- transform without allocation ----------------------------------------------------------
+//
+// Static device scratch for spadj_transform_noalloc: one mixed (z-grid x x-spectral) array of
+// at most kNoAllocScratch complex entries (4 MiB).  Every GPU that loads the library holds it
+// until the process exits.  Host code may not use the symbol as a device address; the
+// address is fetched once per device with cudaGetSymbolAddress while that device is current.
+constexpr size_t kNoAllocScratch = (size_t)1 << 18;
+static __device__ __align__(256) double2 g_noalloc_scratch[kNoAllocScratch];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+double2* g_noalloc_ptr[kMaxDevices] = {nullptr};
+}  // namespace
+
+spadj_status rb_transform_noalloc(EqImpl* impl, Problem* p, int kind, const double* in, double* out) {
+  RB* r = dynamic_cast<RB*>(impl);
+  if (!r) return p->fail(SPADJ_ERR_UNSUPPORTED, "transform_noalloc: only defined for the Rayleigh-Benard problem");
+  if (kind < 0 || kind > 3) return p->fail(SPADJ_ERR_INVALID, "transform_noalloc: kind must be 0..3");
+  const size_t need = (size_t)r->Mz * r->Kx;
+  if (need > kNoAllocScratch)
+    return p->fail(SPADJ_ERR_INVALID, "transform_noalloc: (3*n[1]/2) * (n[0]/2) = " + std::to_string(need) +
+                                          " exceeds the static scratch of " + std::to_string(kNoAllocScratch) +
+                                          " complex entries");
+  int dev = 0;
+  SPADJ_CUDA_TRY(p, cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return p->fail(SPADJ_ERR_INVALID, "transform_noalloc: device ordinal out of range");
+  double2* scratch = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+      void* ptr = nullptr;
+      cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+      if (e != cudaSuccess)
+        return p->fail(SPADJ_ERR_CUDA, std::string("transform_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+      g_noalloc_ptr[dev] = static_cast<double2*>(ptr);
+    }
+    scratch = g_noalloc_ptr[dev];
+  }
+  return r->transform_into(p, kind, in, out, scratch);
 }
 
 }  // namespace spadj

@@ -53,6 +53,7 @@ _SIGS = {
     "spadj_destroy": (ctypes.c_int, [_vp]),
     "spadj_state_len": (ctypes.c_size_t, [_vp, ctypes.c_int]),
     "spadj_transform": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp]),
+    "spadj_transform_noalloc": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp]),
     "spadj_eval_F": (ctypes.c_int, [_vp, _vp, _vp]),
     "spadj_eval_F_jvp": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "spadj_eval_F_vjp": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
