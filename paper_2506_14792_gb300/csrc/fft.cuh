@@ -41,21 +41,27 @@ __device__ __forceinline__ double2 cscale(double2 a, double s) { return make_dou
 // multiply by i*s (s = +-1)
 __device__ __forceinline__ double2 cmul_i(double2 a, double s) { return make_double2(-s * a.y, s * a.x); }
 
-// Twiddle exp(sign * 2 pi i m / L) from the M-table (M = 2L): entry 2m, conjugated for sign=+1.
-__device__ __forceinline__ double2 twL(const double2* __restrict__ WM, int m, int sign) {
+// Twiddle exp(SIGN * 2 pi i m / L) from the M-table (M = 2L): entry 2m, conjugated for SIGN=+1.
+template <int SIGN>
+__device__ __forceinline__ double2 twL(const double2* __restrict__ WM, int m) {
   double2 w = __ldg(&WM[2 * m]);
-  return sign > 0 ? cconj(w) : w;
+  return SIGN > 0 ? cconj(w) : w;
+}
+// SIGN * i * a (exact: a swap and a sign change, no multiply)
+template <int SIGN>
+__device__ __forceinline__ double2 rot(double2 a) {
+  return SIGN > 0 ? make_double2(-a.y, a.x) : make_double2(a.y, -a.x);
 }
 
-// Complex FFT of length p.n held in buffer a (b is scratch of the same size).  sign = -1:
-// forward exp(-), sign = +1: inverse exp(+) (unnormalised).  Returns the buffer holding
+// Complex FFT of length p.n held in buffer a (b is scratch of the same size).  SIGN = -1:
+// forward exp(-), SIGN = +1: inverse exp(+) (unnormalised).  Returns the buffer holding
 // the result (a or b).  All threads of the CTA must call it; it synchronises internally
 // and on return the result is visible to every thread.
-static __device__ __noinline__ double2* cfft_smem(double2* a, double2* b, const FFTPlan p,
-                                           const double2* __restrict__ WM, int sign) {
+template <int SIGN>
+static __device__ __noinline__ double2* cfft_smem_t(double2* a, double2* b, const FFTPlan p,
+                                                    const double2* __restrict__ WM) {
   const int n = p.n;
   const int tid = threadIdx.x, nt = blockDim.x;
-  const double s = (double)sign;
   int Ns = 1;
   for (int pass = 0; pass < p.nrad; ++pass) {
     const int R = p.rad[pass];
@@ -67,31 +73,31 @@ static __device__ __noinline__ double2* cfft_smem(double2* a, double2* b, const 
       if (R == 4) {
         double2 v0 = a[j], v1 = a[j + nb], v2 = a[j + 2 * nb], v3 = a[j + 3 * nb];
         if (k) {
-          v1 = cmul(v1, twL(WM, k * tstep, sign));
-          v2 = cmul(v2, twL(WM, 2 * k * tstep, sign));
-          v3 = cmul(v3, twL(WM, 3 * k * tstep, sign));
+          v1 = cmul(v1, twL<SIGN>(WM, k * tstep));
+          v2 = cmul(v2, twL<SIGN>(WM, 2 * k * tstep));
+          v3 = cmul(v3, twL<SIGN>(WM, 3 * k * tstep));
         }
-        double2 t0 = cadd(v0, v2), t1 = csub(v0, v2), t2 = cadd(v1, v3);
-        double2 t3 = cmul_i(csub(v1, v3), s);
+        const double2 t0 = cadd(v0, v2), t1 = csub(v0, v2), t2 = cadd(v1, v3);
+        const double2 t3 = rot<SIGN>(csub(v1, v3));
         b[base] = cadd(t0, t2);
         b[base + Ns] = cadd(t1, t3);
         b[base + 2 * Ns] = csub(t0, t2);
         b[base + 3 * Ns] = csub(t1, t3);
       } else if (R == 2) {
         double2 v0 = a[j], v1 = a[j + nb];
-        if (k) v1 = cmul(v1, twL(WM, k * tstep, sign));
+        if (k) v1 = cmul(v1, twL<SIGN>(WM, k * tstep));
         b[base] = cadd(v0, v1);
         b[base + Ns] = csub(v0, v1);
       } else {  // R == 3
         double2 v0 = a[j], v1 = a[j + nb], v2 = a[j + 2 * nb];
         if (k) {
-          v1 = cmul(v1, twL(WM, k * tstep, sign));
-          v2 = cmul(v2, twL(WM, 2 * k * tstep, sign));
+          v1 = cmul(v1, twL<SIGN>(WM, k * tstep));
+          v2 = cmul(v2, twL<SIGN>(WM, 2 * k * tstep));
         }
         const double h = 0.86602540378443864676;  // sqrt(3)/2
-        double2 t = cadd(v1, v2);
-        double2 m = make_double2(fma(-0.5, t.x, v0.x), fma(-0.5, t.y, v0.y));
-        double2 d = cmul_i(csub(v1, v2), s * h);
+        const double2 t = cadd(v1, v2);
+        const double2 m = make_double2(fma(-0.5, t.x, v0.x), fma(-0.5, t.y, v0.y));
+        const double2 d = rot<SIGN>(cscale(csub(v1, v2), h));
         b[base] = cadd(v0, t);
         b[base + Ns] = cadd(m, d);
         b[base + 2 * Ns] = csub(m, d);
@@ -104,28 +110,39 @@ static __device__ __noinline__ double2* cfft_smem(double2* a, double2* b, const 
   return a;
 }
 
+__device__ __forceinline__ double2* cfft_smem(double2* a, double2* b, const FFTPlan p, const double2* __restrict__ WM,
+                                              int sign) {
+  return sign > 0 ? cfft_smem_t<1>(a, b, p, WM) : cfft_smem_t<-1>(a, b, p, WM);
+}
+
 // ---- real transforms on the packed half-length sequence ---------------------------------
 //
 // c2r: coefficients c_k (k < K, read through get(k)) of a real field, g_j = sum over the
 // Hermitian-completed spectrum with weights w0 (k = 0, real part only) and w (k >= 1):
 //   g_j = w0 Re c_0 + w * 2 Re sum_{k=1}^{K-1} c_k e^{2 pi i k j / M}
 // Fills Z (length L) so that the inverse L-point FFT of Z is z_j = g_{2j} + i g_{2j+1}.
-template <class Get>
-__device__ __forceinline__ void c2r_pre(double2* Z, Get get, int K, int L, const double2* __restrict__ WM,
-                                        double w0, double w) {
+template <bool UNIT, class Get>
+__device__ __forceinline__ void c2r_pre_t(double2* Z, Get get, int K, int L, const double2* __restrict__ WM,
+                                          double w0, double w) {
   for (int k = threadIdx.x; k < L; k += blockDim.x) {
     double2 xk = make_double2(0.0, 0.0), xc = make_double2(0.0, 0.0);
     if (k == 0) {
-      xk = make_double2(w0 * get(0).x, 0.0);
+      xk = make_double2(UNIT ? get(0).x : w0 * get(0).x, 0.0);
     } else if (k < K) {
-      xk = cscale(get(k), w);
+      xk = UNIT ? get(k) : cscale(get(k), w);
     }
     const int kc = L - k;  // partner index (k = 0 pairs with the unstored Nyquist L)
-    if (k > 0 && kc < K) xc = cconj(cscale(get(kc), w));
+    if (k > 0 && kc < K) xc = cconj(UNIT ? get(kc) : cscale(get(kc), w));
     double2 e = cadd(xk, xc);
     double2 o = cmul(csub(xk, xc), cconj(__ldg(&WM[k])));  // * exp(+2 pi i k / M)
     Z[k] = make_double2(e.x - o.y, e.y + o.x);            // e + i o
   }
+}
+template <class Get>
+__device__ __forceinline__ void c2r_pre(double2* Z, Get get, int K, int L, const double2* __restrict__ WM,
+                                        double w0, double w) {
+  if (w0 == 1.0 && w == 1.0) c2r_pre_t<true>(Z, get, K, L, WM, w0, w);
+  else c2r_pre_t<false>(Z, get, K, L, WM, w0, w);
 }
 
 // r2c post: z = forward L-point FFT of the packed real field; returns

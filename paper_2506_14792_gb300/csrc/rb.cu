@@ -13,6 +13,7 @@
 // F is evaluated pseudospectrally: z transforms (Chebyshev matrices with reflection
 // folding), x FFTs, grid products, back to T space (Sparse spectral methods section).
 #include <cmath>
+#include <functional>
 #include <mutex>
 #include <vector>
 
@@ -37,11 +38,18 @@ struct RB : EqImpl {
   size_t npts = 0;  // grid points Mz*Mx
   XParams xp{};
   // device constants
-  DevBuf wm, czE, cdzE, gzF, gzTE, czTF, cdzTF, gmat, phi;
+  DevBuf wm, czE, cdzE, gzF, gzTE, czTF, cdzTF, gmat, phi, phiT;
   // device work buffers
   DevBuf Z, G0, G1, dG, Gb, Fg, Y, f0, f1, df0, df1, x1, dx1, vb2, vb1, xb1, tmpx, tmpy, ybar, ybar2, cur, nxt,
       partial, Jdev, seedbuf, slots, traj_tmp;
   size_t zsmem = 0, xsmem = 0, ssmem = 0;
+  // internal streams (joined to the caller's stream by events) and captured step graphs
+  cudaStream_t gs = nullptr, gs2 = nullptr;
+  cudaEvent_t evIn = nullptr, evOut = nullptr, evFork = nullptr, evJoin = nullptr;
+  cudaGraphExec_t gFwd[2] = {nullptr, nullptr};
+  cudaGraphExec_t gAdj[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+  double2* Sb[2] = {nullptr, nullptr};  // state ping-pong buffers
+  double2* Yb[2] = {nullptr, nullptr};  // cotangent ping-pong buffers
 
   size_t state_len(int which) const override {
     if (which == 0) return 2 * ns;
@@ -93,7 +101,7 @@ struct RB : EqImpl {
     if (!rbhost::build_phi(o, Kx, Lx, nu, kappa, dt * gam, ph, &err)) return p->fail(SPADJ_ERR_INVALID, err);
     // split Phi' (3N x 3N per pencil) into its two reflection-parity blocks
     const int Nh = N / 2, H = 3 * Nh, np = 3 * N;
-    std::vector<double> pb((size_t)Kx * 2 * H * H);
+    std::vector<double> pb((size_t)Kx * 2 * H * H), pbT((size_t)Kx * 2 * H * H);
     auto cls_idx = [&](int cls, int c) {  // class-local index -> global prognostic index
       const int f = c / Nh, h = c % Nh;
       const int n = 2 * h + ((f == 0) ? cls : 1 - cls);
@@ -103,7 +111,11 @@ struct RB : EqImpl {
       for (int cls = 0; cls < 2; ++cls)
         for (int r = 0; r < H; ++r)
           for (int c = 0; c < H; ++c)
-            pb[(((size_t)m * 2 + cls) * H + r) * H + c] = ph[(size_t)m * np * np + (size_t)cls_idx(cls, r) * np + cls_idx(cls, c)];
+          {
+            const double v = ph[(size_t)m * np * np + (size_t)cls_idx(cls, r) * np + cls_idx(cls, c)];
+            pb[(((size_t)m * 2 + cls) * H + r) * H + c] = v;   // [r][c]
+            pbT[(((size_t)m * 2 + cls) * H + c) * H + r] = v;  // [c][r]
+          }
     // half matrices for the reflection-folded z transforms
     const int Mh = Mz / 2;
     std::vector<double> hczE((size_t)Mh * N), hcdzE((size_t)Mh * N), hgzF((size_t)N * Mh), hgzTE((size_t)Mh * N),
@@ -136,6 +148,7 @@ struct RB : EqImpl {
     SPADJ_CUDA_TRY(p, up(cdzTF, hcdzTF.data(), sizeof(double) * hcdzTF.size()));
     SPADJ_CUDA_TRY(p, up(gmat, o.G.data(), sizeof(double) * o.G.size()));
     SPADJ_CUDA_TRY(p, up(phi, pb.data(), sizeof(double) * pb.size()));
+    SPADJ_CUDA_TRY(p, up(phiT, pbT.data(), sizeof(double) * pbT.size()));
     SPADJ_CUDA_TRY(p, cudaStreamSynchronize(p->stream));
     xp.WM = wm.as<double2>();
     // work buffers
@@ -149,11 +162,17 @@ struct RB : EqImpl {
     SPADJ_CUDA_TRY(p, Fg.ensure(3 * gb));
     for (DevBuf* b : {&f0, &f1, &df0, &df1, &x1, &dx1, &vb2, &vb1, &xb1, &tmpx, &tmpy, &ybar, &ybar2, &cur, &nxt, &seedbuf})
       SPADJ_CUDA_TRY(p, b->ensure(sb));
+    Sb[0] = cur.as<double2>(); Sb[1] = nxt.as<double2>();
+    Yb[0] = ybar.as<double2>(); Yb[1] = ybar2.as<double2>();
+    SPADJ_CUDA_TRY(p, cudaStreamCreateWithFlags(&gs, cudaStreamNonBlocking));
+    SPADJ_CUDA_TRY(p, cudaStreamCreateWithFlags(&gs2, cudaStreamNonBlocking));
+    for (cudaEvent_t* e : {&evIn, &evOut, &evFork, &evJoin})
+      SPADJ_CUDA_TRY(p, cudaEventCreateWithFlags(e, cudaEventDisableTiming));
     SPADJ_CUDA_TRY(p, partial.ensure(sizeof(double) * Kx));
     SPADJ_CUDA_TRY(p, Jdev.ensure(sizeof(double)));
     zsmem = (size_t)2 * 2 * (size_t)std::max(N, Mz / 2) * kTM * sizeof(double2);
     xsmem = sizeof(double2) * (4 * L + Kx);
-    ssmem = sizeof(double) * (size_t)H * kSolveRows + sizeof(double2) * (H + 4 * kSolveRows);
+    ssmem = sizeof(double2) * (H + 4 * solve_rows(H));
     return SPADJ_OK;
   }
 
@@ -172,9 +191,10 @@ struct RB : EqImpl {
   }
   spadj_status launch_z(Problem* p, ZJobs& js) {
     js.ncols = Kx;
-    dim3 grid((Kx + kTM - 1) / kTM, js.n);
+    dim3 grid(Kx, js.n);
+    const int threads = zmm_threads(js.expand, js.j[0].I);
     cudaEvent_t t = p->tic();
-    zmm_kernel<<<grid, 128, zsmem, p->stream>>>(js);
+    zmm_kernel<<<grid, threads, zsmem, p->stream>>>(js);
     p->toc(t, KC_ZTRANSFORM, zflops(js));
     return check_launch(p, "rb zmm");
   }
@@ -354,11 +374,12 @@ struct RB : EqImpl {
   spadj_status solve(Problem* p, int transpose, int nin, const double2* const* in, const double* a, double2* out) {
     SolveArgs S{};
     for (int t = 0; t < nin; ++t) { S.in[t] = in[t]; S.a[t] = a[t]; }
-    S.nin = nin; S.out = out; S.transpose = transpose; S.phi = phi.as<double>(); S.Kx = Kx; S.N = N;
+    S.nin = nin; S.out = out; S.transpose = transpose; S.phiF = phiT.as<double>(); S.phiA = phi.as<double>();
+    S.Kx = Kx; S.N = N;
     const int H = 3 * N / 2;
-    dim3 grid(Kx, 2, (H + kSolveRows - 1) / kSolveRows);
+    dim3 grid(Kx, 2, 2);
     cudaEvent_t t = p->tic();
-    solve_kernel<<<grid, 128, ssmem, p->stream>>>(S);
+    solve_kernel<<<grid, 4 * solve_rows(H), ssmem, p->stream>>>(S);
     // two real H x H matvecs per pencil, each on two right-hand sides (re, im)
     p->toc(t, KC_SOLVE, 2.0 * Kx * 2.0 * H * H * 2.0);
     return check_launch(p, "rb solve");
@@ -396,12 +417,25 @@ struct RB : EqImpl {
   // xb0 = cotangent of X_n from xb2 = cotangent of X_{n+1}, primal x0 = X_n.
   spadj_status step_adj(Problem* p, const double2* x0, const double2* xb2, double2* xb0) {
     spadj_status s;
+    // the transposed stage-2 solve does not depend on the stage recomputation: it runs on the
+    // second internal stream and overlaps it
+    SPADJ_CUDA_TRY(p, cudaEventRecord(evFork, p->stream));
+    SPADJ_CUDA_TRY(p, cudaStreamWaitEvent(gs2, evFork, 0));
+    {
+      cudaStream_t main = p->stream;
+      p->stream = gs2;
+      const double2* in[1] = {xb2};
+      double a[1] = {1.0};
+      s = solve(p, 1, 1, in, a, st(vb2));
+      p->stream = main;
+      if (s != SPADJ_OK) return s;
+    }
+    SPADJ_CUDA_TRY(p, cudaEventRecord(evJoin, gs2));
     if ((s = evalF(p, x0, st(f0), G0)) != SPADJ_OK) return s;
     { const double2* in[2] = {x0, st(f0)}; double a[2] = {1.0, dt * A10};
       if ((s = solve(p, 0, 2, in, a, st(x1))) != SPADJ_OK) return s; }
     if (nonlinear && (s = c2g_fields(p, st(x1), G1)) != SPADJ_OK) return s;
-    { const double2* in[1] = {xb2}; double a[1] = {1.0};
-      if ((s = solve(p, 1, 1, in, a, st(vb2))) != SPADJ_OK) return s; }
+    SPADJ_CUDA_TRY(p, cudaStreamWaitEvent(p->stream, evJoin, 0));
     // xb1 = c vb2 + (dF/dx1)^dagger (dt A21 vb2)
     { const double2* fb[1] = {st(vb2)}; double al[1] = {dt * A21};
       const double2* ad[1] = {st(vb2)}; double be[1] = {cc};
@@ -499,48 +533,118 @@ struct RB : EqImpl {
     return solve(p, transpose, 1, in, a, reinterpret_cast<double2*>(x));
   }
 
+  // Run the library's work on its internal stream, ordered after the caller's stream on
+  // entry and before it on exit.
+  struct StreamScope {
+    RB* r;
+    Problem* p;
+    cudaStream_t us;
+    StreamScope(RB* r_, Problem* p_) : r(r_), p(p_), us(p_->stream) {
+      cudaEventRecord(r->evIn, us);
+      cudaStreamWaitEvent(r->gs, r->evIn, 0);
+      p->stream = r->gs;
+    }
+    ~StreamScope() {
+      cudaEventRecord(r->evOut, r->gs);
+      cudaStreamWaitEvent(us, r->evOut, 0);
+      p->stream = us;
+    }
+  };
+
+  bool use_graphs(Problem* p) const { return !p->timing.enabled; }
+
+  spadj_status capture(Problem* p, cudaGraphExec_t* exec, const std::function<spadj_status()>& body) {
+    SPADJ_CUDA_TRY(p, cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal));
+    spadj_status s = body();
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(p->stream, &g);
+    if (s != SPADJ_OK) {
+      if (g) cudaGraphDestroy(g);
+      return s;
+    }
+    if (e != cudaSuccess) return p->fail(SPADJ_ERR_CUDA, std::string("rb: graph capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return p->fail(SPADJ_ERR_CUDA, std::string("rb: graph instantiate: ") + cudaGetErrorString(e));
+    return SPADJ_OK;
+  }
+
+  // one forward step Sb[ci] -> Sb[1-ci] (captured graph when timing is off)
+  spadj_status run_fwd(Problem* p, int ci) {
+    double2* x0 = Sb[ci];
+    double2* x2 = Sb[1 - ci];
+    if (!use_graphs(p)) return step_fwd(p, x0, x2);
+    if (!gFwd[ci]) {
+      spadj_status s = capture(p, &gFwd[ci], [&] { return step_fwd(p, x0, x2); });
+      if (s != SPADJ_OK) return s;
+    }
+    SPADJ_CUDA_TRY(p, cudaGraphLaunch(gFwd[ci], p->stream));
+    return SPADJ_OK;
+  }
+
+  // one adjoint step at state Sb[ci]: Yb[yi] (cotangent of X_{n+1}) -> Yb[1-yi] (of X_n)
+  spadj_status run_adj(Problem* p, int ci, int yi) {
+    const double2* x0 = Sb[ci];
+    const double2* xb2 = Yb[yi];
+    double2* xb0 = Yb[1 - yi];
+    if (!use_graphs(p)) return step_adj(p, x0, xb2, xb0);
+    if (!gAdj[ci][yi]) {
+      spadj_status s = capture(p, &gAdj[ci][yi], [&] { return step_adj(p, x0, xb2, xb0); });
+      if (s != SPADJ_OK) return s;
+    }
+    SPADJ_CUDA_TRY(p, cudaGraphLaunch(gAdj[ci][yi], p->stream));
+    return SPADJ_OK;
+  }
+
   spadj_status forward(Problem* p, int n_steps, const double* x0, double* x_out, double* traj) override {
     if (n_steps < 0) return p->fail(SPADJ_ERR_INVALID, "forward: n_steps < 0");
     const size_t sb = sizeof(double2) * ns;
-    SPADJ_CUDA_TRY(p, cudaMemcpyAsync(cur.ptr, x0, sb, cudaMemcpyDeviceToDevice, p->stream));
+    StreamScope scope(this, p);
+    int ci = 0;
+    SPADJ_CUDA_TRY(p, cudaMemcpyAsync(Sb[ci], x0, sb, cudaMemcpyDeviceToDevice, p->stream));
     if (traj) SPADJ_CUDA_TRY(p, cudaMemcpyAsync(traj, x0, sb, cudaMemcpyDeviceToDevice, p->stream));
     for (int n = 0; n < n_steps; ++n) {
-      spadj_status s = step_fwd(p, cur.as<double2>(), nxt.as<double2>());
+      spadj_status s = run_fwd(p, ci);
       if (s != SPADJ_OK) return s;
-      std::swap(cur, nxt);
+      ci = 1 - ci;
       if (traj)
-        SPADJ_CUDA_TRY(p, cudaMemcpyAsync(traj + (size_t)(n + 1) * 2 * ns, cur.ptr, sb, cudaMemcpyDeviceToDevice, p->stream));
+        SPADJ_CUDA_TRY(p, cudaMemcpyAsync(traj + (size_t)(n + 1) * 2 * ns, Sb[ci], sb, cudaMemcpyDeviceToDevice, p->stream));
     }
-    SPADJ_CUDA_TRY(p, cudaMemcpyAsync(x_out, cur.ptr, sb, cudaMemcpyDeviceToDevice, p->stream));
+    SPADJ_CUDA_TRY(p, cudaMemcpyAsync(x_out, Sb[ci], sb, cudaMemcpyDeviceToDevice, p->stream));
     return SPADJ_OK;
   }
 
   spadj_status tangent(Problem* p, int n_steps, const double* x0, const double* dx0, double* dx_out) override {
     if (n_steps < 0) return p->fail(SPADJ_ERR_INVALID, "tangent: n_steps < 0");
     const size_t sb = sizeof(double2) * ns;
-    SPADJ_CUDA_TRY(p, cudaMemcpyAsync(cur.ptr, x0, sb, cudaMemcpyDeviceToDevice, p->stream));
-    SPADJ_CUDA_TRY(p, cudaMemcpyAsync(tmpx.ptr, dx0, sb, cudaMemcpyDeviceToDevice, p->stream));
+    StreamScope scope(this, p);
+    double2* T[2] = {tmpx.as<double2>(), tmpy.as<double2>()};
+    int ci = 0;
+    SPADJ_CUDA_TRY(p, cudaMemcpyAsync(Sb[ci], x0, sb, cudaMemcpyDeviceToDevice, p->stream));
+    SPADJ_CUDA_TRY(p, cudaMemcpyAsync(T[ci], dx0, sb, cudaMemcpyDeviceToDevice, p->stream));
     for (int n = 0; n < n_steps; ++n) {
-      spadj_status s = step_tan(p, cur.as<double2>(), tmpx.as<double2>(), nxt.as<double2>(), tmpy.as<double2>());
+      spadj_status s = step_tan(p, Sb[ci], T[ci], Sb[1 - ci], T[1 - ci]);
       if (s != SPADJ_OK) return s;
-      std::swap(cur, nxt);
-      std::swap(tmpx, tmpy);
+      ci = 1 - ci;
     }
-    SPADJ_CUDA_TRY(p, cudaMemcpyAsync(dx_out, tmpx.ptr, sb, cudaMemcpyDeviceToDevice, p->stream));
+    SPADJ_CUDA_TRY(p, cudaMemcpyAsync(dx_out, T[ci], sb, cudaMemcpyDeviceToDevice, p->stream));
     return SPADJ_OK;
   }
 
   spadj_status adjoint(Problem* p, int n_steps, const double* traj, const double* y_final, double* grad) override {
     if (n_steps < 1) return p->fail(SPADJ_ERR_INVALID, "adjoint: n_steps < 1");
     const size_t sb = sizeof(double2) * ns;
-    SPADJ_CUDA_TRY(p, cudaMemcpyAsync(ybar.ptr, y_final, sb, cudaMemcpyDeviceToDevice, p->stream));
+    StreamScope scope(this, p);
+    int yi = 0;
+    SPADJ_CUDA_TRY(p, cudaMemcpyAsync(Yb[yi], y_final, sb, cudaMemcpyDeviceToDevice, p->stream));
     for (int n = n_steps - 1; n >= 0; --n) {
       const double2* xn = reinterpret_cast<const double2*>(traj) + (size_t)n * ns;
-      spadj_status s = step_adj(p, xn, ybar.as<double2>(), ybar2.as<double2>());
+      SPADJ_CUDA_TRY(p, cudaMemcpyAsync(Sb[0], xn, sb, cudaMemcpyDeviceToDevice, p->stream));
+      spadj_status s = run_adj(p, 0, yi);
       if (s != SPADJ_OK) return s;
-      std::swap(ybar, ybar2);
+      yi = 1 - yi;
     }
-    SPADJ_CUDA_TRY(p, cudaMemcpyAsync(grad, ybar.ptr, sb, cudaMemcpyDeviceToDevice, p->stream));
+    SPADJ_CUDA_TRY(p, cudaMemcpyAsync(grad, Yb[yi], sb, cudaMemcpyDeviceToDevice, p->stream));
     return SPADJ_OK;
   }
 
@@ -570,7 +674,9 @@ struct RB : EqImpl {
     SPADJ_CUDA_TRY(p, slots.ensure(sb * (size_t)S));
     CkptPlanner planner;
     std::vector<CkptOp> ops = planner.plan(n_steps, S);
-    SPADJ_CUDA_TRY(p, cudaMemcpyAsync(cur.ptr, x0, sb, cudaMemcpyDeviceToDevice, p->stream));
+    StreamScope scope(this, p);
+    int ci = 0, yi = 0;
+    SPADJ_CUDA_TRY(p, cudaMemcpyAsync(Sb[ci], x0, sb, cudaMemcpyDeviceToDevice, p->stream));
     int cur_step = 0;
     int recompute = 0;
     bool have_seed = false;
@@ -579,38 +685,39 @@ struct RB : EqImpl {
       spadj_status s = SPADJ_OK;
       switch (op.type) {
         case CK_STORE:
-          SPADJ_CUDA_TRY(p, cudaMemcpyAsync(slot_ptr(op.slot), cur.ptr, sb, cudaMemcpyDeviceToDevice, p->stream));
+          SPADJ_CUDA_TRY(p, cudaMemcpyAsync(slot_ptr(op.slot), Sb[ci], sb, cudaMemcpyDeviceToDevice, p->stream));
           break;
         case CK_RESTORE:
           if (cur_step != op.a) {
-            SPADJ_CUDA_TRY(p, cudaMemcpyAsync(cur.ptr, slot_ptr(op.slot), sb, cudaMemcpyDeviceToDevice, p->stream));
+            SPADJ_CUDA_TRY(p, cudaMemcpyAsync(Sb[ci], slot_ptr(op.slot), sb, cudaMemcpyDeviceToDevice, p->stream));
             cur_step = op.a;
           }
           break;
         case CK_ADVANCE:
           for (int k = op.a; k < op.b; ++k) {
-            if ((s = step_fwd(p, cur.as<double2>(), nxt.as<double2>())) != SPADJ_OK) return s;
-            std::swap(cur, nxt);
+            if ((s = run_fwd(p, ci)) != SPADJ_OK) return s;
+            ci = 1 - ci;
             ++recompute;
           }
           cur_step = op.b;
           break;
         case CK_OBJECTIVE:
-          if ((s = objective(p, objective_kind, obj_data, cur.as<double>(), Jdev.as<double>(), ybar.as<double>())) != SPADJ_OK)
+          if ((s = objective(p, objective_kind, obj_data, reinterpret_cast<const double*>(Sb[ci]), Jdev.as<double>(),
+                             reinterpret_cast<double*>(Yb[yi]))) != SPADJ_OK)
             return s;
           have_seed = true;
           break;
         case CK_ADJOINT:
           if (!have_seed) return p->fail(SPADJ_ERR_INVALID, "gradient: schedule reached an adjoint step before the objective");
-          if ((s = step_adj(p, cur.as<double2>(), ybar.as<double2>(), ybar2.as<double2>())) != SPADJ_OK) return s;
-          std::swap(ybar, ybar2);
+          if ((s = run_adj(p, ci, yi)) != SPADJ_OK) return s;
+          yi = 1 - yi;
           break;
         default:
           break;
       }
     }
     last_recompute = recompute;
-    SPADJ_CUDA_TRY(p, cudaMemcpyAsync(grad, ybar.ptr, sb, cudaMemcpyDeviceToDevice, p->stream));
+    SPADJ_CUDA_TRY(p, cudaMemcpyAsync(grad, Yb[yi], sb, cudaMemcpyDeviceToDevice, p->stream));
     if (J_host) {
       SPADJ_CUDA_TRY(p, cudaMemcpyAsync(J_host, Jdev.ptr, sizeof(double), cudaMemcpyDeviceToHost, p->stream));
       SPADJ_CUDA_TRY(p, cudaStreamSynchronize(p->stream));
@@ -620,7 +727,15 @@ struct RB : EqImpl {
   }
 
   ~RB() override {
-    for (DevBuf* b : {&wm, &czE, &cdzE, &gzF, &gzTE, &czTF, &cdzTF, &gmat, &phi, &Z, &G0, &G1, &dG, &Gb, &Fg, &Y, &f0,
+    if (gs) cudaStreamSynchronize(gs);
+    if (gs2) cudaStreamSynchronize(gs2);
+    for (cudaGraphExec_t g : {gFwd[0], gFwd[1], gAdj[0][0], gAdj[0][1], gAdj[1][0], gAdj[1][1]})
+      if (g) cudaGraphExecDestroy(g);
+    for (cudaEvent_t e : {evIn, evOut, evFork, evJoin})
+      if (e) cudaEventDestroy(e);
+    if (gs) cudaStreamDestroy(gs);
+    if (gs2) cudaStreamDestroy(gs2);
+    for (DevBuf* b : {&wm, &czE, &cdzE, &gzF, &gzTE, &czTF, &cdzTF, &gmat, &phi, &phiT, &Z, &G0, &G1, &dG, &Gb, &Fg, &Y, &f0,
                       &f1, &df0, &df1, &x1, &dx1, &vb2, &vb1, &xb1, &tmpx, &tmpy, &ybar, &ybar2, &cur, &nxt, &partial,
                       &Jdev, &seedbuf, &slots, &traj_tmp})
       b->release();

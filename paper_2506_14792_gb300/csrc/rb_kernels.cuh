@@ -42,105 +42,110 @@ struct ZJobs {
   int expand; // 1: expand, 0: fold
 };
 
-constexpr int kTM = 4;  // columns per CTA
+// One CTA per (column, job); the reduction of every output is split over the two lanes of a
+// lane pair and combined with a shuffle, so an expand job runs 2*Mz/2 threads and a fold job
+// 2*N threads per column.
+constexpr int kTM = 1;  // columns per CTA
 
-__global__ void __launch_bounds__(128) zmm_kernel(const __grid_constant__ ZJobs js) {
+__host__ __device__ inline int zmm_threads(int expand, int I) { return 2 * (expand ? I / 2 : I); }
+
+__global__ void __launch_bounds__(256) zmm_kernel(const __grid_constant__ ZJobs js) {
   const ZJob& J = js.j[blockIdx.y];
-  const int m0 = blockIdx.x * kTM;
-  const int ncols = js.ncols;
+  const int m = blockIdx.x;
   extern __shared__ double2 sb[];
   const int tid = threadIdx.x, nt = blockDim.x;
   const int K = J.K, I = J.I;
-  const int Kh = js.expand ? K : K / 2;  // staged rows per term
-  // stage inputs: expand -> raw coefficient columns; fold -> (s, d) = f_j +- f_{Mz-1-j}
+  const int Kh = js.expand ? K : K / 2;  // staged entries per term (and per s/d array)
+  // stage this column: expand -> coefficients; fold -> (s, d) = f_j +- f_{Mz-1-j}
   for (int t = 0; t < J.nterm; ++t) {
-    double2* s = sb + (size_t)t * 2 * Kh * kTM;
-    const double2* src = J.in[t];
-    const bool kfast = (J.ik == 1);
-    for (int idx = tid; idx < Kh * kTM; idx += nt) {
-      int k, mm;
-      if (kfast) { k = idx % Kh; mm = idx / Kh; } else { mm = idx % kTM; k = idx / kTM; }
-      const int m = m0 + mm;
-      double2 v = make_double2(0.0, 0.0), v2 = make_double2(0.0, 0.0);
-      if (m < ncols) {
-        v = src[(size_t)k * J.ik + (size_t)m * J.im];
-        if (!js.expand) v2 = src[(size_t)(K - 1 - k) * J.ik + (size_t)m * J.im];
-      }
+    double2* s = sb + (size_t)t * 2 * Kh;
+    const double2* src = J.in[t] + (size_t)m * J.im;
+    for (int k = tid; k < Kh; k += nt) {
+      const double2 v = src[(size_t)k * J.ik];
       if (js.expand) {
-        s[k * kTM + mm] = v;
+        s[k] = v;
       } else {
-        s[k * kTM + mm] = make_double2(v.x + v2.x, v.y + v2.y);             // s_j
-        s[(Kh + k) * kTM + mm] = make_double2(v.x - v2.x, v.y - v2.y);      // d_j
+        const double2 v2 = src[(size_t)(K - 1 - k) * J.ik];
+        s[k] = make_double2(v.x + v2.x, v.y + v2.y);       // s_j
+        s[Kh + k] = make_double2(v.x - v2.x, v.y - v2.y);  // d_j
       }
     }
   }
   __syncthreads();
-  const int mm = tid % kTM;
-  const int ig = tid / kTM, ng = nt / kTM;
-  const int m = m0 + mm;
+  const int u = tid >> 1, hf = tid & 1;
   if (js.expand) {
     const int Ih = I / 2;
-    for (int i = ig; i < Ih; i += ng) {
-      double2 lo = make_double2(0.0, 0.0), hi = make_double2(0.0, 0.0);
-      for (int t = 0; t < J.nterm; ++t) {
-        const double* a = J.mat[t] + (size_t)i * K;
-        const double2* s = sb + (size_t)t * 2 * Kh * kTM + mm;
-        double2 E = make_double2(0.0, 0.0), O = make_double2(0.0, 0.0);
-        int k = 0;
-        for (; k + 1 < K; k += 2) {
-          const double ae = __ldg(a + k), ao = __ldg(a + k + 1);
-          const double2 ve = s[k * kTM], vo = s[(k + 1) * kTM];
-          E.x = fma(ae, ve.x, E.x); E.y = fma(ae, ve.y, E.y);
-          O.x = fma(ao, vo.x, O.x); O.y = fma(ao, vo.y, O.y);
-        }
-        if (k < K) {
-          const double ae = __ldg(a + k);
-          const double2 ve = s[k * kTM];
-          E.x = fma(ae, ve.x, E.x); E.y = fma(ae, ve.y, E.y);
-        }
-        const double al = J.alpha[t];
-        // out_j = E + O ; out_{Mz-1-j} = E - O (parity (-1)^n) or -E + O (derivative parity)
-        const double se = J.deriv[t] ? -1.0 : 1.0;
-        lo.x = fma(al, E.x + O.x, lo.x); lo.y = fma(al, E.y + O.y, lo.y);
-        hi.x = fma(al, se * (E.x - O.x), hi.x); hi.y = fma(al, se * (E.y - O.y), hi.y);
+    if (u >= Ih) return;
+    const int k0 = hf * (K / 2), k1 = hf ? K : K / 2;  // K even: both halves start on an even k
+    double2 lo = make_double2(0.0, 0.0), hi = make_double2(0.0, 0.0);
+    for (int t = 0; t < J.nterm; ++t) {
+      const double* a = J.mat[t] + (size_t)u * K;
+      const double2* s = sb + (size_t)t * 2 * Kh;
+      double2 E = make_double2(0.0, 0.0), O = make_double2(0.0, 0.0);
+#pragma unroll 4
+      for (int k = k0; k < k1; k += 2) {
+        const double ae = __ldg(a + k), ao = __ldg(a + k + 1);
+        const double2 ve = s[k], vo = s[k + 1];
+        E.x = fma(ae, ve.x, E.x); E.y = fma(ae, ve.y, E.y);
+        O.x = fma(ao, vo.x, O.x); O.y = fma(ao, vo.y, O.y);
       }
-      if (m < ncols) {
-        const size_t o1 = (size_t)i * J.oi + (size_t)m * J.om;
-        const size_t o2 = (size_t)(I - 1 - i) * J.oi + (size_t)m * J.om;
-        for (int a = 0; a < J.nadd; ++a) {
-          const double2 p = J.add[a][o1], q = J.add[a][o2];
-          lo.x = fma(J.beta[a], p.x, lo.x); lo.y = fma(J.beta[a], p.y, lo.y);
-          hi.x = fma(J.beta[a], q.x, hi.x); hi.y = fma(J.beta[a], q.y, hi.y);
-        }
-        J.out[o1] = lo;
-        J.out[o2] = hi;
+      E.x += __shfl_xor_sync(__activemask(), E.x, 1);
+      E.y += __shfl_xor_sync(__activemask(), E.y, 1);
+      O.x += __shfl_xor_sync(__activemask(), O.x, 1);
+      O.y += __shfl_xor_sync(__activemask(), O.y, 1);
+      const double al = J.alpha[t];
+      // out_j = E + O ; out_{Mz-1-j} = E - O (parity (-1)^n) or -E + O (derivative parity)
+      const double se = J.deriv[t] ? -1.0 : 1.0;
+      lo.x = fma(al, E.x + O.x, lo.x); lo.y = fma(al, E.y + O.y, lo.y);
+      hi.x = fma(al, se * (E.x - O.x), hi.x); hi.y = fma(al, se * (E.y - O.y), hi.y);
+    }
+    if (hf == 0) {
+      const size_t o1 = (size_t)u * J.oi + (size_t)m * J.om;
+      const size_t o2 = (size_t)(I - 1 - u) * J.oi + (size_t)m * J.om;
+      for (int a = 0; a < J.nadd; ++a) {
+        const double2 p = J.add[a][o1], q = J.add[a][o2];
+        lo.x = fma(J.beta[a], p.x, lo.x); lo.y = fma(J.beta[a], p.y, lo.y);
+        hi.x = fma(J.beta[a], q.x, hi.x); hi.y = fma(J.beta[a], q.y, hi.y);
       }
+      J.out[o1] = lo;
+      J.out[o2] = hi;
     }
   } else {
+    if (u >= I) return;
     const int Kf = K / 2;
-    for (int i = ig; i < I; i += ng) {
-      double2 acc = make_double2(0.0, 0.0);
-      for (int t = 0; t < J.nterm; ++t) {
-        const double* a = J.mat[t] + (size_t)i * Kf;
-        // even i pairs with s for parity (-1)^n, with d for derivative parity
-        const bool use_s = ((i & 1) == 0) != (J.deriv[t] != 0);
-        const double2* s = sb + (size_t)t * 2 * Kh * kTM + (use_s ? 0 : Kh * kTM) + mm;
-        double2 v = make_double2(0.0, 0.0);
-        for (int k = 0; k < Kf; ++k) {
-          const double av = __ldg(a + k);
-          const double2 x = s[k * kTM];
-          v.x = fma(av, x.x, v.x); v.y = fma(av, x.y, v.y);
-        }
-        acc.x = fma(J.alpha[t], v.x, acc.x); acc.y = fma(J.alpha[t], v.y, acc.y);
+    const int k0 = hf * (Kf / 2), k1 = hf ? Kf : Kf / 2;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int t = 0; t < J.nterm; ++t) {
+      const double* a = J.mat[t] + (size_t)u * Kf;
+      // even rows pair with s for parity (-1)^n, with d for derivative parity
+      const bool use_s = ((u & 1) == 0) != (J.deriv[t] != 0);
+      const double2* s = sb + (size_t)t * 2 * Kh + (use_s ? 0 : Kh);
+      double2 v0 = make_double2(0.0, 0.0), v1 = make_double2(0.0, 0.0);
+      int k = k0;
+#pragma unroll 4
+      for (; k + 1 < k1; k += 2) {
+        const double a0 = __ldg(a + k), a1 = __ldg(a + k + 1);
+        const double2 x0 = s[k], x1 = s[k + 1];
+        v0.x = fma(a0, x0.x, v0.x); v0.y = fma(a0, x0.y, v0.y);
+        v1.x = fma(a1, x1.x, v1.x); v1.y = fma(a1, x1.y, v1.y);
       }
-      if (m < ncols) {
-        const size_t o = (size_t)i * J.oi + (size_t)m * J.om;
-        for (int a = 0; a < J.nadd; ++a) {
-          const double2 p = J.add[a][o];
-          acc.x = fma(J.beta[a], p.x, acc.x); acc.y = fma(J.beta[a], p.y, acc.y);
-        }
-        J.out[o] = acc;
+      if (k < k1) {
+        const double a0 = __ldg(a + k);
+        const double2 x0 = s[k];
+        v0.x = fma(a0, x0.x, v0.x); v0.y = fma(a0, x0.y, v0.y);
       }
+      double vx = v0.x + v1.x, vy = v0.y + v1.y;
+      vx += __shfl_xor_sync(__activemask(), vx, 1);
+      vy += __shfl_xor_sync(__activemask(), vy, 1);
+      acc.x = fma(J.alpha[t], vx, acc.x); acc.y = fma(J.alpha[t], vy, acc.y);
+    }
+    if (hf == 0) {
+      const size_t o = (size_t)u * J.oi + (size_t)m * J.om;
+      for (int a = 0; a < J.nadd; ++a) {
+        const double2 p = J.add[a][o];
+        acc.x = fma(J.beta[a], p.x, acc.x); acc.y = fma(J.beta[a], p.y, acc.y);
+      }
+      J.out[o] = acc;
     }
   }
 }
@@ -283,26 +288,33 @@ __global__ void prod_vjp_kernel(const double* __restrict__ G, const double* __re
 
 // Stage solve x = Phi v per pencil and parity class (or the adjoint v = Phi^H x), with the
 // right-hand side formed on the fly as v = sum_t a_t in_t.  Phi = Dc Phi' Dr with real
-// Phi' stored per pencil as two (3N/2)^2 parity blocks; Dr, Dc^H and the projection of the
-// mean pencil onto real coefficients are applied on load and store.
+// Phi' stored per pencil as two (3N/2)^2 parity blocks, once as [k][r] = Phi'[r][k] (read by
+// the forward map) and once as [k][r] = Phi'[k][r] (read by the adjoint map), so that the
+// threads of a warp, which own consecutive output rows r, read consecutive addresses.  Dr,
+// Dc^H and the projection of the mean pencil onto real coefficients are applied on load and
+// store.  CTA = (pencil, class, half of the rows); thread = (row, quarter of the columns).
 struct SolveArgs {
   const double2* in[4];
   double a[4];
   int nin;
   double2* out;
   int transpose;
-  const double* phi;  // [Kx][2][H][H], H = 3N/2
+  const double* phiF;  // [Kx][2][H][H] as [k][r] = Phi'[r][k]
+  const double* phiA;  // [Kx][2][H][H] as [k][r] = Phi'[k][r]
   int Kx, N;
 };
 
-constexpr int kSolveRows = 32;  // output rows per CTA (4 warps split the reduction in quarters)
+__host__ __device__ inline int solve_rows(int H) { return (H + 1) / 2; }
 
-__global__ void __launch_bounds__(128) solve_kernel(const __grid_constant__ SolveArgs S) {
-  const int m = blockIdx.x, cls = blockIdx.y, r0 = blockIdx.z * kSolveRows;
+__global__ void __launch_bounds__(1024) solve_kernel(const __grid_constant__ SolveArgs S) {
+  const int m = blockIdx.x, cls = blockIdx.y;
   const int N = S.N, Nh = N / 2, H = 3 * Nh, Kx = S.Kx;
-  extern __shared__ double sphi[];      // [H][kSolveRows] block of Phi' (or its transpose)
-  double2* v = reinterpret_cast<double2*>(sphi + (size_t)H * kSolveRows);  // [H]
-  const double* blk = S.phi + ((size_t)m * 2 + cls) * H * H;
+  const int RH = solve_rows(H);
+  const int r0 = blockIdx.z * RH;
+  extern __shared__ double2 sv[];  // v[H], then red[4][RH]
+  double2* v = sv;
+  double2* red = sv + H;
+  const double* blk = (S.transpose ? S.phiA : S.phiF) + ((size_t)m * 2 + cls) * H * H;
   const int tid = threadIdx.x, nt = blockDim.x;
   // class index c -> (field f, mode n)
   for (int c = tid; c < H; c += nt) {
@@ -319,41 +331,32 @@ __global__ void __launch_bounds__(128) solve_kernel(const __grid_constant__ Solv
     if (f == 0) x = make_double2(x.y, -x.x);        // times -i (Dr, or Dc^H)
     v[c] = x;
   }
-  // stage rows r0..r0+R of Phi' (forward) or columns r0..r0+R (adjoint) as [k][r]
-  const int R = min(kSolveRows, H - r0);
-  for (int idx = tid; idx < H * kSolveRows; idx += nt) {
-    int k, r;
-    double val = 0.0;
-    if (S.transpose) {  // need Phi'[k][r0 + r]: coalesced over r
-      k = idx / kSolveRows; r = idx % kSolveRows;
-      if (r < R) val = blk[(size_t)k * H + r0 + r];
-    } else {            // need Phi'[r0 + r][k]: coalesced over k
-      r = idx / H; k = idx % H;
-      if (r < R) val = blk[(size_t)(r0 + r) * H + k];
-    }
-    sphi[k * kSolveRows + r] = val;
-  }
   __syncthreads();
-  // thread (r, q): partial dot product over the q-th quarter of the columns
-  double2* red = v + H;  // [4][kSolveRows]
-  {
-    const int r = tid % kSolveRows, q = tid / kSolveRows;
-    const int kq = (H + 3) / 4;
-    const int k0 = q * kq, k1 = min(H, k0 + kq);
-    double2 acc = make_double2(0.0, 0.0);
-    for (int k = k0; k < k1; ++k) {
-      const double p = sphi[k * kSolveRows + r];
-      const double2 x = v[k];
-      acc.x = fma(p, x.x, acc.x);
-      acc.y = fma(p, x.y, acc.y);
+  const int rl = tid % RH, q = tid / RH;
+  const int r = r0 + rl;
+  const int kq = (H + 3) / 4;
+  const int k0 = q * kq, k1 = min(H, k0 + kq);
+  double2 acc0 = make_double2(0.0, 0.0), acc1 = make_double2(0.0, 0.0);
+  if (r < H && q < 4) {
+    int k = k0;
+    for (; k + 1 < k1; k += 2) {
+      const double p0 = __ldg(blk + (size_t)k * H + r), p1 = __ldg(blk + (size_t)(k + 1) * H + r);
+      const double2 x0 = v[k], x1 = v[k + 1];
+      acc0.x = fma(p0, x0.x, acc0.x); acc0.y = fma(p0, x0.y, acc0.y);
+      acc1.x = fma(p1, x1.x, acc1.x); acc1.y = fma(p1, x1.y, acc1.y);
     }
-    red[q * kSolveRows + r] = acc;
+    if (k < k1) {
+      const double p0 = __ldg(blk + (size_t)k * H + r);
+      const double2 x0 = v[k];
+      acc0.x = fma(p0, x0.x, acc0.x); acc0.y = fma(p0, x0.y, acc0.y);
+    }
   }
+  if (q < 4) red[q * RH + rl] = cadd(acc0, acc1);
   __syncthreads();
-  for (int r = tid; r < R; r += nt) {
-    double2 acc = red[r];
-    for (int q = 1; q < 4; ++q) acc = cadd(acc, red[q * kSolveRows + r]);
-    const int c = r0 + r;
+  if (tid < RH && r0 + tid < H) {
+    double2 acc = red[tid];
+    for (int qq = 1; qq < 4; ++qq) acc = cadd(acc, red[qq * RH + tid]);
+    const int c = r0 + tid;
     const int f = c / Nh, h = c % Nh;
     const int n = 2 * h + ((f == 0) ? cls : 1 - cls);
     if (f == 0) acc = make_double2(-acc.y, acc.x);  // times i (Dc, or Dr^H)
