@@ -187,6 +187,16 @@ spadj_status spadj_gradient(spadj_problem* prob, const double* x0, int n_steps, 
 spadj_status spadj_timing(spadj_problem* prob, int enable);
 spadj_status spadj_timing_report(spadj_problem* prob, int kernel_class, double* ms, double* flops, long* launches);
 
+/* Vector-Jacobian product of the trajectory map (the reverse-mode building block behind
+ * spadj_gradient and the torch.autograd binding): grad_x0 = sum_i (dX_{n_i}/dX_0)^T seed_i for
+ * cotangents seeds[i] (device, layout [n_seeds][state]) injected at steps seed_steps[i]
+ * (host ints in 0..n_steps, distinct).  Multistep problems keep the whole trajectory; the RK
+ * problem uses ckpt_slots binomial checkpoint slots (<= 0: store every step).  This is the
+ * adjoint sweep of Supplementary A.4 with the objective's partial derivatives replaced by the
+ * given cotangents (4D-Var style injection at intermediate steps included). */
+spadj_status spadj_vjp(spadj_problem* prob, const double* x0, int n_steps, int ckpt_slots, int n_seeds,
+                       const int* seed_steps, const double* seeds, double* grad_x0);
+
 /* One-line description of the last failure on this problem (or of the last failed
  * spadj_create when prob is NULL).  Never NULL. */
 const char* spadj_last_error(const spadj_problem* prob);

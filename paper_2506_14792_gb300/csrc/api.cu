@@ -100,6 +100,22 @@ spadj_status spadj_solve(spadj_problem* p, int transpose, const double* v, doubl
   return spadj::rb_pencil_solve(p->impl, p, transpose, v, x);
 }
 
+spadj_status spadj_vjp(spadj_problem* p, const double* x0, int n_steps, int ckpt_slots, int n_seeds,
+                       const int* seed_steps, const double* seeds, double* grad_x0) {
+  if (!p) return SPADJ_ERR_INVALID;
+  if (bad_ptr(x0) || bad_ptr(grad_x0) || (n_seeds > 0 && (bad_ptr(seed_steps) || bad_ptr(seeds))))
+    return p->fail(SPADJ_ERR_INVALID, "vjp: NULL array");
+  if (n_steps < 1 || n_seeds < 0) return p->fail(SPADJ_ERR_INVALID, "vjp: need n_steps >= 1 and n_seeds >= 0");
+  std::vector<int> seed_at((size_t)n_steps + 1, -1);
+  for (int i = 0; i < n_seeds; ++i) {
+    const int n = seed_steps[i];
+    if (n < 0 || n > n_steps) return p->fail(SPADJ_ERR_INVALID, "vjp: seed step outside 0..n_steps");
+    if (seed_at[n] >= 0) return p->fail(SPADJ_ERR_INVALID, "vjp: repeated seed step");
+    seed_at[n] = i;
+  }
+  return p->impl->vjp(p, x0, n_steps, ckpt_slots, seed_at, seeds, grad_x0);
+}
+
 spadj_status spadj_checkpoint_schedule(int n_steps, int slots, int* ops, int max_ops, int* n_ops) {
   if (n_steps < 1 || slots < 1 || !n_ops) {
     g_create_error = "checkpoint_schedule: need n_steps >= 1, slots >= 1, n_ops != NULL";

@@ -291,9 +291,12 @@ __global__ void __launch_bounds__(64) trajectory_kernel(BurgersParams P, int n_s
 }
 
 // Adjoint sweep (eq. IMEX_adjoint) over traj = X_0..X_N, seeded by y_final = dJ/dX_N.
+// seed_at (nullable, device, n_steps+1 ints): index into seeds ([n][member][k]) of the
+// cotangent injected at X_n, or -1; when seed_at is NULL the only seed is y_final at X_N.
 template <int Q>
 __global__ void __launch_bounds__(64) adjoint_kernel(BurgersParams P, int n_steps, const double* __restrict__ traj,
-                                                     const double* __restrict__ y_final, double* __restrict__ grad) {
+                                                     const double* __restrict__ y_final, double* __restrict__ grad,
+                                                     const int* __restrict__ seed_at, const double* __restrict__ seeds) {
   Smem s = carve(P);
   extern __shared__ double2 sm[];
   double2* S2 = sm + 4 * P.L + 2 * P.K;
@@ -308,7 +311,7 @@ __global__ void __launch_bounds__(64) adjoint_kernel(BurgersParams P, int n_step
     if (n == n_steps) {
       for (int q = 0; q < Q; ++q) {
         int k = tid + q * G;
-        lam[q] = (k < K) ? row(y_final, b, K)[k] : z;
+        lam[q] = (k < K && y_final) ? row(y_final, b, K)[k] : z;
       }
     } else {
       Coef c1 = step_coef(P, n + 1);
@@ -329,6 +332,13 @@ __global__ void __launch_bounds__(64) adjoint_kernel(BurgersParams P, int n_step
         lam[q] = make_double2(v.x - c1.a1 * Y1[q].x - c2.a2 * Y2[q].x, v.y - c1.a1 * Y1[q].y - c2.a2 * Y2[q].y);
       }
       __syncthreads();
+    }
+    if (seed_at && seed_at[n] >= 0) {
+      const double* sv = seeds + (size_t)seed_at[n] * nb * 2 * K;
+      for (int q = 0; q < Q; ++q) {
+        int k = tid + q * G;
+        if (k < K) lam[q] = cadd(lam[q], row(sv, b, K)[k]);
+      }
     }
     if (n == 0) {
       double2* g = row(grad, b, K);
@@ -466,11 +476,37 @@ struct Burgers : EqImpl {
     });
   }
 
+  const int* seed_dev = nullptr;     // set only during vjp()
+  const double* seeds_dev = nullptr;
+  DevBuf seedmap;
+
+  spadj_status vjp(Problem* p, const double* x0, int n_steps, int ckpt_slots, const std::vector<int>& seed_at,
+                   const double* seeds, double* grad) override {
+    (void)ckpt_slots;  // the per-member persistent kernels keep the whole trajectory (store-all)
+    if (n_steps < 1) return p->fail(SPADJ_ERR_INVALID, "vjp: n_steps < 1");
+    const size_t sl = state_len(0);
+    SPADJ_CUDA_TRY(p, traj.ensure(sizeof(double) * sl * (size_t)(n_steps + 1)));
+    SPADJ_CUDA_TRY(p, seedmap.ensure(sizeof(int) * (size_t)(n_steps + 1)));
+    SPADJ_CUDA_TRY(p, cudaMemcpyAsync(seedmap.ptr, seed_at.data(), sizeof(int) * (n_steps + 1), cudaMemcpyHostToDevice,
+                                      p->stream));
+    double* T = traj.as<double>();
+    spadj_status st = forward(p, n_steps, x0, T + (size_t)n_steps * sl, T);
+    if (st != SPADJ_OK) return st;
+    seed_dev = seedmap.as<int>();
+    seeds_dev = seeds;
+    st = adjoint(p, n_steps, T, nullptr, grad);
+    seed_dev = nullptr;
+    seeds_dev = nullptr;
+    if (st != SPADJ_OK) return st;
+    SPADJ_CUDA_TRY(p, cudaStreamSynchronize(p->stream));  // seed_at host staging is pageable
+    return SPADJ_OK;
+  }
+
   spadj_status adjoint(Problem* p, int n_steps, const double* trj, const double* y_final, double* grad) override {
     if (n_steps < 1) return p->fail(SPADJ_ERR_INVALID, "adjoint: n_steps < 1");
     cudaEvent_t t = p->tic();
     spadj_status s = dispatchQ(p, [&](auto q) {
-      adjoint_kernel<decltype(q)::value><<<B, G, smem, p->stream>>>(P, n_steps, trj, y_final, grad);
+      adjoint_kernel<decltype(q)::value><<<B, G, smem, p->stream>>>(P, n_steps, trj, y_final, grad, seed_dev, seeds_dev);
     });
     p->toc(t, KC_FUSED, (double)B * n_steps * (3 * fft_flops() + 2.0 * P.M + 12.0 * P.K));
     return s;
@@ -511,6 +547,7 @@ struct Burgers : EqImpl {
 
   ~Burgers() override {
     wm.release();
+    seedmap.release();
     traj.release();
     seed.release();
     Jd.release();

@@ -59,6 +59,9 @@ struct EqImpl {
   virtual spadj_status gradient(Problem* p, const double* x0, int n_steps, int objective,
                                 const double* obj_data, int ckpt_slots, double* J_host, double* grad_x0,
                                 double* grad_p) = 0;
+  // Reverse sweep seeded by caller cotangents: seed_at[n] indexes `seeds` for X_n (or -1).
+  virtual spadj_status vjp(Problem* p, const double* x0, int n_steps, int ckpt_slots,
+                           const std::vector<int>& seed_at, const double* seeds, double* grad_x0) = 0;
 };
 
 // Optional per-kernel-class timing: CUDA events recorded on the problem's stream around

@@ -664,11 +664,15 @@ struct RB : EqImpl {
 
   int last_recompute = 0;
 
-  spadj_status gradient(Problem* p, const double* x0, int n_steps, int objective_kind, const double* obj_data,
-                        int ckpt_slots, double* J_host, double* grad, double* grad_p) override {
-    (void)grad_p;
+  // Checkpointed reverse sweep.  objective_kind >= 0: seed dJ/dX_N from the objective kernel
+  // (J to J_host).  objective_kind < 0: seeds supplied by the caller, seed_at[n] = index into
+  // `seeds` ([n_seeds][state], device) of the cotangent injected at X_n, or -1.
+  spadj_status reverse(Problem* p, const double* x0, int n_steps, int ckpt_slots, int objective_kind,
+                       const double* obj_data, const std::vector<int>& seed_at, const double* seeds, double* J_host,
+                       double* grad) {
     if (n_steps < 1) return p->fail(SPADJ_ERR_INVALID, "gradient: n_steps < 1");
-    if (objective_kind != SPADJ_OBJ_ENERGY) return p->fail(SPADJ_ERR_UNSUPPORTED, "rb: objective must be ENERGY");
+    if (objective_kind >= 0 && objective_kind != SPADJ_OBJ_ENERGY)
+      return p->fail(SPADJ_ERR_UNSUPPORTED, "rb: objective must be ENERGY");
     int S = (ckpt_slots <= 0 || ckpt_slots > n_steps + 1) ? n_steps + 1 : ckpt_slots;
     const size_t sb = sizeof(double2) * ns;
     SPADJ_CUDA_TRY(p, slots.ensure(sb * (size_t)S));
@@ -681,6 +685,10 @@ struct RB : EqImpl {
     int recompute = 0;
     bool have_seed = false;
     auto slot_ptr = [&](int sl) { return slots.as<char>() + (size_t)sl * sb; };
+    auto seed_ptr = [&](int n) -> const double2* {
+      if (objective_kind >= 0 || n < 0 || n >= (int)seed_at.size() || seed_at[n] < 0) return nullptr;
+      return reinterpret_cast<const double2*>(seeds) + (size_t)seed_at[n] * ns;
+    };
     for (const CkptOp& op : ops) {
       spadj_status s = SPADJ_OK;
       switch (op.type) {
@@ -702,15 +710,25 @@ struct RB : EqImpl {
           cur_step = op.b;
           break;
         case CK_OBJECTIVE:
-          if ((s = objective(p, objective_kind, obj_data, reinterpret_cast<const double*>(Sb[ci]), Jdev.as<double>(),
-                             reinterpret_cast<double*>(Yb[yi]))) != SPADJ_OK)
-            return s;
+          if (objective_kind >= 0) {
+            if ((s = objective(p, objective_kind, obj_data, reinterpret_cast<const double*>(Sb[ci]),
+                               Jdev.as<double>(), reinterpret_cast<double*>(Yb[yi]))) != SPADJ_OK)
+              return s;
+          } else if (const double2* sp = seed_ptr(n_steps)) {
+            SPADJ_CUDA_TRY(p, cudaMemcpyAsync(Yb[yi], sp, sb, cudaMemcpyDeviceToDevice, p->stream));
+          } else {
+            SPADJ_CUDA_TRY(p, cudaMemsetAsync(Yb[yi], 0, sb, p->stream));
+          }
           have_seed = true;
           break;
         case CK_ADJOINT:
           if (!have_seed) return p->fail(SPADJ_ERR_INVALID, "gradient: schedule reached an adjoint step before the objective");
           if ((s = run_adj(p, ci, yi)) != SPADJ_OK) return s;
           yi = 1 - yi;
+          if (const double2* sp = seed_ptr(op.a)) {  // cotangent injected at X_a
+            axpy_kernel<<<64, 256, 0, p->stream>>>(Yb[yi], Yb[yi], 1.0, sp, 1.0, nullptr, 0.0, ns);
+            if ((s = check_launch(p, "rb seed")) != SPADJ_OK) return s;
+          }
           break;
         default:
           break;
@@ -718,12 +736,24 @@ struct RB : EqImpl {
     }
     last_recompute = recompute;
     SPADJ_CUDA_TRY(p, cudaMemcpyAsync(grad, Yb[yi], sb, cudaMemcpyDeviceToDevice, p->stream));
-    if (J_host) {
+    if (J_host && objective_kind >= 0) {
       SPADJ_CUDA_TRY(p, cudaMemcpyAsync(J_host, Jdev.ptr, sizeof(double), cudaMemcpyDeviceToHost, p->stream));
       SPADJ_CUDA_TRY(p, cudaStreamSynchronize(p->stream));
       if (!std::isfinite(J_host[0])) return p->fail(SPADJ_ERR_NONFINITE, "rb: objective is not finite");
     }
     return SPADJ_OK;
+  }
+
+  spadj_status gradient(Problem* p, const double* x0, int n_steps, int objective_kind, const double* obj_data,
+                        int ckpt_slots, double* J_host, double* grad, double* grad_p) override {
+    (void)grad_p;
+    if (objective_kind < 0) return p->fail(SPADJ_ERR_INVALID, "gradient: unknown objective");
+    return reverse(p, x0, n_steps, ckpt_slots, objective_kind, obj_data, {}, nullptr, J_host, grad);
+  }
+
+  spadj_status vjp(Problem* p, const double* x0, int n_steps, int ckpt_slots, const std::vector<int>& seed_at,
+                   const double* seeds, double* grad) override {
+    return reverse(p, x0, n_steps, ckpt_slots, -1, nullptr, seed_at, seeds, nullptr, grad);
   }
 
   ~RB() override {

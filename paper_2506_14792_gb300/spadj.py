@@ -58,6 +58,7 @@ _SIGS = {
     "spadj_eval_F_jvp": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "spadj_eval_F_vjp": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "spadj_solve": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp]),
+    "spadj_vjp": (ctypes.c_int, [_vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp]),
     "spadj_checkpoint_schedule": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "spadj_forward": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp]),
     "spadj_tangent": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp]),
@@ -221,6 +222,15 @@ class Problem:
                                            _ptr(obj_data), ckpt_slots, jp,
                                            _ptr(_as_f64(grad_x0, n, "grad_x0")), _ptr(grad_p)))
         return J
+
+    def vjp(self, x0, n_steps, seed_steps, seeds, grad_x0, ckpt_slots=0):
+        """grad_x0 = sum_i (dX_{seed_steps[i]}/dX_0)^T seeds[i]; seeds is [n_seeds][state] on the device."""
+        n = self.state_len(0)
+        steps = (ctypes.c_int * len(seed_steps))(*[int(s) for s in seed_steps])
+        _chk(self.h, lib().spadj_vjp(self.h, _ptr(_as_f64(x0, n, "x0")), n_steps, ckpt_slots, len(seed_steps),
+                                      steps, _ptr(_as_f64(seeds, n * len(seed_steps), "seeds")),
+                                      _ptr(_as_f64(grad_x0, n, "grad_x0"))))
+        return grad_x0
 
     KERNEL_CLASSES = ("z_transform", "x_fft", "pointwise", "pencil_solve", "objective", "fused_trajectory")
 
