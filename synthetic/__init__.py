@@ -56,3 +56,34 @@ def rb_ic(Nx, Nz, seed=2, amp=1e-3):
     s = np.zeros((3, K, Nz), dtype=np.complex128)
     s[2] = amp * th
     return s
+
+
+def kolmogorov_ic(N, seed, urms=1.0):
+    """Vorticity coefficients [N/2][N] complex (layout of the Kolmogorov problem: kx half
+    spectrum, ky in FFT order, ky = -N/2 row zero, kx = 0 column Hermitian) with velocity
+    energy spectrum E(k) ~ k^-3 for 1 <= |k| <= N/3 (|w_k| ~ 1/|k|), random phases, scaled
+    to rms velocity `urms` (Parseval over the Hermitian-completed spectrum)."""
+    Kx = N // 2
+    rng = np.random.default_rng(seed)
+    kx = np.arange(Kx)[:, None]
+    ky = np.fft.fftfreq(N, 1.0 / N)[None, :]
+    k = np.sqrt(kx ** 2 + ky ** 2)
+    band = (k >= 1.0) & (k <= N / 3.0) & (ky != -N // 2)
+    phase = np.exp(2j * np.pi * rng.random((Kx, N)))
+    w = np.where(band, phase / np.where(k > 0, k, 1.0), 0.0)
+    # Hermitian kx = 0 column: w(0, -ky) = conj w(0, ky)
+    col = w[0].copy()
+    neg = np.concatenate([[0], np.arange(N - 1, 0, -1)])
+    half = (ky[0] > 0)
+    col[neg[half]] = np.conj(col[half])
+    col[0] = 0.0
+    w[0] = col
+    # rms velocity^2 = sum over the full spectrum of |w|^2 / |k|^2 (kx >= 1 counted twice)
+    weight = np.where(kx == 0, 1.0, 2.0)
+    e = np.sum(weight * np.abs(w) ** 2 / np.where(k > 0, k, 1.0) ** 2)
+    return w * (urms / np.sqrt(e))
+
+
+def kolmogorov_batch(sizes, seeds):
+    """List of per-member ICs for a mixed-resolution batch."""
+    return [kolmogorov_ic(n, s) for n, s in zip(sizes, seeds)]
