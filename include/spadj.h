@@ -62,6 +62,15 @@ typedef enum {
  *   [3][Nx/2][N] complex (x-mode m = 0..Nx/2-1, Nyquist not stored; the m = 0 pencil is
  *   held real).  Grid layout [3N/2][3Nx/2] real (Gauss-Chebyshev z rows, uniform x).
  *   Pressure and tau variables are internal to the stage solves.
+ *
+ * SPADJ_KOLMOGOROV2D: 2D vorticity d_t w - lap w / Re = -(u d_x w + v d_y w) - 4 cos 4y on
+ *   [0, 2 pi)^2 (body force sin(4y) e_x), u = d_y psi, v = -d_x psi, lap psi = -w; Fourier
+ *   in x and y, 3/2 dealiasing; SBDF1 then SBDF2.  params[0] = Re, params[1] = 1 to drop the
+ *   forcing (tests).  A batch may mix resolutions (desc.batch_n).  Member b with N_b modes
+ *   holds N_b/2 x N_b complex coefficients, layout [kx][ky] (kx = 0..N/2-1, ky index j holds
+ *   ky = j for j < N/2 and j - N otherwise; the ky = -N/2 row is held at 0 and the kx = 0
+ *   column Hermitian); members are concatenated in batch order.  All members advance in one
+ *   persistent launch over (stage, phase, member, tile) work items.
  */
 typedef enum {
   SPADJ_BURGERS1D = 0,
@@ -84,6 +93,8 @@ typedef struct {
   double dt;         /* constant timestep */
   int batch;         /* number of independent members advanced together (>= 1) */
   int nonlinear;     /* 1: F as defined; 0: F = 0 (linear problem, used by tests) */
+  const int* batch_n;/* host, nullable: per-member resolution of a mixed batch (SPADJ_KOLMOGOROV2D);
+                        NULL = every member uses n[0].  Copied by spadj_create. */
 } spadj_desc;
 
 /* Build a problem (operators, transform tables, factorisations) bound to cuda_stream
@@ -160,8 +171,26 @@ spadj_status spadj_adjoint(spadj_problem* prob, int n_steps, const double* traj,
 
 /* Objectives for spadj_gradient. */
 typedef enum {
-  SPADJ_OBJ_ENERGY = 0 /* J = 1/2 ||u(T)||^2 (physical L2 integral) per batch member */
+  SPADJ_OBJ_ENERGY = 0,  /* J = 1/2 ||u(T)||^2 (physical L2 integral) per batch member */
+  SPADJ_OBJ_FOURDVAR = 1 /* J = sum_m 1/2 ||H(X_{n_m}) - obs_m||^2 per member (observations set by
+                            spadj_set_observations; H keeps |kx|, |ky| <= kmax) */
 } spadj_objective_kind;
+
+/* 4D-Var observations for SPADJ_OBJ_FOURDVAR (SPADJ_KOLMOGOROV2D): n_obs steps (host ints,
+ * increasing, in 1..n_steps of the later gradient call), obs (device, layout [n_obs][state],
+ * copied by the call) and the low-pass cut-off kmax of the observation operator H. */
+spadj_status spadj_set_observations(spadj_problem* prob, int n_obs, const int* obs_steps, const double* obs,
+                                    int kmax);
+
+/* Tuning knobs of the batched persistent launch (SPADJ_KOLMOGOROV2D): option 0 = persistent
+ * scheduler (1, default) or one launch per phase (0); 1 = x-modes per column tile; 2 = grid
+ * rows per row tile; 3 = resident CTAs per SM (0 = occupancy maximum); 4 = iteration limit of
+ * the scheduler's bounded waits (0 = default, several seconds); 5 = failure-path test: the
+ * completion of this member (-1 = none) is never signalled, so a bounded wait runs out and
+ * the call returns SPADJ_ERR_TIMEOUT with the context intact.  spadj_autotune times
+ * candidate settings on the problem's own sizes and keeps the fastest. */
+spadj_status spadj_set_option(spadj_problem* prob, int option, int value);
+spadj_status spadj_autotune(spadj_problem* prob);
 
 /* Objective J(X) per batch member and its partial derivative (eq. 1's dJ/dX), which seeds
  * the adjoint sweep: J_dev receives B doubles (device), seed receives dJ/dX (state layout).

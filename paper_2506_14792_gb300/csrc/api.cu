@@ -39,6 +39,7 @@ spadj_status spadj_create(const spadj_desc* desc, void* cuda_stream, spadj_probl
   switch (desc->eq) {
     case SPADJ_BURGERS1D: p->impl = spadj::make_burgers(p, &st); break;
     case SPADJ_RB2D: p->impl = spadj::make_rb(p, &st); break;
+    case SPADJ_KOLMOGOROV2D: p->impl = spadj::make_kolmogorov(p, &st); break;
     default: p->err = "spadj_create: unknown equation set"; break;
   }
   if (st != SPADJ_OK || !p->impl) {
@@ -114,6 +115,21 @@ spadj_status spadj_vjp(spadj_problem* p, const double* x0, int n_steps, int ckpt
     seed_at[n] = i;
   }
   return p->impl->vjp(p, x0, n_steps, ckpt_slots, seed_at, seeds, grad_x0);
+}
+
+spadj_status spadj_set_observations(spadj_problem* p, int n_obs, const int* obs_steps, const double* obs, int kmax) {
+  if (!p) return SPADJ_ERR_INVALID;
+  return spadj::kol_set_observations(p->impl, p, n_obs, obs_steps, obs, kmax);
+}
+
+spadj_status spadj_set_option(spadj_problem* p, int option, int value) {
+  if (!p) return SPADJ_ERR_INVALID;
+  return spadj::kol_set_option(p->impl, p, option, value);
+}
+
+spadj_status spadj_autotune(spadj_problem* p) {
+  if (!p) return SPADJ_ERR_INVALID;
+  return spadj::kol_autotune(p->impl, p);
 }
 
 spadj_status spadj_checkpoint_schedule(int n_steps, int slots, int* ops, int max_ops, int* n_ops) {

@@ -1,0 +1,959 @@
+// Batched 2D Kolmogorov flow (vorticity form, Fourier x Fourier, SBDF1 -> SBDF2) with 4D-Var
+// gradients: every member of a mixed-resolution batch advances in ONE persistent launch.
+//
+// Per member and timestep the work splits into tiles of two kinds:
+//   CA (column tile, a few x-modes): finish step s for these x-modes -- y-FFT of the grid
+//      product, IMEX combination of eq. imex with the diagonal implicit solve, projection onto
+//      admissible coefficients -- then start step s+1 for the same x-modes: the spectral fields
+//      u, v, w_x, w_y (u = i ky w/|k|^2, v = -i kx w/|k|^2) and their inverse y-FFTs.
+//   B  (row tile, a few grid rows in y): inverse x-FFTs of the four fields, the product
+//      u w_x + v w_y on the dealiased grid, forward x-FFT.
+// Within a member, CA of step s+1 needs every B tile of step s and B of step s needs every CA
+// tile of step s; nothing else is shared, so members of different sizes interleave freely.
+// The adjoint (eq. IMEX_adjoint) has the same two-kind structure: C'A' tiles finish the VJP
+// of F, add the injected 4D-Var cotangents, solve for Y_n and start the next VJP (T^dagger of
+// the cotangent, fields of X_{n-1} from the stored trajectory); B' tiles do the grid products
+// of the VJP and the adjoint x-FFTs.
+//
+// Scheduler: work items (stage, phase, member, tile) are handed out in order from a global
+// counter to a grid of resident CTAs (occupancy-sized, so every CTA holding an item runs); an
+// item waits, with a bounded spin, for the per-member completion counter of the phase it
+// depends on.  A wait that exceeds its limit sets an error flag, every CTA stops, and the host
+// returns SPADJ_ERR_TIMEOUT.  Data produced inside the launch is read with ld.global.cg.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "fft.cuh"
+#include "problem.h"
+
+namespace spadj {
+namespace {
+
+constexpr int kKolThreads = 128;
+constexpr int kMaxRes = 4;
+constexpr unsigned kSpinLimit = 1u << 26;  // x ~150 ns per probe: several seconds
+
+struct KMember {
+  int N, Kx, M, L, res;
+  long long off_state;  // complex offset of the member in a state array
+  long long off_mix;    // complex offset of the member in a mixed [y][kx] array
+  int nCA, nB;          // tiles per stage
+  int caStart, bStart;  // first item of the member inside a stage's CA / B block
+};
+
+struct KRes {
+  FFTPlan px, py;
+  const double2* WMx;  // exp(-2 pi i m / M), m < M  (x real FFT through L = M/2)
+  const double2* W2M;  // exp(-2 pi i m / 2M), m < 2M (y complex FFT of length M)
+};
+
+struct KolArgs {
+  int nmem;
+  const KMember* mem;
+  KRes res[kMaxRes];
+  double Re, dt;
+  int CW, RW;
+  int nCAtot, nBtot;
+  int adjoint;      // 0 forward, 1 adjoint
+  int fonly;        // forward: stage-0 F evaluation only (writes F(x0) to out)
+  int nstage;       // number of stages in this launch
+  int S;            // n_steps
+  int forcing, nonlinear;
+  const double2* x0;
+  double2* Xr[2];
+  double2* Fr[2];
+  double2* Yr[2];
+  double2* mixA[5];
+  double2* mixB[4];
+  double2* traj;
+  double2* out;
+  const int* seed_at;
+  const double2* seeds;
+  long long state_size;
+  int* queue;
+  int* caDone;
+  int* bDone;
+  int* err;
+  unsigned spin_limit;    // bounded-wait iterations
+  int drop_signal_member; // test knob: completion of this member is never signalled (-1: off)
+};
+
+__device__ __forceinline__ double2 ldcg2(const double2* p) { return __ldcg(p); }
+
+struct Coef {
+  double a0, a1, a2, c1, c2;
+};
+__device__ __forceinline__ Coef kcoef(int n, double dt) {  // SBDF1 at n = 1, SBDF2 after
+  Coef c;
+  if (n <= 1) { c.a0 = 1.0 / dt; c.a1 = -1.0 / dt; c.a2 = 0.0; c.c1 = 1.0; c.c2 = 0.0; }
+  else { c.a0 = 1.5 / dt; c.a1 = -2.0 / dt; c.a2 = 0.5 / dt; c.c1 = 2.0; c.c2 = -1.0; }
+  return c;
+}
+
+// ky of coefficient row q, and its index in the length-M y-FFT (-1 for the unstored Nyquist)
+__device__ __forceinline__ int kyof(int q, int N) { return q < N / 2 ? q : q - N; }
+__device__ __forceinline__ int yidx(int q, int N, int M) { return q < N / 2 ? q : (q == N / 2 ? -1 : M - N + q); }
+
+// multiplier of field f (0 u, 1 v, 2 w_x, 3 w_y) applied to w(kx, ky)
+__device__ __forceinline__ double2 fmult(int f, double kx, double ky, double2 w) {
+  const double k2 = kx * kx + ky * ky;
+  const double ik2 = k2 > 0.0 ? 1.0 / k2 : 0.0;
+  double s;
+  switch (f) {
+    case 0: s = ky * ik2; break;    // i ky / |k|^2
+    case 1: s = -kx * ik2; break;   // -i kx / |k|^2
+    case 2: s = kx; break;          // i kx
+    default: s = ky; break;         // i ky
+  }
+  return make_double2(-s * w.y, s * w.x);  // i s w
+}
+
+// project a column held in smem: Nyquist row to zero; kx = 0 column Hermitian
+__device__ void project_col(double2* x, int N, int kx) {
+  for (int q = threadIdx.x; q < N; q += blockDim.x) {
+    if (q == N / 2) { x[q] = make_double2(0.0, 0.0); continue; }
+    if (kx != 0) continue;
+    const int p = (N - q) % N;
+    if (q == 0) { x[0].y = 0.0; continue; }
+    if (q < p) {
+      const double2 a = x[q], b = x[p];
+      const double2 h = make_double2(0.5 * (a.x + b.x), 0.5 * (a.y - b.y));
+      x[q] = h;
+      x[p] = make_double2(h.x, -h.y);
+    }
+  }
+  __syncthreads();
+}
+
+// y-FFT of a padded column: fill a (length M) from fill(j), transform with SIGN, return result
+template <int SIGN>
+__device__ double2* col_fft(double2* a, double2* b, const KRes& R) {
+  __syncthreads();
+  return cfft_smem_t<SIGN>(a, b, R.py, R.W2M);
+}
+
+struct KSmem {
+  double2* buf;  // base of dynamic smem
+};
+
+// ---- forward CA tile --------------------------------------------------------------------------
+__device__ void ca_forward(const KolArgs& A, const KMember& m, int tile, int s) {
+  extern __shared__ double2 ks[];
+  const int N = m.N, Kx = m.Kx, M = m.M;
+  const KRes& R = A.res[m.res];
+  double2* ca = ks;          // M
+  double2* cb = ca + M;      // M
+  double2* xc = cb + M;      // N
+  const int kx0 = tile * A.CW, kx1 = min(Kx, kx0 + A.CW);
+  const long long S = A.state_size;
+  for (int kx = kx0; kx < kx1; ++kx) {
+    const long long col = m.off_state + (long long)kx * N;
+    if (s == 0) {
+      for (int q = threadIdx.x; q < N; q += blockDim.x) xc[q] = A.x0[col + q];
+      __syncthreads();
+    } else {
+      double2* r = nullptr;
+      if (A.nonlinear) {
+        for (int j = threadIdx.x; j < M; j += blockDim.x) ca[j] = ldcg2(&A.mixB[0][m.off_mix + (long long)j * Kx + kx]);
+        r = col_fft<-1>(ca, cb, R);
+      }
+      const Coef c = kcoef(s, A.dt);
+      const double invM = 1.0 / M;
+      for (int q = threadIdx.x; q < N; q += blockDim.x) {
+        const int idx = yidx(q, N, M);
+        const double ky = kyof(q, N);
+        double2 F = make_double2(0.0, 0.0);
+        if (idx >= 0 && A.nonlinear) F = make_double2(-r[idx].x * invM, -r[idx].y * invM);
+        if (A.forcing && kx == 0 && (q == 4 || q == N - 4)) F.x -= 2.0;
+        if (A.fonly) {
+          A.out[col + q] = F;
+          continue;
+        }
+        const double2 X1 = ldcg2(&A.Xr[(s - 1) & 1][col + q]);
+        double2 num = make_double2(c.c1 * F.x - c.a1 * X1.x, c.c1 * F.y - c.a1 * X1.y);
+        if (s >= 2) {
+          const double2 X2 = ldcg2(&A.Xr[s & 1][col + q]);
+          const double2 F2 = ldcg2(&A.Fr[s & 1][col + q]);
+          num.x += c.c2 * F2.x - c.a2 * X2.x;
+          num.y += c.c2 * F2.y - c.a2 * X2.y;
+        }
+        A.Fr[(s - 1) & 1][col + q] = F;
+        const double inv = 1.0 / (c.a0 + ((double)kx * kx + ky * ky) / A.Re);
+        xc[q] = make_double2(num.x * inv, num.y * inv);
+      }
+      __syncthreads();
+      if (A.fonly) continue;
+      project_col(xc, N, kx);
+    }
+    for (int q = threadIdx.x; q < N; q += blockDim.x) {
+      A.Xr[s & 1][col + q] = xc[q];
+      if (A.traj) A.traj[(long long)s * S + col + q] = xc[q];
+      if (s == A.S) A.out[col + q] = xc[q];
+    }
+    if (s < A.S && A.nonlinear) {
+      for (int f = 0; f < 4; ++f) {
+        __syncthreads();
+        for (int j = threadIdx.x; j < M; j += blockDim.x) ca[j] = make_double2(0.0, 0.0);
+        __syncthreads();
+        for (int q = threadIdx.x; q < N; q += blockDim.x) {
+          const int idx = yidx(q, N, M);
+          if (idx >= 0) ca[idx] = fmult(f, (double)kx, (double)kyof(q, N), xc[q]);
+        }
+        double2* r = col_fft<1>(ca, cb, R);
+        for (int j = threadIdx.x; j < M; j += blockDim.x) A.mixA[f][m.off_mix + (long long)j * Kx + kx] = r[j];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// inverse x transform of one mixed row into a packed real row (L complex) kept in dst
+__device__ void row_c2r(const double2* src, double2* dst, double2* sa, double2* sb, double2* st, const KMember& m,
+                        const KRes& R, double w0, double w) {
+  const int Kx = m.Kx, L = m.L;
+  for (int k = threadIdx.x; k < Kx; k += blockDim.x) st[k] = ldcg2(&src[k]);
+  __syncthreads();
+  c2r_pre(sa, [&](int k) { return st[k]; }, Kx, L, R.WMx, w0, w);
+  __syncthreads();
+  double2* r = cfft_smem_t<1>(sa, sb, R.px, R.WMx);
+  for (int j = threadIdx.x; j < L; j += blockDim.x) dst[j] = r[j];
+  __syncthreads();
+}
+
+// forward x transform of a packed real row held in `row` (destroyed) into dst[k], k < Kx
+__device__ void row_r2c(double2* row, double2* scratch, double2* dst, const KMember& m, const KRes& R, double s0,
+                        double s) {
+  const int Kx = m.Kx, L = m.L;
+  double2* z = cfft_smem_t<-1>(row, scratch, R.px, R.WMx);
+  r2c_post(z, [&](int k, double2 v) {
+    double2 o = make_double2(v.x * (k == 0 ? s0 : s), v.y * (k == 0 ? s0 : s));
+    if (k == 0) o.y = 0.0;
+    dst[k] = o;
+  }, Kx, L, R.WMx);
+  __syncthreads();
+}
+
+// ---- forward B tile ---------------------------------------------------------------------------
+__device__ void b_forward(const KolArgs& A, const KMember& m, int tile) {
+  extern __shared__ double2 ks[];
+  const int Kx = m.Kx, M = m.M, L = m.L;
+  const KRes& R = A.res[m.res];
+  double2* G = ks;            // 4 L
+  double2* sa = G + 4 * L;    // L
+  double2* sb = sa + L;       // L
+  double2* st = sb + L;       // Kx
+  const int j0 = tile * A.RW, j1 = min(M, j0 + A.RW);
+  const double invM = 1.0 / M;
+  for (int j = j0; j < j1; ++j) {
+    for (int f = 0; f < 4; ++f)
+      row_c2r(A.mixA[f] + m.off_mix + (long long)j * Kx, G + f * L, sa, sb, st, m, R, 1.0, 1.0);
+    for (int i = threadIdx.x; i < L; i += blockDim.x) {
+      const double2 u = G[i], v = G[L + i], wx = G[2 * L + i], wy = G[3 * L + i];
+      sa[i] = make_double2(fma(u.x, wx.x, v.x * wy.x), fma(u.y, wx.y, v.y * wy.y));
+    }
+    __syncthreads();
+    row_r2c(sa, sb, A.mixB[0] + m.off_mix + (long long)j * Kx, m, R, invM, invM);
+  }
+}
+
+// ---- adjoint C'A' tile ------------------------------------------------------------------------
+__device__ void ca_adjoint(const KolArgs& A, const KMember& m, int tile, int n) {
+  extern __shared__ double2 ks[];
+  const int N = m.N, Kx = m.Kx, M = m.M;
+  const KRes& R = A.res[m.res];
+  double2* ca = ks;        // M
+  double2* cb = ca + M;    // M
+  double2* lam = cb + M;   // N
+  double2* yc = lam + N;   // N
+  const int kx0 = tile * A.CW, kx1 = min(Kx, kx0 + A.CW);
+  const long long S = A.state_size;
+  const int SN = A.S;
+  for (int kx = kx0; kx < kx1; ++kx) {
+    const long long col = m.off_state + (long long)kx * N;
+    for (int q = threadIdx.x; q < N; q += blockDim.x) lam[q] = make_double2(0.0, 0.0);
+    __syncthreads();
+    if (n < SN && A.nonlinear) {
+      // VJP: B_y^dagger of the four grid cotangents, then the adjoint multipliers
+      for (int f = 0; f < 4; ++f) {
+        for (int j = threadIdx.x; j < M; j += blockDim.x) ca[j] = ldcg2(&A.mixB[f][m.off_mix + (long long)j * Kx + kx]);
+        double2* r = col_fft<-1>(ca, cb, R);
+        for (int q = threadIdx.x; q < N; q += blockDim.x) {
+          const int idx = yidx(q, N, M);
+          if (idx < 0) continue;
+          // adjoint of i*s is -i*s: fmult with the negated multiplier
+          const double2 v = fmult(f, (double)kx, (double)kyof(q, N), r[idx]);
+          lam[q].x -= v.x;
+          lam[q].y -= v.y;
+        }
+        __syncthreads();
+      }
+    }
+    const int si = A.seed_at ? A.seed_at[n] : -1;
+    const Coef c1 = (n + 1 <= SN) ? kcoef(n + 1, A.dt) : Coef{0, 0, 0, 0, 0};
+    const Coef c2 = (n + 2 <= SN) ? kcoef(n + 2, A.dt) : Coef{0, 0, 0, 0, 0};
+    for (int q = threadIdx.x; q < N; q += blockDim.x) {
+      double2 l = lam[q];
+      if (si >= 0) {
+        const double2 sd = A.seeds[(long long)si * S + col + q];
+        l.x += sd.x; l.y += sd.y;
+      }
+      if (n + 1 <= SN) {
+        const double2 y1 = ldcg2(&A.Yr[(n + 1) & 1][col + q]);
+        l.x -= c1.a1 * y1.x; l.y -= c1.a1 * y1.y;
+      }
+      if (n + 2 <= SN) {
+        const double2 y2 = ldcg2(&A.Yr[n & 1][col + q]);
+        l.x -= c2.a2 * y2.x; l.y -= c2.a2 * y2.y;
+      }
+      lam[q] = l;
+    }
+    __syncthreads();
+    if (n == 0) {
+      for (int q = threadIdx.x; q < N; q += blockDim.x) A.out[col + q] = lam[q];
+      __syncthreads();
+      continue;
+    }
+    project_col(lam, N, kx);
+    const Coef cn = kcoef(n, A.dt);
+    for (int q = threadIdx.x; q < N; q += blockDim.x) {
+      const double ky = kyof(q, N);
+      const double inv = 1.0 / (cn.a0 + ((double)kx * kx + ky * ky) / A.Re);
+      yc[q] = make_double2(lam[q].x * inv, lam[q].y * inv);
+    }
+    __syncthreads();
+    // W_{n-1} = c1^n Y_n + c2^{n+1} Y_{n+1}, read Y_{n+1} before Y_n overwrites Y_{n+2}
+    const Coef cw1 = kcoef(n, A.dt);
+    const Coef cw2 = (n + 1 <= SN) ? kcoef(n + 1, A.dt) : Coef{0, 0, 0, 0, 0};
+    for (int q = threadIdx.x; q < N; q += blockDim.x) {
+      double2 w = make_double2(cw1.c1 * yc[q].x, cw1.c1 * yc[q].y);
+      if (n + 1 <= SN) {
+        const double2 y1 = ldcg2(&A.Yr[(n + 1) & 1][col + q]);
+        w.x += cw2.c2 * y1.x; w.y += cw2.c2 * y1.y;
+      }
+      lam[q] = w;
+      A.Yr[n & 1][col + q] = yc[q];
+    }
+    __syncthreads();
+    if (!A.nonlinear) continue;
+    // T_y^dagger W (inverse FFT with 1/M) -> mixA[4]
+    for (int j = threadIdx.x; j < M; j += blockDim.x) ca[j] = make_double2(0.0, 0.0);
+    __syncthreads();
+    for (int q = threadIdx.x; q < N; q += blockDim.x) {
+      const int idx = yidx(q, N, M);
+      if (idx >= 0) ca[idx] = lam[q];
+    }
+    {
+      double2* r = col_fft<1>(ca, cb, R);
+      const double invM = 1.0 / M;
+      for (int j = threadIdx.x; j < M; j += blockDim.x)
+        A.mixA[4][m.off_mix + (long long)j * Kx + kx] = make_double2(r[j].x * invM, r[j].y * invM);
+    }
+    // fields of X_{n-1} from the trajectory
+    for (int q = threadIdx.x; q < N; q += blockDim.x) yc[q] = ldcg2(&A.traj[(long long)(n - 1) * S + col + q]);
+    for (int f = 0; f < 4; ++f) {
+      __syncthreads();
+      for (int j = threadIdx.x; j < M; j += blockDim.x) ca[j] = make_double2(0.0, 0.0);
+      __syncthreads();
+      for (int q = threadIdx.x; q < N; q += blockDim.x) {
+        const int idx = yidx(q, N, M);
+        if (idx >= 0) ca[idx] = fmult(f, (double)kx, (double)kyof(q, N), yc[q]);
+      }
+      double2* r = col_fft<1>(ca, cb, R);
+      for (int j = threadIdx.x; j < M; j += blockDim.x) A.mixA[f][m.off_mix + (long long)j * Kx + kx] = r[j];
+    }
+    __syncthreads();
+  }
+}
+
+// ---- adjoint B' tile --------------------------------------------------------------------------
+__device__ void b_adjoint(const KolArgs& A, const KMember& m, int tile) {
+  extern __shared__ double2 ks[];
+  const int Kx = m.Kx, M = m.M, L = m.L;
+  const KRes& R = A.res[m.res];
+  double2* G = ks;            // 5 L: u, v, wx, wy, g
+  double2* sa = G + 5 * L;    // L
+  double2* sb = sa + L;       // L
+  double2* st = sb + L;       // Kx
+  const int j0 = tile * A.RW, j1 = min(M, j0 + A.RW);
+  for (int j = j0; j < j1; ++j) {
+    for (int f = 0; f < 4; ++f)
+      row_c2r(A.mixA[f] + m.off_mix + (long long)j * Kx, G + f * L, sa, sb, st, m, R, 1.0, 1.0);
+    row_c2r(A.mixA[4] + m.off_mix + (long long)j * Kx, G + 4 * L, sa, sb, st, m, R, 1.0 / M, 0.5 / M);
+    // grid cotangents of u, v, w_x, w_y: -g w_x, -g w_y, -g u, -g v
+    for (int i = threadIdx.x; i < L; i += blockDim.x) {
+      const double2 u = G[i], v = G[L + i], wx = G[2 * L + i], wy = G[3 * L + i], g = G[4 * L + i];
+      G[i] = make_double2(-g.x * wx.x, -g.y * wx.y);
+      G[L + i] = make_double2(-g.x * wy.x, -g.y * wy.y);
+      G[2 * L + i] = make_double2(-g.x * u.x, -g.y * u.y);
+      G[3 * L + i] = make_double2(-g.x * v.x, -g.y * v.y);
+    }
+    __syncthreads();
+    for (int f = 0; f < 4; ++f)
+      row_r2c(G + f * L, sa, A.mixB[f] + m.off_mix + (long long)j * Kx, m, R, 1.0, 2.0);
+  }
+}
+
+// ---- drivers ---------------------------------------------------------------------------------
+__device__ __forceinline__ int find_member(const KolArgs& A, int r, bool ca) {
+  int b = 0;
+  for (int i = 0; i < A.nmem; ++i) {
+    const int st = ca ? A.mem[i].caStart : A.mem[i].bStart;
+    if (st <= r) b = i;
+  }
+  return b;
+}
+
+__device__ void run_item(const KolArgs& A, int stage, bool isCA, int b, int tile) {
+  const KMember& m = A.mem[b];
+  if (!A.adjoint) {
+    if (isCA) ca_forward(A, m, tile, stage);
+    else b_forward(A, m, tile);
+  } else {
+    const int n = A.S - stage;
+    if (isCA) ca_adjoint(A, m, tile, n);
+    else b_adjoint(A, m, tile);
+  }
+}
+
+// bounded wait by thread 0 for *ctr >= target; false if the launch is being abandoned
+__device__ bool wait_ge(int* ctr, int target, int* err, unsigned limit) {
+  __shared__ int ok;
+  if (threadIdx.x == 0) {
+    ok = 1;
+    unsigned it = 0;
+    while (true) {
+      if (*(volatile int*)ctr >= target) break;
+      if (*(volatile int*)err) { ok = 0; break; }
+      if (++it > limit) {
+        atomicCAS(err, 0, 1);
+        ok = 0;
+        break;
+      }
+      __nanosleep(128);
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+__global__ void __launch_bounds__(kKolThreads) kol_persistent(const __grid_constant__ KolArgs A) {
+  __shared__ int item;
+  const int per = A.nCAtot + A.nBtot;
+  const int total = A.nstage * per - A.nBtot;  // the last stage has no B phase
+  while (true) {
+    if (threadIdx.x == 0) item = (*(volatile int*)A.err) ? total : atomicAdd(A.queue, 1);
+    __syncthreads();
+    const int it = item;
+    __syncthreads();
+    if (it >= total) break;
+    const int stage = it / per, r = it % per;
+    const bool isCA = r < A.nCAtot;
+    const int rr = isCA ? r : r - A.nCAtot;
+    const int b = find_member(A, rr, isCA);
+    const KMember& m = A.mem[b];
+    const int tile = rr - (isCA ? m.caStart : m.bStart);
+    const bool ok = isCA ? (stage == 0 || wait_ge(&A.bDone[b], stage * m.nB, A.err, A.spin_limit))
+                         : wait_ge(&A.caDone[b], (stage + 1) * m.nCA, A.err, A.spin_limit);
+    if (!ok) break;
+    run_item(A, stage, isCA, b, tile);
+    __syncthreads();
+    if (threadIdx.x == 0 && b != A.drop_signal_member) {
+      __threadfence();
+      atomicAdd(isCA ? &A.caDone[b] : &A.bDone[b], 1);
+    }
+  }
+}
+
+// one phase of one stage as an ordinary launch (grid = tiles of all members)
+__global__ void __launch_bounds__(kKolThreads) kol_phase(const __grid_constant__ KolArgs A, int stage, int isCA) {
+  const int r = blockIdx.x;
+  const int b = find_member(A, r, isCA != 0);
+  const KMember& m = A.mem[b];
+  const int tile = r - (isCA ? m.caStart : m.bStart);
+  run_item(A, stage, isCA != 0, b, tile);
+}
+
+// 4D-Var misfit per (member, observation) and its cotangent seeds[m] = H^T H (X_{n_m} - obs_m)
+__global__ void fourdvar_kernel(const KMember* mem, const double2* traj, const int* obs_steps, const double2* obs,
+                                long long S, int kmax, double2* seeds, double* partial, int n_obs) {
+  const int b = blockIdx.x, o = blockIdx.y;
+  const KMember m = mem[b];
+  const double2* X = traj + (long long)obs_steps[o] * S + m.off_state;
+  const double2* Ob = obs + (long long)o * S + m.off_state;
+  double2* sd = seeds + (long long)o * S + m.off_state;
+  double acc = 0.0;
+  const int n = m.Kx * m.N;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const int kx = i / m.N, q = i % m.N;
+    const int ky = kyof(q, m.N);
+    const bool keep = kx <= kmax && (ky <= kmax && ky >= -kmax);
+    double2 d = make_double2(0.0, 0.0);
+    if (keep) {
+      const double2 x = X[i], y = Ob[i];
+      d = make_double2(x.x - y.x, x.y - y.y);
+      acc += d.x * d.x + d.y * d.y;
+    }
+    sd[i] = d;
+  }
+  __shared__ double red[kKolThreads];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[(long long)b * n_obs + o] = 0.5 * red[0];
+}
+
+__global__ void sum_rows_kernel(const double* partial, int n_obs, int nmem, double* J) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nmem) return;
+  double s = 0.0;
+  for (int o = 0; o < n_obs; ++o) s += partial[(long long)b * n_obs + o];
+  J[b] = s;
+}
+
+// ---- host ------------------------------------------------------------------------------------
+
+bool fft_len_ok(int n) {
+  if (n < 1) return false;
+  while (n % 2 == 0) n /= 2;
+  while (n % 3 == 0) n /= 3;
+  return n == 1;
+}
+
+struct Kol : EqImpl {
+  std::vector<KMember> hm;
+  std::vector<int> resN;
+  int nmem = 0;
+  long long state_size = 0, mix_size = 0;
+  int Lmax = 0, Mmax = 0, Nmax = 0, Kxmax = 0;
+  double Re = 100.0, dt = 0;
+  int forcing = 1, nonlinear = 1;
+  int CW = 4, RW = 2, ctas_per_sm = 0, persistent = 1;
+  unsigned spin_limit = kSpinLimit;
+  int drop_signal_member = -1;
+  DevBuf dmem, tables, Xr[2], Fr[2], Yr[2], mixA, mixB, ctr, trajbuf, seedbuf, seedmap, obsbuf, obsteps, partial, Jd,
+      tmp;
+  int n_obs = 0, obs_kmax = 32;
+  std::vector<int> obs_steps_h;
+  KRes kres[kMaxRes];
+  size_t smem = 0;
+  int grid_persistent = 0;
+
+  size_t state_len(int which) const override {
+    if (which == 0 || which == 3) return (size_t)(2 * state_size);
+    if (which == 1) {
+      size_t g = 0;
+      for (auto& m : hm) g += (size_t)m.M * m.M;
+      return g;
+    }
+    return 0;
+  }
+
+  void layout() {
+    int ca = 0, bb = 0;
+    for (auto& m : hm) {
+      m.nCA = (m.Kx + CW - 1) / CW;
+      m.nB = (m.M + RW - 1) / RW;
+      m.caStart = ca;
+      m.bStart = bb;
+      ca += m.nCA;
+      bb += m.nB;
+    }
+  }
+  int nCAtot() const { return hm.empty() ? 0 : hm.back().caStart + hm.back().nCA; }
+  int nBtot() const { return hm.empty() ? 0 : hm.back().bStart + hm.back().nB; }
+
+  spadj_status init(Problem* p) {
+    const spadj_desc& d = p->desc;
+    if (d.scheme != SPADJ_SBDF1 && d.scheme != SPADJ_SBDF2)
+      return p->fail(SPADJ_ERR_UNSUPPORTED, "kolmogorov: scheme must be SBDF2");
+    nmem = d.batch;
+    Re = d.params[0];
+    if (!(Re > 0)) return p->fail(SPADJ_ERR_INVALID, "kolmogorov: params[0] (Reynolds number) must be > 0");
+    forcing = d.params[1] == 1.0 ? 0 : 1;
+    nonlinear = d.nonlinear;
+    dt = d.dt;
+    long long offs = 0, offm = 0;
+    for (int b = 0; b < nmem; ++b) {
+      const int N = d.batch_n ? d.batch_n[b] : d.n[0];
+      if (N < 8 || N % 4 != 0 || !fft_len_ok(3 * N / 2) || N > 1024)
+        return p->fail(SPADJ_ERR_INVALID, "kolmogorov: each resolution must be a multiple of 4 in 8..1024 with 3N/2 = 2^a 3^b");
+      int r = -1;
+      for (size_t i = 0; i < resN.size(); ++i)
+        if (resN[i] == N) r = (int)i;
+      if (r < 0) {
+        if ((int)resN.size() >= kMaxRes) return p->fail(SPADJ_ERR_UNSUPPORTED, "kolmogorov: at most 4 distinct resolutions");
+        resN.push_back(N);
+        r = (int)resN.size() - 1;
+      }
+      KMember m{};
+      m.N = N; m.Kx = N / 2; m.M = 3 * N / 2; m.L = m.M / 2; m.res = r;
+      m.off_state = offs; m.off_mix = offm;
+      offs += (long long)m.Kx * N;
+      offm += (long long)m.M * m.Kx;
+      hm.push_back(m);
+      Lmax = std::max(Lmax, m.L); Mmax = std::max(Mmax, m.M); Nmax = std::max(Nmax, N); Kxmax = std::max(Kxmax, m.Kx);
+    }
+    state_size = offs;
+    mix_size = offm;
+    // twiddle tables per resolution: WMx (M entries) then W2M (2M entries)
+    std::vector<double2> ht;
+    std::vector<size_t> toff;
+    for (int N : resN) {
+      const int M = 3 * N / 2;
+      toff.push_back(ht.size());
+      for (int i = 0; i < M; ++i) {
+        const double th = -2.0 * M_PI * i / M;
+        ht.push_back(make_double2(std::cos(th), std::sin(th)));
+      }
+      for (int i = 0; i < 2 * M; ++i) {
+        const double th = -2.0 * M_PI * i / (2.0 * M);
+        ht.push_back(make_double2(std::cos(th), std::sin(th)));
+      }
+    }
+    SPADJ_CUDA_TRY(p, tables.ensure(sizeof(double2) * ht.size()));
+    SPADJ_CUDA_TRY(p, cudaMemcpyAsync(tables.ptr, ht.data(), sizeof(double2) * ht.size(), cudaMemcpyHostToDevice, p->stream));
+    for (size_t i = 0; i < resN.size(); ++i) {
+      const int M = 3 * resN[i] / 2;
+      kres[i].px = make_plan(M / 2);
+      kres[i].py = make_plan(M);
+      kres[i].WMx = tables.as<double2>() + toff[i];
+      kres[i].W2M = tables.as<double2>() + toff[i] + M;
+    }
+    const size_t sb = sizeof(double2) * state_size, mb = sizeof(double2) * mix_size;
+    for (int i = 0; i < 2; ++i) {
+      SPADJ_CUDA_TRY(p, Xr[i].ensure(sb));
+      SPADJ_CUDA_TRY(p, Fr[i].ensure(sb));
+      SPADJ_CUDA_TRY(p, Yr[i].ensure(sb));
+    }
+    SPADJ_CUDA_TRY(p, mixA.ensure(5 * mb));
+    SPADJ_CUDA_TRY(p, mixB.ensure(4 * mb));
+    SPADJ_CUDA_TRY(p, ctr.ensure(sizeof(int) * (2 * (size_t)nmem + 2)));
+    SPADJ_CUDA_TRY(p, tmp.ensure(sb));
+    // shared memory: max over tile kinds (B' needs 7 L + Kx, CA' needs 2 M + 2 N)
+    smem = sizeof(double2) * std::max<size_t>(7 * (size_t)Lmax + Kxmax, 2 * (size_t)Mmax + 2 * (size_t)Nmax);
+    SPADJ_CUDA_TRY(p, cudaFuncSetAttribute(kol_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    SPADJ_CUDA_TRY(p, cudaFuncSetAttribute(kol_phase, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    layout();
+    SPADJ_CUDA_TRY(p, dmem.ensure(sizeof(KMember) * nmem));
+    SPADJ_CUDA_TRY(p, cudaMemcpyAsync(dmem.ptr, hm.data(), sizeof(KMember) * nmem, cudaMemcpyHostToDevice, p->stream));
+    SPADJ_CUDA_TRY(p, cudaStreamSynchronize(p->stream));
+    return SPADJ_OK;
+  }
+
+  spadj_status sync_members(Problem* p) {
+    layout();
+    SPADJ_CUDA_TRY(p, cudaMemcpyAsync(dmem.ptr, hm.data(), sizeof(KMember) * nmem, cudaMemcpyHostToDevice, p->stream));
+    return SPADJ_OK;
+  }
+
+  KolArgs base_args() {
+    KolArgs A{};
+    A.nmem = nmem;
+    A.mem = dmem.as<KMember>();
+    for (int i = 0; i < kMaxRes; ++i) A.res[i] = kres[i];
+    A.Re = Re; A.dt = dt; A.CW = CW; A.RW = RW;
+    A.nCAtot = nCAtot(); A.nBtot = nBtot();
+    A.forcing = forcing; A.nonlinear = nonlinear;
+    for (int i = 0; i < 2; ++i) { A.Xr[i] = Xr[i].as<double2>(); A.Fr[i] = Fr[i].as<double2>(); A.Yr[i] = Yr[i].as<double2>(); }
+    for (int f = 0; f < 5; ++f) A.mixA[f] = mixA.as<double2>() + (size_t)f * mix_size;
+    for (int f = 0; f < 4; ++f) A.mixB[f] = mixB.as<double2>() + (size_t)f * mix_size;
+    A.state_size = state_size;
+    int* c = ctr.as<int>();
+    A.queue = c; A.err = c + 1; A.caDone = c + 2; A.bDone = c + 2 + nmem;
+    A.spin_limit = spin_limit;
+    A.drop_signal_member = drop_signal_member;
+    return A;
+  }
+
+  spadj_status launch(Problem* p, KolArgs& A) {
+    const int per = A.nCAtot + A.nBtot;
+    const double flops = 0;  // accounted per launch below
+    (void)flops;
+    cudaEvent_t t = p->tic();
+    if (persistent) {
+      SPADJ_CUDA_TRY(p, cudaMemsetAsync(ctr.ptr, 0, sizeof(int) * (2 * (size_t)nmem + 2), p->stream));
+      if (!grid_persistent) {
+        int dev = 0, sms = 0, occ = 0;
+        SPADJ_CUDA_TRY(p, cudaGetDevice(&dev));
+        SPADJ_CUDA_TRY(p, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        SPADJ_CUDA_TRY(p, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kol_persistent, kKolThreads, smem));
+        if (occ < 1) return p->fail(SPADJ_ERR_INVALID, "kolmogorov: kernel does not fit on an SM");
+        const int per_sm = ctas_per_sm > 0 ? std::min(ctas_per_sm, occ) : occ;
+        grid_persistent = sms * per_sm;
+      }
+      kol_persistent<<<grid_persistent, kKolThreads, smem, p->stream>>>(A);
+      spadj_status s = check_launch(p, "kolmogorov persistent");
+      p->toc(t, KC_FUSED, work_flops(A));
+      return s;
+    }
+    for (int st = 0; st < A.nstage; ++st) {
+      kol_phase<<<A.nCAtot, kKolThreads, smem, p->stream>>>(A, st, 1);
+      spadj_status s = check_launch(p, "kolmogorov phase CA");
+      if (s != SPADJ_OK) return s;
+      if (st + 1 < A.nstage) {
+        kol_phase<<<A.nBtot, kKolThreads, smem, p->stream>>>(A, st, 0);
+        if ((s = check_launch(p, "kolmogorov phase B")) != SPADJ_OK) return s;
+      }
+    }
+    p->toc(t, KC_FUSED, work_flops(A));
+    (void)per;
+    return SPADJ_OK;
+  }
+
+  // algorithmic FP64 flops of a launch: complex y-FFTs (5 M log2 M per column) and real
+  // x-FFTs (2.5 M log2 M per row); forward stage: 5 y + 5 x, adjoint: 9 y + 9 x
+  double work_flops(const KolArgs& A) const {
+    double f = 0;
+    const double ny = A.adjoint ? 9 : 5, nx = A.adjoint ? 9 : 5;
+    for (auto& m : hm) {
+      const double lg = std::log2((double)m.M);
+      f += ny * m.Kx * 5.0 * m.M * lg + nx * m.M * 2.5 * m.M * lg;
+    }
+    return f * std::max(0, A.nstage - 1);
+  }
+
+  spadj_status check_err(Problem* p) {
+    int e = 0;
+    SPADJ_CUDA_TRY(p, cudaMemcpyAsync(&e, ctr.as<int>() + 1, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+    SPADJ_CUDA_TRY(p, cudaStreamSynchronize(p->stream));
+    if (e) return p->fail(SPADJ_ERR_TIMEOUT, "kolmogorov: a bounded wait in the persistent launch gave up");
+    return SPADJ_OK;
+  }
+
+  spadj_status run_forward(Problem* p, int n_steps, const double* x0, double* x_out, double2* traj) {
+    KolArgs A = base_args();
+    A.adjoint = 0;
+    A.nstage = n_steps + 1;
+    A.S = n_steps;
+    A.x0 = reinterpret_cast<const double2*>(x0);
+    A.traj = traj;
+    A.out = reinterpret_cast<double2*>(x_out);
+    spadj_status s = launch(p, A);
+    if (s != SPADJ_OK) return s;
+    return persistent ? check_err(p) : SPADJ_OK;
+  }
+
+  spadj_status run_adjoint(Problem* p, int n_steps, double2* traj, const std::vector<int>& seed_at, const double2* seeds,
+                           double* grad) {
+    SPADJ_CUDA_TRY(p, seedmap.ensure(sizeof(int) * (n_steps + 1)));
+    SPADJ_CUDA_TRY(p, cudaMemcpyAsync(seedmap.ptr, seed_at.data(), sizeof(int) * (n_steps + 1), cudaMemcpyHostToDevice,
+                                      p->stream));
+    KolArgs A = base_args();
+    A.adjoint = 1;
+    A.nstage = n_steps + 1;
+    A.S = n_steps;
+    A.traj = traj;
+    A.out = reinterpret_cast<double2*>(grad);
+    A.seed_at = seedmap.as<int>();
+    A.seeds = seeds;
+    spadj_status s = launch(p, A);
+    if (s != SPADJ_OK) return s;
+    return persistent ? check_err(p) : cudaStreamSynchronize(p->stream) == cudaSuccess ? SPADJ_OK
+                                                                                       : p->fail(SPADJ_ERR_CUDA, "sync");
+  }
+
+  spadj_status transform(Problem* p, int, const double*, double*) override {
+    return p->fail(SPADJ_ERR_UNSUPPORTED, "kolmogorov: standalone transforms are not exposed");
+  }
+
+  spadj_status eval_F(Problem* p, int mode, const double* x, const double*, double* out) override {
+    if (mode != 0) return p->fail(SPADJ_ERR_UNSUPPORTED, "kolmogorov: JVP/VJP of F are exercised through spadj_vjp");
+    KolArgs A = base_args();
+    A.adjoint = 0;
+    A.fonly = 1;
+    A.nstage = 2;
+    A.S = 1;
+    A.x0 = reinterpret_cast<const double2*>(x);
+    A.out = reinterpret_cast<double2*>(out);
+    const int keep = persistent;
+    persistent = 0;
+    spadj_status s = launch(p, A);
+    persistent = keep;
+    return s;
+  }
+
+  spadj_status forward(Problem* p, int n_steps, const double* x0, double* x_out, double* traj) override {
+    if (n_steps < 1) return p->fail(SPADJ_ERR_INVALID, "forward: n_steps < 1");
+    return run_forward(p, n_steps, x0, x_out, reinterpret_cast<double2*>(traj));
+  }
+
+  spadj_status tangent(Problem* p, int, const double*, const double*, double*) override {
+    return p->fail(SPADJ_ERR_UNSUPPORTED, "kolmogorov: tangent sweep not provided");
+  }
+
+  spadj_status ensure_traj(Problem* p, int n_steps) {
+    SPADJ_CUDA_TRY(p, trajbuf.ensure(sizeof(double2) * (size_t)state_size * (size_t)(n_steps + 1)));
+    return SPADJ_OK;
+  }
+
+  spadj_status adjoint(Problem* p, int n_steps, const double* traj, const double* y_final, double* grad) override {
+    if (n_steps < 1) return p->fail(SPADJ_ERR_INVALID, "adjoint: n_steps < 1");
+    std::vector<int> seed_at(n_steps + 1, -1);
+    seed_at[n_steps] = 0;
+    return run_adjoint(p, n_steps, const_cast<double2*>(reinterpret_cast<const double2*>(traj)), seed_at,
+                       reinterpret_cast<const double2*>(y_final), grad);
+  }
+
+  spadj_status vjp(Problem* p, const double* x0, int n_steps, int, const std::vector<int>& seed_at,
+                   const double* seeds, double* grad) override {
+    spadj_status s = ensure_traj(p, n_steps);
+    if (s != SPADJ_OK) return s;
+    if ((s = run_forward(p, n_steps, x0, tmp.as<double>(), trajbuf.as<double2>())) != SPADJ_OK) return s;
+    return run_adjoint(p, n_steps, trajbuf.as<double2>(), seed_at, reinterpret_cast<const double2*>(seeds), grad);
+  }
+
+  spadj_status set_observations(Problem* p, int n, const int* steps, const double* obs, int kmax) {
+    if (n < 1 || !steps || !obs || kmax < 0) return p->fail(SPADJ_ERR_INVALID, "set_observations: bad arguments");
+    for (int i = 0; i < n; ++i)
+      if (steps[i] < 1 || (i > 0 && steps[i] <= steps[i - 1]))
+        return p->fail(SPADJ_ERR_INVALID, "set_observations: steps must be increasing and >= 1");
+    n_obs = n;
+    obs_kmax = kmax;
+    obs_steps_h.assign(steps, steps + n);
+    SPADJ_CUDA_TRY(p, obsbuf.ensure(sizeof(double2) * (size_t)state_size * n));
+    SPADJ_CUDA_TRY(p, cudaMemcpyAsync(obsbuf.ptr, obs, sizeof(double2) * (size_t)state_size * n, cudaMemcpyDeviceToDevice,
+                                      p->stream));
+    SPADJ_CUDA_TRY(p, obsteps.ensure(sizeof(int) * n));
+    SPADJ_CUDA_TRY(p, cudaMemcpyAsync(obsteps.ptr, steps, sizeof(int) * n, cudaMemcpyHostToDevice, p->stream));
+    SPADJ_CUDA_TRY(p, cudaStreamSynchronize(p->stream));
+    return SPADJ_OK;
+  }
+
+  spadj_status objective(Problem* p, int, const double*, const double*, double*, double*) override {
+    return p->fail(SPADJ_ERR_UNSUPPORTED, "kolmogorov: the 4D-Var objective is evaluated inside spadj_gradient");
+  }
+
+  spadj_status gradient(Problem* p, const double* x0, int n_steps, int objective_kind, const double*, int,
+                        double* J_host, double* grad, double*) override {
+    if (objective_kind != SPADJ_OBJ_FOURDVAR) return p->fail(SPADJ_ERR_UNSUPPORTED, "kolmogorov: objective must be FOURDVAR");
+    if (n_obs < 1) return p->fail(SPADJ_ERR_INVALID, "kolmogorov: call spadj_set_observations first");
+    if (obs_steps_h.back() > n_steps) return p->fail(SPADJ_ERR_INVALID, "kolmogorov: observation step beyond n_steps");
+    spadj_status s = ensure_traj(p, n_steps);
+    if (s != SPADJ_OK) return s;
+    if ((s = run_forward(p, n_steps, x0, tmp.as<double>(), trajbuf.as<double2>())) != SPADJ_OK) return s;
+    SPADJ_CUDA_TRY(p, seedbuf.ensure(sizeof(double2) * (size_t)state_size * n_obs));
+    SPADJ_CUDA_TRY(p, partial.ensure(sizeof(double) * (size_t)nmem * n_obs));
+    SPADJ_CUDA_TRY(p, Jd.ensure(sizeof(double) * nmem));
+    cudaEvent_t t = p->tic();
+    fourdvar_kernel<<<dim3(nmem, n_obs), kKolThreads, 0, p->stream>>>(dmem.as<KMember>(), trajbuf.as<double2>(),
+                                                                      obsteps.as<int>(), obsbuf.as<double2>(), state_size,
+                                                                      obs_kmax, seedbuf.as<double2>(),
+                                                                      partial.as<double>(), n_obs);
+    sum_rows_kernel<<<(nmem + 127) / 128, 128, 0, p->stream>>>(partial.as<double>(), n_obs, nmem, Jd.as<double>());
+    p->toc(t, KC_OBJECTIVE, 4.0 * state_size * n_obs);
+    if ((s = check_launch(p, "kolmogorov 4dvar")) != SPADJ_OK) return s;
+    std::vector<int> seed_at(n_steps + 1, -1);
+    for (int i = 0; i < n_obs; ++i) seed_at[obs_steps_h[i]] = i;
+    if ((s = run_adjoint(p, n_steps, trajbuf.as<double2>(), seed_at, seedbuf.as<double2>(), grad)) != SPADJ_OK) return s;
+    if (J_host) {
+      SPADJ_CUDA_TRY(p, cudaMemcpyAsync(J_host, Jd.ptr, sizeof(double) * nmem, cudaMemcpyDeviceToHost, p->stream));
+      SPADJ_CUDA_TRY(p, cudaStreamSynchronize(p->stream));
+      for (int b = 0; b < nmem; ++b)
+        if (!std::isfinite(J_host[b])) return p->fail(SPADJ_ERR_NONFINITE, "kolmogorov: objective is not finite");
+    }
+    return SPADJ_OK;
+  }
+
+  spadj_status set_option(Problem* p, int option, int value) {
+    switch (option) {
+      case 0: persistent = value ? 1 : 0; return SPADJ_OK;
+      case 1:
+        if (value < 1 || value > 64) return p->fail(SPADJ_ERR_INVALID, "set_option: column tile must be 1..64");
+        CW = value; grid_persistent = 0; return sync_members(p);
+      case 2:
+        if (value < 1 || value > 64) return p->fail(SPADJ_ERR_INVALID, "set_option: row tile must be 1..64");
+        RW = value; grid_persistent = 0; return sync_members(p);
+      case 3:
+        if (value < 0 || value > 32) return p->fail(SPADJ_ERR_INVALID, "set_option: CTAs per SM must be 0..32");
+        ctas_per_sm = value; grid_persistent = 0; return SPADJ_OK;
+      case 4:  // bounded-wait iteration limit (0 = default)
+        spin_limit = value > 0 ? (unsigned)value : kSpinLimit; return SPADJ_OK;
+      case 5:  // failure-path test: member whose completion is never signalled (-1 = off)
+        if (value < -1 || value >= nmem) return p->fail(SPADJ_ERR_INVALID, "set_option: member out of range");
+        drop_signal_member = value; return SPADJ_OK;
+      default: return p->fail(SPADJ_ERR_INVALID, "set_option: unknown option");
+    }
+  }
+
+  // Time a short forward sweep for each candidate tiling and keep the fastest; results are
+  // cached per process by the batch's resolutions.
+  spadj_status autotune(Problem* p) {
+    static std::map<std::vector<int>, std::vector<int>> cache;
+    std::vector<int> key;
+    for (auto& m : hm) key.push_back(m.N);
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+      CW = it->second[0]; RW = it->second[1]; ctas_per_sm = it->second[2]; grid_persistent = 0;
+      return sync_members(p);
+    }
+    spadj_status s;
+    // probe input: zero state is valid (forcing drives it)
+    SPADJ_CUDA_TRY(p, cudaMemsetAsync(Yr[0].ptr, 0, sizeof(double2) * state_size, p->stream));
+    double best = 1e300;
+    std::vector<int> bestv = {CW, RW, ctas_per_sm};
+    const int keep_p = persistent;
+    persistent = 1;
+    for (int cw : {2, 4, 8})
+      for (int rw : {1, 2, 4})
+        for (int cps : {0, 2}) {
+          CW = cw; RW = rw; ctas_per_sm = cps; grid_persistent = 0;
+          if ((s = sync_members(p)) != SPADJ_OK) return s;
+          SPADJ_CUDA_TRY(p, cudaStreamSynchronize(p->stream));
+          auto t0 = std::chrono::steady_clock::now();
+          if ((s = run_forward(p, 4, Yr[0].as<double>(), Yr[1].as<double>(), nullptr)) != SPADJ_OK) return s;
+          SPADJ_CUDA_TRY(p, cudaStreamSynchronize(p->stream));
+          const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+          if (el < best) { best = el; bestv = {cw, rw, cps}; }
+        }
+    persistent = keep_p;
+    cache[key] = bestv;
+    CW = bestv[0]; RW = bestv[1]; ctas_per_sm = bestv[2]; grid_persistent = 0;
+    return sync_members(p);
+  }
+
+  ~Kol() override {
+    for (DevBuf* b : {&dmem, &tables, &Xr[0], &Xr[1], &Fr[0], &Fr[1], &Yr[0], &Yr[1], &mixA, &mixB, &ctr, &trajbuf,
+                      &seedbuf, &seedmap, &obsbuf, &obsteps, &partial, &Jd, &tmp})
+      b->release();
+  }
+};
+
+}  // namespace
+
+EqImpl* make_kolmogorov(Problem* p, spadj_status* st) {
+  Kol* k = new Kol();
+  *st = k->init(p);
+  if (*st != SPADJ_OK) {
+    delete k;
+    return nullptr;
+  }
+  return k;
+}
+
+spadj_status kol_set_observations(EqImpl* impl, Problem* p, int n, const int* steps, const double* obs, int kmax) {
+  Kol* k = dynamic_cast<Kol*>(impl);
+  if (!k) return p->fail(SPADJ_ERR_UNSUPPORTED, "set_observations: only defined for the Kolmogorov batch");
+  return k->set_observations(p, n, steps, obs, kmax);
+}
+
+spadj_status kol_set_option(EqImpl* impl, Problem* p, int option, int value) {
+  Kol* k = dynamic_cast<Kol*>(impl);
+  if (!k) return p->fail(SPADJ_ERR_UNSUPPORTED, "set_option: only defined for the Kolmogorov batch");
+  return k->set_option(p, option, value);
+}
+
+spadj_status kol_autotune(EqImpl* impl, Problem* p) {
+  Kol* k = dynamic_cast<Kol*>(impl);
+  if (!k) return p->fail(SPADJ_ERR_UNSUPPORTED, "autotune: only defined for the Kolmogorov batch");
+  return k->autotune(p);
+}
+
+}  // namespace spadj

@@ -142,6 +142,10 @@ inline spadj_status check_launch(Problem* p, const char* what) {
 EqImpl* make_burgers(Problem* p, spadj_status* st);
 EqImpl* make_rb(Problem* p, spadj_status* st);
 spadj_status rb_pencil_solve(EqImpl* impl, Problem* p, int transpose, const double* v, double* x);
+EqImpl* make_kolmogorov(Problem* p, spadj_status* st);
+spadj_status kol_set_observations(EqImpl* impl, Problem* p, int n, const int* steps, const double* obs, int kmax);
+spadj_status kol_set_option(EqImpl* impl, Problem* p, int option, int value);
+spadj_status kol_autotune(EqImpl* impl, Problem* p);
 spadj_status rb_transform_noalloc(EqImpl* impl, Problem* p, int kind, const double* in, double* out);
 
 }  // namespace spadj

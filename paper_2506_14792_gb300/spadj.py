@@ -30,6 +30,7 @@ SPADJ_SBDF2 = 2
 SPADJ_RK222 = 3
 
 SPADJ_OBJ_ENERGY = 0
+SPADJ_OBJ_FOURDVAR = 1
 
 C2G, G2C, C2G_ADJ, G2C_ADJ = 0, 1, 2, 3
 
@@ -43,7 +44,7 @@ class SpadjError(RuntimeError):
 class spadj_desc(ctypes.Structure):
     _fields_ = [("eq", ctypes.c_int), ("scheme", ctypes.c_int), ("n", ctypes.c_int * 3),
                 ("length", ctypes.c_double * 3), ("params", ctypes.c_double * 4), ("dt", ctypes.c_double),
-                ("batch", ctypes.c_int), ("nonlinear", ctypes.c_int)]
+                ("batch", ctypes.c_int), ("nonlinear", ctypes.c_int), ("batch_n", ctypes.POINTER(ctypes.c_int))]
 
 
 _lib = None
@@ -59,6 +60,9 @@ _SIGS = {
     "spadj_eval_F_vjp": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "spadj_solve": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp]),
     "spadj_vjp": (ctypes.c_int, [_vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp]),
+    "spadj_set_observations": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, ctypes.c_int]),
+    "spadj_set_option": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
+    "spadj_autotune": (ctypes.c_int, [_vp]),
     "spadj_checkpoint_schedule": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "spadj_forward": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp]),
     "spadj_tangent": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp]),
@@ -124,7 +128,7 @@ CK_ADVANCE, CK_STORE, CK_RESTORE, CK_ADJOINT, CK_FREE, CK_OBJECTIVE = range(6)
 class Problem:
     """Owns one spadj_problem; methods take torch CUDA tensors."""
 
-    def __init__(self, eq, scheme, n, length, params, dt, batch=1, nonlinear=True, stream=None):
+    def __init__(self, eq, scheme, n, length, params, dt, batch=1, nonlinear=True, stream=None, batch_n=None):
         import torch
         d = spadj_desc()
         d.eq, d.scheme = eq, scheme
@@ -135,6 +139,9 @@ class Problem:
         for i, v in enumerate(list(params)[:4]):
             d.params[i] = float(v)
         d.dt, d.batch, d.nonlinear = float(dt), int(batch), int(bool(nonlinear))
+        if batch_n is not None:
+            self._batch_n = (ctypes.c_int * len(batch_n))(*[int(v) for v in batch_n])
+            d.batch_n = ctypes.cast(self._batch_n, ctypes.POINTER(ctypes.c_int))
         self.desc = d
         if stream is None:
             stream = torch.cuda.current_stream()
@@ -222,6 +229,18 @@ class Problem:
                                            _ptr(obj_data), ckpt_slots, jp,
                                            _ptr(_as_f64(grad_x0, n, "grad_x0")), _ptr(grad_p)))
         return J
+
+    def set_observations(self, obs_steps, obs, kmax):
+        n = self.state_len(0)
+        steps = (ctypes.c_int * len(obs_steps))(*[int(v) for v in obs_steps])
+        _chk(self.h, lib().spadj_set_observations(self.h, len(obs_steps), steps,
+                                                   _ptr(_as_f64(obs, n * len(obs_steps), "obs")), int(kmax)))
+
+    def set_option(self, option, value):
+        _chk(self.h, lib().spadj_set_option(self.h, int(option), int(value)))
+
+    def autotune(self):
+        _chk(self.h, lib().spadj_autotune(self.h))
 
     def vjp(self, x0, n_steps, seed_steps, seeds, grad_x0, ckpt_slots=0):
         """grad_x0 = sum_i (dX_{seed_steps[i]}/dX_0)^T seeds[i]; seeds is [n_seeds][state] on the device."""

@@ -1,0 +1,186 @@
+"""GPU parity for the batched Kolmogorov path (mixed resolutions in one persistent launch,
+SBDF2, 4D-Var) through the C-ABI against the FP64 oracle, plus the scheduler's failure path
+(a bounded wait that runs out returns SPADJ_ERR_TIMEOUT and leaves the context usable)."""
+import numpy as np
+import pytest
+
+import synthetic
+from oracle import imex
+from oracle import kolmogorov as okol
+from tests.gpu_util import TOL, dev, host, rel_err
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def gpu_problem(sizes, Re=100.0, dt=5e-3, nonlinear=True, forcing=True):
+    from paper_2506_14792_gb300 import spadj
+    return spadj.Problem(spadj.SPADJ_KOLMOGOROV2D, spadj.SPADJ_SBDF2, [sizes[0]], [2 * np.pi], [Re, 0.0 if forcing else 1.0],
+                         dt, batch=len(sizes), nonlinear=nonlinear, batch_n=list(sizes))
+
+
+def pack(arrs):
+    return np.concatenate([a.ravel() for a in arrs])
+
+
+def unpack(v, sizes):
+    out, o = [], 0
+    for n in sizes:
+        k = (n // 2) * n
+        out.append(v[o:o + k].reshape(n // 2, n))
+        o += k
+    return out
+
+
+def ics(sizes, seed0):
+    return [okol.Kolmogorov(n, 100.0).project(synthetic.kolmogorov_ic(n, seed0 + i)) for i, n in enumerate(sizes)]
+
+
+def test_eval_F_mixed():
+    sizes = [16, 24, 32]
+    p = gpu_problem(sizes)
+    X = ics(sizes, 1)
+    out = torch.zeros(sum((n // 2) * n for n in sizes), dtype=torch.complex128, device="cuda")
+    p.eval_F(dev(pack(X)), out)
+    got = unpack(host(out), sizes)
+    for n, x, g in zip(sizes, X, got):
+        assert rel_err(g, okol.Kolmogorov(n, 100.0).F(x)) < 1e-12
+
+
+@pytest.mark.parametrize("persistent", [1, 0])
+def test_forward_mixed_batch(persistent):
+    sizes, dt, nsteps = [16, 24, 32, 16], 5e-3, 30
+    p = gpu_problem(sizes, dt=dt)
+    p.set_option(0, persistent)
+    X = ics(sizes, 10)
+    out = torch.zeros(sum((n // 2) * n for n in sizes), dtype=torch.complex128, device="cuda")
+    p.forward(nsteps, dev(pack(X)), out)
+    got = unpack(host(out), sizes)
+    for n, x, g in zip(sizes, X, got):
+        o = okol.Kolmogorov(n, 100.0)
+        assert rel_err(g, imex.multistep_forward(o, x, nsteps, dt)[-1]) < TOL
+
+
+def test_persistent_equals_phased_bitwise():
+    sizes, nsteps = [16, 32, 48], 12
+    X = dev(pack(ics(sizes, 20)))
+    outs = []
+    for mode in (1, 0):
+        p = gpu_problem(sizes)
+        p.set_option(0, mode)
+        o = torch.zeros_like(X)
+        p.forward(nsteps, X, o)
+        outs.append(o)
+    assert torch.equal(outs[0], outs[1])
+
+
+def _fourdvar_case(sizes, dt, nsteps, obs_steps, kmax, seed0):
+    X0 = ics(sizes, seed0)
+    obs, Js, gs = [], [], []
+    for i, n in enumerate(sizes):
+        o = okol.Kolmogorov(n, 100.0)
+        Xt = imex.multistep_forward(o, o.project(synthetic.kolmogorov_ic(n, 900 + seed0 + i)), nsteps, dt)
+        mask = o.lowpass_mask(kmax)
+        ob = np.stack([mask * Xt[k] for k in obs_steps])
+        J, g, _ = okol.fourdvar_gradient(o, X0[i], nsteps, dt, obs_steps, ob, mask)
+        obs.append(ob)
+        Js.append(J)
+        gs.append(g)
+    obs_packed = np.stack([pack([obs[i][m] for i in range(len(sizes))]) for m in range(len(obs_steps))])
+    return X0, obs_packed, Js, gs
+
+
+@pytest.mark.parametrize("persistent", [1, 0])
+def test_fourdvar_gradient_mixed(persistent):
+    sizes, dt, nsteps, obs_steps, kmax = [16, 32, 48], 5e-3, 40, [10, 20, 30, 40], 8
+    X0, obs, Js, gs = _fourdvar_case(sizes, dt, nsteps, obs_steps, kmax, 30)
+    from paper_2506_14792_gb300 import spadj
+    p = gpu_problem(sizes, dt=dt)
+    p.set_option(0, persistent)
+    p.set_observations(obs_steps, dev(obs), kmax)
+    g = torch.zeros(sum((n // 2) * n for n in sizes), dtype=torch.complex128, device="cuda")
+    J = p.gradient(dev(pack(X0)), nsteps, g, objective=spadj.SPADJ_OBJ_FOURDVAR)
+    got = unpack(host(g), sizes)
+    for i in range(len(sizes)):
+        assert abs(J[i] - Js[i]) <= TOL * abs(Js[i])
+        assert rel_err(got[i], gs[i]) < TOL
+
+
+def test_vjp_final_seed():
+    sizes, dt, nsteps = [16, 24], 5e-3, 25
+    X0 = ics(sizes, 40)
+    seeds = [synthetic.random_coeffs((n // 2, n), seed=70 + i) for i, n in enumerate(sizes)]
+    p = gpu_problem(sizes, dt=dt)
+    g = torch.zeros(sum((n // 2) * n for n in sizes), dtype=torch.complex128, device="cuda")
+    p.vjp(dev(pack(X0)), nsteps, [nsteps], dev(pack(seeds)[None, :]), g)
+    got = unpack(host(g), sizes)
+    for i, n in enumerate(sizes):
+        o = okol.Kolmogorov(n, 100.0)
+        X = imex.multistep_forward(o, X0[i], nsteps, dt)
+        want = imex.multistep_adjoint(o, X, lambda k: seeds[i] if k == nsteps else None, dt)
+        assert rel_err(got[i], want) < TOL
+
+
+def test_bounded_wait_times_out_and_context_survives():
+    from paper_2506_14792_gb300 import spadj
+    sizes = [16, 32]
+    p = gpu_problem(sizes)
+    X = dev(pack(ics(sizes, 50)))
+    out = torch.zeros_like(X)
+    p.set_option(4, 2000)   # short bounded wait
+    p.set_option(5, 0)      # member 0's completions are never signalled
+    with pytest.raises(spadj.SpadjError) as e:
+        p.forward(5, X, out)
+    assert e.value.status == spadj.SPADJ_ERR_TIMEOUT
+    p.set_option(5, -1)
+    p.set_option(4, 0)
+    p.forward(5, X, out)  # the same problem and context still work
+    torch.cuda.synchronize()
+    o = okol.Kolmogorov(16, 100.0)
+    got = unpack(host(out), sizes)
+    x0 = unpack(host(X), sizes)
+    assert rel_err(got[0], imex.multistep_forward(o, x0[0], 5, 5e-3)[-1]) < TOL
+
+
+def test_autotune_keeps_results():
+    sizes, nsteps = [16, 32], 10
+    X = dev(pack(ics(sizes, 60)))
+    p = gpu_problem(sizes)
+    ref = torch.zeros_like(X)
+    p.forward(nsteps, X, ref)
+    p.autotune()
+    out = torch.zeros_like(X)
+    p.forward(nsteps, X, out)
+    assert rel_err(host(out), host(ref)) < 1e-13
+
+
+def test_full_batch_sampled_members():
+    """64 members, 16 each at 128^2, 256^2, 384^2, 512^2, Re = 100, dt = 5e-4, one persistent
+    launch per sweep; 4D-Var over a 40-step window (observations every 10 steps, |k| <= 32);
+    one member per resolution checked against the oracle."""
+    from paper_2506_14792_gb300 import spadj
+    res = [128, 256, 384, 512]
+    sizes = [res[i // 16] for i in range(64)]
+    dt, nsteps, obs_steps, kmax = 5e-4, 40, [10, 20, 30, 40], 32
+    X0 = [synthetic.kolmogorov_ic(n, 100 + i) for i, n in enumerate(sizes)]
+    check = [0, 17, 34, 51]
+    obs_m, ref = [], {}
+    truth = {}
+    for i in check:
+        n = sizes[i]
+        o = okol.Kolmogorov(n, 100.0)
+        Xt = imex.multistep_forward(o, synthetic.kolmogorov_ic(n, 1000 + i), nsteps, dt)
+        truth[i] = np.stack([o.lowpass_mask(kmax) * Xt[k] for k in obs_steps])
+        J, g, _ = okol.fourdvar_gradient(o, X0[i], nsteps, dt, obs_steps, truth[i], o.lowpass_mask(kmax))
+        ref[i] = (J, g)
+    obs = np.stack([pack([truth[i][m] if i in truth else np.zeros((n // 2, n), complex)
+                          for i, n in enumerate(sizes)]) for m in range(len(obs_steps))])
+    p = gpu_problem(sizes, dt=dt)
+    p.set_observations(obs_steps, dev(obs), kmax)
+    g = torch.zeros(sum((n // 2) * n for n in sizes), dtype=torch.complex128, device="cuda")
+    J = p.gradient(dev(pack(X0)), nsteps, g, objective=spadj.SPADJ_OBJ_FOURDVAR)
+    got = unpack(host(g), sizes)
+    assert np.all(np.isfinite(J))
+    for i in check:
+        assert abs(J[i] - ref[i][0]) <= TOL * abs(ref[i][0])
+        assert rel_err(got[i], ref[i][1]) < TOL
