@@ -184,7 +184,91 @@ class RayleighBenard:
                 "factorisations cached)" % (nsteps, self.nsteps), el)
 
 
-WORKLOADS = {"burgers": Burgers, "rb": RayleighBenard}
+class KolmogorovBatch:
+    """Batched 2D Kolmogorov, Re=100, forcing sin(4y), 64 members (16 each at 128^2, 256^2,
+    384^2, 512^2) in one persistent launch per sweep, SBDF2 dt=5e-4, 2000 steps, 4D-Var misfit
+    to 8 observation times (every 250 steps, |k| <= 32).  Observations come from a separate
+    truth run of the same solver (synthetic data)."""
+    name = "kolmogorov2d_batch64_mixed128-512_Re100_sbdf2_2000steps_4dvar8"
+
+    def __init__(self, nsteps=2000, dt=5e-4, Re=100.0):
+        self.res = [128, 256, 384, 512]
+        self.sizes = [self.res[i // 16] for i in range(64)]
+        self.nsteps, self.dt, self.Re = nsteps, dt, Re
+        self.dof = sum(n * n for n in self.sizes)
+        self.flush_l2 = False
+        self.B = 64
+
+    def config(self):
+        return {"workload": self.name, "members": 64, "resolutions": self.res, "Re": self.Re, "dt": self.dt,
+                "steps": self.nsteps, "observations": self.obs_steps(), "dof_per_step": self.dof,
+                "l2": "working set > L2 (stored trajectory %.0f GB)" % (16 * sum((n // 2) * n for n in self.sizes)
+                                                                        * (self.nsteps + 1) / 1e9)}
+
+    def obs_steps(self):
+        k = max(1, self.nsteps // 8)
+        return [k * (i + 1) for i in range(8)]
+
+    def units_per_step(self):
+        return self.dof * self.nsteps
+
+    def setup(self, device):
+        import torch
+        from paper_2506_14792_gb300 import spadj
+        self.torch = torch
+        self.sp = spadj
+        self.p = spadj.Problem(spadj.SPADJ_KOLMOGOROV2D, spadj.SPADJ_SBDF2, [128], [2 * np.pi], [self.Re, 0.0],
+                               self.dt, batch=64, batch_n=self.sizes)
+        pack = lambda arrs: np.concatenate([a.ravel() for a in arrs])
+        self.x0_host = pack([synthetic.kolmogorov_ic(n, 100 + i) for i, n in enumerate(self.sizes)])
+        truth = torch.from_numpy(pack([synthetic.kolmogorov_ic(n, 5000 + i) for i, n in enumerate(self.sizes)])).to(device)
+        # observations: truth states at the observation steps (segments of the same solver),
+        # low-passed by the objective's observation operator inside the library
+        obs, cur, last = [], truth, 0
+        for k in self.obs_steps():
+            nxt = torch.empty_like(cur)
+            self.p.forward(k - last, cur, nxt)
+            obs.append(nxt)
+            cur, last = nxt, k
+        self.p.set_observations(self.obs_steps(), torch.stack(obs).contiguous(), 32)
+        self.p.autotune()
+        self.x0 = torch.from_numpy(self.x0_host).to(device)
+        self.grad = torch.empty_like(self.x0)
+        self.x0_pin = torch.from_numpy(self.x0_host).pin_memory()
+        self.grad_pin = torch.empty(self.x0.shape, dtype=torch.complex128).pin_memory()
+        self.x0_dev2 = torch.empty_like(self.x0)
+
+    def step(self, ev=None):
+        self.p.gradient(self.x0, self.nsteps, self.grad, objective=self.sp.SPADJ_OBJ_FOURDVAR, want_J=False)
+
+    def e2e_step(self):
+        self.x0_dev2.copy_(self.x0_pin, non_blocking=True)
+        J = self.p.gradient(self.x0_dev2, self.nsteps, self.grad, objective=self.sp.SPADJ_OBJ_FOURDVAR)
+        self.grad_pin.copy_(self.grad, non_blocking=True)
+        return J
+
+    def e2e_bytes(self):
+        n = self.x0_host.nbytes
+        return n, n + 8 * 64
+
+    def cpu_sample(self, nsteps=4):
+        """Oracle 4D-Var gradient of one 128^2 and one 512^2 member over a short window, scaled to
+        the batch's dof mix (dof*steps/s of the two members together)."""
+        from oracle import kolmogorov as okol
+        t = time.perf_counter()
+        d = 0
+        for n in (128, 512):
+            o = okol.Kolmogorov(n, self.Re)
+            X0 = o.project(synthetic.kolmogorov_ic(n, 7))
+            mask = o.lowpass_mask(32)
+            obs = np.stack([np.zeros_like(X0)] * 2)
+            okol.fourdvar_gradient(o, X0, nsteps, self.dt, [nsteps // 2, nsteps], obs, mask)
+            d += n * n
+        el = time.perf_counter() - t
+        return d * nsteps / el, "one 128^2 and one 512^2 member, %d-step 4D-Var gradient (numpy FP64)" % nsteps, el
+
+
+WORKLOADS = {"burgers": Burgers, "rb": RayleighBenard, "kolmogorov": KolmogorovBatch}
 DEFAULT_WORKLOAD = "rb"
 
 

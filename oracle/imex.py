@@ -203,3 +203,36 @@ def rk_adjoint(prob, stages, dJ, dt, A, H):
         src = dJ(n)
         Ybar = lam if src is None else lam + src
     return Ybar
+
+
+def multistep_adjoint_params(prob, X, dJ, dt, order=2):
+    """(dJ/dX_0, dJ/dp) for parameters p of the explicit term.
+
+    F(X_m; p) enters eq. imex of step m + i with weight c_i^{m+i}, so the parameter cotangent
+    is sum_m (dF(X_m)/dp)^dagger W_m with W_m = sum_i c_i^{m+i} Y_{m+i}, the same combination
+    whose state VJP enters eq. IMEX_adjoint at X_m (eqs. 5-6 with F appearing on the
+    right-hand side of the timestepper)."""
+    nsteps = len(X) - 1
+    Y = [None] * (nsteps + 1)
+    coeffs = [None] + [sbdf_coeffs(n, order, dt) for n in range(1, nsteps + 1)]
+    gp = 0
+    for n in range(nsteps, -1, -1):
+        lam = dJ(n)
+        lam = 0 if lam is None else lam
+        W = 0
+        for i in range(1, order + 1):
+            m = n + i
+            if m > nsteps:
+                continue
+            a, b, c = coeffs[m]
+            if i > len(a) - 1:
+                continue
+            W = W + c[i] * Y[m]
+            lam = lam - (a[i] * prob.Mt(Y[m]) + b[i] * prob.Lt(Y[m]))
+        if not isinstance(W, int):
+            lam = lam + prob.F_vjp(X[n], W)
+            gp = gp + prob.F_param_vjp(X[n], W)
+        if n == 0:
+            return lam, gp
+        a, b, _ = coeffs[n]
+        Y[n] = prob.solve_t(a[0], b[0], prob.project(lam))

@@ -87,3 +87,17 @@ def kolmogorov_ic(N, seed, urms=1.0):
 def kolmogorov_batch(sizes, seeds):
     """List of per-member ICs for a mixed-resolution batch."""
     return [kolmogorov_ic(n, s) for n, s in zip(sizes, seeds)]
+
+
+def cnn_params(seed, scale_out=0.1):
+    """Seeded initial weights of the 1-32-32-32-1 closure CNN: N(0, 1/fan_in) weights, zero
+    biases, last layer scaled by `scale_out` (flat vector, layer by layer: W then b)."""
+    rng = np.random.default_rng(seed)
+    ch = (1, 32, 32, 32, 1)
+    parts = []
+    for k, (ci, co) in enumerate(zip(ch[:-1], ch[1:])):
+        W = rng.standard_normal((co, ci, 3, 3)) / np.sqrt(9.0 * ci)
+        if k == 3:
+            W *= scale_out
+        parts += [W.ravel(), np.zeros(co)]
+    return np.concatenate(parts)
