@@ -95,6 +95,8 @@ typedef struct {
   int nonlinear;     /* 1: F as defined; 0: F = 0 (linear problem, used by tests) */
   const int* batch_n;/* host, nullable: per-member resolution of a mixed batch (SPADJ_KOLMOGOROV2D);
                         NULL = every member uses n[0].  Copied by spadj_create. */
+  int closure;       /* SPADJ_KOLMOGOROV2D: 1 adds the learned CNN closure C(w; p) to F on the grid
+                        (uniform resolution; parameters set by spadj_set_params, initially 0) */
 } spadj_desc;
 
 /* Build a problem (operators, transform tables, factorisations) bound to cuda_stream
@@ -181,6 +183,12 @@ typedef enum {
  * copied by the call) and the low-pass cut-off kmax of the observation operator H. */
 spadj_status spadj_set_observations(spadj_problem* prob, int n_obs, const int* obs_steps, const double* obs,
                                     int kmax);
+
+/* Parameters p of the learned closure (device, spadj_state_len(prob, 2) float64 values: per
+ * layer the 3x3 weights W[o][c][a][b] then the biases; channels 1 -> 32 -> 32 -> 32 -> 1, tanh
+ * after the first three layers, periodic padding).  The network runs with BF16 operands and
+ * FP32 accumulation; spadj_gradient's grad_p receives dJ/dp (eq. 6 with p entering F). */
+spadj_status spadj_set_params(spadj_problem* prob, const double* params);
 
 /* Tuning knobs of the batched persistent launch (SPADJ_KOLMOGOROV2D): option 0 = persistent
  * scheduler (1, default) or one launch per phase (0); 1 = x-modes per column tile; 2 = grid

@@ -127,6 +127,12 @@ spadj_status spadj_set_option(spadj_problem* p, int option, int value) {
   return spadj::kol_set_option(p->impl, p, option, value);
 }
 
+spadj_status spadj_set_params(spadj_problem* p, const double* params) {
+  if (!p) return SPADJ_ERR_INVALID;
+  if (bad_ptr(params)) return p->fail(SPADJ_ERR_INVALID, "set_params: NULL array");
+  return spadj::kol_set_params(p->impl, p, params);
+}
+
 spadj_status spadj_autotune(spadj_problem* p) {
   if (!p) return SPADJ_ERR_INVALID;
   return spadj::kol_autotune(p->impl, p);

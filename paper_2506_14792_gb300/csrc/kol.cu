@@ -27,6 +27,7 @@
 #include <string>
 #include <vector>
 
+#include "closure.cuh"
 #include "fft.cuh"
 #include "problem.h"
 
@@ -41,6 +42,7 @@ struct KMember {
   int N, Kx, M, L, res;
   long long off_state;  // complex offset of the member in a state array
   long long off_mix;    // complex offset of the member in a mixed [y][kx] array
+  long long off_grid;   // offset of the member in a real [y][x] grid array
   int nCA, nB;          // tiles per stage
   int caStart, bStart;  // first item of the member inside a stage's CA / B block
 };
@@ -67,8 +69,11 @@ struct KolArgs {
   double2* Xr[2];
   double2* Fr[2];
   double2* Yr[2];
-  double2* mixA[5];
-  double2* mixB[4];
+  double2* mixA[6];
+  double2* mixB[5];
+  int closure;            // learned closure active: omega itself is carried as a fifth field
+  double* gridW;          // closure input grid (vorticity), [member][y][x]
+  double* gridG;          // adjoint: T^dagger of the cotangent on the grid
   double2* traj;
   double2* out;
   const int* seed_at;
@@ -157,7 +162,7 @@ __device__ void ca_forward(const KolArgs& A, const KMember& m, int tile, int s) 
       __syncthreads();
     } else {
       double2* r = nullptr;
-      if (A.nonlinear) {
+      if (A.nonlinear || A.closure) {
         for (int j = threadIdx.x; j < M; j += blockDim.x) ca[j] = ldcg2(&A.mixB[0][m.off_mix + (long long)j * Kx + kx]);
         r = col_fft<-1>(ca, cb, R);
       }
@@ -167,7 +172,7 @@ __device__ void ca_forward(const KolArgs& A, const KMember& m, int tile, int s) 
         const int idx = yidx(q, N, M);
         const double ky = kyof(q, N);
         double2 F = make_double2(0.0, 0.0);
-        if (idx >= 0 && A.nonlinear) F = make_double2(-r[idx].x * invM, -r[idx].y * invM);
+        if (idx >= 0 && (A.nonlinear || A.closure)) F = make_double2(-r[idx].x * invM, -r[idx].y * invM);
         if (A.forcing && kx == 0 && (q == 4 || q == N - 4)) F.x -= 2.0;
         if (A.fonly) {
           A.out[col + q] = F;
@@ -194,14 +199,15 @@ __device__ void ca_forward(const KolArgs& A, const KMember& m, int tile, int s) 
       if (A.traj) A.traj[(long long)s * S + col + q] = xc[q];
       if (s == A.S) A.out[col + q] = xc[q];
     }
-    if (s < A.S && A.nonlinear) {
-      for (int f = 0; f < 4; ++f) {
+    if (s < A.S && (A.nonlinear || A.closure)) {
+      const int nf = A.closure ? 5 : 4;
+      for (int f = 0; f < nf; ++f) {
         __syncthreads();
         for (int j = threadIdx.x; j < M; j += blockDim.x) ca[j] = make_double2(0.0, 0.0);
         __syncthreads();
         for (int q = threadIdx.x; q < N; q += blockDim.x) {
           const int idx = yidx(q, N, M);
-          if (idx >= 0) ca[idx] = fmult(f, (double)kx, (double)kyof(q, N), xc[q]);
+          if (idx >= 0) ca[idx] = f < 4 ? fmult(f, (double)kx, (double)kyof(q, N), xc[q]) : xc[q];
         }
         double2* r = col_fft<1>(ca, cb, R);
         for (int j = threadIdx.x; j < M; j += blockDim.x) A.mixA[f][m.off_mix + (long long)j * Kx + kx] = r[j];
@@ -220,7 +226,9 @@ __device__ void row_c2r(const double2* src, double2* dst, double2* sa, double2* 
   c2r_pre(sa, [&](int k) { return st[k]; }, Kx, L, R.WMx, w0, w);
   __syncthreads();
   double2* r = cfft_smem_t<1>(sa, sb, R.px, R.WMx);
-  for (int j = threadIdx.x; j < L; j += blockDim.x) dst[j] = r[j];
+  if (r != dst) {
+    for (int j = threadIdx.x; j < L; j += blockDim.x) dst[j] = r[j];
+  }
   __syncthreads();
 }
 
@@ -249,11 +257,21 @@ __device__ void b_forward(const KolArgs& A, const KMember& m, int tile) {
   const int j0 = tile * A.RW, j1 = min(M, j0 + A.RW);
   const double invM = 1.0 / M;
   for (int j = j0; j < j1; ++j) {
-    for (int f = 0; f < 4; ++f)
-      row_c2r(A.mixA[f] + m.off_mix + (long long)j * Kx, G + f * L, sa, sb, st, m, R, 1.0, 1.0);
-    for (int i = threadIdx.x; i < L; i += blockDim.x) {
-      const double2 u = G[i], v = G[L + i], wx = G[2 * L + i], wy = G[3 * L + i];
-      sa[i] = make_double2(fma(u.x, wx.x, v.x * wy.x), fma(u.y, wx.y, v.y * wy.y));
+    if (A.closure) {
+      row_c2r(A.mixA[4] + m.off_mix + (long long)j * Kx, sa, sa, sb, st, m, R, 1.0, 1.0);
+      double2* gw = reinterpret_cast<double2*>(A.gridW + m.off_grid + (long long)j * M);
+      for (int i = threadIdx.x; i < L; i += blockDim.x) gw[i] = sa[i];
+      __syncthreads();
+    }
+    if (A.nonlinear) {
+      for (int f = 0; f < 4; ++f)
+        row_c2r(A.mixA[f] + m.off_mix + (long long)j * Kx, G + f * L, sa, sb, st, m, R, 1.0, 1.0);
+      for (int i = threadIdx.x; i < L; i += blockDim.x) {
+        const double2 u = G[i], v = G[L + i], wx = G[2 * L + i], wy = G[3 * L + i];
+        sa[i] = make_double2(fma(u.x, wx.x, v.x * wy.x), fma(u.y, wx.y, v.y * wy.y));
+      }
+    } else {
+      for (int i = threadIdx.x; i < L; i += blockDim.x) sa[i] = make_double2(0.0, 0.0);
     }
     __syncthreads();
     row_r2c(sa, sb, A.mixB[0] + m.off_mix + (long long)j * Kx, m, R, invM, invM);
@@ -276,14 +294,20 @@ __device__ void ca_adjoint(const KolArgs& A, const KMember& m, int tile, int n) 
     const long long col = m.off_state + (long long)kx * N;
     for (int q = threadIdx.x; q < N; q += blockDim.x) lam[q] = make_double2(0.0, 0.0);
     __syncthreads();
-    if (n < SN && A.nonlinear) {
-      // VJP: B_y^dagger of the four grid cotangents, then the adjoint multipliers
-      for (int f = 0; f < 4; ++f) {
+    if (n < SN && (A.nonlinear || A.closure)) {
+      // VJP: B_y^dagger of the grid cotangents, then the adjoint multipliers (identity for the
+      // closure's input field)
+      for (int f = A.nonlinear ? 0 : 4; f < (A.closure ? 5 : 4); ++f) {
         for (int j = threadIdx.x; j < M; j += blockDim.x) ca[j] = ldcg2(&A.mixB[f][m.off_mix + (long long)j * Kx + kx]);
         double2* r = col_fft<-1>(ca, cb, R);
         for (int q = threadIdx.x; q < N; q += blockDim.x) {
           const int idx = yidx(q, N, M);
           if (idx < 0) continue;
+          if (f == 4) {
+            lam[q].x += r[idx].x;
+            lam[q].y += r[idx].y;
+            continue;
+          }
           // adjoint of i*s is -i*s: fmult with the negated multiplier
           const double2 v = fmult(f, (double)kx, (double)kyof(q, N), r[idx]);
           lam[q].x -= v.x;
@@ -338,7 +362,7 @@ __device__ void ca_adjoint(const KolArgs& A, const KMember& m, int tile, int n) 
       A.Yr[n & 1][col + q] = yc[q];
     }
     __syncthreads();
-    if (!A.nonlinear) continue;
+    if (!A.nonlinear && !A.closure) continue;
     // T_y^dagger W (inverse FFT with 1/M) -> mixA[4]
     for (int j = threadIdx.x; j < M; j += blockDim.x) ca[j] = make_double2(0.0, 0.0);
     __syncthreads();
@@ -354,16 +378,18 @@ __device__ void ca_adjoint(const KolArgs& A, const KMember& m, int tile, int n) 
     }
     // fields of X_{n-1} from the trajectory
     for (int q = threadIdx.x; q < N; q += blockDim.x) yc[q] = ldcg2(&A.traj[(long long)(n - 1) * S + col + q]);
-    for (int f = 0; f < 4; ++f) {
+    for (int f = A.nonlinear ? 0 : 4; f < (A.closure ? 5 : 4); ++f) {
       __syncthreads();
       for (int j = threadIdx.x; j < M; j += blockDim.x) ca[j] = make_double2(0.0, 0.0);
       __syncthreads();
       for (int q = threadIdx.x; q < N; q += blockDim.x) {
         const int idx = yidx(q, N, M);
-        if (idx >= 0) ca[idx] = fmult(f, (double)kx, (double)kyof(q, N), yc[q]);
+        if (idx >= 0) ca[idx] = f < 4 ? fmult(f, (double)kx, (double)kyof(q, N), yc[q]) : yc[q];
       }
       double2* r = col_fft<1>(ca, cb, R);
-      for (int j = threadIdx.x; j < M; j += blockDim.x) A.mixA[f][m.off_mix + (long long)j * Kx + kx] = r[j];
+      // the closure's input field goes to slot 5 (slot 4 holds T^dagger W)
+      double2* dstf = A.mixA[f < 4 ? f : 5];
+      for (int j = threadIdx.x; j < M; j += blockDim.x) dstf[m.off_mix + (long long)j * Kx + kx] = r[j];
     }
     __syncthreads();
   }
@@ -380,9 +406,17 @@ __device__ void b_adjoint(const KolArgs& A, const KMember& m, int tile) {
   double2* st = sb + L;       // Kx
   const int j0 = tile * A.RW, j1 = min(M, j0 + A.RW);
   for (int j = j0; j < j1; ++j) {
+    row_c2r(A.mixA[4] + m.off_mix + (long long)j * Kx, G + 4 * L, sa, sb, st, m, R, 1.0 / M, 0.5 / M);
+    if (A.closure) {  // closure input omega and the grid cotangent g, for the CNN's backward pass
+      row_c2r(A.mixA[5] + m.off_mix + (long long)j * Kx, sa, sa, sb, st, m, R, 1.0, 1.0);
+      double2* gw = reinterpret_cast<double2*>(A.gridW + m.off_grid + (long long)j * M);
+      double2* gg = reinterpret_cast<double2*>(A.gridG + m.off_grid + (long long)j * M);
+      for (int i = threadIdx.x; i < L; i += blockDim.x) { gw[i] = sa[i]; gg[i] = G[4 * L + i]; }
+      __syncthreads();
+    }
+    if (!A.nonlinear) continue;
     for (int f = 0; f < 4; ++f)
       row_c2r(A.mixA[f] + m.off_mix + (long long)j * Kx, G + f * L, sa, sb, st, m, R, 1.0, 1.0);
-    row_c2r(A.mixA[4] + m.off_mix + (long long)j * Kx, G + 4 * L, sa, sb, st, m, R, 1.0 / M, 0.5 / M);
     // grid cotangents of u, v, w_x, w_y: -g w_x, -g w_y, -g u, -g v
     for (int i = threadIdx.x; i < L; i += blockDim.x) {
       const double2 u = G[i], v = G[L + i], wx = G[2 * L + i], wy = G[3 * L + i], g = G[4 * L + i];
@@ -478,6 +512,35 @@ __global__ void __launch_bounds__(kKolThreads) kol_phase(const __grid_constant__
   run_item(A, stage, isCA != 0, b, tile);
 }
 
+// x-forward transform of grid rows of the closure: mode 0 mixB[0] -= T_x(corr row) (the
+// closure term enters F = -P + C with P stored), mode 1 mixB[4] = B_x^dagger(grid row).
+__global__ void __launch_bounds__(kKolThreads) closure_rows_kernel(const __grid_constant__ KolArgs A, const double* grid,
+                                                                  int mode) {
+  extern __shared__ double2 ks[];
+  const int b = blockIdx.y;
+  const KMember& m = A.mem[b];
+  const int j = blockIdx.x;
+  if (j >= m.M) return;
+  const KRes& R = A.res[m.res];
+  const int L = m.L, Kx = m.Kx;
+  double2* sa = ks;
+  double2* sb = sa + L;
+  double2* st = sb + L;
+  const double2* g = reinterpret_cast<const double2*>(grid + m.off_grid + (long long)j * m.M);
+  for (int i = threadIdx.x; i < L; i += blockDim.x) sa[i] = g[i];
+  __syncthreads();
+  if (mode == 0) {
+    row_r2c(sa, sb, st, m, R, 1.0 / m.M, 1.0 / m.M);
+    double2* dst = A.mixB[0] + m.off_mix + (long long)j * Kx;
+    for (int k = threadIdx.x; k < Kx; k += blockDim.x) {
+      const double2 v = dst[k];
+      dst[k] = make_double2(v.x - st[k].x, v.y - st[k].y);
+    }
+  } else {
+    row_r2c(sa, sb, A.mixB[4] + m.off_mix + (long long)j * Kx, m, R, 1.0, 2.0);
+  }
+}
+
 // 4D-Var misfit per (member, observation) and its cotangent seeds[m] = H^T H (X_{n_m} - obs_m)
 __global__ void fourdvar_kernel(const KMember* mem, const double2* traj, const int* obs_steps, const double2* obs,
                                 long long S, int kmax, double2* seeds, double* partial, int n_obs) {
@@ -531,7 +594,9 @@ struct Kol : EqImpl {
   std::vector<KMember> hm;
   std::vector<int> resN;
   int nmem = 0;
-  long long state_size = 0, mix_size = 0;
+  long long state_size = 0, mix_size = 0, grid_size = 0;
+  int closure = 0;
+  DevBuf gridW, gridG, corr, xq, hbuf[3], dact[3], dh, dz, pbuf, wq, bq, part, gp;
   int Lmax = 0, Mmax = 0, Nmax = 0, Kxmax = 0;
   double Re = 100.0, dt = 0;
   int forcing = 1, nonlinear = 1;
@@ -553,6 +618,7 @@ struct Kol : EqImpl {
       for (auto& m : hm) g += (size_t)m.M * m.M;
       return g;
     }
+    if (which == 2) return closure ? (size_t)cnn::n_params() : 0;
     return 0;
   }
 
@@ -580,7 +646,8 @@ struct Kol : EqImpl {
     forcing = d.params[1] == 1.0 ? 0 : 1;
     nonlinear = d.nonlinear;
     dt = d.dt;
-    long long offs = 0, offm = 0;
+    long long offs = 0, offm = 0, offg = 0;
+    closure = d.closure ? 1 : 0;
     for (int b = 0; b < nmem; ++b) {
       const int N = d.batch_n ? d.batch_n[b] : d.n[0];
       if (N < 8 || N % 4 != 0 || !fft_len_ok(3 * N / 2) || N > 1024)
@@ -595,14 +662,18 @@ struct Kol : EqImpl {
       }
       KMember m{};
       m.N = N; m.Kx = N / 2; m.M = 3 * N / 2; m.L = m.M / 2; m.res = r;
-      m.off_state = offs; m.off_mix = offm;
+      m.off_state = offs; m.off_mix = offm; m.off_grid = offg;
       offs += (long long)m.Kx * N;
       offm += (long long)m.M * m.Kx;
+      offg += (long long)m.M * m.M;
+      if (closure && b > 0 && N != hm[0].N)
+        return p->fail(SPADJ_ERR_UNSUPPORTED, "kolmogorov: the learned closure needs one resolution for the whole batch");
       hm.push_back(m);
       Lmax = std::max(Lmax, m.L); Mmax = std::max(Mmax, m.M); Nmax = std::max(Nmax, N); Kxmax = std::max(Kxmax, m.Kx);
     }
     state_size = offs;
     mix_size = offm;
+    grid_size = offg;
     // twiddle tables per resolution: WMx (M entries) then W2M (2M entries)
     std::vector<double2> ht;
     std::vector<size_t> toff;
@@ -633,12 +704,37 @@ struct Kol : EqImpl {
       SPADJ_CUDA_TRY(p, Fr[i].ensure(sb));
       SPADJ_CUDA_TRY(p, Yr[i].ensure(sb));
     }
-    SPADJ_CUDA_TRY(p, mixA.ensure(5 * mb));
-    SPADJ_CUDA_TRY(p, mixB.ensure(4 * mb));
+    SPADJ_CUDA_TRY(p, mixA.ensure(6 * mb));
+    SPADJ_CUDA_TRY(p, mixB.ensure(5 * mb));
+    if (closure) {
+      persistent = 0;  // the CNN needs whole-member grid phases between the row and column phases
+      const size_t gb = sizeof(double) * grid_size;
+      const size_t np = (size_t)cnn::n_params();
+      const size_t act = (size_t)grid_size * cnn::kHid;
+      SPADJ_CUDA_TRY(p, gridW.ensure(gb));
+      SPADJ_CUDA_TRY(p, gridG.ensure(gb));
+      SPADJ_CUDA_TRY(p, corr.ensure(gb));
+      SPADJ_CUDA_TRY(p, xq.ensure(sizeof(__nv_bfloat16) * grid_size));
+      for (int l = 0; l < 3; ++l) {
+        SPADJ_CUDA_TRY(p, hbuf[l].ensure(sizeof(__nv_bfloat16) * act));
+        SPADJ_CUDA_TRY(p, dact[l].ensure(sizeof(float) * act));
+      }
+      SPADJ_CUDA_TRY(p, dh.ensure(sizeof(float) * act));
+      SPADJ_CUDA_TRY(p, dz.ensure(sizeof(__nv_bfloat16) * act));
+      SPADJ_CUDA_TRY(p, pbuf.ensure(sizeof(double) * np));
+      SPADJ_CUDA_TRY(p, wq.ensure(sizeof(__nv_bfloat16) * np));
+      SPADJ_CUDA_TRY(p, bq.ensure(sizeof(float) * np));
+      SPADJ_CUDA_TRY(p, part.ensure(sizeof(float) * np * nmem));
+      SPADJ_CUDA_TRY(p, gp.ensure(sizeof(double) * np));
+      SPADJ_CUDA_TRY(p, cudaMemsetAsync(pbuf.ptr, 0, sizeof(double) * np, p->stream));
+      cnn::convert_kernel<<<64, 256, 0, p->stream>>>(pbuf.as<double>(), wq.as<__nv_bfloat16>(), bq.as<float>());
+      spadj_status st = check_launch(p, "closure convert");
+      if (st != SPADJ_OK) return st;
+    }
     SPADJ_CUDA_TRY(p, ctr.ensure(sizeof(int) * (2 * (size_t)nmem + 2)));
     SPADJ_CUDA_TRY(p, tmp.ensure(sb));
     // shared memory: max over tile kinds (B' needs 7 L + Kx, CA' needs 2 M + 2 N)
-    smem = sizeof(double2) * std::max<size_t>(7 * (size_t)Lmax + Kxmax, 2 * (size_t)Mmax + 2 * (size_t)Nmax);
+    smem = sizeof(double2) * std::max<size_t>(8 * (size_t)Lmax + Kxmax, 2 * (size_t)Mmax + 2 * (size_t)Nmax);
     SPADJ_CUDA_TRY(p, cudaFuncSetAttribute(kol_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     SPADJ_CUDA_TRY(p, cudaFuncSetAttribute(kol_phase, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     layout();
@@ -663,8 +759,11 @@ struct Kol : EqImpl {
     A.nCAtot = nCAtot(); A.nBtot = nBtot();
     A.forcing = forcing; A.nonlinear = nonlinear;
     for (int i = 0; i < 2; ++i) { A.Xr[i] = Xr[i].as<double2>(); A.Fr[i] = Fr[i].as<double2>(); A.Yr[i] = Yr[i].as<double2>(); }
-    for (int f = 0; f < 5; ++f) A.mixA[f] = mixA.as<double2>() + (size_t)f * mix_size;
-    for (int f = 0; f < 4; ++f) A.mixB[f] = mixB.as<double2>() + (size_t)f * mix_size;
+    for (int f = 0; f < 6; ++f) A.mixA[f] = mixA.as<double2>() + (size_t)f * mix_size;
+    for (int f = 0; f < 5; ++f) A.mixB[f] = mixB.as<double2>() + (size_t)f * mix_size;
+    A.closure = closure;
+    A.gridW = gridW.as<double>();
+    A.gridG = gridG.as<double>();
     A.state_size = state_size;
     int* c = ctr.as<int>();
     A.queue = c; A.err = c + 1; A.caDone = c + 2; A.bDone = c + 2 + nmem;
@@ -701,6 +800,10 @@ struct Kol : EqImpl {
       if (st + 1 < A.nstage) {
         kol_phase<<<A.nBtot, kKolThreads, smem, p->stream>>>(A, st, 0);
         if ((s = check_launch(p, "kolmogorov phase B")) != SPADJ_OK) return s;
+        if (closure) {
+          s = A.adjoint ? closure_backward(p, A) : closure_forward(p, A);
+          if (s != SPADJ_OK) return s;
+        }
       }
     }
     p->toc(t, KC_FUSED, work_flops(A));
@@ -758,6 +861,64 @@ struct Kol : EqImpl {
     if (s != SPADJ_OK) return s;
     return persistent ? check_err(p) : cudaStreamSynchronize(p->stream) == cudaSuccess ? SPADJ_OK
                                                                                        : p->fail(SPADJ_ERR_CUDA, "sync");
+  }
+
+  // ---- learned closure ---------------------------------------------------------------------
+  int cnn_grid(long long n) const { return (int)std::min<long long>((n + 255) / 256, 4096); }
+
+  spadj_status closure_forward(Problem* p, const KolArgs& A) {
+    const int M = hm[0].M, nb = nmem;
+    const long long P = (long long)M * M * nb;
+    cudaEvent_t t = p->tic();
+    cnn::quantize_kernel<<<cnn_grid(P), 256, 0, p->stream>>>(gridW.as<double>(), xq.as<__nv_bfloat16>(), (int)P);
+    const __nv_bfloat16* in = xq.as<__nv_bfloat16>();
+    for (int l = 0; l < cnn::kLayers; ++l) {
+      const int co = (l == cnn::kLayers - 1) ? 1 : cnn::kHid;
+      cnn::fwd_kernel<<<cnn_grid(P * co), 256, 0, p->stream>>>(
+          l, M, nb, in, wq.as<__nv_bfloat16>(), bq.as<float>(), l < 3 ? hbuf[l].as<__nv_bfloat16>() : nullptr, nullptr,
+          l == 3 ? corr.as<double>() : nullptr);
+      if (l < 3) in = hbuf[l].as<__nv_bfloat16>();
+    }
+    closure_rows_kernel<<<dim3(M, nb), kKolThreads, smem, p->stream>>>(A, corr.as<double>(), 0);
+    p->toc(t, KC_POINTWISE, 2.0 * P * (9.0 * 32 + 2 * 9.0 * 32 * 32 + 9.0 * 32));
+    return check_launch(p, "closure forward");
+  }
+
+  spadj_status closure_backward(Problem* p, const KolArgs& A) {
+    const int M = hm[0].M, nb = nmem, np = cnn::n_params();
+    const long long P = (long long)M * M * nb;
+    cudaEvent_t t = p->tic();
+    cnn::quantize_kernel<<<cnn_grid(P), 256, 0, p->stream>>>(gridW.as<double>(), xq.as<__nv_bfloat16>(), (int)P);
+    const __nv_bfloat16* ins[4] = {xq.as<__nv_bfloat16>(), hbuf[0].as<__nv_bfloat16>(), hbuf[1].as<__nv_bfloat16>(),
+                                   hbuf[2].as<__nv_bfloat16>()};
+    for (int l = 0; l < 3; ++l)
+      cnn::fwd_kernel<<<cnn_grid(P * cnn::kHid), 256, 0, p->stream>>>(l, M, nb, ins[l], wq.as<__nv_bfloat16>(),
+                                                                       bq.as<float>(), hbuf[l].as<__nv_bfloat16>(),
+                                                                       dact[l].as<float>(), nullptr);
+    for (int l = cnn::kLayers - 1; l >= 0; --l) {
+      const int co = (l == cnn::kLayers - 1) ? 1 : cnn::kHid, ci = (l == 0) ? 1 : cnn::kHid;
+      if (l == cnn::kLayers - 1)
+        cnn::dz_kernel<<<cnn_grid(P), 256, 0, p->stream>>>(P, nullptr, nullptr, gridG.as<double>(), dz.as<__nv_bfloat16>());
+      else
+        cnn::dz_kernel<<<cnn_grid(P * co), 256, 0, p->stream>>>(P * co, dh.as<float>(), dact[l].as<float>(), nullptr,
+                                                                 dz.as<__nv_bfloat16>());
+      cnn::wgrad_kernel<<<dim3(co * 10, nb), 256, 0, p->stream>>>(l, M, ins[l], dz.as<__nv_bfloat16>(), part.as<float>(), np);
+      cnn::dgrad_kernel<<<cnn_grid(P * ci), 256, 0, p->stream>>>(l, M, nb, dz.as<__nv_bfloat16>(), wq.as<__nv_bfloat16>(),
+                                                                  l > 0 ? dh.as<float>() : nullptr,
+                                                                  l == 0 ? corr.as<double>() : nullptr);
+    }
+    cnn::reduce_params_kernel<<<64, 256, 0, p->stream>>>(part.as<float>(), nb, np, gp.as<double>());
+    closure_rows_kernel<<<dim3(M, nb), kKolThreads, smem, p->stream>>>(A, corr.as<double>(), 1);
+    p->toc(t, KC_POINTWISE, 6.0 * P * (9.0 * 32 + 2 * 9.0 * 32 * 32 + 9.0 * 32));
+    return check_launch(p, "closure backward");
+  }
+
+  spadj_status set_params(Problem* p, const double* params) {
+    if (!closure) return p->fail(SPADJ_ERR_UNSUPPORTED, "set_params: the problem has no learned closure");
+    const size_t np = (size_t)cnn::n_params();
+    SPADJ_CUDA_TRY(p, cudaMemcpyAsync(pbuf.ptr, params, sizeof(double) * np, cudaMemcpyDeviceToDevice, p->stream));
+    cnn::convert_kernel<<<64, 256, 0, p->stream>>>(pbuf.as<double>(), wq.as<__nv_bfloat16>(), bq.as<float>());
+    return check_launch(p, "closure convert");
   }
 
   spadj_status transform(Problem* p, int, const double*, double*) override {
@@ -832,7 +993,7 @@ struct Kol : EqImpl {
   }
 
   spadj_status gradient(Problem* p, const double* x0, int n_steps, int objective_kind, const double*, int,
-                        double* J_host, double* grad, double*) override {
+                        double* J_host, double* grad, double* grad_p) override {
     if (objective_kind != SPADJ_OBJ_FOURDVAR) return p->fail(SPADJ_ERR_UNSUPPORTED, "kolmogorov: objective must be FOURDVAR");
     if (n_obs < 1) return p->fail(SPADJ_ERR_INVALID, "kolmogorov: call spadj_set_observations first");
     if (obs_steps_h.back() > n_steps) return p->fail(SPADJ_ERR_INVALID, "kolmogorov: observation step beyond n_steps");
@@ -852,7 +1013,13 @@ struct Kol : EqImpl {
     if ((s = check_launch(p, "kolmogorov 4dvar")) != SPADJ_OK) return s;
     std::vector<int> seed_at(n_steps + 1, -1);
     for (int i = 0; i < n_obs; ++i) seed_at[obs_steps_h[i]] = i;
+    if (closure) SPADJ_CUDA_TRY(p, cudaMemsetAsync(gp.ptr, 0, sizeof(double) * cnn::n_params(), p->stream));
     if ((s = run_adjoint(p, n_steps, trajbuf.as<double2>(), seed_at, seedbuf.as<double2>(), grad)) != SPADJ_OK) return s;
+    if (grad_p) {
+      if (!closure) return p->fail(SPADJ_ERR_INVALID, "gradient: grad_p requested but the problem has no parameters");
+      SPADJ_CUDA_TRY(p, cudaMemcpyAsync(grad_p, gp.ptr, sizeof(double) * cnn::n_params(), cudaMemcpyDeviceToDevice,
+                                        p->stream));
+    }
     if (J_host) {
       SPADJ_CUDA_TRY(p, cudaMemcpyAsync(J_host, Jd.ptr, sizeof(double) * nmem, cudaMemcpyDeviceToHost, p->stream));
       SPADJ_CUDA_TRY(p, cudaStreamSynchronize(p->stream));
@@ -864,7 +1031,10 @@ struct Kol : EqImpl {
 
   spadj_status set_option(Problem* p, int option, int value) {
     switch (option) {
-      case 0: persistent = value ? 1 : 0; return SPADJ_OK;
+      case 0:
+        if (value && closure) return p->fail(SPADJ_ERR_UNSUPPORTED, "set_option: the closure runs with per-phase launches");
+        persistent = value ? 1 : 0;
+        return SPADJ_OK;
       case 1:
         if (value < 1 || value > 64) return p->fail(SPADJ_ERR_INVALID, "set_option: column tile must be 1..64");
         CW = value; grid_persistent = 0; return sync_members(p);
@@ -920,6 +1090,9 @@ struct Kol : EqImpl {
   }
 
   ~Kol() override {
+    for (DevBuf* b : {&gridW, &gridG, &corr, &xq, &hbuf[0], &hbuf[1], &hbuf[2], &dact[0], &dact[1], &dact[2], &dh, &dz,
+                      &pbuf, &wq, &bq, &part, &gp})
+      b->release();
     for (DevBuf* b : {&dmem, &tables, &Xr[0], &Xr[1], &Fr[0], &Fr[1], &Yr[0], &Yr[1], &mixA, &mixB, &ctr, &trajbuf,
                       &seedbuf, &seedmap, &obsbuf, &obsteps, &partial, &Jd, &tmp})
       b->release();
@@ -948,6 +1121,12 @@ spadj_status kol_set_option(EqImpl* impl, Problem* p, int option, int value) {
   Kol* k = dynamic_cast<Kol*>(impl);
   if (!k) return p->fail(SPADJ_ERR_UNSUPPORTED, "set_option: only defined for the Kolmogorov batch");
   return k->set_option(p, option, value);
+}
+
+spadj_status kol_set_params(EqImpl* impl, Problem* p, const double* params) {
+  Kol* k = dynamic_cast<Kol*>(impl);
+  if (!k) return p->fail(SPADJ_ERR_UNSUPPORTED, "set_params: only defined for the Kolmogorov batch with a closure");
+  return k->set_params(p, params);
 }
 
 spadj_status kol_autotune(EqImpl* impl, Problem* p) {

@@ -146,6 +146,7 @@ EqImpl* make_kolmogorov(Problem* p, spadj_status* st);
 spadj_status kol_set_observations(EqImpl* impl, Problem* p, int n, const int* steps, const double* obs, int kmax);
 spadj_status kol_set_option(EqImpl* impl, Problem* p, int option, int value);
 spadj_status kol_autotune(EqImpl* impl, Problem* p);
+spadj_status kol_set_params(EqImpl* impl, Problem* p, const double* params);
 spadj_status rb_transform_noalloc(EqImpl* impl, Problem* p, int kind, const double* in, double* out);
 
 }  // namespace spadj

@@ -44,7 +44,8 @@ class SpadjError(RuntimeError):
 class spadj_desc(ctypes.Structure):
     _fields_ = [("eq", ctypes.c_int), ("scheme", ctypes.c_int), ("n", ctypes.c_int * 3),
                 ("length", ctypes.c_double * 3), ("params", ctypes.c_double * 4), ("dt", ctypes.c_double),
-                ("batch", ctypes.c_int), ("nonlinear", ctypes.c_int), ("batch_n", ctypes.POINTER(ctypes.c_int))]
+                ("batch", ctypes.c_int), ("nonlinear", ctypes.c_int), ("batch_n", ctypes.POINTER(ctypes.c_int)),
+                ("closure", ctypes.c_int)]
 
 
 _lib = None
@@ -63,6 +64,7 @@ _SIGS = {
     "spadj_set_observations": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, ctypes.c_int]),
     "spadj_set_option": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
     "spadj_autotune": (ctypes.c_int, [_vp]),
+    "spadj_set_params": (ctypes.c_int, [_vp, _vp]),
     "spadj_checkpoint_schedule": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "spadj_forward": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp]),
     "spadj_tangent": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp]),
@@ -128,7 +130,8 @@ CK_ADVANCE, CK_STORE, CK_RESTORE, CK_ADJOINT, CK_FREE, CK_OBJECTIVE = range(6)
 class Problem:
     """Owns one spadj_problem; methods take torch CUDA tensors."""
 
-    def __init__(self, eq, scheme, n, length, params, dt, batch=1, nonlinear=True, stream=None, batch_n=None):
+    def __init__(self, eq, scheme, n, length, params, dt, batch=1, nonlinear=True, stream=None, batch_n=None,
+                 closure=False):
         import torch
         d = spadj_desc()
         d.eq, d.scheme = eq, scheme
@@ -139,6 +142,7 @@ class Problem:
         for i, v in enumerate(list(params)[:4]):
             d.params[i] = float(v)
         d.dt, d.batch, d.nonlinear = float(dt), int(batch), int(bool(nonlinear))
+        d.closure = int(bool(closure))
         if batch_n is not None:
             self._batch_n = (ctypes.c_int * len(batch_n))(*[int(v) for v in batch_n])
             d.batch_n = ctypes.cast(self._batch_n, ctypes.POINTER(ctypes.c_int))
@@ -225,9 +229,10 @@ class Problem:
         n = self.state_len(0)
         J = np.zeros(self.desc.batch, dtype=np.float64) if want_J else None
         jp = J.ctypes.data_as(ctypes.c_void_p) if want_J else None
+        gp = None if grad_p is None else _ptr(_as_f64(grad_p, self.state_len(2), "grad_p"))
         _chk(self.h, lib().spadj_gradient(self.h, _ptr(_as_f64(x0, n, "x0")), n_steps, objective,
                                            _ptr(obj_data), ckpt_slots, jp,
-                                           _ptr(_as_f64(grad_x0, n, "grad_x0")), _ptr(grad_p)))
+                                           _ptr(_as_f64(grad_x0, n, "grad_x0")), gp))
         return J
 
     def set_observations(self, obs_steps, obs, kmax):
@@ -235,6 +240,9 @@ class Problem:
         steps = (ctypes.c_int * len(obs_steps))(*[int(v) for v in obs_steps])
         _chk(self.h, lib().spadj_set_observations(self.h, len(obs_steps), steps,
                                                    _ptr(_as_f64(obs, n * len(obs_steps), "obs")), int(kmax)))
+
+    def set_params(self, params):
+        _chk(self.h, lib().spadj_set_params(self.h, _ptr(_as_f64(params, self.state_len(2), "params"))))
 
     def set_option(self, option, value):
         _chk(self.h, lib().spadj_set_option(self.h, int(option), int(value)))
