@@ -1,0 +1,107 @@
+"""Training of the learned closure through the coarse adjoint (argument marshalling and the
+optimiser only; every solve, transform, CNN pass and gradient runs in libspadj.so).
+
+Fine trajectories come from the library's own Kolmogorov solver at the fine resolution;
+the training loss over an unrolled window of coarse steps is the 4D-Var misfit
+sum_m 1/2 ||R(w_fine(t_m)) - w_coarse(t_m; p)||^2, R the spectral truncation to the coarse
+grid, and its gradient with respect to the CNN parameters p comes from spadj_gradient's
+adjoint sweep (eq. 6 with p entering F).  Adam updates p.
+"""
+import numpy as np
+import torch
+
+from . import spadj
+
+
+def restrict_index(Nf, Nc):
+    """Flat indices into a fine member [Nf/2][Nf] of the coarse coefficients [Nc/2][Nc]
+    (kx < Nc/2, |ky| < Nc/2); the coarse Nyquist row maps to -1 (held at zero)."""
+    Kc = Nc // 2
+    ky = np.fft.fftfreq(Nc, 1.0 / Nc).astype(int)
+    jf = np.where(ky >= 0, ky, Nf + ky)
+    idx = (np.arange(Kc)[:, None] * Nf + jf[None, :]).astype(np.int64)
+    idx[:, Nc // 2] = -1
+    return idx.ravel()
+
+
+def restrict(fine, nmem, Nf, Nc):
+    """fine [..., nmem * Nf/2 * Nf] (complex, device) -> [..., nmem * Nc/2 * Nc]."""
+    idx = torch.from_numpy(restrict_index(Nf, Nc)).to(fine.device)
+    lead = fine.shape[:-1]
+    f = fine.reshape(lead + (nmem, (Nf // 2) * Nf))
+    safe = torch.clamp(idx, min=0)
+    out = f[..., safe] * (idx >= 0).to(fine.dtype)
+    return out.reshape(lead + (nmem * (Nc // 2) * Nc,))
+
+
+def fine_snapshots(x0_fine, nmem, Nf, Re, dt_f, ratio, ncoarse):
+    """Fine trajectories from the library's solver; states every `ratio` fine steps."""
+    p = spadj.Problem(spadj.SPADJ_KOLMOGOROV2D, spadj.SPADJ_SBDF2, [Nf], [2 * np.pi], [Re, 0.0], dt_f, batch=nmem)
+    nf = ratio * ncoarse
+    traj = torch.empty((nf + 1,) + tuple(x0_fine.shape), dtype=x0_fine.dtype, device=x0_fine.device)
+    p.forward(nf, x0_fine, traj[-1], traj)
+    snaps = traj[::ratio].clone()
+    del traj
+    p.close()
+    return snaps  # [ncoarse + 1][state]
+
+
+class Adam:
+    def __init__(self, n, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8, device="cuda"):
+        self.m = torch.zeros(n, dtype=torch.float64, device=device)
+        self.v = torch.zeros_like(self.m)
+        self.t = 0
+        self.lr, self.b1, self.b2, self.eps = lr, b1, b2, eps
+
+    def step(self, p, g):
+        self.t += 1
+        self.m.mul_(self.b1).add_(g, alpha=1 - self.b1)
+        self.v.mul_(self.b2).addcmul_(g, g, value=1 - self.b2)
+        mh = self.m / (1 - self.b1 ** self.t)
+        vh = self.v / (1 - self.b2 ** self.t)
+        p.sub_(self.lr * mh / (vh.sqrt() + self.eps))
+
+
+def coarse_problem(nmem, Nc, Re, dt_c):
+    return spadj.Problem(spadj.SPADJ_KOLMOGOROV2D, spadj.SPADJ_SBDF2, [Nc], [2 * np.pi], [Re, 0.0], dt_c, batch=nmem,
+                         closure=True)
+
+
+def train(params, coarse_snaps, nmem, Nc, Re, dt_c, iters, lr=1e-3, log=None):
+    """Adam on the closure parameters; coarse_snaps [ncoarse + 1][state] (restricted fine states,
+    the first one is the coarse initial condition).  Returns the per-iteration losses."""
+    nco = coarse_snaps.shape[0] - 1
+    p = coarse_problem(nmem, Nc, Re, dt_c)
+    steps = list(range(1, nco + 1))
+    p.set_observations(steps, coarse_snaps[1:].contiguous(), Nc // 2 - 1)
+    opt = Adam(params.numel(), lr=lr, device=params.device)
+    g = torch.empty_like(coarse_snaps[0])
+    gp = torch.empty_like(params)
+    losses = []
+    for it in range(iters):
+        p.set_params(params)
+        J = p.gradient(coarse_snaps[0].contiguous(), nco, g, objective=spadj.SPADJ_OBJ_FOURDVAR, grad_p=gp)
+        losses.append(float(np.sum(J)))
+        opt.step(params, gp)
+        if log is not None and it % 10 == 0:
+            log(it, losses[-1])
+    p.close()
+    return losses
+
+
+def rollout_errors(params, coarse_snaps, nmem, Nc, Re, dt_c, at_steps):
+    """Relative coefficient-space errors ||w_c(t) - R(w_f(t))|| / ||R(w_f(t))|| per member at the
+    given coarse steps, for the closure with `params` (zero parameters = plain coarse solver)."""
+    nco = max(at_steps)
+    p = coarse_problem(nmem, Nc, Re, dt_c)
+    p.set_params(params)
+    traj = torch.empty((nco + 1,) + tuple(coarse_snaps[0].shape), dtype=coarse_snaps.dtype, device=coarse_snaps.device)
+    p.forward(nco, coarse_snaps[0].contiguous(), traj[-1], traj)
+    out = {}
+    K = (Nc // 2) * Nc
+    for s in at_steps:
+        d = (traj[s] - coarse_snaps[s]).reshape(nmem, K)
+        r = coarse_snaps[s].reshape(nmem, K)
+        out[s] = (d.abs().pow(2).sum(1).sqrt() / r.abs().pow(2).sum(1).sqrt()).cpu().numpy()
+    p.close()
+    return out

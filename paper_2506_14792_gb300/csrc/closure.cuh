@@ -179,3 +179,204 @@ __global__ void reduce_params_kernel(const float* __restrict__ part, int nb, int
 
 }  // namespace cnn
 }  // namespace spadj
+
+namespace spadj {
+namespace cnn {
+
+// ---- tensor-core kernels for the 32 -> 32 layers (BF16 mma.sync m16n8k16, FP32 accumulate) ----
+//
+// Implicit GEMM per member: rows = pixels, columns = 32 output channels, reduction = 9 taps x 32
+// input channels (18 k-steps of 16).  A CTA of 4 warps owns 64 consecutive pixels; warp w owns
+// pixels 16w..16w+15 and all four 8-column tiles.  The forward pass (dir = +1) gathers
+// in[pixel shifted by (a - 1, b - 1)] with weights W[o][a][b][c]; the input gradient (dir = -1)
+// gathers dz[pixel shifted by (1 - a, 1 - b)] with the transposed weights W[c][a][b][o].
+// Fragment layout of m16n8k16 (bf16): A rows g = lane/4 (+8), k pairs 2(lane%4) (+8);
+// B k pairs 2(lane%4) (+8), column g; C rows g (+8), column pairs 2(lane%4).
+
+__device__ __forceinline__ void mma_bf16(float* c, const unsigned* a, const unsigned* b) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+__device__ __forceinline__ unsigned pack2(__nv_bfloat16 lo, __nv_bfloat16 hi) {
+  return (unsigned)__bfloat16_as_ushort(lo) | ((unsigned)__bfloat16_as_ushort(hi) << 16);
+}
+
+// out[p][n] = sum_{a,b,c} Wt[n][a][b][c] * in[shift(p, a, b)][c]  (+ bias, tanh for dir = +1)
+// mode 0: forward hidden layer (writes h, dact); mode 1: input gradient (writes din FP32)
+__global__ void __launch_bounds__(128) conv32_mma_kernel(int l, int M, int nb, int mode,
+                                                         const __nv_bfloat16* __restrict__ in,
+                                                         const __nv_bfloat16* __restrict__ wq,
+                                                         const float* __restrict__ bq,
+                                                         __nv_bfloat16* __restrict__ h, float* __restrict__ dact,
+                                                         float* __restrict__ din) {
+  __shared__ __nv_bfloat16 sw[32 * 9 * 32];  // weights as [n][tap][k] (k = reduction channel)
+  const __nv_bfloat16* W = wq + w_off(l);
+  // forward: Wt[n=o][tap][k=c] = W[o][a][b][c]; gradient: Wt[n=c][tap][k=o] = W[o][a][b][c]
+  for (int i = threadIdx.x; i < 32 * 9 * 32; i += blockDim.x) {
+    const int n = i / (9 * 32), tap = (i / 32) % 9, k = i % 32;
+    sw[i] = mode == 0 ? W[(n * 9 + tap) * 32 + k] : W[(k * 9 + tap) * 32 + n];
+  }
+  __syncthreads();
+  const long long P = (long long)M * M;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int g = lane / 4, t4 = lane % 4;
+  const long long tiles = (P * nb + 63) / 64;
+  for (long long tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    const long long p0 = tile * 64 + warp * 16;
+    // the two pixel rows of this lane's A fragment
+    long long pr[2];
+    int ys[2], xs[2];
+    long long mbr[2];
+    bool ok[2];
+    for (int r = 0; r < 2; ++r) {
+      pr[r] = p0 + g + 8 * r;
+      ok[r] = pr[r] < P * nb;
+      const long long pc = ok[r] ? pr[r] : 0;
+      mbr[r] = pc / P;
+      const int pp = (int)(pc % P);
+      ys[r] = pp / M;
+      xs[r] = pp % M;
+    }
+    float acc[4][4];
+    for (int nt = 0; nt < 4; ++nt)
+      for (int q = 0; q < 4; ++q) acc[nt][q] = 0.0f;
+    for (int tap = 0; tap < 9; ++tap) {
+      const int a = tap / 3, b = tap % 3;
+      const int dx = mode == 0 ? a - 1 : 1 - a, dy = mode == 0 ? b - 1 : 1 - b;
+      const __nv_bfloat16* src[2];
+      for (int r = 0; r < 2; ++r) {
+        const int xx = (xs[r] + dx + M) % M, yy = (ys[r] + dy + M) % M;
+        src[r] = in + (mbr[r] * P + (long long)yy * M + xx) * 32;
+      }
+      for (int kh = 0; kh < 2; ++kh) {  // 16-channel halves of the 32 input channels
+        const int k0 = kh * 16 + 2 * t4;
+        unsigned af[4];
+        const __nv_bfloat16 z = __float2bfloat16_rn(0.0f);
+        af[0] = ok[0] ? pack2(src[0][k0], src[0][k0 + 1]) : pack2(z, z);
+        af[1] = ok[1] ? pack2(src[1][k0], src[1][k0 + 1]) : pack2(z, z);
+        af[2] = ok[0] ? pack2(src[0][k0 + 8], src[0][k0 + 9]) : pack2(z, z);
+        af[3] = ok[1] ? pack2(src[1][k0 + 8], src[1][k0 + 9]) : pack2(z, z);
+        for (int nt = 0; nt < 4; ++nt) {
+          const __nv_bfloat16* wr = sw + ((nt * 8 + g) * 9 + tap) * 32;
+          unsigned bf[2] = {pack2(wr[k0], wr[k0 + 1]), pack2(wr[k0 + 8], wr[k0 + 9])};
+          mma_bf16(acc[nt], af, bf);
+        }
+      }
+    }
+    const float* B = bq + w_off(l) + 32 * 32 * 9;
+    for (int nt = 0; nt < 4; ++nt)
+      for (int q = 0; q < 4; ++q) {
+        const int r = q / 2;
+        if (!ok[r]) continue;
+        const int n = nt * 8 + 2 * t4 + (q % 2);
+        const long long idx = pr[r] * 32 + n;
+        if (mode == 0) {
+          const float th = tanhf(acc[nt][q] + B[n]);
+          h[idx] = __float2bfloat16_rn(th);
+          if (dact) dact[idx] = 1.0f - th * th;
+        } else {
+          din[idx] = acc[nt][q];
+        }
+      }
+  }
+}
+
+// weight gradient of a 32 -> 32 layer: dW[o][c][a][b] = sum_p dz[p][o] in[shift(p, a, b)][c].
+// GEMM per tap: rows o (32 = 2 m-tiles), columns c (32 = 4 n-tiles), reduction over pixels.
+// CTA = (member, tap, pixel chunk); its 4 warps split the chunk; partial sums reduced in smem and
+// written to part[member][chunk]... summed over chunks in a fixed order by wgrad32_finish.
+__global__ void __launch_bounds__(128) wgrad32_mma_kernel(int l, int M, const __nv_bfloat16* __restrict__ in,
+                                                          const __nv_bfloat16* __restrict__ dz,
+                                                          float* __restrict__ chunkbuf, int nchunk) {
+  const long long P = (long long)M * M;
+  const int tap = blockIdx.y, mb = blockIdx.z, chunk = blockIdx.x;
+  const int a = tap / 3, b = tap % 3;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int g = lane / 4, t4 = lane % 4;
+  const long long per = (P + nchunk - 1) / nchunk;
+  const long long pbeg = chunk * per, pend = min(P, pbeg + per);
+  float acc[2][4][4];
+  for (int mt = 0; mt < 2; ++mt)
+    for (int nt = 0; nt < 4; ++nt)
+      for (int q = 0; q < 4; ++q) acc[mt][nt][q] = 0.0f;
+  const __nv_bfloat16 z = __float2bfloat16_rn(0.0f);
+  // k-steps of 16 pixels, interleaved over the 4 warps
+  for (long long k0 = pbeg + warp * 16; k0 < pend; k0 += 64) {
+    // pixels of this lane's k pairs: k0 + 2 t4 + {0, 1} and + 8
+    long long pk[4] = {k0 + 2 * t4, k0 + 2 * t4 + 1, k0 + 2 * t4 + 8, k0 + 2 * t4 + 9};
+    const __nv_bfloat16* sh[4];
+    bool okk[4];
+    for (int i = 0; i < 4; ++i) {
+      okk[i] = pk[i] < pend;
+      const long long pc = okk[i] ? pk[i] : pbeg;
+      const int y = (int)(pc / M), x = (int)(pc % M);
+      const int xx = (x + a - 1 + M) % M, yy = (y + b - 1 + M) % M;
+      sh[i] = in + ((long long)mb * P + (long long)yy * M + xx) * 32;
+    }
+    const __nv_bfloat16* dzr[4];
+    for (int i = 0; i < 4; ++i) dzr[i] = dz + ((long long)mb * P + (okk[i] ? pk[i] : pbeg)) * 32;
+    for (int mt = 0; mt < 2; ++mt) {
+      // A[o][p] = dz[p][o]: rows o = 16 mt + g (+8), k pairs = pixels
+      const int o0 = mt * 16 + g, o1 = o0 + 8;
+      unsigned af[4];
+      af[0] = pack2(okk[0] ? dzr[0][o0] : z, okk[1] ? dzr[1][o0] : z);
+      af[1] = pack2(okk[0] ? dzr[0][o1] : z, okk[1] ? dzr[1][o1] : z);
+      af[2] = pack2(okk[2] ? dzr[2][o0] : z, okk[3] ? dzr[3][o0] : z);
+      af[3] = pack2(okk[2] ? dzr[2][o1] : z, okk[3] ? dzr[3][o1] : z);
+      for (int nt = 0; nt < 4; ++nt) {
+        // B[p][c] = in[shift(p)][c]: column c = 8 nt + g, k pairs = pixels
+        const int c = nt * 8 + g;
+        unsigned bf[2] = {pack2(okk[0] ? sh[0][c] : z, okk[1] ? sh[1][c] : z),
+                          pack2(okk[2] ? sh[2][c] : z, okk[3] ? sh[3][c] : z)};
+        mma_bf16(acc[mt][nt], af, bf);
+      }
+    }
+  }
+  // reduce the 4 warps in smem (fixed order) and write the chunk's 32 x 32 block
+  __shared__ float red[4][32 * 32];
+  for (int mt = 0; mt < 2; ++mt)
+    for (int nt = 0; nt < 4; ++nt)
+      for (int q = 0; q < 4; ++q) {
+        const int o = mt * 16 + g + 8 * (q / 2), c = nt * 8 + 2 * t4 + (q % 2);
+        red[warp][o * 32 + c] = acc[mt][nt][q];
+      }
+  __syncthreads();
+  float* dst = chunkbuf + (((long long)mb * 9 + tap) * nchunk + chunk) * 1024;
+  for (int i = threadIdx.x; i < 1024; i += blockDim.x) dst[i] = ((red[0][i] + red[1][i]) + red[2][i]) + red[3][i];
+}
+
+// sum the chunks of wgrad32_mma_kernel in order into part[mb][w_off(l) + flat W index]
+__global__ void wgrad32_finish_kernel(int l, const float* __restrict__ chunkbuf, int nchunk, float* __restrict__ part,
+                                      int npar) {
+  const int mb = blockIdx.y;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 9 * 1024; i += gridDim.x * blockDim.x) {
+    const int tap = i / 1024, oc = i % 1024, o = oc / 32, c = oc % 32;
+    const float* src = chunkbuf + (((long long)mb * 9 + tap) * nchunk) * 1024 + oc;
+    float s = 0.0f;
+    for (int k = 0; k < nchunk; ++k) s += src[(long long)k * 1024];
+    part[(long long)mb * npar + w_off(l) + (o * 32 + c) * 9 + tap] = s;
+  }
+}
+
+// bias gradient of a 32-channel layer (the weights are handled by the tensor-core kernels)
+__global__ void bgrad32_kernel(int l, int M, const __nv_bfloat16* __restrict__ dz, float* __restrict__ part, int npar) {
+  const long long P = (long long)M * M;
+  const int mb = blockIdx.y, o = blockIdx.x;
+  __shared__ float red[256];
+  float acc = 0.0f;
+  for (long long p = threadIdx.x; p < P; p += blockDim.x) acc += __bfloat162float(dz[((long long)mb * P + p) * 32 + o]);
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float s = 0.0f;
+    for (int k = 0; k < (int)blockDim.x; ++k) s += red[k];
+    part[(long long)mb * npar + w_off(l) + 32 * 32 * 9 + o] = s;
+  }
+}
+
+}  // namespace cnn
+}  // namespace spadj

@@ -596,7 +596,8 @@ struct Kol : EqImpl {
   int nmem = 0;
   long long state_size = 0, mix_size = 0, grid_size = 0;
   int closure = 0;
-  DevBuf gridW, gridG, corr, xq, hbuf[3], dact[3], dh, dz, pbuf, wq, bq, part, gp;
+  DevBuf gridW, gridG, corr, xq, hbuf[3], dact[3], dh, dz, pbuf, wq, bq, part, gp, chunkbuf;
+  static constexpr int kWgradChunks = 8;
   int Lmax = 0, Mmax = 0, Nmax = 0, Kxmax = 0;
   double Re = 100.0, dt = 0;
   int forcing = 1, nonlinear = 1;
@@ -726,6 +727,7 @@ struct Kol : EqImpl {
       SPADJ_CUDA_TRY(p, bq.ensure(sizeof(float) * np));
       SPADJ_CUDA_TRY(p, part.ensure(sizeof(float) * np * nmem));
       SPADJ_CUDA_TRY(p, gp.ensure(sizeof(double) * np));
+      SPADJ_CUDA_TRY(p, chunkbuf.ensure(sizeof(float) * (size_t)nmem * 9 * kWgradChunks * 1024));
       SPADJ_CUDA_TRY(p, cudaMemsetAsync(pbuf.ptr, 0, sizeof(double) * np, p->stream));
       cnn::convert_kernel<<<64, 256, 0, p->stream>>>(pbuf.as<double>(), wq.as<__nv_bfloat16>(), bq.as<float>());
       spadj_status st = check_launch(p, "closure convert");
@@ -865,6 +867,7 @@ struct Kol : EqImpl {
 
   // ---- learned closure ---------------------------------------------------------------------
   int cnn_grid(long long n) const { return (int)std::min<long long>((n + 255) / 256, 4096); }
+  int mma_grid(long long npix) const { return (int)std::min<long long>((npix + 63) / 64, 8192); }
 
   spadj_status closure_forward(Problem* p, const KolArgs& A) {
     const int M = hm[0].M, nb = nmem;
@@ -874,9 +877,13 @@ struct Kol : EqImpl {
     const __nv_bfloat16* in = xq.as<__nv_bfloat16>();
     for (int l = 0; l < cnn::kLayers; ++l) {
       const int co = (l == cnn::kLayers - 1) ? 1 : cnn::kHid;
-      cnn::fwd_kernel<<<cnn_grid(P * co), 256, 0, p->stream>>>(
-          l, M, nb, in, wq.as<__nv_bfloat16>(), bq.as<float>(), l < 3 ? hbuf[l].as<__nv_bfloat16>() : nullptr, nullptr,
-          l == 3 ? corr.as<double>() : nullptr);
+      if (l == 1 || l == 2)  // 32 -> 32: tensor cores
+        cnn::conv32_mma_kernel<<<mma_grid(P), 128, 0, p->stream>>>(l, M, nb, 0, in, wq.as<__nv_bfloat16>(), bq.as<float>(),
+                                                                    hbuf[l].as<__nv_bfloat16>(), nullptr, nullptr);
+      else
+        cnn::fwd_kernel<<<cnn_grid(P * co), 256, 0, p->stream>>>(
+            l, M, nb, in, wq.as<__nv_bfloat16>(), bq.as<float>(), l < 3 ? hbuf[l].as<__nv_bfloat16>() : nullptr, nullptr,
+            l == 3 ? corr.as<double>() : nullptr);
       if (l < 3) in = hbuf[l].as<__nv_bfloat16>();
     }
     closure_rows_kernel<<<dim3(M, nb), kKolThreads, smem, p->stream>>>(A, corr.as<double>(), 0);
@@ -891,10 +898,16 @@ struct Kol : EqImpl {
     cnn::quantize_kernel<<<cnn_grid(P), 256, 0, p->stream>>>(gridW.as<double>(), xq.as<__nv_bfloat16>(), (int)P);
     const __nv_bfloat16* ins[4] = {xq.as<__nv_bfloat16>(), hbuf[0].as<__nv_bfloat16>(), hbuf[1].as<__nv_bfloat16>(),
                                    hbuf[2].as<__nv_bfloat16>()};
-    for (int l = 0; l < 3; ++l)
-      cnn::fwd_kernel<<<cnn_grid(P * cnn::kHid), 256, 0, p->stream>>>(l, M, nb, ins[l], wq.as<__nv_bfloat16>(),
-                                                                       bq.as<float>(), hbuf[l].as<__nv_bfloat16>(),
-                                                                       dact[l].as<float>(), nullptr);
+    for (int l = 0; l < 3; ++l) {
+      if (l == 0)
+        cnn::fwd_kernel<<<cnn_grid(P * cnn::kHid), 256, 0, p->stream>>>(l, M, nb, ins[l], wq.as<__nv_bfloat16>(),
+                                                                         bq.as<float>(), hbuf[l].as<__nv_bfloat16>(),
+                                                                         dact[l].as<float>(), nullptr);
+      else
+        cnn::conv32_mma_kernel<<<mma_grid(P), 128, 0, p->stream>>>(l, M, nb, 0, ins[l], wq.as<__nv_bfloat16>(),
+                                                                    bq.as<float>(), hbuf[l].as<__nv_bfloat16>(),
+                                                                    dact[l].as<float>(), nullptr);
+    }
     for (int l = cnn::kLayers - 1; l >= 0; --l) {
       const int co = (l == cnn::kLayers - 1) ? 1 : cnn::kHid, ci = (l == 0) ? 1 : cnn::kHid;
       if (l == cnn::kLayers - 1)
@@ -902,10 +915,22 @@ struct Kol : EqImpl {
       else
         cnn::dz_kernel<<<cnn_grid(P * co), 256, 0, p->stream>>>(P * co, dh.as<float>(), dact[l].as<float>(), nullptr,
                                                                  dz.as<__nv_bfloat16>());
-      cnn::wgrad_kernel<<<dim3(co * 10, nb), 256, 0, p->stream>>>(l, M, ins[l], dz.as<__nv_bfloat16>(), part.as<float>(), np);
-      cnn::dgrad_kernel<<<cnn_grid(P * ci), 256, 0, p->stream>>>(l, M, nb, dz.as<__nv_bfloat16>(), wq.as<__nv_bfloat16>(),
-                                                                  l > 0 ? dh.as<float>() : nullptr,
-                                                                  l == 0 ? corr.as<double>() : nullptr);
+      if (l == 1 || l == 2) {  // 32 -> 32: tensor cores
+        cnn::wgrad32_mma_kernel<<<dim3(kWgradChunks, 9, nb), 128, 0, p->stream>>>(l, M, ins[l], dz.as<__nv_bfloat16>(),
+                                                                                 chunkbuf.as<float>(), kWgradChunks);
+        cnn::wgrad32_finish_kernel<<<dim3(36, nb), 256, 0, p->stream>>>(l, chunkbuf.as<float>(), kWgradChunks,
+                                                                        part.as<float>(), np);
+        cnn::bgrad32_kernel<<<dim3(32, nb), 256, 0, p->stream>>>(l, M, dz.as<__nv_bfloat16>(), part.as<float>(), np);
+        cnn::conv32_mma_kernel<<<mma_grid(P), 128, 0, p->stream>>>(l, M, nb, 1, dz.as<__nv_bfloat16>(),
+                                                                    wq.as<__nv_bfloat16>(), bq.as<float>(), nullptr,
+                                                                    nullptr, dh.as<float>());
+      } else {
+        cnn::wgrad_kernel<<<dim3(co * 10, nb), 256, 0, p->stream>>>(l, M, ins[l], dz.as<__nv_bfloat16>(), part.as<float>(),
+                                                                    np);
+        cnn::dgrad_kernel<<<cnn_grid(P * ci), 256, 0, p->stream>>>(l, M, nb, dz.as<__nv_bfloat16>(),
+                                                                    wq.as<__nv_bfloat16>(), l > 0 ? dh.as<float>() : nullptr,
+                                                                    l == 0 ? corr.as<double>() : nullptr);
+      }
     }
     cnn::reduce_params_kernel<<<64, 256, 0, p->stream>>>(part.as<float>(), nb, np, gp.as<double>());
     closure_rows_kernel<<<dim3(M, nb), kKolThreads, smem, p->stream>>>(A, corr.as<double>(), 1);
@@ -1091,7 +1116,7 @@ struct Kol : EqImpl {
 
   ~Kol() override {
     for (DevBuf* b : {&gridW, &gridG, &corr, &xq, &hbuf[0], &hbuf[1], &hbuf[2], &dact[0], &dact[1], &dact[2], &dh, &dz,
-                      &pbuf, &wq, &bq, &part, &gp})
+                      &pbuf, &wq, &bq, &part, &gp, &chunkbuf})
       b->release();
     for (DevBuf* b : {&dmem, &tables, &Xr[0], &Xr[1], &Fr[0], &Fr[1], &Yr[0], &Yr[1], &mixA, &mixB, &ctr, &trajbuf,
                       &seedbuf, &seedmap, &obsbuf, &obsteps, &partial, &Jd, &tmp})
