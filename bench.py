@@ -320,6 +320,22 @@ class ClockSampler:
 # arms
 # ---------------------------------------------------------------------------------------
 
+def reduce_max(x, device=None):
+    """Max of a float over all ranks (identity without torch.distributed); gloo or nccl."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device if device is not None else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_rank_step, steps, world, ms_max):
+    """Whole-job throughput: the units every rank processed over the slowest rank's time."""
+    return units_per_rank_step * steps * world / (ms_max / 1e3)
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -397,13 +413,9 @@ def run_gpu(args, wl):
     barrier()
     rep = wl.p.timing_report()
     wl.p.timing(False)
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = reduce_max(ms, dev)
     units = wl.units_per_step() * args.steps * ws
-    value = units / (ms / 1e3)
+    value = job_value(wl.units_per_step(), args.steps, ws, ms)
 
     # end to end through the public API with host buffers
     for _ in range(max(1, args.warmup // 2)):
@@ -416,12 +428,7 @@ def run_gpu(args, wl):
         wl.e2e_step()
     e1.record(stream)
     barrier()
-    e2e_ms = e0.elapsed_time(e1)
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = reduce_max(e0.elapsed_time(e1), dev)
     bi, bo = wl.e2e_bytes()
 
     # roofline of the dominant kernel class (FP64 ALU bound on GB300)
