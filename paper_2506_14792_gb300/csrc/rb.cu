@@ -219,11 +219,13 @@ struct RB : EqImpl {
   }
   XJob xc2r(const double2* in, int cmul, double w0, double w, double* out) {
     XJob j{};
+    j.prod = -1;
     j.dir = 0; j.cin = in; j.cmul = cmul; j.w0 = w0; j.w = w; j.rout = out;
     return j;
   }
   XJob xr2c(const double* in0, int mul0, const double* in1, int mul1, double s0, double s, double2* out) {
     XJob j{};
+    j.prod = -1;
     j.dir = 1; j.rin[0] = in0; j.rmul[0] = mul0; j.nr = 1;
     if (in1) { j.rin[1] = in1; j.rmul[1] = mul1; j.nr = 2; }
     j.s0 = s0; j.s = s; j.cout = out;
@@ -259,10 +261,18 @@ struct RB : EqImpl {
     return launch_x(p, xj);
   }
 
-  // three grid fields Fg -> T-space state f (g2c: 1/Mx r2c, then Gz)
-  spadj_status g2c3(Problem* p, double2* f) {
+  // the three grid products of F (or of its JVP when dGp is non-null) -> T-space state f
+  // (products formed inside the x-forward FFT; g2c: 1/Mx r2c, then Gz)
+  spadj_status g2c3(Problem* p, double2* f, const double* Gp, const double* dGp) {
     XJobs xj{};
-    for (int q = 0; q < 3; ++q) xj.j[q] = xr2c(grid(Fg, q), 0, nullptr, 0, 1.0 / Mx, 1.0 / Mx, mix(Y, q));
+    for (int q = 0; q < 3; ++q) {
+      xj.j[q] = xr2c(nullptr, 0, nullptr, 0, 1.0 / Mx, 1.0 / Mx, mix(Y, q));
+      xj.j[q].prod = q;
+      xj.j[q].G = Gp;
+      xj.j[q].dG = dGp;
+      xj.j[q].npts = (int)npts;
+      xj.j[q].nr = 1;
+    }
     xj.n = 3;
     spadj_status s = launch_x(p, xj);
     if (s != SPADJ_OK) return s;
@@ -283,11 +293,7 @@ struct RB : EqImpl {
       cudaMemsetAsync(f, 0, sizeof(double2) * ns, p->stream);
       return check_launch(p, "rb zero F");
     }
-    cudaEvent_t tp = p->tic();
-    prod_fwd_kernel<<<prod_grid(), 256, 0, p->stream>>>(G.as<double>(), Fg.as<double>(), (int)npts);
-    p->toc(tp, KC_POINTWISE, 12.0 * npts);
-    if ((s = check_launch(p, "rb prod")) != SPADJ_OK) return s;
-    return g2c3(p, f);
+    return g2c3(p, f, G.as<double>(), nullptr);
   }
 
   // df = (dF/dx)(x) dx, with the grid fields of x already in G
@@ -298,11 +304,7 @@ struct RB : EqImpl {
     }
     spadj_status s = c2g_fields(p, dx, dG);
     if (s != SPADJ_OK) return s;
-    cudaEvent_t tp = p->tic();
-    prod_jvp_kernel<<<prod_grid(), 256, 0, p->stream>>>(G.as<double>(), dG.as<double>(), Fg.as<double>(), (int)npts);
-    p->toc(tp, KC_POINTWISE, 24.0 * npts);
-    if ((s = check_launch(p, "rb prod jvp")) != SPADJ_OK) return s;
-    return g2c3(p, df);
+    return g2c3(p, df, G.as<double>(), dG.as<double>());
   }
 
   // out = sum_a beta_a add_a + (dF/dx)(x)^dagger (sum_t alpha_t fb_t), grid fields of x in G.

@@ -157,6 +157,12 @@ __global__ void __launch_bounds__(256) zmm_kernel(const __grid_constant__ ZJobs 
 //                mult = 1 or -i*k, scale = s0 (k = 0) or s (k >= 1).
 struct XJob {
   int dir;
+  // dir 1 with prod >= 0: the input row is the grid product of output field prod (0 F_u,
+  // 1 F_w, 2 F_t) formed from the grid fields G (and the tangent fields dG when non-null)
+  int prod;
+  const double* G;
+  const double* dG;
+  int npts;
   const double2* cin;
   int cmul;
   double w0, w;
@@ -206,10 +212,34 @@ __global__ void __launch_bounds__(64) xfft_kernel(const __grid_constant__ XJobs 
     double2* g = reinterpret_cast<double2*>(J.rout + (size_t)row * Mx);
     for (int j = threadIdx.x; j < L; j += blockDim.x) g[j] = z[j];
   } else {
-    for (int t = 0; t < J.nr; ++t) {
-      double2* a = (t == 0) ? A : C;
-      const double2* g = reinterpret_cast<const double2*>(J.rin[t] + (size_t)row * Mx);
-      for (int j = threadIdx.x; j < L; j += blockDim.x) a[j] = g[j];
+    if (J.prod >= 0) {
+      // F_q = -(u * d_x q + w * d_z q) on the grid (slots: 0 u, 1 ux, 2 uz, 3 w, 4 wx, 5 wz, 6 tx, 7 tz)
+      const int sx = J.prod == 0 ? 1 : (J.prod == 1 ? 4 : 6);
+      const int sz = sx + 1;
+      auto rowp = [&](const double* base, int slot) {
+        return reinterpret_cast<const double2*>(base + (size_t)slot * J.npts + (size_t)row * Mx);
+      };
+      const double2 *u = rowp(J.G, 0), *w = rowp(J.G, 3), *qx = rowp(J.G, sx), *qz = rowp(J.G, sz);
+      if (!J.dG) {
+        for (int j = threadIdx.x; j < L; j += blockDim.x) {
+          const double2 a = u[j], b = qx[j], c = w[j], d = qz[j];
+          A[j] = make_double2(-fma(a.x, b.x, c.x * d.x), -fma(a.y, b.y, c.y * d.y));
+        }
+      } else {
+        const double2 *du = rowp(J.dG, 0), *dw = rowp(J.dG, 3), *dqx = rowp(J.dG, sx), *dqz = rowp(J.dG, sz);
+        for (int j = threadIdx.x; j < L; j += blockDim.x) {
+          const double2 a = u[j], b = qx[j], c = w[j], d = qz[j];
+          const double2 da = du[j], db = dqx[j], dc = dw[j], dd = dqz[j];
+          A[j] = make_double2(-(da.x * b.x + a.x * db.x + dc.x * d.x + c.x * dd.x),
+                              -(da.y * b.y + a.y * db.y + dc.y * d.y + c.y * dd.y));
+        }
+      }
+    } else {
+      for (int t = 0; t < J.nr; ++t) {
+        double2* a = (t == 0) ? A : C;
+        const double2* g = reinterpret_cast<const double2*>(J.rin[t] + (size_t)row * Mx);
+        for (int j = threadIdx.x; j < L; j += blockDim.x) a[j] = g[j];
+      }
     }
     __syncthreads();
     double2* z0 = cfft_smem(A, B, P.plan, P.WM, -1);
@@ -241,32 +271,10 @@ __global__ void __launch_bounds__(64) xfft_kernel(const __grid_constant__ XJobs 
   }
 }
 
-// Grid-point products.  Slots of the primal/tangent grid arrays: 0 u, 1 ux, 2 uz,
-// 3 w, 4 wx, 5 wz, 6 tx, 7 tz; outputs F: 0 F_u, 1 F_w, 2 F_t.
-__global__ void prod_fwd_kernel(const double* __restrict__ G, double* __restrict__ F, int npts) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < npts; i += gridDim.x * blockDim.x) {
-    const double u = G[0 * (size_t)npts + i], ux = G[1 * (size_t)npts + i], uz = G[2 * (size_t)npts + i];
-    const double w = G[3 * (size_t)npts + i], wx = G[4 * (size_t)npts + i], wz = G[5 * (size_t)npts + i];
-    const double tx = G[6 * (size_t)npts + i], tz = G[7 * (size_t)npts + i];
-    F[0 * (size_t)npts + i] = -fma(u, ux, w * uz);
-    F[1 * (size_t)npts + i] = -fma(u, wx, w * wz);
-    F[2 * (size_t)npts + i] = -fma(u, tx, w * tz);
-  }
-}
-
-__global__ void prod_jvp_kernel(const double* __restrict__ G, const double* __restrict__ dG, double* __restrict__ F,
-                                int npts) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < npts; i += gridDim.x * blockDim.x) {
-    double g[8], d[8];
-#pragma unroll
-    for (int s = 0; s < 8; ++s) { g[s] = G[s * (size_t)npts + i]; d[s] = dG[s * (size_t)npts + i]; }
-    F[0 * (size_t)npts + i] = -(d[0] * g[1] + g[0] * d[1] + d[3] * g[2] + g[3] * d[2]);
-    F[1 * (size_t)npts + i] = -(d[0] * g[4] + g[0] * d[4] + d[3] * g[5] + g[3] * d[5]);
-    F[2 * (size_t)npts + i] = -(d[0] * g[6] + g[0] * d[6] + d[3] * g[7] + g[3] * d[7]);
-  }
-}
-
-// Reverse of prod_fwd: from grid cotangents (gu, gw, gt) of (F_u, F_w, F_t) produce the
+// Grid-field slots: 0 u, 1 ux, 2 uz, 3 w, 4 wx, 5 wz, 6 tx, 7 tz (the forward and tangent
+// products are formed inside xfft_kernel; the reverse products have their own kernel).
+// Reverse of the products F_u = -(u ux + w uz), F_w = -(u wx + w wz), F_t = -(u tx + w tz):
+// from grid cotangents (gu, gw, gt) of (F_u, F_w, F_t) produce the
 // cotangents of the 8 grid fields.
 __global__ void prod_vjp_kernel(const double* __restrict__ G, const double* __restrict__ gF, double* __restrict__ Gb,
                                 int npts) {
