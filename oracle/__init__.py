@@ -22,6 +22,8 @@ Every routine follows the paper's own statement of the method
 * ``kolmogorov``  -- 2D periodic vorticity equation with sin(4y) forcing and a
                      4D-Var misfit objective.
 * ``cnn``         -- FP64 reference of the 3x3 periodic CNN closure.
+* ``couette``     -- 3D plane Couette flow, Fourier(x, y) x Chebyshev-tau, with the
+                     energy-gain (optimal perturbation) objective.
 
 Pins (what fixes each function independently of itself) live in
 ``tests/test_oracle_*.py`` and are listed in the design notes.

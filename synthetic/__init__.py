@@ -101,3 +101,67 @@ def cnn_params(seed, scale_out=0.1):
             W *= scale_out
         parts += [W.ravel(), np.zeros(co)]
     return np.concatenate(parts)
+
+
+def couette_ic(Nx, Ny, Nz, seed=5, norm=1e-4, Lx=4.0 * np.pi, Ly=2.0 * np.pi, nz0=6):
+    """Plane-Couette initial velocity (3, Nx/2, Ny, Nz) complex (u, v, w; kx half spectrum,
+    ky in FFT order, Chebyshev T_n in z on [-1, 1]).
+
+    u0 = curl(Psi (1 - z^2)^2) with a random vector potential Psi whose (kx, ky) coefficients
+    are N(0,1) draws times |k_h|^-2 for 0 < |k_h|, kx index <= Nx/4, |ky| <= Ny/4, and whose z
+    dependence is a Chebyshev series of degree < nz0 with a 2^-n envelope; the (1 - z^2)^2
+    factor makes u0 vanish at both walls and the curl makes it divergence-free.  The ky = -Ny/2
+    row is zero and the kx = 0 plane Hermitian.  Scaled to the volume-averaged norm
+    ((1/V) int |u0|^2 dV)^(1/2) = `norm`.  Polynomial products, derivatives and integrals in z
+    use numpy.polynomial.chebyshev; the degree stays below Nz so the field is exact."""
+    from numpy.polynomial import chebyshev as C
+    Kx, N = Nx // 2, Nz
+    nz0 = max(1, min(nz0, N - 5))
+    rng = np.random.default_rng(seed)
+    alpha = 2.0 * np.pi / Lx * np.arange(Kx)
+    kyi = np.fft.fftfreq(Ny, 1.0 / Ny).astype(int)
+    beta = 2.0 * np.pi / Ly * kyi
+    draw = rng.standard_normal((3, Kx, Ny, nz0)) + 1j * rng.standard_normal((3, Kx, Ny, nz0))
+    kh = np.sqrt(alpha[:, None] ** 2 + beta[None, :] ** 2)
+    band = (np.arange(Kx)[:, None] <= Nx // 4) & (np.abs(kyi)[None, :] <= Ny // 4) & (kh > 0)
+    band &= (kyi != -(Ny // 2))[None, :]
+    env = np.where(band, 1.0 / np.where(kh > 0, kh, 1.0) ** 2, 0.0)
+    psi = draw * env[None, :, :, None] * (0.5 ** np.arange(nz0))[None, None, None, :]
+    # Hermitian kx = 0 plane: psi(0, -ky) = conj psi(0, ky)
+    neg = np.concatenate([[0], np.arange(Ny - 1, 0, -1)])
+    pos = kyi > 0
+    psi[:, 0, neg[pos]] = np.conj(psi[:, 0, pos])
+    psi[:, 0, 0] = psi[:, 0, 0].real
+    bump = C.poly2cheb([1.0, 0.0, -2.0, 0.0, 1.0])  # (1 - z^2)^2
+
+    def series(c):  # Chebyshev coefficients (..., deg) -> (..., N) of c * bump
+        out = np.zeros(c.shape[:-1] + (N,), dtype=np.complex128)
+        for idx in np.ndindex(c.shape[:-1]):
+            if np.any(c[idx] != 0):
+                p = C.chebmul(c[idx], bump)
+                out[idx][:len(p)] = p
+        return out
+
+    def dz(c):
+        out = np.zeros_like(c)
+        for idx in np.ndindex(c.shape[:-1]):
+            d = C.chebder(c[idx])
+            out[idx][:len(d)] = d
+        return out
+
+    P = series(psi)                      # Psi (1 - z^2)^2, (3, Kx, Ny, N)
+    ia = 1j * alpha[:, None, None]
+    ib = 1j * beta[None, :, None]
+    u = np.stack([ib * P[2] - dz(P[1]), dz(P[0]) - ia * P[2], ia * P[1] - ib * P[0]])
+    # (1/V) int |u|^2 dV = 1/2 sum_{kx, ky} w_kx int_{-1}^{1} |u_hat(z)|^2 dz, w = 1 (kx = 0), 2
+    wk = np.where(np.arange(Kx) == 0, 1.0, 2.0)
+    e = 0.0
+    for f in range(3):
+        for m in range(Kx):
+            for j in range(Ny):
+                c = u[f, m, j]
+                if np.any(c != 0):
+                    sq = C.chebadd(C.chebmul(c.real, c.real), C.chebmul(c.imag, c.imag))
+                    I = C.chebint(sq)
+                    e += 0.5 * wk[m] * (C.chebval(1.0, I) - C.chebval(-1.0, I))
+    return u * (norm / np.sqrt(e))
