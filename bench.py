@@ -7,7 +7,7 @@ reference arm (``--impl reference``) times the FP64 CPU oracle on a bounded samp
 the same workload.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
-                       [--workload rb|burgers]
+                       [--workload rb|burgers|kolmogorov|couette]
 Under torchrun (N > 1) each rank runs an independent replica / shard; the time is the
 max over ranks and the value counts the units of all ranks.
 """
@@ -268,7 +268,82 @@ class KolmogorovBatch:
         return d * nsteps / el, "one 128^2 and one 512^2 member, %d-step 4D-Var gradient (numpy FP64)" % nsteps, el
 
 
-WORKLOADS = {"burgers": Burgers, "rb": RayleighBenard, "kolmogorov": KolmogorovBatch}
+class Couette:
+    """3D plane Couette, Fourier(x, y) 128 x 64 x Chebyshev(z) 64 tau, Re=1000, SBDF2 dt=5e-3,
+    4000 steps, energy gain E(T)/E(0) of a divergence-free initial field of norm 1e-4,
+    checkpoint slots sized to a 180 GB HBM budget."""
+    name = "couette3d_128x64x64_Re1000_sbdf2_4000steps_gain"
+
+    def __init__(self, Nx=128, Ny=64, Nz=64, Re=1000.0, dt=5e-3, nsteps=4000, seed=5, norm=1e-4, budget=180e9):
+        self.Nx, self.Ny, self.Nz, self.Re, self.dt, self.nsteps = Nx, Ny, Nz, Re, dt, nsteps
+        self.seed, self.norm, self.budget = seed, norm, budget
+        self.dof = 3 * Nx * Ny * Nz
+        self.B = 1
+        self.flush_l2 = False
+        self.slot_bytes = 3 * 16 * 3 * (Nx // 2) * Ny * Nz  # (x_n, x_{n-1}, f_{n-1})
+
+    @property
+    def slots(self):
+        return int(min(self.nsteps + 1, self.budget // self.slot_bytes))
+
+    def config(self):
+        return {"workload": self.name, "Nx": self.Nx, "Ny": self.Ny, "Nz": self.Nz, "Re": self.Re, "dt": self.dt,
+                "steps": self.nsteps, "scheme": "SBDF1 -> SBDF2", "objective": "energy gain E(T)/E(0)",
+                "checkpoint_slots": self.slots, "dof": self.dof,
+                "l2": "working set > L2 (pencil operators 4.8 GB read every step)"}
+
+    def units_per_step(self):
+        return self.dof * self.nsteps
+
+    def _ic(self):
+        u = synthetic.couette_ic(self.Nx, self.Ny, self.Nz, seed=self.seed, norm=self.norm)
+        return np.ascontiguousarray(np.transpose(u, (0, 2, 1, 3)))  # library layout [3][Ny][Nx/2][Nz]
+
+    def setup(self, device):
+        import torch
+        from paper_2506_14792_gb300 import spadj
+        self.sp = spadj
+        self.p = spadj.Problem(spadj.SPADJ_COUETTE3D, spadj.SPADJ_SBDF2, [self.Nx, self.Ny, self.Nz],
+                               [4 * np.pi, 2 * np.pi], [self.Re], self.dt)
+        self.s0 = self._ic()
+        self.x0 = torch.from_numpy(self.s0).to(device)
+        self.grad = torch.empty_like(self.x0)
+        self.x0_pin = torch.from_numpy(self.s0).pin_memory()
+        self.grad_pin = torch.empty(self.x0.shape, dtype=torch.complex128).pin_memory()
+        self.x0_dev2 = torch.empty_like(self.x0)
+
+    def step(self, ev=None):
+        self.p.gradient(self.x0, self.nsteps, self.grad, objective=self.sp.SPADJ_OBJ_GAIN, ckpt_slots=self.slots,
+                        want_J=False)
+
+    def e2e_step(self):
+        self.x0_dev2.copy_(self.x0_pin, non_blocking=True)
+        J = self.p.gradient(self.x0_dev2, self.nsteps, self.grad, objective=self.sp.SPADJ_OBJ_GAIN,
+                            ckpt_slots=self.slots)
+        self.grad_pin.copy_(self.grad, non_blocking=True)
+        return J
+
+    def e2e_bytes(self):
+        n = self.s0.nbytes
+        return n, n + 8
+
+    def cpu_sample(self, nsteps=40, size=(32, 16, 32)):
+        """Oracle gain gradient (store-all) on a reduced grid of the same equations: the dense
+        per-pencil LU oracle cannot factor the 4096 full-size pencils within the sample budget."""
+        from oracle import couette as oco
+        o = oco.Couette(*size, self.Re)
+        X0 = o.pencils(synthetic.couette_ic(*size, seed=self.seed, norm=self.norm))
+        oco.gain_gradient(o, X0, 1, self.dt)  # factorisations cached outside the timed sample
+        t = time.perf_counter()
+        oco.gain_gradient(o, X0, nsteps, self.dt)
+        el = time.perf_counter() - t
+        dof = 3 * size[0] * size[1] * size[2]
+        return (dof * nsteps / el,
+                "reduced grid %dx%dx%d, %d steps of the gain gradient (forward+adjoint, store-all, numpy/scipy "
+                "FP64, factorisations cached)" % (size + (nsteps,)), el)
+
+
+WORKLOADS = {"burgers": Burgers, "rb": RayleighBenard, "kolmogorov": KolmogorovBatch, "couette": Couette}
 DEFAULT_WORKLOAD = "rb"
 
 

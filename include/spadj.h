@@ -71,11 +71,23 @@ typedef enum {
  *   ky = j for j < N/2 and j - N otherwise; the ky = -N/2 row is held at 0 and the kx = 0
  *   column Hermitian); members are concatenated in batch order.  All members advance in one
  *   persistent launch over (stage, phase, member, tile) work items.
+ *
+ * SPADJ_COUETTE3D: perturbation u = (u, v, w) of plane Couette flow U = z between walls at
+ *   z = -1, +1 moving with -1, +1:  dt u - lap u / Re + U dx u + w U' e_x + grad p = u x curl u,
+ *   div u = 0, no-slip (p is the dynamic pressure).  x in [0, length[0]) (default 4 pi) and
+ *   y in [0, length[1]) (default 2 pi) periodic Fourier (Nx = n[0], Ny = n[1] modes), z
+ *   Chebyshev-T (N = n[2] modes) with tau terms as for SPADJ_RB2D; 3/2 dealiasing on all axes.
+ *   params[0] = Re.  Scheme SBDF2 (SBDF1 first step).  State: u, v, w coefficients, layout
+ *   [3][Ny][Nx/2][N] complex (ky index j in FFT order as for SPADJ_KOLMOGOROV2D, kx index
+ *   m = 0..Nx/2-1 with the Nyquist not stored; the ky = -Ny/2 row is held at 0 and the kx = 0
+ *   plane Hermitian in ky).  Grid layout [3N/2][3Ny/2][3Nx/2] real (Gauss-Chebyshev z).
+ *   Pressure and tau variables are internal to the step solves.
  */
 typedef enum {
   SPADJ_BURGERS1D = 0,
   SPADJ_RB2D = 1,
-  SPADJ_KOLMOGOROV2D = 2
+  SPADJ_KOLMOGOROV2D = 2,
+  SPADJ_COUETTE3D = 3
 } spadj_eq;
 
 typedef enum {
@@ -144,7 +156,9 @@ spadj_status spadj_eval_F_jvp(spadj_problem* prob, const double* x, const double
 spadj_status spadj_eval_F_vjp(spadj_problem* prob, const double* x, const double* y, double* out);
 
 /* Stage solve of the sparse pencil systems (Methods, "Linear system solves"), defined for
- * SPADJ_RB2D: x = prognostic part of (M + dt*gamma*L)^-1 [S1S0 v; 0] per x-mode pencil,
+ * SPADJ_RB2D: x = prognostic part of (M + dt*gamma*L)^-1 [S1S0 v; 0] per x-mode pencil, and
+ * for SPADJ_COUETTE3D: x = P (prognostic part of ((3/(2 dt)) M + L)^-1 [S1S0 v; 0]) per
+ * (kx, ky) pencil (the SBDF2 step matrix; P the projection onto admissible coefficients),
  * v and x in the state layout (T coefficients).  transpose = 1 applies the adjoint map
  * (Hermitian transpose, reusing the same factorisation).  SPADJ_ERR_UNSUPPORTED otherwise. */
 spadj_status spadj_solve(spadj_problem* prob, int transpose, const double* v, double* x);
@@ -173,9 +187,15 @@ spadj_status spadj_adjoint(spadj_problem* prob, int n_steps, const double* traj,
 
 /* Objectives for spadj_gradient. */
 typedef enum {
-  SPADJ_OBJ_ENERGY = 0,  /* J = 1/2 ||u(T)||^2 (physical L2 integral) per batch member */
-  SPADJ_OBJ_FOURDVAR = 1 /* J = sum_m 1/2 ||H(X_{n_m}) - obs_m||^2 per member (observations set by
-                            spadj_set_observations; H keeps |kx|, |ky| <= kmax) */
+  SPADJ_OBJ_ENERGY = 0,   /* J = 1/2 ||u(T)||^2 (physical L2 integral) per batch member; for
+                             SPADJ_COUETTE3D J = E(X_N) = (1/V) int |u|^2 dV */
+  SPADJ_OBJ_FOURDVAR = 1, /* J = sum_m 1/2 ||H(X_{n_m}) - obs_m||^2 per member (observations set by
+                             spadj_set_observations; H keeps |kx|, |ky| <= kmax) */
+  SPADJ_OBJ_GAIN = 2      /* SPADJ_COUETTE3D: energy gain J = E(X_N) / E(X_0) with the
+                             volume-weighted norm E(X) = (1/V) int |u|^2 dV (optimal
+                             perturbation objective); spadj_objective takes X_0 as obj_data
+                             and returns dJ/dX_N only, spadj_gradient includes the explicit
+                             dependence on X_0 */
 } spadj_objective_kind;
 
 /* 4D-Var observations for SPADJ_OBJ_FOURDVAR (SPADJ_KOLMOGOROV2D): n_obs steps (host ints,
@@ -219,16 +239,17 @@ spadj_status spadj_gradient(spadj_problem* prob, const double* x0, int n_steps, 
  * returns, per kernel class, the summed device time (ms), the summed algorithmic FP64
  * flop count and the number of launches since timing was (re)enabled.  Classes:
  * 0 z (Chebyshev) transforms, 1 x (Fourier) FFTs, 2 grid-point products, 3 pencil solves,
- * 4 objective, 5 fused persistent trajectory kernels.  spadj_timing synchronises the
- * stream and resets the counters. */
+ * 4 objective, 5 fused persistent trajectory kernels, 6 y (Fourier) FFTs.  spadj_timing
+ * synchronises the stream and resets the counters. */
 spadj_status spadj_timing(spadj_problem* prob, int enable);
 spadj_status spadj_timing_report(spadj_problem* prob, int kernel_class, double* ms, double* flops, long* launches);
 
 /* Vector-Jacobian product of the trajectory map (the reverse-mode building block behind
  * spadj_gradient and the torch.autograd binding): grad_x0 = sum_i (dX_{n_i}/dX_0)^T seed_i for
  * cotangents seeds[i] (device, layout [n_seeds][state]) injected at steps seed_steps[i]
- * (host ints in 0..n_steps, distinct).  Multistep problems keep the whole trajectory; the RK
- * problem uses ckpt_slots binomial checkpoint slots (<= 0: store every step).  This is the
+ * (host ints in 0..n_steps, distinct).  The Burgers and Kolmogorov problems keep the whole
+ * trajectory; SPADJ_RB2D and SPADJ_COUETTE3D use ckpt_slots binomial checkpoint slots (<= 0:
+ * store every step).  This is the
  * adjoint sweep of Supplementary A.4 with the objective's partial derivatives replaced by the
  * given cotangents (4D-Var style injection at intermediate steps included). */
 spadj_status spadj_vjp(spadj_problem* prob, const double* x0, int n_steps, int ckpt_slots, int n_seeds,

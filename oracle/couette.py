@@ -47,7 +47,7 @@ from . import fourier
 class Couette:
     NTAU = 7
 
-    def __init__(self, Nx, Ny, Nz, Re, Lx=4.0 * np.pi, Ly=2.0 * np.pi, dealias=1.5, nonlinear=True):
+    def __init__(self, Nx, Ny, Nz, Re, Lx=4.0 * np.pi, Ly=2.0 * np.pi, dealias=1.5, nonlinear=True, pencils=True):
         assert Nx % 2 == 0 and Ny % 2 == 0 and Nz >= 6
         self.Nx, self.Ny, self.Nz = Nx, Ny, Nz
         self.Kx = Nx // 2
@@ -77,6 +77,9 @@ class Couette:
         self.Cz = cb.c2g_matrix(N, self.Mz)
         self.Gz = cb.g2c_matrix(N, self.Mz)
         self.G = cb.gram(N)  # int_{-1}^{1} T_m T_n dz
+        self._lu = {}
+        if not pencils:  # transforms, F and the objective only (large sizes)
+            return
         shape = (self.Kx, Ny, self.nvar, self.nvar)
         self.Mmat = np.zeros(shape, dtype=np.complex128)
         self.Lmat = np.zeros(shape, dtype=np.complex128)
@@ -84,7 +87,6 @@ class Couette:
             for j in range(Ny):
                 self.Mmat[m, j], self.Lmat[m, j] = self.pencil_matrices(self.alpha[m], self.beta[j],
                                                                         mean=(m == 0 and j == 0))
-        self._lu = {}
 
     # ---- pencil operators ---------------------------------------------------------------
     def pencil_matrices(self, a, b, mean=False):

@@ -40,6 +40,7 @@ spadj_status spadj_create(const spadj_desc* desc, void* cuda_stream, spadj_probl
     case SPADJ_BURGERS1D: p->impl = spadj::make_burgers(p, &st); break;
     case SPADJ_RB2D: p->impl = spadj::make_rb(p, &st); break;
     case SPADJ_KOLMOGOROV2D: p->impl = spadj::make_kolmogorov(p, &st); break;
+    case SPADJ_COUETTE3D: p->impl = spadj::make_couette(p, &st); break;
     default: p->err = "spadj_create: unknown equation set"; break;
   }
   if (st != SPADJ_OK || !p->impl) {
@@ -98,6 +99,7 @@ spadj_status spadj_eval_F_vjp(spadj_problem* p, const double* x, const double* y
 spadj_status spadj_solve(spadj_problem* p, int transpose, const double* v, double* x) {
   if (!p) return SPADJ_ERR_INVALID;
   if (bad_ptr(v) || bad_ptr(x)) return p->fail(SPADJ_ERR_INVALID, "solve: NULL array");
+  if (p->desc.eq == SPADJ_COUETTE3D) return spadj::cou_pencil_solve(p->impl, p, transpose, v, x);
   return spadj::rb_pencil_solve(p->impl, p, transpose, v, x);
 }
 

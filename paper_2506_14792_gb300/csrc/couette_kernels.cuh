@@ -1,0 +1,295 @@
+// Device kernels of the plane-Couette path (Fourier x, Fourier y, Chebyshev z; FP64) that the
+// Rayleigh-Benard kernels (z transforms, x FFTs) do not already cover.
+//
+// Layouts (Kx = Nx/2 x-modes, Ny y-modes in FFT order, N Chebyshev modes; pencil index
+// p = jy * Kx + mx; Mx x My x Mz dealiased grid):
+//   coefficients  [field][Ny][Kx][N]    complex (one pencil contiguous)
+//   z-mixed       [Mz][Ny][Kx]          complex (z on the grid, x and y spectral)
+//   y-mixed       [Mz][My][Kx]          complex (z and y on the grid, x spectral)
+//   grid          [Mz][My][Mx]          real
+#pragma once
+#include "fft.cuh"
+
+namespace spadj {
+namespace couk {
+// internal linkage: every translation unit that includes this header gets its own kernels
+namespace {
+
+// ky index q (FFT order) -> wavenumber integer, and position in the length-My padded axis
+// (-1 for the unstored Nyquist row)
+__device__ __forceinline__ int ky_of(int q, int Ny) { return q < Ny / 2 ? q : q - Ny; }
+__device__ __forceinline__ int ypos(int q, int Ny, int My) { return q < Ny / 2 ? q : (q == Ny / 2 ? -1 : My - Ny + q); }
+
+constexpr int kYMaxJobs = 8;
+
+// One y-transform job over all z rows.
+//   dir 0 (coefficients -> y grid): column (row i, kx m) of out = scale * sum over ky of
+//         e^{i ky y} * (sum_t alpha_t mult_t(in_t)), zero-padded from Ny to My (Nyquist dropped);
+//         mult: 0 none, 1 i*kx, 2 i*ky.
+//   dir 1 (y grid -> coefficients): out = scale * (forward FFT of in_0 column) truncated to Ny
+//         (Nyquist row written as zero).
+struct YJob {
+  int dir;
+  const double2* in[3];
+  double alpha[3];
+  int mult[3];
+  int nin;
+  double scale;
+  double2* out;
+};
+struct YJobs {
+  YJob j[kYMaxJobs];
+  int n;
+};
+struct YParams {
+  int Kx, Ny, My, TK, ntile;
+  double kxs, kys;
+  FFTPlan plan;
+  const double2* W2;  // exp(-2 pi i m / (2 My)), m < 2 My
+};
+
+// CTA = (z row, tile of TK adjacent kx columns, job); the TK columns are transformed together.
+__global__ void __launch_bounds__(128) yfft_kernel(const __grid_constant__ YJobs js, YParams P) {
+  const YJob& J = js.j[blockIdx.y];
+  const int i = blockIdx.x / P.ntile, tile = blockIdx.x % P.ntile;
+  const int TK = P.TK, Kx = P.Kx, Ny = P.Ny, My = P.My;
+  const int m0 = tile * TK;
+  const int tk = min(TK, Kx - m0);
+  extern __shared__ double2 sy[];
+  double2* a = sy;
+  double2* b = sy + (size_t)My * TK;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (J.dir == 0) {
+    for (int idx = tid; idx < My * TK; idx += nt) a[idx] = make_double2(0.0, 0.0);
+    __syncthreads();
+    for (int idx = tid; idx < Ny * TK; idx += nt) {
+      const int q = idx / TK, c = idx - q * TK;
+      const int e = ypos(q, Ny, My);
+      if (c >= tk || e < 0) continue;
+      const int m = m0 + c;
+      const size_t g = ((size_t)i * Ny + q) * Kx + m;
+      double2 v = make_double2(0.0, 0.0);
+      for (int t = 0; t < J.nin; ++t) {
+        double2 x = J.in[t][g];
+        if (J.mult[t]) {
+          const double k = J.mult[t] == 1 ? P.kxs * m : P.kys * ky_of(q, Ny);
+          x = make_double2(-k * x.y, k * x.x);
+        }
+        v.x = fma(J.alpha[t], x.x, v.x);
+        v.y = fma(J.alpha[t], x.y, v.y);
+      }
+      a[e * TK + c] = v;
+    }
+    __syncthreads();
+    const double2* r = cfft_smem_batch<1>(a, b, P.plan, P.W2, TK);
+    for (int idx = tid; idx < My * TK; idx += nt) {
+      const int e = idx / TK, c = idx - e * TK;
+      if (c < tk) J.out[((size_t)i * My + e) * Kx + m0 + c] = cscale(r[idx], J.scale);
+    }
+  } else {
+    for (int idx = tid; idx < My * TK; idx += nt) {
+      const int e = idx / TK, c = idx - e * TK;
+      a[idx] = c < tk ? J.in[0][((size_t)i * My + e) * Kx + m0 + c] : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+    const double2* r = cfft_smem_batch<-1>(a, b, P.plan, P.W2, TK);
+    for (int idx = tid; idx < Ny * TK; idx += nt) {
+      const int q = idx / TK, c = idx - q * TK;
+      if (c >= tk) continue;
+      const int e = ypos(q, Ny, My);
+      J.out[((size_t)i * Ny + q) * Kx + m0 + c] = e < 0 ? make_double2(0.0, 0.0) : cscale(r[e * TK + c], J.scale);
+    }
+  }
+}
+
+// Step solve for the pencil pair (kx m, ky +jh) and (kx m, ky -jh), which share Phi up to
+// D = diag(1, -1, 1) on (u, v, w):  x = P Phi v  (forward) or  v = Phi^H P x  (transpose), with
+// v (or x) formed on load as sum_t a_t in_t.  P is the orthogonal projection onto admissible
+// coefficients (kx = 0 plane Hermitian in ky, mean pencil real, ky Nyquist row zero); it is
+// self-adjoint.  phiF[jh][m] is stored as [k][r] = Phi[r][k], phiA[jh][m] as [r][k] = Phi[r][k],
+// so the threads of a warp (consecutive output rows) read consecutive addresses.
+// CTA = (m, jh) with jh = Ny/2 writing the zero Nyquist row; thread = output row.
+struct CouSolveArgs {
+  const double2* in[4];
+  double a[4];
+  int nin;
+  double2* out;
+  int transpose;
+  const double2* phiF;
+  const double2* phiA;
+  int Kx, Ny, N;
+};
+
+__global__ void __launch_bounds__(1024) cou_solve_kernel(const __grid_constant__ CouSolveArgs S) {
+  const int m = blockIdx.x, jh = blockIdx.y;
+  const int Kx = S.Kx, Ny = S.Ny, N = S.N, H = 3 * N;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  auto off = [&](int c, int j) { return (((size_t)(c / N) * Ny + j) * Kx + m) * N + (c % N); };
+  if (jh == Ny / 2) {
+    for (int c = tid; c < H; c += nt) S.out[off(c, jh)] = make_double2(0.0, 0.0);
+    return;
+  }
+  const int j1 = jh, j2 = (Ny - jh) % Ny;
+  const bool two = j2 != j1;
+  extern __shared__ double2 sv[];
+  double2* v1 = sv;
+  double2* v2 = sv + H;
+  for (int c = tid; c < H; c += nt) {
+    double2 x1 = make_double2(0.0, 0.0), x2 = make_double2(0.0, 0.0);
+    for (int t = 0; t < S.nin; ++t) {
+      const double2 y1 = S.in[t][off(c, j1)];
+      x1.x = fma(S.a[t], y1.x, x1.x);
+      x1.y = fma(S.a[t], y1.y, x1.y);
+      if (two) {
+        const double2 y2 = S.in[t][off(c, j2)];
+        x2.x = fma(S.a[t], y2.x, x2.x);
+        x2.y = fma(S.a[t], y2.y, x2.y);
+      }
+    }
+    if (S.transpose && m == 0) {  // projection of the input (self-adjoint)
+      if (two) {
+        const double2 h = make_double2(0.5 * (x1.x + x2.x), 0.5 * (x1.y - x2.y));
+        x1 = h;
+        x2 = cconj(h);
+      } else {
+        x1.y = 0.0;
+      }
+    }
+    if (c / N == 1) x2 = make_double2(-x2.x, -x2.y);  // D
+    v1[c] = x1;
+    v2[c] = x2;
+  }
+  __syncthreads();
+  const size_t pp = (size_t)jh * Kx + m;
+  const double2* blk = (S.transpose ? S.phiA : S.phiF) + pp * H * H;
+  for (int r = tid; r < H; r += nt) {
+    double2 a1 = make_double2(0.0, 0.0), a2 = make_double2(0.0, 0.0);
+    double2 b1 = make_double2(0.0, 0.0), b2 = make_double2(0.0, 0.0);
+    int k = 0;
+    if (!S.transpose) {
+      // x[r] = sum_k Phi[r][k] v[k]
+      for (; k + 1 < H; k += 2) {
+        const double2 p0 = __ldg(blk + (size_t)k * H + r), p1 = __ldg(blk + (size_t)(k + 1) * H + r);
+        const double2 u0 = v1[k], u1 = v1[k + 1];
+        a1.x = fma(p0.x, u0.x, fma(-p0.y, u0.y, a1.x)); a1.y = fma(p0.x, u0.y, fma(p0.y, u0.x, a1.y));
+        b1.x = fma(p1.x, u1.x, fma(-p1.y, u1.y, b1.x)); b1.y = fma(p1.x, u1.y, fma(p1.y, u1.x, b1.y));
+        if (two) {
+          const double2 w0 = v2[k], w1 = v2[k + 1];
+          a2.x = fma(p0.x, w0.x, fma(-p0.y, w0.y, a2.x)); a2.y = fma(p0.x, w0.y, fma(p0.y, w0.x, a2.y));
+          b2.x = fma(p1.x, w1.x, fma(-p1.y, w1.y, b2.x)); b2.y = fma(p1.x, w1.y, fma(p1.y, w1.x, b2.y));
+        }
+      }
+      for (; k < H; ++k) {
+        const double2 p0 = __ldg(blk + (size_t)k * H + r);
+        const double2 u0 = v1[k];
+        a1.x = fma(p0.x, u0.x, fma(-p0.y, u0.y, a1.x)); a1.y = fma(p0.x, u0.y, fma(p0.y, u0.x, a1.y));
+        if (two) {
+          const double2 w0 = v2[k];
+          a2.x = fma(p0.x, w0.x, fma(-p0.y, w0.y, a2.x)); a2.y = fma(p0.x, w0.y, fma(p0.y, w0.x, a2.y));
+        }
+      }
+    } else {
+      // v[r] = sum_k conj(Phi[k][r]) x[k]
+      for (; k + 1 < H; k += 2) {
+        const double2 p0 = __ldg(blk + (size_t)k * H + r), p1 = __ldg(blk + (size_t)(k + 1) * H + r);
+        const double2 u0 = v1[k], u1 = v1[k + 1];
+        a1.x = fma(p0.x, u0.x, fma(p0.y, u0.y, a1.x)); a1.y = fma(p0.x, u0.y, fma(-p0.y, u0.x, a1.y));
+        b1.x = fma(p1.x, u1.x, fma(p1.y, u1.y, b1.x)); b1.y = fma(p1.x, u1.y, fma(-p1.y, u1.x, b1.y));
+        if (two) {
+          const double2 w0 = v2[k], w1 = v2[k + 1];
+          a2.x = fma(p0.x, w0.x, fma(p0.y, w0.y, a2.x)); a2.y = fma(p0.x, w0.y, fma(-p0.y, w0.x, a2.y));
+          b2.x = fma(p1.x, w1.x, fma(p1.y, w1.y, b2.x)); b2.y = fma(p1.x, w1.y, fma(-p1.y, w1.x, b2.y));
+        }
+      }
+      for (; k < H; ++k) {
+        const double2 p0 = __ldg(blk + (size_t)k * H + r);
+        const double2 u0 = v1[k];
+        a1.x = fma(p0.x, u0.x, fma(p0.y, u0.y, a1.x)); a1.y = fma(p0.x, u0.y, fma(-p0.y, u0.x, a1.y));
+        if (two) {
+          const double2 w0 = v2[k];
+          a2.x = fma(p0.x, w0.x, fma(p0.y, w0.y, a2.x)); a2.y = fma(p0.x, w0.y, fma(-p0.y, w0.x, a2.y));
+        }
+      }
+    }
+    double2 x1 = cadd(a1, b1), x2 = cadd(a2, b2);
+    if (r / N == 1) x2 = make_double2(-x2.x, -x2.y);  // D
+    if (!S.transpose && m == 0) {  // projection of the output
+      if (two) {
+        const double2 h = make_double2(0.5 * (x1.x + x2.x), 0.5 * (x1.y - x2.y));
+        x1 = h;
+        x2 = cconj(h);
+      } else {
+        x1.y = 0.0;
+      }
+    }
+    S.out[off(r, j1)] = x1;
+    if (two) S.out[off(r, j2)] = x2;
+  }
+}
+
+// Reverse of the products F = u x omega on the grid (slots 0 u, 1 v, 2 w, 3 omega_x,
+// 4 omega_y, 5 omega_z; cotangents gF of (F_x, F_y, F_z)) -> cotangents Gb of the six fields.
+__global__ void cou_prod_vjp_kernel(const double* __restrict__ G, const double* __restrict__ gF,
+                                    double* __restrict__ Gb, size_t npts) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < npts; i += (size_t)gridDim.x * blockDim.x) {
+    const double u = G[i], v = G[npts + i], w = G[2 * npts + i];
+    const double ox = G[3 * npts + i], oy = G[4 * npts + i], oz = G[5 * npts + i];
+    const double gx = gF[i], gy = gF[npts + i], gz = gF[2 * npts + i];
+    Gb[i] = fma(gz, oy, -gy * oz);
+    Gb[npts + i] = fma(gx, oz, -gz * ox);
+    Gb[2 * npts + i] = fma(gy, ox, -gx * oy);
+    Gb[3 * npts + i] = fma(gy, w, -gz * v);
+    Gb[4 * npts + i] = fma(gz, u, -gx * w);
+    Gb[5 * npts + i] = fma(gx, v, -gy * u);
+  }
+}
+
+// Energy E = (1/V) int |u|^2 dV = 1/2 sum_p w_kx sum_{u,v,w} c^H G c (G = int T_m T_n dz over
+// [-1, 1], w_kx = 1 for kx = 0 and 2 otherwise): per-pencil partial sums.  With `seed`
+// non-null also seed = scale[0] * w_kx * G c (the gradient of E times a device scalar).
+__global__ void cou_energy_kernel(const double2* __restrict__ x, const double* __restrict__ Gm, int Kx, int Ny,
+                                  int N, double* __restrict__ partial, const double* __restrict__ scale,
+                                  double2* __restrict__ seed) {
+  const int p = blockIdx.x;
+  const int j = p / Kx, m = p % Kx;
+  const double wm = (m == 0) ? 1.0 : 2.0;
+  const double sc = seed ? wm * scale[0] : 0.0;
+  double acc = 0.0;
+  for (int idx = threadIdx.x; idx < 3 * N; idx += blockDim.x) {
+    const int f = idx / N, i = idx % N;
+    const size_t base = (((size_t)f * Ny + j) * Kx + m) * N;
+    double2 g = make_double2(0.0, 0.0);
+    for (int k = 0; k < N; ++k) {
+      const double2 c = x[base + k];
+      const double gv = __ldg(&Gm[i * N + k]);
+      g.x = fma(gv, c.x, g.x);
+      g.y = fma(gv, c.y, g.y);
+    }
+    const double2 ci = x[base + i];
+    acc += ci.x * g.x + ci.y * g.y;
+    if (seed) seed[base + i] = make_double2(sc * g.x, sc * g.y);
+  }
+  __shared__ double red[128];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && partial) partial[p] = 0.5 * wm * red[0];
+}
+
+// e[0] = E(X_0), e[1] = E(X_N) -> J = e1 / e0 and the seed scales s[0] = 1 / e0 (for X_N),
+// s[1] = -e1 / e0^2 (for X_0).
+__global__ void gain_kernel(const double* __restrict__ e, double* __restrict__ J, double* __restrict__ s) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    const double e0 = e[0], e1 = e[1];
+    J[0] = e1 / e0;
+    s[0] = 1.0 / e0;
+    s[1] = -e1 / (e0 * e0);
+  }
+}
+
+}  // namespace
+}  // namespace couk
+}  // namespace spadj

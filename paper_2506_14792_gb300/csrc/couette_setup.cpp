@@ -1,0 +1,209 @@
+// Host-side construction of the plane-Couette per-pencil solution operators (once per
+// problem and timestep scheme, off the per-step path).
+//
+// Perturbation equations about U(z) = z on z in [-1, 1] (Supplementary A.4 IVP form):
+//   dt u - nu lap u + U dx u + w U' e_x + grad p = F,   div u = 0,   u = 0 at z = +-1.
+// Per wavenumber pair (kx, ky) the Chebyshev-T coefficients of u, v, w, p and seven tau
+// variables are the unknowns (Sparse spectral methods section): momentum rows on C^(2),
+// continuity on C^(1), first-order tau lifts (tau_q1 through d/dz of the last C^(1) mode,
+// tau_q2 on the last C^(2) mode, tau_w1 also in the last continuity row), boundary rows
+// T_n(+-1), and the gauge int p dz = 0 with tau_p on the mean pencil.  The advection
+// U dx = i kx z is the exact product z T_n (degree N) converted with S1 S0 and truncated.
+//
+// A multistep right-hand side is [S1S0 v_u; S1S0 v_v; S1S0 v_w; 0...] with v in T space
+// (b_i = 0 for i >= 1), and only the prognostic block of the solution is used, so the step
+// solve is the linear map Phi (3N x 3N per pencil).  The pencil matrix is complex (the
+// advection term is imaginary), so Phi is complex; it is computed here by LU with partial
+// pivoting (one factorisation per pencil and scheme, reused every step: Methods "Linear
+// system solves") and applied on the GPU as a dense matvec.
+#include "couette_setup.h"
+
+#include <cmath>
+#include <complex>
+#include <thread>
+
+namespace spadj {
+namespace couhost {
+namespace {
+
+using cd = std::complex<double>;
+
+bool lu_factor(std::vector<cd>& a, std::vector<int>& piv, int n) {
+  piv.resize(n);
+  for (int k = 0; k < n; ++k) {
+    int p = k;
+    double best = std::abs(a[(size_t)k * n + k]);
+    for (int i = k + 1; i < n; ++i) {
+      const double v = std::abs(a[(size_t)i * n + k]);
+      if (v > best) { best = v; p = i; }
+    }
+    if (best == 0.0) return false;
+    piv[k] = p;
+    if (p != k)
+      for (int j = 0; j < n; ++j) std::swap(a[(size_t)k * n + j], a[(size_t)p * n + j]);
+    const cd inv = 1.0 / a[(size_t)k * n + k];
+    const cd* rk = &a[(size_t)k * n];
+    for (int i = k + 1; i < n; ++i) {
+      const cd l = a[(size_t)i * n + k] * inv;
+      a[(size_t)i * n + k] = l;
+      if (l == 0.0) continue;
+      cd* ri = &a[(size_t)i * n];
+      for (int j = k + 1; j < n; ++j) ri[j] -= l * rk[j];
+    }
+  }
+  return true;
+}
+
+// Solve A X = B for nr right-hand sides held row-major in B (n x nr), overwritten.
+void lu_solve_multi(const std::vector<cd>& a, const std::vector<int>& piv, int n, std::vector<cd>& B, int nr) {
+  for (int k = 0; k < n; ++k)
+    if (piv[k] != k)
+      for (int c = 0; c < nr; ++c) std::swap(B[(size_t)k * nr + c], B[(size_t)piv[k] * nr + c]);
+  for (int i = 1; i < n; ++i) {
+    cd* bi = &B[(size_t)i * nr];
+    for (int j = 0; j < i; ++j) {
+      const cd l = a[(size_t)i * n + j];
+      if (l == 0.0) continue;
+      const cd* bj = &B[(size_t)j * nr];
+      for (int c = 0; c < nr; ++c) bi[c] -= l * bj[c];
+    }
+  }
+  for (int i = n - 1; i >= 0; --i) {
+    cd* bi = &B[(size_t)i * nr];
+    for (int j = i + 1; j < n; ++j) {
+      const cd u = a[(size_t)i * n + j];
+      if (u == 0.0) continue;
+      const cd* bj = &B[(size_t)j * nr];
+      for (int c = 0; c < nr; ++c) bi[c] -= u * bj[c];
+    }
+    const cd inv = 1.0 / a[(size_t)i * n + i];
+    for (int c = 0; c < nr; ++c) bi[c] *= inv;
+  }
+}
+
+// a0 M + L for the pencil (alpha, beta); ordering as documented in couette_setup.h.
+void assemble_pencil(const rbhost::Operators& o, const std::vector<double>& ZS, double al, double be, bool mean,
+                     double nu, double a0, std::vector<cd>& A) {
+  const int N = o.N, nv = 4 * N + 7;
+  A.assign((size_t)nv * nv, cd(0.0, 0.0));
+  auto at = [&](int r, int c) -> cd& { return A[(size_t)r * nv + c]; };
+  const int U = 0, V = N, W = 2 * N, P = 3 * N;
+  const int tu1 = 4 * N, tu2 = tu1 + 1, tv1 = tu1 + 2, tv2 = tu1 + 3, tw1 = tu1 + 4, tw2 = tu1 + 5, tp = tu1 + 6;
+  const double k2 = al * al + be * be;
+  const cd ia(0.0, al), ib(0.0, be);
+  for (int r = 0; r < N; ++r)
+    for (int c = 0; c < N; ++c) {
+      const double ss = o.SS[r * N + c], dd = o.DD[r * N + c];
+      const cd diag = a0 * ss - nu * (dd - k2 * ss) + ia * ZS[r * N + c];
+      at(U + r, U + c) = diag;
+      at(V + r, V + c) = diag;
+      at(W + r, W + c) = diag;
+      at(U + r, W + c) = ss;            // w U' e_x, U' = 1
+      at(U + r, P + c) = ia * ss;       // dx p
+      at(V + r, P + c) = ib * ss;       // dy p
+      at(W + r, P + c) = o.SD[r * N + c];  // dz p
+      at(P + r, U + c) = ia * o.S0[r * N + c];  // continuity (C^(1) rows)
+      at(P + r, V + c) = ib * o.S0[r * N + c];
+      at(P + r, W + c) = o.D0[r * N + c];
+    }
+  // -nu d/dz(lift(tau_q1)) enters row N-2 of the q-equation with -nu * lift_val
+  at(U + o.lift_row, tu1) = -nu * o.lift_val;
+  at(V + o.lift_row, tv1) = -nu * o.lift_val;
+  at(W + o.lift_row, tw1) = -nu * o.lift_val;
+  at(U + N - 1, tu2) = 1.0;
+  at(V + N - 1, tv2) = 1.0;
+  at(W + N - 1, tw2) = 1.0;
+  at(P + N - 1, tw1) = 1.0;
+  const int r0 = 4 * N;
+  for (int n = 0; n < N; ++n) {
+    const double bot = (n % 2 == 0) ? 1.0 : -1.0;
+    at(r0 + 0, U + n) = bot;
+    at(r0 + 1, U + n) = 1.0;
+    at(r0 + 2, V + n) = bot;
+    at(r0 + 3, V + n) = 1.0;
+    at(r0 + 4, W + n) = bot;
+    at(r0 + 5, W + n) = 1.0;
+  }
+  if (mean) {
+    at(P + 0, tp) = 1.0;
+    for (int n = 0; n < N; n += 2) at(r0 + 6, P + n) = 2.0 / (1.0 - (double)n * n);
+  } else {
+    at(r0 + 6, tp) = 1.0;
+  }
+}
+
+}  // namespace
+
+bool build_phi(const rbhost::Operators& o, int Kx, int Ny, double Lx, double Ly, double nu, double a0,
+               std::vector<double>& phiF, std::vector<double>& phiA, std::string* err) {
+  const int N = o.N, nv = 4 * N + 7, H = 3 * N, Nyh = Ny / 2;
+  // ZS = (S1 S0 on N + 1 modes) * (z T_n in the T basis of degree N), first N rows
+  std::vector<double> S0e = rbhost::op_S0(N + 1), S1e = rbhost::op_S1(N + 1);
+  std::vector<double> SSe = rbhost::matmul(S1e, S0e, N + 1);
+  std::vector<double> ZS((size_t)N * N, 0.0);
+  for (int r = 0; r < N; ++r)
+    for (int n = 0; n < N; ++n) {
+      // z T_0 = T_1; z T_n = (T_{n+1} + T_{n-1}) / 2
+      double v = 0.0;
+      if (n == 0) {
+        v = SSe[(size_t)r * (N + 1) + 1];
+      } else {
+        v = 0.5 * (SSe[(size_t)r * (N + 1) + n + 1] + SSe[(size_t)r * (N + 1) + n - 1]);
+      }
+      ZS[(size_t)r * N + n] = v;
+    }
+  const size_t per = (size_t)H * H * 2;
+  const int npen = Kx * Nyh;
+  phiF.assign((size_t)npen * per, 0.0);
+  phiA.assign((size_t)npen * per, 0.0);
+  std::vector<int> bad(npen, 0);
+  auto work = [&](int p0, int p1) {
+    std::vector<cd> A, B;
+    std::vector<int> piv;
+    for (int pp = p0; pp < p1; ++pp) {
+      const int jh = pp / Kx, m = pp % Kx;
+      const double al = 2.0 * M_PI / Lx * m, be = 2.0 * M_PI / Ly * jh;
+      assemble_pencil(o, ZS, al, be, m == 0 && jh == 0, nu, a0, A);
+      if (!lu_factor(A, piv, nv)) {
+        bad[pp] = 1;
+        continue;
+      }
+      B.assign((size_t)nv * H, cd(0.0, 0.0));
+      for (int f = 0; f < 3; ++f)
+        for (int c = 0; c < N; ++c)
+          for (int r = 0; r < N; ++r) B[(size_t)(f * N + r) * H + f * N + c] = o.SS[r * N + c];
+      lu_solve_multi(A, piv, nv, B, H);
+      double* F = &phiF[(size_t)pp * per];
+      double* Aa = &phiA[(size_t)pp * per];
+      for (int r = 0; r < H; ++r)
+        for (int k = 0; k < H; ++k) {
+          const cd v = B[(size_t)r * H + k];
+          F[2 * ((size_t)k * H + r)] = v.real();
+          F[2 * ((size_t)k * H + r) + 1] = v.imag();
+          Aa[2 * ((size_t)r * H + k)] = v.real();
+          Aa[2 * ((size_t)r * H + k) + 1] = v.imag();
+        }
+    }
+  };
+  unsigned nt = std::thread::hardware_concurrency();
+  if (nt == 0) nt = 1;
+  if (nt > 64) nt = 64;
+  if ((int)nt > npen) nt = npen;
+  std::vector<std::thread> th;
+  const int chunk = (npen + nt - 1) / nt;
+  for (unsigned t = 0; t < nt; ++t) {
+    const int p0 = t * chunk, p1 = std::min(npen, p0 + chunk);
+    if (p0 < p1) th.emplace_back(work, p0, p1);
+  }
+  for (auto& t : th) t.join();
+  for (int pp = 0; pp < npen; ++pp)
+    if (bad[pp]) {
+      if (err) *err = "couette: singular pencil matrix at (kx, ky) index (" + std::to_string(pp % Kx) + ", " +
+                      std::to_string(pp / Kx) + ")";
+      return false;
+    }
+  return true;
+}
+
+}  // namespace couhost
+}  // namespace spadj

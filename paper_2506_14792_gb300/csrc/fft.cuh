@@ -110,6 +110,65 @@ static __device__ __noinline__ double2* cfft_smem_t(double2* a, double2* b, cons
   return a;
 }
 
+// nb interleaved complex FFTs of length p.n: element e of sequence c at a[e * nb + c] (the
+// layout of a tile of nb adjacent columns).  Same passes as cfft_smem_t; threads stride over
+// (butterfly, sequence) pairs so consecutive threads touch consecutive sequences.
+template <int SIGN>
+static __device__ __noinline__ double2* cfft_smem_batch(double2* a, double2* b, const FFTPlan p,
+                                                        const double2* __restrict__ WM, int nb) {
+  const int n = p.n;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  int Ns = 1;
+  for (int pass = 0; pass < p.nrad; ++pass) {
+    const int R = p.rad[pass];
+    const int nbf = n / R;
+    const int tstep = n / (Ns * R);
+    for (int idx = tid; idx < nbf * nb; idx += nt) {
+      const int j = idx / nb, c = idx - j * nb;
+      const int k = j % Ns;
+      const int base = (j - k) * R + k;
+      auto A = [&](int e) -> double2 { return a[e * nb + c]; };
+      auto Bw = [&](int e, double2 v) { b[e * nb + c] = v; };
+      if (R == 4) {
+        double2 v0 = A(j), v1 = A(j + nbf), v2 = A(j + 2 * nbf), v3 = A(j + 3 * nbf);
+        if (k) {
+          v1 = cmul(v1, twL<SIGN>(WM, k * tstep));
+          v2 = cmul(v2, twL<SIGN>(WM, 2 * k * tstep));
+          v3 = cmul(v3, twL<SIGN>(WM, 3 * k * tstep));
+        }
+        const double2 t0 = cadd(v0, v2), t1 = csub(v0, v2), t2 = cadd(v1, v3);
+        const double2 t3 = rot<SIGN>(csub(v1, v3));
+        Bw(base, cadd(t0, t2));
+        Bw(base + Ns, cadd(t1, t3));
+        Bw(base + 2 * Ns, csub(t0, t2));
+        Bw(base + 3 * Ns, csub(t1, t3));
+      } else if (R == 2) {
+        double2 v0 = A(j), v1 = A(j + nbf);
+        if (k) v1 = cmul(v1, twL<SIGN>(WM, k * tstep));
+        Bw(base, cadd(v0, v1));
+        Bw(base + Ns, csub(v0, v1));
+      } else {
+        double2 v0 = A(j), v1 = A(j + nbf), v2 = A(j + 2 * nbf);
+        if (k) {
+          v1 = cmul(v1, twL<SIGN>(WM, k * tstep));
+          v2 = cmul(v2, twL<SIGN>(WM, 2 * k * tstep));
+        }
+        const double h = 0.86602540378443864676;
+        const double2 t = cadd(v1, v2);
+        const double2 m = make_double2(fma(-0.5, t.x, v0.x), fma(-0.5, t.y, v0.y));
+        const double2 d = rot<SIGN>(cscale(csub(v1, v2), h));
+        Bw(base, cadd(v0, t));
+        Bw(base + Ns, cadd(m, d));
+        Bw(base + 2 * Ns, csub(m, d));
+      }
+    }
+    __syncthreads();
+    double2* tmp = a; a = b; b = tmp;
+    Ns *= R;
+  }
+  return a;
+}
+
 __device__ __forceinline__ double2* cfft_smem(double2* a, double2* b, const FFTPlan p, const double2* __restrict__ WM,
                                               int sign) {
   return sign > 0 ? cfft_smem_t<1>(a, b, p, WM) : cfft_smem_t<-1>(a, b, p, WM);

@@ -67,7 +67,7 @@ struct EqImpl {
 // Optional per-kernel-class timing: CUDA events recorded on the problem's stream around
 // every launch of the library, with the algorithmic FP64 flop count of that launch.
 enum KernelClass { KC_ZTRANSFORM = 0, KC_XFFT = 1, KC_POINTWISE = 2, KC_SOLVE = 3, KC_OBJECTIVE = 4, KC_FUSED = 5,
-                   KC_COUNT = 6 };
+                   KC_YFFT = 6, KC_COUNT = 7 };
 
 struct Timing {
   bool enabled = false;
@@ -148,6 +148,8 @@ spadj_status kol_set_option(EqImpl* impl, Problem* p, int option, int value);
 spadj_status kol_autotune(EqImpl* impl, Problem* p);
 spadj_status kol_set_params(EqImpl* impl, Problem* p, const double* params);
 spadj_status rb_transform_noalloc(EqImpl* impl, Problem* p, int kind, const double* in, double* out);
+EqImpl* make_couette(Problem* p, spadj_status* st);
+spadj_status cou_pencil_solve(EqImpl* impl, Problem* p, int transpose, const double* v, double* x);
 
 }  // namespace spadj
 

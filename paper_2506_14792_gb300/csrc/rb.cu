@@ -219,13 +219,11 @@ struct RB : EqImpl {
   }
   XJob xc2r(const double2* in, int cmul, double w0, double w, double* out) {
     XJob j{};
-    j.prod = -1;
     j.dir = 0; j.cin = in; j.cmul = cmul; j.w0 = w0; j.w = w; j.rout = out;
     return j;
   }
   XJob xr2c(const double* in0, int mul0, const double* in1, int mul1, double s0, double s, double2* out) {
     XJob j{};
-    j.prod = -1;
     j.dir = 1; j.rin[0] = in0; j.rmul[0] = mul0; j.nr = 1;
     if (in1) { j.rin[1] = in1; j.rmul[1] = mul1; j.nr = 2; }
     j.s0 = s0; j.s = s; j.cout = out;
@@ -266,8 +264,12 @@ struct RB : EqImpl {
   spadj_status g2c3(Problem* p, double2* f, const double* Gp, const double* dGp) {
     XJobs xj{};
     for (int q = 0; q < 3; ++q) {
+      // F_q = -(u dx q + w dz q), slots 0 u, 1 ux, 2 uz, 3 w, 4 wx, 5 wz, 6 tx, 7 tz
+      static const int qx[3] = {1, 4, 6};
       xj.j[q] = xr2c(nullptr, 0, nullptr, 0, 1.0 / Mx, 1.0 / Mx, mix(Y, q));
-      xj.j[q].prod = q;
+      xj.j[q].nprod = 2;
+      xj.j[q].pa[0] = 0; xj.j[q].pb[0] = qx[q]; xj.j[q].ps[0] = -1.0;
+      xj.j[q].pa[1] = 3; xj.j[q].pb[1] = qx[q] + 1; xj.j[q].ps[1] = -1.0;
       xj.j[q].G = Gp;
       xj.j[q].dG = dGp;
       xj.j[q].npts = (int)npts;

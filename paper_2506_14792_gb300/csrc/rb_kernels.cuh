@@ -13,11 +13,16 @@
 
 namespace spadj {
 namespace rbk {
+// internal linkage: every translation unit that includes this header gets its own kernels
+namespace {
 
 constexpr int kZMaxJobs = 9;
 constexpr int kXMaxJobs = 12;
 
-// One z-transform job: out = sum_t alpha_t * mat_t * in_t (+ sum_a beta_a * add_a).
+// One z-transform job: out = sum_t alpha_t * mat_t * v_t (+ sum_a beta_a * add_a), where the
+// staged column v_t = mult_t(in_t) + sum_{e: xterm_e = t} xalpha_e * xmult_e(xin_e) combines
+// inputs that share matrix t before the matrix is applied (in_t may be NULL; mult: 0 none,
+// 1 i*kx, 2 i*ky of the column; only the Fourier-Fourier-Chebyshev layouts use them).
 //   expand: K = N coefficients -> I = Mz grid rows; mat_t is (Mz/2) x N (rows j < Mz/2)
 //   fold:   K = Mz grid rows -> I = N coefficients; mat_t is N x (Mz/2) (columns j < Mz/2)
 // deriv_t = 1 when mat_t has the reflection parity of a z-derivative (-(-1)^n).
@@ -26,9 +31,15 @@ struct ZJob {
   const double* mat[2];
   double alpha[2];
   int deriv[2];
+  int mult[2];
   int nterm;
-  const double2* add[2];
-  double beta[2];
+  const double2* xin[2];
+  double xalpha[2];
+  int xmult[2];
+  int xterm[2];
+  int nx;
+  const double2* add[3];
+  double beta[3];
   int nadd;
   double2* out;
   int I, K;
@@ -38,9 +49,25 @@ struct ZJob {
 struct ZJobs {
   ZJob j[kZMaxJobs];
   int n;
-  int ncols;  // Kx
+  int ncols;  // columns (pencils)
   int expand; // 1: expand, 0: fold
+  // column m = jy * kxn + mx has wavenumbers kx = kxs * mx, ky = kys * (jy < nyk/2 ? jy : jy - nyk)
+  int kxn, nyk;
+  double kxs, kys;
 };
+
+// i * (kx or ky of column m) * v
+__device__ __forceinline__ double2 zmult(const ZJobs& js, int type, int m, double2 v) {
+  if (type == 0) return v;
+  double k;
+  if (type == 1) {
+    k = js.kxs * (m % js.kxn);
+  } else {
+    const int jy = m / js.kxn;
+    k = js.kys * (jy < js.nyk / 2 ? jy : jy - js.nyk);
+  }
+  return make_double2(-k * v.y, k * v.x);
+}
 
 // One CTA per (column, job); the reduction of every output is split over the two lanes of a
 // lane pair and combined with a shuffle, so an expand job runs 2*Mz/2 threads and a fold job
@@ -57,15 +84,25 @@ __global__ void __launch_bounds__(256) zmm_kernel(const __grid_constant__ ZJobs 
   const int K = J.K, I = J.I;
   const int Kh = js.expand ? K : K / 2;  // staged entries per term (and per s/d array)
   // stage this column: expand -> coefficients; fold -> (s, d) = f_j +- f_{Mz-1-j}
+  auto comb = [&](int t, int k) {
+    double2 v = J.in[t] ? zmult(js, J.mult[t], m, J.in[t][(size_t)m * J.im + (size_t)k * J.ik])
+                        : make_double2(0.0, 0.0);
+    for (int e = 0; e < J.nx; ++e) {
+      if (J.xterm[e] != t) continue;
+      const double2 x = zmult(js, J.xmult[e], m, J.xin[e][(size_t)m * J.im + (size_t)k * J.ik]);
+      v.x = fma(J.xalpha[e], x.x, v.x);
+      v.y = fma(J.xalpha[e], x.y, v.y);
+    }
+    return v;
+  };
   for (int t = 0; t < J.nterm; ++t) {
     double2* s = sb + (size_t)t * 2 * Kh;
-    const double2* src = J.in[t] + (size_t)m * J.im;
     for (int k = tid; k < Kh; k += nt) {
-      const double2 v = src[(size_t)k * J.ik];
+      const double2 v = comb(t, k);
       if (js.expand) {
         s[k] = v;
       } else {
-        const double2 v2 = src[(size_t)(K - 1 - k) * J.ik];
+        const double2 v2 = comb(t, K - 1 - k);
         s[k] = make_double2(v.x + v2.x, v.y + v2.y);       // s_j
         s[Kh + k] = make_double2(v.x - v2.x, v.y - v2.y);  // d_j
       }
@@ -157,9 +194,12 @@ __global__ void __launch_bounds__(256) zmm_kernel(const __grid_constant__ ZJobs 
 //                mult = 1 or -i*k, scale = s0 (k = 0) or s (k >= 1).
 struct XJob {
   int dir;
-  // dir 1 with prod >= 0: the input row is the grid product of output field prod (0 F_u,
-  // 1 F_w, 2 F_t) formed from the grid fields G (and the tangent fields dG when non-null)
-  int prod;
+  // dir 1 with nprod > 0: the input row is the grid product sum_t ps_t G[pa_t] G[pb_t] of
+  // grid fields (slots of G, npts points each), or its tangent
+  // sum_t ps_t (dG[pa_t] G[pb_t] + G[pa_t] dG[pb_t]) when dG is non-null
+  int nprod;
+  int pa[2], pb[2];
+  double ps[2];
   const double* G;
   const double* dG;
   int npts;
@@ -212,26 +252,26 @@ __global__ void __launch_bounds__(64) xfft_kernel(const __grid_constant__ XJobs 
     double2* g = reinterpret_cast<double2*>(J.rout + (size_t)row * Mx);
     for (int j = threadIdx.x; j < L; j += blockDim.x) g[j] = z[j];
   } else {
-    if (J.prod >= 0) {
-      // F_q = -(u * d_x q + w * d_z q) on the grid (slots: 0 u, 1 ux, 2 uz, 3 w, 4 wx, 5 wz, 6 tx, 7 tz)
-      const int sx = J.prod == 0 ? 1 : (J.prod == 1 ? 4 : 6);
-      const int sz = sx + 1;
+    if (J.nprod > 0) {
       auto rowp = [&](const double* base, int slot) {
         return reinterpret_cast<const double2*>(base + (size_t)slot * J.npts + (size_t)row * Mx);
       };
-      const double2 *u = rowp(J.G, 0), *w = rowp(J.G, 3), *qx = rowp(J.G, sx), *qz = rowp(J.G, sz);
+      const double2 *a0 = rowp(J.G, J.pa[0]), *b0 = rowp(J.G, J.pb[0]);
+      const double2 *a1 = rowp(J.G, J.pa[1]), *b1 = rowp(J.G, J.pb[1]);
+      const double p0 = J.ps[0], p1 = J.ps[1];
       if (!J.dG) {
         for (int j = threadIdx.x; j < L; j += blockDim.x) {
-          const double2 a = u[j], b = qx[j], c = w[j], d = qz[j];
-          A[j] = make_double2(-fma(a.x, b.x, c.x * d.x), -fma(a.y, b.y, c.y * d.y));
+          const double2 a = a0[j], b = b0[j], c = a1[j], d = b1[j];
+          A[j] = make_double2(fma(p0 * a.x, b.x, p1 * (c.x * d.x)), fma(p0 * a.y, b.y, p1 * (c.y * d.y)));
         }
       } else {
-        const double2 *du = rowp(J.dG, 0), *dw = rowp(J.dG, 3), *dqx = rowp(J.dG, sx), *dqz = rowp(J.dG, sz);
+        const double2 *da0 = rowp(J.dG, J.pa[0]), *db0 = rowp(J.dG, J.pb[0]);
+        const double2 *da1 = rowp(J.dG, J.pa[1]), *db1 = rowp(J.dG, J.pb[1]);
         for (int j = threadIdx.x; j < L; j += blockDim.x) {
-          const double2 a = u[j], b = qx[j], c = w[j], d = qz[j];
-          const double2 da = du[j], db = dqx[j], dc = dw[j], dd = dqz[j];
-          A[j] = make_double2(-(da.x * b.x + a.x * db.x + dc.x * d.x + c.x * dd.x),
-                              -(da.y * b.y + a.y * db.y + dc.y * d.y + c.y * dd.y));
+          const double2 a = a0[j], b = b0[j], c = a1[j], d = b1[j];
+          const double2 da = da0[j], db = db0[j], dc = da1[j], dd = db1[j];
+          A[j] = make_double2(p0 * (da.x * b.x + a.x * db.x) + p1 * (dc.x * d.x + c.x * dd.x),
+                              p0 * (da.y * b.y + a.y * db.y) + p1 * (dc.y * d.y + c.y * dd.y));
         }
       }
     } else {
@@ -272,7 +312,8 @@ __global__ void __launch_bounds__(64) xfft_kernel(const __grid_constant__ XJobs 
 }
 
 // Grid-field slots: 0 u, 1 ux, 2 uz, 3 w, 4 wx, 5 wz, 6 tx, 7 tz (the forward and tangent
-// products are formed inside xfft_kernel; the reverse products have their own kernel).
+// products are formed inside xfft_kernel from product specs; the reverse products have their
+// own kernel).
 // Reverse of the products F_u = -(u ux + w uz), F_w = -(u wx + w wz), F_t = -(u tx + w tz):
 // from grid cotangents (gu, gw, gt) of (F_u, F_w, F_t) produce the
 // cotangents of the 8 grid fields.
@@ -434,5 +475,6 @@ __global__ void axpy_kernel(double2* __restrict__ y, const double2* __restrict__
   }
 }
 
+}  // namespace
 }  // namespace rbk
 }  // namespace spadj

@@ -27,23 +27,23 @@ namespace spadj {
 namespace rbhost {
 
 namespace {
-
 using Mat = std::vector<double>;  // row-major
+}  // namespace
 
 // d/dxi T_n = n C1_{n-1}
-Mat op_D0(int N, double s) {
+std::vector<double> op_D0(int N, double s) {
   Mat m(N * N, 0.0);
   for (int n = 1; n < N; ++n) m[(n - 1) * N + n] = n * s;
   return m;
 }
 // d/dxi C1_n = 2 C2_{n-1}
-Mat op_D1(int N, double s) {
+std::vector<double> op_D1(int N, double s) {
   Mat m(N * N, 0.0);
   for (int n = 1; n < N; ++n) m[(n - 1) * N + n] = 2.0 * s;
   return m;
 }
 // T -> C1 conversion
-Mat op_S0(int N) {
+std::vector<double> op_S0(int N) {
   Mat m(N * N, 0.0);
   m[0] = 1.0;
   if (N > 1) m[1 * N + 1] = 0.5;
@@ -54,7 +54,7 @@ Mat op_S0(int N) {
   return m;
 }
 // C1 -> C2 conversion
-Mat op_S1(int N) {
+std::vector<double> op_S1(int N) {
   Mat m(N * N, 0.0);
   for (int n = 0; n < N; ++n) {
     m[n * N + n] = 1.0 / (n + 1);
@@ -62,7 +62,7 @@ Mat op_S1(int N) {
   }
   return m;
 }
-Mat matmul(const Mat& a, const Mat& b, int N) {
+std::vector<double> matmul(const std::vector<double>& a, const std::vector<double>& b, int N) {
   Mat c(N * N, 0.0);
   for (int i = 0; i < N; ++i)
     for (int k = 0; k < N; ++k) {
@@ -72,6 +72,8 @@ Mat matmul(const Mat& a, const Mat& b, int N) {
     }
   return c;
 }
+
+namespace {
 
 // In-place LU with partial pivoting of an n x n row-major matrix; returns false if singular.
 bool lu_factor(std::vector<double>& a, std::vector<int>& piv, int n) {
@@ -121,11 +123,10 @@ void lu_solve(const std::vector<double>& a, const std::vector<int>& piv, int n, 
 
 }  // namespace
 
-Operators build_operators(int N, int Mz) {
+Operators build_operators(int N, int Mz, double zs) {
   Operators o;
   o.N = N;
   o.Mz = Mz;
-  const double zs = 2.0;  // z in [0, 1]: d/dz = 2 d/dxi
   Mat S0 = op_S0(N), S1 = op_S1(N), D0 = op_D0(N, zs), D1 = op_D1(N, zs);
   o.SS = matmul(S1, S0, N);
   o.DD = matmul(D1, D0, N);
@@ -162,11 +163,11 @@ Operators build_operators(int N, int Mz) {
       for (int k = 0; k < N; ++k) s += o.Cz[(size_t)j * N + k] * o.Dz[k * N + n];
       o.Cdz[(size_t)j * N + n] = s;
     }
-  // int_0^1 T_m T_n dz = (1/2) int_{-1}^{1} T_m T_n dxi = (I_{m+n} + I_{|m-n|}) / 4
+  // int T_m T_n dz over the interval = (1/zs) int_{-1}^{1} T_m T_n dxi = (I_{m+n} + I_{|m-n|}) / (2 zs)
   auto I = [](int k) { return (k % 2 == 0) ? 2.0 / (1.0 - (double)k * k) : 0.0; };
   o.G.assign(N * N, 0.0);
   for (int m = 0; m < N; ++m)
-    for (int n = 0; n < N; ++n) o.G[m * N + n] = 0.25 * (I(m + n) + I(std::abs(m - n)));
+    for (int n = 0; n < N; ++n) o.G[m * N + n] = (0.5 / zs) * (I(m + n) + I(std::abs(m - n)));
   return o;
 }
 

@@ -24,6 +24,7 @@ SPADJ_ERR_UNSUPPORTED = -6
 SPADJ_BURGERS1D = 0
 SPADJ_RB2D = 1
 SPADJ_KOLMOGOROV2D = 2
+SPADJ_COUETTE3D = 3
 
 SPADJ_SBDF1 = 1
 SPADJ_SBDF2 = 2
@@ -31,6 +32,7 @@ SPADJ_RK222 = 3
 
 SPADJ_OBJ_ENERGY = 0
 SPADJ_OBJ_FOURDVAR = 1
+SPADJ_OBJ_GAIN = 2
 
 C2G, G2C, C2G_ADJ, G2C_ADJ = 0, 1, 2, 3
 
@@ -259,7 +261,7 @@ class Problem:
                                       _ptr(_as_f64(grad_x0, n, "grad_x0"))))
         return grad_x0
 
-    KERNEL_CLASSES = ("z_transform", "x_fft", "pointwise", "pencil_solve", "objective", "fused_trajectory")
+    KERNEL_CLASSES = ("z_transform", "x_fft", "pointwise", "pencil_solve", "objective", "fused_trajectory", "y_fft")
 
     def timing(self, enable=True):
         _chk(self.h, lib().spadj_timing(self.h, int(bool(enable))))

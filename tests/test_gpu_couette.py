@@ -1,0 +1,280 @@
+"""GPU parity for the plane-Couette path (Fourier x, y x Chebyshev-tau z, SBDF1 -> SBDF2)
+through the C-ABI against the FP64 oracle: transforms and their adjoints, the explicit term
+u x omega with its JVP/VJP, the pencil step solve and its adjoint, forward/tangent/adjoint
+trajectories, the energy-gain gradient with binomial checkpointing (checkpointed == store-all
+bitwise), cotangent injection, and at the full size 128 x 64 x 64 (Re = 1000, dt = 5e-3)
+the explicit term, sampled pencil solves and trajectory properties (dot test, central FD)."""
+import numpy as np
+import pytest
+
+import synthetic
+from oracle import couette as oco
+from oracle import imex
+from tests.gpu_util import TOL, dev, host, rel_err
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+SMALL = [(8, 4, 8), (16, 6, 12), (32, 8, 16)]
+RE, DT = 1000.0, 5e-3
+
+
+def gpu_problem(Nx, Ny, Nz, Re=RE, dt=DT, nonlinear=True, scheme=None):
+    from paper_2506_14792_gb300 import spadj
+    sch = spadj.SPADJ_SBDF2 if scheme is None else scheme
+    return spadj.Problem(spadj.SPADJ_COUETTE3D, sch, [Nx, Ny, Nz], [4 * np.pi, 2 * np.pi], [Re], dt,
+                         nonlinear=nonlinear)
+
+
+def to_gpu(s):
+    """oracle fields (3, Kx, Ny, N) -> library layout (3, Ny, Kx, N)"""
+    return np.ascontiguousarray(np.transpose(s, (0, 2, 1, 3)))
+
+
+def to_oracle(g):
+    return np.ascontiguousarray(np.transpose(g, (0, 2, 1, 3)))
+
+
+def rand_fields(o, seed, amp=1.0, project=True):
+    s = synthetic.random_coeffs((3, o.Kx, o.Ny, o.N), seed=seed, scale=amp)
+    if project:
+        s = o.state(o.project(o.pencils(s)))
+    return s
+
+
+def F_T(o, Fe):
+    N = o.N
+    return np.stack([np.linalg.solve(o.SS, np.moveaxis(Fe[..., f * N:(f + 1) * N], -1, 0).reshape(N, -1))
+                     .reshape((N, o.Kx, o.Ny)).transpose(1, 2, 0) for f in range(3)])
+
+
+def vjp_T(o, X, fbar):
+    """(dF_T/dX)^dagger fbar = F_vjp(X, Y) with the C^(2) rows of Y = S1S0^-T fbar."""
+    N = o.N
+    Y = np.zeros((o.Kx, o.Ny, o.nvar), complex)
+    for f in range(3):
+        Y[..., f * N:(f + 1) * N] = np.linalg.solve(o.SS.T, fbar[f].reshape(-1, N).T).T.reshape(o.Kx, o.Ny, N)
+    return o.state(o.F_vjp(X, Y))
+
+
+def step_solve(o, v, a0, transpose=False):
+    """P (prognostic part of (a0 M + L)^-1 [S1S0 v; 0]) or its adjoint map."""
+    N = o.N
+    if not transpose:
+        R = np.zeros((o.Kx, o.Ny, o.nvar), complex)
+        for f in range(3):
+            R[..., f * N:(f + 1) * N] = v[f] @ o.SS.T
+        return o.state(o.project(o.solve(a0, 1.0, R)))
+    Y = o.solve_t(a0, 1.0, o.project(o.pencils(v)))
+    return np.stack([Y[..., f * N:(f + 1) * N] @ o.SS for f in range(3)])
+
+
+def _zc(shape):
+    return torch.zeros(shape, dtype=torch.complex128, device="cuda")
+
+
+@pytest.mark.parametrize("Nx,Ny,Nz", SMALL)
+def test_transforms(Nx, Ny, Nz):
+    from paper_2506_14792_gb300 import spadj
+    o = oco.Couette(Nx, Ny, Nz, RE, pencils=False)
+    p = gpu_problem(Nx, Ny, Nz)
+    c = synthetic.random_coeffs((o.Kx, o.Ny, o.N), seed=Nx + Ny)
+    g = np.random.default_rng(Nz).standard_normal((o.Mx, o.My, o.Mz))
+    cg = dev(np.ascontiguousarray(c.transpose(1, 0, 2)))
+    gg = dev(np.ascontiguousarray(g.transpose(2, 1, 0)))
+    og = torch.zeros((o.Mz, o.My, o.Mx), dtype=torch.float64, device="cuda")
+    oc = _zc((o.Ny, o.Kx, o.N))
+    p.transform(spadj.C2G, cg, og)
+    assert rel_err(host(og).transpose(2, 1, 0), o.c2g(c)) < 1e-13
+    p.transform(spadj.G2C_ADJ, cg, og)
+    assert rel_err(host(og).transpose(2, 1, 0), o.g2c_adj(c)) < 1e-13
+    p.transform(spadj.G2C, gg, oc)
+    assert rel_err(host(oc).transpose(1, 0, 2), o.g2c(g)) < 1e-13
+    p.transform(spadj.C2G_ADJ, gg, oc)
+    assert rel_err(host(oc).transpose(1, 0, 2), o.c2g_adj(g)) < 1e-13
+
+
+@pytest.mark.parametrize("Nx,Ny,Nz", SMALL)
+def test_F_jvp_vjp(Nx, Ny, Nz):
+    o = oco.Couette(Nx, Ny, Nz, RE, pencils=False)
+    p = gpu_problem(Nx, Ny, Nz)
+    s, d = rand_fields(o, 1), rand_fields(o, 2)
+    X = o.pencils(s)
+    out = _zc((3, o.Ny, o.Kx, o.N))
+    p.eval_F(dev(to_gpu(s)), out)
+    assert rel_err(to_oracle(host(out)), F_T(o, o.F(X))) < 1e-12
+    p.eval_F_jvp(dev(to_gpu(s)), dev(to_gpu(d)), out)
+    assert rel_err(to_oracle(host(out)), F_T(o, o.F_jvp(X, o.pencils(d)))) < 1e-12
+    p.eval_F_vjp(dev(to_gpu(s)), dev(to_gpu(d)), out)
+    assert rel_err(to_oracle(host(out)), vjp_T(o, X, d)) < 1e-12
+
+
+@pytest.mark.parametrize("Nx,Ny,Nz", SMALL)
+def test_pencil_solve_and_adjoint(Nx, Ny, Nz):
+    o = oco.Couette(Nx, Ny, Nz, RE)
+    p = gpu_problem(Nx, Ny, Nz)
+    v = rand_fields(o, 3, project=False)
+    out = _zc((3, o.Ny, o.Kx, o.N))
+    p.solve(dev(to_gpu(v)), out)
+    assert rel_err(to_oracle(host(out)), step_solve(o, v, 1.5 / DT)) < 1e-12
+    p.solve(dev(to_gpu(v)), out, transpose=True)
+    assert rel_err(to_oracle(host(out)), step_solve(o, v, 1.5 / DT, transpose=True)) < 1e-12
+
+
+@pytest.fixture(scope="module")
+def traj_case():
+    Nx, Ny, Nz, n = 16, 6, 12, 12
+    o = oco.Couette(Nx, Ny, Nz, RE)
+    u0 = synthetic.couette_ic(Nx, Ny, Nz, seed=5, norm=0.05)
+    X0 = o.pencils(u0)
+    J, g, X = oco.gain_gradient(o, X0, n, DT)
+    return o, u0, X0, J, g, X, n
+
+
+def test_forward_tangent_adjoint(traj_case):
+    o, u0, X0, J, g, X, n = traj_case
+    p = gpu_problem(o.Nx, o.Ny, o.Nz)
+    x0 = dev(to_gpu(u0))
+    xN = _zc(x0.shape)
+    traj = _zc((n + 1,) + tuple(x0.shape))
+    p.forward(n, x0, xN, traj)
+    assert rel_err(to_oracle(host(xN)), o.state(X[-1])) < TOL
+    assert rel_err(to_oracle(host(traj[n // 2])), o.state(X[n // 2])) < TOL
+    d = rand_fields(o, 11, amp=0.05)
+    dxN = _zc(x0.shape)
+    p.tangent(n, x0, dev(to_gpu(d)), dxN)
+    dX = imex.multistep_tangent(o, X, o.pencils(d), DT)
+    assert rel_err(to_oracle(host(dxN)), o.state(dX[-1])) < TOL
+    ybar = rand_fields(o, 12, project=False)
+    gr = _zc(x0.shape)
+    p.adjoint(n, traj, dev(to_gpu(ybar)), gr)
+    want = imex.multistep_adjoint(o, X, lambda k: o.pencils(ybar) if k == n else None, DT)
+    assert rel_err(to_oracle(host(gr)), o.state(want)) < TOL
+
+
+def test_gain_gradient_and_checkpointing(traj_case):
+    from paper_2506_14792_gb300 import spadj
+    o, u0, X0, J, g, X, n = traj_case
+    p = gpu_problem(o.Nx, o.Ny, o.Nz)
+    x0 = dev(to_gpu(u0))
+    gr = _zc(x0.shape)
+    Jg = p.gradient(x0, n, gr, objective=spadj.SPADJ_OBJ_GAIN, ckpt_slots=0)
+    assert abs(Jg[0] - J) < TOL * abs(J)
+    assert rel_err(to_oracle(host(gr)), o.state(g)) < TOL
+    for slots in (2, 3, 5):
+        gc = _zc(x0.shape)
+        Jc = p.gradient(x0, n, gc, objective=spadj.SPADJ_OBJ_GAIN, ckpt_slots=slots)
+        assert Jc[0] == Jg[0]
+        assert torch.equal(gc, gr), slots
+
+
+def test_energy_objective_and_vjp(traj_case):
+    from paper_2506_14792_gb300 import spadj
+    o, u0, X0, J, g, X, n = traj_case
+    p = gpu_problem(o.Nx, o.Ny, o.Nz)
+    x0 = dev(to_gpu(u0))
+    gr = _zc(x0.shape)
+    Je = p.gradient(x0, n, gr, objective=spadj.SPADJ_OBJ_ENERGY, ckpt_slots=4)
+    want = imex.multistep_adjoint(o, X, lambda k: o.energy_grad(X[k]) if k == n else None, DT)
+    assert abs(Je[0] - o.energy(X[-1])) < TOL * o.energy(X[-1])
+    assert rel_err(to_oracle(host(gr)), o.state(want)) < TOL
+    # cotangents injected at steps 0, 4 and n
+    steps = [0, 4, n]
+    seeds = [rand_fields(o, 40 + i, project=False) for i in range(3)]
+    sd = dev(np.stack([to_gpu(s) for s in seeds]))
+    gv = _zc(x0.shape)
+    p.vjp(x0, n, steps, sd, gv, ckpt_slots=3)
+    src = {k: o.pencils(s) for k, s in zip(steps, seeds)}
+    want = imex.multistep_adjoint(o, X, lambda k: src.get(k), DT)
+    assert rel_err(to_oracle(host(gv)), o.state(want)) < TOL
+
+
+def test_linear_and_sbdf1():
+    from paper_2506_14792_gb300 import spadj
+    Nx, Ny, Nz, n = 8, 4, 8, 7
+    for nonlinear, scheme, order in [(False, spadj.SPADJ_SBDF2, 2), (True, spadj.SPADJ_SBDF1, 1)]:
+        o = oco.Couette(Nx, Ny, Nz, 300.0, nonlinear=nonlinear)
+        p = gpu_problem(Nx, Ny, Nz, Re=300.0, dt=1e-2, nonlinear=nonlinear, scheme=scheme)
+        u0 = synthetic.couette_ic(Nx, Ny, Nz, seed=9, norm=0.2)
+        X = imex.multistep_forward(o, o.pencils(u0), n, 1e-2, order=order)
+        E0, EN = o.energy(X[0]), o.energy(X[-1])
+        dJ = lambda k: (o.energy_grad(X[k]) / E0 if k == n else (-(EN / E0 ** 2) * o.energy_grad(X[0])
+                                                                  if k == 0 else None))
+        want = imex.multistep_adjoint(o, X, dJ, 1e-2, order=order)
+        gr = _zc((3, Ny, Nx // 2, Nz))
+        Jg = p.gradient(dev(to_gpu(u0)), n, gr, objective=spadj.SPADJ_OBJ_GAIN)
+        assert abs(Jg[0] - EN / E0) < TOL * EN / E0
+        assert rel_err(to_oracle(host(gr)), o.state(want)) < TOL
+
+
+# ---- full configuration 128 x 64 x 64, Re = 1000, dt = 5e-3 --------------------------------
+
+FULL = (128, 64, 64)
+
+
+@pytest.fixture(scope="module")
+def full_case():
+    p = gpu_problem(*FULL)
+    u0 = synthetic.couette_ic(*FULL, seed=5)
+    return p, u0
+
+
+def test_full_explicit_term(full_case):
+    p, u0 = full_case
+    o = oco.Couette(*FULL, RE, pencils=False)
+    out = _zc(to_gpu(u0).shape)
+    p.eval_F(dev(to_gpu(u0)), out)
+    assert rel_err(to_oracle(host(out)), F_T(o, o.F(o.pencils(u0)))) < 1e-12
+
+
+def test_full_sampled_pencil_solves(full_case):
+    p, u0 = full_case
+    o = oco.Couette(*FULL, RE, pencils=False)
+    N = o.N
+    v = rand_fields(o, 21, project=False)
+    out = _zc(to_gpu(v).shape)
+    p.solve(dev(to_gpu(v)), out)
+    got = to_oracle(host(out))
+    p.solve(dev(to_gpu(v)), out, transpose=True)
+    got_t = to_oracle(host(out))
+    a0 = 1.5 / DT
+    for m, j in [(1, 1), (5, 3), (63, 31), (17, 40), (30, 63), (2, 0)]:
+        Mm, Lm = o.pencil_matrices(o.alpha[m], o.beta[j])
+        A = a0 * Mm + Lm
+        R = np.zeros(o.nvar, complex)
+        for f in range(3):
+            R[f * N:(f + 1) * N] = o.SS @ v[f, m, j]
+        x = np.linalg.solve(A, R)[:3 * N]
+        assert rel_err(got[:, m, j].ravel(), x) < 1e-11, (m, j)
+        y = np.linalg.solve(A.conj().T, np.concatenate([v[:, m, j].ravel(), np.zeros(N + 7)]))
+        want_t = np.concatenate([o.SS.T @ y[f * N:(f + 1) * N] for f in range(3)])
+        assert rel_err(got_t[:, m, j].ravel(), want_t) < 1e-11, (m, j)
+
+
+def test_full_trajectory_dot_and_fd(full_case):
+    from paper_2506_14792_gb300 import spadj
+    p, u0 = full_case
+    n = 6
+    x0 = dev(to_gpu(u0))
+    o = oco.Couette(*FULL, RE, pencils=False)
+    dx = dev(to_gpu(rand_fields(o, 31, amp=1e-5)))
+    ybar = dev(to_gpu(rand_fields(o, 32)))
+    traj = _zc((n + 1,) + tuple(x0.shape))
+    xN = _zc(x0.shape)
+    p.forward(n, x0, xN, traj)
+    dxN = _zc(x0.shape)
+    p.tangent(n, x0, dx, dxN)
+    gr = _zc(x0.shape)
+    p.adjoint(n, traj, ybar, gr)
+    lhs = float(torch.sum((torch.conj(ybar) * dxN).real))
+    rhs = float(torch.sum((torch.conj(gr) * dx).real))
+    assert abs(lhs - rhs) <= 1e-11 * abs(lhs)
+    g = _zc(x0.shape)
+    J = p.gradient(x0, n, g, objective=spadj.SPADJ_OBJ_GAIN, ckpt_slots=3)[0]
+    d = dev(to_gpu(synthetic.couette_ic(*FULL, seed=77, norm=1e-4)))
+    eps = 1e-4
+    Jp = p.gradient(x0 + eps * d, n, _zc(x0.shape), objective=spadj.SPADJ_OBJ_GAIN)[0]
+    Jm = p.gradient(x0 - eps * d, n, _zc(x0.shape), objective=spadj.SPADJ_OBJ_GAIN)[0]
+    fd = (Jp - Jm) / (2 * eps)
+    ad = float(torch.sum((torch.conj(g) * d).real))
+    assert abs(fd - ad) <= 1e-6 * abs(fd), (fd, ad, J)
