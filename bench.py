@@ -546,10 +546,22 @@ def main():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
     ap.add_argument("--nsteps", type=int, default=None, help="override the workload's time steps (profiling runs)")
+    ap.add_argument("--size", default=None,
+                    help="override the grid of the rb (Nx,Nz) or couette (Nx,Ny,Nz) workload (profiling runs)")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]()
     if args.nsteps is not None:
         wl.nsteps = args.nsteps
+    if args.size:
+        dims = [int(v) for v in args.size.split(",")]
+        if args.workload == "couette" and len(dims) == 3:
+            wl = Couette(*dims, nsteps=wl.nsteps)
+            wl.name = "couette3d_%dx%dx%d_Re1000_sbdf2_%dsteps_gain" % (dims[0], dims[1], dims[2], wl.nsteps)
+        elif args.workload == "rb" and len(dims) == 2:
+            wl = RayleighBenard(*dims, nsteps=wl.nsteps)
+            wl.name = "rayleigh_benard2d_%dx%d_Ra1e6_rk222_%dsteps" % (dims[0], dims[1], wl.nsteps)
+        else:
+            ap.error("--size takes Nx,Nz for rb and Nx,Ny,Nz for couette")
     if args.impl == "reference":
         return run_reference(args, wl)
     return run_gpu(args, wl)

@@ -34,6 +34,55 @@ def restrict(fine, nmem, Nf, Nc):
     return out.reshape(lead + (nmem * (Nc // 2) * Nc,))
 
 
+def spin_up(x0_fine, nmem, Nf, Re, dt_f, nsteps):
+    """Advance fine initial states nsteps fine steps (so the training windows start from
+    developed flow rather than from the synthetic spectra)."""
+    p = spadj.Problem(spadj.SPADJ_KOLMOGOROV2D, spadj.SPADJ_SBDF2, [Nf], [2 * np.pi], [Re, 0.0], dt_f, batch=nmem)
+    y = torch.empty_like(x0_fine)
+    p.forward(nsteps, x0_fine, y)
+    p.close()
+    return y
+
+
+def make_dataset(x0_fine, nmem, Nf, Nc, Re, dt_f, ratio, ncoarse, spin=0, chunk=64):
+    """Restricted fine snapshots [ncoarse + 1][nmem * Nc/2 * Nc] for fine initial states
+    x0_fine (concatenated members), generated `chunk` members at a time by the library's own
+    fine solver (spun up `spin` fine steps first)."""
+    per = (Nf // 2) * Nf
+    out = []
+    for c in range(0, nmem, chunk):
+        k = min(chunk, nmem - c)
+        x = x0_fine[c * per:(c + k) * per].contiguous()
+        if spin:
+            x = spin_up(x, k, Nf, Re, dt_f, spin)
+        f = fine_snapshots(x, k, Nf, Re, dt_f, ratio, ncoarse)
+        out.append(restrict(f, k, Nf, Nc))
+        del f
+    return torch.cat(out, dim=1).contiguous()
+
+
+def train_selected(params, train_snaps, ntrain, val_snaps, nval, Nc, Re, dt_c, iters, every=25, lr=3e-3,
+                   log=None):
+    """Adam on the training windows with model selection on held-aside validation windows:
+    every `every` iterations the summed validation error at T/4, T/2 and T is evaluated and the
+    best parameters so far are kept (early stopping).  Returns (best params, history)."""
+    nco = train_snaps.shape[0] - 1
+    at = [nco // 4, nco // 2, nco]
+    best, best_p, hist = None, params.clone(), []
+    done = 0
+    while done < iters:
+        train(params, train_snaps, ntrain, Nc, Re, dt_c, every, lr=lr)
+        done += every
+        v = rollout_errors(params, val_snaps, nval, Nc, Re, dt_c, at)
+        score = float(sum(v[k].mean() for k in at))
+        hist.append((done, score))
+        if log is not None:
+            log(done, score)
+        if best is None or score < best:
+            best, best_p = score, params.clone()
+    return best_p, hist
+
+
 def fine_snapshots(x0_fine, nmem, Nf, Re, dt_f, ratio, ncoarse):
     """Fine trajectories from the library's solver; states every `ratio` fine steps."""
     p = spadj.Problem(spadj.SPADJ_KOLMOGOROV2D, spadj.SPADJ_SBDF2, [Nf], [2 * np.pi], [Re, 0.0], dt_f, batch=nmem)
