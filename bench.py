@@ -450,6 +450,8 @@ def run_gpu(args, wl):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     wl.setup(dev)
+    if args.pdl:
+        wl.p.set_option(6, 1)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev) if wl.flush_l2 else None
 
@@ -545,6 +547,7 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
+    ap.add_argument("--pdl", action="store_true", help="programmatic dependent launch of consecutive kernels")
     ap.add_argument("--nsteps", type=int, default=None, help="override the workload's time steps (profiling runs)")
     ap.add_argument("--size", default=None,
                     help="override the grid of the rb (Nx,Nz) or couette (Nx,Ny,Nz) workload (profiling runs)")

@@ -215,8 +215,11 @@ spadj_status spadj_set_params(spadj_problem* prob, const double* params);
  * rows per row tile; 3 = resident CTAs per SM (0 = occupancy maximum); 4 = iteration limit of
  * the scheduler's bounded waits (0 = default, several seconds); 5 = failure-path test: the
  * completion of this member (-1 = none) is never signalled, so a bounded wait runs out and
- * the call returns SPADJ_ERR_TIMEOUT with the context intact.  spadj_autotune times
- * candidate settings on the problem's own sizes and keeps the fastest. */
+ * the call returns SPADJ_ERR_TIMEOUT with the context intact.  Option 6 (SPADJ_RB2D,
+ * SPADJ_COUETTE3D) = programmatic dependent launch of consecutive kernels (1: the next kernel
+ * is scheduled while its predecessor drains and waits for it on the device; 0, default: plain
+ * stream order); set it before the first sweep (the step graphs are captured once).
+ * spadj_autotune times candidate settings on the problem's own sizes and keeps the fastest. */
 spadj_status spadj_set_option(spadj_problem* prob, int option, int value);
 spadj_status spadj_autotune(spadj_problem* prob);
 

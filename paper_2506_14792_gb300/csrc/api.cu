@@ -126,6 +126,10 @@ spadj_status spadj_set_observations(spadj_problem* p, int n_obs, const int* obs_
 
 spadj_status spadj_set_option(spadj_problem* p, int option, int value) {
   if (!p) return SPADJ_ERR_INVALID;
+  if (option == 6) {
+    p->pdl = value != 0;
+    return SPADJ_OK;
+  }
   return spadj::kol_set_option(p->impl, p, option, value);
 }
 

@@ -199,7 +199,7 @@ struct Couette : EqImpl {
     for (int i = 0; i < js.n; ++i) f += 4.0 * P * N * (Mz / 2) * js.j[i].nterm;
     const int threads = zmm_threads(js.expand, js.j[0].I);
     cudaEvent_t t = p->tic();
-    zmm_kernel<<<dim3(P, js.n), threads, zsmem, p->stream>>>(js);
+    SPADJ_CUDA_TRY(p, launch_kernel(p->pdl, zmm_kernel, dim3(P, js.n), dim3(threads), zsmem, p->stream, js));
     p->toc(t, KC_ZTRANSFORM, f);
     return check_launch(p, "couette zmm");
   }
@@ -219,7 +219,7 @@ struct Couette : EqImpl {
   spadj_status launch_y(Problem* p, YJobs& js) {
     const double f = js.n * (double)Mz * Kx * 5.0 * My * std::log2((double)My);
     cudaEvent_t t = p->tic();
-    yfft_kernel<<<dim3(Mz * yp.ntile, js.n), 128, ysmem, p->stream>>>(js, yp);
+    SPADJ_CUDA_TRY(p, launch_kernel(p->pdl, yfft_kernel, dim3(Mz * yp.ntile, js.n), dim3(128), ysmem, p->stream, js, yp));
     p->toc(t, KC_YFFT, f);
     return check_launch(p, "couette yfft");
   }
@@ -236,7 +236,7 @@ struct Couette : EqImpl {
   spadj_status launch_x(Problem* p, XJobs& js) {
     const double f = js.n * (double)Mz * My * 2.5 * Mx * std::log2((double)Mx);
     cudaEvent_t t = p->tic();
-    xfft_kernel<<<dim3(Mz * My, js.n), 64, xsmem, p->stream>>>(js, xp);
+    SPADJ_CUDA_TRY(p, launch_kernel(p->pdl, xfft_kernel, dim3(Mz * My, js.n), dim3(64), xsmem, p->stream, js, xp));
     p->toc(t, KC_XFFT, f);
     return check_launch(p, "couette xfft");
   }
@@ -353,7 +353,8 @@ struct Couette : EqImpl {
     if ((s = launch_x(p, xj)) != SPADJ_OK) return s;
     cudaEvent_t tp = p->tic();
     const int pg = (int)std::min<size_t>((npts + 255) / 256, 4096);
-    cou_prod_vjp_kernel<<<pg, 256, 0, p->stream>>>(G.as<double>(), Fg.as<double>(), Gb.as<double>(), npts);
+    SPADJ_CUDA_TRY(p, launch_kernel(p->pdl, cou_prod_vjp_kernel, dim3(pg), dim3(256), 0, p->stream,
+                                    (const double*)G.as<double>(), (const double*)Fg.as<double>(), Gb.as<double>(), npts));
     p->toc(tp, KC_POINTWISE, 18.0 * npts);
     if ((s = check_launch(p, "couette prod vjp")) != SPADJ_OK) return s;
     // (T^-1)^dagger: r2c with factor 2 on kx >= 1, forward FFT in y (truncated), then z folds
@@ -403,7 +404,8 @@ struct Couette : EqImpl {
     const int H = 3 * N;
     const int threads = ((H + 31) / 32) * 32;
     cudaEvent_t t = p->tic();
-    cou_solve_kernel<<<dim3(Kx, Ny / 2 + 1), threads, sizeof(double2) * 2 * H, p->stream>>>(S);
+    SPADJ_CUDA_TRY(p, launch_kernel(p->pdl, cou_solve_kernel, dim3(Kx, Ny / 2 + 1), dim3(threads),
+                                    sizeof(double2) * 2 * H, p->stream, S));
     p->toc(t, KC_SOLVE, 8.0 * H * H * (double)Kx * (Ny - 1));
     return check_launch(p, "couette solve");
   }

@@ -9,6 +9,7 @@
 //   grid          [Mz][My][Mx]          real
 #pragma once
 #include "fft.cuh"
+#include "pdl.cuh"
 
 namespace spadj {
 namespace couk {
@@ -50,6 +51,8 @@ struct YParams {
 
 // CTA = (z row, tile of TK adjacent kx columns, job); the TK columns are transformed together.
 __global__ void __launch_bounds__(128) yfft_kernel(const __grid_constant__ YJobs js, YParams P) {
+  pdl_trigger();
+  pdl_wait();
   const YJob& J = js.j[blockIdx.y];
   const int i = blockIdx.x / P.ntile, tile = blockIdx.x % P.ntile;
   const int TK = P.TK, Kx = P.Kx, Ny = P.Ny, My = P.My;
@@ -121,6 +124,8 @@ struct CouSolveArgs {
 };
 
 __global__ void __launch_bounds__(1024) cou_solve_kernel(const __grid_constant__ CouSolveArgs S) {
+  pdl_trigger();
+  pdl_wait();
   const int m = blockIdx.x, jh = blockIdx.y;
   const int Kx = S.Kx, Ny = S.Ny, N = S.N, H = 3 * N;
   const int tid = threadIdx.x, nt = blockDim.x;
@@ -231,6 +236,8 @@ __global__ void __launch_bounds__(1024) cou_solve_kernel(const __grid_constant__
 // 4 omega_y, 5 omega_z; cotangents gF of (F_x, F_y, F_z)) -> cotangents Gb of the six fields.
 __global__ void cou_prod_vjp_kernel(const double* __restrict__ G, const double* __restrict__ gF,
                                     double* __restrict__ Gb, size_t npts) {
+  pdl_trigger();
+  pdl_wait();
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < npts; i += (size_t)gridDim.x * blockDim.x) {
     const double u = G[i], v = G[npts + i], w = G[2 * npts + i];
     const double ox = G[3 * npts + i], oy = G[4 * npts + i], oz = G[5 * npts + i];

@@ -174,6 +174,7 @@ __device__ __forceinline__ double2* cfft_smem(double2* a, double2* b, const FFTP
   return sign > 0 ? cfft_smem_t<1>(a, b, p, WM) : cfft_smem_t<-1>(a, b, p, WM);
 }
 
+
 // ---- real transforms on the packed half-length sequence ---------------------------------
 //
 // c2r: coefficients c_k (k < K, read through get(k)) of a real field, g_j = sum over the

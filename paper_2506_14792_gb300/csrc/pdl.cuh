@@ -1,0 +1,43 @@
+// Programmatic dependent launch (sm_90+): a kernel launched with the programmatic
+// stream-serialisation attribute may be scheduled while its predecessor in the stream is
+// still running.  Kernels signal early that their dependents may launch (pdl_trigger) and
+// wait for the predecessor's completion and memory visibility (pdl_wait) before they read
+// anything it produces or write anything it may still read; only constant data (transform
+// matrices, solution operators) is touched before the wait.  Without the attribute both
+// instructions return immediately, so the same kernels serve ordinary launches.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <utility>
+
+namespace spadj {
+
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// 8-byte asynchronous global -> shared copy (completes at cp_async_wait_all)
+__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gmem_src) {
+  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Launch `kernel` on `st`, with the programmatic stream-serialisation attribute when pdl.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_kernel(bool pdl, void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                                 cudaStream_t st, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
+}  // namespace spadj

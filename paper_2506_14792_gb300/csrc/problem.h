@@ -6,6 +6,7 @@
 #include <string>
 #include <vector>
 
+#include "pdl.cuh"
 #include "spadj.h"
 
 namespace spadj {
@@ -111,6 +112,7 @@ struct Problem {
   std::string err;
   EqImpl* impl = nullptr;
   Timing timing;
+  bool pdl = false;  // programmatic dependent launch of consecutive kernels (spadj_set_option 6)
   cudaEvent_t tic() {
     if (!timing.enabled) return nullptr;
     cudaEvent_t e = timing.get();

@@ -172,7 +172,9 @@ struct RB : EqImpl {
     SPADJ_CUDA_TRY(p, Jdev.ensure(sizeof(double)));
     zsmem = (size_t)2 * 2 * (size_t)std::max(N, Mz / 2) * kTM * sizeof(double2);
     xsmem = sizeof(double2) * (4 * L + Kx);
-    ssmem = sizeof(double2) * (H + 4 * solve_rows(H));
+    ssmem = sizeof(double2) * (H + 4 * solve_rows(H)) + sizeof(double) * (size_t)H * solve_rows(H);
+    if (ssmem > 48 * 1024)
+      SPADJ_CUDA_TRY(p, cudaFuncSetAttribute(solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssmem));
     return SPADJ_OK;
   }
 
@@ -194,14 +196,13 @@ struct RB : EqImpl {
     dim3 grid(Kx, js.n);
     const int threads = zmm_threads(js.expand, js.j[0].I);
     cudaEvent_t t = p->tic();
-    zmm_kernel<<<grid, threads, zsmem, p->stream>>>(js);
+    SPADJ_CUDA_TRY(p, launch_kernel(p->pdl, zmm_kernel, grid, dim3(threads), zsmem, p->stream, js));
     p->toc(t, KC_ZTRANSFORM, zflops(js));
     return check_launch(p, "rb zmm");
   }
   spadj_status launch_x(Problem* p, XJobs& js) {
-    dim3 grid(Mz, js.n);
     cudaEvent_t t = p->tic();
-    xfft_kernel<<<grid, 64, xsmem, p->stream>>>(js, xp);
+    SPADJ_CUDA_TRY(p, launch_kernel(p->pdl, xfft_kernel, dim3(Mz, js.n), dim3(64), xsmem, p->stream, js, xp));
     p->toc(t, KC_XFFT, xflops(js));
     return check_launch(p, "rb xfft");
   }
@@ -336,7 +337,9 @@ struct RB : EqImpl {
       xj.n = 3;
       if ((s = launch_x(p, xj)) != SPADJ_OK) return s;
       cudaEvent_t tp = p->tic();
-      prod_vjp_kernel<<<prod_grid(), 256, 0, p->stream>>>(G.as<double>(), Fg.as<double>(), Gb.as<double>(), (int)npts);
+      SPADJ_CUDA_TRY(p, launch_kernel(p->pdl, prod_vjp_kernel, dim3(prod_grid()), dim3(256), 0, p->stream,
+                                      (const double*)G.as<double>(), (const double*)Fg.as<double>(), Gb.as<double>(),
+                                      (int)npts));
       p->toc(tp, KC_POINTWISE, 24.0 * npts);
       if ((s = check_launch(p, "rb prod vjp")) != SPADJ_OK) return s;
       // (T^-1)^dagger in x: r2c with factor 2 on k >= 1, x-derivative adjoint -ik
@@ -383,7 +386,7 @@ struct RB : EqImpl {
     const int H = 3 * N / 2;
     dim3 grid(Kx, 2, 2);
     cudaEvent_t t = p->tic();
-    solve_kernel<<<grid, 4 * solve_rows(H), ssmem, p->stream>>>(S);
+    SPADJ_CUDA_TRY(p, launch_kernel(p->pdl, solve_kernel, grid, dim3(4 * solve_rows(H)), ssmem, p->stream, S));
     // two real H x H matvecs per pencil, each on two right-hand sides (re, im)
     p->toc(t, KC_SOLVE, 2.0 * Kx * 2.0 * H * H * 2.0);
     return check_launch(p, "rb solve");

@@ -10,6 +10,7 @@
 // every grid-to-coefficient reduction runs over Mz/2 folded samples ("fold").
 #pragma once
 #include "fft.cuh"
+#include "pdl.cuh"
 
 namespace spadj {
 namespace rbk {
@@ -77,6 +78,8 @@ constexpr int kTM = 1;  // columns per CTA
 __host__ __device__ inline int zmm_threads(int expand, int I) { return 2 * (expand ? I / 2 : I); }
 
 __global__ void __launch_bounds__(256) zmm_kernel(const __grid_constant__ ZJobs js) {
+  pdl_trigger();
+  pdl_wait();
   const ZJob& J = js.j[blockIdx.y];
   const int m = blockIdx.x;
   extern __shared__ double2 sb[];
@@ -226,6 +229,8 @@ struct XParams {
 };
 
 __global__ void __launch_bounds__(64) xfft_kernel(const __grid_constant__ XJobs js, XParams P) {
+  pdl_trigger();
+  pdl_wait();
   const XJob& J = js.j[blockIdx.y];
   const int row = blockIdx.x;
   const int L = P.L, Kx = P.Kx, Mx = P.Mx;
@@ -319,6 +324,8 @@ __global__ void __launch_bounds__(64) xfft_kernel(const __grid_constant__ XJobs 
 // cotangents of the 8 grid fields.
 __global__ void prod_vjp_kernel(const double* __restrict__ G, const double* __restrict__ gF, double* __restrict__ Gb,
                                 int npts) {
+  pdl_trigger();
+  pdl_wait();
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < npts; i += gridDim.x * blockDim.x) {
     const double u = G[0 * (size_t)npts + i], ux = G[1 * (size_t)npts + i], uz = G[2 * (size_t)npts + i];
     const double w = G[3 * (size_t)npts + i], wx = G[4 * (size_t)npts + i], wz = G[5 * (size_t)npts + i];
@@ -341,7 +348,9 @@ __global__ void prod_vjp_kernel(const double* __restrict__ G, const double* __re
 // the forward map) and once as [k][r] = Phi'[k][r] (read by the adjoint map), so that the
 // threads of a warp, which own consecutive output rows r, read consecutive addresses.  Dr,
 // Dc^H and the projection of the mean pencil onto real coefficients are applied on load and
-// store.  CTA = (pencil, class, half of the rows); thread = (row, quarter of the columns).
+// store.  CTA = (pencil, class, half of the rows); thread = (row, quarter of the columns).  The
+// CTA's rows of the operator are staged in shared memory by cp.async before the kernel waits
+// for its predecessor (programmatic dependent launch), so the staging overlaps that kernel.
 struct SolveArgs {
   const double2* in[4];
   double a[4];
@@ -356,15 +365,25 @@ struct SolveArgs {
 __host__ __device__ inline int solve_rows(int H) { return (H + 1) / 2; }
 
 __global__ void __launch_bounds__(1024) solve_kernel(const __grid_constant__ SolveArgs S) {
+  pdl_trigger();
   const int m = blockIdx.x, cls = blockIdx.y;
   const int N = S.N, Nh = N / 2, H = 3 * Nh, Kx = S.Kx;
   const int RH = solve_rows(H);
   const int r0 = blockIdx.z * RH;
-  extern __shared__ double2 sv[];  // v[H], then red[4][RH]
+  const int nr = min(RH, H - r0);
+  extern __shared__ double2 sv[];  // v[H], red[4][RH], then this CTA's operator rows ph[H][RH]
   double2* v = sv;
   double2* red = sv + H;
+  double* ph = reinterpret_cast<double*>(sv + H + 4 * RH);
   const double* blk = (S.transpose ? S.phiA : S.phiF) + ((size_t)m * 2 + cls) * H * H;
   const int tid = threadIdx.x, nt = blockDim.x;
+  // the operator does not depend on the preceding kernels: stage it while they finish
+  for (int idx = tid; idx < H * nr; idx += nt) {
+    const int k = idx / nr, rl = idx - k * nr;
+    cp_async8(ph + (size_t)k * RH + rl, blk + (size_t)k * H + r0 + rl);
+  }
+  cp_async_commit();
+  pdl_wait();
   // class index c -> (field f, mode n)
   for (int c = tid; c < H; c += nt) {
     const int f = c / Nh, h = c % Nh;
@@ -380,6 +399,7 @@ __global__ void __launch_bounds__(1024) solve_kernel(const __grid_constant__ Sol
     if (f == 0) x = make_double2(x.y, -x.x);        // times -i (Dr, or Dc^H)
     v[c] = x;
   }
+  cp_async_wait_all();
   __syncthreads();
   const int rl = tid % RH, q = tid / RH;
   const int r = r0 + rl;
@@ -389,13 +409,13 @@ __global__ void __launch_bounds__(1024) solve_kernel(const __grid_constant__ Sol
   if (r < H && q < 4) {
     int k = k0;
     for (; k + 1 < k1; k += 2) {
-      const double p0 = __ldg(blk + (size_t)k * H + r), p1 = __ldg(blk + (size_t)(k + 1) * H + r);
+      const double p0 = ph[(size_t)k * RH + rl], p1 = ph[(size_t)(k + 1) * RH + rl];
       const double2 x0 = v[k], x1 = v[k + 1];
       acc0.x = fma(p0, x0.x, acc0.x); acc0.y = fma(p0, x0.y, acc0.y);
       acc1.x = fma(p1, x1.x, acc1.x); acc1.y = fma(p1, x1.y, acc1.y);
     }
     if (k < k1) {
-      const double p0 = __ldg(blk + (size_t)k * H + r);
+      const double p0 = ph[(size_t)k * RH + rl];
       const double2 x0 = v[k];
       acc0.x = fma(p0, x0.x, acc0.x); acc0.y = fma(p0, x0.y, acc0.y);
     }
@@ -466,6 +486,8 @@ __global__ void sum_kernel(const double* __restrict__ partial, int n, double* __
 __global__ void axpy_kernel(double2* __restrict__ y, const double2* __restrict__ x0, double a0,
                             const double2* __restrict__ x1, double a1, const double2* __restrict__ x2, double a2,
                             size_t n) {
+  pdl_trigger();
+  pdl_wait();
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     double2 v = x0[i];
     double2 r = make_double2(a0 * v.x, a0 * v.y);
