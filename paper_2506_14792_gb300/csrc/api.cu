@@ -130,6 +130,10 @@ spadj_status spadj_set_option(spadj_problem* p, int option, int value) {
     p->pdl = value != 0;
     return SPADJ_OK;
   }
+  if (option == 7) {
+    p->fuse_columns = value != 0;
+    return SPADJ_OK;
+  }
   return spadj::kol_set_option(p->impl, p, option, value);
 }
 

@@ -112,7 +112,8 @@ struct Problem {
   std::string err;
   EqImpl* impl = nullptr;
   Timing timing;
-  bool pdl = false;  // programmatic dependent launch of consecutive kernels (spadj_set_option 6)
+  bool pdl = false;          // programmatic dependent launch of consecutive kernels (spadj_set_option 6)
+  bool fuse_columns = true;  // RB: fused fold + solve + expand cluster kernel (spadj_set_option 7)
   cudaEvent_t tic() {
     if (!timing.enabled) return nullptr;
     cudaEvent_t e = timing.get();

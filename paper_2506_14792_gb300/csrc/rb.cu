@@ -42,7 +42,8 @@ struct RB : EqImpl {
   // device work buffers
   DevBuf Z, G0, G1, dG, Gb, Fg, Y, f0, f1, df0, df1, x1, dx1, vb2, vb1, xb1, tmpx, tmpy, ybar, ybar2, cur, nxt,
       partial, Jdev, seedbuf, slots, traj_tmp;
-  size_t zsmem = 0, xsmem = 0, ssmem = 0;
+  size_t zsmem = 0, xsmem = 0, ssmem = 0, csmem = 0;
+  bool fused = false;  // fused column stage (rb_colstep_kernel) usable for these sizes
   // internal streams (joined to the caller's stream by events) and captured step graphs
   cudaStream_t gs = nullptr, gs2 = nullptr;
   cudaEvent_t evIn = nullptr, evOut = nullptr, evFork = nullptr, evJoin = nullptr;
@@ -173,6 +174,10 @@ struct RB : EqImpl {
     zsmem = (size_t)2 * 2 * (size_t)std::max(N, Mz / 2) * kTM * sizeof(double2);
     xsmem = sizeof(double2) * (4 * L + Kx);
     ssmem = sizeof(double2) * (H + 4 * solve_rows(H)) + sizeof(double) * (size_t)H * solve_rows(H);
+    csmem = colstep_smem(N, Mz);
+    fused = nonlinear && csmem <= 200 * 1024;
+    if (fused)
+      SPADJ_CUDA_TRY(p, cudaFuncSetAttribute(rb_colstep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csmem));
     if (ssmem > 48 * 1024)
       SPADJ_CUDA_TRY(p, cudaFuncSetAttribute(solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssmem));
     return SPADJ_OK;
@@ -247,6 +252,11 @@ struct RB : EqImpl {
     zj.n = 6;
     spadj_status s = launch_z(p, zj);
     if (s != SPADJ_OK) return s;
+    return c2r_fields(p, G);
+  }
+
+  // x-inverse FFTs of the six mixed columns in Z into the eight grid fields of G
+  spadj_status c2r_fields(Problem* p, DevBuf& G) {
     XJobs xj{};
     xj.j[0] = xc2r(mix(Z, 0), 0, 1.0, 1.0, grid(G, 0));
     xj.j[1] = xc2r(mix(Z, 0), 1, 1.0, 1.0, grid(G, 1));
@@ -263,10 +273,21 @@ struct RB : EqImpl {
   // the three grid products of F (or of its JVP when dGp is non-null) -> T-space state f
   // (products formed inside the x-forward FFT; g2c: 1/Mx r2c, then Gz)
   spadj_status g2c3(Problem* p, double2* f, const double* Gp, const double* dGp) {
+    spadj_status s = products_r2c(p, Gp, dGp);
+    if (s != SPADJ_OK) return s;
+    ZJobs zj{};
+    zj.expand = 0;
+    for (int q = 0; q < 3; ++q) zj.j[q] = zfold(mix(Y, q), gzF.as<double>(), 0, f + (size_t)q * Kx * N);
+    zj.n = 3;
+    return launch_z(p, zj);
+  }
+
+  // x-forward FFTs of the grid products F_q = -(u dx q + w dz q) (or their tangents when dGp is
+  // non-null) into the mixed rows Y; slots 0 u, 1 ux, 2 uz, 3 w, 4 wx, 5 wz, 6 tx, 7 tz
+  spadj_status products_r2c(Problem* p, const double* Gp, const double* dGp = nullptr) {
     XJobs xj{};
+    static const int qx[3] = {1, 4, 6};
     for (int q = 0; q < 3; ++q) {
-      // F_q = -(u dx q + w dz q), slots 0 u, 1 ux, 2 uz, 3 w, 4 wx, 5 wz, 6 tx, 7 tz
-      static const int qx[3] = {1, 4, 6};
       xj.j[q] = xr2c(nullptr, 0, nullptr, 0, 1.0 / Mx, 1.0 / Mx, mix(Y, q));
       xj.j[q].nprod = 2;
       xj.j[q].pa[0] = 0; xj.j[q].pb[0] = qx[q]; xj.j[q].ps[0] = -1.0;
@@ -277,13 +298,7 @@ struct RB : EqImpl {
       xj.j[q].nr = 1;
     }
     xj.n = 3;
-    spadj_status s = launch_x(p, xj);
-    if (s != SPADJ_OK) return s;
-    ZJobs zj{};
-    zj.expand = 0;
-    for (int q = 0; q < 3; ++q) zj.j[q] = zfold(mix(Y, q), gzF.as<double>(), 0, f + (size_t)q * Kx * N);
-    zj.n = 3;
-    return launch_z(p, zj);
+    return launch_x(p, xj);
   }
 
   int prod_grid() const { return (int)std::min<size_t>((npts + 255) / 256, 1024); }
@@ -392,8 +407,57 @@ struct RB : EqImpl {
     return check_launch(p, "rb solve");
   }
 
+  // ---- fused column stage -------------------------------------------------------------------
+  // f = Gz Y (into f), x = Phi (sum_t a_t in_t + af f) (into x), and, when expand, the six
+  // grid-field columns of x into Z; one cluster of two CTAs per pencil.
+  spadj_status colstep(Problem* p, double2* f, int nin, const double2* const* in, const double* a, double af,
+                       double2* x, bool expand) {
+    ColStepArgs S{};
+    for (int q = 0; q < 3; ++q) S.yin[q] = mix(Y, q);
+    S.gzF = gzF.as<double>();
+    S.f_out = f;
+    for (int t = 0; t < nin; ++t) { S.in[t] = in[t]; S.a[t] = a[t]; }
+    S.nin = nin;
+    S.af = af;
+    S.phiF = phiT.as<double>();
+    S.x_out = x;
+    S.czE = czE.as<double>();
+    S.cdzE = cdzE.as<double>();
+    S.zout = expand ? Z.as<double2>() : nullptr;
+    S.nmix = nmix;
+    S.Kx = Kx; S.N = N; S.Mz = Mz;
+    const int H = 3 * N / 2;
+    // algorithmic flops: fold 4 N (Mz/2) per field column, solve 2 classes x 4 H^2, expand as zflops
+    const double fl = (double)Kx * (3 * 4.0 * N * (Mz / 2) + 2 * 4.0 * H * H + (expand ? 6 * 4.0 * N * (Mz / 2) : 0.0));
+    cudaEvent_t t = p->tic();
+    rb_colstep_kernel<<<2 * Kx, 256, csmem, p->stream>>>(S);
+    p->toc(t, KC_FUSED, fl);
+    return check_launch(p, "rb colstep");
+  }
+  // stage 1 of the step from x0: grid fields G0 of x0, f0 = F(x0), x1 = Phi(x0 + dt A10 f0) and
+  // the grid fields G1 of x1
+  spadj_status stage1_fused(Problem* p, const double2* x0) {
+    spadj_status s = c2g_fields(p, x0, G0);
+    if (s != SPADJ_OK) return s;
+    if ((s = products_r2c(p, G0.as<double>())) != SPADJ_OK) return s;
+    const double2* in[1] = {x0};
+    double a[1] = {1.0};
+    if ((s = colstep(p, st(f0), 1, in, a, dt * A10, st(x1), true)) != SPADJ_OK) return s;
+    return c2r_fields(p, G1);
+  }
+
   // ---- RK222 steps ---------------------------------------------------------------------------
+  bool use_fused(Problem* p) const { return fused && p->fuse_columns; }
+
   spadj_status step_fwd(Problem* p, const double2* x0, double2* x2) {
+    if (use_fused(p)) {
+      spadj_status s = stage1_fused(p, x0);
+      if (s != SPADJ_OK) return s;
+      if ((s = products_r2c(p, G1.as<double>())) != SPADJ_OK) return s;
+      const double2* in[3] = {x0, st(f0), st(x1)};
+      double a[3] = {1.0 - cc, dt * (A20 - cc * A10), cc};
+      return colstep(p, st(f1), 3, in, a, dt * A21, x2, false);
+    }
     spadj_status s;
     if ((s = evalF(p, x0, st(f0), G0)) != SPADJ_OK) return s;
     { const double2* in[2] = {x0, st(f0)}; double a[2] = {1.0, dt * A10};
@@ -438,10 +502,14 @@ struct RB : EqImpl {
       if (s != SPADJ_OK) return s;
     }
     SPADJ_CUDA_TRY(p, cudaEventRecord(evJoin, gs2));
-    if ((s = evalF(p, x0, st(f0), G0)) != SPADJ_OK) return s;
-    { const double2* in[2] = {x0, st(f0)}; double a[2] = {1.0, dt * A10};
-      if ((s = solve(p, 0, 2, in, a, st(x1))) != SPADJ_OK) return s; }
-    if (nonlinear && (s = c2g_fields(p, st(x1), G1)) != SPADJ_OK) return s;
+    if (use_fused(p)) {
+      if ((s = stage1_fused(p, x0)) != SPADJ_OK) return s;
+    } else {
+      if ((s = evalF(p, x0, st(f0), G0)) != SPADJ_OK) return s;
+      { const double2* in[2] = {x0, st(f0)}; double a[2] = {1.0, dt * A10};
+        if ((s = solve(p, 0, 2, in, a, st(x1))) != SPADJ_OK) return s; }
+      if (nonlinear && (s = c2g_fields(p, st(x1), G1)) != SPADJ_OK) return s;
+    }
     SPADJ_CUDA_TRY(p, cudaStreamWaitEvent(p->stream, evJoin, 0));
     // xb1 = c vb2 + (dF/dx1)^dagger (dt A21 vb2)
     { const double2* fb[1] = {st(vb2)}; double al[1] = {dt * A21};

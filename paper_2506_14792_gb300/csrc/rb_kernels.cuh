@@ -9,6 +9,8 @@
 // so every output pair (j, Mz-1-j) costs one half-length dot product ("expand"), and
 // every grid-to-coefficient reduction runs over Mz/2 folded samples ("fold").
 #pragma once
+#include <cooperative_groups.h>
+
 #include "fft.cuh"
 #include "pdl.cuh"
 
@@ -432,6 +434,152 @@ __global__ void __launch_bounds__(1024) solve_kernel(const __grid_constant__ Sol
     if (!S.transpose && m == 0) acc.y = 0.0;        // projection onto real mean pencil
     S.out[((size_t)f * Kx + m) * N + n] = acc;
   }
+}
+
+// Fused column stage of the RK222 forward step for one x-mode pencil, as a cluster of two
+// CTAs (one per z-parity class, cluster rank = class):
+//   1. fold: f = Gz Y for the three grid-product rows Y_q (mixed [Mz][Kx]) restricted to the
+//      modes of this class (the reflection-folded Chebyshev reduction of zmm_kernel);
+//   2. solve: x = Phi (sum_t a_t in_t + af f) for this class (solve_kernel's arithmetic, with
+//      the class block of Phi' staged in shared memory by cp.async during the fold);
+//   3. when zout is set: the two CTAs exchange their halves of x through distributed shared
+//      memory and each expands three of the six grid fields (u, dz u, w, dz w, theta,
+//      dz theta; class 0 the values, class 1 the z-derivatives) into zout[6][Mz][Kx].
+// f and x are also written in the state layout [3][Kx][N].  Replaces zmm fold + solve +
+// zmm expand (three launches) by one.
+struct ColStepArgs {
+  const double2* yin[3];  // grid products after the x-forward FFT, mixed layout
+  const double* gzF;      // N x (Mz/2) fold matrix
+  double2* f_out;
+  const double2* in[4];
+  double a[4];
+  int nin;
+  double af;
+  const double* phiF;     // [Kx][2][H][H] as [k][r]
+  double2* x_out;
+  const double* czE;      // (Mz/2) x N
+  const double* cdzE;     // (Mz/2) x N (z-derivative parity)
+  double2* zout;          // nullable
+  size_t nmix;
+  int Kx, N, Mz;
+};
+
+__host__ __device__ inline size_t colstep_smem(int N, int Mz) {
+  const int H = 3 * N / 2;
+  return sizeof(double) * (size_t)H * H + sizeof(double2) * (size_t)(3 * (Mz / 2) + 3 * N + H + H);
+}
+
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256) rb_colstep_kernel(const __grid_constant__ ColStepArgs S) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int cls = (int)cluster.block_rank();
+  const int m = blockIdx.x >> 1;
+  const int N = S.N, Nh = N / 2, H = 3 * Nh, Kx = S.Kx, Mz = S.Mz, Mh = Mz / 2;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  extern __shared__ double2 cs[];
+  double* ph = reinterpret_cast<double*>(cs);          // [H][H] as [k][r]
+  double2* sd = cs + (size_t)H * H / 2;                // [3][Mh] folded samples (s or d)
+  double2* fs = sd + 3 * Mh;                           // [3][N] f (this class's modes)
+  double2* v = fs + 3 * N;                             // [H] right-hand side (class order)
+  double2* xc = v + H;                                 // [H] solution (class order)
+  const double* blk = S.phiF + ((size_t)m * 2 + cls) * H * H;
+  pdl_trigger();
+  for (int idx = tid; idx < H * H / 2; idx += nt)
+    cp_async16(reinterpret_cast<double2*>(ph) + idx, reinterpret_cast<const double2*>(blk) + idx);
+  cp_async_commit();
+  pdl_wait();
+  // class-local mode of field q: parity (q == 0 ? cls : 1 - cls); fold with s (even) or d (odd)
+  for (int idx = tid; idx < 3 * Mh; idx += nt) {
+    const int q = idx / Mh, j = idx - q * Mh;
+    const int par = (q == 0) ? cls : 1 - cls;
+    const double2 a = S.yin[q][(size_t)j * Kx + m], b = S.yin[q][(size_t)(Mz - 1 - j) * Kx + m];
+    sd[idx] = par == 0 ? make_double2(a.x + b.x, a.y + b.y) : make_double2(a.x - b.x, a.y - b.y);
+  }
+  __syncthreads();
+  for (int idx = tid; idx < 3 * Nh; idx += nt) {
+    const int q = idx / Nh, h = idx - q * Nh;
+    const int n = 2 * h + ((q == 0) ? cls : 1 - cls);
+    const double* g = S.gzF + (size_t)n * Mh;
+    const double2* w = sd + q * Mh;
+    double2 a0 = make_double2(0.0, 0.0), a1 = make_double2(0.0, 0.0);
+    int j = 0;
+    for (; j + 1 < Mh; j += 2) {
+      const double g0 = __ldg(g + j), g1 = __ldg(g + j + 1);
+      a0.x = fma(g0, w[j].x, a0.x); a0.y = fma(g0, w[j].y, a0.y);
+      a1.x = fma(g1, w[j + 1].x, a1.x); a1.y = fma(g1, w[j + 1].y, a1.y);
+    }
+    if (j < Mh) {
+      const double g0 = __ldg(g + j);
+      a0.x = fma(g0, w[j].x, a0.x); a0.y = fma(g0, w[j].y, a0.y);
+    }
+    const double2 f = cadd(a0, a1);
+    fs[q * N + n] = f;
+    S.f_out[((size_t)q * Kx + m) * N + n] = f;
+  }
+  __syncthreads();
+  for (int c = tid; c < H; c += nt) {
+    const int q = c / Nh, h = c % Nh;
+    const int n = 2 * h + ((q == 0) ? cls : 1 - cls);
+    const size_t off = ((size_t)q * Kx + m) * N + n;
+    const double2 f = fs[q * N + n];
+    double2 x = make_double2(S.af * f.x, S.af * f.y);
+    for (int t = 0; t < S.nin; ++t) {
+      const double2 y = S.in[t][off];
+      x.x = fma(S.a[t], y.x, x.x);
+      x.y = fma(S.a[t], y.y, x.y);
+    }
+    if (q == 0) x = make_double2(x.y, -x.x);  // times -i (Dr)
+    v[c] = x;
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  for (int r = tid; r < H; r += nt) {
+    double2 a0 = make_double2(0.0, 0.0), a1 = make_double2(0.0, 0.0);
+    int k = 0;
+    for (; k + 1 < H; k += 2) {
+      const double p0 = ph[(size_t)k * H + r], p1 = ph[(size_t)(k + 1) * H + r];
+      const double2 x0 = v[k], x1 = v[k + 1];
+      a0.x = fma(p0, x0.x, a0.x); a0.y = fma(p0, x0.y, a0.y);
+      a1.x = fma(p1, x1.x, a1.x); a1.y = fma(p1, x1.y, a1.y);
+    }
+    if (k < H) {
+      const double p0 = ph[(size_t)k * H + r];
+      a0.x = fma(p0, v[k].x, a0.x); a0.y = fma(p0, v[k].y, a0.y);
+    }
+    double2 acc = cadd(a0, a1);
+    const int q = r / Nh, h = r % Nh;
+    const int n = 2 * h + ((q == 0) ? cls : 1 - cls);
+    if (q == 0) acc = make_double2(-acc.y, acc.x);  // times i (Dc)
+    if (m == 0) acc.y = 0.0;                        // projection onto the real mean pencil
+    xc[r] = acc;
+    S.x_out[((size_t)q * Kx + m) * N + n] = acc;
+  }
+  if (!S.zout) return;
+  cluster.sync();  // both halves of x are in shared memory
+  const double2* xo = cluster.map_shared_rank(xc, 1 - cls);
+  // expand: field q, value (cls 0) or z-derivative (cls 1); even/odd mode sums from the class
+  // that holds them (modes of parity cls' are in CTA cls' = (q == 0 ? par : 1 - par))
+  const double* Cm = cls == 0 ? S.czE : S.cdzE;
+  for (int idx = tid; idx < 3 * Mh; idx += nt) {
+    const int q = idx / Mh, j = idx - q * Mh;
+    const double* crow = Cm + (size_t)j * N;
+    // modes 2h (even) live in CTA (q == 0 ? 0 : 1), modes 2h + 1 (odd) in the other one
+    const int even_cta = (q == 0) ? 0 : 1;
+    const double2* xe = (even_cta == cls ? xc : xo) + q * Nh;
+    const double2* xd = (even_cta == cls ? xo : xc) + q * Nh;
+    double2 E = make_double2(0.0, 0.0), O = make_double2(0.0, 0.0);
+    for (int h = 0; h < Nh; ++h) {
+      const double ce = __ldg(crow + 2 * h), co = __ldg(crow + 2 * h + 1);
+      const double2 e = xe[h], o = xd[h];
+      E.x = fma(ce, e.x, E.x); E.y = fma(ce, e.y, E.y);
+      O.x = fma(co, o.x, O.x); O.y = fma(co, o.y, O.y);
+    }
+    const double se = cls == 0 ? 1.0 : -1.0;  // reflection parity of T_n (values) or dT_n/dz
+    double2* out = S.zout + (size_t)(2 * q + cls) * S.nmix;
+    out[(size_t)j * Kx + m] = make_double2(E.x + O.x, E.y + O.y);
+    out[(size_t)(Mz - 1 - j) * Kx + m] = make_double2(se * (E.x - O.x), se * (E.y - O.y));
+  }
+  cluster.sync();  // the partner's shared memory stays alive until both expansions are done
 }
 
 // Kinetic energy J = (Lx/2) sum_{u,w} sum_m w_m c_m^H G c_m and its gradient

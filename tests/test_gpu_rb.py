@@ -189,3 +189,20 @@ def test_full_config_properties():
         eps = 1e-4 * np.linalg.norm(s0) / np.linalg.norm(d)
         fd = (Jof(s0 + eps * d) - Jof(s0 - eps * d)) / (2 * eps)
         assert abs(fd - imex.inner(gh, d)) <= 1e-6 * abs(fd)
+
+
+def test_fused_column_stage_matches_separate_kernels():
+    """The fused fold + solve + expand cluster kernel and the three separate kernels compute the
+    same gradient (the summation order of the fold differs, so agreement is to rounding)."""
+    Nx, Nz, n = 32, 16, 8
+    o = orb.RayleighBenard(Nx, Nz, 1e6)
+    s0 = synthetic.rb_ic(Nx, Nz, seed=2, amp=0.3)
+    out = []
+    for fuse in (1, 0):
+        p = gpu_problem(Nx, Nz, dt=1e-2)
+        p.set_option(7, fuse)
+        g = _z((3, o.Kx, o.N))
+        J = p.gradient(dev(s0), n, g, ckpt_slots=3)
+        out.append((J[0], host(g)))
+    assert abs(out[0][0] - out[1][0]) <= 1e-13 * abs(out[1][0])
+    assert rel_err(out[0][1], out[1][1]) < 1e-12
