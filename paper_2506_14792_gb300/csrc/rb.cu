@@ -40,16 +40,27 @@ struct RB : EqImpl {
   // device constants
   DevBuf wm, czE, cdzE, gzF, gzTE, czTF, cdzTF, gmat, phi, phiT;
   // device work buffers
-  DevBuf Z, G0, G1, dG, Gb, Fg, Y, f0, f1, df0, df1, x1, dx1, vb2, vb1, xb1, tmpx, tmpy, ybar, ybar2, cur, nxt,
-      partial, Jdev, seedbuf, slots, traj_tmp;
+  DevBuf dG, Gb, Fg, df0, df1, dx1, vb2, vb1, xb1, tmpx, tmpy, ybar, ybar2, cur, nxt, curB, nxtB, partial, Jdev,
+      seedbuf, slots, traj_tmp;
+  // Buffers of one forward step.  Lane 0 runs the forward sweep and the adjoint steps, lane 1
+  // the recomputation of checkpointed segments, concurrently on its own stream.
+  struct WS {
+    DevBuf Z, Y, G0, G1, f0, f1, x1;
+  };
+  WS ws[2];
+  WS* w = &ws[0];
   size_t zsmem = 0, xsmem = 0, ssmem = 0, csmem = 0;
   bool fused = false;  // fused column stage (rb_colstep_kernel) usable for these sizes
   // internal streams (joined to the caller's stream by events) and captured step graphs
-  cudaStream_t gs = nullptr, gs2 = nullptr;
+  cudaStream_t gs = nullptr, gs2 = nullptr, gsB = nullptr;
   cudaEvent_t evIn = nullptr, evOut = nullptr, evFork = nullptr, evJoin = nullptr;
+  cudaEvent_t evReady = nullptr, evFree = nullptr, evBdone = nullptr;  // lane handoffs
+  cudaEvent_t evAdj[2] = {nullptr, nullptr}, evCopied[2] = {nullptr, nullptr};
   cudaGraphExec_t gFwd[2] = {nullptr, nullptr};
+  cudaGraphExec_t gFwdB[2] = {nullptr, nullptr};  // lane 1 forward step graphs
   cudaGraphExec_t gAdj[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
   double2* Sb[2] = {nullptr, nullptr};  // state ping-pong buffers
+  double2* SbB[2] = {nullptr, nullptr};  // lane 1 state ping-pong buffers
   double2* Yb[2] = {nullptr, nullptr};  // cotangent ping-pong buffers
 
   size_t state_len(int which) const override {
@@ -154,20 +165,26 @@ struct RB : EqImpl {
     xp.WM = wm.as<double2>();
     // work buffers
     const size_t sb = sizeof(double2) * ns, mb = sizeof(double2) * nmix, gb = sizeof(double) * npts;
-    SPADJ_CUDA_TRY(p, Z.ensure(6 * mb));
-    SPADJ_CUDA_TRY(p, Y.ensure(6 * mb));
-    SPADJ_CUDA_TRY(p, G0.ensure(8 * gb));
-    SPADJ_CUDA_TRY(p, G1.ensure(8 * gb));
+    for (WS& l : ws) {
+      SPADJ_CUDA_TRY(p, l.Z.ensure(6 * mb));
+      SPADJ_CUDA_TRY(p, l.Y.ensure(6 * mb));
+      SPADJ_CUDA_TRY(p, l.G0.ensure(8 * gb));
+      SPADJ_CUDA_TRY(p, l.G1.ensure(8 * gb));
+      for (DevBuf* b : {&l.f0, &l.f1, &l.x1}) SPADJ_CUDA_TRY(p, b->ensure(sb));
+    }
     SPADJ_CUDA_TRY(p, dG.ensure(8 * gb));
     SPADJ_CUDA_TRY(p, Gb.ensure(8 * gb));
     SPADJ_CUDA_TRY(p, Fg.ensure(3 * gb));
-    for (DevBuf* b : {&f0, &f1, &df0, &df1, &x1, &dx1, &vb2, &vb1, &xb1, &tmpx, &tmpy, &ybar, &ybar2, &cur, &nxt, &seedbuf})
+    for (DevBuf* b : {&df0, &df1, &dx1, &vb2, &vb1, &xb1, &tmpx, &tmpy, &ybar, &ybar2, &cur, &nxt, &curB, &nxtB, &seedbuf})
       SPADJ_CUDA_TRY(p, b->ensure(sb));
     Sb[0] = cur.as<double2>(); Sb[1] = nxt.as<double2>();
+    SbB[0] = curB.as<double2>(); SbB[1] = nxtB.as<double2>();
     Yb[0] = ybar.as<double2>(); Yb[1] = ybar2.as<double2>();
     SPADJ_CUDA_TRY(p, cudaStreamCreateWithFlags(&gs, cudaStreamNonBlocking));
     SPADJ_CUDA_TRY(p, cudaStreamCreateWithFlags(&gs2, cudaStreamNonBlocking));
-    for (cudaEvent_t* e : {&evIn, &evOut, &evFork, &evJoin})
+    SPADJ_CUDA_TRY(p, cudaStreamCreateWithFlags(&gsB, cudaStreamNonBlocking));
+    for (cudaEvent_t* e : {&evIn, &evOut, &evFork, &evJoin, &evReady, &evFree, &evBdone, &evAdj[0], &evAdj[1],
+                           &evCopied[0], &evCopied[1]})
       SPADJ_CUDA_TRY(p, cudaEventCreateWithFlags(e, cudaEventDisableTiming));
     SPADJ_CUDA_TRY(p, partial.ensure(sizeof(double) * Kx));
     SPADJ_CUDA_TRY(p, Jdev.ensure(sizeof(double)));
@@ -241,14 +258,14 @@ struct RB : EqImpl {
     ZJobs zj{};
     zj.expand = 1;
     const double2* u = x;
-    const double2* w = x + (size_t)Kx * N;
+    const double2* wf = x + (size_t)Kx * N;
     const double2* t = x + (size_t)2 * Kx * N;
-    zj.j[0] = zexpand(u, czE.as<double>(), 0, mix(Z, 0));
-    zj.j[1] = zexpand(u, cdzE.as<double>(), 1, mix(Z, 1));
-    zj.j[2] = zexpand(w, czE.as<double>(), 0, mix(Z, 2));
-    zj.j[3] = zexpand(w, cdzE.as<double>(), 1, mix(Z, 3));
-    zj.j[4] = zexpand(t, czE.as<double>(), 0, mix(Z, 4));
-    zj.j[5] = zexpand(t, cdzE.as<double>(), 1, mix(Z, 5));
+    zj.j[0] = zexpand(u, czE.as<double>(), 0, mix(w->Z, 0));
+    zj.j[1] = zexpand(u, cdzE.as<double>(), 1, mix(w->Z, 1));
+    zj.j[2] = zexpand(wf, czE.as<double>(), 0, mix(w->Z, 2));
+    zj.j[3] = zexpand(wf, cdzE.as<double>(), 1, mix(w->Z, 3));
+    zj.j[4] = zexpand(t, czE.as<double>(), 0, mix(w->Z, 4));
+    zj.j[5] = zexpand(t, cdzE.as<double>(), 1, mix(w->Z, 5));
     zj.n = 6;
     spadj_status s = launch_z(p, zj);
     if (s != SPADJ_OK) return s;
@@ -258,14 +275,14 @@ struct RB : EqImpl {
   // x-inverse FFTs of the six mixed columns in Z into the eight grid fields of G
   spadj_status c2r_fields(Problem* p, DevBuf& G) {
     XJobs xj{};
-    xj.j[0] = xc2r(mix(Z, 0), 0, 1.0, 1.0, grid(G, 0));
-    xj.j[1] = xc2r(mix(Z, 0), 1, 1.0, 1.0, grid(G, 1));
-    xj.j[2] = xc2r(mix(Z, 1), 0, 1.0, 1.0, grid(G, 2));
-    xj.j[3] = xc2r(mix(Z, 2), 0, 1.0, 1.0, grid(G, 3));
-    xj.j[4] = xc2r(mix(Z, 2), 1, 1.0, 1.0, grid(G, 4));
-    xj.j[5] = xc2r(mix(Z, 3), 0, 1.0, 1.0, grid(G, 5));
-    xj.j[6] = xc2r(mix(Z, 4), 1, 1.0, 1.0, grid(G, 6));
-    xj.j[7] = xc2r(mix(Z, 5), 0, 1.0, 1.0, grid(G, 7));
+    xj.j[0] = xc2r(mix(w->Z, 0), 0, 1.0, 1.0, grid(G, 0));
+    xj.j[1] = xc2r(mix(w->Z, 0), 1, 1.0, 1.0, grid(G, 1));
+    xj.j[2] = xc2r(mix(w->Z, 1), 0, 1.0, 1.0, grid(G, 2));
+    xj.j[3] = xc2r(mix(w->Z, 2), 0, 1.0, 1.0, grid(G, 3));
+    xj.j[4] = xc2r(mix(w->Z, 2), 1, 1.0, 1.0, grid(G, 4));
+    xj.j[5] = xc2r(mix(w->Z, 3), 0, 1.0, 1.0, grid(G, 5));
+    xj.j[6] = xc2r(mix(w->Z, 4), 1, 1.0, 1.0, grid(G, 6));
+    xj.j[7] = xc2r(mix(w->Z, 5), 0, 1.0, 1.0, grid(G, 7));
     xj.n = 8;
     return launch_x(p, xj);
   }
@@ -277,7 +294,7 @@ struct RB : EqImpl {
     if (s != SPADJ_OK) return s;
     ZJobs zj{};
     zj.expand = 0;
-    for (int q = 0; q < 3; ++q) zj.j[q] = zfold(mix(Y, q), gzF.as<double>(), 0, f + (size_t)q * Kx * N);
+    for (int q = 0; q < 3; ++q) zj.j[q] = zfold(mix(w->Y, q), gzF.as<double>(), 0, f + (size_t)q * Kx * N);
     zj.n = 3;
     return launch_z(p, zj);
   }
@@ -288,7 +305,7 @@ struct RB : EqImpl {
     XJobs xj{};
     static const int qx[3] = {1, 4, 6};
     for (int q = 0; q < 3; ++q) {
-      xj.j[q] = xr2c(nullptr, 0, nullptr, 0, 1.0 / Mx, 1.0 / Mx, mix(Y, q));
+      xj.j[q] = xr2c(nullptr, 0, nullptr, 0, 1.0 / Mx, 1.0 / Mx, mix(w->Y, q));
       xj.j[q].nprod = 2;
       xj.j[q].pa[0] = 0; xj.j[q].pb[0] = qx[q]; xj.j[q].ps[0] = -1.0;
       xj.j[q].pa[1] = 3; xj.j[q].pb[1] = qx[q] + 1; xj.j[q].ps[1] = -1.0;
@@ -342,13 +359,13 @@ struct RB : EqImpl {
           j.deriv[t] = 0;
         }
         j.nterm = nfb;
-        j.out = mix(Z, q); j.I = Mz; j.K = N; j.ik = 1; j.im = N; j.oi = Kx; j.om = 1;
+        j.out = mix(w->Z, q); j.I = Mz; j.K = N; j.ik = 1; j.im = N; j.oi = Kx; j.om = 1;
         zj.j[q] = j;
       }
       zj.n = 3;
       if ((s = launch_z(p, zj)) != SPADJ_OK) return s;
       XJobs xj{};
-      for (int q = 0; q < 3; ++q) xj.j[q] = xc2r(mix(Z, q), 0, 1.0 / Mx, 0.5 / Mx, grid(Fg, q));
+      for (int q = 0; q < 3; ++q) xj.j[q] = xc2r(mix(w->Z, q), 0, 1.0 / Mx, 0.5 / Mx, grid(Fg, q));
       xj.n = 3;
       if ((s = launch_x(p, xj)) != SPADJ_OK) return s;
       cudaEvent_t tp = p->tic();
@@ -359,12 +376,12 @@ struct RB : EqImpl {
       if ((s = check_launch(p, "rb prod vjp")) != SPADJ_OK) return s;
       // (T^-1)^dagger in x: r2c with factor 2 on k >= 1, x-derivative adjoint -ik
       XJobs xb{};
-      xb.j[0] = xr2c(grid(Gb, 0), 0, grid(Gb, 1), 2, 1.0, 2.0, mix(Y, 0));  // a_u
-      xb.j[1] = xr2c(grid(Gb, 2), 0, nullptr, 0, 1.0, 2.0, mix(Y, 1));      // b_u
-      xb.j[2] = xr2c(grid(Gb, 3), 0, grid(Gb, 4), 2, 1.0, 2.0, mix(Y, 2));  // a_w
-      xb.j[3] = xr2c(grid(Gb, 5), 0, nullptr, 0, 1.0, 2.0, mix(Y, 3));      // b_w
-      xb.j[4] = xr2c(grid(Gb, 6), 2, nullptr, 0, 1.0, 2.0, mix(Y, 4));      // a_t
-      xb.j[5] = xr2c(grid(Gb, 7), 0, nullptr, 0, 1.0, 2.0, mix(Y, 5));      // b_t
+      xb.j[0] = xr2c(grid(Gb, 0), 0, grid(Gb, 1), 2, 1.0, 2.0, mix(w->Y, 0));  // a_u
+      xb.j[1] = xr2c(grid(Gb, 2), 0, nullptr, 0, 1.0, 2.0, mix(w->Y, 1));      // b_u
+      xb.j[2] = xr2c(grid(Gb, 3), 0, grid(Gb, 4), 2, 1.0, 2.0, mix(w->Y, 2));  // a_w
+      xb.j[3] = xr2c(grid(Gb, 5), 0, nullptr, 0, 1.0, 2.0, mix(w->Y, 3));      // b_w
+      xb.j[4] = xr2c(grid(Gb, 6), 2, nullptr, 0, 1.0, 2.0, mix(w->Y, 4));      // a_t
+      xb.j[5] = xr2c(grid(Gb, 7), 0, nullptr, 0, 1.0, 2.0, mix(w->Y, 5));      // b_t
       xb.n = 6;
       if ((s = launch_x(p, xb)) != SPADJ_OK) return s;
     }
@@ -374,11 +391,11 @@ struct RB : EqImpl {
     for (int q = 0; q < 3; ++q) {
       ZJob j{};
       if (nonlinear) {
-        j.in[0] = mix(Y, 2 * q); j.mat[0] = czTF.as<double>(); j.alpha[0] = 1.0; j.deriv[0] = 0;
-        j.in[1] = mix(Y, 2 * q + 1); j.mat[1] = cdzTF.as<double>(); j.alpha[1] = 1.0; j.deriv[1] = 1;
+        j.in[0] = mix(w->Y, 2 * q); j.mat[0] = czTF.as<double>(); j.alpha[0] = 1.0; j.deriv[0] = 0;
+        j.in[1] = mix(w->Y, 2 * q + 1); j.mat[1] = cdzTF.as<double>(); j.alpha[1] = 1.0; j.deriv[1] = 1;
         j.nterm = 2;
       } else {
-        j.in[0] = mix(Y, 0); j.mat[0] = czTF.as<double>(); j.alpha[0] = 0.0; j.nterm = 1;
+        j.in[0] = mix(w->Y, 0); j.mat[0] = czTF.as<double>(); j.alpha[0] = 0.0; j.nterm = 1;
       }
       for (int a = 0; a < nadd; ++a) { j.add[a] = add[a] + (size_t)q * Kx * N; j.beta[a] = beta[a]; }
       j.nadd = nadd;
@@ -388,7 +405,7 @@ struct RB : EqImpl {
     zf.n = 3;
     if (!nonlinear) {
       // alpha = 0 term reads a mixed buffer that must be finite
-      cudaMemsetAsync(Y.ptr, 0, sizeof(double2) * nmix, p->stream);
+      cudaMemsetAsync(w->Y.ptr, 0, sizeof(double2) * nmix, p->stream);
     }
     return launch_z(p, zf);
   }
@@ -413,7 +430,7 @@ struct RB : EqImpl {
   spadj_status colstep(Problem* p, double2* f, int nin, const double2* const* in, const double* a, double af,
                        double2* x, bool expand) {
     ColStepArgs S{};
-    for (int q = 0; q < 3; ++q) S.yin[q] = mix(Y, q);
+    for (int q = 0; q < 3; ++q) S.yin[q] = mix(w->Y, q);
     S.gzF = gzF.as<double>();
     S.f_out = f;
     for (int t = 0; t < nin; ++t) { S.in[t] = in[t]; S.a[t] = a[t]; }
@@ -423,7 +440,7 @@ struct RB : EqImpl {
     S.x_out = x;
     S.czE = czE.as<double>();
     S.cdzE = cdzE.as<double>();
-    S.zout = expand ? Z.as<double2>() : nullptr;
+    S.zout = expand ? w->Z.as<double2>() : nullptr;
     S.nmix = nmix;
     S.Kx = Kx; S.N = N; S.Mz = Mz;
     const int H = 3 * N / 2;
@@ -437,13 +454,13 @@ struct RB : EqImpl {
   // stage 1 of the step from x0: grid fields G0 of x0, f0 = F(x0), x1 = Phi(x0 + dt A10 f0) and
   // the grid fields G1 of x1
   spadj_status stage1_fused(Problem* p, const double2* x0) {
-    spadj_status s = c2g_fields(p, x0, G0);
+    spadj_status s = c2g_fields(p, x0, w->G0);
     if (s != SPADJ_OK) return s;
-    if ((s = products_r2c(p, G0.as<double>())) != SPADJ_OK) return s;
+    if ((s = products_r2c(p, w->G0.as<double>())) != SPADJ_OK) return s;
     const double2* in[1] = {x0};
     double a[1] = {1.0};
-    if ((s = colstep(p, st(f0), 1, in, a, dt * A10, st(x1), true)) != SPADJ_OK) return s;
-    return c2r_fields(p, G1);
+    if ((s = colstep(p, st(w->f0), 1, in, a, dt * A10, st(w->x1), true)) != SPADJ_OK) return s;
+    return c2r_fields(p, w->G1);
   }
 
   // ---- RK222 steps ---------------------------------------------------------------------------
@@ -453,33 +470,33 @@ struct RB : EqImpl {
     if (use_fused(p)) {
       spadj_status s = stage1_fused(p, x0);
       if (s != SPADJ_OK) return s;
-      if ((s = products_r2c(p, G1.as<double>())) != SPADJ_OK) return s;
-      const double2* in[3] = {x0, st(f0), st(x1)};
+      if ((s = products_r2c(p, w->G1.as<double>())) != SPADJ_OK) return s;
+      const double2* in[3] = {x0, st(w->f0), st(w->x1)};
       double a[3] = {1.0 - cc, dt * (A20 - cc * A10), cc};
-      return colstep(p, st(f1), 3, in, a, dt * A21, x2, false);
+      return colstep(p, st(w->f1), 3, in, a, dt * A21, x2, false);
     }
     spadj_status s;
-    if ((s = evalF(p, x0, st(f0), G0)) != SPADJ_OK) return s;
-    { const double2* in[2] = {x0, st(f0)}; double a[2] = {1.0, dt * A10};
-      if ((s = solve(p, 0, 2, in, a, st(x1))) != SPADJ_OK) return s; }
-    if ((s = evalF(p, st(x1), st(f1), G1)) != SPADJ_OK) return s;
-    const double2* in[4] = {x0, st(f0), st(f1), st(x1)};
+    if ((s = evalF(p, x0, st(w->f0), w->G0)) != SPADJ_OK) return s;
+    { const double2* in[2] = {x0, st(w->f0)}; double a[2] = {1.0, dt * A10};
+      if ((s = solve(p, 0, 2, in, a, st(w->x1))) != SPADJ_OK) return s; }
+    if ((s = evalF(p, st(w->x1), st(w->f1), w->G1)) != SPADJ_OK) return s;
+    const double2* in[4] = {x0, st(w->f0), st(w->f1), st(w->x1)};
     double a[4] = {1.0 - cc, dt * (A20 - cc * A10), dt * A21, cc};
     return solve(p, 0, 4, in, a, x2);
   }
 
   spadj_status step_tan(Problem* p, const double2* x0, const double2* dx0, double2* x2, double2* dx2) {
     spadj_status s;
-    if ((s = evalF(p, x0, st(f0), G0)) != SPADJ_OK) return s;
-    if ((s = evalJvp(p, G0, dx0, st(df0))) != SPADJ_OK) return s;
-    { const double2* in[2] = {x0, st(f0)}; double a[2] = {1.0, dt * A10};
-      if ((s = solve(p, 0, 2, in, a, st(x1))) != SPADJ_OK) return s; }
+    if ((s = evalF(p, x0, st(w->f0), w->G0)) != SPADJ_OK) return s;
+    if ((s = evalJvp(p, w->G0, dx0, st(df0))) != SPADJ_OK) return s;
+    { const double2* in[2] = {x0, st(w->f0)}; double a[2] = {1.0, dt * A10};
+      if ((s = solve(p, 0, 2, in, a, st(w->x1))) != SPADJ_OK) return s; }
     { const double2* in[2] = {dx0, st(df0)}; double a[2] = {1.0, dt * A10};
       if ((s = solve(p, 0, 2, in, a, st(dx1))) != SPADJ_OK) return s; }
-    if ((s = evalF(p, st(x1), st(f1), G1)) != SPADJ_OK) return s;
-    if ((s = evalJvp(p, G1, st(dx1), st(df1))) != SPADJ_OK) return s;
+    if ((s = evalF(p, st(w->x1), st(w->f1), w->G1)) != SPADJ_OK) return s;
+    if ((s = evalJvp(p, w->G1, st(dx1), st(df1))) != SPADJ_OK) return s;
     double a[4] = {1.0 - cc, dt * (A20 - cc * A10), dt * A21, cc};
-    { const double2* in[4] = {x0, st(f0), st(f1), st(x1)};
+    { const double2* in[4] = {x0, st(w->f0), st(w->f1), st(w->x1)};
       if ((s = solve(p, 0, 4, in, a, x2)) != SPADJ_OK) return s; }
     const double2* in[4] = {dx0, st(df0), st(df1), st(dx1)};
     return solve(p, 0, 4, in, a, dx2);
@@ -505,16 +522,16 @@ struct RB : EqImpl {
     if (use_fused(p)) {
       if ((s = stage1_fused(p, x0)) != SPADJ_OK) return s;
     } else {
-      if ((s = evalF(p, x0, st(f0), G0)) != SPADJ_OK) return s;
-      { const double2* in[2] = {x0, st(f0)}; double a[2] = {1.0, dt * A10};
-        if ((s = solve(p, 0, 2, in, a, st(x1))) != SPADJ_OK) return s; }
-      if (nonlinear && (s = c2g_fields(p, st(x1), G1)) != SPADJ_OK) return s;
+      if ((s = evalF(p, x0, st(w->f0), w->G0)) != SPADJ_OK) return s;
+      { const double2* in[2] = {x0, st(w->f0)}; double a[2] = {1.0, dt * A10};
+        if ((s = solve(p, 0, 2, in, a, st(w->x1))) != SPADJ_OK) return s; }
+      if (nonlinear && (s = c2g_fields(p, st(w->x1), w->G1)) != SPADJ_OK) return s;
     }
     SPADJ_CUDA_TRY(p, cudaStreamWaitEvent(p->stream, evJoin, 0));
     // xb1 = c vb2 + (dF/dx1)^dagger (dt A21 vb2)
     { const double2* fb[1] = {st(vb2)}; double al[1] = {dt * A21};
       const double2* ad[1] = {st(vb2)}; double be[1] = {cc};
-      if ((s = evalVjp(p, G1, 1, fb, al, 1, ad, be, st(xb1))) != SPADJ_OK) return s; }
+      if ((s = evalVjp(p, w->G1, 1, fb, al, 1, ad, be, st(xb1))) != SPADJ_OK) return s; }
     { const double2* in[1] = {st(xb1)}; double a[1] = {1.0};
       if ((s = solve(p, 1, 1, in, a, st(vb1))) != SPADJ_OK) return s; }
     // xb0 = (1-c) vb2 + vb1 + (dF/dx0)^dagger (dt(A20 - c A10) vb2 + dt A10 vb1)
@@ -522,7 +539,7 @@ struct RB : EqImpl {
     double al[2] = {dt * (A20 - cc * A10), dt * A10};
     const double2* ad[2] = {st(vb2), st(vb1)};
     double be[2] = {1.0 - cc, 1.0};
-    return evalVjp(p, G0, 2, fb, al, 2, ad, be, xb0);
+    return evalVjp(p, w->G0, 2, fb, al, 2, ad, be, xb0);
   }
 
   // ---- C-ABI operations ----------------------------------------------------------------------
@@ -534,23 +551,23 @@ struct RB : EqImpl {
     if (kind == 0 || kind == 3) {
       ZJobs zj{};
       zj.expand = 1;
-      zj.j[0] = zexpand(ci, kind == 0 ? czE.as<double>() : gzTE.as<double>(), 0, mix(Z, 0));
+      zj.j[0] = zexpand(ci, kind == 0 ? czE.as<double>() : gzTE.as<double>(), 0, mix(w->Z, 0));
       zj.n = 1;
       if ((s = launch_z(p, zj)) != SPADJ_OK) return s;
       XJobs xj{};
-      xj.j[0] = kind == 0 ? xc2r(mix(Z, 0), 0, 1.0, 1.0, out) : xc2r(mix(Z, 0), 0, 1.0 / Mx, 0.5 / Mx, out);
+      xj.j[0] = kind == 0 ? xc2r(mix(w->Z, 0), 0, 1.0, 1.0, out) : xc2r(mix(w->Z, 0), 0, 1.0 / Mx, 0.5 / Mx, out);
       xj.n = 1;
       return launch_x(p, xj);
     }
     if (kind == 1 || kind == 2) {
       XJobs xj{};
-      xj.j[0] = kind == 1 ? xr2c(in, 0, nullptr, 0, 1.0 / Mx, 1.0 / Mx, mix(Y, 0))
-                          : xr2c(in, 0, nullptr, 0, 1.0, 2.0, mix(Y, 0));
+      xj.j[0] = kind == 1 ? xr2c(in, 0, nullptr, 0, 1.0 / Mx, 1.0 / Mx, mix(w->Y, 0))
+                          : xr2c(in, 0, nullptr, 0, 1.0, 2.0, mix(w->Y, 0));
       xj.n = 1;
       if ((s = launch_x(p, xj)) != SPADJ_OK) return s;
       ZJobs zj{};
       zj.expand = 0;
-      zj.j[0] = zfold(mix(Y, 0), kind == 1 ? gzF.as<double>() : czTF.as<double>(), 0, co);
+      zj.j[0] = zfold(mix(w->Y, 0), kind == 1 ? gzF.as<double>() : czTF.as<double>(), 0, co);
       zj.n = 1;
       return launch_z(p, zj);
     }
@@ -594,12 +611,12 @@ struct RB : EqImpl {
     const double2* dc = reinterpret_cast<const double2*>(dx);
     double2* oc = reinterpret_cast<double2*>(out);
     spadj_status s;
-    if (mode == 0) return evalF(p, xc, oc, G0);
-    if ((s = c2g_fields(p, xc, G0)) != SPADJ_OK) return s;
-    if (mode == 1) return evalJvp(p, G0, dc, oc);
+    if (mode == 0) return evalF(p, xc, oc, w->G0);
+    if ((s = c2g_fields(p, xc, w->G0)) != SPADJ_OK) return s;
+    if (mode == 1) return evalJvp(p, w->G0, dc, oc);
     const double2* fb[1] = {dc};
     double al[1] = {1.0};
-    return evalVjp(p, G0, 1, fb, al, 0, nullptr, nullptr, oc);
+    return evalVjp(p, w->G0, 1, fb, al, 0, nullptr, nullptr, oc);
   }
 
   spadj_status pencil_solve(Problem* p, int transpose, const double* v, double* x) {
@@ -655,6 +672,28 @@ struct RB : EqImpl {
     }
     SPADJ_CUDA_TRY(p, cudaGraphLaunch(gFwd[ci], p->stream));
     return SPADJ_OK;
+  }
+
+  // one forward step of lane 1 (stream gsB, workspace ws[1]): SbB[ci] -> SbB[1-ci]
+  spadj_status run_fwd_lane1(Problem* p, int ci) {
+    cudaStream_t main = p->stream;
+    p->stream = gsB;
+    w = &ws[1];
+    double2* x0 = SbB[ci];
+    double2* x2 = SbB[1 - ci];
+    spadj_status s = SPADJ_OK;
+    if (!use_graphs(p)) {
+      s = step_fwd(p, x0, x2);
+    } else {
+      if (!gFwdB[ci]) s = capture(p, &gFwdB[ci], [&] { return step_fwd(p, x0, x2); });
+      if (s == SPADJ_OK) {
+        cudaError_t e = cudaGraphLaunch(gFwdB[ci], p->stream);
+        if (e != cudaSuccess) s = p->fail(SPADJ_ERR_CUDA, std::string("rb: graph launch: ") + cudaGetErrorString(e));
+      }
+    }
+    w = &ws[0];
+    p->stream = main;
+    return s;
   }
 
   // one adjoint step at state Sb[ci]: Yb[yi] (cotangent of X_{n+1}) -> Yb[1-yi] (of X_n)
@@ -742,6 +781,12 @@ struct RB : EqImpl {
   // Checkpointed reverse sweep.  objective_kind >= 0: seed dJ/dX_N from the objective kernel
   // (J to J_host).  objective_kind < 0: seeds supplied by the caller, seed_at[n] = index into
   // `seeds` ([n_seeds][state], device) of the cotangent injected at X_n, or -1.
+  //
+  // Two lanes run the binomial schedule concurrently: lane 1 (stream gsB, workspace ws[1])
+  // executes the forward sweep, every recomputation and the checkpoint copies; lane 0 (the
+  // problem's internal stream) the objective and the adjoint steps.  The state X_k for the
+  // adjoint step k moves from lane 1 into the staging buffer Sb[k % 2], so lane 1 recomputes
+  // the states of the next adjoint step while lane 0 is still reversing step k.
   spadj_status reverse(Problem* p, const double* x0, int n_steps, int ckpt_slots, int objective_kind,
                        const double* obj_data, const std::vector<int>& seed_at, const double* seeds, double* J_host,
                        double* grad) {
@@ -754,8 +799,10 @@ struct RB : EqImpl {
     CkptPlanner planner;
     std::vector<CkptOp> ops = planner.plan(n_steps, S);
     StreamScope scope(this, p);
-    int ci = 0, yi = 0;
-    SPADJ_CUDA_TRY(p, cudaMemcpyAsync(Sb[ci], x0, sb, cudaMemcpyDeviceToDevice, p->stream));
+    SPADJ_CUDA_TRY(p, cudaEventRecord(evFree, p->stream));
+    SPADJ_CUDA_TRY(p, cudaStreamWaitEvent(gsB, evFree, 0));
+    int ciB = 0, yi = 0;
+    SPADJ_CUDA_TRY(p, cudaMemcpyAsync(SbB[ciB], x0, sb, cudaMemcpyDeviceToDevice, gsB));
     int cur_step = 0;
     int recompute = 0;
     bool have_seed = false;
@@ -764,29 +811,39 @@ struct RB : EqImpl {
       if (objective_kind >= 0 || n < 0 || n >= (int)seed_at.size() || seed_at[n] < 0) return nullptr;
       return reinterpret_cast<const double2*>(seeds) + (size_t)seed_at[n] * ns;
     };
+    // X_k (current state of lane 1) -> Sb[k % 2] for lane 0
+    auto handoff = [&](int k) -> spadj_status {
+      const int c = k & 1;
+      SPADJ_CUDA_TRY(p, cudaStreamWaitEvent(gsB, evAdj[c], 0));  // the step that last read Sb[c] is done
+      SPADJ_CUDA_TRY(p, cudaMemcpyAsync(Sb[c], SbB[ciB], sb, cudaMemcpyDeviceToDevice, gsB));
+      SPADJ_CUDA_TRY(p, cudaEventRecord(evCopied[c], gsB));
+      SPADJ_CUDA_TRY(p, cudaStreamWaitEvent(p->stream, evCopied[c], 0));
+      return SPADJ_OK;
+    };
     for (const CkptOp& op : ops) {
       spadj_status s = SPADJ_OK;
       switch (op.type) {
         case CK_STORE:
-          SPADJ_CUDA_TRY(p, cudaMemcpyAsync(slot_ptr(op.slot), Sb[ci], sb, cudaMemcpyDeviceToDevice, p->stream));
+          SPADJ_CUDA_TRY(p, cudaMemcpyAsync(slot_ptr(op.slot), SbB[ciB], sb, cudaMemcpyDeviceToDevice, gsB));
           break;
         case CK_RESTORE:
           if (cur_step != op.a) {
-            SPADJ_CUDA_TRY(p, cudaMemcpyAsync(Sb[ci], slot_ptr(op.slot), sb, cudaMemcpyDeviceToDevice, p->stream));
+            SPADJ_CUDA_TRY(p, cudaMemcpyAsync(SbB[ciB], slot_ptr(op.slot), sb, cudaMemcpyDeviceToDevice, gsB));
             cur_step = op.a;
           }
           break;
         case CK_ADVANCE:
           for (int k = op.a; k < op.b; ++k) {
-            if ((s = run_fwd(p, ci)) != SPADJ_OK) return s;
-            ci = 1 - ci;
+            if ((s = run_fwd_lane1(p, ciB)) != SPADJ_OK) return s;
+            ciB = 1 - ciB;
             ++recompute;
           }
           cur_step = op.b;
           break;
         case CK_OBJECTIVE:
+          if ((s = handoff(n_steps)) != SPADJ_OK) return s;
           if (objective_kind >= 0) {
-            if ((s = objective(p, objective_kind, obj_data, reinterpret_cast<const double*>(Sb[ci]),
+            if ((s = objective(p, objective_kind, obj_data, reinterpret_cast<const double*>(Sb[n_steps & 1]),
                                Jdev.as<double>(), reinterpret_cast<double*>(Yb[yi]))) != SPADJ_OK)
               return s;
           } else if (const double2* sp = seed_ptr(n_steps)) {
@@ -794,22 +851,29 @@ struct RB : EqImpl {
           } else {
             SPADJ_CUDA_TRY(p, cudaMemsetAsync(Yb[yi], 0, sb, p->stream));
           }
+          SPADJ_CUDA_TRY(p, cudaEventRecord(evAdj[n_steps & 1], p->stream));
           have_seed = true;
           break;
-        case CK_ADJOINT:
+        case CK_ADJOINT: {
           if (!have_seed) return p->fail(SPADJ_ERR_INVALID, "gradient: schedule reached an adjoint step before the objective");
-          if ((s = run_adj(p, ci, yi)) != SPADJ_OK) return s;
+          const int c = op.a & 1;
+          if ((s = handoff(op.a)) != SPADJ_OK) return s;
+          if ((s = run_adj(p, c, yi)) != SPADJ_OK) return s;
+          SPADJ_CUDA_TRY(p, cudaEventRecord(evAdj[c], p->stream));
           yi = 1 - yi;
           if (const double2* sp = seed_ptr(op.a)) {  // cotangent injected at X_a
             axpy_kernel<<<64, 256, 0, p->stream>>>(Yb[yi], Yb[yi], 1.0, sp, 1.0, nullptr, 0.0, ns);
             if ((s = check_launch(p, "rb seed")) != SPADJ_OK) return s;
           }
           break;
+        }
         default:
           break;
       }
     }
     last_recompute = recompute;
+    SPADJ_CUDA_TRY(p, cudaEventRecord(evBdone, gsB));
+    SPADJ_CUDA_TRY(p, cudaStreamWaitEvent(p->stream, evBdone, 0));
     SPADJ_CUDA_TRY(p, cudaMemcpyAsync(grad, Yb[yi], sb, cudaMemcpyDeviceToDevice, p->stream));
     if (J_host && objective_kind >= 0) {
       SPADJ_CUDA_TRY(p, cudaMemcpyAsync(J_host, Jdev.ptr, sizeof(double), cudaMemcpyDeviceToHost, p->stream));
@@ -832,17 +896,20 @@ struct RB : EqImpl {
   }
 
   ~RB() override {
-    if (gs) cudaStreamSynchronize(gs);
-    if (gs2) cudaStreamSynchronize(gs2);
-    for (cudaGraphExec_t g : {gFwd[0], gFwd[1], gAdj[0][0], gAdj[0][1], gAdj[1][0], gAdj[1][1]})
+    for (cudaStream_t st : {gs, gs2, gsB})
+      if (st) cudaStreamSynchronize(st);
+    for (cudaGraphExec_t g : {gFwd[0], gFwd[1], gFwdB[0], gFwdB[1], gAdj[0][0], gAdj[0][1], gAdj[1][0], gAdj[1][1]})
       if (g) cudaGraphExecDestroy(g);
-    for (cudaEvent_t e : {evIn, evOut, evFork, evJoin})
+    for (cudaEvent_t e : {evIn, evOut, evFork, evJoin, evReady, evFree, evBdone, evAdj[0], evAdj[1], evCopied[0],
+                          evCopied[1]})
       if (e) cudaEventDestroy(e);
-    if (gs) cudaStreamDestroy(gs);
-    if (gs2) cudaStreamDestroy(gs2);
-    for (DevBuf* b : {&wm, &czE, &cdzE, &gzF, &gzTE, &czTF, &cdzTF, &gmat, &phi, &phiT, &Z, &G0, &G1, &dG, &Gb, &Fg, &Y, &f0,
-                      &f1, &df0, &df1, &x1, &dx1, &vb2, &vb1, &xb1, &tmpx, &tmpy, &ybar, &ybar2, &cur, &nxt, &partial,
-                      &Jdev, &seedbuf, &slots, &traj_tmp})
+    for (cudaStream_t st : {gs, gs2, gsB})
+      if (st) cudaStreamDestroy(st);
+    for (WS& l : ws)
+      for (DevBuf* b : {&l.Z, &l.Y, &l.G0, &l.G1, &l.f0, &l.f1, &l.x1}) b->release();
+    for (DevBuf* b : {&wm, &czE, &cdzE, &gzF, &gzTE, &czTF, &cdzTF, &gmat, &phi, &phiT, &dG, &Gb, &Fg, &df0, &df1, &dx1,
+                      &vb2, &vb1, &xb1, &tmpx, &tmpy, &ybar, &ybar2, &cur, &nxt, &curB, &nxtB, &partial, &Jdev,
+                      &seedbuf, &slots, &traj_tmp})
       b->release();
   }
 };
