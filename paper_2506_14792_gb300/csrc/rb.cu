@@ -49,7 +49,7 @@ struct RB : EqImpl {
   };
   WS ws[2];
   WS* w = &ws[0];
-  size_t zsmem = 0, xsmem = 0, ssmem = 0, csmem = 0;
+  size_t zsmem = 0, xsmem = 0, ssmem = 0, csmem = 0, ctsmem = 0;
   bool fused = false;  // fused column stage (rb_colstep_kernel) usable for these sizes
   // internal streams (joined to the caller's stream by events) and captured step graphs
   cudaStream_t gs = nullptr, gs2 = nullptr, gsB = nullptr;
@@ -192,9 +192,12 @@ struct RB : EqImpl {
     xsmem = sizeof(double2) * (4 * L + Kx);
     ssmem = sizeof(double2) * (H + 4 * solve_rows(H)) + sizeof(double) * (size_t)H * solve_rows(H);
     csmem = colstep_smem(N, Mz);
-    fused = nonlinear && csmem <= 200 * 1024;
-    if (fused)
+    ctsmem = colstepT_smem(N, Mz);
+    fused = nonlinear && std::max(csmem, ctsmem) <= 200 * 1024;
+    if (fused) {
       SPADJ_CUDA_TRY(p, cudaFuncSetAttribute(rb_colstep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csmem));
+      SPADJ_CUDA_TRY(p, cudaFuncSetAttribute(rb_colstepT_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ctsmem));
+    }
     if (ssmem > 48 * 1024)
       SPADJ_CUDA_TRY(p, cudaFuncSetAttribute(solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssmem));
     return SPADJ_OK;
@@ -347,45 +350,57 @@ struct RB : EqImpl {
                        const double2* const* add, const double* beta, double2* out) {
     spadj_status s;
     if (nonlinear) {
-      // T^dagger: Gz^T (expand) then c2r with weights 1/Mx, 1/(2Mx)
-      ZJobs zj{};
-      zj.expand = 1;
-      for (int q = 0; q < 3; ++q) {
-        ZJob j{};
-        for (int t = 0; t < nfb; ++t) {
-          j.in[t] = fb[t] + (size_t)q * Kx * N;
-          j.mat[t] = gzTE.as<double>();
-          j.alpha[t] = alpha[t];
-          j.deriv[t] = 0;
-        }
-        j.nterm = nfb;
-        j.out = mix(w->Z, q); j.I = Mz; j.K = N; j.ik = 1; j.im = N; j.oi = Kx; j.om = 1;
-        zj.j[q] = j;
-      }
-      zj.n = 3;
-      if ((s = launch_z(p, zj)) != SPADJ_OK) return s;
-      XJobs xj{};
-      for (int q = 0; q < 3; ++q) xj.j[q] = xc2r(mix(w->Z, q), 0, 1.0 / Mx, 0.5 / Mx, grid(Fg, q));
-      xj.n = 3;
-      if ((s = launch_x(p, xj)) != SPADJ_OK) return s;
-      cudaEvent_t tp = p->tic();
-      SPADJ_CUDA_TRY(p, launch_kernel(p->pdl, prod_vjp_kernel, dim3(prod_grid()), dim3(256), 0, p->stream,
-                                      (const double*)G.as<double>(), (const double*)Fg.as<double>(), Gb.as<double>(),
-                                      (int)npts));
-      p->toc(tp, KC_POINTWISE, 24.0 * npts);
-      if ((s = check_launch(p, "rb prod vjp")) != SPADJ_OK) return s;
-      // (T^-1)^dagger in x: r2c with factor 2 on k >= 1, x-derivative adjoint -ik
-      XJobs xb{};
-      xb.j[0] = xr2c(grid(Gb, 0), 0, grid(Gb, 1), 2, 1.0, 2.0, mix(w->Y, 0));  // a_u
-      xb.j[1] = xr2c(grid(Gb, 2), 0, nullptr, 0, 1.0, 2.0, mix(w->Y, 1));      // b_u
-      xb.j[2] = xr2c(grid(Gb, 3), 0, grid(Gb, 4), 2, 1.0, 2.0, mix(w->Y, 2));  // a_w
-      xb.j[3] = xr2c(grid(Gb, 5), 0, nullptr, 0, 1.0, 2.0, mix(w->Y, 3));      // b_w
-      xb.j[4] = xr2c(grid(Gb, 6), 2, nullptr, 0, 1.0, 2.0, mix(w->Y, 4));      // a_t
-      xb.j[5] = xr2c(grid(Gb, 7), 0, nullptr, 0, 1.0, 2.0, mix(w->Y, 5));      // b_t
-      xb.n = 6;
-      if ((s = launch_x(p, xb)) != SPADJ_OK) return s;
+      if ((s = vjp_expand(p, nfb, fb, alpha)) != SPADJ_OK) return s;
+      if ((s = vjp_middle(p, G)) != SPADJ_OK) return s;
     }
-    // z part: out_q = Cz^T a_q + C'z^T b_q (+ addends)
+    return vjp_fold(p, nadd, add, beta, out);
+  }
+
+  // T^dagger in z: Z_q = Gz^T (sum_t alpha_t fb_t) (one matrix pass on the combined column)
+  spadj_status vjp_expand(Problem* p, int nfb, const double2* const* fb, const double* alpha) {
+    ZJobs zj{};
+    zj.expand = 1;
+    for (int q = 0; q < 3; ++q) {
+      ZJob j{};
+      j.mat[0] = gzTE.as<double>(); j.alpha[0] = 1.0; j.deriv[0] = 0; j.nterm = 1;
+      for (int t = 0; t < nfb; ++t) {
+        j.xin[t] = fb[t] + (size_t)q * Kx * N; j.xalpha[t] = alpha[t]; j.xterm[t] = 0;
+      }
+      j.nx = nfb;
+      j.out = mix(w->Z, q); j.I = Mz; j.K = N; j.ik = 1; j.im = N; j.oi = Kx; j.om = 1;
+      zj.j[q] = j;
+    }
+    zj.n = 3;
+    return launch_z(p, zj);
+  }
+
+  // from Z (T^dagger in z done): c2r with weights 1/Mx, 1/(2Mx), reverse of the grid products
+  // with the fields G, then (T^-1)^dagger in x (r2c, factor 2 on k >= 1, -ik) into Y
+  spadj_status vjp_middle(Problem* p, DevBuf& G) {
+    spadj_status s;
+    XJobs xj{};
+    for (int q = 0; q < 3; ++q) xj.j[q] = xc2r(mix(w->Z, q), 0, 1.0 / Mx, 0.5 / Mx, grid(Fg, q));
+    xj.n = 3;
+    if ((s = launch_x(p, xj)) != SPADJ_OK) return s;
+    cudaEvent_t tp = p->tic();
+    SPADJ_CUDA_TRY(p, launch_kernel(p->pdl, prod_vjp_kernel, dim3(prod_grid()), dim3(256), 0, p->stream,
+                                    (const double*)G.as<double>(), (const double*)Fg.as<double>(), Gb.as<double>(),
+                                    (int)npts));
+    p->toc(tp, KC_POINTWISE, 24.0 * npts);
+    if ((s = check_launch(p, "rb prod vjp")) != SPADJ_OK) return s;
+    XJobs xb{};
+    xb.j[0] = xr2c(grid(Gb, 0), 0, grid(Gb, 1), 2, 1.0, 2.0, mix(w->Y, 0));  // a_u
+    xb.j[1] = xr2c(grid(Gb, 2), 0, nullptr, 0, 1.0, 2.0, mix(w->Y, 1));      // b_u
+    xb.j[2] = xr2c(grid(Gb, 3), 0, grid(Gb, 4), 2, 1.0, 2.0, mix(w->Y, 2));  // a_w
+    xb.j[3] = xr2c(grid(Gb, 5), 0, nullptr, 0, 1.0, 2.0, mix(w->Y, 3));      // b_w
+    xb.j[4] = xr2c(grid(Gb, 6), 2, nullptr, 0, 1.0, 2.0, mix(w->Y, 4));      // a_t
+    xb.j[5] = xr2c(grid(Gb, 7), 0, nullptr, 0, 1.0, 2.0, mix(w->Y, 5));      // b_t
+    xb.n = 6;
+    return launch_x(p, xb);
+  }
+
+  // z part: out_q = Cz^T a_q + C'z^T b_q (+ addends)
+  spadj_status vjp_fold(Problem* p, int nadd, const double2* const* add, const double* beta, double2* out) {
     ZJobs zf{};
     zf.expand = 0;
     for (int q = 0; q < 3; ++q) {
@@ -408,6 +423,33 @@ struct RB : EqImpl {
       cudaMemsetAsync(w->Y.ptr, 0, sizeof(double2) * nmix, p->stream);
     }
     return launch_z(p, zf);
+  }
+
+  // fused adjoint column stage: xb = fold(Y) + sum_a beta_a add_a, vb = Phi^H xb (into vb),
+  // Z = Gz^T (al0 c0 + al1 vb)
+  spadj_status colstepT(Problem* p, int nadd, const double2* const* add, const double* beta, double2* vb,
+                        const double2* c0, double al0, double al1) {
+    ColStepTArgs S{};
+    for (int e = 0; e < 6; ++e) S.yin[e] = mix(w->Y, e);
+    S.czTF = czTF.as<double>();
+    S.cdzTF = cdzTF.as<double>();
+    for (int a = 0; a < nadd; ++a) { S.add[a] = add[a]; S.beta[a] = beta[a]; }
+    S.nadd = nadd;
+    S.phiA = phi.as<double>();
+    S.v_out = vb;
+    S.c0 = c0;
+    S.al0 = al0;
+    S.al1 = al1;
+    S.gzTE = gzTE.as<double>();
+    S.zout = w->Z.as<double2>();
+    S.nmix = nmix;
+    S.Kx = Kx; S.N = N; S.Mz = Mz;
+    const int H = 3 * N / 2;
+    const double fl = (double)Kx * (3 * 2 * 4.0 * N * (Mz / 2) + 2 * 4.0 * H * H + 3 * 4.0 * N * (Mz / 2));
+    cudaEvent_t t = p->tic();
+    rb_colstepT_kernel<<<2 * Kx, 256, ctsmem, p->stream>>>(S);
+    p->toc(t, KC_FUSED, fl);
+    return check_launch(p, "rb colstepT");
   }
 
   spadj_status solve(Problem* p, int transpose, int nin, const double2* const* in, const double* a, double2* out) {
@@ -528,6 +570,19 @@ struct RB : EqImpl {
       if (nonlinear && (s = c2g_fields(p, st(w->x1), w->G1)) != SPADJ_OK) return s;
     }
     SPADJ_CUDA_TRY(p, cudaStreamWaitEvent(p->stream, evJoin, 0));
+    if (use_fused(p)) {
+      // xb1 = c vb2 + (dF/dx1)^dagger (dt A21 vb2); vb1 = Phi^H xb1; then the first transform
+      // of the second product, Gz^T (dt(A20 - c A10) vb2 + dt A10 vb1), in the same cluster kernel
+      { const double2* fb[1] = {st(vb2)}; double al[1] = {dt * A21};
+        if ((s = vjp_expand(p, 1, fb, al)) != SPADJ_OK) return s; }
+      if ((s = vjp_middle(p, w->G1)) != SPADJ_OK) return s;
+      { const double2* ad[1] = {st(vb2)}; double be[1] = {cc};
+        if ((s = colstepT(p, 1, ad, be, st(vb1), st(vb2), dt * (A20 - cc * A10), dt * A10)) != SPADJ_OK) return s; }
+      if ((s = vjp_middle(p, w->G0)) != SPADJ_OK) return s;
+      const double2* ad[2] = {st(vb2), st(vb1)};
+      double be[2] = {1.0 - cc, 1.0};
+      return vjp_fold(p, 2, ad, be, xb0);
+    }
     // xb1 = c vb2 + (dF/dx1)^dagger (dt A21 vb2)
     { const double2* fb[1] = {st(vb2)}; double al[1] = {dt * A21};
       const double2* ad[1] = {st(vb2)}; double be[1] = {cc};

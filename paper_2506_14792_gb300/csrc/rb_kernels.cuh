@@ -582,6 +582,140 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256) rb_colstep_kern
   cluster.sync();  // the partner's shared memory stays alive until both expansions are done
 }
 
+// Fused column stage of the RK222 adjoint step (the transpose of rb_colstep_kernel's chain)
+// for one x-mode pencil, as a cluster of two CTAs (one per z-parity class):
+//   1. fold: xb = Cz^T a_q + (Cz Dz)^T b_q + sum_a beta_a add_a for the six mixed rows
+//      (a_u, b_u, a_w, b_w, a_t, b_t) restricted to this class's modes;
+//   2. transposed solve: vb = Phi^H xb for this class (solve_kernel's transpose arithmetic,
+//      the class block of Phi' staged in shared memory by cp.async during the fold);
+//   3. the two CTAs exchange their halves of vb through distributed shared memory and each
+//      expands, for half of the Gauss rows, the three columns Gz^T (al0 c0 + al1 vb) into
+//      zout[3][Mz][Kx] (the first transform of the next vector-Jacobian product).
+// vb is also written in the state layout.  Replaces zmm fold + solve + zmm expand.
+struct ColStepTArgs {
+  const double2* yin[6];
+  const double* czTF;    // N x (Mz/2)
+  const double* cdzTF;   // N x (Mz/2), z-derivative parity
+  const double2* add[2];
+  double beta[2];
+  int nadd;
+  const double* phiA;    // [Kx][2][H][H] as [k][r] = Phi'[k][r]
+  double2* v_out;
+  const double2* c0;
+  double al0, al1;
+  const double* gzTE;    // (Mz/2) x N
+  double2* zout;
+  size_t nmix;
+  int Kx, N, Mz;
+};
+
+__host__ __device__ inline size_t colstepT_smem(int N, int Mz) {
+  const int H = 3 * N / 2;
+  return sizeof(double) * (size_t)H * H + sizeof(double2) * (size_t)(6 * (Mz / 2) + H + H);
+}
+
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256) rb_colstepT_kernel(const __grid_constant__ ColStepTArgs S) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int cls = (int)cluster.block_rank();
+  const int m = blockIdx.x >> 1;
+  const int N = S.N, Nh = N / 2, H = 3 * Nh, Kx = S.Kx, Mz = S.Mz, Mh = Mz / 2;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  extern __shared__ double2 cs[];
+  double* ph = reinterpret_cast<double*>(cs);   // [H][H] as [k][r]
+  double2* sd = cs + (size_t)H * H / 2;         // [6][Mh] folded samples
+  double2* xv = sd + 6 * Mh;                    // [H] right-hand side (class order)
+  double2* vc = xv + H;                         // [H] solution (class order)
+  pdl_trigger();
+  const double* blk = S.phiA + ((size_t)m * 2 + cls) * H * H;
+  for (int idx = tid; idx < H * H / 2; idx += nt)
+    cp_async16(reinterpret_cast<double2*>(ph) + idx, reinterpret_cast<const double2*>(blk) + idx);
+  cp_async_commit();
+  pdl_wait();
+  // row e = 2q + term: term 0 (values) folds with s for even modes, term 1 (z-derivative
+  // parity) with s for odd modes; this class's modes of field q have parity (q == 0 ? cls : 1 - cls)
+  for (int idx = tid; idx < 6 * Mh; idx += nt) {
+    const int e = idx / Mh, j = idx - e * Mh;
+    const int q = e >> 1, term = e & 1;
+    const int par = (q == 0) ? cls : 1 - cls;
+    const bool use_s = (par == 0) != (term == 1);
+    const double2 a = S.yin[e][(size_t)j * Kx + m], b = S.yin[e][(size_t)(Mz - 1 - j) * Kx + m];
+    sd[idx] = use_s ? make_double2(a.x + b.x, a.y + b.y) : make_double2(a.x - b.x, a.y - b.y);
+  }
+  __syncthreads();
+  for (int c = tid; c < H; c += nt) {
+    const int q = c / Nh, h = c % Nh;
+    const int n = 2 * h + ((q == 0) ? cls : 1 - cls);
+    const double* g0 = S.czTF + (size_t)n * Mh;
+    const double* g1 = S.cdzTF + (size_t)n * Mh;
+    const double2* w0 = sd + (2 * q) * Mh;
+    const double2* w1 = sd + (2 * q + 1) * Mh;
+    double2 a0 = make_double2(0.0, 0.0), a1 = make_double2(0.0, 0.0);
+    for (int j = 0; j < Mh; ++j) {
+      const double c0 = __ldg(g0 + j), c1 = __ldg(g1 + j);
+      a0.x = fma(c0, w0[j].x, a0.x); a0.y = fma(c0, w0[j].y, a0.y);
+      a1.x = fma(c1, w1[j].x, a1.x); a1.y = fma(c1, w1[j].y, a1.y);
+    }
+    double2 x = cadd(a0, a1);
+    const size_t off = ((size_t)q * Kx + m) * N + n;
+    for (int a = 0; a < S.nadd; ++a) {
+      const double2 y = S.add[a][off];
+      x.x = fma(S.beta[a], y.x, x.x);
+      x.y = fma(S.beta[a], y.y, x.y);
+    }
+    if (m == 0) x.y = 0.0;                     // projection (self-adjoint)
+    if (q == 0) x = make_double2(x.y, -x.x);  // times -i (Dc^H)
+    xv[c] = x;
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  for (int r = tid; r < H; r += nt) {
+    double2 a0 = make_double2(0.0, 0.0), a1 = make_double2(0.0, 0.0);
+    int k = 0;
+    for (; k + 1 < H; k += 2) {
+      const double p0 = ph[(size_t)k * H + r], p1 = ph[(size_t)(k + 1) * H + r];
+      const double2 x0 = xv[k], x1 = xv[k + 1];
+      a0.x = fma(p0, x0.x, a0.x); a0.y = fma(p0, x0.y, a0.y);
+      a1.x = fma(p1, x1.x, a1.x); a1.y = fma(p1, x1.y, a1.y);
+    }
+    if (k < H) {
+      const double p0 = ph[(size_t)k * H + r];
+      a0.x = fma(p0, xv[k].x, a0.x); a0.y = fma(p0, xv[k].y, a0.y);
+    }
+    double2 acc = cadd(a0, a1);
+    const int q = r / Nh, h = r % Nh;
+    const int n = 2 * h + ((q == 0) ? cls : 1 - cls);
+    if (q == 0) acc = make_double2(-acc.y, acc.x);  // times i (Dr^H)
+    vc[r] = acc;
+    S.v_out[((size_t)q * Kx + m) * N + n] = acc;
+  }
+  cluster.sync();
+  const double2* vo = cluster.map_shared_rank(vc, 1 - cls);
+  const int jh = (Mh + 1) / 2;
+  const int j0 = cls == 0 ? 0 : jh, j1 = cls == 0 ? jh : Mh;
+  for (int idx = tid; idx < 3 * (j1 - j0); idx += nt) {
+    const int q = idx / (j1 - j0), j = j0 + idx % (j1 - j0);
+    const double* grow = S.gzTE + (size_t)j * N;
+    const int even_cta = (q == 0) ? 0 : 1;
+    const double2* ve = (even_cta == cls ? vc : vo) + q * Nh;
+    const double2* vd = (even_cta == cls ? vo : vc) + q * Nh;
+    const double2* c0 = S.c0 + ((size_t)q * Kx + m) * N;
+    double2 E = make_double2(0.0, 0.0), O = make_double2(0.0, 0.0);
+    for (int h = 0; h < Nh; ++h) {
+      const double ge = __ldg(grow + 2 * h), go = __ldg(grow + 2 * h + 1);
+      const double2 ce = c0[2 * h], co = c0[2 * h + 1];
+      const double2 xe = make_double2(fma(S.al0, ce.x, S.al1 * ve[h].x), fma(S.al0, ce.y, S.al1 * ve[h].y));
+      const double2 xo = make_double2(fma(S.al0, co.x, S.al1 * vd[h].x), fma(S.al0, co.y, S.al1 * vd[h].y));
+      E.x = fma(ge, xe.x, E.x); E.y = fma(ge, xe.y, E.y);
+      O.x = fma(go, xo.x, O.x); O.y = fma(go, xo.y, O.y);
+    }
+    double2* out = S.zout + (size_t)q * S.nmix;
+    out[(size_t)j * Kx + m] = make_double2(E.x + O.x, E.y + O.y);
+    out[(size_t)(Mz - 1 - j) * Kx + m] = make_double2(E.x - O.x, E.y - O.y);
+  }
+  cluster.sync();
+}
+
 // Kinetic energy J = (Lx/2) sum_{u,w} sum_m w_m c_m^H G c_m and its gradient
 // seed = Lx w_m G c_m (w_0 = 1, w_m = 2; real part only on the mean pencil).
 __global__ void energy_kernel(const double2* __restrict__ x, const double* __restrict__ G, double Lx, int Kx, int N,
