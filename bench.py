@@ -96,6 +96,9 @@ class Burgers:
         self.p.objective(self.xN, self.J, self.seedv)
         self.p.adjoint(self.nsteps, self.traj, self.seedv, self.grad)
 
+    def forward_step(self):
+        self.p.forward(self.nsteps, self.x0, self.xN)
+
     def e2e_step(self):
         """Public API call with host buffers: pinned H2D of x0, spadj_gradient (J to host), D2H of grad."""
         self.x0_dev2.copy_(self.x0_pin, non_blocking=True)
@@ -156,6 +159,9 @@ class RayleighBenard:
 
     def step(self, ev=None):
         self.p.gradient(self.x0, self.nsteps, self.grad, ckpt_slots=self.slots, want_J=False)
+
+    def forward_step(self):
+        self.p.forward(self.nsteps, self.x0, self.x0_dev2)
 
     def e2e_step(self):
         self.x0_dev2.copy_(self.x0_pin, non_blocking=True)
@@ -241,6 +247,9 @@ class KolmogorovBatch:
     def step(self, ev=None):
         self.p.gradient(self.x0, self.nsteps, self.grad, objective=self.sp.SPADJ_OBJ_FOURDVAR, want_J=False)
 
+    def forward_step(self):
+        self.p.forward(self.nsteps, self.x0, self.x0_dev2)
+
     def e2e_step(self):
         self.x0_dev2.copy_(self.x0_pin, non_blocking=True)
         J = self.p.gradient(self.x0_dev2, self.nsteps, self.grad, objective=self.sp.SPADJ_OBJ_FOURDVAR)
@@ -315,6 +324,9 @@ class Couette:
     def step(self, ev=None):
         self.p.gradient(self.x0, self.nsteps, self.grad, objective=self.sp.SPADJ_OBJ_GAIN, ckpt_slots=self.slots,
                         want_J=False)
+
+    def forward_step(self):
+        self.p.forward(self.nsteps, self.x0, self.x0_dev2)
 
     def e2e_step(self):
         self.x0_dev2.copy_(self.x0_pin, non_blocking=True)
@@ -482,6 +494,17 @@ def run_gpu(args, wl):
     barrier()
     clocks = clk.stop()
     ms = float(sum(starts[i].elapsed_time(ends[i]) for i in range(args.steps)))
+    # adjoint/forward cost ratio: one forward sweep alone (same workload, outside the timed region)
+    f0 = torch.cuda.Event(enable_timing=True)
+    f1 = torch.cuda.Event(enable_timing=True)
+    wl.forward_step()
+    barrier()
+    f0.record(stream)
+    wl.forward_step()
+    f1.record(stream)
+    barrier()
+    fwd_ms = f0.elapsed_time(f1)
+    adj_ratio = (ms / args.steps - fwd_ms) / fwd_ms
     # per-kernel breakdown: one more step of the same workload with the library bracketing each
     # of its launches by CUDA events on this stream (kept out of the timed region: the events
     # add host work between launches)
@@ -536,7 +559,9 @@ def run_gpu(args, wl):
             "gpu_launches": launches,
             "e2e": {"value": units / (e2e_ms / 1e3), "unit": "dof*steps/s", "h2d_bytes_per_step": bi,
                     "d2h_bytes_per_step": bo},
-            "roofline": roof, "cpu_baseline": cpu, "clocks": clocks}
+            "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
+            "adjoint_forward_ratio": {"value": adj_ratio, "forward_ms": fwd_ms,
+                                      "definition": "(gradient - forward sweep) / forward sweep, same workload"}}
     print(json.dumps(line))
     return 0
 

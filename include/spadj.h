@@ -191,11 +191,16 @@ typedef enum {
                              SPADJ_COUETTE3D J = E(X_N) = (1/V) int |u|^2 dV */
   SPADJ_OBJ_FOURDVAR = 1, /* J = sum_m 1/2 ||H(X_{n_m}) - obs_m||^2 per member (observations set by
                              spadj_set_observations; H keeps |kx|, |ky| <= kmax) */
-  SPADJ_OBJ_GAIN = 2      /* SPADJ_COUETTE3D: energy gain J = E(X_N) / E(X_0) with the
+  SPADJ_OBJ_GAIN = 2,     /* SPADJ_COUETTE3D: energy gain J = E(X_N) / E(X_0) with the
                              volume-weighted norm E(X) = (1/V) int |u|^2 dV (optimal
                              perturbation objective); spadj_objective takes X_0 as obj_data
                              and returns dJ/dX_N only, spadj_gradient includes the explicit
                              dependence on X_0 */
+  SPADJ_OBJ_ENERGY_INTEGRAL = 3 /* SPADJ_COUETTE3D, spadj_gradient only: J = I(T) with
+                             dI/dt = E(X), I(0) = 0, the ODE added to the equation set and
+                             integrated by the same IMEX scheme (Supplementary A.4), so the
+                             time integral has the scheme's accuracy and its cotangents enter
+                             the adjoint sweep at every step */
 } spadj_objective_kind;
 
 /* 4D-Var observations for SPADJ_OBJ_FOURDVAR (SPADJ_KOLMOGOROV2D): n_obs steps (host ints,

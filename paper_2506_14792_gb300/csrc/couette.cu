@@ -40,7 +40,7 @@ struct Couette : EqImpl {
   XParams xp{};
   YParams yp{};
   DevBuf wmx, w2y, czE, cdzE, gzF, gzTE, czTF, cdzTF, gmat, phi1F, phi1A, phi2F, phi2A, one;
-  DevBuf Zm, Ym, Gf, dGf, Gb, Fg, Xr, Fr, dXr, dFr, Wr, xbar, src0, partial, edev, sdev, Jdev, slots;
+  DevBuf Zm, Ym, Gf, dGf, Gb, Fg, Xr, Fr, dXr, dFr, Wr, xbar, src0, partial, edev, sdev, Jdev, slots, wts;
   size_t zsmem = 0, xsmem = 0, ysmem = 0;
 
   size_t state_len(int which) const override {
@@ -583,8 +583,38 @@ struct Couette : EqImpl {
   spadj_status reverse(Problem* p, const double* x0, int n_steps, int ckpt_slots, int objective_kind,
                        const std::vector<int>& seed_at, const double* seeds, double* J_host, double* grad) {
     if (n_steps < 1) return p->fail(SPADJ_ERR_INVALID, "gradient: n_steps < 1");
-    if (objective_kind >= 0 && objective_kind != SPADJ_OBJ_ENERGY && objective_kind != SPADJ_OBJ_GAIN)
-      return p->fail(SPADJ_ERR_UNSUPPORTED, "couette: objective must be ENERGY or GAIN");
+    if (objective_kind >= 0 && objective_kind != SPADJ_OBJ_ENERGY && objective_kind != SPADJ_OBJ_GAIN &&
+        objective_kind != SPADJ_OBJ_ENERGY_INTEGRAL)
+      return p->fail(SPADJ_ERR_UNSUPPORTED, "couette: objective must be ENERGY, GAIN or ENERGY_INTEGRAL");
+    const bool integral = objective_kind == SPADJ_OBJ_ENERGY_INTEGRAL;
+    if (integral) {
+      // dI/dt = E(X) added to the equation set (M = 1, L = 0 for I): the scalar adjoint of the
+      // I-equation, a_0^m Y_m = [m == N] - sum_i a_i^{m+i} Y_{m+i}, gives the weight
+      // s_n = sum_i c_i^{n+i} Y_{n+i} with which grad E(X_n) enters the state adjoint, and
+      // I_N = sum_n s_n E(X_n)
+      std::vector<double> Y((size_t)n_steps + 3, 0.0), sw((size_t)n_steps, 0.0);
+      double a[3], c[3];
+      for (int m = n_steps; m >= 1; --m) {
+        double r = (m == n_steps) ? 1.0 : 0.0;
+        for (int i = 1; i <= 2; ++i) {
+          if (m + i > n_steps) continue;
+          coeffs(m + i, a, c);
+          r -= a[i] * Y[m + i];
+        }
+        coeffs(m, a, c);
+        Y[m] = r / a[0];
+      }
+      for (int n = 0; n < n_steps; ++n)
+        for (int i = 1; i <= 2; ++i) {
+          if (n + i > n_steps) continue;
+          coeffs(n + i, a, c);
+          sw[n] += c[i] * Y[n + i];
+        }
+      SPADJ_CUDA_TRY(p, wts.ensure(sizeof(double) * (size_t)n_steps));
+      SPADJ_CUDA_TRY(p, cudaMemcpyAsync(wts.ptr, sw.data(), sizeof(double) * n_steps, cudaMemcpyHostToDevice, p->stream));
+      SPADJ_CUDA_TRY(p, cudaMemsetAsync(Jdev.ptr, 0, sizeof(double), p->stream));
+      SPADJ_CUDA_TRY(p, cudaStreamSynchronize(p->stream));  // the host weights go out of scope
+    }
     const int S = (ckpt_slots <= 0 || ckpt_slots > n_steps + 1) ? n_steps + 1 : ckpt_slots;
     const size_t sb = sizeof(double2) * ns;
     SPADJ_CUDA_TRY(p, slots.ensure(3 * sb * (size_t)S));
@@ -625,7 +655,9 @@ struct Couette : EqImpl {
           break;
         case CK_OBJECTIVE: {
           double2* xb = xbar.as<double2>();
-          if (objective_kind >= 0) {
+          if (integral) {
+            SPADJ_CUDA_TRY(p, cudaMemsetAsync(xb, 0, sb, p->stream));  // J = I_N has no X_N term
+          } else if (objective_kind >= 0) {
             if ((s = objective_at(p, objective_kind, x0c, st(Xr, r.xc), Jdev.as<double>(), xb,
                                   objective_kind == SPADJ_OBJ_GAIN)) != SPADJ_OK)
               return s;
@@ -646,6 +678,13 @@ struct Couette : EqImpl {
           const int k = op.a;
           const double2* src = seed_ptr(k);
           if (objective_kind == SPADJ_OBJ_GAIN && k == 0) src = src0.as<double2>();
+          if (integral) {  // s_k grad E(X_k) into src0, and J += s_k E(X_k)
+            const double* wk = wts.as<double>() + k;
+            if ((s = energy(p, st(Xr, r.xc), edev.as<double>(), wk, src0.as<double2>())) != SPADJ_OK) return s;
+            integral_accum_kernel<<<1, 1, 0, p->stream>>>(edev.as<double>(), wk, Jdev.as<double>());
+            if ((s = check_launch(p, "couette integral")) != SPADJ_OK) return s;
+            src = src0.as<double2>();
+          }
           if ((s = reverse_index(p, k, n_steps, st(Xr, r.xc), src, xbar.as<double2>())) != SPADJ_OK) return s;
           break;
         }
@@ -753,7 +792,7 @@ struct Couette : EqImpl {
   ~Couette() override {
     for (DevBuf* b : {&wmx, &w2y, &czE, &cdzE, &gzF, &gzTE, &czTF, &cdzTF, &gmat, &phi1F, &phi1A, &phi2F, &phi2A, &one,
                       &Zm, &Ym, &Gf, &dGf, &Gb, &Fg, &Xr, &Fr, &dXr, &dFr, &Wr, &xbar, &src0, &partial, &edev, &sdev,
-                      &Jdev, &slots})
+                      &Jdev, &slots, &wts})
       b->release();
   }
 };

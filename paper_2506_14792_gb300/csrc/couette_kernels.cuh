@@ -286,6 +286,11 @@ __global__ void cou_energy_kernel(const double2* __restrict__ x, const double* _
   if (threadIdx.x == 0 && partial) partial[p] = 0.5 * wm * red[0];
 }
 
+// J += w[0] * e[0] (time-integrated objective: one term of I_N = sum_n s_n E(X_n))
+__global__ void integral_accum_kernel(const double* __restrict__ e, const double* __restrict__ w, double* __restrict__ J) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) J[0] = fma(w[0], e[0], J[0]);
+}
+
 // e[0] = E(X_0), e[1] = E(X_N) -> J = e1 / e0 and the seed scales s[0] = 1 / e0 (for X_N),
 // s[1] = -e1 / e0^2 (for X_0).
 __global__ void gain_kernel(const double* __restrict__ e, double* __restrict__ J, double* __restrict__ s) {

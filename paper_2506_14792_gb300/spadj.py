@@ -33,6 +33,7 @@ SPADJ_RK222 = 3
 SPADJ_OBJ_ENERGY = 0
 SPADJ_OBJ_FOURDVAR = 1
 SPADJ_OBJ_GAIN = 2
+SPADJ_OBJ_ENERGY_INTEGRAL = 3
 
 C2G, G2C, C2G_ADJ, G2C_ADJ = 0, 1, 2, 3
 
