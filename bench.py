@@ -466,6 +466,8 @@ def run_gpu(args, wl):
         wl.p.set_option(6, 1)
     if args.no_fuse:
         wl.p.set_option(7, 0)
+    if args.x_rows:
+        wl.p.set_option(8, args.x_rows)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev) if wl.flush_l2 else None
 
@@ -576,6 +578,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
     ap.add_argument("--pdl", action="store_true", help="programmatic dependent launch of consecutive kernels")
     ap.add_argument("--no-fuse", action="store_true", help="RB: separate fold / solve / expand kernels")
+    ap.add_argument("--x-rows", type=int, default=0, help="x-FFT rows per CTA (1, 2, 4; 0 = tuned)")
     ap.add_argument("--nsteps", type=int, default=None, help="override the workload's time steps (profiling runs)")
     ap.add_argument("--size", default=None,
                     help="override the grid of the rb (Nx,Nz) or couette (Nx,Ny,Nz) workload (profiling runs)")

@@ -225,7 +225,9 @@ spadj_status spadj_set_params(spadj_problem* prob, const double* params);
  * is scheduled while its predecessor drains and waits for it on the device; 0, default: plain
  * stream order); option 7 (SPADJ_RB2D) = fused column stage (1, default: the z fold, the stage
  * solve and the z expansion of each x-mode pencil run in one two-CTA cluster kernel; 0: three
- * separate kernels).  Set both before the first sweep (the step graphs are captured once).
+ * separate kernels); option 8 (SPADJ_RB2D, SPADJ_COUETTE3D) = grid rows per CTA of the x FFTs
+ * (1, 2 or 4; by default the fastest is picked by timing when the problem is created).  Set
+ * them before the first sweep (the step graphs are captured once).
  * spadj_autotune times candidate settings on the problem's own sizes and keeps the fastest. */
 spadj_status spadj_set_option(spadj_problem* prob, int option, int value);
 spadj_status spadj_autotune(spadj_problem* prob);

@@ -134,6 +134,11 @@ spadj_status spadj_set_option(spadj_problem* p, int option, int value) {
     p->fuse_columns = value != 0;
     return SPADJ_OK;
   }
+  if (option == 8) {
+    if (value != 1 && value != 2 && value != 4) return p->fail(SPADJ_ERR_INVALID, "set_option 8: rows per CTA must be 1, 2 or 4");
+    p->x_rows = value;
+    return SPADJ_OK;
+  }
   return spadj::kol_set_option(p->impl, p, option, value);
 }
 

@@ -42,6 +42,7 @@ struct Couette : EqImpl {
   DevBuf wmx, w2y, czE, cdzE, gzF, gzTE, czTF, cdzTF, gmat, phi1F, phi1A, phi2F, phi2A, one;
   DevBuf Zm, Ym, Gf, dGf, Gb, Fg, Xr, Fr, dXr, dFr, Wr, xbar, src0, partial, edev, sdev, Jdev, slots, wts;
   size_t zsmem = 0, xsmem = 0, ysmem = 0;
+  int xnb = 1;  // x-FFT rows per CTA (tuned at creation)
 
   size_t state_len(int which) const override {
     if (which == 0) return 2 * ns;
@@ -168,6 +169,15 @@ struct Couette : EqImpl {
     zsmem = (size_t)2 * 2 * (size_t)std::max(N, Mz / 2) * kTM * sizeof(double2);
     xsmem = sizeof(double2) * (4 * L + Kx);
     ysmem = sizeof(double2) * 2 * (size_t)My * yp.TK;
+    {  // x-FFT rows per CTA, timed on the six inverse transforms of one F evaluation
+      SPADJ_CUDA_TRY(p, cudaMemsetAsync(Ym.ptr, 0, Ym.bytes, p->stream));
+      XJobs xj{};
+      for (int q = 0; q < 6; ++q) xj.j[q] = xc2r(ym(q), 1.0, 1.0, grid(Gf, q));
+      xj.n = 6;
+      cudaError_t e = cudaSuccess;
+      xnb = tune_xfft_rows(xj, xp, Mz * My, p->stream, p->x_rows, &e);
+      SPADJ_CUDA_TRY(p, e);
+    }
     return SPADJ_OK;
   }
 
@@ -236,7 +246,7 @@ struct Couette : EqImpl {
   spadj_status launch_x(Problem* p, XJobs& js) {
     const double f = js.n * (double)Mz * My * 2.5 * Mx * std::log2((double)Mx);
     cudaEvent_t t = p->tic();
-    SPADJ_CUDA_TRY(p, launch_kernel(p->pdl, xfft_kernel, dim3(Mz * My, js.n), dim3(64), xsmem, p->stream, js, xp));
+    SPADJ_CUDA_TRY(p, launch_xfft(p->pdl, p->x_rows ? p->x_rows : xnb, js, xp, Mz * My, p->stream));
     p->toc(t, KC_XFFT, f);
     return check_launch(p, "couette xfft");
   }

@@ -114,6 +114,7 @@ struct Problem {
   Timing timing;
   bool pdl = false;          // programmatic dependent launch of consecutive kernels (spadj_set_option 6)
   bool fuse_columns = true;  // RB: fused fold + solve + expand cluster kernel (spadj_set_option 7)
+  int x_rows = 0;            // x-FFT rows per CTA: 0 = tuned at creation, else 1, 2 or 4 (option 8)
   cudaEvent_t tic() {
     if (!timing.enabled) return nullptr;
     cudaEvent_t e = timing.get();

@@ -51,6 +51,7 @@ struct RB : EqImpl {
   WS* w = &ws[0];
   size_t zsmem = 0, xsmem = 0, ssmem = 0, csmem = 0, ctsmem = 0;
   bool fused = false;  // fused column stage (rb_colstep_kernel) usable for these sizes
+  int xnb = 1;         // x-FFT rows per CTA (tuned at creation)
   // internal streams (joined to the caller's stream by events) and captured step graphs
   cudaStream_t gs = nullptr, gs2 = nullptr, gsB = nullptr;
   cudaEvent_t evIn = nullptr, evOut = nullptr, evFork = nullptr, evJoin = nullptr;
@@ -198,6 +199,12 @@ struct RB : EqImpl {
       SPADJ_CUDA_TRY(p, cudaFuncSetAttribute(rb_colstep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csmem));
       SPADJ_CUDA_TRY(p, cudaFuncSetAttribute(rb_colstepT_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ctsmem));
     }
+    {  // x-FFT rows per CTA, timed on the eight inverse transforms of one F evaluation
+      SPADJ_CUDA_TRY(p, cudaMemsetAsync(w->Z.ptr, 0, w->Z.bytes, p->stream));
+      cudaError_t e = cudaSuccess;
+      xnb = tune_xfft_rows(c2r_jobs(w->G0), xp, Mz, p->stream, p->x_rows, &e);
+      SPADJ_CUDA_TRY(p, e);
+    }
     if (ssmem > 48 * 1024)
       SPADJ_CUDA_TRY(p, cudaFuncSetAttribute(solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssmem));
     return SPADJ_OK;
@@ -227,7 +234,7 @@ struct RB : EqImpl {
   }
   spadj_status launch_x(Problem* p, XJobs& js) {
     cudaEvent_t t = p->tic();
-    SPADJ_CUDA_TRY(p, launch_kernel(p->pdl, xfft_kernel, dim3(Mz, js.n), dim3(64), xsmem, p->stream, js, xp));
+    SPADJ_CUDA_TRY(p, launch_xfft(p->pdl, p->x_rows ? p->x_rows : xnb, js, xp, Mz, p->stream));
     p->toc(t, KC_XFFT, xflops(js));
     return check_launch(p, "rb xfft");
   }
@@ -277,6 +284,10 @@ struct RB : EqImpl {
 
   // x-inverse FFTs of the six mixed columns in Z into the eight grid fields of G
   spadj_status c2r_fields(Problem* p, DevBuf& G) {
+    XJobs xj = c2r_jobs(G);
+    return launch_x(p, xj);
+  }
+  XJobs c2r_jobs(DevBuf& G) {
     XJobs xj{};
     xj.j[0] = xc2r(mix(w->Z, 0), 0, 1.0, 1.0, grid(G, 0));
     xj.j[1] = xc2r(mix(w->Z, 0), 1, 1.0, 1.0, grid(G, 1));
@@ -287,7 +298,7 @@ struct RB : EqImpl {
     xj.j[6] = xc2r(mix(w->Z, 4), 1, 1.0, 1.0, grid(G, 6));
     xj.j[7] = xc2r(mix(w->Z, 5), 0, 1.0, 1.0, grid(G, 7));
     xj.n = 8;
-    return launch_x(p, xj);
+    return xj;
   }
 
   // the three grid products of F (or of its JVP when dGp is non-null) -> T-space state f

@@ -318,6 +318,166 @@ __global__ void __launch_bounds__(64) xfft_kernel(const __grid_constant__ XJobs 
   }
 }
 
+// xfft_kernel's jobs for nb rows per CTA (nb <= 4): the rows are interleaved in shared memory
+// (element e of row c at e * nb + c) and transformed together by cfft_smem_batch, so short rows
+// keep all threads of the CTA busy in every Stockham pass and share its barriers.
+__global__ void __launch_bounds__(64) xfftm_kernel(const __grid_constant__ XJobs js, XParams P, int nb, int nrows) {
+  pdl_trigger();
+  pdl_wait();
+  const XJob& J = js.j[blockIdx.y];
+  const int row0 = blockIdx.x * nb;
+  const int L = P.L, Kx = P.Kx, Mx = P.Mx;
+  extern __shared__ double2 sx[];
+  double2* A = sx;
+  double2* B = A + (size_t)L * nb;
+  double2* C = B + (size_t)L * nb;
+  double2* D = C + (size_t)L * nb;
+  double2* S = D + (size_t)L * nb;  // [nb][Kx]
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (J.dir == 0) {
+    for (int idx = tid; idx < nb * Kx; idx += nt) {
+      const int c = idx / Kx, k = idx - c * Kx;
+      double2 v = make_double2(0.0, 0.0);
+      if (row0 + c < nrows) {
+        v = J.cin[(size_t)(row0 + c) * Kx + k];
+        if (J.cmul == 1) {  // i k v
+          const double kk = P.kscale * k;
+          v = make_double2(-kk * v.y, kk * v.x);
+        }
+      }
+      S[idx] = v;
+    }
+    __syncthreads();
+    // packed spectrum of each real row (c2r_pre), interleaved
+    for (int idx = tid; idx < nb * L; idx += nt) {
+      const int k = idx / nb, c = idx - k * nb;
+      const double2* Sr = S + (size_t)c * Kx;
+      double2 xk = make_double2(0.0, 0.0), xc = make_double2(0.0, 0.0);
+      if (k == 0) xk = make_double2(J.w0 * Sr[0].x, 0.0);
+      else if (k < Kx) xk = cscale(Sr[k], J.w);
+      const int kc = L - k;
+      if (k > 0 && kc < Kx) xc = cconj(cscale(Sr[kc], J.w));
+      const double2 e = cadd(xk, xc);
+      const double2 o = cmul(csub(xk, xc), cconj(__ldg(&P.WM[k])));
+      A[idx] = make_double2(e.x - o.y, e.y + o.x);
+    }
+    __syncthreads();
+    const double2* z = cfft_smem_batch<1>(A, B, P.plan, P.WM, nb);
+    for (int idx = tid; idx < nb * L; idx += nt) {
+      const int c = idx / L, j = idx - c * L;
+      if (row0 + c < nrows) reinterpret_cast<double2*>(J.rout + (size_t)(row0 + c) * Mx)[j] = z[j * nb + c];
+    }
+    return;
+  }
+  const int nin = J.nprod > 0 ? 1 : J.nr;
+  for (int idx = tid; idx < nb * L; idx += nt) {
+    const int c = idx / L, j = idx - c * L;
+    double2 v0 = make_double2(0.0, 0.0), v1 = make_double2(0.0, 0.0);
+    if (row0 + c < nrows) {
+      const size_t ro = (size_t)(row0 + c) * Mx;
+      if (J.nprod > 0) {
+        auto at = [&](const double* base, int slot) {
+          return reinterpret_cast<const double2*>(base + (size_t)slot * J.npts + ro)[j];
+        };
+        const double2 a = at(J.G, J.pa[0]), b = at(J.G, J.pb[0]), cc = at(J.G, J.pa[1]), d = at(J.G, J.pb[1]);
+        const double p0 = J.ps[0], p1 = J.ps[1];
+        if (!J.dG) {
+          v0 = make_double2(fma(p0 * a.x, b.x, p1 * (cc.x * d.x)), fma(p0 * a.y, b.y, p1 * (cc.y * d.y)));
+        } else {
+          const double2 da = at(J.dG, J.pa[0]), db = at(J.dG, J.pb[0]), dc = at(J.dG, J.pa[1]), dd = at(J.dG, J.pb[1]);
+          v0 = make_double2(p0 * (da.x * b.x + a.x * db.x) + p1 * (dc.x * d.x + cc.x * dd.x),
+                            p0 * (da.y * b.y + a.y * db.y) + p1 * (dc.y * d.y + cc.y * dd.y));
+        }
+      } else {
+        v0 = reinterpret_cast<const double2*>(J.rin[0] + ro)[j];
+        if (nin > 1) v1 = reinterpret_cast<const double2*>(J.rin[1] + ro)[j];
+      }
+    }
+    A[j * nb + c] = v0;
+    if (nin > 1) C[j * nb + c] = v1;
+  }
+  __syncthreads();
+  const double2* z0 = cfft_smem_batch<-1>(A, B, P.plan, P.WM, nb);
+  const double2* z1 = nin > 1 ? cfft_smem_batch<-1>(C, D, P.plan, P.WM, nb) : nullptr;
+  for (int idx = tid; idx < nb * Kx; idx += nt) {
+    const int c = idx / Kx, k = idx - c * Kx;
+    if (row0 + c >= nrows) continue;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int t = 0; t < nin; ++t) {
+      const double2* Z = t == 0 ? z0 : z1;
+      const double2 zk = Z[k * nb + c];
+      const double2 zc = cconj(Z[(k == 0 ? 0 : L - k) * nb + c]);
+      const double2 e = cscale(cadd(zk, zc), 0.5);
+      const double2 d = csub(zk, zc);
+      const double2 o = make_double2(0.5 * d.y, -0.5 * d.x);
+      double2 X = cadd(e, cmul(o, __ldg(&P.WM[k])));
+      if (J.rmul[t] == 2) {  // -i k X
+        const double kk = P.kscale * k;
+        X = make_double2(kk * X.y, -kk * X.x);
+      }
+      acc = cadd(acc, X);
+    }
+    const double sc = (k == 0) ? J.s0 : J.s;
+    double2 out = cscale(acc, sc);
+    if (k == 0) out.y = 0.0;
+    J.cout[(size_t)(row0 + c) * Kx + k] = out;
+  }
+}
+
+inline size_t xfftm_smem(int L, int Kx, int nb) { return sizeof(double2) * (size_t)nb * (4 * L + Kx); }
+constexpr int kXRowsMax = 4;
+
+// x-transform jobs over nrows rows with nb rows per CTA (nb = 1: xfft_kernel)
+inline cudaError_t launch_xfft(bool pdl, int nb, const XJobs& js, const XParams& xp, int nrows, cudaStream_t st) {
+  if (nb <= 1)
+    return launch_kernel(pdl, xfft_kernel, dim3(nrows, js.n), dim3(64), xfftm_smem(xp.L, xp.Kx, 1), st, js, xp);
+  return launch_kernel(pdl, xfftm_kernel, dim3((nrows + nb - 1) / nb, js.n), dim3(64), xfftm_smem(xp.L, xp.Kx, nb), st,
+                       js, xp, nb, nrows);
+}
+
+// Rows per CTA for the x transforms of this problem: `forced` (1, 2 or 4) or, when 0, the
+// fastest of 1, 2, 4 on the problem's own job set (timed with CUDA events, first run of each
+// discarded).  Also raises the shared-memory limit of the multi-row kernel when needed.
+inline int tune_xfft_rows(const XJobs& js, const XParams& xp, int nrows, cudaStream_t st, int forced,
+                          cudaError_t* err) {
+  *err = cudaSuccess;
+  // candidates whose shared memory fits one CTA (raising the opt-in limit where needed)
+  bool ok[kXRowsMax + 1] = {false, false, false, false, false};
+  for (int nb : {1, 2, 4}) {
+    const size_t sm = xfftm_smem(xp.L, xp.Kx, nb);
+    if (sm <= 48 * 1024) {
+      ok[nb] = true;
+    } else if (sm <= 227 * 1024) {
+      cudaError_t e = nb == 1 ? cudaFuncSetAttribute(xfft_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)
+                              : cudaFuncSetAttribute(xfftm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      ok[nb] = e == cudaSuccess;
+      cudaGetLastError();
+    }
+  }
+  if (forced == 1 || forced == 2 || forced == 4) return forced;
+  if (!ok[1]) return 1;  // rows too long for any variant: launches will report the error
+  cudaEvent_t a = nullptr, b = nullptr;
+  if ((*err = cudaEventCreate(&a)) != cudaSuccess) return 1;
+  if ((*err = cudaEventCreate(&b)) != cudaSuccess) { cudaEventDestroy(a); return 1; }
+  int best_nb = 1;
+  float best = 1e30f;
+  for (int nb : {1, 2, 4}) {
+    if (!ok[nb]) continue;
+    for (int rep = 0; rep < 4 && *err == cudaSuccess; ++rep) {
+      cudaEventRecord(a, st);
+      *err = launch_xfft(false, nb, js, xp, nrows, st);
+      cudaEventRecord(b, st);
+      if (*err == cudaSuccess) *err = cudaEventSynchronize(b);
+      float ms = 0.f;
+      if (*err == cudaSuccess) cudaEventElapsedTime(&ms, a, b);
+      if (rep > 0 && ms < best) { best = ms; best_nb = nb; }
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return best_nb;
+}
+
 // Grid-field slots: 0 u, 1 ux, 2 uz, 3 w, 4 wx, 5 wz, 6 tx, 7 tz (the forward and tangent
 // products are formed inside xfft_kernel from product specs; the reverse products have their
 // own kernel).

@@ -121,6 +121,24 @@ def test_pencil_solve_and_adjoint(Nx, Ny, Nz):
     assert rel_err(to_oracle(host(out)), step_solve(o, v, 1.5 / DT, transpose=True)) < 1e-12
 
 
+@pytest.mark.parametrize("Nx,Ny,Nz", [(16, 6, 12), (32, 8, 16)])
+def test_x_rows_per_cta_bitwise(Nx, Ny, Nz):
+    """F and its VJP agree bitwise for 1, 2 and 4 x-FFT rows per CTA."""
+    o = oco.Couette(Nx, Ny, Nz, RE, pencils=False)
+    s, d = rand_fields(o, 21), rand_fields(o, 22)
+    outs = []
+    for nb in (1, 2, 4):
+        p = gpu_problem(Nx, Ny, Nz)
+        p.set_option(8, nb)
+        f = _zc((3, o.Ny, o.Kx, o.N))
+        v = _zc((3, o.Ny, o.Kx, o.N))
+        p.eval_F(dev(to_gpu(s)), f)
+        p.eval_F_vjp(dev(to_gpu(s)), dev(to_gpu(d)), v)
+        outs.append((f, v))
+    for f, v in outs[1:]:
+        assert torch.equal(f, outs[0][0]) and torch.equal(v, outs[0][1])
+
+
 @pytest.fixture(scope="module")
 def traj_case():
     Nx, Ny, Nz, n = 16, 6, 12, 12

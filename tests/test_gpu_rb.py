@@ -206,3 +206,22 @@ def test_fused_column_stage_matches_separate_kernels():
         out.append((J[0], host(g)))
     assert abs(out[0][0] - out[1][0]) <= 1e-13 * abs(out[1][0])
     assert rel_err(out[0][1], out[1][1]) < 1e-12
+
+
+@pytest.mark.parametrize("Nx,Nz", [(16, 12), (256, 64)])
+def test_x_rows_per_cta_bitwise(Nx, Nz):
+    """The multi-row x FFT (rows interleaved, transformed together) performs the same
+    arithmetic per row as the one-row kernel: F and its VJP agree bitwise for 1, 2, 4 rows."""
+    o = orb.RayleighBenard(Nx, Nz, 1e6)
+    s, d = _rand_state(o, 7), _rand_state(o, 8)
+    outs = []
+    for nb in (1, 2, 4):
+        p = gpu_problem(Nx, Nz)
+        p.set_option(8, nb)
+        f = _z((3, o.Kx, o.N))
+        v = _z((3, o.Kx, o.N))
+        p.eval_F(dev(s), f)
+        p.eval_F_vjp(dev(s), dev(d), v)
+        outs.append((f, v))
+    for f, v in outs[1:]:
+        assert torch.equal(f, outs[0][0]) and torch.equal(v, outs[0][1])
