@@ -267,6 +267,18 @@ spadj_status spadj_timing_report(spadj_problem* prob, int kernel_class, double* 
 spadj_status spadj_vjp(spadj_problem* prob, const double* x0, int n_steps, int ckpt_slots, int n_seeds,
                        const int* seed_steps, const double* seeds, double* grad_x0);
 
+/* Resolvent gains of the linear operator (SPADJ_COUETTE3D): for every (kx, ky) pencil, the
+ * leading gain sigma_1 = max ||R f||_E / ||f||_E of R(omega) = prognostic part of
+ * (i omega M + L)^-1 [S1S0 f; 0] (the response of u, v, w to a momentum forcing f at frequency
+ * omega) in the energy norm ||c||_E^2 = sum over u, v, w of c^H G c (G_mn = int T_m T_n dz),
+ * by n_iter power iterations on R^H G R f = sigma^2 G f for all pencils at once, with the
+ * transposed pencil solves supplying R^H (the LBVP adjoint).  f (device, state layout) is the
+ * initial forcing on entry and the leading forcing (unit energy per pencil) on exit; gains
+ * (device, [Ny][Nx/2] doubles) receives sigma_1 per pencil (0 where the initial forcing of the
+ * pencil is zero).  The pencil factorisations of (i omega M + L) are built on the first call
+ * for a frequency and kept until another frequency is asked for. */
+spadj_status spadj_resolvent(spadj_problem* prob, double omega, int n_iter, double* f, double* gains);
+
 /* One-line description of the last failure on this problem (or of the last failed
  * spadj_create when prob is NULL).  Never NULL. */
 const char* spadj_last_error(const spadj_problem* prob);

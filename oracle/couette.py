@@ -335,3 +335,28 @@ def gain_gradient(prob, X0, nsteps, dt):
 
     g = imex.multistep_adjoint(prob, X, dJ, dt)
     return J, g, X
+
+
+# ---- resolvent gains (linear operator of the pencils, energy norm) -------------------------
+def resolvent_matrix(prob, a, b, omega):
+    """R = prognostic part of (i omega M + L)^-1 [S1S0 f; 0] for the pencil (kx, ky) = (a, b):
+    the response of (u, v, w) to a forcing f of the momentum equations at frequency omega
+    (3N x 3N, T coefficients in and out)."""
+    N = prob.N
+    Mm, Lm = prob.pencil_matrices(a, b, mean=(a == 0 and b == 0))
+    A = 1j * omega * Mm + Lm
+    B = np.zeros((prob.nvar, 3 * N), dtype=np.complex128)
+    for f in range(3):
+        B[f * N:(f + 1) * N, f * N:(f + 1) * N] = prob.SS
+    return np.linalg.solve(A, B)[:3 * N]
+
+
+def resolvent_gain(prob, a, b, omega):
+    """Leading gain sigma_1 = max ||R f||_E / ||f||_E in the energy norm ||c||_E^2 = c^H G3 c,
+    G3 = blockdiag(G, G, G) (int T_m T_n dz), from the generalised Hermitian eigenproblem
+    R^H G3 R f = sigma^2 G3 f."""
+    import scipy.linalg as sla
+    R = resolvent_matrix(prob, a, b, omega)
+    G3 = sla.block_diag(prob.G, prob.G, prob.G)
+    ev = sla.eigh(R.conj().T @ G3 @ R, G3, eigvals_only=True)
+    return float(np.sqrt(ev[-1]))

@@ -103,6 +103,12 @@ spadj_status spadj_solve(spadj_problem* p, int transpose, const double* v, doubl
   return spadj::rb_pencil_solve(p->impl, p, transpose, v, x);
 }
 
+spadj_status spadj_resolvent(spadj_problem* p, double omega, int n_iter, double* f, double* gains) {
+  if (!p) return SPADJ_ERR_INVALID;
+  if (bad_ptr(f) || bad_ptr(gains)) return p->fail(SPADJ_ERR_INVALID, "resolvent: NULL array");
+  return spadj::cou_resolvent(p->impl, p, omega, n_iter, f, gains);
+}
+
 spadj_status spadj_vjp(spadj_problem* p, const double* x0, int n_steps, int ckpt_slots, int n_seeds,
                        const int* seed_steps, const double* seeds, double* grad_x0) {
   if (!p) return SPADJ_ERR_INVALID;

@@ -41,7 +41,11 @@ struct Couette : EqImpl {
   YParams yp{};
   DevBuf wmx, w2y, czE, cdzE, gzF, gzTE, czTF, cdzTF, gmat, phi1F, phi1A, phi2F, phi2A, one;
   DevBuf Zm, Ym, Gf, dGf, Gb, Fg, Xr, Fr, dXr, dFr, Wr, xbar, src0, partial, edev, sdev, Jdev, slots, wts;
+  DevBuf phiRF, phiRA, ginv, nrm, g2;  // resolvent operators of the last frequency, G^-1, per-pencil norms
+  double res_omega = 0.0;
+  bool res_built = false;
   size_t zsmem = 0, xsmem = 0, ysmem = 0;
+  rbhost::Operators ops;
   int xnb = 1;  // x-FFT rows per CTA (tuned at creation)
 
   size_t state_len(int which) const override {
@@ -99,6 +103,7 @@ struct Couette : EqImpl {
       return p->fail(SPADJ_ERR_INVALID, "couette: 3*n[0]/4 and 3*n[1]/2 must be of the form 2^a 3^b");
 
     rbhost::Operators o = rbhost::build_operators(N, Mz, 1.0);
+    ops = o;
     std::vector<double> f1, a1, f2, a2;
     std::string err;
     if (!couhost::build_phi(o, Kx, Ny, Lx, Ly, nu, 1.0 / dt, f1, a1, &err)) return p->fail(SPADJ_ERR_INVALID, err);
@@ -405,11 +410,17 @@ struct Couette : EqImpl {
   // scheme order 1 or 2 selects the SBDF1 or SBDF2 operator.
   spadj_status solve(Problem* p, int transpose, int ord, int nin, const double2* const* in, const double* a,
                      double2* out) {
+    return solve_with(p, transpose, (ord == 1 ? phi1F : phi2F).as<double2>(), (ord == 1 ? phi1A : phi2A).as<double2>(),
+                      1, nin, in, a, out);
+  }
+  spadj_status solve_with(Problem* p, int transpose, const double2* phiF_, const double2* phiA_, int project, int nin,
+                          const double2* const* in, const double* a, double2* out) {
     CouSolveArgs S{};
     for (int t = 0; t < nin; ++t) { S.in[t] = in[t]; S.a[t] = a[t]; }
     S.nin = nin; S.out = out; S.transpose = transpose;
-    S.phiF = (ord == 1 ? phi1F : phi2F).as<double2>();
-    S.phiA = (ord == 1 ? phi1A : phi2A).as<double2>();
+    S.phiF = phiF_;
+    S.phiA = phiA_;
+    S.project = project;
     S.Kx = Kx; S.Ny = Ny; S.N = N;
     const int H = 3 * N;
     const int threads = ((H + 31) / 32) * 32;
@@ -743,6 +754,80 @@ struct Couette : EqImpl {
     return reverse(p, x0, n_steps, ckpt_slots, -1, seed_at, seeds, nullptr, grad);
   }
 
+  // ---- resolvent gains -----------------------------------------------------------------------
+  // Leading gain per (kx, ky) pencil of the resolvent R(omega) = [(i omega M + L)^-1]_prog S1S0
+  // in the energy norm ||c||^2 = c^H G c per field: power iteration on the generalised problem
+  // R^H G R f = sigma^2 G f, all pencils at once.  f (state layout) holds the initial forcing on
+  // entry and the leading forcing (unit energy per pencil) on exit; gains[Ny][Kx] the gains.
+  spadj_status resolvent(Problem* p, double omega, int n_iter, double* f_io, double* gains) {
+    if (n_iter < 1) return p->fail(SPADJ_ERR_INVALID, "resolvent: n_iter < 1");
+    if (!res_built || omega != res_omega) {
+      std::vector<double> rf, ra;
+      std::string err;
+      if (!couhost::build_phi(ops, Kx, Ny, Lx, Ly, nu, std::complex<double>(0.0, omega), rf, ra, &err))
+        return p->fail(SPADJ_ERR_INVALID, err);
+      SPADJ_CUDA_TRY(p, phiRF.ensure(sizeof(double) * rf.size()));
+      SPADJ_CUDA_TRY(p, phiRA.ensure(sizeof(double) * ra.size()));
+      SPADJ_CUDA_TRY(p, cudaMemcpy(phiRF.ptr, rf.data(), sizeof(double) * rf.size(), cudaMemcpyHostToDevice));
+      SPADJ_CUDA_TRY(p, cudaMemcpy(phiRA.ptr, ra.data(), sizeof(double) * ra.size(), cudaMemcpyHostToDevice));
+      res_built = true;
+      res_omega = omega;
+    }
+    if (!ginv.ptr) {  // G^-1 by Gauss-Jordan elimination with partial pivoting (G is SPD, N x N)
+      std::vector<double> A(ops.G), I((size_t)N * N, 0.0);
+      for (int i = 0; i < N; ++i) I[(size_t)i * N + i] = 1.0;
+      for (int k = 0; k < N; ++k) {
+        int piv = k;
+        for (int i = k + 1; i < N; ++i)
+          if (std::fabs(A[(size_t)i * N + k]) > std::fabs(A[(size_t)piv * N + k])) piv = i;
+        for (int j = 0; j < N; ++j) {
+          std::swap(A[(size_t)k * N + j], A[(size_t)piv * N + j]);
+          std::swap(I[(size_t)k * N + j], I[(size_t)piv * N + j]);
+        }
+        const double d = A[(size_t)k * N + k];
+        for (int j = 0; j < N; ++j) { A[(size_t)k * N + j] /= d; I[(size_t)k * N + j] /= d; }
+        for (int i = 0; i < N; ++i) {
+          if (i == k) continue;
+          const double l = A[(size_t)i * N + k];
+          if (l == 0.0) continue;
+          for (int j = 0; j < N; ++j) { A[(size_t)i * N + j] -= l * A[(size_t)k * N + j]; I[(size_t)i * N + j] -= l * I[(size_t)k * N + j]; }
+        }
+      }
+      SPADJ_CUDA_TRY(p, ginv.ensure(sizeof(double) * I.size()));
+      SPADJ_CUDA_TRY(p, cudaMemcpy(ginv.ptr, I.data(), sizeof(double) * I.size(), cudaMemcpyHostToDevice));
+    }
+    SPADJ_CUDA_TRY(p, nrm.ensure(sizeof(double) * P));
+    SPADJ_CUDA_TRY(p, g2.ensure(sizeof(double) * P));
+    double2* f = reinterpret_cast<double2*>(f_io);
+    double2* y = st(Wr, 0);
+    double2* z = st(Wr, 1);
+    double2* t = st(Wr, 2);
+    spadj_status s;
+    auto gram = [&](const double2* in, const DevBuf& mat, double2* out, double* nr) -> spadj_status {
+      cudaEvent_t ev = p->tic();
+      cou_gram_kernel<<<P, 128, 0, p->stream>>>(in, mat.as<double>(), Kx, Ny, N, out, nr);
+      p->toc(ev, KC_OBJECTIVE, 8.0 * (double)P * 3 * N * N);
+      return check_launch(p, "couette gram");
+    };
+    auto normalise = [&](double* gout) -> spadj_status {
+      if ((s = gram(f, gmat, t, nrm.as<double>())) != SPADJ_OK) return s;
+      cou_pencil_scale_kernel<<<P, 128, 0, p->stream>>>(f, nrm.as<double>(), Kx, Ny, N, g2.as<double>(), gout);
+      return check_launch(p, "couette scale");
+    };
+    if ((s = normalise(nullptr)) != SPADJ_OK) return s;
+    const double one_[1] = {1.0};
+    for (int it = 0; it < n_iter; ++it) {
+      { const double2* in[1] = {f};
+        if ((s = solve_with(p, 0, phiRF.as<double2>(), phiRA.as<double2>(), 0, 1, in, one_, y)) != SPADJ_OK) return s; }
+      if ((s = gram(y, gmat, z, g2.as<double>())) != SPADJ_OK) return s;  // ||R f||_G^2 with ||f||_G = 1
+      { const double2* in[1] = {z};
+        if ((s = solve_with(p, 1, phiRF.as<double2>(), phiRA.as<double2>(), 0, 1, in, one_, t)) != SPADJ_OK) return s; }
+      if ((s = gram(t, ginv, f, nullptr)) != SPADJ_OK) return s;
+      if ((s = normalise(it + 1 == n_iter ? gains : nullptr)) != SPADJ_OK) return s;
+    }
+    return SPADJ_OK;
+  }
+
   // ---- single operations ---------------------------------------------------------------------
   spadj_status transform(Problem* p, int kind, const double* in, double* out) override {
     const double2* ci = reinterpret_cast<const double2*>(in);
@@ -802,7 +887,7 @@ struct Couette : EqImpl {
   ~Couette() override {
     for (DevBuf* b : {&wmx, &w2y, &czE, &cdzE, &gzF, &gzTE, &czTF, &cdzTF, &gmat, &phi1F, &phi1A, &phi2F, &phi2A, &one,
                       &Zm, &Ym, &Gf, &dGf, &Gb, &Fg, &Xr, &Fr, &dXr, &dFr, &Wr, &xbar, &src0, &partial, &edev, &sdev,
-                      &Jdev, &slots, &wts})
+                      &Jdev, &slots, &wts, &phiRF, &phiRA, &ginv, &nrm, &g2})
       b->release();
   }
 };
@@ -817,6 +902,12 @@ EqImpl* make_couette(Problem* p, spadj_status* st) {
     return nullptr;
   }
   return c;
+}
+
+spadj_status cou_resolvent(EqImpl* impl, Problem* p, double omega, int n_iter, double* f, double* gains) {
+  Couette* c = dynamic_cast<Couette*>(impl);
+  if (!c) return p->fail(SPADJ_ERR_UNSUPPORTED, "resolvent: only defined for the plane-Couette problem");
+  return c->resolvent(p, omega, n_iter, f, gains);
 }
 
 spadj_status cou_pencil_solve(EqImpl* impl, Problem* p, int transpose, const double* v, double* x) {

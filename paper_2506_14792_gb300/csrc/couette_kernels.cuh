@@ -121,6 +121,7 @@ struct CouSolveArgs {
   const double2* phiF;
   const double2* phiA;
   int Kx, Ny, N;
+  int project;  // 1: apply P (timestep solves); 0: plain per-pencil operator (resolvent)
 };
 
 __global__ void __launch_bounds__(1024) cou_solve_kernel(const __grid_constant__ CouSolveArgs S) {
@@ -130,7 +131,7 @@ __global__ void __launch_bounds__(1024) cou_solve_kernel(const __grid_constant__
   const int Kx = S.Kx, Ny = S.Ny, N = S.N, H = 3 * N;
   const int tid = threadIdx.x, nt = blockDim.x;
   auto off = [&](int c, int j) { return (((size_t)(c / N) * Ny + j) * Kx + m) * N + (c % N); };
-  if (jh == Ny / 2) {
+  if (jh == Ny / 2) {  // the ky = -Ny/2 row is not stored: held at zero
     for (int c = tid; c < H; c += nt) S.out[off(c, jh)] = make_double2(0.0, 0.0);
     return;
   }
@@ -151,7 +152,7 @@ __global__ void __launch_bounds__(1024) cou_solve_kernel(const __grid_constant__
         x2.y = fma(S.a[t], y2.y, x2.y);
       }
     }
-    if (S.transpose && m == 0) {  // projection of the input (self-adjoint)
+    if (S.project && S.transpose && m == 0) {  // projection of the input (self-adjoint)
       if (two) {
         const double2 h = make_double2(0.5 * (x1.x + x2.x), 0.5 * (x1.y - x2.y));
         x1 = h;
@@ -218,7 +219,7 @@ __global__ void __launch_bounds__(1024) cou_solve_kernel(const __grid_constant__
     }
     double2 x1 = cadd(a1, b1), x2 = cadd(a2, b2);
     if (r / N == 1) x2 = make_double2(-x2.x, -x2.y);  // D
-    if (!S.transpose && m == 0) {  // projection of the output
+    if (S.project && !S.transpose && m == 0) {  // projection of the output
       if (two) {
         const double2 h = make_double2(0.5 * (x1.x + x2.x), 0.5 * (x1.y - x2.y));
         x1 = h;
@@ -289,6 +290,54 @@ __global__ void cou_energy_kernel(const double2* __restrict__ x, const double* _
 // J += w[0] * e[0] (time-integrated objective: one term of I_N = sum_n s_n E(X_n))
 __global__ void integral_accum_kernel(const double* __restrict__ e, const double* __restrict__ w, double* __restrict__ J) {
   if (threadIdx.x == 0 && blockIdx.x == 0) J[0] = fma(w[0], e[0], J[0]);
+}
+
+// Per-pencil energy-norm algebra of the resolvent power iteration (Mat = the Gram matrix
+// G = int T_m T_n dz or its inverse, N x N, applied to each of the three fields):
+//   out = Mat in, and nrm[p] = Re(in^H out) when nrm is set.
+__global__ void cou_gram_kernel(const double2* __restrict__ in, const double* __restrict__ Mat, int Kx, int Ny, int N,
+                                double2* __restrict__ out, double* __restrict__ nrm) {
+  const int p = blockIdx.x;
+  const int j = p / Kx, m = p % Kx;
+  double acc = 0.0;
+  for (int idx = threadIdx.x; idx < 3 * N; idx += blockDim.x) {
+    const int f = idx / N, i = idx % N;
+    const size_t base = (((size_t)f * Ny + j) * Kx + m) * N;
+    double2 g = make_double2(0.0, 0.0);
+    for (int k = 0; k < N; ++k) {
+      const double2 c = in[base + k];
+      const double mv = __ldg(&Mat[i * N + k]);
+      g.x = fma(mv, c.x, g.x);
+      g.y = fma(mv, c.y, g.y);
+    }
+    out[base + i] = g;
+    const double2 ci = in[base + i];
+    acc += ci.x * g.x + ci.y * g.y;
+  }
+  if (!nrm) return;
+  __shared__ double red[128];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) nrm[p] = red[0];
+}
+
+// x /= sqrt(s[p]) per pencil (x = 0 where s[p] <= 0); gains[p] = sqrt(g2[p]) when gains is set
+__global__ void cou_pencil_scale_kernel(double2* __restrict__ x, const double* __restrict__ s, int Kx, int Ny, int N,
+                                        const double* __restrict__ g2, double* __restrict__ gains) {
+  const int p = blockIdx.x;
+  const int j = p / Kx, m = p % Kx;
+  const double sp = s[p];
+  const double inv = sp > 0.0 ? 1.0 / sqrt(sp) : 0.0;
+  for (int idx = threadIdx.x; idx < 3 * N; idx += blockDim.x) {
+    const int f = idx / N, i = idx % N;
+    const size_t o = (((size_t)f * Ny + j) * Kx + m) * N + i;
+    x[o] = make_double2(inv * x[o].x, inv * x[o].y);
+  }
+  if (gains && threadIdx.x == 0) gains[p] = sqrt(fmax(g2[p], 0.0));
 }
 
 // e[0] = E(X_0), e[1] = E(X_N) -> J = e1 / e0 and the seed scales s[0] = 1 / e0 (for X_N),

@@ -83,7 +83,7 @@ void lu_solve_multi(const std::vector<cd>& a, const std::vector<int>& piv, int n
 
 // a0 M + L for the pencil (alpha, beta); ordering as documented in couette_setup.h.
 void assemble_pencil(const rbhost::Operators& o, const std::vector<double>& ZS, double al, double be, bool mean,
-                     double nu, double a0, std::vector<cd>& A) {
+                     double nu, cd a0, std::vector<cd>& A) {
   const int N = o.N, nv = 4 * N + 7;
   A.assign((size_t)nv * nv, cd(0.0, 0.0));
   auto at = [&](int r, int c) -> cd& { return A[(size_t)r * nv + c]; };
@@ -134,7 +134,7 @@ void assemble_pencil(const rbhost::Operators& o, const std::vector<double>& ZS, 
 
 }  // namespace
 
-bool build_phi(const rbhost::Operators& o, int Kx, int Ny, double Lx, double Ly, double nu, double a0,
+bool build_phi(const rbhost::Operators& o, int Kx, int Ny, double Lx, double Ly, double nu, cd a0,
                std::vector<double>& phiF, std::vector<double>& phiA, std::string* err) {
   const int N = o.N, nv = 4 * N + 7, H = 3 * N, Nyh = Ny / 2;
   // ZS = (S1 S0 on N + 1 modes) * (z T_n in the T basis of degree N), first N rows

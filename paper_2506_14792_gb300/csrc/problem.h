@@ -154,6 +154,7 @@ spadj_status kol_set_params(EqImpl* impl, Problem* p, const double* params);
 spadj_status rb_transform_noalloc(EqImpl* impl, Problem* p, int kind, const double* in, double* out);
 EqImpl* make_couette(Problem* p, spadj_status* st);
 spadj_status cou_pencil_solve(EqImpl* impl, Problem* p, int transpose, const double* v, double* x);
+spadj_status cou_resolvent(EqImpl* impl, Problem* p, double omega, int n_iter, double* f, double* gains);
 
 }  // namespace spadj
 

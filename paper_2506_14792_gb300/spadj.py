@@ -64,6 +64,7 @@ _SIGS = {
     "spadj_eval_F_vjp": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "spadj_solve": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp]),
     "spadj_vjp": (ctypes.c_int, [_vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp]),
+    "spadj_resolvent": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_int, _vp, _vp]),
     "spadj_set_observations": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, ctypes.c_int]),
     "spadj_set_option": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
     "spadj_autotune": (ctypes.c_int, [_vp]),
@@ -261,6 +262,14 @@ class Problem:
                                       steps, _ptr(_as_f64(seeds, n * len(seed_steps), "seeds")),
                                       _ptr(_as_f64(grad_x0, n, "grad_x0"))))
         return grad_x0
+
+    def resolvent(self, omega, n_iter, f, gains):
+        """Leading energy-norm resolvent gain per (kx, ky) pencil at frequency omega (power
+        iteration); f: initial forcing in, leading forcing out; gains: [Ny][Nx/2] float64."""
+        n = self.state_len(0)
+        _chk(self.h, lib().spadj_resolvent(self.h, float(omega), int(n_iter), _ptr(_as_f64(f, n, "f")),
+                                            _ptr(_as_f64(gains, self.desc.n[1] * (self.desc.n[0] // 2), "gains"))))
+        return gains
 
     KERNEL_CLASSES = ("z_transform", "x_fft", "pointwise", "pencil_solve", "objective", "fused_trajectory", "y_fft")
 

@@ -313,3 +313,23 @@ def test_full_trajectory_dot_and_fd(full_case):
     fd = (Jp - Jm) / (2 * eps)
     ad = float(torch.sum((torch.conj(g) * d).real))
     assert abs(fd - ad) <= 1e-6 * abs(fd), (fd, ad, J)
+
+
+
+def test_resolvent_gains_all_pencils():
+    """Energy-norm resolvent gains of every (kx, ky) pencil from the batched power iteration
+    (forward and transposed pencil solves) against the oracle's dense generalised eigenproblem."""
+    Nx, Ny, Nz, Re, om = 8, 4, 16, 300.0, 0.3
+    o = oco.Couette(Nx, Ny, Nz, Re, pencils=False)
+    p = gpu_problem(Nx, Ny, Nz, Re=Re)
+    f = dev(to_gpu(synthetic.random_coeffs((3, o.Kx, o.Ny, o.N), seed=61)))
+    gains = torch.zeros((Ny, Nx // 2), dtype=torch.float64, device="cuda")
+    p.resolvent(om, 120, f, gains)
+    gh = host(gains)
+    for j in range(Ny):
+        for m in range(o.Kx):
+            if j == Ny // 2:
+                assert gh[j, m] == 0.0  # the unstored ky Nyquist row
+                continue
+            want = oco.resolvent_gain(o, o.alpha[m], o.beta[j], om)
+            assert abs(gh[j, m] - want) <= 1e-10 * want, (j, m, gh[j, m], want)

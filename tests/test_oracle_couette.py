@@ -295,3 +295,23 @@ def test_couette_algebraic_initial_values_inert(couette_traj):
     Xa = imex.multistep_forward(p, X0, 3, 2e-2)[-1]
     Xc = imex.multistep_forward(p, Xb, 3, 2e-2)[-1]
     np.testing.assert_array_equal(p.state(Xa), p.state(Xc))
+
+
+def test_resolvent_gain_stokes_and_lift_up():
+    """Resolvent gains in the energy norm.  Mean pencil: the operator is diffusion of u and v
+    with no-slip walls, whose slowest mode decays at nu (pi/2)^2, so sigma_1 = 1/|i omega +
+    nu (pi/2)^2|; the tau discretisation converges to it at fourth order in N.  Streamwise-
+    independent pencil at omega = 0: lift-up makes sigma_1 grow as Re^2, sigma_1 / Re^2
+    converging as Re grows."""
+    for om in (0.0, 0.3):
+        errs = []
+        for N in (16, 24, 32):
+            p = co.Couette(4, 4, N, 300.0, pencils=False)
+            exact = 1.0 / np.hypot(om, p.nu * (np.pi / 2) ** 2)
+            errs.append(abs(co.resolvent_gain(p, 0.0, 0.0, om) / exact - 1.0))
+        rates = np.log(np.array(errs[:-1]) / np.array(errs[1:])) / np.log(np.array([24 / 16, 32 / 24]))
+        assert errs[-1] < 1e-6 and np.all(rates > 3.5), (errs, rates)
+    g = [co.resolvent_gain(co.Couette(4, 4, 48, Re, pencils=False), 0.0, 2.0, 0.0) / Re ** 2
+         for Re in (1000.0, 2000.0, 4000.0)]
+    d1, d2 = abs(g[1] / g[0] - 1), abs(g[2] / g[1] - 1)
+    assert d1 < 2e-4 and 3.0 < d1 / d2 < 5.0, (g, d1, d2)  # sigma_1 = c Re^2 (1 + O(Re^-2))
