@@ -267,6 +267,13 @@ spadj_status spadj_timing_report(spadj_problem* prob, int kernel_class, double* 
 spadj_status spadj_vjp(spadj_problem* prob, const double* x0, int n_steps, int ckpt_slots, int n_seeds,
                        const int* seed_steps, const double* seeds, double* grad_x0);
 
+/* Hessian-vector product (SPADJ_COUETTE3D, objective SPADJ_OBJ_ENERGY: J = E(X_N)):
+ * hv = (d^2 J / dX_0^2) v by tangent-over-adjoint: a forward sweep with its tangent along v
+ * (both trajectories stored, 2 (n_steps + 1) states of device memory held by the problem),
+ * then the adjoint recurrence and its tangent run together (three vector-Jacobian products and
+ * two transposed pencil solves per step).  x0, v, hv: device, state layout. */
+spadj_status spadj_hvp(spadj_problem* prob, const double* x0, const double* v, int n_steps, double* hv);
+
 /* Resolvent gains of the linear operator (SPADJ_COUETTE3D): for every (kx, ky) pencil, the
  * leading gain sigma_1 = max ||R f||_E / ||f||_E of R(omega) = prognostic part of
  * (i omega M + L)^-1 [S1S0 f; 0] (the response of u, v, w to a momentum forcing f at frequency

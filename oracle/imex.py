@@ -319,3 +319,39 @@ def integral_gradient(prob, X0, nsteps, dt, g, g_grad, order=2):
     seed = Aug(0.0 * X0, 1.0)
     lam = multistep_adjoint(aug, V, lambda n: seed if n == nsteps else None, dt, order)
     return J, lam.X, V
+
+
+# --------------------------------------------------------------------------------------
+# Hessian-vector products (tangent over adjoint, for explicit terms quadratic in X)
+# --------------------------------------------------------------------------------------
+
+def multistep_hvp(prob, X, dX, dJ, d2J, dt, order=2):
+    """(d^2 J / dX_0^2) v: the tangent, along the trajectory perturbation dX (the tangent of X
+    for dX_0 = v), of the adjoint recurrence of multistep_adjoint.  Differentiating
+    eq. IMEX_adjoint gives the same recurrence for dY with the extra source
+    sum_i c_i^{n+i} d/de[(dF/dX)(X_n + e dX_n)]^dagger Y_{n+i}, which for F quadratic in X is
+    F_vjp(dX_n, Y_{n+i}); d2J(n) is the tangent of dJ/dX_n (its Hessian applied to dX_n)."""
+    nsteps = len(X) - 1
+    Y = [None] * (nsteps + 1)
+    dY = [None] * (nsteps + 1)
+    coeffs = [None] + [sbdf_coeffs(n, order, dt) for n in range(1, nsteps + 1)]
+    for n in range(nsteps, -1, -1):
+        lam = dJ(n)
+        lam = 0 if lam is None else lam
+        dlam = d2J(n)
+        dlam = 0 if dlam is None else dlam
+        for i in range(1, order + 1):
+            m = n + i
+            if m > nsteps:
+                continue
+            a, b, c = coeffs[m]
+            if i > len(a) - 1:
+                continue
+            lam = lam + c[i] * prob.F_vjp(X[n], Y[m]) - (a[i] * prob.Mt(Y[m]) + b[i] * prob.Lt(Y[m]))
+            dlam = dlam + c[i] * (prob.F_vjp(X[n], dY[m]) + prob.F_vjp(dX[n], Y[m])) \
+                - (a[i] * prob.Mt(dY[m]) + b[i] * prob.Lt(dY[m]))
+        if n == 0:
+            return dlam
+        a, b, _ = coeffs[n]
+        Y[n] = prob.solve_t(a[0], b[0], prob.project(lam))
+        dY[n] = prob.solve_t(a[0], b[0], prob.project(dlam))

@@ -103,6 +103,12 @@ spadj_status spadj_solve(spadj_problem* p, int transpose, const double* v, doubl
   return spadj::rb_pencil_solve(p->impl, p, transpose, v, x);
 }
 
+spadj_status spadj_hvp(spadj_problem* p, const double* x0, const double* v, int n_steps, double* hv) {
+  if (!p) return SPADJ_ERR_INVALID;
+  if (bad_ptr(x0) || bad_ptr(v) || bad_ptr(hv)) return p->fail(SPADJ_ERR_INVALID, "hvp: NULL array");
+  return spadj::cou_hvp(p->impl, p, x0, v, n_steps, hv);
+}
+
 spadj_status spadj_resolvent(spadj_problem* p, double omega, int n_iter, double* f, double* gains) {
   if (!p) return SPADJ_ERR_INVALID;
   if (bad_ptr(f) || bad_ptr(gains)) return p->fail(SPADJ_ERR_INVALID, "resolvent: NULL array");

@@ -42,6 +42,7 @@ struct Couette : EqImpl {
   DevBuf wmx, w2y, czE, cdzE, gzF, gzTE, czTF, cdzTF, gmat, phi1F, phi1A, phi2F, phi2A, one;
   DevBuf Zm, Ym, Gf, dGf, Gb, Fg, Xr, Fr, dXr, dFr, Wr, xbar, src0, partial, edev, sdev, Jdev, slots, wts;
   DevBuf phiRF, phiRA, ginv, nrm, g2;  // resolvent operators of the last frequency, G^-1, per-pencil norms
+  DevBuf htraj, hdtraj, dWr, dxbar, htmp;  // Hessian-vector product: trajectories and second-order cotangents
   double res_omega = 0.0;
   bool res_built = false;
   size_t zsmem = 0, xsmem = 0, ysmem = 0;
@@ -754,6 +755,97 @@ struct Couette : EqImpl {
     return reverse(p, x0, n_steps, ckpt_slots, -1, seed_at, seeds, nullptr, grad);
   }
 
+  // ---- Hessian-vector product ----------------------------------------------------------------
+  // hv = (d^2 J / dX_0^2) v for J = E(X_N): forward sweep with its tangent along v (both
+  // trajectories stored), then the adjoint recurrence and its tangent together.  F = u x omega
+  // is quadratic, so the tangent of (dF/dx)(x_k)^H w along dx_k is (dF/dx)(dx_k)^H w: the VJP
+  // evaluated with the grid fields of dx_k.  The objective's Hessian is grad E (linear).
+  spadj_status hvp(Problem* p, const double* x0, const double* v, int n_steps, double* hv) {
+    if (n_steps < 1) return p->fail(SPADJ_ERR_INVALID, "hvp: n_steps < 1");
+    const size_t sb = sizeof(double2) * ns;
+    SPADJ_CUDA_TRY(p, htraj.ensure(sb * ((size_t)n_steps + 1)));
+    SPADJ_CUDA_TRY(p, hdtraj.ensure(sb * ((size_t)n_steps + 1)));
+    SPADJ_CUDA_TRY(p, dWr.ensure(3 * sb));
+    SPADJ_CUDA_TRY(p, dxbar.ensure(sb));
+    SPADJ_CUDA_TRY(p, htmp.ensure(sb));
+    SPADJ_CUDA_TRY(p, dXr.ensure(3 * sb));
+    SPADJ_CUDA_TRY(p, dFr.ensure(2 * sb));
+    double2* X = htraj.as<double2>();
+    double2* dX = hdtraj.as<double2>();
+    auto xs = [&](double2* base, int n) { return base + (size_t)n * ns; };
+    // forward and tangent, stored
+    Ring r;
+    SPADJ_CUDA_TRY(p, cudaMemcpyAsync(st(Xr, r.xc), x0, sb, cudaMemcpyDeviceToDevice, p->stream));
+    SPADJ_CUDA_TRY(p, cudaMemcpyAsync(st(dXr, r.xc), v, sb, cudaMemcpyDeviceToDevice, p->stream));
+    SPADJ_CUDA_TRY(p, cudaMemcpyAsync(xs(X, 0), x0, sb, cudaMemcpyDeviceToDevice, p->stream));
+    SPADJ_CUDA_TRY(p, cudaMemcpyAsync(xs(dX, 0), v, sb, cudaMemcpyDeviceToDevice, p->stream));
+    spadj_status s;
+    for (int n = 1; n <= n_steps; ++n) {
+      if ((s = evalF(p, st(Xr, r.xc), st(Fr, r.fc), Gf)) != SPADJ_OK) return s;
+      if ((s = evalJvp(p, Gf, st(dXr, r.xc), st(dFr, r.fc))) != SPADJ_OK) return s;
+      if ((s = step(p, n, st(Xr, r.xc), st(Xr, r.xp), st(Fr, r.fc), st(Fr, r.fp), st(Xr, r.xn))) != SPADJ_OK) return s;
+      if ((s = step(p, n, st(dXr, r.xc), st(dXr, r.xp), st(dFr, r.fc), st(dFr, r.fp), st(dXr, r.xn))) != SPADJ_OK)
+        return s;
+      r.advance();
+      SPADJ_CUDA_TRY(p, cudaMemcpyAsync(xs(X, n), st(Xr, r.xc), sb, cudaMemcpyDeviceToDevice, p->stream));
+      SPADJ_CUDA_TRY(p, cudaMemcpyAsync(xs(dX, n), st(dXr, r.xc), sb, cudaMemcpyDeviceToDevice, p->stream));
+    }
+    // seeds at X_N: grad E(X_N) and its tangent grad E(dX_N)
+    double2* xb = xbar.as<double2>();
+    double2* dxb = dxbar.as<double2>();
+    auto dW = [&](int n) { return st(dWr, n % 3); };
+    if ((s = energy(p, xs(X, n_steps), edev.as<double>(), one.as<double>(), xb)) != SPADJ_OK) return s;
+    if ((s = energy(p, xs(dX, n_steps), edev.as<double>() + 1, one.as<double>(), dxb)) != SPADJ_OK) return s;
+    { const double2* in[1] = {xb}; double w1[1] = {1.0};
+      if ((s = solve(p, 1, step_order(n_steps), 1, in, w1, W(n_steps))) != SPADJ_OK) return s; }
+    { const double2* in[1] = {dxb}; double w1[1] = {1.0};
+      if ((s = solve(p, 1, step_order(n_steps), 1, in, w1, dW(n_steps))) != SPADJ_OK) return s; }
+    for (int k = n_steps - 1; k >= 0; --k) {
+      const double2* fb[2];
+      const double2* dfb[2];
+      double al[2];
+      int nfb = 0;
+      const double2* ad[2];
+      const double2* dad[2];
+      double be[2];
+      int nad = 0;
+      double a[3], c[3];
+      if (k + 1 <= n_steps) {
+        coeffs(k + 1, a, c);
+        fb[nfb] = W(k + 1); dfb[nfb] = dW(k + 1); al[nfb++] = c[1];
+        ad[nad] = W(k + 1); dad[nad] = dW(k + 1); be[nad++] = -a[1];
+      }
+      if (k + 2 <= n_steps && step_order(k + 2) == 2) {
+        coeffs(k + 2, a, c);
+        fb[nfb] = W(k + 2); dfb[nfb] = dW(k + 2); al[nfb++] = c[2];
+        ad[nad] = W(k + 2); dad[nad] = dW(k + 2); be[nad++] = -a[2];
+      }
+      if (nonlinear) {
+        if ((s = c2g6(p, xs(X, k), Gf)) != SPADJ_OK) return s;
+        if ((s = evalVjp(p, Gf, nfb, fb, al, nad, ad, be, xb)) != SPADJ_OK) return s;
+        if ((s = evalVjp(p, Gf, nfb, dfb, al, nad, dad, be, htmp.as<double2>())) != SPADJ_OK) return s;
+        if ((s = c2g6(p, xs(dX, k), dGf)) != SPADJ_OK) return s;
+        const double2* ad1[1] = {htmp.as<double2>()};
+        double be1[1] = {1.0};
+        if ((s = evalVjp(p, dGf, nfb, fb, al, 1, ad1, be1, dxb)) != SPADJ_OK) return s;
+      } else {
+        axpy_kernel<<<256, 256, 0, p->stream>>>(xb, ad[0], be[0], nad > 1 ? ad[1] : nullptr, nad > 1 ? be[1] : 0.0,
+                                                nullptr, 0.0, ns);
+        axpy_kernel<<<256, 256, 0, p->stream>>>(dxb, dad[0], be[0], nad > 1 ? dad[1] : nullptr, nad > 1 ? be[1] : 0.0,
+                                                nullptr, 0.0, ns);
+        if ((s = check_launch(p, "couette axpy")) != SPADJ_OK) return s;
+      }
+      if (k >= 1) {
+        { const double2* in[1] = {xb}; double w1[1] = {1.0};
+          if ((s = solve(p, 1, step_order(k), 1, in, w1, W(k))) != SPADJ_OK) return s; }
+        { const double2* in[1] = {dxb}; double w1[1] = {1.0};
+          if ((s = solve(p, 1, step_order(k), 1, in, w1, dW(k))) != SPADJ_OK) return s; }
+      }
+    }
+    SPADJ_CUDA_TRY(p, cudaMemcpyAsync(hv, dxb, sb, cudaMemcpyDeviceToDevice, p->stream));
+    return SPADJ_OK;
+  }
+
   // ---- resolvent gains -----------------------------------------------------------------------
   // Leading gain per (kx, ky) pencil of the resolvent R(omega) = [(i omega M + L)^-1]_prog S1S0
   // in the energy norm ||c||^2 = c^H G c per field: power iteration on the generalised problem
@@ -887,7 +979,7 @@ struct Couette : EqImpl {
   ~Couette() override {
     for (DevBuf* b : {&wmx, &w2y, &czE, &cdzE, &gzF, &gzTE, &czTF, &cdzTF, &gmat, &phi1F, &phi1A, &phi2F, &phi2A, &one,
                       &Zm, &Ym, &Gf, &dGf, &Gb, &Fg, &Xr, &Fr, &dXr, &dFr, &Wr, &xbar, &src0, &partial, &edev, &sdev,
-                      &Jdev, &slots, &wts, &phiRF, &phiRA, &ginv, &nrm, &g2})
+                      &Jdev, &slots, &wts, &phiRF, &phiRA, &ginv, &nrm, &g2, &htraj, &hdtraj, &dWr, &dxbar, &htmp})
       b->release();
   }
 };
@@ -902,6 +994,12 @@ EqImpl* make_couette(Problem* p, spadj_status* st) {
     return nullptr;
   }
   return c;
+}
+
+spadj_status cou_hvp(EqImpl* impl, Problem* p, const double* x0, const double* v, int n_steps, double* hv) {
+  Couette* c = dynamic_cast<Couette*>(impl);
+  if (!c) return p->fail(SPADJ_ERR_UNSUPPORTED, "hvp: only defined for the plane-Couette problem");
+  return c->hvp(p, x0, v, n_steps, hv);
 }
 
 spadj_status cou_resolvent(EqImpl* impl, Problem* p, double omega, int n_iter, double* f, double* gains) {

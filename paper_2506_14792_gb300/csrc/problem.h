@@ -155,6 +155,7 @@ spadj_status rb_transform_noalloc(EqImpl* impl, Problem* p, int kind, const doub
 EqImpl* make_couette(Problem* p, spadj_status* st);
 spadj_status cou_pencil_solve(EqImpl* impl, Problem* p, int transpose, const double* v, double* x);
 spadj_status cou_resolvent(EqImpl* impl, Problem* p, double omega, int n_iter, double* f, double* gains);
+spadj_status cou_hvp(EqImpl* impl, Problem* p, const double* x0, const double* v, int n_steps, double* hv);
 
 }  // namespace spadj
 

@@ -65,6 +65,7 @@ _SIGS = {
     "spadj_solve": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp]),
     "spadj_vjp": (ctypes.c_int, [_vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp]),
     "spadj_resolvent": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_int, _vp, _vp]),
+    "spadj_hvp": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _vp]),
     "spadj_set_observations": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, ctypes.c_int]),
     "spadj_set_option": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
     "spadj_autotune": (ctypes.c_int, [_vp]),
@@ -262,6 +263,13 @@ class Problem:
                                       steps, _ptr(_as_f64(seeds, n * len(seed_steps), "seeds")),
                                       _ptr(_as_f64(grad_x0, n, "grad_x0"))))
         return grad_x0
+
+    def hvp(self, x0, v, n_steps, hv):
+        """hv = Hessian of J = E(X_N) with respect to X_0 applied to v (tangent over adjoint)."""
+        n = self.state_len(0)
+        _chk(self.h, lib().spadj_hvp(self.h, _ptr(_as_f64(x0, n, "x0")), _ptr(_as_f64(v, n, "v")), int(n_steps),
+                                      _ptr(_as_f64(hv, n, "hv"))))
+        return hv
 
     def resolvent(self, omega, n_iter, f, gains):
         """Leading energy-norm resolvent gain per (kx, ky) pencil at frequency omega (power

@@ -333,3 +333,17 @@ def test_resolvent_gains_all_pencils():
                 continue
             want = oco.resolvent_gain(o, o.alpha[m], o.beta[j], om)
             assert abs(gh[j, m] - want) <= 1e-10 * want, (j, m, gh[j, m], want)
+
+
+
+def test_hessian_vector_product(traj_case):
+    """Tangent-over-adjoint Hessian-vector product of J = E(X_N) against the oracle's."""
+    o, u0, X0, J, g, X, n = traj_case
+    v = synthetic.couette_ic(o.Nx, o.Ny, o.Nz, seed=91, norm=0.05)
+    dX = imex.multistep_tangent(o, X, o.pencils(v), DT)
+    want = imex.multistep_hvp(o, X, dX, lambda k: o.energy_grad(X[k]) if k == n else None,
+                              lambda k: o.energy_grad(dX[k]) if k == n else None, DT)
+    p = gpu_problem(o.Nx, o.Ny, o.Nz)
+    hv = _zc(to_gpu(u0).shape)
+    p.hvp(dev(to_gpu(u0)), dev(to_gpu(v)), n, hv)
+    assert rel_err(to_oracle(host(hv)), o.state(want)) < TOL

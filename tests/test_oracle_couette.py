@@ -315,3 +315,29 @@ def test_resolvent_gain_stokes_and_lift_up():
          for Re in (1000.0, 2000.0, 4000.0)]
     d1, d2 = abs(g[1] / g[0] - 1), abs(g[2] / g[1] - 1)
     assert d1 < 2e-4 and 3.0 < d1 / d2 < 5.0, (g, d1, d2)  # sigma_1 = c Re^2 (1 + O(Re^-2))
+
+
+def test_hessian_vector_product_fd_and_symmetry():
+    """Tangent-over-adjoint Hessian-vector product of J = E(X_N): equals the central difference
+    of the adjoint gradient (F is quadratic, so the FD error is O(eps^2)) and is symmetric."""
+    p = co.Couette(8, 6, 10, 300.0)
+    X0 = p.pencils(synthetic.couette_ic(8, 6, 10, seed=5, norm=0.3))
+    n, dt = 12, 2e-2
+    X = imex.multistep_forward(p, X0, n, dt)
+
+    def grad(x0):
+        Xs = imex.multistep_forward(p, x0, n, dt)
+        return imex.multistep_adjoint(p, Xs, lambda k: p.energy_grad(Xs[k]) if k == n else None, dt)
+
+    def hvp(v):
+        dX = imex.multistep_tangent(p, X, v, dt)
+        return imex.multistep_hvp(p, X, dX, lambda k: p.energy_grad(X[k]) if k == n else None,
+                                  lambda k: p.energy_grad(dX[k]) if k == n else None, dt)
+
+    v1 = p.pencils(synthetic.couette_ic(8, 6, 10, seed=77, norm=1.0))
+    v2 = p.pencils(synthetic.couette_ic(8, 6, 10, seed=78, norm=1.0))
+    h1, h2 = hvp(v1), hvp(v2)
+    eps = 1e-4
+    fd = (grad(X0 + eps * v1) - grad(X0 - eps * v1)) / (2 * eps)
+    assert np.max(np.abs(h1 - fd)) <= 1e-8 * np.max(np.abs(fd))
+    assert abs(inner(h1, v2) - inner(v1, h2)) <= 1e-12 * abs(inner(h1, v2))
