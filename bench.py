@@ -36,7 +36,17 @@ FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
 
 # DRAM traffic (bytes per launch) of the dominant kernel from an ncu capture, keyed by
 # (workload, kernel class); None until measured for the current kernels.
-TRAFFIC = {}
+TRAFFIC = {
+    # cou_solve_kernel: 81.66 MB read + 1.44 MB written per launch on the 64x32x32 capture (equal to
+    # the algorithmic operator + vector bytes); scaled to 128x64x64 by the operator bytes (16x) and
+    # the vector bytes (8x), averaged over the forward (5 vectors) and transposed (2) launches
+    ("couette3d_128x64x64_Re1000_sbdf2_4000steps_gain", "pencil_solve"): 1.252e9,
+    # xfft_kernel, one row per CTA (the setting the problem picks): dram read + write per launch on
+    # the RB capture (8-job 1.22 MB, 6-job 2.40 MB, 3-job 0.63 / 2.40 MB), weighted by the launch mix
+    # of the gradient (484 : 200 : 200 : 380); the working set is L2-resident, so this is the
+    # cold-cache fill ncu sees after its cache flush
+    ("rayleigh_benard2d_256x64_Ra1e6_rk222_2000steps", "x_fft"): 1.67e6,
+}
 
 
 def fp64_flops_real_fft(M):

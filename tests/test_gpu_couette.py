@@ -318,22 +318,35 @@ def test_full_trajectory_dot_and_fd(full_case):
 
 def test_resolvent_gains_all_pencils():
     """Energy-norm resolvent gains of every (kx, ky) pencil from the batched power iteration
-    (forward and transposed pencil solves) against the oracle's dense generalised eigenproblem."""
-    Nx, Ny, Nz, Re, om = 8, 4, 16, 300.0, 0.3
+    (forward and transposed pencil solves) against the oracle's dense generalised eigenproblem.
+    Where the power iteration has converged ((lambda_next / lambda_1)^n_iter < 1e-20 by the
+    oracle's spectrum) the gain must agree to 1e-10; elsewhere (the mean pencil at omega != 0,
+    whose two slowest Stokes modes nearly tie) it must be a lower bound within 1e-2, as a
+    Rayleigh quotient is."""
+    import scipy.linalg as sla
+    Nx, Ny, Nz, Re, n_iter = 8, 4, 16, 300.0, 120
     o = oco.Couette(Nx, Ny, Nz, Re, pencils=False)
+    G3 = sla.block_diag(o.G, o.G, o.G)
     p = gpu_problem(Nx, Ny, Nz, Re=Re)
-    f = dev(to_gpu(synthetic.random_coeffs((3, o.Kx, o.Ny, o.N), seed=61)))
-    gains = torch.zeros((Ny, Nx // 2), dtype=torch.float64, device="cuda")
-    p.resolvent(om, 120, f, gains)
-    gh = host(gains)
-    for j in range(Ny):
-        for m in range(o.Kx):
-            if j == Ny // 2:
-                assert gh[j, m] == 0.0  # the unstored ky Nyquist row
-                continue
-            want = oco.resolvent_gain(o, o.alpha[m], o.beta[j], om)
-            assert abs(gh[j, m] - want) <= 1e-10 * want, (j, m, gh[j, m], want)
-
+    for om in (0.0, 0.3):
+        f = dev(to_gpu(synthetic.random_coeffs((3, o.Kx, o.Ny, o.N), seed=61)))
+        gains = torch.zeros((Ny, Nx // 2), dtype=torch.float64, device="cuda")
+        p.resolvent(om, n_iter, f, gains)
+        gh = host(gains)
+        for j in range(Ny):
+            for m in range(o.Kx):
+                if j == Ny // 2:
+                    assert gh[j, m] == 0.0  # the unstored ky Nyquist row
+                    continue
+                R = oco.resolvent_matrix(o, o.alpha[m], o.beta[j], om)
+                ev = sla.eigh(R.conj().T @ G3 @ R, G3, eigvals_only=True)[::-1]
+                want = float(np.sqrt(ev[0]))
+                assert abs(want - oco.resolvent_gain(o, o.alpha[m], o.beta[j], om)) <= 1e-12 * want
+                nxt = next((e for e in ev[1:] if e < ev[0] * (1 - 1e-9)), 0.0)
+                if (nxt / ev[0]) ** n_iter < 1e-20:
+                    assert abs(gh[j, m] - want) <= 1e-10 * want, (om, j, m, gh[j, m], want)
+                else:
+                    assert want * (1 - 1e-2) <= gh[j, m] <= want * (1 + 1e-12), (om, j, m, gh[j, m], want)
 
 
 def test_hessian_vector_product(traj_case):
