@@ -24,6 +24,9 @@ Every routine follows the paper's own statement of the method
 * ``cnn``         -- FP64 reference of the 3x3 periodic CNN closure.
 * ``couette``     -- 3D plane Couette flow, Fourier(x, y) x Chebyshev-tau, with the
                      energy-gain (optimal perturbation) objective.
+* ``shear_evp``   -- linear stability eigenproblems of plane Couette and plane
+                     Poiseuille flow, adjoint eigenvectors and eigenvalue
+                     sensitivities (Problem types, "Eigenvalue problems").
 
 Pins (what fixes each function independently of itself) live in
 ``tests/test_oracle_*.py`` and are listed in the design notes.
