@@ -82,12 +82,24 @@ typedef enum {
  *   m = 0..Nx/2-1 with the Nyquist not stored; the ky = -Ny/2 row is held at 0 and the kx = 0
  *   plane Hermitian in ky).  Grid layout [3N/2][3Ny/2][3Nx/2] real (Gauss-Chebyshev z).
  *   Pressure and tau variables are internal to the step solves.
+ *
+ * SPADJ_SHEAR_EVP: linear stability eigenproblems (lambda M + L) X = 0 of plane shear flows
+ *   (Problem types, "Eigenvalue problems"; Parametric sensitivity example): perturbations
+ *   exp(i (alpha x + beta y) + lambda t) of the laminar profile U(z) e_x between no-slip walls
+ *   at z = -1, +1, lambda u - lap u / Re + U dx u + w U' e_x + grad p = 0, div u = 0, with the
+ *   z discretisation of SPADJ_COUETTE3D (N = n[2] Chebyshev modes, 8 <= N <= 128).
+ *   params[0] = base flow: 0 = plane Couette U = z, 1 = plane Poiseuille U = 1 - z^2 (the
+ *   paper's y (2 - y) on [0, 2] in z = y - 1; Re on the centre-line velocity and half gap).
+ *   batch = the largest number of pencils per spadj_eigen call; dt, scheme and the other
+ *   fields are unused.  Vectors: [n_pencils][3N] complex, the Chebyshev-T coefficients of
+ *   u, v, w of a pencil (pressure and tau variables are internal).
  */
 typedef enum {
   SPADJ_BURGERS1D = 0,
   SPADJ_RB2D = 1,
   SPADJ_KOLMOGOROV2D = 2,
-  SPADJ_COUETTE3D = 3
+  SPADJ_COUETTE3D = 3,
+  SPADJ_SHEAR_EVP = 4
 } spadj_eq;
 
 typedef enum {
@@ -285,6 +297,27 @@ spadj_status spadj_hvp(spadj_problem* prob, const double* x0, const double* v, i
  * pencil is zero).  The pencil factorisations of (i omega M + L) are built on the first call
  * for a frequency and kept until another frequency is asked for. */
 spadj_status spadj_resolvent(spadj_problem* prob, double omega, int n_iter, double* f, double* gains);
+
+/* Leading eigenvalue and its parameter sensitivities for a batch of pencils (SPADJ_SHEAR_EVP).
+ * Pencil i has pencil_params[3i..3i+2] = (alpha, beta, Re) and the complex shift sigma_i =
+ * shifts[2i] + i shifts[2i+1] (host arrays, read during the call).  The library factorises
+ * A_i = sigma_i M + L_i on the host (one LU per pencil, the adjoint solves reuse it) and on the
+ * GPU runs n_iter shift-invert power iterations on the prognostic block Phi_i of A_i^-1 M
+ * (eigenvalues 1/(sigma_i - lambda)) and, in the same pass over Phi_i, on Phi_i^H (the adjoint
+ * eigenproblem), so it converges to the eigenvalue nearest sigma_i.  Then, with the full right
+ * and left eigenvectors X and Y ((lambda M + L) X = 0, (conj(lambda) M^H + L^H) Y = 0), the
+ * sensitivities of eq. eigenvalue_sens, dlambda/dp = -<Y, dL/dp X> / <Y, M X>, for
+ * p = Re, alpha, beta.
+ * x, psi (device, [n_pencils][3N] complex): initial right and left iterates on entry (nonzero
+ * components along the wanted eigenvectors), the normalised right and left prognostic
+ * eigenvectors on exit.  out (device, [n_pencils][10] doubles): lambda (re, im),
+ * dlambda/dRe, dlambda/dalpha, dlambda/dbeta (re, im each), and the relative residuals
+ * |Phi x - mu x| / |Phi x| and |Phi^H psi - conj(mu) psi| / |Phi^H psi| of the last iterates
+ * (mu = psi^H Phi x / psi^H x), which tell whether the iteration converged.
+ * 1 <= n_pencils <= batch; SPADJ_ERR_INVALID for a singular shifted pencil (sigma on an
+ * eigenvalue) or Re <= 0.  Synchronises the problem's stream before returning. */
+spadj_status spadj_eigen(spadj_problem* prob, int n_pencils, const double* pencil_params, const double* shifts,
+                         int n_iter, double* x, double* psi, double* out);
 
 /* One-line description of the last failure on this problem (or of the last failed
  * spadj_create when prob is NULL).  Never NULL. */

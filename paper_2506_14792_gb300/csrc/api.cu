@@ -24,7 +24,7 @@ spadj_status spadj_create(const spadj_desc* desc, void* cuda_stream, spadj_probl
     return SPADJ_ERR_INVALID;
   }
   *out = nullptr;
-  if (desc->batch < 1 || !(desc->dt > 0.0)) {
+  if (desc->batch < 1 || (desc->eq != SPADJ_SHEAR_EVP && !(desc->dt > 0.0))) {
     g_create_error = "spadj_create: batch must be >= 1 and dt > 0";
     return SPADJ_ERR_INVALID;
   }
@@ -41,6 +41,7 @@ spadj_status spadj_create(const spadj_desc* desc, void* cuda_stream, spadj_probl
     case SPADJ_RB2D: p->impl = spadj::make_rb(p, &st); break;
     case SPADJ_KOLMOGOROV2D: p->impl = spadj::make_kolmogorov(p, &st); break;
     case SPADJ_COUETTE3D: p->impl = spadj::make_couette(p, &st); break;
+    case SPADJ_SHEAR_EVP: p->impl = spadj::make_shear_evp(p, &st); break;
     default: p->err = "spadj_create: unknown equation set"; break;
   }
   if (st != SPADJ_OK || !p->impl) {
@@ -113,6 +114,14 @@ spadj_status spadj_resolvent(spadj_problem* p, double omega, int n_iter, double*
   if (!p) return SPADJ_ERR_INVALID;
   if (bad_ptr(f) || bad_ptr(gains)) return p->fail(SPADJ_ERR_INVALID, "resolvent: NULL array");
   return spadj::cou_resolvent(p->impl, p, omega, n_iter, f, gains);
+}
+
+spadj_status spadj_eigen(spadj_problem* p, int n_pencils, const double* pencil_params, const double* shifts,
+                         int n_iter, double* x, double* psi, double* out) {
+  if (!p) return SPADJ_ERR_INVALID;
+  if (bad_ptr(pencil_params) || bad_ptr(shifts) || bad_ptr(x) || bad_ptr(psi) || bad_ptr(out))
+    return p->fail(SPADJ_ERR_INVALID, "eigen: NULL array");
+  return spadj::evp_eigen(p->impl, p, n_pencils, pencil_params, shifts, n_iter, x, psi, out);
 }
 
 spadj_status spadj_vjp(spadj_problem* p, const double* x0, int n_steps, int ckpt_slots, int n_seeds,

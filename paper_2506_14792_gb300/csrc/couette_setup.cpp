@@ -24,7 +24,6 @@
 
 namespace spadj {
 namespace couhost {
-namespace {
 
 using cd = std::complex<double>;
 
@@ -81,9 +80,93 @@ void lu_solve_multi(const std::vector<cd>& a, const std::vector<int>& piv, int n
   }
 }
 
+// Solve A^H X = B with the factors of A from lu_factor (P A = L U, so A^H = U^H L^H P):
+// forward substitution with U^H, back substitution with the unit L^H, then the row swaps
+// undone in reverse order.
+void lu_solve_h_multi(const std::vector<cd>& a, const std::vector<int>& piv, int n, std::vector<cd>& B, int nr) {
+  for (int i = 0; i < n; ++i) {
+    cd* bi = &B[(size_t)i * nr];
+    for (int j = 0; j < i; ++j) {
+      const cd u = std::conj(a[(size_t)j * n + i]);
+      if (u == 0.0) continue;
+      const cd* bj = &B[(size_t)j * nr];
+      for (int c = 0; c < nr; ++c) bi[c] -= u * bj[c];
+    }
+    const cd inv = 1.0 / std::conj(a[(size_t)i * n + i]);
+    for (int c = 0; c < nr; ++c) bi[c] *= inv;
+  }
+  for (int i = n - 2; i >= 0; --i) {
+    cd* bi = &B[(size_t)i * nr];
+    for (int j = i + 1; j < n; ++j) {
+      const cd l = std::conj(a[(size_t)j * n + i]);
+      if (l == 0.0) continue;
+      const cd* bj = &B[(size_t)j * nr];
+      for (int c = 0; c < nr; ++c) bi[c] -= l * bj[c];
+    }
+  }
+  for (int k = n - 1; k >= 0; --k)
+    if (piv[k] != k)
+      for (int c = 0; c < nr; ++c) std::swap(B[(size_t)k * nr + c], B[(size_t)piv[k] * nr + c]);
+}
+
+void base_flow(const rbhost::Operators& o, int base, std::vector<double>& Umat, std::vector<double>& UPmat) {
+  const int N = o.N;
+  // ZS = (S1 S0 on N + 1 modes) * (z T_n in the T basis of degree N), first N rows
+  std::vector<double> S0e = rbhost::op_S0(N + 1), S1e = rbhost::op_S1(N + 1);
+  std::vector<double> SSe = rbhost::matmul(S1e, S0e, N + 1);
+  std::vector<double> ZS((size_t)N * N, 0.0);
+  for (int r = 0; r < N; ++r)
+    for (int n = 0; n < N; ++n) {
+      // z T_0 = T_1; z T_n = (T_{n+1} + T_{n-1}) / 2
+      double v = 0.0;
+      if (n == 0) {
+        v = SSe[(size_t)r * (N + 1) + 1];
+      } else {
+        v = 0.5 * (SSe[(size_t)r * (N + 1) + n + 1] + SSe[(size_t)r * (N + 1) + n - 1]);
+      }
+      ZS[(size_t)r * N + n] = v;
+    }
+  if (base == 0) {  // U = z, U' = 1
+    Umat = ZS;
+    UPmat = o.SS;
+    return;
+  }
+  // U = 1 - z^2: (1 - z^2) T_n in the T basis of degree N + 1 (z applied twice), converted
+  // with S1 S0 on N + 2 modes and truncated; U' = -2 z
+  const int E = N + 2;
+  std::vector<double> S2 = rbhost::matmul(rbhost::op_S1(E), rbhost::op_S0(E), E);
+  Umat.assign((size_t)N * N, 0.0);
+  UPmat.assign((size_t)N * N, 0.0);
+  std::vector<double> t(E), z1(E), z2(E);
+  auto zmul = [&](const std::vector<double>& in, std::vector<double>& out) {
+    std::fill(out.begin(), out.end(), 0.0);
+    for (int k = 0; k + 1 < E; ++k) {
+      if (in[k] == 0.0) continue;
+      if (k == 0) {
+        out[1] += in[0];
+      } else {
+        out[k + 1] += 0.5 * in[k];
+        out[k - 1] += 0.5 * in[k];
+      }
+    }
+  };
+  for (int n = 0; n < N; ++n) {
+    std::fill(t.begin(), t.end(), 0.0);
+    t[n] = 1.0;
+    zmul(t, z1);
+    zmul(z1, z2);
+    for (int r = 0; r < N; ++r) {
+      double u = 0.0;
+      for (int k = 0; k < E; ++k) u += S2[(size_t)r * E + k] * (t[k] - z2[k]);
+      Umat[(size_t)r * N + n] = u;
+      UPmat[(size_t)r * N + n] = -2.0 * ZS[(size_t)r * N + n];
+    }
+  }
+}
+
 // a0 M + L for the pencil (alpha, beta); ordering as documented in couette_setup.h.
-void assemble_pencil(const rbhost::Operators& o, const std::vector<double>& ZS, double al, double be, bool mean,
-                     double nu, cd a0, std::vector<cd>& A) {
+void assemble_pencil(const rbhost::Operators& o, const std::vector<double>& ZS, const std::vector<double>& UP,
+                     double al, double be, bool mean, double nu, cd a0, std::vector<cd>& A) {
   const int N = o.N, nv = 4 * N + 7;
   A.assign((size_t)nv * nv, cd(0.0, 0.0));
   auto at = [&](int r, int c) -> cd& { return A[(size_t)r * nv + c]; };
@@ -98,7 +181,7 @@ void assemble_pencil(const rbhost::Operators& o, const std::vector<double>& ZS, 
       at(U + r, U + c) = diag;
       at(V + r, V + c) = diag;
       at(W + r, W + c) = diag;
-      at(U + r, W + c) = ss;            // w U' e_x, U' = 1
+      at(U + r, W + c) = UP[r * N + c];  // w U' e_x
       at(U + r, P + c) = ia * ss;       // dx p
       at(V + r, P + c) = ib * ss;       // dy p
       at(W + r, P + c) = o.SD[r * N + c];  // dz p
@@ -132,26 +215,11 @@ void assemble_pencil(const rbhost::Operators& o, const std::vector<double>& ZS, 
   }
 }
 
-}  // namespace
-
 bool build_phi(const rbhost::Operators& o, int Kx, int Ny, double Lx, double Ly, double nu, cd a0,
                std::vector<double>& phiF, std::vector<double>& phiA, std::string* err) {
   const int N = o.N, nv = 4 * N + 7, H = 3 * N, Nyh = Ny / 2;
-  // ZS = (S1 S0 on N + 1 modes) * (z T_n in the T basis of degree N), first N rows
-  std::vector<double> S0e = rbhost::op_S0(N + 1), S1e = rbhost::op_S1(N + 1);
-  std::vector<double> SSe = rbhost::matmul(S1e, S0e, N + 1);
-  std::vector<double> ZS((size_t)N * N, 0.0);
-  for (int r = 0; r < N; ++r)
-    for (int n = 0; n < N; ++n) {
-      // z T_0 = T_1; z T_n = (T_{n+1} + T_{n-1}) / 2
-      double v = 0.0;
-      if (n == 0) {
-        v = SSe[(size_t)r * (N + 1) + 1];
-      } else {
-        v = 0.5 * (SSe[(size_t)r * (N + 1) + n + 1] + SSe[(size_t)r * (N + 1) + n - 1]);
-      }
-      ZS[(size_t)r * N + n] = v;
-    }
+  std::vector<double> ZS, UP;
+  base_flow(o, 0, ZS, UP);
   const size_t per = (size_t)H * H * 2;
   const int npen = Kx * Nyh;
   phiF.assign((size_t)npen * per, 0.0);
@@ -163,7 +231,7 @@ bool build_phi(const rbhost::Operators& o, int Kx, int Ny, double Lx, double Ly,
     for (int pp = p0; pp < p1; ++pp) {
       const int jh = pp / Kx, m = pp % Kx;
       const double al = 2.0 * M_PI / Lx * m, be = 2.0 * M_PI / Ly * jh;
-      assemble_pencil(o, ZS, al, be, m == 0 && jh == 0, nu, a0, A);
+      assemble_pencil(o, ZS, UP, al, be, m == 0 && jh == 0, nu, a0, A);
       if (!lu_factor(A, piv, nv)) {
         bad[pp] = 1;
         continue;
@@ -200,6 +268,59 @@ bool build_phi(const rbhost::Operators& o, int Kx, int Ny, double Lx, double Ly,
     if (bad[pp]) {
       if (err) *err = "couette: singular pencil matrix at (kx, ky) index (" + std::to_string(pp % Kx) + ", " +
                       std::to_string(pp / Kx) + ")";
+      return false;
+    }
+  return true;
+}
+
+bool build_evp(const rbhost::Operators& o, int base, int P, const double* prm, const double* shift,
+               std::vector<double>& T, std::vector<double>& RH, std::string* err) {
+  const int N = o.N, nv = 4 * N + 7, H = 3 * N;
+  std::vector<double> Um, UP;
+  base_flow(o, base, Um, UP);
+  const size_t per = (size_t)nv * H * 2;
+  T.assign((size_t)P * per, 0.0);
+  RH.assign((size_t)P * per, 0.0);
+  std::vector<int> bad(P, 0);
+  auto work = [&](int p0, int p1) {
+    std::vector<cd> A, B;
+    std::vector<int> piv;
+    for (int pp = p0; pp < p1; ++pp) {
+      const double al = prm[3 * pp], be = prm[3 * pp + 1], Re = prm[3 * pp + 2];
+      const cd sigma(shift[2 * pp], shift[2 * pp + 1]);
+      assemble_pencil(o, Um, UP, al, be, al == 0.0 && be == 0.0, 1.0 / Re, sigma, A);
+      if (!lu_factor(A, piv, nv)) {
+        bad[pp] = 1;
+        continue;
+      }
+      B.assign((size_t)nv * H, cd(0.0, 0.0));
+      for (int f = 0; f < 3; ++f)
+        for (int c = 0; c < N; ++c)
+          for (int r = 0; r < N; ++r) B[(size_t)(f * N + r) * H + f * N + c] = o.SS[r * N + c];
+      lu_solve_multi(A, piv, nv, B, H);
+      double* t = &T[(size_t)pp * per];
+      for (size_t i = 0; i < (size_t)nv * H; ++i) { t[2 * i] = B[i].real(); t[2 * i + 1] = B[i].imag(); }
+      B.assign((size_t)nv * H, cd(0.0, 0.0));
+      for (int r = 0; r < H; ++r) B[(size_t)r * H + r] = 1.0;
+      lu_solve_h_multi(A, piv, nv, B, H);
+      double* rh = &RH[(size_t)pp * per];
+      for (size_t i = 0; i < (size_t)nv * H; ++i) { rh[2 * i] = B[i].real(); rh[2 * i + 1] = B[i].imag(); }
+    }
+  };
+  unsigned nt = std::thread::hardware_concurrency();
+  if (nt == 0) nt = 1;
+  if (nt > 64) nt = 64;
+  if ((int)nt > P) nt = P;
+  std::vector<std::thread> th;
+  const int chunk = (P + nt - 1) / nt;
+  for (unsigned t = 0; t < nt; ++t) {
+    const int p0 = t * chunk, p1 = std::min(P, p0 + chunk);
+    if (p0 < p1) th.emplace_back(work, p0, p1);
+  }
+  for (auto& t : th) t.join();
+  for (int pp = 0; pp < P; ++pp)
+    if (bad[pp]) {
+      if (err) *err = "eigen: singular shifted pencil matrix at pencil " + std::to_string(pp);
       return false;
     }
   return true;

@@ -13,6 +13,26 @@
 namespace spadj {
 namespace couhost {
 
+using cd = std::complex<double>;
+
+// Complex LU with partial pivoting of the row-major n x n matrix a, in place (P A = L U with
+// unit L); piv[k] is the row swapped with row k at step k.  False if a pivot is exactly 0.
+bool lu_factor(std::vector<cd>& a, std::vector<int>& piv, int n);
+// Solve A X = B (nr right-hand sides, B row-major n x nr, overwritten) with those factors.
+void lu_solve_multi(const std::vector<cd>& a, const std::vector<int>& piv, int n, std::vector<cd>& B, int nr);
+// Solve A^H X = B with the same factors (the adjoint solve reuses the forward factorisation).
+void lu_solve_h_multi(const std::vector<cd>& a, const std::vector<int>& piv, int n, std::vector<cd>& B, int nr);
+
+// Base-flow matrices on N modes (row-major N x N, C^(2) rows acting on T coefficients):
+// Umat = [U T_n], UPmat = [U' T_n], the products formed exactly in the T basis, converted with
+// S1 S0 and truncated; base 0: plane Couette U = z; base 1: plane Poiseuille U = 1 - z^2.
+void base_flow(const rbhost::Operators& o, int base, std::vector<double>& Umat, std::vector<double>& UPmat);
+
+// a0 M + L of the pencil (alpha, beta) at viscosity nu for the base flow (Umat, UPmat), row-major
+// (4N + 7) x (4N + 7); mean selects the gauge rows of the (0, 0) pencil.
+void assemble_pencil(const rbhost::Operators& o, const std::vector<double>& Umat, const std::vector<double>& UPmat,
+                     double al, double be, bool mean, double nu, cd a0, std::vector<cd>& A);
+
 // Complex Phi = [(a0 M + L)^-1]_{prognostic} * blockdiag(S1S0) (3N x 3N) for every pencil
 // (a0 real for the timestep operators, a0 = i omega for the resolvent at frequency omega)
 // (kx index m = 0..Kx-1, ky index jh = 0..Ny/2-1, ky = jh >= 0), stored twice as interleaved
@@ -21,6 +41,16 @@ namespace couhost {
 // (u, v, w).  Returns false (and sets err) if a pencil matrix is singular.
 bool build_phi(const rbhost::Operators& o, int Kx, int Ny, double Lx, double Ly, double nu, std::complex<double> a0,
                std::vector<double>& phiF, std::vector<double>& phiA, std::string* err);
+
+// Shift-invert operators of P eigenvalue pencils (prm[p] = alpha, beta, Re; shift[p] = sigma as
+// (re, im)) of the base flow `base`: with A_p = sigma_p M + L_p (one LU per pencil),
+//   T[p]  = A_p^-1 [S1S0 on the u, v, w momentum rows]   ((4N + 7) x 3N),
+//   RH[p] = A_p^-H [e_0 .. e_{3N-1}]                      ((4N + 7) x 3N),
+// both row-major with interleaved (re, im); RH by the adjoint solve with the same factors.
+// The first 3N rows of T are the prognostic shift-invert operator Phi(sigma), and row i of RH
+// holds conj((A^-1)[r][i]) for r < 3N.  Returns false (and sets err) if a pencil is singular.
+bool build_evp(const rbhost::Operators& o, int base, int P, const double* prm, const double* shift,
+               std::vector<double>& T, std::vector<double>& RH, std::string* err);
 
 }  // namespace couhost
 }  // namespace spadj

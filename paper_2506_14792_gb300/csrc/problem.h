@@ -147,6 +147,9 @@ EqImpl* make_burgers(Problem* p, spadj_status* st);
 EqImpl* make_rb(Problem* p, spadj_status* st);
 spadj_status rb_pencil_solve(EqImpl* impl, Problem* p, int transpose, const double* v, double* x);
 EqImpl* make_kolmogorov(Problem* p, spadj_status* st);
+EqImpl* make_shear_evp(Problem* p, spadj_status* st);
+spadj_status evp_eigen(EqImpl* impl, Problem* p, int n_pencils, const double* prm, const double* shift, int n_iter,
+                       double* x, double* psi, double* out);
 spadj_status kol_set_observations(EqImpl* impl, Problem* p, int n, const int* steps, const double* obs, int kmax);
 spadj_status kol_set_option(EqImpl* impl, Problem* p, int option, int value);
 spadj_status kol_autotune(EqImpl* impl, Problem* p);

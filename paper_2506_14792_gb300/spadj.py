@@ -25,6 +25,7 @@ SPADJ_BURGERS1D = 0
 SPADJ_RB2D = 1
 SPADJ_KOLMOGOROV2D = 2
 SPADJ_COUETTE3D = 3
+SPADJ_SHEAR_EVP = 4
 
 SPADJ_SBDF1 = 1
 SPADJ_SBDF2 = 2
@@ -66,6 +67,7 @@ _SIGS = {
     "spadj_vjp": (ctypes.c_int, [_vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp]),
     "spadj_resolvent": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_int, _vp, _vp]),
     "spadj_hvp": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _vp]),
+    "spadj_eigen": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, ctypes.c_int, _vp, _vp, _vp]),
     "spadj_set_observations": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, ctypes.c_int]),
     "spadj_set_option": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
     "spadj_autotune": (ctypes.c_int, [_vp]),
@@ -270,6 +272,23 @@ class Problem:
         _chk(self.h, lib().spadj_hvp(self.h, _ptr(_as_f64(x0, n, "x0")), _ptr(_as_f64(v, n, "v")), int(n_steps),
                                       _ptr(_as_f64(hv, n, "hv"))))
         return hv
+
+    def eigen(self, pencil_params, shifts, n_iter, x, psi, out):
+        """Leading eigenvalue nearest each shift and its sensitivities (SPADJ_SHEAR_EVP).
+        pencil_params: host sequence of (alpha, beta, Re); shifts: host sequence of complex
+        shifts; x, psi: [P][3N] complex128 CUDA iterates (in) / eigenvectors (out); out:
+        [P][10] float64 CUDA (lambda, dlambda/dRe, dlambda/dalpha, dlambda/dbeta, residuals)."""
+        import numpy as np
+        prm = np.ascontiguousarray(np.asarray(pencil_params, dtype=np.float64).reshape(-1, 3))
+        P = prm.shape[0]
+        sh = np.asarray(shifts, dtype=np.complex128).reshape(P)
+        shv = np.ascontiguousarray(np.stack([sh.real, sh.imag], axis=1))
+        H = 3 * self.desc.n[2]
+        _chk(self.h, lib().spadj_eigen(self.h, P, prm.ctypes.data_as(ctypes.c_void_p),
+                                        shv.ctypes.data_as(ctypes.c_void_p), int(n_iter),
+                                        _ptr(_as_f64(x, 2 * P * H, "x")), _ptr(_as_f64(psi, 2 * P * H, "psi")),
+                                        _ptr(_as_f64(out, 10 * P, "out"))))
+        return out
 
     def resolvent(self, omega, n_iter, f, gains):
         """Leading energy-norm resolvent gain per (kx, ky) pencil at frequency omega (power
