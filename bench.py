@@ -7,7 +7,7 @@ reference arm (``--impl reference``) times the FP64 CPU oracle on a bounded samp
 the same workload.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
-                       [--workload rb|burgers|kolmogorov|couette]
+                       [--workload rb|burgers|kolmogorov|couette|poiseuille_evp]
 Under torchrun (N > 1) each rank runs an independent replica / shard; the time is the
 max over ranks and the value counts the units of all ranks.
 """
@@ -365,7 +365,76 @@ class Couette:
                 "FP64, factorisations cached)" % (size + (nsteps,)), el)
 
 
-WORKLOADS = {"burgers": Burgers, "rb": RayleighBenard, "kolmogorov": KolmogorovBatch, "couette": Couette}
+class PoiseuilleEvp:
+    """Batched linear-stability eigenvalues of plane Poiseuille flow with their adjoint
+    sensitivities (Parametric sensitivity example): 608 pencils (alpha 0.6..1.3 x beta 0..1.4,
+    Re = 8000, N = 64 Chebyshev modes), shifts on the wall-mode branch lambda ~ -0.25 i alpha,
+    100 shift-invert iterations per pencil (forward and adjoint together), then eigenvectors
+    and dlambda/d(Re, alpha, beta).  One step = one spadj_eigen call."""
+    name = "poiseuille_evp_N64_608pencils_Re8000_100iter"
+    metric = "eigenvalue+sensitivity solves/s (leading mode, dlambda/d(Re, alpha, beta))"
+    unit = "solves/s"
+
+    def __init__(self, N=64, Re=8000.0, n_alpha=38, n_beta=16, n_iter=100, seed=12):
+        self.N, self.Re, self.n_iter, self.seed = N, Re, n_iter, seed
+        al = np.linspace(0.6, 1.3, n_alpha)
+        be = np.linspace(0.0, 1.4, n_beta)
+        self.cases = np.array([(a, b, Re) for b in be for a in al])
+        self.P = len(self.cases)
+        self.shifts = -0.25j * self.cases[:, 0]
+        self.flush_l2 = False
+
+    def config(self):
+        return {"workload": self.name, "N": self.N, "Re": self.Re, "pencils": self.P, "iterations": self.n_iter,
+                "base_flow": "plane Poiseuille U = 1 - z^2", "alpha": [0.6, 1.3], "beta": [0.0, 1.4],
+                "l2": "pencil operators 359 MB > L2, re-read every iteration"}
+
+    def units_per_step(self):
+        return self.P
+
+    def setup(self, device):
+        import torch
+        from paper_2506_14792_gb300 import stability
+        self.p = stability.shear_evp_problem(self.N, "poiseuille", self.P)
+        rng = np.random.default_rng(self.seed)
+        H = 3 * self.N
+        self.x_init = torch.tensor(rng.standard_normal((self.P, H)) + 1j * rng.standard_normal((self.P, H)))
+        self.psi_init = torch.tensor(rng.standard_normal((self.P, H)) + 1j * rng.standard_normal((self.P, H)))
+        self.x = self.x_init.to(device)
+        self.psi = self.psi_init.to(device)
+        self.out = torch.zeros((self.P, 10), dtype=torch.float64, device=device)
+        self.out_host = torch.zeros((self.P, 10), dtype=torch.float64).pin_memory()
+
+    def step(self):
+        self.x.copy_(self.x_init, non_blocking=True)
+        self.psi.copy_(self.psi_init, non_blocking=True)
+        self.p.eigen(self.cases, self.shifts, self.n_iter, self.x, self.psi, self.out)
+        self.out_host.copy_(self.out)
+
+    def e2e_bytes(self):
+        nv, H = 4 * self.N + 7, 3 * self.N
+        h2d = self.P * (2 * nv * H * 16 + 2 * H * 16 + 5 * 8)  # operators T, RH; iterates; params, shifts
+        return h2d, self.P * 10 * 8
+
+    def cpu_sample(self, n=6):
+        """Oracle: dense QZ eigenpairs with left vectors and eq. eigenvalue_sens for n pencils of
+        the batch (numpy/scipy FP64)."""
+        from oracle.shear_evp import ShearEVP
+        e = ShearEVP(self.N, "poiseuille")
+        idx = np.linspace(0, self.P - 1, n).astype(int)
+        t = time.perf_counter()
+        for i in idx:
+            a, b, Re = self.cases[i]
+            lam_all, X, Y = e.eigs(a, b, Re)
+            j = int(np.argmin(np.abs(lam_all - self.shifts[i])))
+            e.sensitivity(a, b, Re, lam_all[j], X[:, j], Y[:, j])
+        el = time.perf_counter() - t
+        return n / el, "%d of the %d pencils: dense QZ (left+right vectors) + sensitivities, N = %d" % (
+            n, self.P, self.N), el
+
+
+WORKLOADS = {"burgers": Burgers, "rb": RayleighBenard, "kolmogorov": KolmogorovBatch, "couette": Couette,
+             "poiseuille_evp": PoiseuilleEvp}
 DEFAULT_WORKLOAD = "rb"
 
 
@@ -453,12 +522,14 @@ def run_reference(args, wl):
         vals.append(v)
         secs.append(el)
     value = float(np.median(vals))
-    line = {"impl": "reference", "metric": "forward+adjoint gradient dof*steps/s (FP64 oracle, CPU)", "value": value,
-            "unit": "dof*steps/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+    metric = getattr(wl, "metric", "forward+adjoint gradient dof*steps/s at 1e-10 rel vs FP64 oracle")
+    unit = getattr(wl, "unit", "dof*steps/s")
+    line = {"impl": "reference", "metric": metric, "value": value,
+            "unit": unit, "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * float(np.median(secs)), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": wl.config(),
-            "cpu_baseline": {"value": value, "unit": "dof*steps/s", "cores": cores, "kind": "oracle", "sample": sample},
-            "e2e": {"value": value, "unit": "dof*steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "cpu_baseline": {"value": value, "unit": unit, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
 
@@ -578,6 +649,83 @@ def run_gpu(args, wl):
     return 0
 
 
+def run_gpu_evp(args, wl):
+    """Bench line of the eigenvalue workload: value from the library's CUDA events around its
+    kernels (operators resident on the device), e2e from the whole spadj_eigen call (host
+    factorisation, operator upload, iterations, result read-back)."""
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    wl.setup(dev)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+            torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        wl.step()
+    barrier()
+    clk = ClockSampler(local)
+    clk.start()
+    time.sleep(0.3)
+    wl.p.timing(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    e0.record(stream)
+    for _ in range(args.steps):
+        wl.step()
+    e1.record(stream)
+    barrier()
+    clocks = clk.stop()
+    rep = wl.p.timing_report()
+    wl.p.timing(False)
+    dev_ms = reduce_max(float(sum(v[0] for v in rep.values())), dev)
+    e2e_ms = reduce_max(e0.elapsed_time(e1), dev)
+    units = wl.units_per_step() * args.steps * ws
+    value = job_value(wl.units_per_step(), args.steps, ws, dev_ms)
+    o = wl.out.cpu().numpy()
+    converged = float(np.mean(np.max(o[:, 8:10], axis=1) <= 1e-11))
+    dom = "pencil_solve"
+    dms, dfl, dn = rep[dom]
+    achieved = dfl / (dms / 1e3) / 1e9
+    per_kernel = {k: {"ms_total": v[0], "launches": v[2], "share": v[0] / sum(x[0] for x in rep.values()),
+                      "gflops": v[1] / (v[0] / 1e3) / 1e9 if v[0] > 0 else None} for k, v in rep.items()}
+    roof = {"kernel": "evp_iter_kernel (pencil_solve)", "bound": "alu", "achieved": achieved,
+            "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s", "frac": achieved / FP64_PEAK_GFLOPS,
+            "traffic": TRAFFIC.get((wl.name, dom)), "avg_launch_us": 1e3 * dms / dn, "flops_per_launch": dfl / dn,
+            "per_kernel": per_kernel,
+            "peak_note": "FP64 FMA peak 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz; 16 flops per operator entry "
+                         "and iteration (forward and adjoint complex matvecs)"}
+    launches = int(sum(v[2] for v in rep.values()))
+    if rank != 0:
+        return 0
+    cpu = None
+    if ws == 1 and not args.no_cpu:
+        v, sample, el = wl.cpu_sample()
+        cpu = {"value": v, "unit": wl.unit, "cores": int(os.environ.get("OPENBLAS_NUM_THREADS", "1")),
+               "kind": "oracle", "sample": sample}
+    bi, bo = wl.e2e_bytes()
+    line = {"metric": wl.metric, "value": value, "unit": wl.unit, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dev_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": dict(wl.config(), parallelism="replicas%d" % ws, converged_fraction=converged),
+            "gpu_launches": launches,
+            "e2e": {"value": units / (e2e_ms / 1e3), "unit": wl.unit, "h2d_bytes_per_step": bi,
+                    "d2h_bytes_per_step": bo, "note": "includes the host LU of every shifted pencil"},
+            "roofline": roof, "cpu_baseline": cpu, "clocks": clocks}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -589,14 +737,23 @@ def main():
     ap.add_argument("--pdl", action="store_true", help="programmatic dependent launch of consecutive kernels")
     ap.add_argument("--no-fuse", action="store_true", help="RB: separate fold / solve / expand kernels")
     ap.add_argument("--x-rows", type=int, default=0, help="x-FFT rows per CTA (1, 2, 4; 0 = tuned)")
-    ap.add_argument("--nsteps", type=int, default=None, help="override the workload's time steps (profiling runs)")
+    ap.add_argument("--nsteps", type=int, default=None,
+                    help="override the workload's time steps, or the iterations of poiseuille_evp (profiling runs)")
     ap.add_argument("--size", default=None,
-                    help="override the grid of the rb (Nx,Nz) or couette (Nx,Ny,Nz) workload (profiling runs)")
+                    help="override the grid of the rb (Nx,Nz) or couette (Nx,Ny,Nz) workload, or the pencil "
+                         "grid (n_alpha,n_beta) of poiseuille_evp (profiling runs)")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]()
     if args.nsteps is not None:
         wl.nsteps = args.nsteps
-    if args.size:
+    if args.workload == "poiseuille_evp" and (args.nsteps is not None or args.size):
+        dims = [int(v) for v in args.size.split(",")] if args.size else [38, 16]
+        if len(dims) != 2:
+            ap.error("--size takes n_alpha,n_beta for poiseuille_evp")
+        it = args.nsteps if args.nsteps is not None else wl.n_iter
+        wl = PoiseuilleEvp(n_alpha=dims[0], n_beta=dims[1], n_iter=it)
+        wl.name = "poiseuille_evp_N64_%dpencils_Re8000_%diter" % (wl.P, it)
+    elif args.size:
         dims = [int(v) for v in args.size.split(",")]
         if args.workload == "couette" and len(dims) == 3:
             wl = Couette(*dims, nsteps=wl.nsteps)
@@ -608,6 +765,8 @@ def main():
             ap.error("--size takes Nx,Nz for rb and Nx,Ny,Nz for couette")
     if args.impl == "reference":
         return run_reference(args, wl)
+    if isinstance(wl, PoiseuilleEvp):
+        return run_gpu_evp(args, wl)
     return run_gpu(args, wl)
 
 

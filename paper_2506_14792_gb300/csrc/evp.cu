@@ -70,10 +70,12 @@ struct EvpIterArgs {
 // One CTA per pencil: n_iter steps of x <- Phi x / |Phi x|, psi <- Phi^H psi / |Phi^H psi| with
 // each row of Phi read once per step for both products (warps over rows, lanes over columns,
 // coalesced), all in shared memory between steps.
+// NC = ceil(3N / 32) column chunks per lane, fixed at compile time so that only the last chunk
+// carries a bounds predicate.
+template <int NC>
 __global__ void __launch_bounds__(kEvpThreads) evp_iter_kernel(const EvpIterArgs A) {
   const int p = blockIdx.x, H = A.H;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int nc = (H + 31) / 32;
   extern __shared__ double2 evsm[];
   double2* x = evsm;
   double2* ps = x + H;
@@ -88,17 +90,17 @@ __global__ void __launch_bounds__(kEvpThreads) evp_iter_kernel(const EvpIterArgs
   double mur = 0.0, mui = 0.0, res_r = 1.0, res_l = 1.0;
   for (int it = 0; it < A.n_iter; ++it) {
     __syncthreads();
-    double2 zacc[kEvpMaxChunks];
+    double2 zacc[NC];
 #pragma unroll
-    for (int c = 0; c < kEvpMaxChunks; ++c) zacc[c] = make_double2(0.0, 0.0);
+    for (int c = 0; c < NC; ++c) zacc[c] = make_double2(0.0, 0.0);
     for (int r = warp; r < H; r += kEvpWarps) {
       const double2* row = Tp + (size_t)r * H;
       const double2 pr = ps[r];
       double ax = 0.0, ay = 0.0;
 #pragma unroll
-      for (int c = 0; c < kEvpMaxChunks; ++c) {
+      for (int c = 0; c < NC; ++c) {
         const int k = c * 32 + lane;
-        if (c < nc && k < H) {
+        if (c < NC - 1 || k < H) {
           const double2 t = __ldg(&row[k]);
           const double2 xv = x[k];
           ax = fma(t.x, xv.x, ax);
@@ -116,9 +118,9 @@ __global__ void __launch_bounds__(kEvpThreads) evp_iter_kernel(const EvpIterArgs
       if (lane == 0) y[r] = make_double2(ax, ay);
     }
 #pragma unroll
-    for (int c = 0; c < kEvpMaxChunks; ++c) {
+    for (int c = 0; c < NC; ++c) {
       const int k = c * 32 + lane;
-      if (c < nc && k < H) zp[(size_t)warp * H + k] = zacc[c];
+      if (c < NC - 1 || k < H) zp[(size_t)warp * H + k] = zacc[c];
     }
     __syncthreads();
     // z = sum of the warp partials (into zp row 0); norms and the two-sided Rayleigh quotient
@@ -180,6 +182,12 @@ __global__ void __launch_bounds__(kEvpThreads) evp_iter_kernel(const EvpIterArgs
     o[9] = res_l;
   }
 }
+
+using EvpIterFn = void (*)(const EvpIterArgs);
+const EvpIterFn kEvpIter[kEvpMaxChunks] = {
+    evp_iter_kernel<1>, evp_iter_kernel<2>, evp_iter_kernel<3>, evp_iter_kernel<4>,
+    evp_iter_kernel<5>, evp_iter_kernel<6>, evp_iter_kernel<7>, evp_iter_kernel<8>,
+    evp_iter_kernel<9>, evp_iter_kernel<10>, evp_iter_kernel<11>, evp_iter_kernel<12>};
 
 // X = T x and Y = RH psi (length nv each) for every pencil: warps over rows, lanes over columns.
 __global__ void __launch_bounds__(kEvpThreads) evp_vectors_kernel(const double2* __restrict__ T,
@@ -323,7 +331,8 @@ struct ShearEvp : EqImpl {
     SPADJ_CUDA_TRY(p, cudaMemcpy(mats.ptr, m.data(), sizeof(double) * m.size(), cudaMemcpyHostToDevice));
     const size_t ismem = sizeof(double2) * (size_t)(3 + kEvpWarps) * H + sizeof(double) * kEvpWarps * 6;
     if (ismem > 48 * 1024)
-      SPADJ_CUDA_TRY(p, cudaFuncSetAttribute(evp_iter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ismem));
+      SPADJ_CUDA_TRY(p, cudaFuncSetAttribute(kEvpIter[(H + 31) / 32 - 1],
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ismem));
     return SPADJ_OK;
   }
 
@@ -357,7 +366,7 @@ struct ShearEvp : EqImpl {
     ia.n_iter = n_iter;
     const size_t ismem = sizeof(double2) * (size_t)(3 + kEvpWarps) * H + sizeof(double) * kEvpWarps * 6;
     cudaEvent_t t0 = p->tic();
-    evp_iter_kernel<<<P, kEvpThreads, ismem, p->stream>>>(ia);
+    kEvpIter[(H + 31) / 32 - 1]<<<P, kEvpThreads, ismem, p->stream>>>(ia);
     // two complex matvecs per step over the 3N x 3N block: 16 flops per entry
     p->toc(t0, KC_SOLVE, 16.0 * (double)H * H * P * n_iter);
     spadj_status s = check_launch(p, "evp iterate");
