@@ -46,7 +46,45 @@ def sbdf_coeffs(n, order, dt):
     if s == 2:  # SBDF2 with constant dt
         return (np.array([1.5 / dt, -2.0 / dt, 0.5 / dt]), np.array([1.0, 0.0, 0.0]),
                 np.array([0.0, 2.0, -1.0]))
-    raise ValueError("only SBDF1 / SBDF2 are defined here")
+    if s in (3, 4):
+        a, c = sbdf_weights(s)
+        b = np.zeros(s + 1)
+        b[0] = 1.0
+        return (np.array([float(v) for v in a]) / dt, b, np.array([float(v) for v in c]))
+    raise ValueError("SBDF orders 1..4 are defined here")
+
+
+def sbdf_weights(s):
+    """Exact rational weights of SBDF<s> with constant step, from the scheme's definition: the
+    implicit part is the backward differentiation formula, a_i = d/dt of the Lagrange basis
+    polynomial of node t_{n-i} through the nodes t_n, ..., t_{n-s}, evaluated at t_n (times dt);
+    the explicit part extrapolates F to t_n, c_i = the Lagrange basis polynomial of t_{n-i}
+    through t_{n-1}, ..., t_{n-s}, evaluated at t_n (c_0 = 0).  Nodes in units of dt."""
+    from fractions import Fraction as Fr
+    nodes = [Fr(-i) for i in range(s + 1)]  # t_{n-i} - t_n
+    a = []
+    for i in range(s + 1):
+        others = [nodes[j] for j in range(s + 1) if j != i]
+        den = Fr(1)
+        for o in others:
+            den *= nodes[i] - o
+        # derivative at 0 of prod (t - o): sum over o of prod over the rest of (0 - o')
+        num = Fr(0)
+        for k in range(len(others)):
+            term = Fr(1)
+            for m, o in enumerate(others):
+                if m != k:
+                    term *= -o
+            num += term
+        a.append(num / den)
+    c = [Fr(0)]
+    for i in range(1, s + 1):
+        v = Fr(1)
+        for j in range(1, s + 1):
+            if j != i:
+                v *= (0 - nodes[j]) / (nodes[i] - nodes[j])
+        c.append(v)
+    return a, c
 
 
 RK222_GAMMA = 1.0 - 1.0 / math.sqrt(2.0)
