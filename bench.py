@@ -549,6 +549,8 @@ def run_gpu(args, wl):
         wl.p.set_option(7, 0)
     if args.x_rows:
         wl.p.set_option(8, args.x_rows)
+    if args.host_slots:
+        wl.p.set_option(9, args.host_slots)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev) if wl.flush_l2 else None
 
@@ -638,7 +640,9 @@ def run_gpu(args, wl):
     line = {"metric": "forward+adjoint gradient dof*steps/s at 1e-10 rel vs FP64 oracle", "value": value,
             "unit": "dof*steps/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64", "data": "synthetic", "config": dict(wl.config(), parallelism="replicas%d" % ws),
+            "dtype": "f64", "data": "synthetic",
+            "config": dict(wl.config(), parallelism="replicas%d" % ws,
+                           **({"host_checkpoint_slots": args.host_slots} if args.host_slots else {})),
             "gpu_launches": launches,
             "e2e": {"value": units / (e2e_ms / 1e3), "unit": "dof*steps/s", "h2d_bytes_per_step": bi,
                     "d2h_bytes_per_step": bo},
@@ -737,6 +741,9 @@ def main():
     ap.add_argument("--pdl", action="store_true", help="programmatic dependent launch of consecutive kernels")
     ap.add_argument("--no-fuse", action="store_true", help="RB: separate fold / solve / expand kernels")
     ap.add_argument("--x-rows", type=int, default=0, help="x-FFT rows per CTA (1, 2, 4; 0 = tuned)")
+    ap.add_argument("--host-slots", type=int, default=0,
+                    help="rb/couette: host checkpoint slots (two-level schedule; device slots then from --hbm-gb)")
+    ap.add_argument("--hbm-gb", type=float, default=None, help="couette: device checkpoint budget in GB")
     ap.add_argument("--nsteps", type=int, default=None,
                     help="override the workload's time steps, or the iterations of poiseuille_evp (profiling runs)")
     ap.add_argument("--size", default=None,
@@ -763,6 +770,10 @@ def main():
             wl.name = "rayleigh_benard2d_%dx%d_Ra1e6_rk222_%dsteps" % (dims[0], dims[1], wl.nsteps)
         else:
             ap.error("--size takes Nx,Nz for rb and Nx,Ny,Nz for couette")
+    if args.hbm_gb is not None:
+        if not isinstance(wl, Couette):
+            ap.error("--hbm-gb applies to the couette workload")
+        wl.budget = args.hbm_gb * 1e9
     if args.impl == "reference":
         return run_reference(args, wl)
     if isinstance(wl, PoiseuilleEvp):

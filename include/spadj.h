@@ -77,7 +77,10 @@ typedef enum {
  *   div u = 0, no-slip (p is the dynamic pressure).  x in [0, length[0]) (default 4 pi) and
  *   y in [0, length[1]) (default 2 pi) periodic Fourier (Nx = n[0], Ny = n[1] modes), z
  *   Chebyshev-T (N = n[2] modes) with tau terms as for SPADJ_RB2D; 3/2 dealiasing on all axes.
- *   params[0] = Re.  Scheme SBDF2 (SBDF1 first step).  State: u, v, w coefficients, layout
+ *   params[0] = Re; params[1] = laminar profile: 0 (default) plane Couette U = z as above,
+ *   1 plane Poiseuille (channel) flow U = 1 - z^2 between stationary walls (the profile of the
+ *   Parametric sensitivity example; its driving pressure gradient is held fixed).  Scheme SBDF2
+ *   (SBDF1 first step).  State: u, v, w coefficients, layout
  *   [3][Ny][Nx/2][N] complex (ky index j in FFT order as for SPADJ_KOLMOGOROV2D, kx index
  *   m = 0..Nx/2-1 with the Nyquist not stored; the ky = -Ny/2 row is held at 0 and the kx = 0
  *   plane Hermitian in ky).  Grid layout [3N/2][3Ny/2][3Nx/2] real (Gauss-Chebyshev z).
@@ -105,7 +108,9 @@ typedef enum {
 typedef enum {
   SPADJ_SBDF1 = 1, /* multistep IMEX, eq. imex, first order */
   SPADJ_SBDF2 = 2, /* multistep IMEX, eq. imex, second order (SBDF1 first step) */
-  SPADJ_RK222 = 3  /* Runge-Kutta IMEX ARS(2,2,2), Supplementary A.4 stage equation */
+  SPADJ_RK222 = 3, /* Runge-Kutta IMEX ARS(2,2,2), Supplementary A.4 stage equation */
+  SPADJ_SBDF3 = 4, /* multistep IMEX, third order (SPADJ_BURGERS1D; SBDF1, SBDF2 first steps) */
+  SPADJ_SBDF4 = 5  /* multistep IMEX, fourth order (SPADJ_BURGERS1D; SBDF1..3 first steps) */
 } spadj_scheme;
 
 typedef struct {
@@ -182,6 +187,15 @@ spadj_status spadj_solve(spadj_problem* prob, int transpose, const double* v, do
  * (state X_a current), 4 free slot, 5 evaluate the objective at state a. */
 spadj_status spadj_checkpoint_schedule(int n_steps, int slots, int* ops, int max_ops, int* n_ops);
 
+/* Two-level schedule used by spadj_gradient / spadj_vjp when host checkpoint slots are set
+ * (spadj_set_option 9, SPADJ_RB2D and SPADJ_COUETTE3D): the first forward sweep stores X_a in
+ * host memory at the start of every segment [a, a + K), K = ceil(n_steps / host_slots), and the
+ * segments are reversed last first, each from its host copy by the binomial schedule on the
+ * `slots` device slots (the paper's RAM + disk checkpointing, after H-revolve).  Same action
+ * encoding as spadj_checkpoint_schedule; host slots are numbered slots .. slots + host_slots - 1. */
+spadj_status spadj_checkpoint_schedule_host(int n_steps, int slots, int host_slots, int* ops, int max_ops,
+                                           int* n_ops);
+
 /* Forward trajectory of n_steps IMEX steps from x0 (eq. imex / RK stage equation).
  * x_out receives X_N.  traj (nullable) receives X_0..X_N, layout [n_steps+1][state]. */
 spadj_status spadj_forward(spadj_problem* prob, int n_steps, const double* x0, double* x_out,
@@ -238,8 +252,11 @@ spadj_status spadj_set_params(spadj_problem* prob, const double* params);
  * stream order); option 7 (SPADJ_RB2D) = fused column stage (1, default: the z fold, the stage
  * solve and the z expansion of each x-mode pencil run in one two-CTA cluster kernel; 0: three
  * separate kernels); option 8 (SPADJ_RB2D, SPADJ_COUETTE3D) = grid rows per CTA of the x FFTs
- * (1, 2 or 4; by default the fastest is picked by timing when the problem is created).  Set
- * them before the first sweep (the step graphs are captured once).
+ * (1, 2 or 4; by default the fastest is picked by timing when the problem is created); option 9
+ * (SPADJ_RB2D, SPADJ_COUETTE3D) = host checkpoint slots of spadj_gradient / spadj_vjp (0, default:
+ * device slots only; h > 0: the two-level schedule of spadj_checkpoint_schedule_host, the host
+ * copies in page-locked memory owned by the problem).  Set them before the first sweep (the step
+ * graphs are captured once).
  * spadj_autotune times candidate settings on the problem's own sizes and keeps the fastest. */
 spadj_status spadj_set_option(spadj_problem* prob, int option, int value);
 spadj_status spadj_autotune(spadj_problem* prob);

@@ -8,7 +8,10 @@ moving with velocities -1, +1, on x in [0, Lx), y in [0, Ly) (periodic):
     dt u - nu lap u + U dx u + w U' e_x + grad p = u x omega,   omega = curl u,
     div u = 0,   u = v = w = 0 at z = -1, +1,   int p dz = 0 on the mean pencil,
 
-nu = 1/Re.  The nonlinear term is written in rotational form, so p is the dynamic pressure
+nu = 1/Re.  ``base="poiseuille"`` replaces the laminar profile by plane Poiseuille (channel) flow
+U(z) = 1 - z^2 between stationary walls (U' = -2 z; the mean pressure gradient that drives it
+stays fixed), the profile of the paper's Parametric sensitivity example; everything else is
+unchanged.  The nonlinear term is written in rotational form, so p is the dynamic pressure
 (pressure plus |u|^2/2); the terms linear in the perturbation (advection by U and the
 shear production w U') are implicit.  IVP form M dX/dt + L X = F(X) (Supplementary A.4).
 
@@ -47,8 +50,10 @@ from . import fourier
 class Couette:
     NTAU = 7
 
-    def __init__(self, Nx, Ny, Nz, Re, Lx=4.0 * np.pi, Ly=2.0 * np.pi, dealias=1.5, nonlinear=True, pencils=True):
-        assert Nx % 2 == 0 and Ny % 2 == 0 and Nz >= 6
+    def __init__(self, Nx, Ny, Nz, Re, Lx=4.0 * np.pi, Ly=2.0 * np.pi, dealias=1.5, nonlinear=True, pencils=True,
+                 base="couette"):
+        assert Nx % 2 == 0 and Ny % 2 == 0 and Nz >= 6 and base in ("couette", "poiseuille")
+        self.base = base
         self.Nx, self.Ny, self.Nz = Nx, Ny, Nz
         self.Kx = Nx // 2
         self.Mx, self.My, self.Mz = (int(round(dealias * n)) for n in (Nx, Ny, Nz))
@@ -73,6 +78,18 @@ class Couette:
             Zt[n + 1, n] += 0.5
             Zt[n - 1, n] += 0.5
         self.ZS = (cb.S1(N + 1) @ cb.S0(N + 1) @ Zt)[:N, :]
+        if base == "couette":  # U = z, U' = 1
+            self.Umat, self.UPmat = self.ZS, self.SS
+        else:  # channel: U = 1 - z^2 (stationary walls), U' = -2 z; z^2 T_n exact in degree N + 1
+            Zt2 = np.zeros((N + 2, N + 1))
+            Zt2[1, 0] = 1.0
+            for n in range(1, N + 1):
+                Zt2[n + 1, n] += 0.5
+                Zt2[n - 1, n] += 0.5
+            one = np.zeros((N + 2, N))
+            one[:N, :] = np.eye(N)
+            self.Umat = (cb.S1(N + 2) @ cb.S0(N + 2) @ (one - Zt2 @ Zt))[:N, :]
+            self.UPmat = -2.0 * self.ZS
         self.Dz = cb.deriv_T(N)
         self.Cz = cb.c2g_matrix(N, self.Mz)
         self.Gz = cb.g2c_matrix(N, self.Mz)
@@ -99,11 +116,11 @@ class Couette:
         u, v, w, p = (slice(i * N, (i + 1) * N) for i in range(4))
         tu1, tu2, tv1, tv2, tw1, tw2, tp = range(4 * N, 4 * N + 7)
         lap = self.DD - (a * a + b * b) * self.SS
-        adv = 1j * a * self.ZS  # U dx with U = z
+        adv = 1j * a * self.Umat  # U dx
         for blk in (u, v, w):
             Mm[blk, blk] = self.SS
             Lm[blk, blk] = -nu * lap + adv
-        Lm[u, w] = self.SS  # w U' e_x, U' = 1
+        Lm[u, w] = self.UPmat  # w U' e_x
         Lm[u, p] = 1j * a * self.SS
         Lm[v, p] = 1j * b * self.SS
         Lm[w, p] = self.SD

@@ -160,6 +160,11 @@ spadj_status spadj_set_option(spadj_problem* p, int option, int value) {
     p->x_rows = value;
     return SPADJ_OK;
   }
+  if (option == 9) {
+    if (value < 0) return p->fail(SPADJ_ERR_INVALID, "set_option 9: host checkpoint slots must be >= 0");
+    p->host_slots = value;
+    return SPADJ_OK;
+  }
   return spadj::kol_set_option(p->impl, p, option, value);
 }
 
@@ -185,6 +190,29 @@ spadj_status spadj_checkpoint_schedule(int n_steps, int slots, int* ops, int max
   if (!ops) return SPADJ_OK;
   if ((int)plan.size() > max_ops) {
     g_create_error = "checkpoint_schedule: max_ops too small";
+    return SPADJ_ERR_INVALID;
+  }
+  for (size_t i = 0; i < plan.size(); ++i) {
+    ops[4 * i + 0] = plan[i].type;
+    ops[4 * i + 1] = plan[i].a;
+    ops[4 * i + 2] = plan[i].b;
+    ops[4 * i + 3] = plan[i].slot;
+  }
+  return SPADJ_OK;
+}
+
+spadj_status spadj_checkpoint_schedule_host(int n_steps, int slots, int host_slots, int* ops, int max_ops,
+                                           int* n_ops) {
+  if (n_steps < 1 || slots < 1 || host_slots < 1 || !n_ops) {
+    g_create_error = "checkpoint_schedule_host: need n_steps >= 1, slots >= 1, host_slots >= 1, n_ops != NULL";
+    return SPADJ_ERR_INVALID;
+  }
+  spadj::CkptPlanner planner;
+  std::vector<spadj::CkptOp> plan = planner.plan2(n_steps, slots, host_slots);
+  *n_ops = (int)plan.size();
+  if (!ops) return SPADJ_OK;
+  if ((int)plan.size() > max_ops) {
+    g_create_error = "checkpoint_schedule_host: max_ops too small";
     return SPADJ_ERR_INVALID;
   }
   for (size_t i = 0; i < plan.size(); ++i) {

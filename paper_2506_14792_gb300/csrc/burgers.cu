@@ -4,7 +4,7 @@
 // steps, keeps the multistep history (X_{n-1}, X_{n-2}, F_{n-1}, F_{n-2}) in registers and
 // evaluates F through shared-memory FFTs (grid of M = 3N/2 points, one L = M/2 complex FFT
 // per real transform).  Kernels:
-//   * forward  -- eq. imex with SBDF1 first step then SBDF2 (Supplementary A.4); M = I and
+//   * forward  -- eq. imex, SBDF<s> with s = min(n, order), order 1..4 (Supplementary A.4); M = I and
 //                 L = nu k^2, so the implicit solve is a per-mode division, fused.
 //   * tangent  -- the JVP of the same recurrence, run alongside the primal.
 //   * adjoint  -- eq. IMEX_adjoint backward over the stored trajectory; one VJP of F per
@@ -198,16 +198,35 @@ __global__ void F_kernel(BurgersParams P, int mode, const double* __restrict__ x
 
 // ---- persistent trajectory kernels ----------------------------------------------------------
 
+// Weights of step n (eq. imex with M = I, b_0 = 1, b_i = 0): SBDF<s>, s = min(n, order) (the
+// scheme starts at lower order while fewer past steps exist).  a: backward differentiation
+// weights (divided by dt), c: extrapolation weights of F; entries beyond s are zero.
+constexpr int kMaxOrder = 4;
 struct Coef {
-  double a0, a1, a2, c1, c2;
+  double a[kMaxOrder + 1], c[kMaxOrder + 1];
 };
+__constant__ double kSbdfA[kMaxOrder][kMaxOrder + 1] = {{1.0, -1.0, 0.0, 0.0, 0.0},
+                                                        {1.5, -2.0, 0.5, 0.0, 0.0},
+                                                        {11.0 / 6.0, -3.0, 1.5, -1.0 / 3.0, 0.0},
+                                                        {25.0 / 12.0, -4.0, 3.0, -4.0 / 3.0, 0.25}};
+__constant__ double kSbdfC[kMaxOrder][kMaxOrder + 1] = {{0.0, 1.0, 0.0, 0.0, 0.0},
+                                                        {0.0, 2.0, -1.0, 0.0, 0.0},
+                                                        {0.0, 3.0, -3.0, 1.0, 0.0},
+                                                        {0.0, 4.0, -6.0, 4.0, -1.0}};
 __device__ __forceinline__ Coef step_coef(const BurgersParams& P, int n) {
   Coef c;
-  if (n <= 1 || P.order == 1) {
-    c.a0 = 1.0 / P.dt; c.a1 = -1.0 / P.dt; c.a2 = 0.0; c.c1 = 1.0; c.c2 = 0.0;
-  } else {
-    c.a0 = 1.5 / P.dt; c.a1 = -2.0 / P.dt; c.a2 = 0.5 / P.dt; c.c1 = 2.0; c.c2 = -1.0;
+  const int s = n < P.order ? n : P.order;
+#pragma unroll
+  for (int i = 0; i <= kMaxOrder; ++i) {
+    c.a[i] = kSbdfA[s - 1][i] / P.dt;
+    c.c[i] = kSbdfC[s - 1][i];
   }
+  return c;
+}
+__device__ __forceinline__ Coef zero_coef() {
+  Coef c;
+#pragma unroll
+  for (int i = 0; i <= kMaxOrder; ++i) c.a[i] = c.c[i] = 0.0;
   return c;
 }
 
@@ -215,8 +234,22 @@ __device__ __forceinline__ double2 axpby(double a, double2 x, double b, double2 
   return make_double2(fma(a, x.x, b * y.x), fma(a, x.y, b * y.y));
 }
 
-// mode 0: forward (optionally storing traj), mode 1: tangent.
-template <int Q>
+// sum over the history terms i = 2..ORD of c_i H_F[i-1] - a_i H_X[i-1] added to r (the i = 1
+// term starts r); terms whose weights are zero add nothing
+template <int ORD>
+__device__ __forceinline__ double2 hist_rhs(const Coef& c, const double2 (&hf)[ORD], const double2 (&hx)[ORD]) {
+  double2 r = axpby(c.c[1], hf[0], -c.a[1], hx[0]);
+#pragma unroll
+  for (int i = 2; i <= ORD; ++i)
+    if (c.c[i] != 0.0 || c.a[i] != 0.0)
+      r = make_double2(r.x + c.c[i] * hf[i - 1].x - c.a[i] * hx[i - 1].x,
+                       r.y + c.c[i] * hf[i - 1].y - c.a[i] * hx[i - 1].y);
+  return r;
+}
+
+// mode 0: forward (optionally storing traj), mode 1: tangent.  ORD = the history length kept
+// in registers (2 for SBDF1/2, 4 for SBDF3/4): X_{n-1..n-ORD}, F_{n-1..n-ORD} (and their tangents).
+template <int Q, int ORD>
 __global__ void __launch_bounds__(64) trajectory_kernel(BurgersParams P, int n_steps, const double* __restrict__ x0,
                                                         const double* __restrict__ dx0, double* __restrict__ x_out,
                                                         double* __restrict__ traj, int tangent) {
@@ -226,19 +259,19 @@ __global__ void __launch_bounds__(64) trajectory_kernel(BurgersParams P, int n_s
   double2* O2 = S2 + P.K;
   const int b = blockIdx.x, K = P.K, G = blockDim.x, tid = threadIdx.x;
   const int nb = gridDim.x;
-  double2 X1[Q], X2[Q], F1[Q], F2[Q], D1[Q], D2[Q], G1[Q], G2[Q];
+  double2 X[Q][ORD], F[Q][ORD], D[Q][ORD], GJ[Q][ORD];
   const double2* xr = row(x0, b, K);
   for (int q = 0; q < Q; ++q) {
     int k = tid + q * G;
     double2 z = make_double2(0.0, 0.0);
-    X1[q] = (k < K) ? xr[k] : z;
-    X2[q] = z; F1[q] = z; F2[q] = z;
-    D1[q] = z; D2[q] = z; G1[q] = z; G2[q] = z;
-    if (tangent && k < K) D1[q] = row(dx0, b, K)[k];
+#pragma unroll
+    for (int i = 0; i < ORD; ++i) X[q][i] = F[q][i] = D[q][i] = GJ[q][i] = z;
+    X[q][0] = (k < K) ? xr[k] : z;
+    if (tangent && k < K) D[q][0] = row(dx0, b, K)[k];
     if (k < K) {
-      s.S[k] = X1[q];
-      if (tangent) S2[k] = D1[q];
-      if (traj) row(traj, b, K)[k] = X1[q];
+      s.S[k] = X[q][0];
+      if (tangent) S2[k] = D[q][0];
+      if (traj) row(traj, b, K)[k] = X[q][0];
     }
   }
   __syncthreads();
@@ -247,7 +280,7 @@ __global__ void __launch_bounds__(64) trajectory_kernel(BurgersParams P, int n_s
     else eval_F(P, s);
     for (int q = 0; q < Q; ++q) {
       int k = tid + q * G;
-      if (k < K) { F1[q] = s.O[k]; if (tangent) G1[q] = O2[k]; }
+      if (k < K) { F[q][0] = s.O[k]; if (tangent) GJ[q][0] = O2[k]; }
     }
   }
   for (int n = 1; n <= n_steps; ++n) {
@@ -256,20 +289,20 @@ __global__ void __launch_bounds__(64) trajectory_kernel(BurgersParams P, int n_s
       int k = tid + q * G;
       if (k >= K) continue;
       double kk = kwav(P, k);
-      double inv = 1.0 / (c.a0 + P.nu * kk * kk);
-      double2 r = axpby(c.c1, F1[q], -c.a1, X1[q]);
-      if (c.c2 != 0.0) r = make_double2(r.x + c.c2 * F2[q].x - c.a2 * X2[q].x, r.y + c.c2 * F2[q].y - c.a2 * X2[q].y);
-      double2 xn = cscale(r, inv);
+      double inv = 1.0 / (c.a[0] + P.nu * kk * kk);
+      double2 xn = cscale(hist_rhs<ORD>(c, F[q], X[q]), inv);
       if (k == 0) xn.y = 0.0;
-      X2[q] = X1[q]; X1[q] = xn; F2[q] = F1[q];
+#pragma unroll
+      for (int i = ORD - 1; i > 0; --i) { X[q][i] = X[q][i - 1]; F[q][i] = F[q][i - 1]; }
+      X[q][0] = xn;
       s.S[k] = xn;
       if (traj) row(traj + (size_t)n * nb * 2 * K, b, K)[k] = xn;
       if (tangent) {
-        double2 rd = axpby(c.c1, G1[q], -c.a1, D1[q]);
-        if (c.c2 != 0.0) rd = make_double2(rd.x + c.c2 * G2[q].x - c.a2 * D2[q].x, rd.y + c.c2 * G2[q].y - c.a2 * D2[q].y);
-        double2 dn = cscale(rd, inv);
+        double2 dn = cscale(hist_rhs<ORD>(c, GJ[q], D[q]), inv);
         if (k == 0) dn.y = 0.0;
-        D2[q] = D1[q]; D1[q] = dn; G2[q] = G1[q];
+#pragma unroll
+        for (int i = ORD - 1; i > 0; --i) { D[q][i] = D[q][i - 1]; GJ[q][i] = GJ[q][i - 1]; }
+        D[q][0] = dn;
         S2[k] = dn;
       }
     }
@@ -279,21 +312,21 @@ __global__ void __launch_bounds__(64) trajectory_kernel(BurgersParams P, int n_s
       else eval_F(P, s);
       for (int q = 0; q < Q; ++q) {
         int k = tid + q * G;
-        if (k < K) { F1[q] = s.O[k]; if (tangent) G1[q] = O2[k]; }
+        if (k < K) { F[q][0] = s.O[k]; if (tangent) GJ[q][0] = O2[k]; }
       }
     }
   }
   double2* o = row(x_out, b, K);
   for (int q = 0; q < Q; ++q) {
     int k = tid + q * G;
-    if (k < K) o[k] = tangent ? D1[q] : X1[q];
+    if (k < K) o[k] = tangent ? D[q][0] : X[q][0];
   }
 }
 
 // Adjoint sweep (eq. IMEX_adjoint) over traj = X_0..X_N, seeded by y_final = dJ/dX_N.
 // seed_at (nullable, device, n_steps+1 ints): index into seeds ([n][member][k]) of the
 // cotangent injected at X_n, or -1; when seed_at is NULL the only seed is y_final at X_N.
-template <int Q>
+template <int Q, int ORD>
 __global__ void __launch_bounds__(64) adjoint_kernel(BurgersParams P, int n_steps, const double* __restrict__ traj,
                                                      const double* __restrict__ y_final, double* __restrict__ grad,
                                                      const int* __restrict__ seed_at, const double* __restrict__ seeds) {
@@ -303,9 +336,11 @@ __global__ void __launch_bounds__(64) adjoint_kernel(BurgersParams P, int n_step
   const int b = blockIdx.x, K = P.K, G = blockDim.x, tid = threadIdx.x;
   const int nb = gridDim.x;
   const size_t stride = (size_t)nb * 2 * K;
-  double2 Y1[Q], Y2[Q];
+  double2 Y[Q][ORD];  // Y_{n+1}, ..., Y_{n+ORD}
   const double2 z = make_double2(0.0, 0.0);
-  for (int q = 0; q < Q; ++q) { Y1[q] = z; Y2[q] = z; }
+  for (int q = 0; q < Q; ++q)
+#pragma unroll
+    for (int i = 0; i < ORD; ++i) Y[q][i] = z;
   for (int n = n_steps; n >= 0; --n) {
     double2 lam[Q];
     if (n == n_steps) {
@@ -314,14 +349,23 @@ __global__ void __launch_bounds__(64) adjoint_kernel(BurgersParams P, int n_step
         lam[q] = (k < K && y_final) ? row(y_final, b, K)[k] : z;
       }
     } else {
-      Coef c1 = step_coef(P, n + 1);
-      Coef c2 = (n + 2 <= n_steps) ? step_coef(P, n + 2) : Coef{0, 0, 0, 0, 0};
+      // the weights of step n+i that multiply X_n: c_i^{n+i}, a_i^{n+i} (zero past the horizon)
+      double wc[ORD + 1], wa[ORD + 1];
+#pragma unroll
+      for (int i = 1; i <= ORD; ++i) {
+        const Coef ci = (n + i <= n_steps) ? step_coef(P, n + i) : zero_coef();
+        wc[i] = ci.c[i];
+        wa[i] = ci.a[i];
+      }
       const double2* xn = row(traj + (size_t)n * stride, b, K);
       for (int q = 0; q < Q; ++q) {
         int k = tid + q * G;
         if (k >= K) continue;
         s.S[k] = xn[k];
-        S2[k] = axpby(c1.c1, Y1[q], c2.c2, Y2[q]);
+        double2 w = axpby(wc[1], Y[q][0], wc[2], Y[q][1]);
+#pragma unroll
+        for (int i = 3; i <= ORD; ++i) w = make_double2(w.x + wc[i] * Y[q][i - 1].x, w.y + wc[i] * Y[q][i - 1].y);
+        S2[k] = w;
       }
       __syncthreads();
       if (P.nonlinear) eval_vjp(P, s, S2);
@@ -329,7 +373,10 @@ __global__ void __launch_bounds__(64) adjoint_kernel(BurgersParams P, int n_step
         int k = tid + q * G;
         if (k >= K) { lam[q] = z; continue; }
         double2 v = P.nonlinear ? s.O[k] : z;
-        lam[q] = make_double2(v.x - c1.a1 * Y1[q].x - c2.a2 * Y2[q].x, v.y - c1.a1 * Y1[q].y - c2.a2 * Y2[q].y);
+        double2 l = make_double2(v.x - wa[1] * Y[q][0].x - wa[2] * Y[q][1].x, v.y - wa[1] * Y[q][0].y - wa[2] * Y[q][1].y);
+#pragma unroll
+        for (int i = 3; i <= ORD; ++i) l = make_double2(l.x - wa[i] * Y[q][i - 1].x, l.y - wa[i] * Y[q][i - 1].y);
+        lam[q] = l;
       }
       __syncthreads();
     }
@@ -353,10 +400,11 @@ __global__ void __launch_bounds__(64) adjoint_kernel(BurgersParams P, int n_step
       int k = tid + q * G;
       if (k >= K) continue;
       double kk = kwav(P, k);
-      double2 y = cscale(lam[q], 1.0 / (c.a0 + P.nu * kk * kk));
+      double2 y = cscale(lam[q], 1.0 / (c.a[0] + P.nu * kk * kk));
       if (k == 0) y.y = 0.0;
-      Y2[q] = Y1[q];
-      Y1[q] = y;
+#pragma unroll
+      for (int i = ORD - 1; i > 0; --i) Y[q][i] = Y[q][i - 1];
+      Y[q][0] = y;
     }
   }
 }
@@ -415,9 +463,13 @@ struct Burgers : EqImpl {
     P.kscale = 2.0 * M_PI / P.length;
     P.nu = d.params[0];
     P.dt = d.dt;
-    P.order = d.scheme == SPADJ_SBDF1 ? 1 : 2;
-    if (d.scheme != SPADJ_SBDF1 && d.scheme != SPADJ_SBDF2)
-      return p->fail(SPADJ_ERR_UNSUPPORTED, "burgers: scheme must be SBDF1 or SBDF2");
+    switch (d.scheme) {
+      case SPADJ_SBDF1: P.order = 1; break;
+      case SPADJ_SBDF2: P.order = 2; break;
+      case SPADJ_SBDF3: P.order = 3; break;
+      case SPADJ_SBDF4: P.order = 4; break;
+      default: return p->fail(SPADJ_ERR_UNSUPPORTED, "burgers: scheme must be SBDF1, SBDF2, SBDF3 or SBDF4");
+    }
     P.nonlinear = d.nonlinear;
     P.plan = make_plan(P.L);
     if (P.plan.nrad < 0) return p->fail(SPADJ_ERR_INVALID, "burgers: 3N/4 must be of the form 2^a 3^b");
@@ -446,12 +498,17 @@ struct Burgers : EqImpl {
     return check_launch(p, "burgers F");
   }
 
+  // modes per thread Q and register history length (2 for SBDF1/2, 4 for SBDF3/4)
   template <class Fn>
   spadj_status dispatchQ(Problem* p, Fn fn) {
     int Q = (P.K + G - 1) / G;
-    if (Q <= 1) fn(std::integral_constant<int, 1>());
-    else if (Q == 2) fn(std::integral_constant<int, 2>());
-    else fn(std::integral_constant<int, 4>());
+    auto byQ = [&](auto ord) {
+      if (Q <= 1) fn(std::integral_constant<int, 1>(), ord);
+      else if (Q == 2) fn(std::integral_constant<int, 2>(), ord);
+      else fn(std::integral_constant<int, 4>(), ord);
+    };
+    if (P.order <= 2) byQ(std::integral_constant<int, 2>());
+    else byQ(std::integral_constant<int, 4>());
     return check_launch(p, "burgers trajectory");
   }
 
@@ -462,8 +519,9 @@ struct Burgers : EqImpl {
   spadj_status forward(Problem* p, int n_steps, const double* x0, double* x_out, double* trj) override {
     if (n_steps < 0) return p->fail(SPADJ_ERR_INVALID, "forward: n_steps < 0");
     cudaEvent_t t = p->tic();
-    spadj_status s = dispatchQ(p, [&](auto q) {
-      trajectory_kernel<decltype(q)::value><<<B, G, smem, p->stream>>>(P, n_steps, x0, nullptr, x_out, trj, 0);
+    spadj_status s = dispatchQ(p, [&](auto q, auto o) {
+      trajectory_kernel<decltype(q)::value, decltype(o)::value><<<B, G, smem, p->stream>>>(P, n_steps, x0, nullptr,
+                                                                                         x_out, trj, 0);
     });
     p->toc(t, KC_FUSED, (double)B * n_steps * (2 * fft_flops() + P.M + 10.0 * P.K));
     return s;
@@ -471,8 +529,9 @@ struct Burgers : EqImpl {
 
   spadj_status tangent(Problem* p, int n_steps, const double* x0, const double* dx0, double* dx_out) override {
     if (n_steps < 0) return p->fail(SPADJ_ERR_INVALID, "tangent: n_steps < 0");
-    return dispatchQ(p, [&](auto q) {
-      trajectory_kernel<decltype(q)::value><<<B, G, smem, p->stream>>>(P, n_steps, x0, dx0, dx_out, nullptr, 1);
+    return dispatchQ(p, [&](auto q, auto o) {
+      trajectory_kernel<decltype(q)::value, decltype(o)::value><<<B, G, smem, p->stream>>>(P, n_steps, x0, dx0, dx_out,
+                                                                                         nullptr, 1);
     });
   }
 
@@ -505,8 +564,9 @@ struct Burgers : EqImpl {
   spadj_status adjoint(Problem* p, int n_steps, const double* trj, const double* y_final, double* grad) override {
     if (n_steps < 1) return p->fail(SPADJ_ERR_INVALID, "adjoint: n_steps < 1");
     cudaEvent_t t = p->tic();
-    spadj_status s = dispatchQ(p, [&](auto q) {
-      adjoint_kernel<decltype(q)::value><<<B, G, smem, p->stream>>>(P, n_steps, trj, y_final, grad, seed_dev, seeds_dev);
+    spadj_status s = dispatchQ(p, [&](auto q, auto o) {
+      adjoint_kernel<decltype(q)::value, decltype(o)::value><<<B, G, smem, p->stream>>>(P, n_steps, trj, y_final, grad,
+                                                                                      seed_dev, seeds_dev);
     });
     p->toc(t, KC_FUSED, (double)B * n_steps * (3 * fft_flops() + 2.0 * P.M + 12.0 * P.K));
     return s;

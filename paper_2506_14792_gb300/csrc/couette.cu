@@ -30,6 +30,7 @@ using namespace couk;
 
 struct Couette : EqImpl {
   int Nx = 0, Ny = 0, N = 0, Kx = 0, Mx = 0, My = 0, Mz = 0, L = 0, P = 0, order = 2;
+  int base = 0;  // laminar profile: 0 plane Couette U = z, 1 plane Poiseuille U = 1 - z^2
   double Lx = 0, Ly = 0, Re = 0, nu = 0, dt = 0;
   int nonlinear = 1;
   size_t nfield = 0;  // complex entries of one field [Ny][Kx][N]
@@ -43,6 +44,7 @@ struct Couette : EqImpl {
   DevBuf Zm, Ym, Gf, dGf, Gb, Fg, Xr, Fr, dXr, dFr, Wr, xbar, src0, partial, edev, sdev, Jdev, slots, wts;
   DevBuf phiRF, phiRA, ginv, nrm, g2;  // resolvent operators of the last frequency, G^-1, per-pencil norms
   DevBuf htraj, hdtraj, dWr, dxbar, htmp;  // Hessian-vector product: trajectories and second-order cotangents
+  HostBuf hslots;  // host tier of the two-level checkpoint schedule
   double res_omega = 0.0;
   bool res_built = false;
   size_t zsmem = 0, xsmem = 0, ysmem = 0;
@@ -78,6 +80,9 @@ struct Couette : EqImpl {
     Re = d.params[0];
     if (!(Re > 0)) return p->fail(SPADJ_ERR_INVALID, "couette: params[0] (Reynolds number) must be > 0");
     nu = 1.0 / Re;
+    base = (int)d.params[1];
+    if ((base != 0 && base != 1) || (double)base != d.params[1])
+      return p->fail(SPADJ_ERR_INVALID, "couette: params[1] must be 0 (plane Couette) or 1 (plane Poiseuille)");
     dt = d.dt;
     nonlinear = d.nonlinear;
     Lx = d.length[0] > 0 ? d.length[0] : 4.0 * M_PI;
@@ -107,8 +112,9 @@ struct Couette : EqImpl {
     ops = o;
     std::vector<double> f1, a1, f2, a2;
     std::string err;
-    if (!couhost::build_phi(o, Kx, Ny, Lx, Ly, nu, 1.0 / dt, f1, a1, &err)) return p->fail(SPADJ_ERR_INVALID, err);
-    if (order == 2 && !couhost::build_phi(o, Kx, Ny, Lx, Ly, nu, 1.5 / dt, f2, a2, &err))
+    if (!couhost::build_phi(o, Kx, Ny, Lx, Ly, nu, 1.0 / dt, f1, a1, &err, base))
+      return p->fail(SPADJ_ERR_INVALID, err);
+    if (order == 2 && !couhost::build_phi(o, Kx, Ny, Lx, Ly, nu, 1.5 / dt, f2, a2, &err, base))
       return p->fail(SPADJ_ERR_INVALID, err);
     const int Mh = Mz / 2;
     std::vector<double> hczE((size_t)Mh * N), hcdzE((size_t)Mh * N), hgzF((size_t)N * Mh), hgzTE((size_t)Mh * N),
@@ -641,13 +647,19 @@ struct Couette : EqImpl {
     const size_t sb = sizeof(double2) * ns;
     SPADJ_CUDA_TRY(p, slots.ensure(3 * sb * (size_t)S));
     CkptPlanner planner;
-    std::vector<CkptOp> ops = planner.plan(n_steps, S);
+    const int H = std::min(p->host_slots, n_steps);
+    std::vector<CkptOp> ops = H > 0 ? planner.plan2(n_steps, S, H) : planner.plan(n_steps, S);
+    if (H > 0) SPADJ_CUDA_TRY(p, hslots.ensure(3 * sb * (size_t)H));
     const double2* x0c = reinterpret_cast<const double2*>(x0);
     Ring r;
     SPADJ_CUDA_TRY(p, cudaMemcpyAsync(st(Xr, r.xc), x0, sb, cudaMemcpyDeviceToDevice, p->stream));
     int cur_step = 0, recompute = 0;
     bool have_seed = false;
-    auto slot = [&](int sl, int part) { return slots.as<char>() + ((size_t)sl * 3 + part) * sb; };
+    // device slots 0..S-1, host slots S..S+H-1; each holds (x_n, x_{n-1}, f_{n-1})
+    auto slot = [&](int sl, int part) {
+      return sl < S ? slots.as<char>() + ((size_t)sl * 3 + part) * sb
+                    : hslots.as<char>() + ((size_t)(sl - S) * 3 + part) * sb;
+    };
     auto seed_ptr = [&](int n) -> const double2* {
       if (objective_kind >= 0 || n < 0 || n >= (int)seed_at.size() || seed_at[n] < 0) return nullptr;
       return reinterpret_cast<const double2*>(seeds) + (size_t)seed_at[n] * ns;
@@ -655,16 +667,19 @@ struct Couette : EqImpl {
     for (const CkptOp& op : ops) {
       spadj_status s = SPADJ_OK;
       switch (op.type) {
-        case CK_STORE:
-          SPADJ_CUDA_TRY(p, cudaMemcpyAsync(slot(op.slot, 0), st(Xr, r.xc), sb, cudaMemcpyDeviceToDevice, p->stream));
-          SPADJ_CUDA_TRY(p, cudaMemcpyAsync(slot(op.slot, 1), st(Xr, r.xp), sb, cudaMemcpyDeviceToDevice, p->stream));
-          SPADJ_CUDA_TRY(p, cudaMemcpyAsync(slot(op.slot, 2), st(Fr, r.fp), sb, cudaMemcpyDeviceToDevice, p->stream));
+        case CK_STORE: {
+          const cudaMemcpyKind k = op.slot < S ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+          SPADJ_CUDA_TRY(p, cudaMemcpyAsync(slot(op.slot, 0), st(Xr, r.xc), sb, k, p->stream));
+          SPADJ_CUDA_TRY(p, cudaMemcpyAsync(slot(op.slot, 1), st(Xr, r.xp), sb, k, p->stream));
+          SPADJ_CUDA_TRY(p, cudaMemcpyAsync(slot(op.slot, 2), st(Fr, r.fp), sb, k, p->stream));
           break;
+        }
         case CK_RESTORE:
           if (cur_step != op.a) {
-            SPADJ_CUDA_TRY(p, cudaMemcpyAsync(st(Xr, r.xc), slot(op.slot, 0), sb, cudaMemcpyDeviceToDevice, p->stream));
-            SPADJ_CUDA_TRY(p, cudaMemcpyAsync(st(Xr, r.xp), slot(op.slot, 1), sb, cudaMemcpyDeviceToDevice, p->stream));
-            SPADJ_CUDA_TRY(p, cudaMemcpyAsync(st(Fr, r.fp), slot(op.slot, 2), sb, cudaMemcpyDeviceToDevice, p->stream));
+            const cudaMemcpyKind k = op.slot < S ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+            SPADJ_CUDA_TRY(p, cudaMemcpyAsync(st(Xr, r.xc), slot(op.slot, 0), sb, k, p->stream));
+            SPADJ_CUDA_TRY(p, cudaMemcpyAsync(st(Xr, r.xp), slot(op.slot, 1), sb, k, p->stream));
+            SPADJ_CUDA_TRY(p, cudaMemcpyAsync(st(Fr, r.fp), slot(op.slot, 2), sb, k, p->stream));
             cur_step = op.a;
           }
           break;
@@ -856,7 +871,7 @@ struct Couette : EqImpl {
     if (!res_built || omega != res_omega) {
       std::vector<double> rf, ra;
       std::string err;
-      if (!couhost::build_phi(ops, Kx, Ny, Lx, Ly, nu, std::complex<double>(0.0, omega), rf, ra, &err))
+      if (!couhost::build_phi(ops, Kx, Ny, Lx, Ly, nu, std::complex<double>(0.0, omega), rf, ra, &err, base))
         return p->fail(SPADJ_ERR_INVALID, err);
       SPADJ_CUDA_TRY(p, phiRF.ensure(sizeof(double) * rf.size()));
       SPADJ_CUDA_TRY(p, phiRA.ensure(sizeof(double) * ra.size()));
@@ -981,6 +996,7 @@ struct Couette : EqImpl {
                       &Zm, &Ym, &Gf, &dGf, &Gb, &Fg, &Xr, &Fr, &dXr, &dFr, &Wr, &xbar, &src0, &partial, &edev, &sdev,
                       &Jdev, &slots, &wts, &phiRF, &phiRA, &ginv, &nrm, &g2, &htraj, &hdtraj, &dWr, &dxbar, &htmp})
       b->release();
+    hslots.release();
   }
 };
 

@@ -18,6 +18,7 @@
 // system solves") and applied on the GPU as a dense matvec.
 #include "couette_setup.h"
 
+#include <algorithm>
 #include <cmath>
 #include <complex>
 #include <thread>
@@ -26,6 +27,21 @@ namespace spadj {
 namespace couhost {
 
 using cd = std::complex<double>;
+
+namespace {
+// y -= l x over n complex entries, written on the interleaved (re, im) doubles so that the
+// compiler vectorises it (std::complex products carry a NaN-recovery branch that blocks it)
+inline void caxpy_sub(cd* y, const cd* x, cd l, int n) {
+  double* __restrict yd = reinterpret_cast<double*>(y);
+  const double* __restrict xd = reinterpret_cast<const double*>(x);
+  const double lr = l.real(), li = l.imag();
+  for (int c = 0; c < n; ++c) {
+    const double xr = xd[2 * c], xi = xd[2 * c + 1];
+    yd[2 * c] -= lr * xr - li * xi;
+    yd[2 * c + 1] -= lr * xi + li * xr;
+  }
+}
+}  // namespace
 
 bool lu_factor(std::vector<cd>& a, std::vector<int>& piv, int n) {
   piv.resize(n);
@@ -46,37 +62,41 @@ bool lu_factor(std::vector<cd>& a, std::vector<int>& piv, int n) {
       const cd l = a[(size_t)i * n + k] * inv;
       a[(size_t)i * n + k] = l;
       if (l == 0.0) continue;
-      cd* ri = &a[(size_t)i * n];
-      for (int j = k + 1; j < n; ++j) ri[j] -= l * rk[j];
+      caxpy_sub(&a[(size_t)i * n + k + 1], rk + k + 1, l, n - k - 1);
     }
   }
   return true;
 }
+
+// Right-hand sides are swept in panels of kPanel columns, so that the rows of a panel stay in
+// cache through a whole substitution (the arithmetic of every entry is unchanged).
+constexpr int kPanel = 32;
 
 // Solve A X = B for nr right-hand sides held row-major in B (n x nr), overwritten.
 void lu_solve_multi(const std::vector<cd>& a, const std::vector<int>& piv, int n, std::vector<cd>& B, int nr) {
   for (int k = 0; k < n; ++k)
     if (piv[k] != k)
       for (int c = 0; c < nr; ++c) std::swap(B[(size_t)k * nr + c], B[(size_t)piv[k] * nr + c]);
-  for (int i = 1; i < n; ++i) {
-    cd* bi = &B[(size_t)i * nr];
-    for (int j = 0; j < i; ++j) {
-      const cd l = a[(size_t)i * n + j];
-      if (l == 0.0) continue;
-      const cd* bj = &B[(size_t)j * nr];
-      for (int c = 0; c < nr; ++c) bi[c] -= l * bj[c];
+  for (int c0 = 0; c0 < nr; c0 += kPanel) {
+    const int w = std::min(kPanel, nr - c0);
+    for (int i = 1; i < n; ++i) {
+      cd* bi = &B[(size_t)i * nr + c0];
+      for (int j = 0; j < i; ++j) {
+        const cd l = a[(size_t)i * n + j];
+        if (l == 0.0) continue;
+        caxpy_sub(bi, &B[(size_t)j * nr + c0], l, w);
+      }
     }
-  }
-  for (int i = n - 1; i >= 0; --i) {
-    cd* bi = &B[(size_t)i * nr];
-    for (int j = i + 1; j < n; ++j) {
-      const cd u = a[(size_t)i * n + j];
-      if (u == 0.0) continue;
-      const cd* bj = &B[(size_t)j * nr];
-      for (int c = 0; c < nr; ++c) bi[c] -= u * bj[c];
+    for (int i = n - 1; i >= 0; --i) {
+      cd* bi = &B[(size_t)i * nr + c0];
+      for (int j = i + 1; j < n; ++j) {
+        const cd u = a[(size_t)i * n + j];
+        if (u == 0.0) continue;
+        caxpy_sub(bi, &B[(size_t)j * nr + c0], u, w);
+      }
+      const cd inv = 1.0 / a[(size_t)i * n + i];
+      for (int c = 0; c < w; ++c) bi[c] *= inv;
     }
-    const cd inv = 1.0 / a[(size_t)i * n + i];
-    for (int c = 0; c < nr; ++c) bi[c] *= inv;
   }
 }
 
@@ -84,24 +104,25 @@ void lu_solve_multi(const std::vector<cd>& a, const std::vector<int>& piv, int n
 // forward substitution with U^H, back substitution with the unit L^H, then the row swaps
 // undone in reverse order.
 void lu_solve_h_multi(const std::vector<cd>& a, const std::vector<int>& piv, int n, std::vector<cd>& B, int nr) {
-  for (int i = 0; i < n; ++i) {
-    cd* bi = &B[(size_t)i * nr];
-    for (int j = 0; j < i; ++j) {
-      const cd u = std::conj(a[(size_t)j * n + i]);
-      if (u == 0.0) continue;
-      const cd* bj = &B[(size_t)j * nr];
-      for (int c = 0; c < nr; ++c) bi[c] -= u * bj[c];
+  for (int c0 = 0; c0 < nr; c0 += kPanel) {
+    const int w = std::min(kPanel, nr - c0);
+    for (int i = 0; i < n; ++i) {
+      cd* bi = &B[(size_t)i * nr + c0];
+      for (int j = 0; j < i; ++j) {
+        const cd u = std::conj(a[(size_t)j * n + i]);
+        if (u == 0.0) continue;
+        caxpy_sub(bi, &B[(size_t)j * nr + c0], u, w);
+      }
+      const cd inv = 1.0 / std::conj(a[(size_t)i * n + i]);
+      for (int c = 0; c < w; ++c) bi[c] *= inv;
     }
-    const cd inv = 1.0 / std::conj(a[(size_t)i * n + i]);
-    for (int c = 0; c < nr; ++c) bi[c] *= inv;
-  }
-  for (int i = n - 2; i >= 0; --i) {
-    cd* bi = &B[(size_t)i * nr];
-    for (int j = i + 1; j < n; ++j) {
-      const cd l = std::conj(a[(size_t)j * n + i]);
-      if (l == 0.0) continue;
-      const cd* bj = &B[(size_t)j * nr];
-      for (int c = 0; c < nr; ++c) bi[c] -= l * bj[c];
+    for (int i = n - 2; i >= 0; --i) {
+      cd* bi = &B[(size_t)i * nr + c0];
+      for (int j = i + 1; j < n; ++j) {
+        const cd l = std::conj(a[(size_t)j * n + i]);
+        if (l == 0.0) continue;
+        caxpy_sub(bi, &B[(size_t)j * nr + c0], l, w);
+      }
     }
   }
   for (int k = n - 1; k >= 0; --k)
@@ -216,10 +237,10 @@ void assemble_pencil(const rbhost::Operators& o, const std::vector<double>& ZS, 
 }
 
 bool build_phi(const rbhost::Operators& o, int Kx, int Ny, double Lx, double Ly, double nu, cd a0,
-               std::vector<double>& phiF, std::vector<double>& phiA, std::string* err) {
+               std::vector<double>& phiF, std::vector<double>& phiA, std::string* err, int base) {
   const int N = o.N, nv = 4 * N + 7, H = 3 * N, Nyh = Ny / 2;
   std::vector<double> ZS, UP;
-  base_flow(o, 0, ZS, UP);
+  base_flow(o, base, ZS, UP);
   const size_t per = (size_t)H * H * 2;
   const int npen = Kx * Nyh;
   phiF.assign((size_t)npen * per, 0.0);

@@ -39,8 +39,9 @@ void assemble_pencil(const rbhost::Operators& o, const std::vector<double>& Umat
 // (re, im) doubles: phiF[jh][m][k][r] = Phi[r][k] and phiA[jh][m][r][k] = Phi[r][k].
 // Pencils with ky < 0 follow from Phi(kx, -ky) = D Phi(kx, ky) D, D = diag(1, -1, 1) on
 // (u, v, w).  Returns false (and sets err) if a pencil matrix is singular.
+// base selects the laminar profile as in base_flow (0 plane Couette, 1 plane Poiseuille).
 bool build_phi(const rbhost::Operators& o, int Kx, int Ny, double Lx, double Ly, double nu, std::complex<double> a0,
-               std::vector<double>& phiF, std::vector<double>& phiA, std::string* err);
+               std::vector<double>& phiF, std::vector<double>& phiA, std::string* err, int base = 0);
 
 // Shift-invert operators of P eigenvalue pencils (prm[p] = alpha, beta, Re; shift[p] = sigma as
 // (re, im)) of the base flow `base`: with A_p = sigma_p M + L_p (one LU per pencil),

@@ -58,6 +58,32 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double* red) {
   }
 }
 
+constexpr int kRows = 4;       // rows per warp block in evp_iter_kernel (2 kRows partial sums per lane)
+constexpr int kRowsLog2V = 3;  // log2(2 kRows)
+
+// Warp reduction of 2 kRows values per lane at once: a butterfly in which every exchange halves
+// the values a lane carries (offsets 16, 8, ...; the lane keeps the half selected by that bit of
+// its index) until one is left, then plain exchanges at the remaining offsets.  Every lane of the
+// group l >> (5 - kRowsLog2V) = m ends with the total of value m.  2 kRows + 1 additions per lane
+// for 2 kRows sums instead of 5 per sum; fixed order, so deterministic.
+__device__ __forceinline__ double warp_reduce_rows(double (&v)[2 * kRows], int lane) {
+  int off = 16;
+#pragma unroll
+  for (int half = kRows; half >= 1; half >>= 1, off >>= 1) {
+    const bool hi = (lane & off) != 0;
+#pragma unroll
+    for (int j = 0; j < half; ++j) {
+      const double send = hi ? v[j] : v[j + half];
+      const double keep = hi ? v[j + half] : v[j];
+      v[j] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+    }
+  }
+  double t = v[0];
+#pragma unroll
+  for (int o = 16 >> kRowsLog2V; o >= 1; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  return t;
+}
+
 struct EvpIterArgs {
   const double2* T;      // [P][nv][H]: rows 0..H-1 are Phi
   double2* x;            // [P][H] right iterate (in / out)
@@ -73,7 +99,7 @@ struct EvpIterArgs {
 // NC = ceil(3N / 32) column chunks per lane, fixed at compile time so that only the last chunk
 // carries a bounds predicate.
 template <int NC>
-__global__ void __launch_bounds__(kEvpThreads) evp_iter_kernel(const EvpIterArgs A) {
+__global__ void __launch_bounds__(kEvpThreads, 2) evp_iter_kernel(const EvpIterArgs A) {
   const int p = blockIdx.x, H = A.H;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   extern __shared__ double2 evsm[];
@@ -93,29 +119,40 @@ __global__ void __launch_bounds__(kEvpThreads) evp_iter_kernel(const EvpIterArgs
     double2 zacc[NC];
 #pragma unroll
     for (int c = 0; c < NC; ++c) zacc[c] = make_double2(0.0, 0.0);
-    for (int r = warp; r < H; r += kEvpWarps) {
-      const double2* row = Tp + (size_t)r * H;
-      const double2 pr = ps[r];
-      double ax = 0.0, ay = 0.0;
+    // blocks of kRows rows per warp: each x chunk is read once per block, and the row sums of
+    // the block are reduced together (warp_reduce_rows) instead of one butterfly per row
+    for (int rb = warp * kRows; rb < H; rb += kRows * kEvpWarps) {
+      double acc[2 * kRows];
+      double2 pr[kRows];
+#pragma unroll
+      for (int i = 0; i < kRows; ++i) {
+        acc[2 * i] = acc[2 * i + 1] = 0.0;
+        pr[i] = rb + i < H ? ps[rb + i] : make_double2(0.0, 0.0);
+      }
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
         const int k = c * 32 + lane;
         if (c < NC - 1 || k < H) {
-          const double2 t = __ldg(&row[k]);
           const double2 xv = x[k];
-          ax = fma(t.x, xv.x, ax);
-          ax = fma(-t.y, xv.y, ax);
-          ay = fma(t.x, xv.y, ay);
-          ay = fma(t.y, xv.x, ay);
-          zacc[c].x = fma(t.x, pr.x, zacc[c].x);  // conj(t) * psi_r
-          zacc[c].x = fma(t.y, pr.y, zacc[c].x);
-          zacc[c].y = fma(t.x, pr.y, zacc[c].y);
-          zacc[c].y = fma(-t.y, pr.x, zacc[c].y);
+#pragma unroll
+          for (int i = 0; i < kRows; ++i) {
+            if (rb + i >= H) continue;
+            const double2 t = __ldg(&Tp[(size_t)(rb + i) * H + k]);
+            acc[2 * i] = fma(t.x, xv.x, acc[2 * i]);
+            acc[2 * i] = fma(-t.y, xv.y, acc[2 * i]);
+            acc[2 * i + 1] = fma(t.x, xv.y, acc[2 * i + 1]);
+            acc[2 * i + 1] = fma(t.y, xv.x, acc[2 * i + 1]);
+            zacc[c].x = fma(t.x, pr[i].x, zacc[c].x);  // conj(t) * psi_r
+            zacc[c].x = fma(t.y, pr[i].y, zacc[c].x);
+            zacc[c].y = fma(t.x, pr[i].y, zacc[c].y);
+            zacc[c].y = fma(-t.y, pr[i].x, zacc[c].y);
+          }
         }
       }
-      ax = warp_sum(ax);
-      ay = warp_sum(ay);
-      if (lane == 0) y[r] = make_double2(ax, ay);
+      const double tot = warp_reduce_rows(acc, lane);
+      // lane group m = lane >> (5 - kRowsLog2V) holds value m = 2 (row - rb) + component
+      const int m = lane >> (5 - kRowsLog2V), r = rb + (m >> 1);
+      if ((lane & ((1 << (5 - kRowsLog2V)) - 1)) == 0 && r < H) reinterpret_cast<double*>(y)[2 * r + (m & 1)] = tot;
     }
 #pragma unroll
     for (int c = 0; c < NC; ++c) {

@@ -42,6 +42,28 @@ struct DevBuf {
   template <class T> T* as() const { return static_cast<T*>(ptr); }
 };
 
+// Page-locked host buffer owned by the library (grown on demand, freed with the problem);
+// the host tier of the two-level checkpoint schedule.
+struct HostBuf {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+  cudaError_t ensure(size_t nbytes) {
+    if (nbytes <= bytes) return cudaSuccess;
+    if (ptr) cudaFreeHost(ptr);
+    ptr = nullptr;
+    bytes = 0;
+    cudaError_t e = cudaHostAlloc(&ptr, nbytes, cudaHostAllocDefault);
+    if (e == cudaSuccess) bytes = nbytes;
+    return e;
+  }
+  void release() {
+    if (ptr) cudaFreeHost(ptr);
+    ptr = nullptr;
+    bytes = 0;
+  }
+  template <class T> T* as() const { return static_cast<T*>(ptr); }
+};
+
 struct Problem;
 
 // One equation set's implementation.  Every method runs asynchronously on prob->stream
@@ -115,6 +137,7 @@ struct Problem {
   bool pdl = false;          // programmatic dependent launch of consecutive kernels (spadj_set_option 6)
   bool fuse_columns = true;  // RB: fused fold + solve + expand cluster kernel (spadj_set_option 7)
   int x_rows = 0;            // x-FFT rows per CTA: 0 = tuned at creation, else 1, 2 or 4 (option 8)
+  int host_slots = 0;        // host checkpoint slots of the two-level schedule, 0 = device only (option 9)
   cudaEvent_t tic() {
     if (!timing.enabled) return nullptr;
     cudaEvent_t e = timing.get();

@@ -42,6 +42,7 @@ struct RB : EqImpl {
   // device work buffers
   DevBuf dG, Gb, Fg, df0, df1, dx1, vb2, vb1, xb1, tmpx, tmpy, ybar, ybar2, cur, nxt, curB, nxtB, partial, Jdev,
       seedbuf, slots, traj_tmp;
+  HostBuf hslots;  // host tier of the two-level checkpoint schedule
   // Buffers of one forward step.  Lane 0 runs the forward sweep and the adjoint steps, lane 1
   // the recomputation of checkpointed segments, concurrently on its own stream.
   struct WS {
@@ -863,7 +864,9 @@ struct RB : EqImpl {
     const size_t sb = sizeof(double2) * ns;
     SPADJ_CUDA_TRY(p, slots.ensure(sb * (size_t)S));
     CkptPlanner planner;
-    std::vector<CkptOp> ops = planner.plan(n_steps, S);
+    const int H = std::min(p->host_slots, n_steps);
+    std::vector<CkptOp> ops = H > 0 ? planner.plan2(n_steps, S, H) : planner.plan(n_steps, S);
+    if (H > 0) SPADJ_CUDA_TRY(p, hslots.ensure(sb * (size_t)H));
     StreamScope scope(this, p);
     SPADJ_CUDA_TRY(p, cudaEventRecord(evFree, p->stream));
     SPADJ_CUDA_TRY(p, cudaStreamWaitEvent(gsB, evFree, 0));
@@ -872,7 +875,10 @@ struct RB : EqImpl {
     int cur_step = 0;
     int recompute = 0;
     bool have_seed = false;
-    auto slot_ptr = [&](int sl) { return slots.as<char>() + (size_t)sl * sb; };
+    // device slots 0..S-1, host slots S..S+H-1
+    auto slot_ptr = [&](int sl) {
+      return sl < S ? slots.as<char>() + (size_t)sl * sb : hslots.as<char>() + (size_t)(sl - S) * sb;
+    };
     auto seed_ptr = [&](int n) -> const double2* {
       if (objective_kind >= 0 || n < 0 || n >= (int)seed_at.size() || seed_at[n] < 0) return nullptr;
       return reinterpret_cast<const double2*>(seeds) + (size_t)seed_at[n] * ns;
@@ -890,11 +896,13 @@ struct RB : EqImpl {
       spadj_status s = SPADJ_OK;
       switch (op.type) {
         case CK_STORE:
-          SPADJ_CUDA_TRY(p, cudaMemcpyAsync(slot_ptr(op.slot), SbB[ciB], sb, cudaMemcpyDeviceToDevice, gsB));
+          SPADJ_CUDA_TRY(p, cudaMemcpyAsync(slot_ptr(op.slot), SbB[ciB], sb,
+                                            op.slot < S ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, gsB));
           break;
         case CK_RESTORE:
           if (cur_step != op.a) {
-            SPADJ_CUDA_TRY(p, cudaMemcpyAsync(SbB[ciB], slot_ptr(op.slot), sb, cudaMemcpyDeviceToDevice, gsB));
+            SPADJ_CUDA_TRY(p, cudaMemcpyAsync(SbB[ciB], slot_ptr(op.slot), sb,
+                                              op.slot < S ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, gsB));
             cur_step = op.a;
           }
           break;
@@ -977,6 +985,7 @@ struct RB : EqImpl {
                       &vb2, &vb1, &xb1, &tmpx, &tmpy, &ybar, &ybar2, &cur, &nxt, &curB, &nxtB, &partial, &Jdev,
                       &seedbuf, &slots, &traj_tmp})
       b->release();
+    hslots.release();
   }
 };
 

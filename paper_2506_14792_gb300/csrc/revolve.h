@@ -8,7 +8,15 @@
 // the slot and reversing [a, m) with s slots; the split keeps the right part within
 // beta(s - 1, t) and the left part within beta(s, t - 1), t minimal for the segment.
 // Slot 0 holds the initial state.  Actions are executed in order by the caller.
+//
+// Two-level variant (plan2): besides the s device slots, h slots in host memory (the paper's
+// optimal-dynamo setup II keeps checkpoints in RAM and on disk, Supplementary Table on the
+// Taylor-remainder tests; H-revolve of Herrmann & Pallez).  The first forward sweep stores
+// X_a on the host at the start of every segment [a, a + K), K = ceil(N / h); the segments are
+// then reversed last first, each from its host copy by the binomial schedule on the device
+// slots.  Host slots are numbered s .. s + h - 1 in the actions.
 #pragma once
+#include <algorithm>
 #include <vector>
 
 namespace spadj {
@@ -81,16 +89,41 @@ struct CkptPlanner {
     rev(a, m, slot_a);
   }
 
-  // total_slots >= 1 (slot 0 = initial state).
-  std::vector<CkptOp> plan(int steps, int total_slots) {
+  // total_slots >= 1 (slot 0 = initial state).  with_objective = false: the caller supplies the
+  // cotangent of X_steps (a segment of a longer sweep), so no CK_OBJECTIVE is planned.
+  std::vector<CkptOp> plan(int steps, int total_slots, bool with_objective = true) {
     n_steps = steps;
     ops.clear();
     free_slots.clear();
-    objective_done = false;
+    objective_done = !with_objective;
     for (int sl = total_slots - 1; sl >= 1; --sl) free_slots.push_back(sl);
     ops.push_back({CK_STORE, 0, 0, 0});
     rev(0, steps, 0);
     return ops;
+  }
+
+  // Two-level schedule with total_slots device slots and host_slots >= 1 host slots.
+  std::vector<CkptOp> plan2(int steps, int total_slots, int host_slots) {
+    std::vector<CkptOp> out;
+    const int K = (steps + host_slots - 1) / host_slots;
+    const int nseg = (steps + K - 1) / K;
+    for (int j = 0; j < nseg; ++j) {
+      if (j > 0) out.push_back({CK_ADVANCE, (j - 1) * K, j * K, -1});
+      out.push_back({CK_STORE, j * K, 0, total_slots + j});
+    }
+    for (int j = nseg - 1; j >= 0; --j) {
+      const int a = j * K, b = std::min(steps, a + K);
+      out.push_back({CK_RESTORE, a, 0, total_slots + j});
+      CkptPlanner sub;
+      for (CkptOp o : sub.plan(b - a, std::min(total_slots, b - a + 1), b == steps)) {
+        o.a += a;
+        if (o.type == CK_ADVANCE) o.b += a;
+        out.push_back(o);
+      }
+      out.push_back({CK_FREE, a, 0, 0});
+      out.push_back({CK_FREE, a, 0, total_slots + j});
+    }
+    return out;
   }
 };
 

@@ -30,6 +30,8 @@ SPADJ_SHEAR_EVP = 4
 SPADJ_SBDF1 = 1
 SPADJ_SBDF2 = 2
 SPADJ_RK222 = 3
+SPADJ_SBDF3 = 4
+SPADJ_SBDF4 = 5
 
 SPADJ_OBJ_ENERGY = 0
 SPADJ_OBJ_FOURDVAR = 1
@@ -67,6 +69,8 @@ _SIGS = {
     "spadj_vjp": (ctypes.c_int, [_vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp]),
     "spadj_resolvent": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_int, _vp, _vp]),
     "spadj_hvp": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _vp]),
+    "spadj_checkpoint_schedule_host": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int,
+                                                      ctypes.POINTER(ctypes.c_int)]),
     "spadj_eigen": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, ctypes.c_int, _vp, _vp, _vp]),
     "spadj_set_observations": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, ctypes.c_int]),
     "spadj_set_option": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
@@ -122,12 +126,17 @@ def _as_f64(t, n, name):
     return t
 
 
-def checkpoint_schedule(n_steps, slots):
-    """Host-side binomial checkpoint schedule: list of (type, a, b, slot) actions."""
+def checkpoint_schedule(n_steps, slots, host_slots=0):
+    """Host-side binomial checkpoint schedule: list of (type, a, b, slot) actions; with
+    host_slots > 0 the two-level (device + host) schedule."""
     n = ctypes.c_int()
-    _chk(None, lib().spadj_checkpoint_schedule(n_steps, slots, None, 0, ctypes.byref(n)))
+    if host_slots:
+        call = lambda buf, m: lib().spadj_checkpoint_schedule_host(n_steps, slots, host_slots, buf, m, ctypes.byref(n))
+    else:
+        call = lambda buf, m: lib().spadj_checkpoint_schedule(n_steps, slots, buf, m, ctypes.byref(n))
+    _chk(None, call(None, 0))
     buf = (ctypes.c_int * (4 * n.value))()
-    _chk(None, lib().spadj_checkpoint_schedule(n_steps, slots, buf, n.value, ctypes.byref(n)))
+    _chk(None, call(buf, n.value))
     return [tuple(buf[4 * i:4 * i + 4]) for i in range(n.value)]
 
 

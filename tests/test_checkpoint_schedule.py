@@ -16,8 +16,8 @@ def _lib():
         build.build()
 
 
-def simulate(n, slots):
-    ops = spadj.checkpoint_schedule(n, slots)
+def simulate(n, slots, host_slots=0):
+    ops = spadj.checkpoint_schedule(n, slots, host_slots)
     store = {}
     cur = 0
     adjoint_order = []
@@ -26,7 +26,7 @@ def simulate(n, slots):
     for typ, a, b, sl in ops:
         if typ == spadj.CK_STORE:
             assert cur == a
-            assert 0 <= sl < min(slots, n + 1)
+            assert 0 <= sl < min(slots, n + 1) or slots <= sl < slots + host_slots
             assert sl not in store
             store[sl] = a
         elif typ == spadj.CK_RESTORE:
@@ -71,3 +71,28 @@ def test_schedule_valid_and_binomial(n, slots):
 def test_rejects_bad_arguments():
     with pytest.raises(spadj.SpadjError):
         spadj.checkpoint_schedule(0, 4)
+
+
+@pytest.mark.parametrize("n,slots,host", [(1, 1, 1), (7, 1, 3), (30, 2, 4), (200, 3, 10), (2000, 16, 40),
+                                          (2000, 4, 2000), (13, 100, 5)])
+def test_two_level_schedule(n, slots, host):
+    """Device + host schedule: valid (every step reversed once in order, objective first, no slot
+    reused before it is freed, host slots in their own range); the host holds one state per
+    segment, stored during the single first sweep; each segment is then reversed within the
+    binomial bound on the device slots."""
+    ops = spadj.checkpoint_schedule(n, slots, host)
+    K = -(-n // host)
+    nseg = -(-n // K)
+    host_stores = [a for typ, a, b, sl in ops if typ == spadj.CK_STORE and sl >= slots]
+    assert host_stores == [j * K for j in range(nseg)]
+    adv = simulate(n, slots, host)
+    s = min(slots, K + 1) - 1
+    first = (nseg - 1) * K
+    if s >= K:  # store-all inside each segment: L - 1 advances per segment, one more for the objective
+        assert adv == first + (n - nseg) + 1
+    else:
+        t = 1
+        while s > 0 and comb(s + t, s) < K:
+            t += 1
+        bound = K * (K + 1) // 2 if s == 0 else t * K + K
+        assert adv <= first + nseg * bound

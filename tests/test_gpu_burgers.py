@@ -85,6 +85,37 @@ def test_forward_tangent_adjoint(N, B, nsteps):
     assert rel_err(host(g), go) < TOL
 
 
+@pytest.mark.parametrize("order", [3, 4])
+@pytest.mark.parametrize("N,B,nsteps", [(16, 2, 9), (256, 3, 120), (512, 2, 40)])
+def test_higher_order_sbdf(order, N, B, nsteps):
+    """SBDF3 / SBDF4 (lower-order first steps): forward, tangent, adjoint and the gradient of
+    the energy against the oracle; the adjoint carries `order` pending cotangents."""
+    from paper_2506_14792_gb300 import spadj
+    dt = 1e-3
+    scheme = {3: spadj.SPADJ_SBDF3, 4: spadj.SPADJ_SBDF4}[order]
+    p = _problem(N, batch=B, dt=dt, scheme=scheme)
+    o = obur.Burgers(N, 0.01)
+    X0 = synthetic.burgers_ic(N, batch=B, seed=6)
+    dX0 = _adm(synthetic.random_coeffs((B, N // 2), seed=16))
+    traj = torch.zeros((nsteps + 1, B, N // 2), dtype=torch.complex128, device="cuda")
+    xN = torch.zeros((B, N // 2), dtype=torch.complex128, device="cuda")
+    p.forward(nsteps, dev(X0), xN, traj)
+    Xo = imex.multistep_forward(o, X0, nsteps, dt, order)
+    assert rel_err(host(traj), np.stack(Xo)) < TOL
+    dxN = torch.zeros_like(xN)
+    p.tangent(nsteps, dev(X0), dev(dX0), dxN)
+    assert rel_err(host(dxN), imex.multistep_tangent(o, Xo, dX0, dt, order)[-1]) < TOL
+    yN = _adm(synthetic.random_coeffs((B, N // 2), seed=17))
+    g = torch.zeros_like(xN)
+    p.adjoint(nsteps, traj, dev(yN), g)
+    go = imex.multistep_adjoint(o, Xo, lambda n: yN if n == nsteps else None, dt, order)
+    assert rel_err(host(g), go) < TOL
+    gr = torch.zeros_like(xN)
+    p.gradient(dev(X0), nsteps, gr)
+    want = imex.multistep_adjoint(o, Xo, lambda n: o.energy_grad(Xo[-1]) if n == nsteps else None, dt, order)
+    assert rel_err(host(gr), want) < TOL
+
+
 def test_gpu_dot_test():
     N, B, nsteps, dt = 256, 4, 300, 1e-3
     p = _problem(N, batch=B, dt=dt)

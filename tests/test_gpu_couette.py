@@ -19,10 +19,11 @@ SMALL = [(8, 4, 8), (16, 6, 12), (32, 8, 16)]
 RE, DT = 1000.0, 5e-3
 
 
-def gpu_problem(Nx, Ny, Nz, Re=RE, dt=DT, nonlinear=True, scheme=None):
+def gpu_problem(Nx, Ny, Nz, Re=RE, dt=DT, nonlinear=True, scheme=None, base="couette"):
     from paper_2506_14792_gb300 import spadj
     sch = spadj.SPADJ_SBDF2 if scheme is None else scheme
-    return spadj.Problem(spadj.SPADJ_COUETTE3D, sch, [Nx, Ny, Nz], [4 * np.pi, 2 * np.pi], [Re], dt,
+    b = {"couette": 0, "poiseuille": 1}[base]
+    return spadj.Problem(spadj.SPADJ_COUETTE3D, sch, [Nx, Ny, Nz], [4 * np.pi, 2 * np.pi], [Re, b], dt,
                          nonlinear=nonlinear)
 
 
@@ -184,6 +185,14 @@ def test_gain_gradient_and_checkpointing(traj_case):
         Jc = p.gradient(x0, n, gc, objective=spadj.SPADJ_OBJ_GAIN, ckpt_slots=slots)
         assert Jc[0] == Jg[0]
         assert torch.equal(gc, gr), slots
+    # two-level schedule: segment starts in page-locked host memory, device slots inside segments
+    for slots, hslots in ((2, 3), (1, 4), (3, 2)):
+        p.set_option(9, hslots)
+        gc = _zc(x0.shape)
+        Jc = p.gradient(x0, n, gc, objective=spadj.SPADJ_OBJ_GAIN, ckpt_slots=slots)
+        assert Jc[0] == Jg[0]
+        assert torch.equal(gc, gr), (slots, hslots)
+    p.set_option(9, 0)
 
 
 def test_energy_objective_and_vjp(traj_case):
@@ -316,7 +325,8 @@ def test_full_trajectory_dot_and_fd(full_case):
 
 
 
-def test_resolvent_gains_all_pencils():
+@pytest.mark.parametrize("base", ["couette", "poiseuille"])
+def test_resolvent_gains_all_pencils(base):
     """Energy-norm resolvent gains of every (kx, ky) pencil from the batched power iteration
     (forward and transposed pencil solves) against the oracle's dense generalised eigenproblem.
     Where the power iteration has converged ((lambda_next / lambda_1)^n_iter < 1e-20 by the
@@ -325,9 +335,9 @@ def test_resolvent_gains_all_pencils():
     Rayleigh quotient is."""
     import scipy.linalg as sla
     Nx, Ny, Nz, Re, n_iter = 8, 4, 16, 300.0, 120
-    o = oco.Couette(Nx, Ny, Nz, Re, pencils=False)
+    o = oco.Couette(Nx, Ny, Nz, Re, pencils=False, base=base)
     G3 = sla.block_diag(o.G, o.G, o.G)
-    p = gpu_problem(Nx, Ny, Nz, Re=Re)
+    p = gpu_problem(Nx, Ny, Nz, Re=Re, base=base)
     for om in (0.0, 0.3):
         f = dev(to_gpu(synthetic.random_coeffs((3, o.Kx, o.Ny, o.N), seed=61)))
         gains = torch.zeros((Ny, Nx // 2), dtype=torch.float64, device="cuda")
@@ -360,3 +370,22 @@ def test_hessian_vector_product(traj_case):
     hv = _zc(to_gpu(u0).shape)
     p.hvp(dev(to_gpu(u0)), dev(to_gpu(v)), n, hv)
     assert rel_err(to_oracle(host(hv)), o.state(want)) < TOL
+
+
+def test_channel_flow_gain_gradient():
+    """Plane Poiseuille (channel) profile: the SBDF2 gain gradient through the GPU path, store-all
+    and checkpointed, against the oracle's."""
+    from paper_2506_14792_gb300 import spadj
+    Nx, Ny, Nz, n = 16, 6, 12, 10
+    o = oco.Couette(Nx, Ny, Nz, RE, base="poiseuille")
+    u0 = synthetic.couette_ic(Nx, Ny, Nz, seed=7, norm=0.05)
+    J, g, X = oco.gain_gradient(o, o.pencils(u0), n, DT)
+    p = gpu_problem(Nx, Ny, Nz, base="poiseuille")
+    x0 = dev(to_gpu(u0))
+    gr = _zc(x0.shape)
+    Jg = p.gradient(x0, n, gr, objective=spadj.SPADJ_OBJ_GAIN, ckpt_slots=0)
+    assert abs(Jg[0] - J) < TOL * abs(J)
+    assert rel_err(to_oracle(host(gr)), o.state(g)) < TOL
+    gc = _zc(x0.shape)
+    p.gradient(x0, n, gc, objective=spadj.SPADJ_OBJ_GAIN, ckpt_slots=3)
+    assert torch.equal(gc, gr)

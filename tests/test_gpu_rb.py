@@ -120,6 +120,28 @@ def test_checkpointed_gradient(small_case, slots):
     assert torch.equal(gr, ref)  # recomputation is bitwise identical to store-all
 
 
+@pytest.mark.parametrize("slots,hslots", [(2, 3), (1, 5), (4, 2), (3, 40)])
+def test_two_level_checkpointing(small_case, slots, hslots):
+    """Device slots plus host slots (the two-level schedule): gradient and a seeded VJP equal
+    the store-all sweep bitwise."""
+    o, s0, J, g, X, stages, dt, nsteps = small_case
+    p = gpu_problem(o.Nx, o.Nz, dt=dt)
+    ref = _z((3, o.Kx, o.N))
+    Jr = p.gradient(dev(s0), nsteps, ref, ckpt_slots=0)
+    p.set_option(9, hslots)
+    gr = _z((3, o.Kx, o.N))
+    Jg = p.gradient(dev(s0), nsteps, gr, ckpt_slots=slots)
+    assert Jg[0] == Jr[0] and torch.equal(gr, ref)
+    steps = [0, nsteps // 2, nsteps]
+    seeds = dev(np.stack([_rand_state(o, 50 + i) for i in range(3)]))
+    v_host = _z((3, o.Kx, o.N))
+    p.vjp(dev(s0), nsteps, steps, seeds, v_host, ckpt_slots=slots)
+    p.set_option(9, 0)
+    v_ref = _z((3, o.Kx, o.N))
+    p.vjp(dev(s0), nsteps, steps, seeds, v_ref, ckpt_slots=0)
+    assert torch.equal(v_host, v_ref)
+
+
 def test_gpu_dot_test(small_case):
     o, s0, J, g, X, stages, dt, nsteps = small_case
     p = gpu_problem(o.Nx, o.Nz, dt=dt)

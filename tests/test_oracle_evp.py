@@ -142,3 +142,14 @@ def test_shift_invert_spectrum():
     want = 1.0 / (sigma - lam)
     assert np.min(np.abs(mu - want)) <= 1e-9 * abs(want)
     assert np.argmax(np.abs(mu)) == np.argmin(np.abs(mu - want))
+
+
+def test_channel_pencils_of_the_3d_problem():
+    """The 3D problem's channel option assembles the Poiseuille pencils pinned above."""
+    o = co.Couette(8, 4, 20, 2000.0, base="poiseuille")
+    e = ShearEVP(20, "poiseuille")
+    for m, j in ((1, 0), (1, 1), (3, 2), (0, 1)):
+        Mo, Lo = o.pencil_matrices(o.alpha[m], o.beta[j])
+        Me, Le = e.matrices(o.alpha[m], o.beta[j], 2000.0)
+        np.testing.assert_allclose(Lo, Le, rtol=0, atol=1e-14)
+        np.testing.assert_array_equal(Mo, Me)
