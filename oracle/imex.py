@@ -99,6 +99,23 @@ def rk222_tableaux():
     return A, H
 
 
+def rk443_tableaux():
+    """ARS(4,4,3) (Ascher, Ruuth & Spiteri 1997, the Runge-Kutta IMEX family the paper's
+    timesteppers follow): explicit tableau A[i][j] and implicit tableau H[i][j] (i, j = 0..4),
+    third order, diagonal 1/2 on every implicit stage and a zero first implicit column."""
+    A = np.zeros((5, 5))
+    H = np.zeros((5, 5))
+    A[1, 0] = 1.0 / 2.0
+    A[2, 0], A[2, 1] = 11.0 / 18.0, 1.0 / 18.0
+    A[3, 0], A[3, 1], A[3, 2] = 5.0 / 6.0, -5.0 / 6.0, 1.0 / 2.0
+    A[4, 0], A[4, 1], A[4, 2], A[4, 3] = 1.0 / 4.0, 7.0 / 4.0, 3.0 / 4.0, -7.0 / 4.0
+    H[1, 1] = 1.0 / 2.0
+    H[2, 1], H[2, 2] = 1.0 / 6.0, 1.0 / 2.0
+    H[3, 1], H[3, 2], H[3, 3] = -1.0 / 2.0, 1.0 / 2.0, 1.0 / 2.0
+    H[4, 1], H[4, 2], H[4, 3], H[4, 4] = 3.0 / 2.0, -3.0 / 2.0, 1.0 / 2.0, 1.0 / 2.0
+    return A, H
+
+
 # --------------------------------------------------------------------------------------
 # Multistep IMEX (eq. imex and eq. IMEX_adjoint)
 # --------------------------------------------------------------------------------------

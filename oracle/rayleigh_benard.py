@@ -275,10 +275,11 @@ class RayleighBenard:
         return x, z
 
 
-def gradient(prob, X0, nsteps, dt):
-    """Kinetic energy at T and its gradient w.r.t. X_0 by the RK222 adjoint (store-all)."""
+def gradient(prob, X0, nsteps, dt, tableaux=None):
+    """Kinetic energy at T and its gradient w.r.t. X_0 by the RK IMEX adjoint (store-all);
+    ARS(2,2,2) unless other (A, H) tableaux are given."""
     from . import imex
-    A, H = imex.rk222_tableaux()
+    A, H = imex.rk222_tableaux() if tableaux is None else tableaux
     X, stages = imex.rk_forward(prob, X0, nsteps, dt, A, H)
     J = prob.kinetic_energy(X[-1])
     dJ = lambda n: prob.kinetic_energy_grad(X[n]) if n == nsteps else None
