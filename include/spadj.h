@@ -58,7 +58,7 @@ typedef enum {
  *   (N = n[1] modes) with tau terms; equations projected on the ultraspherical C^(2)
  *   (momentum, temperature) and C^(1) (continuity) bases, no-slip, fixed temperature
  *   (Sparse spectral methods section).  params[0] = Ra, params[1] = Pr (nu = (Ra/Pr)^-1/2,
- *   kappa = (Ra Pr)^-1/2).  Scheme RK222.  State: u, w, theta coefficients, layout
+ *   kappa = (Ra Pr)^-1/2).  Scheme RK222 (or RK443).  State: u, w, theta coefficients, layout
  *   [3][Nx/2][N] complex (x-mode m = 0..Nx/2-1, Nyquist not stored; the m = 0 pencil is
  *   held real).  Grid layout [3N/2][3Nx/2] real (Gauss-Chebyshev z rows, uniform x).
  *   Pressure and tau variables are internal to the stage solves.
@@ -110,7 +110,8 @@ typedef enum {
   SPADJ_SBDF2 = 2, /* multistep IMEX, eq. imex, second order (SBDF1 first step) */
   SPADJ_RK222 = 3, /* Runge-Kutta IMEX ARS(2,2,2), Supplementary A.4 stage equation */
   SPADJ_SBDF3 = 4, /* multistep IMEX, third order (SPADJ_BURGERS1D; SBDF1, SBDF2 first steps) */
-  SPADJ_SBDF4 = 5  /* multistep IMEX, fourth order (SPADJ_BURGERS1D; SBDF1..3 first steps) */
+  SPADJ_SBDF4 = 5, /* multistep IMEX, fourth order (SPADJ_BURGERS1D; SBDF1..3 first steps) */
+  SPADJ_RK443 = 6  /* Runge-Kutta IMEX ARS(4,4,3), third order (SPADJ_RB2D; separate kernels) */
 } spadj_scheme;
 
 typedef struct {

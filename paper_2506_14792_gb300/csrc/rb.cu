@@ -32,6 +32,11 @@ struct RB : EqImpl {
   int Nx = 0, Kx = 0, N = 0, Mx = 0, Mz = 0, L = 0;
   double Lx = 4.0, nu = 0, kappa = 0, dt = 0, Ra = 0, Pr = 1;
   double A10, A20, A21, H21, gam, cc;
+  // generic Runge-Kutta IMEX path (ARS(4,4,3)): S implicit stages, tableaux tA (explicit) and
+  // tH (implicit, diagonal gam, zero first column)
+  bool generic = false;
+  int S = 2;
+  double tA[5][5] = {}, tH[5][5] = {};
   int nonlinear = 1;
   size_t ns = 0;    // complex entries of one state [3][Kx][N]
   size_t nmix = 0;  // complex entries of one mixed array [Mz][Kx]
@@ -47,7 +52,10 @@ struct RB : EqImpl {
   // the recomputation of checkpointed segments, concurrently on its own stream.
   struct WS {
     DevBuf Z, Y, G0, G1, f0, f1, x1;
+    DevBuf rx[4], rv[4], rf[4];  // generic scheme: stage values x_i, pre-solve vectors v_i, F(x_{i-1})
   };
+  // generic scheme, lane 0: tangent stages and adjoint cotangents
+  DevBuf tdx[4], tdv[4], tdf[4], axb[4], avb[4], afb[4], aacc, atmp, axs;
   WS ws[2];
   WS* w = &ws[0];
   size_t zsmem = 0, xsmem = 0, ssmem = 0, csmem = 0, ctsmem = 0;
@@ -82,7 +90,9 @@ struct RB : EqImpl {
     N = d.n[1];
     if (Nx < 4 || Nx % 4 != 0 || N < 8 || N % 4 != 0)
       return p->fail(SPADJ_ERR_INVALID, "rb: n[0] must be a multiple of 4 (>= 4) and n[1] a multiple of 4 (>= 8)");
-    if (d.scheme != SPADJ_RK222) return p->fail(SPADJ_ERR_UNSUPPORTED, "rb: scheme must be RK222");
+    if (d.scheme != SPADJ_RK222 && d.scheme != SPADJ_RK443)
+      return p->fail(SPADJ_ERR_UNSUPPORTED, "rb: scheme must be RK222 or RK443");
+    generic = d.scheme == SPADJ_RK443;
     if (d.batch != 1) return p->fail(SPADJ_ERR_UNSUPPORTED, "rb: batch must be 1 (one problem per handle)");
     Kx = Nx / 2;
     Mx = 3 * Nx / 2;
@@ -101,6 +111,22 @@ struct RB : EqImpl {
     const double del = 1.0 - 1.0 / (2.0 * gam);
     A10 = gam; A20 = del; A21 = 1.0 - del; H21 = 1.0 - gam;
     cc = H21 / gam;
+    if (generic) {  // ARS(4,4,3), Ascher, Ruuth & Spiteri (1997)
+      S = 4;
+      gam = 0.5;
+      const double a[5][5] = {{0, 0, 0, 0, 0},
+                              {1.0 / 2.0, 0, 0, 0, 0},
+                              {11.0 / 18.0, 1.0 / 18.0, 0, 0, 0},
+                              {5.0 / 6.0, -5.0 / 6.0, 1.0 / 2.0, 0, 0},
+                              {1.0 / 4.0, 7.0 / 4.0, 3.0 / 4.0, -7.0 / 4.0, 0}};
+      const double h[5][5] = {{0, 0, 0, 0, 0},
+                              {0, 1.0 / 2.0, 0, 0, 0},
+                              {0, 1.0 / 6.0, 1.0 / 2.0, 0, 0},
+                              {0, -1.0 / 2.0, 1.0 / 2.0, 1.0 / 2.0, 0},
+                              {0, 3.0 / 2.0, -3.0 / 2.0, 1.0 / 2.0, 1.0 / 2.0}};
+      for (int i = 0; i < 5; ++i)
+        for (int j = 0; j < 5; ++j) { tA[i][j] = a[i][j]; tH[i][j] = h[i][j]; }
+    }
     ns = (size_t)3 * Kx * N;
     nmix = (size_t)Mz * Kx;
     npts = (size_t)Mz * Mx;
@@ -174,6 +200,14 @@ struct RB : EqImpl {
       SPADJ_CUDA_TRY(p, l.G1.ensure(8 * gb));
       for (DevBuf* b : {&l.f0, &l.f1, &l.x1}) SPADJ_CUDA_TRY(p, b->ensure(sb));
     }
+    if (generic) {
+      for (WS& l : ws)
+        for (int i = 0; i < 4; ++i)
+          for (DevBuf* b : {&l.rx[i], &l.rv[i], &l.rf[i]}) SPADJ_CUDA_TRY(p, b->ensure(sb));
+      for (int i = 0; i < 4; ++i)
+        for (DevBuf* b : {&tdx[i], &tdv[i], &tdf[i], &axb[i], &avb[i], &afb[i]}) SPADJ_CUDA_TRY(p, b->ensure(sb));
+      for (DevBuf* b : {&aacc, &atmp, &axs}) SPADJ_CUDA_TRY(p, b->ensure(sb));
+    }
     SPADJ_CUDA_TRY(p, dG.ensure(8 * gb));
     SPADJ_CUDA_TRY(p, Gb.ensure(8 * gb));
     SPADJ_CUDA_TRY(p, Fg.ensure(3 * gb));
@@ -195,7 +229,7 @@ struct RB : EqImpl {
     ssmem = sizeof(double2) * (H + 4 * solve_rows(H)) + sizeof(double) * (size_t)H * solve_rows(H);
     csmem = colstep_smem(N, Mz);
     ctsmem = colstepT_smem(N, Mz);
-    fused = nonlinear && std::max(csmem, ctsmem) <= 200 * 1024;
+    fused = nonlinear && !generic && std::max(csmem, ctsmem) <= 200 * 1024;
     if (fused) {
       SPADJ_CUDA_TRY(p, cudaFuncSetAttribute(rb_colstep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csmem));
       SPADJ_CUDA_TRY(p, cudaFuncSetAttribute(rb_colstepT_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ctsmem));
@@ -517,10 +551,141 @@ struct RB : EqImpl {
     return c2r_fields(p, w->G1);
   }
 
+  // ---- generic Runge-Kutta IMEX steps (separate kernels) ---------------------------------------
+  // Stage i = 1..S of the stage equation (M + dt gam L) X_i = M X_0 + dt sum_{j<i} (A_ij F_j -
+  // H_ij L X_j) in prognostic form: dt gam L X_j = S1S0 (v_j - x_j) for the solved stages (the
+  // first implicit column is zero), so
+  //   v_i = x_0 + sum_{j<i} dt A_ij f_j - sum_{1<=j<i} (H_ij / gam)(v_j - x_j),  x_i = Phi v_i,
+  //   f_i = F(x_i) (i < S),  X_{n+1} = x_S.
+
+  // out = sum_t a_t in_t (n >= 1); in[0] may be out itself (accumulation)
+  spadj_status lincomb(Problem* p, double2* out, int n, const double2* const* in, const double* a) {
+    int t = 0;
+    bool first = true;
+    while (first || t < n) {
+      const double2* x0 = out;
+      double a0 = 1.0;
+      if (first) { x0 = in[0]; a0 = a[0]; t = 1; }
+      const double2* x1 = nullptr;
+      const double2* x2 = nullptr;
+      double a1 = 0.0, a2 = 0.0;
+      if (t < n) { x1 = in[t]; a1 = a[t]; ++t; }
+      if (t < n) { x2 = in[t]; a2 = a[t]; ++t; }
+      cudaEvent_t ev = p->tic();
+      axpy_kernel<<<64, 256, 0, p->stream>>>(out, x0, a0, x1, a1, x2, a2, ns);
+      p->toc(ev, KC_POINTWISE, 4.0 * (double)ns);
+      spadj_status s = check_launch(p, "rb combine");
+      if (s != SPADJ_OK) return s;
+      first = false;
+    }
+    return SPADJ_OK;
+  }
+
+  // stage vectors of lane w: x_i (i >= 1), v_i (i >= 1), f_j (j >= 0)
+  double2* gx(int i) { return st(w->rx[i - 1]); }
+  double2* gv(int i) { return st(w->rv[i - 1]); }
+  double2* gf(int j) { return st(w->rf[j]); }
+
+  // terms of v_i (pointers, weights) over x_0, f_j and (v_j, x_j); the tangent's stage vectors
+  // (dx_0, df_j, dv_j, dx_j) when tangent
+  int stage_terms(int i, const double2* x0, const double2** in, double* a, bool tangent) {
+    int n = 0;
+    in[n] = x0; a[n++] = 1.0;
+    for (int j = 0; j < i; ++j)
+      if (tA[i][j] != 0.0) { in[n] = tangent ? st(tdf[j]) : gf(j); a[n++] = dt * tA[i][j]; }
+    for (int j = 1; j < i; ++j) {
+      const double h = tH[i][j] / gam;
+      if (h == 0.0) continue;
+      in[n] = tangent ? st(tdv[j - 1]) : gv(j); a[n++] = -h;
+      in[n] = tangent ? st(tdx[j - 1]) : gx(j); a[n++] = h;
+    }
+    return n;
+  }
+
+  // one step x0 -> x_out (and its tangent dx0 -> dx_out when dx0 is non-null)
+  spadj_status gen_step(Problem* p, const double2* x0, const double2* dx0, double2* x_out, double2* dx_out) {
+    spadj_status s;
+    const double one[1] = {1.0};
+    if ((s = evalF(p, x0, gf(0), w->G0)) != SPADJ_OK) return s;
+    if (dx0 && (s = evalJvp(p, w->G0, dx0, st(tdf[0]))) != SPADJ_OK) return s;
+    for (int i = 1; i <= S; ++i) {
+      const double2* in[16];
+      double a[16];
+      int n = stage_terms(i, x0, in, a, false);
+      if ((s = lincomb(p, gv(i), n, in, a)) != SPADJ_OK) return s;
+      double2* xi = i == S ? x_out : gx(i);
+      { const double2* v[1] = {gv(i)};
+        if ((s = solve(p, 0, 1, v, one, xi)) != SPADJ_OK) return s; }
+      if (dx0) {
+        n = stage_terms(i, dx0, in, a, true);
+        if ((s = lincomb(p, st(tdv[i - 1]), n, in, a)) != SPADJ_OK) return s;
+        double2* dxi = i == S ? dx_out : st(tdx[i - 1]);
+        const double2* v[1] = {st(tdv[i - 1])};
+        if ((s = solve(p, 0, 1, v, one, dxi)) != SPADJ_OK) return s;
+      }
+      if (i < S) {
+        if ((s = evalF(p, xi, gf(i), w->G0)) != SPADJ_OK) return s;
+        if (dx0 && (s = evalJvp(p, w->G0, st(tdx[i - 1]), st(tdf[i]))) != SPADJ_OK) return s;
+      }
+    }
+    return SPADJ_OK;
+  }
+
+  // exact reverse of gen_step: xb_in = cotangent of X_{n+1} -> xb0 = cotangent of X_n
+  spadj_status gen_step_adj(Problem* p, const double2* x0, const double2* xb_in, double2* xb0) {
+    spadj_status s;
+    if ((s = gen_step(p, x0, nullptr, st(axs), nullptr)) != SPADJ_OK) return s;  // stage values
+    const size_t sb = sizeof(double2) * ns;
+    for (int i = 0; i < S; ++i) {
+      SPADJ_CUDA_TRY(p, cudaMemsetAsync(afb[i].ptr, 0, sb, p->stream));  // fbar_0..fbar_{S-1}
+      SPADJ_CUDA_TRY(p, cudaMemsetAsync(axb[i].ptr, 0, sb, p->stream));  // xbar_1..xbar_{S-1}
+      SPADJ_CUDA_TRY(p, cudaMemsetAsync(avb[i].ptr, 0, sb, p->stream));  // vbar_1..vbar_S
+    }
+    SPADJ_CUDA_TRY(p, cudaMemsetAsync(aacc.ptr, 0, sb, p->stream));
+    const double one[1] = {1.0};
+    for (int i = S; i >= 1; --i) {
+      double2* xbi = i == S ? const_cast<double2*>(xb_in) : st(axb[i - 1]);
+      if (i < S && nonlinear) {  // xbar_i += (dF/dx)(x_i)^H fbar_i
+        if ((s = c2g_fields(p, gx(i), w->G0)) != SPADJ_OK) return s;
+        const double2* fb[1] = {st(afb[i])};
+        const double2* ad[1] = {xbi};
+        if ((s = evalVjp(p, w->G0, 1, fb, one, 1, ad, one, xbi)) != SPADJ_OK) return s;
+      }
+      double2* vbi = st(avb[i - 1]);
+      { const double2* v[1] = {xbi};  // vbar_i += Phi^H xbar_i
+        if ((s = solve(p, 1, 1, v, one, st(atmp))) != SPADJ_OK) return s; }
+      { const double2* in[2] = {vbi, st(atmp)}; const double a[2] = {1.0, 1.0};
+        if ((s = lincomb(p, vbi, 2, in, a)) != SPADJ_OK) return s; }
+      // v_i = x_0 + sum_j dt A_ij f_j - sum_j h_ij (v_j - x_j): distribute vbar_i
+      { const double2* in[2] = {st(aacc), vbi}; const double a[2] = {1.0, 1.0};
+        if ((s = lincomb(p, st(aacc), 2, in, a)) != SPADJ_OK) return s; }
+      for (int j = 0; j < i; ++j)
+        if (tA[i][j] != 0.0) {
+          const double2* in[2] = {st(afb[j]), vbi};
+          const double a[2] = {1.0, dt * tA[i][j]};
+          if ((s = lincomb(p, st(afb[j]), 2, in, a)) != SPADJ_OK) return s;
+        }
+      for (int j = 1; j < i; ++j) {
+        const double h = tH[i][j] / gam;
+        if (h == 0.0) continue;
+        { const double2* in[2] = {st(avb[j - 1]), vbi}; const double a[2] = {1.0, -h};
+          if ((s = lincomb(p, st(avb[j - 1]), 2, in, a)) != SPADJ_OK) return s; }
+        { const double2* in[2] = {st(axb[j - 1]), vbi}; const double a[2] = {1.0, h};
+          if ((s = lincomb(p, st(axb[j - 1]), 2, in, a)) != SPADJ_OK) return s; }
+      }
+    }
+    // xbar_0 = acc + (dF/dx)(x_0)^H fbar_0
+    if (nonlinear && (s = c2g_fields(p, x0, w->G0)) != SPADJ_OK) return s;
+    const double2* fb[1] = {st(afb[0])};
+    const double2* ad[1] = {st(aacc)};
+    return evalVjp(p, w->G0, 1, fb, one, 1, ad, one, xb0);
+  }
+
   // ---- RK222 steps ---------------------------------------------------------------------------
   bool use_fused(Problem* p) const { return fused && p->fuse_columns; }
 
   spadj_status step_fwd(Problem* p, const double2* x0, double2* x2) {
+    if (generic) return gen_step(p, x0, nullptr, x2, nullptr);
     if (use_fused(p)) {
       spadj_status s = stage1_fused(p, x0);
       if (s != SPADJ_OK) return s;
@@ -540,6 +705,7 @@ struct RB : EqImpl {
   }
 
   spadj_status step_tan(Problem* p, const double2* x0, const double2* dx0, double2* x2, double2* dx2) {
+    if (generic) return gen_step(p, x0, dx0, x2, dx2);
     spadj_status s;
     if ((s = evalF(p, x0, st(w->f0), w->G0)) != SPADJ_OK) return s;
     if ((s = evalJvp(p, w->G0, dx0, st(df0))) != SPADJ_OK) return s;
@@ -558,6 +724,7 @@ struct RB : EqImpl {
 
   // xb0 = cotangent of X_n from xb2 = cotangent of X_{n+1}, primal x0 = X_n.
   spadj_status step_adj(Problem* p, const double2* x0, const double2* xb2, double2* xb0) {
+    if (generic) return gen_step_adj(p, x0, xb2, xb0);
     spadj_status s;
     // the transposed stage-2 solve does not depend on the stage recomputation: it runs on the
     // second internal stream and overlaps it
@@ -979,8 +1146,14 @@ struct RB : EqImpl {
       if (e) cudaEventDestroy(e);
     for (cudaStream_t st : {gs, gs2, gsB})
       if (st) cudaStreamDestroy(st);
-    for (WS& l : ws)
+    for (WS& l : ws) {
       for (DevBuf* b : {&l.Z, &l.Y, &l.G0, &l.G1, &l.f0, &l.f1, &l.x1}) b->release();
+      for (int i = 0; i < 4; ++i)
+        for (DevBuf* b : {&l.rx[i], &l.rv[i], &l.rf[i]}) b->release();
+    }
+    for (int i = 0; i < 4; ++i)
+      for (DevBuf* b : {&tdx[i], &tdv[i], &tdf[i], &axb[i], &avb[i], &afb[i]}) b->release();
+    for (DevBuf* b : {&aacc, &atmp, &axs}) b->release();
     for (DevBuf* b : {&wm, &czE, &cdzE, &gzF, &gzTE, &czTF, &cdzTF, &gmat, &phi, &phiT, &dG, &Gb, &Fg, &df0, &df1, &dx1,
                       &vb2, &vb1, &xb1, &tmpx, &tmpy, &ybar, &ybar2, &cur, &nxt, &curB, &nxtB, &partial, &Jdev,
                       &seedbuf, &slots, &traj_tmp})

@@ -32,6 +32,7 @@ SPADJ_SBDF2 = 2
 SPADJ_RK222 = 3
 SPADJ_SBDF3 = 4
 SPADJ_SBDF4 = 5
+SPADJ_RK443 = 6
 
 SPADJ_OBJ_ENERGY = 0
 SPADJ_OBJ_FOURDVAR = 1

@@ -2,9 +2,10 @@
 import numpy as np
 
 
-def gpu_problem(Nx, Nz, Ra=1e6, Pr=1.0, dt=1e-3, nonlinear=True, Lx=4.0):
+def gpu_problem(Nx, Nz, Ra=1e6, Pr=1.0, dt=1e-3, nonlinear=True, Lx=4.0, scheme=None):
     from paper_2506_14792_gb300 import spadj
-    return spadj.Problem(spadj.SPADJ_RB2D, spadj.SPADJ_RK222, [Nx, Nz], [Lx], [Ra, Pr], dt, nonlinear=nonlinear)
+    sch = spadj.SPADJ_RK222 if scheme is None else scheme
+    return spadj.Problem(spadj.SPADJ_RB2D, sch, [Nx, Nz], [Lx], [Ra, Pr], dt, nonlinear=nonlinear)
 
 
 def F_T(o, X):

@@ -107,6 +107,36 @@ def test_forward_tangent_adjoint_trajectories(small_case):
     assert rel_err(host(gr), o.state(g)) < TOL
 
 
+@pytest.mark.parametrize("Nx,Nz,nonlinear", [(16, 12, True), (32, 16, True), (16, 12, False)])
+def test_rk443_forward_tangent_adjoint_gradient(Nx, Nz, nonlinear):
+    """ARS(4,4,3) on the separate kernels: trajectory, tangent, adjoint over the stored trajectory
+    and the checkpointed gradient against the oracle's RK stage equation and its adjoint."""
+    from paper_2506_14792_gb300 import spadj
+    dt, nsteps = 1e-2, 10
+    o = orb.RayleighBenard(Nx, Nz, 1e6, nonlinear=nonlinear)
+    s0 = synthetic.rb_ic(Nx, Nz, seed=2, amp=0.3)
+    tab = imex.rk443_tableaux()
+    J, g, X, stages = orb.gradient(o, o.pencils(s0), nsteps, dt, tab)
+    p = gpu_problem(Nx, Nz, dt=dt, scheme=spadj.SPADJ_RK443, nonlinear=nonlinear)
+    traj = _z((nsteps + 1, 3, o.Kx, o.N))
+    xN = _z((3, o.Kx, o.N))
+    p.forward(nsteps, dev(s0), xN, traj)
+    assert rel_err(host(traj), np.stack([o.state(x) for x in X])) < TOL
+    d0 = synthetic.rb_ic(Nx, Nz, seed=7, amp=1.0)
+    dxN = _z((3, o.Kx, o.N))
+    p.tangent(nsteps, dev(s0), dev(d0), dxN)
+    dX = imex.rk_tangent(o, stages, o.pencils(d0), dt, *tab)
+    assert rel_err(host(dxN), o.state(dX[-1])) < TOL
+    yN = o.state(o.kinetic_energy_grad(X[-1]))
+    gr = _z((3, o.Kx, o.N))
+    p.adjoint(nsteps, traj, dev(yN), gr)
+    assert rel_err(host(gr), o.state(g)) < TOL
+    gc = _z((3, o.Kx, o.N))
+    Jg = p.gradient(dev(s0), nsteps, gc, ckpt_slots=3)
+    assert abs(Jg[0] - J) <= TOL * abs(J)
+    assert rel_err(host(gc), o.state(g)) < TOL
+
+
 @pytest.mark.parametrize("slots", [0, 2, 5, 31])
 def test_checkpointed_gradient(small_case, slots):
     o, s0, J, g, X, stages, dt, nsteps = small_case
