@@ -46,6 +46,9 @@ TRAFFIC = {
     # of the gradient (484 : 200 : 200 : 380); the working set is L2-resident, so this is the
     # cold-cache fill ncu sees after its cache flush
     ("rayleigh_benard2d_256x64_Ra1e6_rk222_2000steps", "x_fft"): 1.67e6,
+    # evp_iter_kernel, full bench launch (608 pencils, 100 iterations): 32.07 GB read + 7.4 MB
+    # written, against 35.9 GB of operator rows streamed by the algorithm (the rest hits in L2)
+    ("poiseuille_evp_N64_608pencils_Re8000_100iter", "pencil_solve"): 3.2075e10,
 }
 
 
