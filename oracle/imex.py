@@ -186,6 +186,12 @@ def multistep_adjoint(prob, X, dJ, dt, order=2):
 # Runge-Kutta IMEX (Supplementary A.4, RK stage equation and its adjoint)
 # --------------------------------------------------------------------------------------
 
+def _dt_of(dt, n):
+    """Step size of step n: dt is a scalar (constant step) or a sequence (one per step; the
+    stage operators M + dt H_ii L change with it and are factorised per distinct value)."""
+    return float(dt[n]) if np.ndim(dt) else float(dt)
+
+
 def rk_step(prob, Xn, dt, A, H):
     """One RK IMEX step; returns the list of stage values [X_{n,0}, ..., X_{n,s}]."""
     s = A.shape[0] - 1
@@ -207,8 +213,8 @@ def rk_forward(prob, X0, nsteps, dt, A, H):
     """Forward trajectory; returns (states [X_0..X_N], stages per step)."""
     X = [X0]
     stages = []
-    for _ in range(nsteps):
-        st = rk_step(prob, X[-1], dt, A, H)
+    for n in range(nsteps):
+        st = rk_step(prob, X[-1], _dt_of(dt, n), A, H)
         stages.append(st)
         X.append(st[-1])
     return X, stages
@@ -218,14 +224,15 @@ def rk_tangent(prob, stages, dX0, dt, A, H):
     """Tangent trajectory [dX_0, ..., dX_N] along recorded RK stages."""
     s = A.shape[0] - 1
     dX = [dX0]
-    for st in stages:
+    for n, st in enumerate(stages):
+        dt_n = _dt_of(dt, n)
         dst = [dX[-1]]
         MdX0 = prob.M(dX[-1])
         for i in range(1, s + 1):
             R = MdX0
             for j in range(i):
-                R = R + dt * (A[i, j] * prob.F_jvp(st[j], dst[j]) - H[i, j] * prob.L(dst[j]))
-            dst.append(prob.project(prob.solve(1.0, dt * H[i, i], R)))
+                R = R + dt_n * (A[i, j] * prob.F_jvp(st[j], dst[j]) - H[i, j] * prob.L(dst[j]))
+            dst.append(prob.project(prob.solve(1.0, dt_n * H[i, i], R)))
         dX.append(dst[-1])
     return dX
 
@@ -245,16 +252,17 @@ def rk_adjoint(prob, stages, dJ, dt, A, H):
     Ybar = 0 * stages[-1][-1] if Ybar is None else Ybar
     for n in range(nsteps - 1, -1, -1):
         st = stages[n]
+        dt_n = _dt_of(dt, n)
         Y = [None] * (s + 1)
-        Y[s] = prob.solve_t(1.0, dt * H[s, s], prob.project(Ybar))
+        Y[s] = prob.solve_t(1.0, dt_n * H[s, s], prob.project(Ybar))
         for i in range(s - 1, 0, -1):
             rhs = 0
             for j in range(i + 1, s + 1):
-                rhs = rhs + dt * (A[j, i] * prob.F_vjp(st[i], Y[j]) - H[j, i] * prob.Lt(Y[j]))
-            Y[i] = prob.solve_t(1.0, dt * H[i, i], prob.project(rhs))
+                rhs = rhs + dt_n * (A[j, i] * prob.F_vjp(st[i], Y[j]) - H[j, i] * prob.Lt(Y[j]))
+            Y[i] = prob.solve_t(1.0, dt_n * H[i, i], prob.project(rhs))
         lam = 0
         for j in range(1, s + 1):
-            lam = lam + prob.Mt(Y[j]) + dt * (A[j, 0] * prob.F_vjp(st[0], Y[j]) - H[j, 0] * prob.Lt(Y[j]))
+            lam = lam + prob.Mt(Y[j]) + dt_n * (A[j, 0] * prob.F_vjp(st[0], Y[j]) - H[j, 0] * prob.Lt(Y[j]))
         src = dJ(n)
         Ybar = lam if src is None else lam + src
     return Ybar
