@@ -316,6 +316,15 @@ spadj_status spadj_hvp(spadj_problem* prob, const double* x0, const double* v, i
  * for a frequency and kept until another frequency is asked for. */
 spadj_status spadj_resolvent(spadj_problem* prob, double omega, int n_iter, double* f, double* gains);
 
+/* Step-size schedule (SPADJ_RB2D): step n of every later forward, tangent, adjoint, gradient and
+ * vjp sweep uses dts[n] (host array of n > 0 sizes, copied; n = 0 restores the descriptor's
+ * constant dt).  The stage operators M + dt gamma L are factorised once per distinct size, when a
+ * sweep first needs it, and kept for later sweeps: the paper's timesteppers reuse their LU
+ * factorisations unless the timestep changes, and rebuild them when it does.  The adjoint of
+ * step n uses the same size as its forward step.  A sweep longer than the schedule fails with
+ * SPADJ_ERR_INVALID; sizes must be positive.  spadj_solve keeps the descriptor's dt. */
+spadj_status spadj_set_dt_schedule(spadj_problem* prob, int n, const double* dts);
+
 /* Leading eigenvalue and its parameter sensitivities for a batch of pencils (SPADJ_SHEAR_EVP).
  * Pencil i has pencil_params[3i..3i+2] = (alpha, beta, Re) and the complex shift sigma_i =
  * shifts[2i] + i shifts[2i+1] (host arrays, read during the call).  The library factorises

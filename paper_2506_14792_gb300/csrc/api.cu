@@ -116,6 +116,12 @@ spadj_status spadj_resolvent(spadj_problem* p, double omega, int n_iter, double*
   return spadj::cou_resolvent(p->impl, p, omega, n_iter, f, gains);
 }
 
+spadj_status spadj_set_dt_schedule(spadj_problem* p, int n, const double* dts) {
+  if (!p) return SPADJ_ERR_INVALID;
+  if (n < 0 || (n > 0 && bad_ptr(dts))) return p->fail(SPADJ_ERR_INVALID, "set_dt_schedule: need n >= 0 and dts");
+  return spadj::rb_set_dt_schedule(p->impl, p, n, dts);
+}
+
 spadj_status spadj_eigen(spadj_problem* p, int n_pencils, const double* pencil_params, const double* shifts,
                          int n_iter, double* x, double* psi, double* out) {
   if (!p) return SPADJ_ERR_INVALID;

@@ -169,6 +169,7 @@ inline spadj_status check_launch(Problem* p, const char* what) {
 EqImpl* make_burgers(Problem* p, spadj_status* st);
 EqImpl* make_rb(Problem* p, spadj_status* st);
 spadj_status rb_pencil_solve(EqImpl* impl, Problem* p, int transpose, const double* v, double* x);
+spadj_status rb_set_dt_schedule(EqImpl* impl, Problem* p, int n, const double* dts);
 EqImpl* make_kolmogorov(Problem* p, spadj_status* st);
 EqImpl* make_shear_evp(Problem* p, spadj_status* st);
 spadj_status evp_eigen(EqImpl* impl, Problem* p, int n_pencils, const double* prm, const double* shift, int n_iter,

@@ -14,6 +14,8 @@
 // folding), x FFTs, grid products, back to T space (Sparse spectral methods section).
 #include <cmath>
 #include <functional>
+#include <memory>
+#include <string>
 #include <mutex>
 #include <vector>
 
@@ -43,7 +45,23 @@ struct RB : EqImpl {
   size_t npts = 0;  // grid points Mz*Mx
   XParams xp{};
   // device constants
-  DevBuf wm, czE, cdzE, gzF, gzTE, czTF, cdzTF, gmat, phi, phiT;
+  DevBuf wm, czE, cdzE, gzF, gzTE, czTF, cdzTF, gmat;
+  // Stage solution operators and the step graphs that use them, one set per step size: the
+  // base dt of the descriptor, plus one per distinct size of a step-size schedule
+  // (spadj_set_dt_schedule), factorised when first needed and kept (Methods: the LU
+  // decompositions are reused unless the timestep changes).
+  struct OpSet {
+    double dt = 0.0;
+    DevBuf phi, phiT;
+    cudaGraphExec_t gFwd[2] = {nullptr, nullptr};
+    cudaGraphExec_t gFwdB[2] = {nullptr, nullptr};  // lane 1 forward step graphs
+    cudaGraphExec_t gAdj[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+  };
+  std::vector<std::unique_ptr<OpSet>> opsets;
+  OpSet* ops_cur = nullptr;
+  double dt_base = 0.0;
+  std::vector<double> sched;  // per-step sizes (empty: dt_base for every step)
+  rbhost::Operators hops;     // host operators for later factorisations
   // device work buffers
   DevBuf dG, Gb, Fg, df0, df1, dx1, vb2, vb1, xb1, tmpx, tmpy, ybar, ybar2, cur, nxt, curB, nxtB, partial, Jdev,
       seedbuf, slots, traj_tmp;
@@ -66,9 +84,6 @@ struct RB : EqImpl {
   cudaEvent_t evIn = nullptr, evOut = nullptr, evFork = nullptr, evJoin = nullptr;
   cudaEvent_t evReady = nullptr, evFree = nullptr, evBdone = nullptr;  // lane handoffs
   cudaEvent_t evAdj[2] = {nullptr, nullptr}, evCopied[2] = {nullptr, nullptr};
-  cudaGraphExec_t gFwd[2] = {nullptr, nullptr};
-  cudaGraphExec_t gFwdB[2] = {nullptr, nullptr};  // lane 1 forward step graphs
-  cudaGraphExec_t gAdj[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
   double2* Sb[2] = {nullptr, nullptr};  // state ping-pong buffers
   double2* SbB[2] = {nullptr, nullptr};  // lane 1 state ping-pong buffers
   double2* Yb[2] = {nullptr, nullptr};  // cotangent ping-pong buffers
@@ -136,26 +151,8 @@ struct RB : EqImpl {
 
     // host operators and solution operators
     rbhost::Operators o = rbhost::build_operators(N, Mz);
-    std::vector<double> ph;
-    std::string err;
-    if (!rbhost::build_phi(o, Kx, Lx, nu, kappa, dt * gam, ph, &err)) return p->fail(SPADJ_ERR_INVALID, err);
-    // split Phi' (3N x 3N per pencil) into its two reflection-parity blocks
-    const int Nh = N / 2, H = 3 * Nh, np = 3 * N;
-    std::vector<double> pb((size_t)Kx * 2 * H * H), pbT((size_t)Kx * 2 * H * H);
-    auto cls_idx = [&](int cls, int c) {  // class-local index -> global prognostic index
-      const int f = c / Nh, h = c % Nh;
-      const int n = 2 * h + ((f == 0) ? cls : 1 - cls);
-      return f * N + n;
-    };
-    for (int m = 0; m < Kx; ++m)
-      for (int cls = 0; cls < 2; ++cls)
-        for (int r = 0; r < H; ++r)
-          for (int c = 0; c < H; ++c)
-          {
-            const double v = ph[(size_t)m * np * np + (size_t)cls_idx(cls, r) * np + cls_idx(cls, c)];
-            pb[(((size_t)m * 2 + cls) * H + r) * H + c] = v;   // [r][c]
-            pbT[(((size_t)m * 2 + cls) * H + c) * H + r] = v;  // [c][r]
-          }
+    hops = o;
+    dt_base = dt;
     // half matrices for the reflection-folded z transforms
     const int Mh = Mz / 2;
     std::vector<double> hczE((size_t)Mh * N), hcdzE((size_t)Mh * N), hgzF((size_t)N * Mh), hgzTE((size_t)Mh * N),
@@ -187,9 +184,11 @@ struct RB : EqImpl {
     SPADJ_CUDA_TRY(p, up(czTF, hczTF.data(), sizeof(double) * hczTF.size()));
     SPADJ_CUDA_TRY(p, up(cdzTF, hcdzTF.data(), sizeof(double) * hcdzTF.size()));
     SPADJ_CUDA_TRY(p, up(gmat, o.G.data(), sizeof(double) * o.G.size()));
-    SPADJ_CUDA_TRY(p, up(phi, pb.data(), sizeof(double) * pb.size()));
-    SPADJ_CUDA_TRY(p, up(phiT, pbT.data(), sizeof(double) * pbT.size()));
     SPADJ_CUDA_TRY(p, cudaStreamSynchronize(p->stream));
+    {
+      spadj_status s = opset_for(p, dt_base, &ops_cur);
+      if (s != SPADJ_OK) return s;
+    }
     xp.WM = wm.as<double2>();
     // work buffers
     const size_t sb = sizeof(double2) * ns, mb = sizeof(double2) * nmix, gb = sizeof(double) * npts;
@@ -226,6 +225,7 @@ struct RB : EqImpl {
     SPADJ_CUDA_TRY(p, Jdev.ensure(sizeof(double)));
     zsmem = (size_t)2 * 2 * (size_t)std::max(N, Mz / 2) * kTM * sizeof(double2);
     xsmem = sizeof(double2) * (4 * L + Kx);
+    const int H = 3 * (N / 2);
     ssmem = sizeof(double2) * (H + 4 * solve_rows(H)) + sizeof(double) * (size_t)H * solve_rows(H);
     csmem = colstep_smem(N, Mz);
     ctsmem = colstepT_smem(N, Mz);
@@ -242,6 +242,77 @@ struct RB : EqImpl {
     }
     if (ssmem > 48 * 1024)
       SPADJ_CUDA_TRY(p, cudaFuncSetAttribute(solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssmem));
+    return SPADJ_OK;
+  }
+
+  // Stage operator set for step size h: found among the factorised ones or built now (host
+  // factorisation of M + h gam L per pencil, split into the two reflection-parity blocks, and
+  // uploaded synchronously).
+  spadj_status opset_for(Problem* p, double h, OpSet** out) {
+    for (auto& os : opsets)
+      if (os->dt == h) { *out = os.get(); return SPADJ_OK; }
+    std::vector<double> ph;
+    std::string err;
+    if (!rbhost::build_phi(hops, Kx, Lx, nu, kappa, h * gam, ph, &err)) return p->fail(SPADJ_ERR_INVALID, err);
+    const int Nh = N / 2, H = 3 * Nh, np = 3 * N;
+    std::vector<double> pb((size_t)Kx * 2 * H * H), pbT((size_t)Kx * 2 * H * H);
+    auto cls_idx = [&](int cls, int c) {  // class-local index -> global prognostic index
+      const int f = c / Nh, hh = c % Nh;
+      const int n = 2 * hh + ((f == 0) ? cls : 1 - cls);
+      return f * N + n;
+    };
+    for (int m = 0; m < Kx; ++m)
+      for (int cls = 0; cls < 2; ++cls)
+        for (int r = 0; r < H; ++r)
+          for (int c = 0; c < H; ++c) {
+            const double v = ph[(size_t)m * np * np + (size_t)cls_idx(cls, r) * np + cls_idx(cls, c)];
+            pb[(((size_t)m * 2 + cls) * H + r) * H + c] = v;   // [r][c]
+            pbT[(((size_t)m * 2 + cls) * H + c) * H + r] = v;  // [c][r]
+          }
+    std::unique_ptr<OpSet> os(new OpSet());
+    os->dt = h;
+    SPADJ_CUDA_TRY(p, os->phi.ensure(sizeof(double) * pb.size()));
+    SPADJ_CUDA_TRY(p, os->phiT.ensure(sizeof(double) * pbT.size()));
+    SPADJ_CUDA_TRY(p, cudaMemcpy(os->phi.ptr, pb.data(), sizeof(double) * pb.size(), cudaMemcpyHostToDevice));
+    SPADJ_CUDA_TRY(p, cudaMemcpy(os->phiT.ptr, pbT.data(), sizeof(double) * pbT.size(), cudaMemcpyHostToDevice));
+    *out = os.get();
+    opsets.push_back(std::move(os));
+    return SPADJ_OK;
+  }
+
+  // Before a sweep of n_steps: every step size it uses has its operators (built here, never in
+  // the middle of the sweep).
+  spadj_status prepare_steps(Problem* p, int n_steps) {
+    if (sched.empty()) return SPADJ_OK;
+    if ((int)sched.size() < n_steps)
+      return p->fail(SPADJ_ERR_INVALID, "rb: the step-size schedule is shorter than n_steps");
+    OpSet* os = nullptr;
+    for (int n = 0; n < n_steps; ++n) {
+      spadj_status s = opset_for(p, sched[n], &os);
+      if (s != SPADJ_OK) return s;
+    }
+    return SPADJ_OK;
+  }
+
+  // Make step n's size and operators current (host state read while its launches are built).
+  // prepare_steps has built every set a sweep selects; a missing one is an internal error.
+  spadj_status select_step(Problem* p, int n) {
+    const double h = sched.empty() ? dt_base : sched[n];
+    if (ops_cur && ops_cur->dt == h) { dt = h; return SPADJ_OK; }
+    for (auto& os : opsets)
+      if (os->dt == h) { ops_cur = os.get(); dt = h; return SPADJ_OK; }
+    return p->fail(SPADJ_ERR_INVALID, "rb: no stage operators for this step size");
+  }
+  void select_base() {
+    dt = dt_base;
+    ops_cur = opsets.empty() ? nullptr : opsets[0].get();
+  }
+
+  spadj_status set_schedule(Problem* p, int n, const double* dts) {
+    for (int i = 0; i < n; ++i)
+      if (!(dts[i] > 0.0) || !std::isfinite(dts[i])) return p->fail(SPADJ_ERR_INVALID, "set_dt_schedule: step sizes must be > 0");
+    sched.assign(dts, dts + n);
+    select_base();
     return SPADJ_OK;
   }
 
@@ -481,7 +552,7 @@ struct RB : EqImpl {
     S.cdzTF = cdzTF.as<double>();
     for (int a = 0; a < nadd; ++a) { S.add[a] = add[a]; S.beta[a] = beta[a]; }
     S.nadd = nadd;
-    S.phiA = phi.as<double>();
+    S.phiA = ops_cur->phi.as<double>();
     S.v_out = vb;
     S.c0 = c0;
     S.al0 = al0;
@@ -501,7 +572,7 @@ struct RB : EqImpl {
   spadj_status solve(Problem* p, int transpose, int nin, const double2* const* in, const double* a, double2* out) {
     SolveArgs S{};
     for (int t = 0; t < nin; ++t) { S.in[t] = in[t]; S.a[t] = a[t]; }
-    S.nin = nin; S.out = out; S.transpose = transpose; S.phiF = phiT.as<double>(); S.phiA = phi.as<double>();
+    S.nin = nin; S.out = out; S.transpose = transpose; S.phiF = ops_cur->phiT.as<double>(); S.phiA = ops_cur->phi.as<double>();
     S.Kx = Kx; S.N = N;
     const int H = 3 * N / 2;
     dim3 grid(Kx, 2, 2);
@@ -524,7 +595,7 @@ struct RB : EqImpl {
     for (int t = 0; t < nin; ++t) { S.in[t] = in[t]; S.a[t] = a[t]; }
     S.nin = nin;
     S.af = af;
-    S.phiF = phiT.as<double>();
+    S.phiF = ops_cur->phiT.as<double>();
     S.x_out = x;
     S.czE = czE.as<double>();
     S.cdzE = cdzE.as<double>();
@@ -854,6 +925,7 @@ struct RB : EqImpl {
   }
 
   spadj_status pencil_solve(Problem* p, int transpose, const double* v, double* x) {
+    select_base();  // the stage operator of the descriptor's dt
     const double2* in[1] = {reinterpret_cast<const double2*>(v)};
     double a[1] = {1.0};
     return solve(p, transpose, 1, in, a, reinterpret_cast<double2*>(x));
@@ -900,11 +972,11 @@ struct RB : EqImpl {
     double2* x0 = Sb[ci];
     double2* x2 = Sb[1 - ci];
     if (!use_graphs(p)) return step_fwd(p, x0, x2);
-    if (!gFwd[ci]) {
-      spadj_status s = capture(p, &gFwd[ci], [&] { return step_fwd(p, x0, x2); });
+    if (!ops_cur->gFwd[ci]) {
+      spadj_status s = capture(p, &ops_cur->gFwd[ci], [&] { return step_fwd(p, x0, x2); });
       if (s != SPADJ_OK) return s;
     }
-    SPADJ_CUDA_TRY(p, cudaGraphLaunch(gFwd[ci], p->stream));
+    SPADJ_CUDA_TRY(p, cudaGraphLaunch(ops_cur->gFwd[ci], p->stream));
     return SPADJ_OK;
   }
 
@@ -919,9 +991,9 @@ struct RB : EqImpl {
     if (!use_graphs(p)) {
       s = step_fwd(p, x0, x2);
     } else {
-      if (!gFwdB[ci]) s = capture(p, &gFwdB[ci], [&] { return step_fwd(p, x0, x2); });
+      if (!ops_cur->gFwdB[ci]) s = capture(p, &ops_cur->gFwdB[ci], [&] { return step_fwd(p, x0, x2); });
       if (s == SPADJ_OK) {
-        cudaError_t e = cudaGraphLaunch(gFwdB[ci], p->stream);
+        cudaError_t e = cudaGraphLaunch(ops_cur->gFwdB[ci], p->stream);
         if (e != cudaSuccess) s = p->fail(SPADJ_ERR_CUDA, std::string("rb: graph launch: ") + cudaGetErrorString(e));
       }
     }
@@ -936,23 +1008,27 @@ struct RB : EqImpl {
     const double2* xb2 = Yb[yi];
     double2* xb0 = Yb[1 - yi];
     if (!use_graphs(p)) return step_adj(p, x0, xb2, xb0);
-    if (!gAdj[ci][yi]) {
-      spadj_status s = capture(p, &gAdj[ci][yi], [&] { return step_adj(p, x0, xb2, xb0); });
+    if (!ops_cur->gAdj[ci][yi]) {
+      spadj_status s = capture(p, &ops_cur->gAdj[ci][yi], [&] { return step_adj(p, x0, xb2, xb0); });
       if (s != SPADJ_OK) return s;
     }
-    SPADJ_CUDA_TRY(p, cudaGraphLaunch(gAdj[ci][yi], p->stream));
+    SPADJ_CUDA_TRY(p, cudaGraphLaunch(ops_cur->gAdj[ci][yi], p->stream));
     return SPADJ_OK;
   }
 
   spadj_status forward(Problem* p, int n_steps, const double* x0, double* x_out, double* traj) override {
     if (n_steps < 0) return p->fail(SPADJ_ERR_INVALID, "forward: n_steps < 0");
+    spadj_status ps = prepare_steps(p, n_steps);
+    if (ps != SPADJ_OK) return ps;
     const size_t sb = sizeof(double2) * ns;
     StreamScope scope(this, p);
     int ci = 0;
     SPADJ_CUDA_TRY(p, cudaMemcpyAsync(Sb[ci], x0, sb, cudaMemcpyDeviceToDevice, p->stream));
     if (traj) SPADJ_CUDA_TRY(p, cudaMemcpyAsync(traj, x0, sb, cudaMemcpyDeviceToDevice, p->stream));
     for (int n = 0; n < n_steps; ++n) {
-      spadj_status s = run_fwd(p, ci);
+      spadj_status s = select_step(p, n);
+      if (s == SPADJ_OK) s = run_fwd(p, ci);
+      select_base();
       if (s != SPADJ_OK) return s;
       ci = 1 - ci;
       if (traj)
@@ -964,6 +1040,8 @@ struct RB : EqImpl {
 
   spadj_status tangent(Problem* p, int n_steps, const double* x0, const double* dx0, double* dx_out) override {
     if (n_steps < 0) return p->fail(SPADJ_ERR_INVALID, "tangent: n_steps < 0");
+    spadj_status ps = prepare_steps(p, n_steps);
+    if (ps != SPADJ_OK) return ps;
     const size_t sb = sizeof(double2) * ns;
     StreamScope scope(this, p);
     double2* T[2] = {tmpx.as<double2>(), tmpy.as<double2>()};
@@ -971,7 +1049,9 @@ struct RB : EqImpl {
     SPADJ_CUDA_TRY(p, cudaMemcpyAsync(Sb[ci], x0, sb, cudaMemcpyDeviceToDevice, p->stream));
     SPADJ_CUDA_TRY(p, cudaMemcpyAsync(T[ci], dx0, sb, cudaMemcpyDeviceToDevice, p->stream));
     for (int n = 0; n < n_steps; ++n) {
-      spadj_status s = step_tan(p, Sb[ci], T[ci], Sb[1 - ci], T[1 - ci]);
+      spadj_status s = select_step(p, n);
+      if (s == SPADJ_OK) s = step_tan(p, Sb[ci], T[ci], Sb[1 - ci], T[1 - ci]);
+      select_base();
       if (s != SPADJ_OK) return s;
       ci = 1 - ci;
     }
@@ -981,6 +1061,8 @@ struct RB : EqImpl {
 
   spadj_status adjoint(Problem* p, int n_steps, const double* traj, const double* y_final, double* grad) override {
     if (n_steps < 1) return p->fail(SPADJ_ERR_INVALID, "adjoint: n_steps < 1");
+    spadj_status ps = prepare_steps(p, n_steps);
+    if (ps != SPADJ_OK) return ps;
     const size_t sb = sizeof(double2) * ns;
     StreamScope scope(this, p);
     int yi = 0;
@@ -988,7 +1070,9 @@ struct RB : EqImpl {
     for (int n = n_steps - 1; n >= 0; --n) {
       const double2* xn = reinterpret_cast<const double2*>(traj) + (size_t)n * ns;
       SPADJ_CUDA_TRY(p, cudaMemcpyAsync(Sb[0], xn, sb, cudaMemcpyDeviceToDevice, p->stream));
-      spadj_status s = run_adj(p, 0, yi);
+      spadj_status s = select_step(p, n);
+      if (s == SPADJ_OK) s = run_adj(p, 0, yi);
+      select_base();
       if (s != SPADJ_OK) return s;
       yi = 1 - yi;
     }
@@ -1027,6 +1111,10 @@ struct RB : EqImpl {
     if (n_steps < 1) return p->fail(SPADJ_ERR_INVALID, "gradient: n_steps < 1");
     if (objective_kind >= 0 && objective_kind != SPADJ_OBJ_ENERGY)
       return p->fail(SPADJ_ERR_UNSUPPORTED, "rb: objective must be ENERGY");
+    {
+      spadj_status ps = prepare_steps(p, n_steps);
+      if (ps != SPADJ_OK) return ps;
+    }
     int S = (ckpt_slots <= 0 || ckpt_slots > n_steps + 1) ? n_steps + 1 : ckpt_slots;
     const size_t sb = sizeof(double2) * ns;
     SPADJ_CUDA_TRY(p, slots.ensure(sb * (size_t)S));
@@ -1075,7 +1163,10 @@ struct RB : EqImpl {
           break;
         case CK_ADVANCE:
           for (int k = op.a; k < op.b; ++k) {
-            if ((s = run_fwd_lane1(p, ciB)) != SPADJ_OK) return s;
+            s = select_step(p, k);
+            if (s == SPADJ_OK) s = run_fwd_lane1(p, ciB);
+            select_base();
+            if (s != SPADJ_OK) return s;
             ciB = 1 - ciB;
             ++recompute;
           }
@@ -1099,7 +1190,10 @@ struct RB : EqImpl {
           if (!have_seed) return p->fail(SPADJ_ERR_INVALID, "gradient: schedule reached an adjoint step before the objective");
           const int c = op.a & 1;
           if ((s = handoff(op.a)) != SPADJ_OK) return s;
-          if ((s = run_adj(p, c, yi)) != SPADJ_OK) return s;
+          s = select_step(p, op.a);
+          if (s == SPADJ_OK) s = run_adj(p, c, yi);
+          select_base();
+          if (s != SPADJ_OK) return s;
           SPADJ_CUDA_TRY(p, cudaEventRecord(evAdj[c], p->stream));
           yi = 1 - yi;
           if (const double2* sp = seed_ptr(op.a)) {  // cotangent injected at X_a
@@ -1139,8 +1233,13 @@ struct RB : EqImpl {
   ~RB() override {
     for (cudaStream_t st : {gs, gs2, gsB})
       if (st) cudaStreamSynchronize(st);
-    for (cudaGraphExec_t g : {gFwd[0], gFwd[1], gFwdB[0], gFwdB[1], gAdj[0][0], gAdj[0][1], gAdj[1][0], gAdj[1][1]})
-      if (g) cudaGraphExecDestroy(g);
+    for (auto& os : opsets) {
+      for (cudaGraphExec_t g : {os->gFwd[0], os->gFwd[1], os->gFwdB[0], os->gFwdB[1], os->gAdj[0][0], os->gAdj[0][1],
+                                os->gAdj[1][0], os->gAdj[1][1]})
+        if (g) cudaGraphExecDestroy(g);
+      os->phi.release();
+      os->phiT.release();
+    }
     for (cudaEvent_t e : {evIn, evOut, evFork, evJoin, evReady, evFree, evBdone, evAdj[0], evAdj[1], evCopied[0],
                           evCopied[1]})
       if (e) cudaEventDestroy(e);
@@ -1154,7 +1253,7 @@ struct RB : EqImpl {
     for (int i = 0; i < 4; ++i)
       for (DevBuf* b : {&tdx[i], &tdv[i], &tdf[i], &axb[i], &avb[i], &afb[i]}) b->release();
     for (DevBuf* b : {&aacc, &atmp, &axs}) b->release();
-    for (DevBuf* b : {&wm, &czE, &cdzE, &gzF, &gzTE, &czTF, &cdzTF, &gmat, &phi, &phiT, &dG, &Gb, &Fg, &df0, &df1, &dx1,
+    for (DevBuf* b : {&wm, &czE, &cdzE, &gzF, &gzTE, &czTF, &cdzTF, &gmat, &dG, &Gb, &Fg, &df0, &df1, &dx1,
                       &vb2, &vb1, &xb1, &tmpx, &tmpy, &ybar, &ybar2, &cur, &nxt, &curB, &nxtB, &partial, &Jdev,
                       &seedbuf, &slots, &traj_tmp})
       b->release();
@@ -1163,6 +1262,12 @@ struct RB : EqImpl {
 };
 
 }  // namespace
+
+spadj_status rb_set_dt_schedule(EqImpl* impl, Problem* p, int n, const double* dts) {
+  RB* r = dynamic_cast<RB*>(impl);
+  if (!r) return p->fail(SPADJ_ERR_UNSUPPORTED, "set_dt_schedule: only defined for the Rayleigh-Benard problem");
+  return r->set_schedule(p, n, dts);
+}
 
 EqImpl* make_rb(Problem* p, spadj_status* st) {
   RB* r = new RB();

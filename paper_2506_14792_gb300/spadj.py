@@ -72,6 +72,7 @@ _SIGS = {
     "spadj_hvp": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _vp]),
     "spadj_checkpoint_schedule_host": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int,
                                                       ctypes.POINTER(ctypes.c_int)]),
+    "spadj_set_dt_schedule": (ctypes.c_int, [_vp, ctypes.c_int, _vp]),
     "spadj_eigen": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, ctypes.c_int, _vp, _vp, _vp]),
     "spadj_set_observations": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, ctypes.c_int]),
     "spadj_set_option": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
@@ -282,6 +283,12 @@ class Problem:
         _chk(self.h, lib().spadj_hvp(self.h, _ptr(_as_f64(x0, n, "x0")), _ptr(_as_f64(v, n, "v")), int(n_steps),
                                       _ptr(_as_f64(hv, n, "hv"))))
         return hv
+
+    def set_dt_schedule(self, dts):
+        """Per-step sizes for later sweeps (SPADJ_RB2D); an empty sequence restores the constant dt."""
+        import numpy as np
+        d = np.ascontiguousarray(np.asarray(dts, dtype=np.float64).reshape(-1))
+        _chk(self.h, lib().spadj_set_dt_schedule(self.h, int(d.size), d.ctypes.data_as(ctypes.c_void_p)))
 
     def eigen(self, pencil_params, shifts, n_iter, x, psi, out):
         """Leading eigenvalue nearest each shift and its sensitivities (SPADJ_SHEAR_EVP).

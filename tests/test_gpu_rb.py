@@ -137,6 +137,45 @@ def test_rk443_forward_tangent_adjoint_gradient(Nx, Nz, nonlinear):
     assert rel_err(host(gc), o.state(g)) < TOL
 
 
+@pytest.mark.parametrize("scheme", ["rk222", "rk443"])
+def test_step_size_schedule(scheme):
+    """Step-dependent sizes (a stage factorisation per distinct size): trajectory, adjoint over
+    it and the checkpointed two-lane gradient against the oracle under the same schedule; an
+    empty schedule restores the constant step."""
+    from paper_2506_14792_gb300 import spadj
+    Nx, Nz = 16, 12
+    sched = [1e-2, 1e-2, 4e-3, 4e-3, 4e-3, 7e-3, 1e-2, 2e-3, 7e-3, 1e-2]
+    n = len(sched)
+    o = orb.RayleighBenard(Nx, Nz, 1e6)
+    s0 = synthetic.rb_ic(Nx, Nz, seed=2, amp=0.3)
+    tab = imex.rk222_tableaux() if scheme == "rk222" else imex.rk443_tableaux()
+    sch = spadj.SPADJ_RK222 if scheme == "rk222" else spadj.SPADJ_RK443
+    J, g, X, stages = orb.gradient(o, o.pencils(s0), n, sched, tab)
+    p = gpu_problem(Nx, Nz, dt=1e-2, scheme=sch)
+    p.set_dt_schedule(sched)
+    traj = _z((n + 1, 3, o.Kx, o.N))
+    xN = _z((3, o.Kx, o.N))
+    p.forward(n, dev(s0), xN, traj)
+    assert rel_err(host(traj), np.stack([o.state(x) for x in X])) < TOL
+    yN = o.state(o.kinetic_energy_grad(X[-1]))
+    gr = _z((3, o.Kx, o.N))
+    p.adjoint(n, traj, dev(yN), gr)
+    assert rel_err(host(gr), o.state(g)) < TOL
+    gc = _z((3, o.Kx, o.N))
+    Jg = p.gradient(dev(s0), n, gc, ckpt_slots=3)
+    assert abs(Jg[0] - J) <= TOL * abs(J)
+    assert rel_err(host(gc), o.state(g)) < TOL
+    with pytest.raises(spadj.SpadjError):
+        p.gradient(dev(s0), n + 1, gc)  # longer than the schedule
+    p.set_dt_schedule([])
+    g1 = _z((3, o.Kx, o.N))
+    p.gradient(dev(s0), 6, g1, ckpt_slots=3)
+    q = gpu_problem(Nx, Nz, dt=1e-2, scheme=sch)
+    g2 = _z((3, o.Kx, o.N))
+    q.gradient(dev(s0), 6, g2, ckpt_slots=3)
+    assert torch.equal(g1, g2)
+
+
 @pytest.mark.parametrize("slots", [0, 2, 5, 31])
 def test_checkpointed_gradient(small_case, slots):
     o, s0, J, g, X, stages, dt, nsteps = small_case
