@@ -49,6 +49,13 @@ TRAFFIC = {
     # evp_iter_kernel, full bench launch (608 pencils, 100 iterations): 32.07 GB read + 7.4 MB
     # written, against 35.9 GB of operator rows streamed by the algorithm (the rest hits in L2)
     ("poiseuille_evp_N64_608pencils_Re8000_100iter", "pencil_solve"): 3.2075e10,
+    # Burgers trajectory + adjoint kernels, captured at 50 steps (forward: 37 MB read + 1.66 GB of
+    # trajectory written; adjoint: 1.715 GB of trajectory read + 31 MB written), trajectory bytes
+    # scaled to 1000 steps by (1001 / 51), averaged over the two launches of a gradient
+    ("burgers1d_N256_sbdf2_1000steps", "fused_trajectory"): 3.32e10,
+    # kol_persistent, captured at 40 steps: 6.78 GB read + 4.87 GB written per sweep (trajectory
+    # and checkpoint traffic of the 64 members), scaled to 2000 steps by 50
+    ("kolmogorov2d_batch64_mixed128-512_Re100_sbdf2_2000steps_4dvar8", "fused_trajectory"): 5.83e11,
 }
 
 
