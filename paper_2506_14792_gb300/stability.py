@@ -62,6 +62,62 @@ def neutral_curve(prob, alphas, Re0, lam0, beta=0.0, n_iter=30, tol=1e-10, max_n
     }
 
 
+def trace_neutral_curves(prob, alpha0, Re0, lam0, directions, ds, n_points, beta=0.0, n_iter=30, tol=1e-12,
+                         max_newton=20, shift_rel=2e-3, seed=0):
+    """Continuation of neutral curves gamma_max(alpha, Re) = 0 (Parametric sensitivity example):
+    from the neutral points (alpha0, Re0) (one per curve, eigenvalues lam0), each curve steps by
+    ds along the tangent of the curve in (alpha, log Re), which the adjoint gradient
+    (dgamma/dalpha, Re dgamma/dRe) gives, in the given direction (+1 or -1), and returns to the
+    curve by Newton steps along the gradient (the minimum-norm correction).  All curves advance
+    together, one spadj_eigen call per Newton step.  Returns arrays of shape (n_points + 1, P):
+    alpha, Re, lam, and the Newton steps each point took.  Turning points in Re are crossed
+    without special treatment, because the parametrisation is by arclength."""
+    import torch
+    a = np.asarray(alpha0, dtype=np.float64).reshape(-1).copy()
+    P = a.size
+    r = np.log(np.broadcast_to(np.asarray(Re0, dtype=np.float64), (P,)).copy())
+    lam = np.broadcast_to(np.asarray(lam0, dtype=np.complex128), (P,)).copy()
+    sgn = np.broadcast_to(np.asarray(directions, dtype=np.float64), (P,)).copy()
+    H = 3 * prob.desc.n[2]
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    x = torch.randn((P, H), dtype=torch.complex128, generator=g).cuda()
+    psi = torch.randn((P, H), dtype=torch.complex128, generator=g).cuda()
+    out = torch.zeros((P, 10), dtype=torch.float64, device="cuda")
+
+    def evaluate(a_, r_, lam_):
+        prm = np.stack([a_, np.full(P, float(beta)), np.exp(r_)], axis=1)
+        prob.eigen(prm, _shift(lam_, shift_rel), n_iter, x, psi, out)
+        o = out.cpu().numpy()
+        lam_n = o[:, 0] + 1j * o[:, 1]
+        grad = np.stack([o[:, 4], o[:, 2] * np.exp(r_)], axis=1)  # (dgamma/dalpha, dgamma/dlog Re)
+        return lam_n, grad
+
+    def correct(a_, r_, lam_):
+        steps = np.zeros(P, dtype=int)
+        for _ in range(max_newton):
+            lam_, grad = evaluate(a_, r_, lam_)
+            gam = lam_.real
+            if np.all(np.abs(gam) <= tol):
+                break
+            n2 = np.sum(grad * grad, axis=1)
+            act = np.abs(gam) > tol
+            a_ = a_ - np.where(act, gam * grad[:, 0] / n2, 0.0)
+            r_ = r_ - np.where(act, gam * grad[:, 1] / n2, 0.0)
+            steps += act
+        return a_, r_, lam_, grad, steps
+
+    a, r, lam, grad, st = correct(a, r, lam)
+    A, R, L, S = [a.copy()], [np.exp(r)], [lam.copy()], [st]
+    for _ in range(n_points):
+        t = np.stack([-grad[:, 1], grad[:, 0]], axis=1)
+        t /= np.linalg.norm(t, axis=1, keepdims=True)
+        a_p = a + sgn * ds * t[:, 0]
+        r_p = r + sgn * ds * t[:, 1]
+        a, r, lam, grad, st = correct(a_p, r_p, lam)
+        A.append(a.copy()); R.append(np.exp(r)); L.append(lam.copy()); S.append(st)
+    return {"alpha": np.array(A), "Re": np.array(R), "lam": np.array(L), "newton_steps": np.array(S)}
+
+
 def shear_evp_problem(N, base="poiseuille", max_pencils=1):
     """A SPADJ_SHEAR_EVP problem with N Chebyshev modes for plane Couette or Poiseuille flow."""
     b = {"couette": 0, "poiseuille": 1}[base]

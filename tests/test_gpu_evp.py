@@ -115,3 +115,23 @@ def test_full_batch_sampled():
         else:  # not converged within 200 iterations: still the nearest eigenvalue to the shift
             assert abs(got - lam) <= 1e-3 * abs(lam)
     assert np.mean(np.max(o[:, 8:10], axis=1) <= 1e-11) >= 0.5
+
+
+def test_neutral_curve_continuation():
+    """Arclength continuation of the neutral curve from the critical point in both directions
+    (tangent from the adjoint gradient, minimum-norm Newton back to gamma = 0): every traced
+    point is neutral for the oracle's dense eigenproblem, and both branches rise above Re_c."""
+    N = 48
+    e = ShearEVP(N, "poiseuille")
+    a_c = 1.02056
+    Re_c, lam_c, _ = e.neutral_re(a_c, 5800.0)
+    prob = stability.shear_evp_problem(N, "poiseuille", 2)
+    res = stability.trace_neutral_curves(prob, [a_c, a_c], Re_c, lam_c, [1.0, -1.0], ds=0.06, n_points=4)
+    A, R = res["alpha"], res["Re"]
+    assert np.all(res["newton_steps"] < 20)
+    for k in range(1, A.shape[0]):
+        for j in range(2):
+            lam_o = e.leading(A[k, j], 0.0, R[k, j])[0]
+            assert abs(lam_o.real) <= 1e-10, (k, j, A[k, j], R[k, j], lam_o)
+    assert np.all(R[1:] > Re_c)
+    assert (A[-1, 0] - a_c) * (A[-1, 1] - a_c) < 0  # the two directions go to opposite sides in alpha
