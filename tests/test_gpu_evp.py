@@ -135,3 +135,31 @@ def test_neutral_curve_continuation():
             assert abs(lam_o.real) <= 1e-10, (k, j, A[k, j], R[k, j], lam_o)
     assert np.all(R[1:] > Re_c)
     assert (A[-1, 0] - a_c) * (A[-1, 1] - a_c) < 0  # the two directions go to opposite sides in alpha
+
+
+def test_largest_chebyshev_size():
+    """N = 128 (3N = 384: twelve 32-column chunks per lane, shared memory above the default
+    limit) against the oracle."""
+    N = 128
+    e = ShearEVP(N, "poiseuille")
+    cases = [(1.0, 0.0, 10000.0), (0.9, 0.4, 6000.0)]
+    shifts, want, iters = [], [], []
+    for a, b, Re in cases:
+        lam_all, X, Y = e.eigs(a, b, Re)
+        sigma, n = _shift_and_iters(lam_all, lam_all[0])
+        shifts.append(sigma)
+        iters.append(n)
+        want.append((lam_all[0], e.sensitivity(a, b, Re, lam_all[0], X[:, 0], Y[:, 0])))
+    prob = stability.shear_evp_problem(N, "poiseuille", len(cases))
+    rng = np.random.default_rng(13)
+    x = torch.tensor(rng.standard_normal((2, 3 * N)) + 1j * rng.standard_normal((2, 3 * N))).cuda()
+    psi = torch.tensor(rng.standard_normal((2, 3 * N)) + 1j * rng.standard_normal((2, 3 * N))).cuda()
+    out = torch.zeros((2, 10), dtype=torch.float64, device="cuda")
+    prob.eigen(cases, shifts, max(iters), x, psi, out)
+    o = out.cpu().numpy()
+    for i, (lam, sens) in enumerate(want):
+        got = o[i, 0] + 1j * o[i, 1]
+        assert abs(got - lam) <= TOL_LAM * abs(lam), (i, got, lam)
+        for t in range(3):
+            g = o[i, 2 + 2 * t] + 1j * o[i, 3 + 2 * t]
+            assert abs(g - sens[t]) <= TOL_SENS * abs(sens[t]) + 1e-13 * abs(lam), (i, t, g, sens[t])
