@@ -34,6 +34,25 @@ PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
 
 
+def hbm_peak_gbs():
+    """Measured HBM copy bandwidth of the GB300s (GB/s), or the recipe's fallback."""
+    try:
+        with open(PEAKS_PATH) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback"
+
+
+def hbm_fraction(traffic, avg_launch_s):
+    """DRAM bytes of one launch of the dominant kernel over its CUDA-event duration, against the
+    measured HBM roof (the metric's "% HBM roofline"); None without an ncu traffic figure."""
+    if not traffic:
+        return None
+    peak, src = hbm_peak_gbs()
+    achieved = traffic / avg_launch_s / 1e9
+    return {"achieved_gbs": achieved, "peak_gbs": peak, "frac": achieved / peak, "peak_source": src}
+
+
 # DRAM traffic (bytes per launch) of the dominant kernel from an ncu capture, keyed by
 # (workload, kernel class); None until measured for the current kernels.
 TRAFFIC = {
@@ -636,6 +655,7 @@ def run_gpu(args, wl):
                       "gflops": v[1] / (v[0] / 1e3) / 1e9 if v[0] > 0 else None} for k, v in rep.items()}
     roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
             "frac": achieved / FP64_PEAK_GFLOPS, "traffic": TRAFFIC.get((wl.name, dom)),
+            "hbm": hbm_fraction(TRAFFIC.get((wl.name, dom)), dms / dn / 1e3),
             "avg_launch_us": 1e3 * dms / dn, "flops_per_launch": dfl / dn, "per_kernel": per_kernel,
             "peak_note": "FP64 FMA peak 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s); "
                          "no tensor-core FP64 path (GB300 FP64 tensor rate is the same)"}
@@ -715,7 +735,8 @@ def run_gpu_evp(args, wl):
                       "gflops": v[1] / (v[0] / 1e3) / 1e9 if v[0] > 0 else None} for k, v in rep.items()}
     roof = {"kernel": "evp_iter_kernel (pencil_solve)", "bound": "alu", "achieved": achieved,
             "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s", "frac": achieved / FP64_PEAK_GFLOPS,
-            "traffic": TRAFFIC.get((wl.name, dom)), "avg_launch_us": 1e3 * dms / dn, "flops_per_launch": dfl / dn,
+            "traffic": TRAFFIC.get((wl.name, dom)), "hbm": hbm_fraction(TRAFFIC.get((wl.name, dom)), dms / dn / 1e3),
+            "avg_launch_us": 1e3 * dms / dn, "flops_per_launch": dfl / dn,
             "per_kernel": per_kernel,
             "peak_note": "FP64 FMA peak 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz; 16 flops per operator entry "
                          "and iteration (forward and adjoint complex matvecs)"}
