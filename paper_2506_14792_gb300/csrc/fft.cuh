@@ -41,6 +41,19 @@ __device__ __forceinline__ double2 cscale(double2 a, double s) { return make_dou
 // multiply by i*s (s = +-1)
 __device__ __forceinline__ double2 cmul_i(double2 a, double s) { return make_double2(-s * a.y, s * a.x); }
 
+// Packed-spectrum entry of a real inverse transform, e + i d conj(w), written as two multiply-add
+// chains (the FP64 pipe is the binding resource: 8 instructions per entry instead of 10).
+__device__ __forceinline__ double2 c2r_combine(double2 e, double2 d, double2 w) {
+  return make_double2(fma(d.x, w.y, fma(-d.y, w.x, e.x)), fma(d.x, w.x, fma(d.y, w.y, e.y)));
+}
+
+// Spectrum entry of a real forward transform from the packed FFT value zk and zc = conj(z_{L-k}):
+// ((zk + zc) - i (zk - zc) w) / 2 as multiply-add chains (10 instructions instead of 14).
+__device__ __forceinline__ double2 r2c_combine(double2 zk, double2 zc, double2 w) {
+  const double sx = zk.x + zc.x, sy = zk.y + zc.y, dx = zk.x - zc.x, dy = zk.y - zc.y;
+  return make_double2(0.5 * fma(dy, w.x, fma(dx, w.y, sx)), 0.5 * fma(dy, w.y, fma(-dx, w.x, sy)));
+}
+
 // Twiddle exp(SIGN * 2 pi i m / L) from the M-table (M = 2L): entry 2m, conjugated for SIGN=+1.
 template <int SIGN>
 __device__ __forceinline__ double2 twL(const double2* __restrict__ WM, int m) {
@@ -193,9 +206,7 @@ __device__ __forceinline__ void c2r_pre_t(double2* Z, Get get, int K, int L, con
     }
     const int kc = L - k;  // partner index (k = 0 pairs with the unstored Nyquist L)
     if (k > 0 && kc < K) xc = cconj(UNIT ? get(kc) : cscale(get(kc), w));
-    double2 e = cadd(xk, xc);
-    double2 o = cmul(csub(xk, xc), cconj(__ldg(&WM[k])));  // * exp(+2 pi i k / M)
-    Z[k] = make_double2(e.x - o.y, e.y + o.x);            // e + i o
+    Z[k] = c2r_combine(cadd(xk, xc), csub(xk, xc), __ldg(&WM[k]));  // e + i (xk - xc) exp(+2 pi i k / M)
   }
 }
 template <class Get>
@@ -209,14 +220,8 @@ __device__ __forceinline__ void c2r_pre(double2* Z, Get get, int K, int L, const
 //   X_k = sum_j g_j e^{-2 pi i k j / M}  for k < K  (via put(k, X_k)).
 template <class Put>
 __device__ __forceinline__ void r2c_post(const double2* Z, Put put, int K, int L, const double2* __restrict__ WM) {
-  for (int k = threadIdx.x; k < K; k += blockDim.x) {
-    double2 zk = Z[k];
-    double2 zc = cconj(Z[k == 0 ? 0 : L - k]);
-    double2 e = cscale(cadd(zk, zc), 0.5);
-    double2 d = csub(zk, zc);
-    double2 o = make_double2(0.5 * d.y, -0.5 * d.x);  // -i/2 (zk - zc)
-    put(k, cadd(e, cmul(o, __ldg(&WM[k]))));
-  }
+  for (int k = threadIdx.x; k < K; k += blockDim.x)
+    put(k, r2c_combine(Z[k], cconj(Z[k == 0 ? 0 : L - k]), __ldg(&WM[k])));
 }
 
 }  // namespace spadj

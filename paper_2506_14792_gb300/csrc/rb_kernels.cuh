@@ -298,12 +298,7 @@ __global__ void __launch_bounds__(64) xfft_kernel(const __grid_constant__ XJobs 
       double2 acc = make_double2(0.0, 0.0);
       for (int t = 0; t < J.nr; ++t) {
         const double2* Z = (t == 0) ? z0 : z1;
-        double2 zk = Z[k];
-        double2 zc = cconj(Z[k == 0 ? 0 : L - k]);
-        double2 e = cscale(cadd(zk, zc), 0.5);
-        double2 d = csub(zk, zc);
-        double2 o = make_double2(0.5 * d.y, -0.5 * d.x);
-        double2 X = cadd(e, cmul(o, __ldg(&P.WM[k])));
+        double2 X = r2c_combine(Z[k], cconj(Z[k == 0 ? 0 : L - k]), __ldg(&P.WM[k]));
         if (J.rmul[t] == 2) {  // -i k X
           const double kk = P.kscale * k;
           X = make_double2(kk * X.y, -kk * X.x);
@@ -357,9 +352,7 @@ __global__ void __launch_bounds__(64) xfftm_kernel(const __grid_constant__ XJobs
       else if (k < Kx) xk = cscale(Sr[k], J.w);
       const int kc = L - k;
       if (k > 0 && kc < Kx) xc = cconj(cscale(Sr[kc], J.w));
-      const double2 e = cadd(xk, xc);
-      const double2 o = cmul(csub(xk, xc), cconj(__ldg(&P.WM[k])));
-      A[idx] = make_double2(e.x - o.y, e.y + o.x);
+      A[idx] = c2r_combine(cadd(xk, xc), csub(xk, xc), __ldg(&P.WM[k]));
     }
     __syncthreads();
     const double2* z = cfft_smem_batch<1>(A, B, P.plan, P.WM, nb);
@@ -405,12 +398,7 @@ __global__ void __launch_bounds__(64) xfftm_kernel(const __grid_constant__ XJobs
     double2 acc = make_double2(0.0, 0.0);
     for (int t = 0; t < nin; ++t) {
       const double2* Z = t == 0 ? z0 : z1;
-      const double2 zk = Z[k * nb + c];
-      const double2 zc = cconj(Z[(k == 0 ? 0 : L - k) * nb + c]);
-      const double2 e = cscale(cadd(zk, zc), 0.5);
-      const double2 d = csub(zk, zc);
-      const double2 o = make_double2(0.5 * d.y, -0.5 * d.x);
-      double2 X = cadd(e, cmul(o, __ldg(&P.WM[k])));
+      double2 X = r2c_combine(Z[k * nb + c], cconj(Z[(k == 0 ? 0 : L - k) * nb + c]), __ldg(&P.WM[k]));
       if (J.rmul[t] == 2) {  // -i k X
         const double kk = P.kscale * k;
         X = make_double2(kk * X.y, -kk * X.x);
