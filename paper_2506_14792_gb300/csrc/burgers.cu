@@ -58,11 +58,12 @@ __device__ double2* c2g_packed(const BurgersParams& P, const double2* S, double2
   return cfft_smem(a, b, P.plan, P.WM, +1);
 }
 
-// forward real FFT of the packed grid in a; writes X_k * scale(k) to O (k < K).
+// forward real FFT of the packed grid in a; writes scale(k, 2 X_k) to O (k < K): the factor 1/2
+// of the real-transform unpacking is left to the scale functors.
 template <class Scale>
 __device__ void g2c_packed(const BurgersParams& P, double2* a, double2* b, double2* O, Scale scale) {
   double2* z = cfft_smem(a, b, P.plan, P.WM, -1);
-  r2c_post(z, [&](int k, double2 v) { O[k] = scale(k, v); }, P.K, P.L, P.WM);
+  r2c_post2(z, [&](int k, double2 v) { O[k] = scale(k, v); }, P.K, P.L, P.WM);
   __syncthreads();
 }
 
@@ -73,13 +74,13 @@ __device__ void eval_F(const BurgersParams& P, Smem& s) {
   double2* u = c2g_packed(P, s.S, s.A, s.B, 1.0, 1.0);
   for (int j = threadIdx.x; j < P.L; j += blockDim.x) {
     double2 v = u[j];
-    u[j] = make_double2(0.5 * v.x * v.x, 0.5 * v.y * v.y);
+    u[j] = make_double2(v.x * v.x, v.y * v.y);  // u^2; the 1/2 goes into the scale below
   }
   __syncthreads();
   double2* other = (u == s.A) ? s.B : s.A;
-  const double invM = 1.0 / P.M;
+  const double q = 0.25 / P.M;  // (1/2 of u^2/2) (1/2 of the unpacking) / M
   g2c_packed(P, u, other, s.O, [&](int k, double2 v) {
-    double kk = kwav(P, k) * invM;  // -i k v / M
+    double kk = kwav(P, k) * q;  // -i k v / M
     return make_double2(kk * v.y, -kk * v.x);
   });
 }
@@ -94,16 +95,20 @@ __device__ void eval_F_and_jvp(const BurgersParams& P, Smem& s, const double2* S
   for (int j = threadIdx.x; j < P.L; j += blockDim.x) {
     double2 v = u[j], dv = du[j];
     du[j] = make_double2(v.x * dv.x, v.y * dv.y);
-    u[j] = make_double2(0.5 * v.x * v.x, 0.5 * v.y * v.y);
+    u[j] = make_double2(v.x * v.x, v.y * v.y);
   }
   __syncthreads();
-  const double invM = 1.0 / P.M;
-  auto mik = [&](int k, double2 v) {
-    double kk = kwav(P, k) * invM;
+  const double qf = 0.25 / P.M, qj = 0.5 / P.M;  // -i k (u^2/2) / M and -i k (u du) / M, unpacking 1/2 included
+  auto mikf = [&](int k, double2 v) {
+    double kk = kwav(P, k) * qf;
     return make_double2(kk * v.y, -kk * v.x);
   };
-  if (want_F) g2c_packed(P, u, uo, s.O, mik);
-  g2c_packed(P, du, duo, O2, mik);
+  auto mikj = [&](int k, double2 v) {
+    double kk = kwav(P, k) * qj;
+    return make_double2(kk * v.y, -kk * v.x);
+  };
+  if (want_F) g2c_packed(P, u, uo, s.O, mikf);
+  g2c_packed(P, du, duo, O2, mikj);
 }
 
 // O <- (dF/dX)(S)^dagger W  with W staged in S2:  B^dagger[(B S) * T^dagger(i k W)]
@@ -123,8 +128,8 @@ __device__ void eval_vjp(const BurgersParams& P, Smem& s, double2* S2) {
     v[j] = make_double2(a.x * b.x, a.y * b.y);
   }
   __syncthreads();
-  g2c_packed(P, v, vo, s.O, [&](int k, double2 x) {
-    return k == 0 ? make_double2(x.x, 0.0) : make_double2(2.0 * x.x, 2.0 * x.y);
+  g2c_packed(P, v, vo, s.O, [&](int k, double2 x) {  // x = 2 X_k
+    return k == 0 ? make_double2(0.5 * x.x, 0.0) : x;
   });
 }
 
@@ -155,11 +160,11 @@ __global__ void transform_kernel(BurgersParams P, int kind, const double* __rest
     __syncthreads();
     double2* y = row(out, b, K);
     if (kind == 1) {
-      const double invM = 1.0 / M;
-      g2c_packed(P, s.A, s.B, s.O, [&](int k, double2 v) { return cscale(v, invM); });
+      const double halfinvM = 0.5 / M;
+      g2c_packed(P, s.A, s.B, s.O, [&](int k, double2 v) { return cscale(v, halfinvM); });
     } else {
       g2c_packed(P, s.A, s.B, s.O, [&](int k, double2 v) {
-        return k == 0 ? make_double2(v.x, 0.0) : cscale(v, 2.0);
+        return k == 0 ? make_double2(0.5 * v.x, 0.0) : v;
       });
     }
     for (int k = threadIdx.x; k < K; k += blockDim.x) y[k] = s.O[k];

@@ -47,11 +47,16 @@ __device__ __forceinline__ double2 c2r_combine(double2 e, double2 d, double2 w) 
   return make_double2(fma(d.x, w.y, fma(-d.y, w.x, e.x)), fma(d.x, w.x, fma(d.y, w.y, e.y)));
 }
 
-// Spectrum entry of a real forward transform from the packed FFT value zk and zc = conj(z_{L-k}):
-// ((zk + zc) - i (zk - zc) w) / 2 as multiply-add chains (10 instructions instead of 14).
-__device__ __forceinline__ double2 r2c_combine(double2 zk, double2 zc, double2 w) {
+// Twice the spectrum entry of a real forward transform from the packed FFT value zk and
+// zc = conj(z_{L-k}): (zk + zc) - i (zk - zc) w as multiply-add chains (8 instructions; the
+// factor 1/2 is left to the caller's scaling).
+__device__ __forceinline__ double2 r2c_combine2(double2 zk, double2 zc, double2 w) {
   const double sx = zk.x + zc.x, sy = zk.y + zc.y, dx = zk.x - zc.x, dy = zk.y - zc.y;
-  return make_double2(0.5 * fma(dy, w.x, fma(dx, w.y, sx)), 0.5 * fma(dy, w.y, fma(-dx, w.x, sy)));
+  return make_double2(fma(dy, w.x, fma(dx, w.y, sx)), fma(dy, w.y, fma(-dx, w.x, sy)));
+}
+// The spectrum entry itself: r2c_combine2 / 2.
+__device__ __forceinline__ double2 r2c_combine(double2 zk, double2 zc, double2 w) {
+  return cscale(r2c_combine2(zk, zc, w), 0.5);
 }
 
 // Twiddle exp(SIGN * 2 pi i m / L) from the M-table (M = 2L): entry 2m, conjugated for SIGN=+1.
@@ -110,10 +115,10 @@ static __device__ __noinline__ double2* cfft_smem_t(double2* a, double2* b, cons
         const double h = 0.86602540378443864676;  // sqrt(3)/2
         const double2 t = cadd(v1, v2);
         const double2 m = make_double2(fma(-0.5, t.x, v0.x), fma(-0.5, t.y, v0.y));
-        const double2 d = rot<SIGN>(cscale(csub(v1, v2), h));
+        const double2 r = rot<SIGN>(csub(v1, v2));  // m +- h r as multiply-adds
         b[base] = cadd(v0, t);
-        b[base + Ns] = cadd(m, d);
-        b[base + 2 * Ns] = csub(m, d);
+        b[base + Ns] = make_double2(fma(h, r.x, m.x), fma(h, r.y, m.y));
+        b[base + 2 * Ns] = make_double2(fma(-h, r.x, m.x), fma(-h, r.y, m.y));
       }
     }
     __syncthreads();
@@ -169,10 +174,10 @@ static __device__ __noinline__ double2* cfft_smem_batch(double2* a, double2* b, 
         const double h = 0.86602540378443864676;
         const double2 t = cadd(v1, v2);
         const double2 m = make_double2(fma(-0.5, t.x, v0.x), fma(-0.5, t.y, v0.y));
-        const double2 d = rot<SIGN>(cscale(csub(v1, v2), h));
+        const double2 r = rot<SIGN>(csub(v1, v2));
         Bw(base, cadd(v0, t));
-        Bw(base + Ns, cadd(m, d));
-        Bw(base + 2 * Ns, csub(m, d));
+        Bw(base + Ns, make_double2(fma(h, r.x, m.x), fma(h, r.y, m.y)));
+        Bw(base + 2 * Ns, make_double2(fma(-h, r.x, m.x), fma(-h, r.y, m.y)));
       }
     }
     __syncthreads();
@@ -218,6 +223,13 @@ __device__ __forceinline__ void c2r_pre(double2* Z, Get get, int K, int L, const
 
 // r2c post: z = forward L-point FFT of the packed real field; returns
 //   X_k = sum_j g_j e^{-2 pi i k j / M}  for k < K  (via put(k, X_k)).
+// r2c_post2: the same with put(k, 2 X_k), for callers that fold the factor 1/2 into their own
+// scaling.
+template <class Put>
+__device__ __forceinline__ void r2c_post2(const double2* Z, Put put, int K, int L, const double2* __restrict__ WM) {
+  for (int k = threadIdx.x; k < K; k += blockDim.x)
+    put(k, r2c_combine2(Z[k], cconj(Z[k == 0 ? 0 : L - k]), __ldg(&WM[k])));
+}
 template <class Put>
 __device__ __forceinline__ void r2c_post(const double2* Z, Put put, int K, int L, const double2* __restrict__ WM) {
   for (int k = threadIdx.x; k < K; k += blockDim.x)

@@ -237,8 +237,9 @@ __device__ void row_r2c(double2* row, double2* scratch, double2* dst, const KMem
                         double s) {
   const int Kx = m.Kx, L = m.L;
   double2* z = cfft_smem_t<-1>(row, scratch, R.px, R.WMx);
-  r2c_post(z, [&](int k, double2 v) {
-    double2 o = make_double2(v.x * (k == 0 ? s0 : s), v.y * (k == 0 ? s0 : s));
+  r2c_post2(z, [&](int k, double2 v) {  // v = 2 X_k
+    const double f = 0.5 * (k == 0 ? s0 : s);
+    double2 o = make_double2(v.x * f, v.y * f);
     if (k == 0) o.y = 0.0;
     dst[k] = o;
   }, Kx, L, R.WMx);

@@ -298,14 +298,14 @@ __global__ void __launch_bounds__(64) xfft_kernel(const __grid_constant__ XJobs 
       double2 acc = make_double2(0.0, 0.0);
       for (int t = 0; t < J.nr; ++t) {
         const double2* Z = (t == 0) ? z0 : z1;
-        double2 X = r2c_combine(Z[k], cconj(Z[k == 0 ? 0 : L - k]), __ldg(&P.WM[k]));
+        double2 X = r2c_combine2(Z[k], cconj(Z[k == 0 ? 0 : L - k]), __ldg(&P.WM[k]));  // twice the entry
         if (J.rmul[t] == 2) {  // -i k X
           const double kk = P.kscale * k;
           X = make_double2(kk * X.y, -kk * X.x);
         }
-        acc = cadd(acc, X);
+        acc = t == 0 ? X : cadd(acc, X);
       }
-      const double sc = (k == 0) ? J.s0 : J.s;
+      const double sc = 0.5 * ((k == 0) ? J.s0 : J.s);
       double2 r = cscale(acc, sc);
       if (k == 0) r.y = 0.0;
       dst[k] = r;
@@ -398,14 +398,14 @@ __global__ void __launch_bounds__(64) xfftm_kernel(const __grid_constant__ XJobs
     double2 acc = make_double2(0.0, 0.0);
     for (int t = 0; t < nin; ++t) {
       const double2* Z = t == 0 ? z0 : z1;
-      double2 X = r2c_combine(Z[k * nb + c], cconj(Z[(k == 0 ? 0 : L - k) * nb + c]), __ldg(&P.WM[k]));
+      double2 X = r2c_combine2(Z[k * nb + c], cconj(Z[(k == 0 ? 0 : L - k) * nb + c]), __ldg(&P.WM[k]));
       if (J.rmul[t] == 2) {  // -i k X
         const double kk = P.kscale * k;
         X = make_double2(kk * X.y, -kk * X.x);
       }
-      acc = cadd(acc, X);
+      acc = t == 0 ? X : cadd(acc, X);
     }
-    const double sc = (k == 0) ? J.s0 : J.s;
+    const double sc = 0.5 * ((k == 0) ? J.s0 : J.s);
     double2 out = cscale(acc, sc);
     if (k == 0) out.y = 0.0;
     J.cout[(size_t)(row0 + c) * Kx + k] = out;
