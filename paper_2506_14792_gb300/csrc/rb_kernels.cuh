@@ -759,7 +759,7 @@ struct ColStepTArgs {
 
 __host__ __device__ inline size_t colstepT_smem(int N, int Mz) {
   const int H = 3 * N / 2;
-  return sizeof(double) * (size_t)H * H + sizeof(double2) * (size_t)(6 * (Mz / 2) + H + H);
+  return sizeof(double) * (size_t)H * H + sizeof(double2) * (size_t)(6 * (Mz / 2) + H + H + 3 * N);
 }
 
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256) rb_colstepT_kernel(const __grid_constant__ ColStepTArgs S) {
@@ -839,23 +839,29 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256) rb_colstepT_ker
   }
   cluster.sync();
   const double2* vo = cluster.map_shared_rank(vc, 1 - cls);
+  // the expanded vector al0 c0 + al1 v of each field, even (cx[q][0][h]) and odd (cx[q][1][h])
+  // modes, formed once here instead of once per output row
+  double2* cx = vc + H;  // [3][2][Nh]
+  for (int idx = tid; idx < 3 * N; idx += nt) {
+    const int q = idx / N, par = (idx / Nh) & 1, h = idx % Nh;
+    const int even_cta = (q == 0) ? 0 : 1;
+    const double2* v = ((even_cta == cls) == (par == 0) ? vc : vo) + q * Nh;
+    const double2 c = S.c0[((size_t)q * Kx + m) * N + 2 * h + par];
+    cx[idx] = make_double2(fma(S.al0, c.x, S.al1 * v[h].x), fma(S.al0, c.y, S.al1 * v[h].y));
+  }
+  __syncthreads();
   const int jh = (Mh + 1) / 2;
   const int j0 = cls == 0 ? 0 : jh, j1 = cls == 0 ? jh : Mh;
   for (int idx = tid; idx < 3 * (j1 - j0); idx += nt) {
     const int q = idx / (j1 - j0), j = j0 + idx % (j1 - j0);
     const double* grow = S.gzTE + (size_t)j * N;
-    const int even_cta = (q == 0) ? 0 : 1;
-    const double2* ve = (even_cta == cls ? vc : vo) + q * Nh;
-    const double2* vd = (even_cta == cls ? vo : vc) + q * Nh;
-    const double2* c0 = S.c0 + ((size_t)q * Kx + m) * N;
+    const double2* xe = cx + (size_t)q * N;
+    const double2* xo = xe + Nh;
     double2 E = make_double2(0.0, 0.0), O = make_double2(0.0, 0.0);
     for (int h = 0; h < Nh; ++h) {
       const double ge = __ldg(grow + 2 * h), go = __ldg(grow + 2 * h + 1);
-      const double2 ce = c0[2 * h], co = c0[2 * h + 1];
-      const double2 xe = make_double2(fma(S.al0, ce.x, S.al1 * ve[h].x), fma(S.al0, ce.y, S.al1 * ve[h].y));
-      const double2 xo = make_double2(fma(S.al0, co.x, S.al1 * vd[h].x), fma(S.al0, co.y, S.al1 * vd[h].y));
-      E.x = fma(ge, xe.x, E.x); E.y = fma(ge, xe.y, E.y);
-      O.x = fma(go, xo.x, O.x); O.y = fma(go, xo.y, O.y);
+      E.x = fma(ge, xe[h].x, E.x); E.y = fma(ge, xe[h].y, E.y);
+      O.x = fma(go, xo[h].x, O.x); O.y = fma(go, xo[h].y, O.y);
     }
     double2* out = S.zout + (size_t)q * S.nmix;
     out[(size_t)j * Kx + m] = make_double2(E.x + O.x, E.y + O.y);
