@@ -21,12 +21,17 @@ namespace {
 
 constexpr int kQMax = 4;  // modes per thread
 
+constexpr int kMaxOrder = 4;
+
 struct BurgersParams {
   int K, L, M;
   double nu, kscale, dt, length;
   int order, nonlinear;
   FFTPlan plan;
   const double2* WM;
+  // SBDF<s> weights, s = 1..kMaxOrder (row s-1): backward differentiation weights already divided
+  // by dt (no division in the step loops) and extrapolation weights of F
+  double wa[kMaxOrder][kMaxOrder + 1], wc[kMaxOrder][kMaxOrder + 1];
 };
 
 struct Smem {
@@ -206,25 +211,25 @@ __global__ void F_kernel(BurgersParams P, int mode, const double* __restrict__ x
 // Weights of step n (eq. imex with M = I, b_0 = 1, b_i = 0): SBDF<s>, s = min(n, order) (the
 // scheme starts at lower order while fewer past steps exist).  a: backward differentiation
 // weights (divided by dt), c: extrapolation weights of F; entries beyond s are zero.
-constexpr int kMaxOrder = 4;
 struct Coef {
   double a[kMaxOrder + 1], c[kMaxOrder + 1];
 };
-__constant__ double kSbdfA[kMaxOrder][kMaxOrder + 1] = {{1.0, -1.0, 0.0, 0.0, 0.0},
-                                                        {1.5, -2.0, 0.5, 0.0, 0.0},
-                                                        {11.0 / 6.0, -3.0, 1.5, -1.0 / 3.0, 0.0},
-                                                        {25.0 / 12.0, -4.0, 3.0, -4.0 / 3.0, 0.25}};
-__constant__ double kSbdfC[kMaxOrder][kMaxOrder + 1] = {{0.0, 1.0, 0.0, 0.0, 0.0},
-                                                        {0.0, 2.0, -1.0, 0.0, 0.0},
-                                                        {0.0, 3.0, -3.0, 1.0, 0.0},
-                                                        {0.0, 4.0, -6.0, 4.0, -1.0}};
+constexpr double kSbdfA[kMaxOrder][kMaxOrder + 1] = {{1.0, -1.0, 0.0, 0.0, 0.0},
+                                                     {1.5, -2.0, 0.5, 0.0, 0.0},
+                                                     {11.0 / 6.0, -3.0, 1.5, -1.0 / 3.0, 0.0},
+                                                     {25.0 / 12.0, -4.0, 3.0, -4.0 / 3.0, 0.25}};
+constexpr double kSbdfC[kMaxOrder][kMaxOrder + 1] = {{0.0, 1.0, 0.0, 0.0, 0.0},
+                                                     {0.0, 2.0, -1.0, 0.0, 0.0},
+                                                     {0.0, 3.0, -3.0, 1.0, 0.0},
+                                                     {0.0, 4.0, -6.0, 4.0, -1.0}};
+__device__ __forceinline__ int step_order(const BurgersParams& P, int n) { return n < P.order ? n : P.order; }
 __device__ __forceinline__ Coef step_coef(const BurgersParams& P, int n) {
   Coef c;
-  const int s = n < P.order ? n : P.order;
+  const int s = step_order(P, n);
 #pragma unroll
   for (int i = 0; i <= kMaxOrder; ++i) {
-    c.a[i] = kSbdfA[s - 1][i] / P.dt;
-    c.c[i] = kSbdfC[s - 1][i];
+    c.a[i] = P.wa[s - 1][i];
+    c.c[i] = P.wc[s - 1][i];
   }
   return c;
 }
@@ -288,13 +293,25 @@ __global__ void __launch_bounds__(64) trajectory_kernel(BurgersParams P, int n_s
       if (k < K) { F[q][0] = s.O[k]; if (tangent) GJ[q][0] = O2[k]; }
     }
   }
+  // nu k^2 per mode and 1 / (a_0 + nu k^2), recomputed only when the step order changes
+  double nk2[Q], inv_m[Q];
+  for (int q = 0; q < Q; ++q) {
+    const double kk = kwav(P, tid + q * G);
+    nk2[q] = P.nu * kk * kk;
+    inv_m[q] = 0.0;
+  }
+  int s_prev = 0;
   for (int n = 1; n <= n_steps; ++n) {
     Coef c = step_coef(P, n);
+    const int s_n = step_order(P, n);
+    if (s_n != s_prev) {
+      for (int q = 0; q < Q; ++q) inv_m[q] = 1.0 / (c.a[0] + nk2[q]);
+      s_prev = s_n;
+    }
     for (int q = 0; q < Q; ++q) {
       int k = tid + q * G;
       if (k >= K) continue;
-      double kk = kwav(P, k);
-      double inv = 1.0 / (c.a[0] + P.nu * kk * kk);
+      const double inv = inv_m[q];
       double2 xn = cscale(hist_rhs<ORD>(c, F[q], X[q]), inv);
       if (k == 0) xn.y = 0.0;
 #pragma unroll
@@ -343,6 +360,15 @@ __global__ void __launch_bounds__(64) adjoint_kernel(BurgersParams P, int n_step
   const size_t stride = (size_t)nb * 2 * K;
   double2 Y[Q][ORD];  // Y_{n+1}, ..., Y_{n+ORD}
   const double2 z = make_double2(0.0, 0.0);
+  // nu k^2 per mode and 1 / (a_0 + nu k^2) of the current step order (steps run backward, so the
+  // order changes only over the first steps)
+  double nk2[Q], inv_m[Q];
+  for (int q = 0; q < Q; ++q) {
+    const double kk = kwav(P, tid + q * G);
+    nk2[q] = P.nu * kk * kk;
+    inv_m[q] = 0.0;
+  }
+  int s_prev = 0;
   for (int q = 0; q < Q; ++q)
 #pragma unroll
     for (int i = 0; i < ORD; ++i) Y[q][i] = z;
@@ -400,12 +426,16 @@ __global__ void __launch_bounds__(64) adjoint_kernel(BurgersParams P, int n_step
       }
       return;
     }
-    Coef c = step_coef(P, n);
+    const int s_n = step_order(P, n);
+    if (s_n != s_prev) {
+      const Coef c = step_coef(P, n);
+      for (int q = 0; q < Q; ++q) inv_m[q] = 1.0 / (c.a[0] + nk2[q]);
+      s_prev = s_n;
+    }
     for (int q = 0; q < Q; ++q) {
       int k = tid + q * G;
       if (k >= K) continue;
-      double kk = kwav(P, k);
-      double2 y = cscale(lam[q], 1.0 / (c.a[0] + P.nu * kk * kk));
+      double2 y = cscale(lam[q], inv_m[q]);
       if (k == 0) y.y = 0.0;
 #pragma unroll
       for (int i = ORD - 1; i > 0; --i) Y[q][i] = Y[q][i - 1];
@@ -476,6 +506,11 @@ struct Burgers : EqImpl {
       default: return p->fail(SPADJ_ERR_UNSUPPORTED, "burgers: scheme must be SBDF1, SBDF2, SBDF3 or SBDF4");
     }
     P.nonlinear = d.nonlinear;
+    for (int s = 0; s < kMaxOrder; ++s)
+      for (int i = 0; i <= kMaxOrder; ++i) {
+        P.wa[s][i] = kSbdfA[s][i] / P.dt;
+        P.wc[s][i] = kSbdfC[s][i];
+      }
     P.plan = make_plan(P.L);
     if (P.plan.nrad < 0) return p->fail(SPADJ_ERR_INVALID, "burgers: 3N/4 must be of the form 2^a 3^b");
     if (P.K > kQMax * G) return p->fail(SPADJ_ERR_INVALID, "burgers: n[0] too large (max 512)");
