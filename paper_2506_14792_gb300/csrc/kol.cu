@@ -58,6 +58,8 @@ struct KolArgs {
   const KMember* mem;
   KRes res[kMaxRes];
   double Re, dt;
+  double invRe;      // 1 / Re
+  double kc[2][5];   // SBDF1 (row 0) and SBDF2 (row 1): a0, a1, a2 (divided by dt), c1, c2
   int CW, RW;
   int nCAtot, nBtot;
   int adjoint;      // 0 forward, 1 adjoint
@@ -92,11 +94,10 @@ __device__ __forceinline__ double2 ldcg2(const double2* p) { return __ldcg(p); }
 struct Coef {
   double a0, a1, a2, c1, c2;
 };
-__device__ __forceinline__ Coef kcoef(int n, double dt) {  // SBDF1 at n = 1, SBDF2 after
-  Coef c;
-  if (n <= 1) { c.a0 = 1.0 / dt; c.a1 = -1.0 / dt; c.a2 = 0.0; c.c1 = 1.0; c.c2 = 0.0; }
-  else { c.a0 = 1.5 / dt; c.a1 = -2.0 / dt; c.a2 = 0.5 / dt; c.c1 = 2.0; c.c2 = -1.0; }
-  return c;
+// SBDF1 at n = 1, SBDF2 after; the weights come divided by dt from the host (no division here)
+__device__ __forceinline__ Coef kcoef(int n, const double (&kc)[2][5]) {
+  const double* w = kc[n <= 1 ? 0 : 1];
+  return Coef{w[0], w[1], w[2], w[3], w[4]};
 }
 
 // ky of coefficient row q, and its index in the length-M y-FFT (-1 for the unstored Nyquist)
@@ -166,7 +167,7 @@ __device__ void ca_forward(const KolArgs& A, const KMember& m, int tile, int s) 
         for (int j = threadIdx.x; j < M; j += blockDim.x) ca[j] = ldcg2(&A.mixB[0][m.off_mix + (long long)j * Kx + kx]);
         r = col_fft<-1>(ca, cb, R);
       }
-      const Coef c = kcoef(s, A.dt);
+      const Coef c = kcoef(s, A.kc);
       const double invM = 1.0 / M;
       for (int q = threadIdx.x; q < N; q += blockDim.x) {
         const int idx = yidx(q, N, M);
@@ -187,7 +188,7 @@ __device__ void ca_forward(const KolArgs& A, const KMember& m, int tile, int s) 
           num.y += c.c2 * F2.y - c.a2 * X2.y;
         }
         A.Fr[(s - 1) & 1][col + q] = F;
-        const double inv = 1.0 / (c.a0 + ((double)kx * kx + ky * ky) / A.Re);
+        const double inv = 1.0 / (c.a0 + ((double)kx * kx + ky * ky) * A.invRe);
         xc[q] = make_double2(num.x * inv, num.y * inv);
       }
       __syncthreads();
@@ -318,8 +319,8 @@ __device__ void ca_adjoint(const KolArgs& A, const KMember& m, int tile, int n) 
       }
     }
     const int si = A.seed_at ? A.seed_at[n] : -1;
-    const Coef c1 = (n + 1 <= SN) ? kcoef(n + 1, A.dt) : Coef{0, 0, 0, 0, 0};
-    const Coef c2 = (n + 2 <= SN) ? kcoef(n + 2, A.dt) : Coef{0, 0, 0, 0, 0};
+    const Coef c1 = (n + 1 <= SN) ? kcoef(n + 1, A.kc) : Coef{0, 0, 0, 0, 0};
+    const Coef c2 = (n + 2 <= SN) ? kcoef(n + 2, A.kc) : Coef{0, 0, 0, 0, 0};
     for (int q = threadIdx.x; q < N; q += blockDim.x) {
       double2 l = lam[q];
       if (si >= 0) {
@@ -343,16 +344,16 @@ __device__ void ca_adjoint(const KolArgs& A, const KMember& m, int tile, int n) 
       continue;
     }
     project_col(lam, N, kx);
-    const Coef cn = kcoef(n, A.dt);
+    const Coef cn = kcoef(n, A.kc);
     for (int q = threadIdx.x; q < N; q += blockDim.x) {
       const double ky = kyof(q, N);
-      const double inv = 1.0 / (cn.a0 + ((double)kx * kx + ky * ky) / A.Re);
+      const double inv = 1.0 / (cn.a0 + ((double)kx * kx + ky * ky) * A.invRe);
       yc[q] = make_double2(lam[q].x * inv, lam[q].y * inv);
     }
     __syncthreads();
     // W_{n-1} = c1^n Y_n + c2^{n+1} Y_{n+1}, read Y_{n+1} before Y_n overwrites Y_{n+2}
-    const Coef cw1 = kcoef(n, A.dt);
-    const Coef cw2 = (n + 1 <= SN) ? kcoef(n + 1, A.dt) : Coef{0, 0, 0, 0, 0};
+    const Coef cw1 = kcoef(n, A.kc);
+    const Coef cw2 = (n + 1 <= SN) ? kcoef(n + 1, A.kc) : Coef{0, 0, 0, 0, 0};
     for (int q = threadIdx.x; q < N; q += blockDim.x) {
       double2 w = make_double2(cw1.c1 * yc[q].x, cw1.c1 * yc[q].y);
       if (n + 1 <= SN) {
@@ -759,6 +760,10 @@ struct Kol : EqImpl {
     A.mem = dmem.as<KMember>();
     for (int i = 0; i < kMaxRes; ++i) A.res[i] = kres[i];
     A.Re = Re; A.dt = dt; A.CW = CW; A.RW = RW;
+    A.invRe = 1.0 / Re;
+    const double kc[2][5] = {{1.0 / dt, -1.0 / dt, 0.0, 1.0, 0.0}, {1.5 / dt, -2.0 / dt, 0.5 / dt, 2.0, -1.0}};
+    for (int r = 0; r < 2; ++r)
+      for (int i = 0; i < 5; ++i) A.kc[r][i] = kc[r][i];
     A.nCAtot = nCAtot(); A.nBtot = nBtot();
     A.forcing = forcing; A.nonlinear = nonlinear;
     for (int i = 0; i < 2; ++i) { A.Xr[i] = Xr[i].as<double2>(); A.Fr[i] = Fr[i].as<double2>(); A.Yr[i] = Yr[i].as<double2>(); }
