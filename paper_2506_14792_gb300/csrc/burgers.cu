@@ -519,10 +519,15 @@ struct Burgers : EqImpl {
       double th = -2.0 * M_PI * (double)m / (double)P.M;
       h[m] = make_double2(std::cos(th), std::sin(th));
     }
-    SPADJ_CUDA_TRY(p, wm.ensure(sizeof(double2) * P.M));
-    SPADJ_CUDA_TRY(p, cudaMemcpyAsync(wm.ptr, h.data(), sizeof(double2) * P.M, cudaMemcpyHostToDevice, p->stream));
+    {  // the butterflies' scaled-twiddle records follow the M-table in the same buffer
+      const std::vector<double2> sct = scaled_twiddle_table(P.plan);
+      h.insert(h.end(), sct.begin(), sct.end());
+    }
+    SPADJ_CUDA_TRY(p, wm.ensure(sizeof(double2) * h.size()));
+    SPADJ_CUDA_TRY(p, cudaMemcpyAsync(wm.ptr, h.data(), sizeof(double2) * h.size(), cudaMemcpyHostToDevice, p->stream));
     SPADJ_CUDA_TRY(p, cudaStreamSynchronize(p->stream));
     P.WM = wm.as<double2>();
+    bind_scaled_twiddles(P.plan, P.WM + P.M);
     smem = sizeof(double2) * (4 * P.L + 4 * P.K);
     return SPADJ_OK;
   }

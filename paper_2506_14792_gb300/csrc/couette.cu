@@ -49,7 +49,7 @@ struct Couette : EqImpl {
   bool res_built = false;
   size_t zsmem = 0, xsmem = 0, ysmem = 0;
   rbhost::Operators ops;
-  int xnb = 1;  // x-FFT rows per CTA (tuned at creation)
+  int xnb = 1;  // x-FFT launch variant, xvar(rows per CTA, threads) (tuned at creation)
 
   size_t state_len(int which) const override {
     if (which == 0) return 2 * ns;
@@ -137,6 +137,11 @@ struct Couette : EqImpl {
       const double th = -2.0 * M_PI * (double)m / (double)(2 * My);
       hwy[m] = make_double2(std::cos(th), std::sin(th));
     }
+    {  // the butterflies' scaled-twiddle records follow each twiddle table in its buffer
+      const std::vector<double2> sx = scaled_twiddle_table(xp.plan), sy = scaled_twiddle_table(yp.plan);
+      hwx.insert(hwx.end(), sx.begin(), sx.end());
+      hwy.insert(hwy.end(), sy.begin(), sy.end());
+    }
     const double hone = 1.0;
     auto up = [&](DevBuf& b, const void* h, size_t bytes) -> cudaError_t {
       cudaError_t e = b.ensure(bytes);
@@ -162,6 +167,8 @@ struct Couette : EqImpl {
     SPADJ_CUDA_TRY(p, cudaStreamSynchronize(p->stream));
     xp.WM = wmx.as<double2>();
     yp.W2 = w2y.as<double2>();
+    bind_scaled_twiddles(xp.plan, xp.WM + Mx);
+    bind_scaled_twiddles(yp.plan, yp.W2 + 2 * My);
     const size_t sb = sizeof(double2) * ns, gb = sizeof(double) * npts;
     SPADJ_CUDA_TRY(p, Zm.ensure(6 * sizeof(double2) * nzm));
     SPADJ_CUDA_TRY(p, Ym.ensure(6 * sizeof(double2) * nym));

@@ -5,19 +5,41 @@
 // so a 3/2-dealiased grid of 384 points costs one 192-point complex FFT.  The complex
 // FFT is a Stockham autosort (ping-pong between two shared buffers, natural order in
 // and out) with radix-4/3/2 passes; all threads of the CTA take part and every pass
-// ends with a CTA barrier.  Twiddles come from a device table
-//   WM[m] = exp(-2 pi i m / M),  m = 0..M-1,
-// whose even entries are the L-point twiddles exp(-2 pi i m / L).
+// ends with a CTA barrier.  The real pre/post-processing takes its twiddles from a device table
+//   WM[m] = exp(-2 pi i m / M),  m = 0..M-1;
+// the twiddled butterflies take theirs from the plan's scaled-twiddle records (below).
+//
+// Scaled twiddles (the multiply-add butterflies of S. Goedecker, SIAM J. Sci. Comput. 18 (1997)
+// 1605): a twiddle w = c + i s acts on v as
+//   w v = lambda (v + tau i v),  lambda = c,   tau = s / c    where |c| >= |s|,
+//                                lambda = i s, tau = -c / s   otherwise,
+// so |tau| <= 1 and lambda is real or imaginary.  q = v + tau i v is two multiply-adds, and a
+// real-or-imaginary coefficient folds into the multiply-add that applies it (an imaginary one
+// swaps the components and carries the sign in its per-component scales; no FP64 instruction).
+// With the ratios of the lambdas precomputed, a twiddled radix-4 butterfly takes 22 FP64
+// instructions (28 with complex products), radix-3 16 (20) and radix-2 6 (8): the FP64 pipe
+// is the binding resource of every transform here.
 #pragma once
 #include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <vector>
 
 namespace spadj {
 
 struct FFTPlan {
-  int n;        // complex length L
-  int nrad;     // number of passes
-  int rad[8];   // radix of each pass (product = n)
+  int n;                  // complex length L
+  int nrad;               // number of passes
+  unsigned char rad[8];   // radix of each pass (product = n)
+  const double2* sc[2];   // device scaled-twiddle records: [0] exp(-), [1] exp(+)
 };
+
+// double2 entries of one record (one twiddle index k of a pass) for radix R
+__host__ __device__ constexpr int sc_rec(int R) { return R == 2 ? 2 : 6; }
+// double2 entries of a pass's records (Ns = product of the earlier radices; none for Ns = 1);
+// a pass's records start after those of the earlier passes
+__host__ __device__ constexpr int sc_pass_entries(int R, int Ns) { return Ns > 1 ? Ns * sc_rec(R) : 0; }
 
 // Factor n = 2^a 3^b into radix-4 passes, then one radix-2 if a is odd, then radix-3.
 inline FFTPlan make_plan(int n) {
@@ -29,6 +51,108 @@ inline FFTPlan make_plan(int n) {
   while (m % 3 == 0) { p.rad[p.nrad++] = 3; m /= 3; }
   if (m != 1) p.nrad = -1;  // unsupported length
   return p;
+}
+
+// ---- host: scaled-twiddle records ---------------------------------------------------------
+//
+// Record of pass (R, Ns) and index k, for the twiddles w_m = exp(SIGN 2 pi i m k / (R Ns)) with
+// forms (lambda_m, tau_m); a real-or-imaginary coefficient is stored as its per-component
+// scales (r, r) (real r) or (-r, r) (imaginary i r, applied to the swapped components), and
+// a flag word (an int64 in a double slot) says which are imaginary:
+//   radix 4: (tau1, tau2) (tau3, flags) lambda2 rho=lambda3/lambda1 lambda1 kappa=SIGN i lambda1
+//   radix 3: (tau1, tau2) rho=lambda2/lambda1 lambda1 -lambda1/2 kappa=(sqrt3/2) SIGN i lambda1
+//            (flags, 0)
+//   radix 2: (tau1, flags) lambda1
+// flags: bit 0 lambda2, bit 1 rho, bit 2 lambda1 imaginary (kappa is then real).  Passes with
+// Ns = 1 have no twiddles and no records.
+struct ScCoef {
+  bool im;
+  double r;
+};
+inline ScCoef sc_form(double c, double s, double* tau) {
+  if (std::fabs(c) >= std::fabs(s)) { *tau = s / c; return {false, c}; }
+  *tau = -c / s;
+  return {true, s};
+}
+inline ScCoef sc_div(ScCoef a, ScCoef b) {  // a / b
+  if (a.im == b.im) return {false, a.r / b.r};
+  return a.im ? ScCoef{true, a.r / b.r} : ScCoef{true, -a.r / b.r};
+}
+inline ScCoef sc_times_i(ScCoef a, double s) { return a.im ? ScCoef{false, -s * a.r} : ScCoef{true, s * a.r}; }
+inline double2 sc_scales(ScCoef a) { return a.im ? make_double2(-a.r, a.r) : make_double2(a.r, a.r); }
+inline double sc_flags(long long f) {
+  double d;
+  std::memcpy(&d, &f, sizeof d);
+  return d;
+}
+
+// double2 entries of one direction's records
+inline int scaled_twiddle_entries(const FFTPlan& p) {
+  int e = 0, Ns = 1;
+  for (int pass = 0; pass < p.nrad; ++pass) {
+    e += sc_pass_entries(p.rad[pass], Ns);
+    Ns *= p.rad[pass];
+  }
+  return e;
+}
+
+// Both directions' records (exp(-) first, then exp(+)), each in pass order; upload them and
+// call bind_scaled_twiddles with the device copy.
+inline std::vector<double2> scaled_twiddle_table(const FFTPlan& p) {
+  std::vector<double2> t[2];
+  const double pi = 3.14159265358979323846;
+  for (int dir = 0; dir < 2; ++dir) {
+    const int SIGN = dir == 0 ? -1 : 1;
+    int Ns = 1;
+    for (int pass = 0; pass < p.nrad; ++pass) {
+      const int R = p.rad[pass];
+      if (Ns > 1) {
+        for (int k = 0; k < Ns; ++k) {
+          ScCoef lam[4];
+          double tau[4] = {0, 0, 0, 0};
+          for (int m = 1; m < R; ++m) {
+            const double th = SIGN * 2.0 * pi * (double)(m * k) / (double)(R * Ns);
+            lam[m] = sc_form(std::cos(th), std::sin(th), &tau[m]);
+          }
+          std::vector<double2>& o = t[dir];
+          if (R == 4) {
+            const ScCoef rho = sc_div(lam[3], lam[1]), kap = sc_times_i(lam[1], SIGN);
+            const long long f = (lam[2].im ? 1 : 0) | (rho.im ? 2 : 0) | (lam[1].im ? 4 : 0);
+            o.push_back(make_double2(tau[1], tau[2]));
+            o.push_back(make_double2(tau[3], sc_flags(f)));
+            o.push_back(sc_scales(lam[2]));
+            o.push_back(sc_scales(rho));
+            o.push_back(sc_scales(lam[1]));
+            o.push_back(sc_scales(kap));
+          } else if (R == 3) {
+            const ScCoef rho = sc_div(lam[2], lam[1]);
+            const ScCoef half = {lam[1].im, -0.5 * lam[1].r};
+            const ScCoef kap = sc_times_i(lam[1], 0.86602540378443864676 * SIGN);
+            const long long f = (rho.im ? 2 : 0) | (lam[1].im ? 4 : 0);
+            o.push_back(make_double2(tau[1], tau[2]));
+            o.push_back(sc_scales(rho));
+            o.push_back(sc_scales(lam[1]));
+            o.push_back(sc_scales(half));
+            o.push_back(sc_scales(kap));
+            o.push_back(make_double2(sc_flags(f), 0.0));
+          } else {
+            const long long f = lam[1].im ? 4 : 0;
+            o.push_back(make_double2(tau[1], sc_flags(f)));
+            o.push_back(sc_scales(lam[1]));
+          }
+        }
+      }
+      Ns *= R;
+    }
+  }
+  std::vector<double2> all(t[0]);
+  all.insert(all.end(), t[1].begin(), t[1].end());
+  if (all.empty()) all.push_back(make_double2(0.0, 0.0));  // one-pass plans: keep a valid pointer
+  return all;
+}
+inline void bind_scaled_twiddles(FFTPlan& p, const double2* dev) {
+  p.sc[0] = dev;
+  p.sc[1] = dev + scaled_twiddle_entries(p);
 }
 
 __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
@@ -59,70 +183,145 @@ __device__ __forceinline__ double2 r2c_combine(double2 zk, double2 zc, double2 w
   return cscale(r2c_combine2(zk, zc, w), 0.5);
 }
 
-// Twiddle exp(SIGN * 2 pi i m / L) from the M-table (M = 2L): entry 2m, conjugated for SIGN=+1.
-template <int SIGN>
-__device__ __forceinline__ double2 twL(const double2* __restrict__ WM, int m) {
-  double2 w = __ldg(&WM[2 * m]);
-  return SIGN > 0 ? cconj(w) : w;
-}
 // SIGN * i * a (exact: a swap and a sign change, no multiply)
 template <int SIGN>
 __device__ __forceinline__ double2 rot(double2 a) {
   return SIGN > 0 ? make_double2(-a.y, a.x) : make_double2(a.y, -a.x);
 }
 
+// ---- device: butterflies ------------------------------------------------------------------
+
+// Components swapped when the coefficient applied to them is imaginary.
+__device__ __forceinline__ double2 sc_swap(double2 z, bool im) { return im ? make_double2(z.y, z.x) : z; }
+// u + zeta z and u - zeta z for zeta with per-component scales a, z already swapped as zeta asks
+__device__ __forceinline__ double2 sc_add(double2 u, double2 a, double2 z) {
+  return make_double2(fma(a.x, z.x, u.x), fma(a.y, z.y, u.y));
+}
+__device__ __forceinline__ double2 sc_sub(double2 u, double2 a, double2 z) {
+  return make_double2(fma(-a.x, z.x, u.x), fma(-a.y, z.y, u.y));
+}
+// v + tau i v
+__device__ __forceinline__ double2 sc_q(double2 v, double t) { return make_double2(fma(-t, v.y, v.x), fma(t, v.x, v.y)); }
+__device__ __forceinline__ long long sc_flagword(double d) { return __double_as_longlong(d); }
+
+// Twiddled radix-4 butterfly in place (outputs in input order), record r: 22 multiply-adds.
+//   A, B = v0 +- w2 v2;  lambda1 (E, F) = w1 v1 +- w3 v3;  y0, y2 = A +- lambda1 E;
+//   y1, y3 = B +- SIGN i lambda1 F
+__device__ __forceinline__ void sc_bfly4(double2& v0, double2& v1, double2& v2, double2& v3,
+                                         const double2* __restrict__ r) {
+  const double2 t12 = __ldg(r), t3f = __ldg(r + 1);
+  const long long f = sc_flagword(t3f.y);
+  const double2 q1 = sc_q(v1, t12.x);
+  const double2 q2 = sc_swap(sc_q(v2, t12.y), f & 1);
+  const double2 q3 = sc_swap(sc_q(v3, t3f.x), f & 2);
+  const double2 l2 = __ldg(r + 2), rho = __ldg(r + 3), l1 = __ldg(r + 4), kap = __ldg(r + 5);
+  const double2 A = sc_add(v0, l2, q2), B = sc_sub(v0, l2, q2);
+  const double2 E = sc_swap(sc_add(q1, rho, q3), f & 4), F = sc_swap(sc_sub(q1, rho, q3), !(f & 4));
+  v0 = sc_add(A, l1, E);
+  v2 = sc_sub(A, l1, E);
+  v1 = sc_add(B, kap, F);
+  v3 = sc_sub(B, kap, F);
+}
+// Twiddled radix-3 butterfly in place, record r: 16 multiply-adds.
+//   lambda1 (E, F) = w1 v1 +- w2 v2;  y0 = v0 + lambda1 E;  M = v0 - lambda1 E / 2;
+//   y1, y2 = M +- (sqrt3/2) SIGN i lambda1 F
+__device__ __forceinline__ void sc_bfly3(double2& v0, double2& v1, double2& v2, const double2* __restrict__ r) {
+  const double2 t12 = __ldg(r);
+  const long long f = sc_flagword(__ldg(&r[5].x));
+  const double2 q1 = sc_q(v1, t12.x);
+  const double2 q2 = sc_swap(sc_q(v2, t12.y), f & 2);
+  const double2 rho = __ldg(r + 1), l1 = __ldg(r + 2), hl = __ldg(r + 3), kap = __ldg(r + 4);
+  const double2 E = sc_swap(sc_add(q1, rho, q2), f & 4), F = sc_swap(sc_sub(q1, rho, q2), !(f & 4));
+  const double2 M = sc_add(v0, hl, E);
+  v0 = sc_add(v0, l1, E);
+  v1 = sc_add(M, kap, F);
+  v2 = sc_sub(M, kap, F);
+}
+// Twiddled radix-2 butterfly in place, record r: 6 multiply-adds.
+__device__ __forceinline__ void sc_bfly2(double2& v0, double2& v1, const double2* __restrict__ r) {
+  const double2 t = __ldg(r), l1 = __ldg(r + 1);
+  const double2 q = sc_swap(sc_q(v1, t.x), sc_flagword(t.y) & 4);
+  const double2 y0 = sc_add(v0, l1, q);
+  v1 = sc_sub(v0, l1, q);
+  v0 = y0;
+}
+// Butterflies of the first pass (Ns = 1: no twiddles).
+template <int SIGN>
+__device__ __forceinline__ void bfly4(double2& v0, double2& v1, double2& v2, double2& v3) {
+  const double2 t0 = cadd(v0, v2), t1 = csub(v0, v2), t2 = cadd(v1, v3);
+  const double2 t3 = rot<SIGN>(csub(v1, v3));
+  v0 = cadd(t0, t2);
+  v1 = cadd(t1, t3);
+  v2 = csub(t0, t2);
+  v3 = csub(t1, t3);
+}
+template <int SIGN>
+__device__ __forceinline__ void bfly3(double2& v0, double2& v1, double2& v2) {
+  const double h = 0.86602540378443864676;  // sqrt(3)/2
+  const double2 t = cadd(v1, v2);
+  const double2 m = make_double2(fma(-0.5, t.x, v0.x), fma(-0.5, t.y, v0.y));
+  const double2 r = rot<SIGN>(csub(v1, v2));  // m +- h r as multiply-adds
+  v0 = cadd(v0, t);
+  v1 = make_double2(fma(h, r.x, m.x), fma(h, r.y, m.y));
+  v2 = make_double2(fma(-h, r.x, m.x), fma(-h, r.y, m.y));
+}
+__device__ __forceinline__ void bfly2(double2& v0, double2& v1) {
+  const double2 y0 = cadd(v0, v1);
+  v1 = csub(v0, v1);
+  v0 = y0;
+}
+
+// One butterfly of a Stockham pass: R inputs through ld(e), outputs through st(e, v).
+template <int SIGN, class Ld, class St>
+__device__ __forceinline__ void stockham_bfly(int R, int Ns, int j, int nbf, const double2* __restrict__ rec,
+                                              Ld ld, St st) {
+  const int k = j % Ns;
+  const int base = (j - k) * R + k;
+  if (R == 4) {
+    double2 v0 = ld(j), v1 = ld(j + nbf), v2 = ld(j + 2 * nbf), v3 = ld(j + 3 * nbf);
+    if (Ns > 1) sc_bfly4(v0, v1, v2, v3, rec + sc_rec(4) * k);
+    else bfly4<SIGN>(v0, v1, v2, v3);
+    st(base, v0);
+    st(base + Ns, v1);
+    st(base + 2 * Ns, v2);
+    st(base + 3 * Ns, v3);
+  } else if (R == 2) {
+    double2 v0 = ld(j), v1 = ld(j + nbf);
+    if (Ns > 1) sc_bfly2(v0, v1, rec + sc_rec(2) * k);
+    else bfly2(v0, v1);
+    st(base, v0);
+    st(base + Ns, v1);
+  } else {  // R == 3
+    double2 v0 = ld(j), v1 = ld(j + nbf), v2 = ld(j + 2 * nbf);
+    if (Ns > 1) sc_bfly3(v0, v1, v2, rec + sc_rec(3) * k);
+    else bfly3<SIGN>(v0, v1, v2);
+    st(base, v0);
+    st(base + Ns, v1);
+    st(base + 2 * Ns, v2);
+  }
+}
+
 // Complex FFT of length p.n held in buffer a (b is scratch of the same size).  SIGN = -1:
 // forward exp(-), SIGN = +1: inverse exp(+) (unnormalised).  Returns the buffer holding
 // the result (a or b).  All threads of the CTA must call it; it synchronises internally
-// and on return the result is visible to every thread.
+// and on return the result is visible to every thread.  The WM argument is unused (the
+// butterflies read the plan's scaled-twiddle records); it stays for the callers' symmetry
+// with the real pre/post-processing.
 template <int SIGN>
 static __device__ __noinline__ double2* cfft_smem_t(double2* a, double2* b, const FFTPlan p,
                                                     const double2* __restrict__ WM) {
   const int n = p.n;
   const int tid = threadIdx.x, nt = blockDim.x;
   int Ns = 1;
+  const double2* __restrict__ rec = p.sc[SIGN > 0 ? 1 : 0];
   for (int pass = 0; pass < p.nrad; ++pass) {
     const int R = p.rad[pass];
-    const int nb = n / R;
-    const int tstep = n / (Ns * R);  // twiddle index stride in L-units
-    for (int j = tid; j < nb; j += nt) {
-      const int k = j % Ns;
-      const int base = (j - k) * R + k;
-      if (R == 4) {
-        double2 v0 = a[j], v1 = a[j + nb], v2 = a[j + 2 * nb], v3 = a[j + 3 * nb];
-        if (k) {
-          v1 = cmul(v1, twL<SIGN>(WM, k * tstep));
-          v2 = cmul(v2, twL<SIGN>(WM, 2 * k * tstep));
-          v3 = cmul(v3, twL<SIGN>(WM, 3 * k * tstep));
-        }
-        const double2 t0 = cadd(v0, v2), t1 = csub(v0, v2), t2 = cadd(v1, v3);
-        const double2 t3 = rot<SIGN>(csub(v1, v3));
-        b[base] = cadd(t0, t2);
-        b[base + Ns] = cadd(t1, t3);
-        b[base + 2 * Ns] = csub(t0, t2);
-        b[base + 3 * Ns] = csub(t1, t3);
-      } else if (R == 2) {
-        double2 v0 = a[j], v1 = a[j + nb];
-        if (k) v1 = cmul(v1, twL<SIGN>(WM, k * tstep));
-        b[base] = cadd(v0, v1);
-        b[base + Ns] = csub(v0, v1);
-      } else {  // R == 3
-        double2 v0 = a[j], v1 = a[j + nb], v2 = a[j + 2 * nb];
-        if (k) {
-          v1 = cmul(v1, twL<SIGN>(WM, k * tstep));
-          v2 = cmul(v2, twL<SIGN>(WM, 2 * k * tstep));
-        }
-        const double h = 0.86602540378443864676;  // sqrt(3)/2
-        const double2 t = cadd(v1, v2);
-        const double2 m = make_double2(fma(-0.5, t.x, v0.x), fma(-0.5, t.y, v0.y));
-        const double2 r = rot<SIGN>(csub(v1, v2));  // m +- h r as multiply-adds
-        b[base] = cadd(v0, t);
-        b[base + Ns] = make_double2(fma(h, r.x, m.x), fma(h, r.y, m.y));
-        b[base + 2 * Ns] = make_double2(fma(-h, r.x, m.x), fma(-h, r.y, m.y));
-      }
-    }
+    const int nbf = n / R;
+    for (int j = tid; j < nbf; j += nt)
+      stockham_bfly<SIGN>(R, Ns, j, nbf, rec, [&](int e) { return a[e]; }, [&](int e, double2 v) { b[e] = v; });
     __syncthreads();
     double2* tmp = a; a = b; b = tmp;
+    rec += sc_pass_entries(R, Ns);
     Ns *= R;
   }
   return a;
@@ -137,51 +336,18 @@ static __device__ __noinline__ double2* cfft_smem_batch(double2* a, double2* b, 
   const int n = p.n;
   const int tid = threadIdx.x, nt = blockDim.x;
   int Ns = 1;
+  const double2* __restrict__ rec = p.sc[SIGN > 0 ? 1 : 0];
   for (int pass = 0; pass < p.nrad; ++pass) {
     const int R = p.rad[pass];
     const int nbf = n / R;
-    const int tstep = n / (Ns * R);
     for (int idx = tid; idx < nbf * nb; idx += nt) {
       const int j = idx / nb, c = idx - j * nb;
-      const int k = j % Ns;
-      const int base = (j - k) * R + k;
-      auto A = [&](int e) -> double2 { return a[e * nb + c]; };
-      auto Bw = [&](int e, double2 v) { b[e * nb + c] = v; };
-      if (R == 4) {
-        double2 v0 = A(j), v1 = A(j + nbf), v2 = A(j + 2 * nbf), v3 = A(j + 3 * nbf);
-        if (k) {
-          v1 = cmul(v1, twL<SIGN>(WM, k * tstep));
-          v2 = cmul(v2, twL<SIGN>(WM, 2 * k * tstep));
-          v3 = cmul(v3, twL<SIGN>(WM, 3 * k * tstep));
-        }
-        const double2 t0 = cadd(v0, v2), t1 = csub(v0, v2), t2 = cadd(v1, v3);
-        const double2 t3 = rot<SIGN>(csub(v1, v3));
-        Bw(base, cadd(t0, t2));
-        Bw(base + Ns, cadd(t1, t3));
-        Bw(base + 2 * Ns, csub(t0, t2));
-        Bw(base + 3 * Ns, csub(t1, t3));
-      } else if (R == 2) {
-        double2 v0 = A(j), v1 = A(j + nbf);
-        if (k) v1 = cmul(v1, twL<SIGN>(WM, k * tstep));
-        Bw(base, cadd(v0, v1));
-        Bw(base + Ns, csub(v0, v1));
-      } else {
-        double2 v0 = A(j), v1 = A(j + nbf), v2 = A(j + 2 * nbf);
-        if (k) {
-          v1 = cmul(v1, twL<SIGN>(WM, k * tstep));
-          v2 = cmul(v2, twL<SIGN>(WM, 2 * k * tstep));
-        }
-        const double h = 0.86602540378443864676;
-        const double2 t = cadd(v1, v2);
-        const double2 m = make_double2(fma(-0.5, t.x, v0.x), fma(-0.5, t.y, v0.y));
-        const double2 r = rot<SIGN>(csub(v1, v2));
-        Bw(base, cadd(v0, t));
-        Bw(base + Ns, make_double2(fma(h, r.x, m.x), fma(h, r.y, m.y)));
-        Bw(base + 2 * Ns, make_double2(fma(-h, r.x, m.x), fma(-h, r.y, m.y)));
-      }
+      stockham_bfly<SIGN>(R, Ns, j, nbf, rec, [&](int e) { return a[e * nb + c]; },
+                          [&](int e, double2 v) { b[e * nb + c] = v; });
     }
     __syncthreads();
     double2* tmp = a; a = b; b = tmp;
+    rec += sc_pass_entries(R, Ns);
     Ns *= R;
   }
   return a;

@@ -679,27 +679,40 @@ struct Kol : EqImpl {
     grid_size = offg;
     // twiddle tables per resolution: WMx (M entries) then W2M (2M entries)
     std::vector<double2> ht;
-    std::vector<size_t> toff;
-    for (int N : resN) {
+    std::vector<size_t> toff, soff;
+    for (size_t i = 0; i < resN.size(); ++i) {
+      const int M = 3 * resN[i] / 2;
+      kres[i].px = make_plan(M / 2);
+      kres[i].py = make_plan(M);
+    }
+    for (size_t i = 0; i < resN.size(); ++i) {
+      const int N = resN[i];
       const int M = 3 * N / 2;
       toff.push_back(ht.size());
-      for (int i = 0; i < M; ++i) {
-        const double th = -2.0 * M_PI * i / M;
+      for (int m = 0; m < M; ++m) {
+        const double th = -2.0 * M_PI * m / M;
         ht.push_back(make_double2(std::cos(th), std::sin(th)));
       }
-      for (int i = 0; i < 2 * M; ++i) {
-        const double th = -2.0 * M_PI * i / (2.0 * M);
+      for (int m = 0; m < 2 * M; ++m) {
+        const double th = -2.0 * M_PI * m / (2.0 * M);
         ht.push_back(make_double2(std::cos(th), std::sin(th)));
       }
+      // the butterflies' scaled-twiddle records of the x and y plans
+      soff.push_back(ht.size());
+      const std::vector<double2> sx = scaled_twiddle_table(kres[i].px);
+      ht.insert(ht.end(), sx.begin(), sx.end());
+      soff.push_back(ht.size());
+      const std::vector<double2> sy = scaled_twiddle_table(kres[i].py);
+      ht.insert(ht.end(), sy.begin(), sy.end());
     }
     SPADJ_CUDA_TRY(p, tables.ensure(sizeof(double2) * ht.size()));
     SPADJ_CUDA_TRY(p, cudaMemcpyAsync(tables.ptr, ht.data(), sizeof(double2) * ht.size(), cudaMemcpyHostToDevice, p->stream));
     for (size_t i = 0; i < resN.size(); ++i) {
       const int M = 3 * resN[i] / 2;
-      kres[i].px = make_plan(M / 2);
-      kres[i].py = make_plan(M);
       kres[i].WMx = tables.as<double2>() + toff[i];
       kres[i].W2M = tables.as<double2>() + toff[i] + M;
+      bind_scaled_twiddles(kres[i].px, tables.as<double2>() + soff[2 * i]);
+      bind_scaled_twiddles(kres[i].py, tables.as<double2>() + soff[2 * i + 1]);
     }
     const size_t sb = sizeof(double2) * state_size, mb = sizeof(double2) * mix_size;
     for (int i = 0; i < 2; ++i) {

@@ -78,7 +78,7 @@ struct RB : EqImpl {
   WS* w = &ws[0];
   size_t zsmem = 0, xsmem = 0, ssmem = 0, csmem = 0, ctsmem = 0;
   bool fused = false;  // fused column stage (rb_colstep_kernel) usable for these sizes
-  int xnb = 1;         // x-FFT rows per CTA (tuned at creation)
+  int xnb = 1;         // x-FFT launch variant, xvar(rows per CTA, threads) (tuned at creation)
   // internal streams (joined to the caller's stream by events) and captured step graphs
   cudaStream_t gs = nullptr, gs2 = nullptr, gsB = nullptr;
   cudaEvent_t evIn = nullptr, evOut = nullptr, evFork = nullptr, evJoin = nullptr;
@@ -171,12 +171,16 @@ struct RB : EqImpl {
       const double th = -2.0 * M_PI * (double)m / (double)Mx;
       hwm[m] = make_double2(std::cos(th), std::sin(th));
     }
+    {  // the butterflies' scaled-twiddle records follow the M-table in the same buffer
+      const std::vector<double2> sct = scaled_twiddle_table(xp.plan);
+      hwm.insert(hwm.end(), sct.begin(), sct.end());
+    }
     auto up = [&](DevBuf& b, const void* h, size_t bytes) -> cudaError_t {
       cudaError_t e = b.ensure(bytes);
       if (e != cudaSuccess) return e;
       return cudaMemcpyAsync(b.ptr, h, bytes, cudaMemcpyHostToDevice, p->stream);
     };
-    SPADJ_CUDA_TRY(p, up(wm, hwm.data(), sizeof(double2) * Mx));
+    SPADJ_CUDA_TRY(p, up(wm, hwm.data(), sizeof(double2) * hwm.size()));
     SPADJ_CUDA_TRY(p, up(czE, hczE.data(), sizeof(double) * hczE.size()));
     SPADJ_CUDA_TRY(p, up(cdzE, hcdzE.data(), sizeof(double) * hcdzE.size()));
     SPADJ_CUDA_TRY(p, up(gzF, hgzF.data(), sizeof(double) * hgzF.size()));
@@ -190,6 +194,7 @@ struct RB : EqImpl {
       if (s != SPADJ_OK) return s;
     }
     xp.WM = wm.as<double2>();
+    bind_scaled_twiddles(xp.plan, xp.WM + Mx);
     // work buffers
     const size_t sb = sizeof(double2) * ns, mb = sizeof(double2) * nmix, gb = sizeof(double) * npts;
     for (WS& l : ws) {
