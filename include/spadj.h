@@ -253,7 +253,8 @@ spadj_status spadj_set_params(spadj_problem* prob, const double* params);
  * stream order); option 7 (SPADJ_RB2D) = fused column stage (1, default: the z fold, the stage
  * solve and the z expansion of each x-mode pencil run in one two-CTA cluster kernel; 0: three
  * separate kernels); option 8 (SPADJ_RB2D, SPADJ_COUETTE3D) = grid rows per CTA of the x FFTs
- * (1, 2 or 4; by default the fastest is picked by timing when the problem is created); option 9
+ * (1, 2 or 4, 64 threads per CTA; by default the fastest of these and of 2 or 4 rows on 96, 128
+ * or 192 threads is picked by timing when the problem is created); option 9
  * (SPADJ_RB2D, SPADJ_COUETTE3D) = host checkpoint slots of spadj_gradient / spadj_vjp (0, default:
  * device slots only; h > 0: the two-level schedule of spadj_checkpoint_schedule_host, the host
  * copies in page-locked memory owned by the problem).  Set them before the first sweep (the step

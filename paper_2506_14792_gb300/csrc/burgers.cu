@@ -93,10 +93,16 @@ __device__ void eval_F(const BurgersParams& P, Smem& s) {
 // From the primal spectrum S and the tangent spectrum S2: O <- F(S) (if want_F) and
 // O2 <- (dF/dX)(S) S2 = -i k T[(B S)(B S2)].
 __device__ void eval_F_and_jvp(const BurgersParams& P, Smem& s, const double2* S2, double2* O2, bool want_F) {
-  double2* u = c2g_packed(P, s.S, s.A, s.B, 1.0, 1.0);
-  double2* du = c2g_packed(P, S2, s.C, s.D, 1.0, 1.0);
-  double2* uo = (u == s.A) ? s.B : s.A;
-  double2* duo = (du == s.C) ? s.D : s.C;
+  // both inverse transforms in the same FFT passes (A|B and C|D are 2L apart)
+  c2r_pre(s.A, [&](int k) { return s.S[k]; }, P.K, P.L, P.WM, 1.0, 1.0);
+  c2r_pre(s.C, [&](int k) { return S2[k]; }, P.K, P.L, P.WM, 1.0, 1.0);
+  __syncthreads();
+  cfft_smem_sets<1>(s.A, s.B, 2 * P.L, 2, P.plan, 1);
+  const bool odd = P.plan.nrad & 1;
+  double2* u = odd ? s.B : s.A;
+  double2* du = odd ? s.D : s.C;
+  double2* uo = odd ? s.A : s.B;
+  double2* duo = odd ? s.C : s.D;
   for (int j = threadIdx.x; j < P.L; j += blockDim.x) {
     double2 v = u[j], dv = du[j];
     du[j] = make_double2(v.x * dv.x, v.y * dv.y);
@@ -118,16 +124,24 @@ __device__ void eval_F_and_jvp(const BurgersParams& P, Smem& s, const double2* S
 
 // O <- (dF/dX)(S)^dagger W  with W staged in S2:  B^dagger[(B S) * T^dagger(i k W)]
 __device__ void eval_vjp(const BurgersParams& P, Smem& s, double2* S2) {
-  double2* u = c2g_packed(P, s.S, s.A, s.B, 1.0, 1.0);
-  // S2 <- i k W (in place, own entries only)
+  // S2 <- i k W / (2M) (in place, own entries only): T^dagger's weights (1/M on the real part of
+  // k = 0, 1/(2M) elsewhere) folded in, the k = 0 entry being 0
+  const double q = 0.5 / P.M;
   for (int k = threadIdx.x; k < P.K; k += blockDim.x) {
     double2 w = S2[k];
-    double kk = kwav(P, k);
+    double kk = kwav(P, k) * q;
     S2[k] = make_double2(-kk * w.y, kk * w.x);
   }
   __syncthreads();
-  double2* v = c2g_packed(P, S2, s.C, s.D, 1.0 / P.M, 0.5 / P.M);
-  double2* vo = (v == s.C) ? s.D : s.C;
+  // both inverse transforms in the same FFT passes (A|B and C|D are 2L apart)
+  c2r_pre(s.A, [&](int k) { return s.S[k]; }, P.K, P.L, P.WM, 1.0, 1.0);
+  c2r_pre(s.C, [&](int k) { return S2[k]; }, P.K, P.L, P.WM, 1.0, 1.0);
+  __syncthreads();
+  cfft_smem_sets<1>(s.A, s.B, 2 * P.L, 2, P.plan, 1);
+  const bool odd = P.plan.nrad & 1;
+  double2* u = odd ? s.B : s.A;
+  double2* v = odd ? s.D : s.C;
+  double2* vo = odd ? s.C : s.D;
   for (int j = threadIdx.x; j < P.L; j += blockDim.x) {
     double2 a = u[j], b = v[j];
     v[j] = make_double2(a.x * b.x, a.y * b.y);

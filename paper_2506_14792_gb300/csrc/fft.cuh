@@ -353,6 +353,36 @@ static __device__ __noinline__ double2* cfft_smem_batch(double2* a, double2* b, 
   return a;
 }
 
+// ns sets of nb interleaved complex FFTs of length p.n (the layout of cfft_smem_batch), set s
+// held in a + s * stride with scratch b + s * stride: the sets' butterflies share every pass and
+// its barrier, and together fill more lanes than one set.  The results are in a (+ s * stride)
+// when p.nrad is even, else in b.
+template <int SIGN>
+static __device__ __noinline__ void cfft_smem_sets(double2* a, double2* b, int stride, int ns, const FFTPlan p,
+                                                   int nb) {
+  const int n = p.n;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  int Ns = 1;
+  const double2* __restrict__ rec = p.sc[SIGN > 0 ? 1 : 0];
+  for (int pass = 0; pass < p.nrad; ++pass) {
+    const int R = p.rad[pass];
+    const int nbf = n / R;
+    const int per = nbf * nb;
+    for (int idx = tid; idx < per * ns; idx += nt) {
+      const int set = idx / per, i = idx - set * per;
+      const int j = i / nb, c = i - j * nb;
+      const double2* as = a + set * stride;
+      double2* bs = b + set * stride;
+      stockham_bfly<SIGN>(R, Ns, j, nbf, rec, [&](int e) { return as[e * nb + c]; },
+                          [&](int e, double2 v) { bs[e * nb + c] = v; });
+    }
+    __syncthreads();
+    double2* tmp = a; a = b; b = tmp;
+    rec += sc_pass_entries(R, Ns);
+    Ns *= R;
+  }
+}
+
 __device__ __forceinline__ double2* cfft_smem(double2* a, double2* b, const FFTPlan p, const double2* __restrict__ WM,
                                               int sign) {
   return sign > 0 ? cfft_smem_t<1>(a, b, p, WM) : cfft_smem_t<-1>(a, b, p, WM);

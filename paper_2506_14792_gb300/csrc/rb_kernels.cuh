@@ -289,9 +289,14 @@ __global__ void __launch_bounds__(64) xfft_kernel(const __grid_constant__ XJobs 
       }
     }
     __syncthreads();
-    double2* z0 = cfft_smem(A, B, P.plan, P.WM, -1);
-    double2* z1 = nullptr;
-    if (J.nr > 1) z1 = cfft_smem(C, D, P.plan, P.WM, -1);
+    double2 *z0, *z1 = nullptr;
+    if (J.nr > 1) {  // both inputs' transforms in the same passes (A|B and C|D are 2L apart)
+      cfft_smem_sets<-1>(A, B, 2 * L, 2, P.plan, 1);
+      z0 = (P.plan.nrad & 1) ? B : A;
+      z1 = (P.plan.nrad & 1) ? D : C;
+    } else {
+      z0 = cfft_smem(A, B, P.plan, P.WM, -1);
+    }
     double2* dst = J.cout + (size_t)row * Kx;
     // r2c post-processing for each input, combined
     for (int k = threadIdx.x; k < Kx; k += blockDim.x) {
@@ -313,10 +318,11 @@ __global__ void __launch_bounds__(64) xfft_kernel(const __grid_constant__ XJobs 
   }
 }
 
+constexpr int kXThreadsMax = 192;
 // xfft_kernel's jobs for nb rows per CTA (nb <= 4): the rows are interleaved in shared memory
 // (element e of row c at e * nb + c) and transformed together by cfft_smem_batch, so short rows
 // keep all threads of the CTA busy in every Stockham pass and share its barriers.
-__global__ void __launch_bounds__(64) xfftm_kernel(const __grid_constant__ XJobs js, XParams P, int nb, int nrows) {
+__global__ void __launch_bounds__(kXThreadsMax) xfftm_kernel(const __grid_constant__ XJobs js, XParams P, int nb, int nrows) {
   pdl_trigger();
   pdl_wait();
   const XJob& J = js.j[blockIdx.y];
@@ -390,8 +396,9 @@ __global__ void __launch_bounds__(64) xfftm_kernel(const __grid_constant__ XJobs
     if (nin > 1) C[j * nb + c] = v1;
   }
   __syncthreads();
-  const double2* z0 = cfft_smem_batch<-1>(A, B, P.plan, P.WM, nb);
-  const double2* z1 = nin > 1 ? cfft_smem_batch<-1>(C, D, P.plan, P.WM, nb) : nullptr;
+  cfft_smem_sets<-1>(A, B, 2 * L * nb, nin, P.plan, nb);  // A|B and C|D are 2 L nb apart
+  const double2* z0 = (P.plan.nrad & 1) ? B : A;
+  const double2* z1 = (P.plan.nrad & 1) ? D : C;
   for (int idx = tid; idx < nb * Kx; idx += nt) {
     const int c = idx / Kx, k = idx - c * Kx;
     if (row0 + c >= nrows) continue;
@@ -415,55 +422,68 @@ __global__ void __launch_bounds__(64) xfftm_kernel(const __grid_constant__ XJobs
 inline size_t xfftm_smem(int L, int Kx, int nb) { return sizeof(double2) * (size_t)nb * (4 * L + Kx); }
 constexpr int kXRowsMax = 4;
 
-// x-transform jobs over nrows rows with nb rows per CTA (nb = 1: xfft_kernel)
-inline cudaError_t launch_xfft(bool pdl, int nb, const XJobs& js, const XParams& xp, int nrows, cudaStream_t st) {
-  if (nb <= 1)
+// Launch variant of the x transforms: rows per CTA nb (low byte) and threads per CTA nt (the
+// bits above; 0 = 64).  nb = 1 with 64 threads is xfft_kernel, everything else xfftm_kernel.
+// Threads per CTA that are a multiple of the butterflies of a pass keep every lane busy in
+// it: for L = 192 (radix 4, 4, 4, 3: 48, 48, 48, 64 butterflies per row) that is 96 threads
+// on two rows or 192 on four.
+constexpr int xvar(int nb, int nt) { return nb | (nt << 8); }
+constexpr int xvar_rows(int xv) { return xv & 0xff; }
+constexpr int xvar_threads(int xv) { return (xv >> 8) ? (xv >> 8) : 64; }
+
+// x-transform jobs over nrows rows in launch variant xv
+inline cudaError_t launch_xfft(bool pdl, int xv, const XJobs& js, const XParams& xp, int nrows, cudaStream_t st) {
+  const int nb = xvar_rows(xv) < 1 ? 1 : xvar_rows(xv), nt = xvar_threads(xv);
+  if (nb == 1 && nt == 64)
     return launch_kernel(pdl, xfft_kernel, dim3(nrows, js.n), dim3(64), xfftm_smem(xp.L, xp.Kx, 1), st, js, xp);
-  return launch_kernel(pdl, xfftm_kernel, dim3((nrows + nb - 1) / nb, js.n), dim3(64), xfftm_smem(xp.L, xp.Kx, nb), st,
+  return launch_kernel(pdl, xfftm_kernel, dim3((nrows + nb - 1) / nb, js.n), dim3(nt), xfftm_smem(xp.L, xp.Kx, nb), st,
                        js, xp, nb, nrows);
 }
 
-// Rows per CTA for the x transforms of this problem: `forced` (1, 2 or 4) or, when 0, the
-// fastest of 1, 2, 4 on the problem's own job set (timed with CUDA events, first run of each
-// discarded).  Also raises the shared-memory limit of the multi-row kernel when needed.
+// Launch variant for the x transforms of this problem: rows `forced` (1, 2 or 4, 64 threads)
+// or, when 0, the fastest of the candidates below on the problem's own job set (timed with
+// CUDA events, first run of each discarded).  Also raises the shared-memory limit of the
+// kernels when needed.
 inline int tune_xfft_rows(const XJobs& js, const XParams& xp, int nrows, cudaStream_t st, int forced,
                           cudaError_t* err) {
   *err = cudaSuccess;
-  // candidates whose shared memory fits one CTA (raising the opt-in limit where needed)
+  // row counts whose shared memory fits one CTA (raising the opt-in limit where needed)
   bool ok[kXRowsMax + 1] = {false, false, false, false, false};
   for (int nb : {1, 2, 4}) {
     const size_t sm = xfftm_smem(xp.L, xp.Kx, nb);
     if (sm <= 48 * 1024) {
       ok[nb] = true;
     } else if (sm <= 227 * 1024) {
-      cudaError_t e = nb == 1 ? cudaFuncSetAttribute(xfft_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)
-                              : cudaFuncSetAttribute(xfftm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      cudaError_t e = cudaFuncSetAttribute(xfftm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      if (e == cudaSuccess && nb == 1)
+        e = cudaFuncSetAttribute(xfft_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
       ok[nb] = e == cudaSuccess;
       cudaGetLastError();
     }
   }
-  if (forced == 1 || forced == 2 || forced == 4) return forced;
-  if (!ok[1]) return 1;  // rows too long for any variant: launches will report the error
+  if (forced == 1 || forced == 2 || forced == 4) return xvar(forced, 64);
+  if (!ok[1]) return xvar(1, 64);  // rows too long for any variant: launches will report the error
   cudaEvent_t a = nullptr, b = nullptr;
-  if ((*err = cudaEventCreate(&a)) != cudaSuccess) return 1;
-  if ((*err = cudaEventCreate(&b)) != cudaSuccess) { cudaEventDestroy(a); return 1; }
-  int best_nb = 1;
+  if ((*err = cudaEventCreate(&a)) != cudaSuccess) return xvar(1, 64);
+  if ((*err = cudaEventCreate(&b)) != cudaSuccess) { cudaEventDestroy(a); return xvar(1, 64); }
+  int best_xv = xvar(1, 64);
   float best = 1e30f;
-  for (int nb : {1, 2, 4}) {
-    if (!ok[nb]) continue;
+  constexpr int cand[] = {xvar(1, 64), xvar(2, 64), xvar(4, 64), xvar(2, 96), xvar(4, 96), xvar(4, 128), xvar(4, 192)};
+  for (int xv : cand) {
+    if (!ok[xvar_rows(xv)]) continue;
     for (int rep = 0; rep < 4 && *err == cudaSuccess; ++rep) {
       cudaEventRecord(a, st);
-      *err = launch_xfft(false, nb, js, xp, nrows, st);
+      *err = launch_xfft(false, xv, js, xp, nrows, st);
       cudaEventRecord(b, st);
       if (*err == cudaSuccess) *err = cudaEventSynchronize(b);
       float ms = 0.f;
       if (*err == cudaSuccess) cudaEventElapsedTime(&ms, a, b);
-      if (rep > 0 && ms < best) { best = ms; best_nb = nb; }
+      if (rep > 0 && ms < best) { best = ms; best_xv = xv; }
     }
   }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
-  return best_nb;
+  return best_xv;
 }
 
 // Grid-field slots: 0 u, 1 ux, 2 uz, 3 w, 4 wx, 5 wz, 6 tx, 7 tz (the forward and tangent
