@@ -395,20 +395,24 @@ __device__ __forceinline__ double2* cfft_smem(double2* a, double2* b, const FFTP
 // Hermitian-completed spectrum with weights w0 (k = 0, real part only) and w (k >= 1):
 //   g_j = w0 Re c_0 + w * 2 Re sum_{k=1}^{K-1} c_k e^{2 pi i k j / M}
 // Fills Z (length L) so that the inverse L-point FFT of Z is z_j = g_{2j} + i g_{2j+1}.
+// Entry k (< L) of the packed spectrum described below (UNIT: w0 = w = 1).
+template <bool UNIT, class Get>
+__device__ __forceinline__ double2 c2r_entry(Get get, int k, int K, int L, const double2* __restrict__ WM, double w0,
+                                             double w) {
+  double2 xk = make_double2(0.0, 0.0), xc = make_double2(0.0, 0.0);
+  if (k == 0) {
+    xk = make_double2(UNIT ? get(0).x : w0 * get(0).x, 0.0);
+  } else if (k < K) {
+    xk = UNIT ? get(k) : cscale(get(k), w);
+  }
+  const int kc = L - k;  // partner index (k = 0 pairs with the unstored Nyquist L)
+  if (k > 0 && kc < K) xc = cconj(UNIT ? get(kc) : cscale(get(kc), w));
+  return c2r_combine(cadd(xk, xc), csub(xk, xc), __ldg(&WM[k]));  // e + i (xk - xc) exp(+2 pi i k / M)
+}
 template <bool UNIT, class Get>
 __device__ __forceinline__ void c2r_pre_t(double2* Z, Get get, int K, int L, const double2* __restrict__ WM,
                                           double w0, double w) {
-  for (int k = threadIdx.x; k < L; k += blockDim.x) {
-    double2 xk = make_double2(0.0, 0.0), xc = make_double2(0.0, 0.0);
-    if (k == 0) {
-      xk = make_double2(UNIT ? get(0).x : w0 * get(0).x, 0.0);
-    } else if (k < K) {
-      xk = UNIT ? get(k) : cscale(get(k), w);
-    }
-    const int kc = L - k;  // partner index (k = 0 pairs with the unstored Nyquist L)
-    if (k > 0 && kc < K) xc = cconj(UNIT ? get(kc) : cscale(get(kc), w));
-    Z[k] = c2r_combine(cadd(xk, xc), csub(xk, xc), __ldg(&WM[k]));  // e + i (xk - xc) exp(+2 pi i k / M)
-  }
+  for (int k = threadIdx.x; k < L; k += blockDim.x) Z[k] = c2r_entry<UNIT>(get, k, K, L, WM, w0, w);
 }
 template <class Get>
 __device__ __forceinline__ void c2r_pre(double2* Z, Get get, int K, int L, const double2* __restrict__ WM,

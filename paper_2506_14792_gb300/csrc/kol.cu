@@ -85,6 +85,7 @@ struct KolArgs {
   int* caDone;
   int* bDone;
   int* err;
+  int smem_entries;       // dynamic shared memory of a CTA, in double2
   unsigned spin_limit;    // bounded-wait iterations
   int drop_signal_member; // test knob: completion of this member is never signalled (-1: off)
 };
@@ -201,17 +202,33 @@ __device__ void ca_forward(const KolArgs& A, const KMember& m, int tile, int s) 
       if (s == A.S) A.out[col + q] = xc[q];
     }
     if (s < A.S && (A.nonlinear || A.closure)) {
+      // the fields' inverse y transforms two at a time, sharing their passes: set p at
+      // ks + 2 p M (scratch + M); the column is read back from the state just written, its
+      // shared slot being reused
       const int nf = A.closure ? 5 : 4;
-      for (int f = 0; f < nf; ++f) {
+      const double2* xs = A.Xr[s & 1] + col;
+      for (int f0 = 0; f0 < nf; f0 += 2) {
+        const int np = min(2, nf - f0);
         __syncthreads();
-        for (int j = threadIdx.x; j < M; j += blockDim.x) ca[j] = make_double2(0.0, 0.0);
-        __syncthreads();
-        for (int q = threadIdx.x; q < N; q += blockDim.x) {
-          const int idx = yidx(q, N, M);
-          if (idx >= 0) ca[idx] = f < 4 ? fmult(f, (double)kx, (double)kyof(q, N), xc[q]) : xc[q];
+        for (int i = threadIdx.x; i < np * M; i += blockDim.x) {
+          const int pq = i / M;
+          ks[pq * 2 * M + (i - pq * M)] = make_double2(0.0, 0.0);
         }
-        double2* r = col_fft<1>(ca, cb, R);
-        for (int j = threadIdx.x; j < M; j += blockDim.x) A.mixA[f][m.off_mix + (long long)j * Kx + kx] = r[j];
+        __syncthreads();
+        for (int i = threadIdx.x; i < np * N; i += blockDim.x) {
+          const int pq = i / N, q = i - pq * N, f = f0 + pq;
+          const int idx = yidx(q, N, M);
+          if (idx < 0) continue;
+          const double2 x = ldcg2(&xs[q]);
+          ks[pq * 2 * M + idx] = f < 4 ? fmult(f, (double)kx, (double)kyof(q, N), x) : x;
+        }
+        __syncthreads();
+        cfft_smem_sets<1>(ks, ks + M, 2 * M, np, R.py, 1);
+        const double2* r = (R.py.nrad & 1) ? ks + M : ks;
+        for (int i = threadIdx.x; i < np * M; i += blockDim.x) {
+          const int pq = i / M, j = i - pq * M;
+          A.mixA[f0 + pq][m.off_mix + (long long)j * Kx + kx] = r[pq * 2 * M + j];
+        }
       }
     }
     __syncthreads();
@@ -247,36 +264,74 @@ __device__ void row_r2c(double2* row, double2* scratch, double2* dst, const KMem
   __syncthreads();
 }
 
+// Inverse x transforms of nf mixed rows at once (weights 1): spectrum f (Kx entries from src(f))
+// is staged in base + (2f+1) L, its packed spectrum built in base + 2f L, and the nf FFTs share
+// their passes (more butterflies per pass than threads in one row's, one barrier per pass for
+// all).  Returns the slot of field 0's packed grid row; field f's is 2 f L further.
+template <class Src>
+__device__ double2* rows_c2r_sets(double2* base, int nf, Src src, const KMember& m, const KRes& R) {
+  const int Kx = m.Kx, L = m.L;
+  for (int idx = threadIdx.x; idx < nf * Kx; idx += blockDim.x) {
+    const int f = idx / Kx, k = idx - f * Kx;
+    base[(2 * f + 1) * L + k] = ldcg2(&src(f)[k]);
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < nf * L; idx += blockDim.x) {
+    const int f = idx / L, k = idx - f * L;
+    const double2* S = base + (2 * f + 1) * L;
+    base[2 * f * L + k] = c2r_entry<true>([&](int i) { return S[i]; }, k, Kx, L, R.WMx, 1.0, 1.0);
+  }
+  __syncthreads();
+  cfft_smem_sets<1>(base, base + L, 2 * L, nf, R.px, 1);
+  return (R.px.nrad & 1) ? base + L : base;
+}
+
+// Forward x transforms of nf packed grid rows at once: row f at a + 2 f L (destroyed), scratch at
+// b + 2 f L; put(f, k, 2 X_k) for k < Kx (the unpacking's 1/2 is left to put).
+template <class Put>
+__device__ void rows_r2c_sets(double2* a, double2* b, int nf, Put put, const KMember& m, const KRes& R) {
+  const int Kx = m.Kx, L = m.L;
+  cfft_smem_sets<-1>(a, b, 2 * L, nf, R.px, 1);
+  const double2* z = (R.px.nrad & 1) ? b : a;
+  for (int idx = threadIdx.x; idx < nf * Kx; idx += blockDim.x) {
+    const int f = idx / Kx, k = idx - f * Kx;
+    const double2* Z = z + 2 * f * L;
+    put(f, k, r2c_combine2(Z[k], cconj(Z[k == 0 ? 0 : L - k]), __ldg(&R.WMx[k])));
+  }
+  __syncthreads();
+}
+
 // ---- forward B tile ---------------------------------------------------------------------------
 __device__ void b_forward(const KolArgs& A, const KMember& m, int tile) {
   extern __shared__ double2 ks[];
   const int Kx = m.Kx, M = m.M, L = m.L;
   const KRes& R = A.res[m.res];
-  double2* G = ks;            // 4 L
-  double2* sa = G + 4 * L;    // L
-  double2* sb = sa + L;       // L
-  double2* st = sb + L;       // Kx
+  // ks[0, 8L): four transform sets (field f: slots 2f, 2f+1 of L entries); ks[8L, 8L+Kx): staging
+  double2* st = ks + 8 * L;
   const int j0 = tile * A.RW, j1 = min(M, j0 + A.RW);
   const double invM = 1.0 / M;
   for (int j = j0; j < j1; ++j) {
     if (A.closure) {
-      row_c2r(A.mixA[4] + m.off_mix + (long long)j * Kx, sa, sa, sb, st, m, R, 1.0, 1.0);
+      row_c2r(A.mixA[4] + m.off_mix + (long long)j * Kx, ks, ks, ks + L, st, m, R, 1.0, 1.0);
       double2* gw = reinterpret_cast<double2*>(A.gridW + m.off_grid + (long long)j * M);
-      for (int i = threadIdx.x; i < L; i += blockDim.x) gw[i] = sa[i];
+      for (int i = threadIdx.x; i < L; i += blockDim.x) gw[i] = ks[i];
       __syncthreads();
     }
+    double2 *prod = ks, *scratch = ks + L;
     if (A.nonlinear) {
-      for (int f = 0; f < 4; ++f)
-        row_c2r(A.mixA[f] + m.off_mix + (long long)j * Kx, G + f * L, sa, sb, st, m, R, 1.0, 1.0);
+      // u, v, w_x, w_y on the grid row, then u w_x + v w_y into the free slot of field 0
+      const double2* r = rows_c2r_sets(ks, 4, [&](int f) { return A.mixA[f] + m.off_mix + (long long)j * Kx; }, m, R);
+      prod = (r == ks) ? ks + L : ks;
+      scratch = prod + 2 * L;
       for (int i = threadIdx.x; i < L; i += blockDim.x) {
-        const double2 u = G[i], v = G[L + i], wx = G[2 * L + i], wy = G[3 * L + i];
-        sa[i] = make_double2(fma(u.x, wx.x, v.x * wy.x), fma(u.y, wx.y, v.y * wy.y));
+        const double2 u = r[i], v = r[2 * L + i], wx = r[4 * L + i], wy = r[6 * L + i];
+        prod[i] = make_double2(fma(u.x, wx.x, v.x * wy.x), fma(u.y, wx.y, v.y * wy.y));
       }
     } else {
-      for (int i = threadIdx.x; i < L; i += blockDim.x) sa[i] = make_double2(0.0, 0.0);
+      for (int i = threadIdx.x; i < L; i += blockDim.x) prod[i] = make_double2(0.0, 0.0);
     }
     __syncthreads();
-    row_r2c(sa, sb, A.mixB[0] + m.off_mix + (long long)j * Kx, m, R, invM, invM);
+    row_r2c(prod, scratch, A.mixB[0] + m.off_mix + (long long)j * Kx, m, R, invM, invM);
   }
 }
 
@@ -285,10 +340,13 @@ __device__ void ca_adjoint(const KolArgs& A, const KMember& m, int tile, int n) 
   extern __shared__ double2 ks[];
   const int N = m.N, Kx = m.Kx, M = m.M;
   const KRes& R = A.res[m.res];
-  double2* ca = ks;        // M
-  double2* cb = ca + M;    // M
-  double2* lam = cb + M;   // N
-  double2* yc = lam + N;   // N
+  // The VJP's forward y transforms run two at a time (sets at ks + 2 p M, scratch + M) when the
+  // accumulator lam fits beside them; otherwise one at a time in ks[0, 2M).
+  const bool pairs = 4 * M + N <= A.smem_entries;
+  double2* ca = ks;                             // M
+  double2* cb = ca + M;                         // M
+  double2* lam = pairs ? ks + 4 * M : cb + M;   // N
+  double2* yc = pairs ? ks + 2 * M : lam + N;   // N (used after the VJP)
   const int kx0 = tile * A.CW, kx1 = min(Kx, kx0 + A.CW);
   const long long S = A.state_size;
   const int SN = A.S;
@@ -299,21 +357,34 @@ __device__ void ca_adjoint(const KolArgs& A, const KMember& m, int tile, int n) 
     if (n < SN && (A.nonlinear || A.closure)) {
       // VJP: B_y^dagger of the grid cotangents, then the adjoint multipliers (identity for the
       // closure's input field)
-      for (int f = A.nonlinear ? 0 : 4; f < (A.closure ? 5 : 4); ++f) {
-        for (int j = threadIdx.x; j < M; j += blockDim.x) ca[j] = ldcg2(&A.mixB[f][m.off_mix + (long long)j * Kx + kx]);
-        double2* r = col_fft<-1>(ca, cb, R);
+      const int fa = A.nonlinear ? 0 : 4, fb = A.closure ? 5 : 4, per = pairs ? 2 : 1;
+      for (int f0 = fa; f0 < fb; f0 += per) {
+        const int np = min(per, fb - f0);
+        for (int i = threadIdx.x; i < np * M; i += blockDim.x) {
+          const int pq = i / M, j = i - pq * M;
+          ks[pq * 2 * M + j] = ldcg2(&A.mixB[f0 + pq][m.off_mix + (long long)j * Kx + kx]);
+        }
+        __syncthreads();
+        cfft_smem_sets<-1>(ks, ks + M, 2 * M, np, R.py, 1);
+        const double2* r = (R.py.nrad & 1) ? ks + M : ks;
         for (int q = threadIdx.x; q < N; q += blockDim.x) {
           const int idx = yidx(q, N, M);
           if (idx < 0) continue;
-          if (f == 4) {
-            lam[q].x += r[idx].x;
-            lam[q].y += r[idx].y;
-            continue;
+          double2 l = lam[q];
+          for (int pq = 0; pq < np; ++pq) {
+            const int f = f0 + pq;
+            const double2 v = r[pq * 2 * M + idx];
+            if (f == 4) {
+              l.x += v.x;
+              l.y += v.y;
+              continue;
+            }
+            // adjoint of i*s is -i*s: fmult with the negated multiplier
+            const double2 fv = fmult(f, (double)kx, (double)kyof(q, N), v);
+            l.x -= fv.x;
+            l.y -= fv.y;
           }
-          // adjoint of i*s is -i*s: fmult with the negated multiplier
-          const double2 v = fmult(f, (double)kx, (double)kyof(q, N), r[idx]);
-          lam[q].x -= v.x;
-          lam[q].y -= v.y;
+          lam[q] = l;
         }
         __syncthreads();
       }
@@ -378,20 +449,33 @@ __device__ void ca_adjoint(const KolArgs& A, const KMember& m, int tile, int n) 
       for (int j = threadIdx.x; j < M; j += blockDim.x)
         A.mixA[4][m.off_mix + (long long)j * Kx + kx] = make_double2(r[j].x * invM, r[j].y * invM);
     }
-    // fields of X_{n-1} from the trajectory
-    for (int q = threadIdx.x; q < N; q += blockDim.x) yc[q] = ldcg2(&A.traj[(long long)(n - 1) * S + col + q]);
-    for (int f = A.nonlinear ? 0 : 4; f < (A.closure ? 5 : 4); ++f) {
+    // fields of X_{n-1} from the trajectory, their inverse y transforms two at a time (sets at
+    // ks + 2 p M, scratch + M; 4M <= the CTA's shared memory for every member)
+    const double2* xs = A.traj + (long long)(n - 1) * S + col;
+    const int fa = A.nonlinear ? 0 : 4, fb = A.closure ? 5 : 4;
+    for (int f0 = fa; f0 < fb; f0 += 2) {
+      const int np = min(2, fb - f0);
       __syncthreads();
-      for (int j = threadIdx.x; j < M; j += blockDim.x) ca[j] = make_double2(0.0, 0.0);
-      __syncthreads();
-      for (int q = threadIdx.x; q < N; q += blockDim.x) {
-        const int idx = yidx(q, N, M);
-        if (idx >= 0) ca[idx] = f < 4 ? fmult(f, (double)kx, (double)kyof(q, N), yc[q]) : yc[q];
+      for (int i = threadIdx.x; i < np * M; i += blockDim.x) {
+        const int pq = i / M;
+        ks[pq * 2 * M + (i - pq * M)] = make_double2(0.0, 0.0);
       }
-      double2* r = col_fft<1>(ca, cb, R);
-      // the closure's input field goes to slot 5 (slot 4 holds T^dagger W)
-      double2* dstf = A.mixA[f < 4 ? f : 5];
-      for (int j = threadIdx.x; j < M; j += blockDim.x) dstf[m.off_mix + (long long)j * Kx + kx] = r[j];
+      __syncthreads();
+      for (int i = threadIdx.x; i < np * N; i += blockDim.x) {
+        const int pq = i / N, q = i - pq * N, f = f0 + pq;
+        const int idx = yidx(q, N, M);
+        if (idx < 0) continue;
+        const double2 x = ldcg2(&xs[q]);
+        ks[pq * 2 * M + idx] = f < 4 ? fmult(f, (double)kx, (double)kyof(q, N), x) : x;
+      }
+      __syncthreads();
+      cfft_smem_sets<1>(ks, ks + M, 2 * M, np, R.py, 1);
+      const double2* r = (R.py.nrad & 1) ? ks + M : ks;
+      for (int i = threadIdx.x; i < np * M; i += blockDim.x) {
+        const int pq = i / M, j = i - pq * M, f = f0 + pq;
+        // the closure's input field goes to slot 5 (slot 4 holds T^dagger W)
+        A.mixA[f < 4 ? f : 5][m.off_mix + (long long)j * Kx + kx] = r[pq * 2 * M + j];
+      }
     }
     __syncthreads();
   }
@@ -402,34 +486,49 @@ __device__ void b_adjoint(const KolArgs& A, const KMember& m, int tile) {
   extern __shared__ double2 ks[];
   const int Kx = m.Kx, M = m.M, L = m.L;
   const KRes& R = A.res[m.res];
-  double2* G = ks;            // 5 L: u, v, wx, wy, g
-  double2* sa = G + 5 * L;    // L
-  double2* sb = sa + L;       // L
-  double2* st = sb + L;       // Kx
+  // ks[0, 8L): four transform sets (field f: slots 2f, 2f+1 of L entries); ks[8L, 8L+Kx): staging
+  double2* st = ks + 8 * L;
   const int j0 = tile * A.RW, j1 = min(M, j0 + A.RW);
   for (int j = j0; j < j1; ++j) {
-    row_c2r(A.mixA[4] + m.off_mix + (long long)j * Kx, G + 4 * L, sa, sb, st, m, R, 1.0 / M, 0.5 / M);
-    if (A.closure) {  // closure input omega and the grid cotangent g, for the CNN's backward pass
-      row_c2r(A.mixA[5] + m.off_mix + (long long)j * Kx, sa, sa, sb, st, m, R, 1.0, 1.0);
+    if (!A.nonlinear) {  // closure only: omega and the grid cotangent g, for the CNN's backward pass
+      if (A.closure) {
+        row_c2r(A.mixA[4] + m.off_mix + (long long)j * Kx, ks, ks, ks + L, st, m, R, 1.0 / M, 0.5 / M);
+        row_c2r(A.mixA[5] + m.off_mix + (long long)j * Kx, ks + 2 * L, ks + 2 * L, ks + 3 * L, st, m, R, 1.0, 1.0);
+        double2* gw = reinterpret_cast<double2*>(A.gridW + m.off_grid + (long long)j * M);
+        double2* gg = reinterpret_cast<double2*>(A.gridG + m.off_grid + (long long)j * M);
+        for (int i = threadIdx.x; i < L; i += blockDim.x) { gw[i] = ks[2 * L + i]; gg[i] = ks[i]; }
+        __syncthreads();
+      }
+      continue;
+    }
+    // u, v, w_x, w_y in one set of transforms; the free slots F_f = fr + 2 f L take g (F_0, with
+    // F_1 as its scratch), the closure's omega (F_2, scratch F_3), then serve as the forward
+    // transforms' scratch
+    double2* r = rows_c2r_sets(ks, 4, [&](int f) { return A.mixA[f] + m.off_mix + (long long)j * Kx; }, m, R);
+    double2* fr = (r == ks) ? ks + L : ks;
+    row_c2r(A.mixA[4] + m.off_mix + (long long)j * Kx, fr, fr, fr + 2 * L, st, m, R, 1.0 / M, 0.5 / M);
+    if (A.closure) {
+      row_c2r(A.mixA[5] + m.off_mix + (long long)j * Kx, fr + 4 * L, fr + 4 * L, fr + 6 * L, st, m, R, 1.0, 1.0);
       double2* gw = reinterpret_cast<double2*>(A.gridW + m.off_grid + (long long)j * M);
       double2* gg = reinterpret_cast<double2*>(A.gridG + m.off_grid + (long long)j * M);
-      for (int i = threadIdx.x; i < L; i += blockDim.x) { gw[i] = sa[i]; gg[i] = G[4 * L + i]; }
+      for (int i = threadIdx.x; i < L; i += blockDim.x) { gw[i] = fr[4 * L + i]; gg[i] = fr[i]; }
       __syncthreads();
     }
-    if (!A.nonlinear) continue;
-    for (int f = 0; f < 4; ++f)
-      row_c2r(A.mixA[f] + m.off_mix + (long long)j * Kx, G + f * L, sa, sb, st, m, R, 1.0, 1.0);
     // grid cotangents of u, v, w_x, w_y: -g w_x, -g w_y, -g u, -g v
     for (int i = threadIdx.x; i < L; i += blockDim.x) {
-      const double2 u = G[i], v = G[L + i], wx = G[2 * L + i], wy = G[3 * L + i], g = G[4 * L + i];
-      G[i] = make_double2(-g.x * wx.x, -g.y * wx.y);
-      G[L + i] = make_double2(-g.x * wy.x, -g.y * wy.y);
-      G[2 * L + i] = make_double2(-g.x * u.x, -g.y * u.y);
-      G[3 * L + i] = make_double2(-g.x * v.x, -g.y * v.y);
+      const double2 u = r[i], v = r[2 * L + i], wx = r[4 * L + i], wy = r[6 * L + i], g = fr[i];
+      r[i] = make_double2(-g.x * wx.x, -g.y * wx.y);
+      r[2 * L + i] = make_double2(-g.x * wy.x, -g.y * wy.y);
+      r[4 * L + i] = make_double2(-g.x * u.x, -g.y * u.y);
+      r[6 * L + i] = make_double2(-g.x * v.x, -g.y * v.y);
     }
     __syncthreads();
-    for (int f = 0; f < 4; ++f)
-      row_r2c(G + f * L, sa, A.mixB[f] + m.off_mix + (long long)j * Kx, m, R, 1.0, 2.0);
+    rows_r2c_sets(r, fr, 4, [&](int f, int k, double2 v) {  // v = 2 X_k; scales 1 (k = 0), 2
+      const double sc = k == 0 ? 0.5 : 1.0;
+      double2 o = make_double2(v.x * sc, v.y * sc);
+      if (k == 0) o.y = 0.0;
+      A.mixB[f][m.off_mix + (long long)j * Kx + k] = o;
+    }, m, R);
   }
 }
 
@@ -750,8 +849,21 @@ struct Kol : EqImpl {
     }
     SPADJ_CUDA_TRY(p, ctr.ensure(sizeof(int) * (2 * (size_t)nmem + 2)));
     SPADJ_CUDA_TRY(p, tmp.ensure(sb));
-    // shared memory: max over tile kinds (B' needs 7 L + Kx, CA' needs 2 M + 2 N)
-    smem = sizeof(double2) * std::max<size_t>(8 * (size_t)Lmax + Kxmax, 2 * (size_t)Mmax + 2 * (size_t)Nmax);
+    // shared memory: max over tile kinds (B and B': 8 L + Kx, four transform sets and their
+    // staging; CA': 2 M + 2 N, or 4 M + N with its VJP transforms in pairs).  The paired form's
+    // size is taken when it keeps as many CTAs resident per SM.
+    {
+      const size_t base = sizeof(double2) * std::max<size_t>(8 * (size_t)Lmax + Kxmax, 2 * (size_t)Mmax + 2 * (size_t)Nmax);
+      const size_t ext = std::max<size_t>(base, sizeof(double2) * (4 * (size_t)Mmax + Nmax));
+      smem = base;
+      if (ext > base && ext <= 227 * 1024) {
+        int ob = 0, oe = 0;
+        SPADJ_CUDA_TRY(p, cudaFuncSetAttribute(kol_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ext));
+        SPADJ_CUDA_TRY(p, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ob, kol_persistent, kKolThreads, base));
+        SPADJ_CUDA_TRY(p, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&oe, kol_persistent, kKolThreads, ext));
+        if (oe >= ob) smem = ext;
+      }
+    }
     SPADJ_CUDA_TRY(p, cudaFuncSetAttribute(kol_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     SPADJ_CUDA_TRY(p, cudaFuncSetAttribute(kol_phase, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     layout();
@@ -789,6 +901,7 @@ struct Kol : EqImpl {
     int* c = ctr.as<int>();
     A.queue = c; A.err = c + 1; A.caDone = c + 2; A.bDone = c + 2 + nmem;
     A.spin_limit = spin_limit;
+    A.smem_entries = (int)(smem / sizeof(double2));
     A.drop_signal_member = drop_signal_member;
     return A;
   }
