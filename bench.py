@@ -61,20 +61,20 @@ TRAFFIC = {
     # the vector bytes (8x), averaged over the forward (5 vectors) and transposed (2) launches
     ("couette3d_128x64x64_Re1000_sbdf2_4000steps_gain", "pencil_solve"): 1.252e9,
     # xfft_kernel, one row per CTA (the setting the problem picks): dram read + write per launch on
-    # the RB capture (8-job 1.22 MB, 6-job 2.40 MB, 3-job 0.63 / 2.40 MB), weighted by the launch mix
+    # the RB capture (8-job 1.23 MB, 6-job 2.41 MB, 3-job 0.64 / 2.41 MB), weighted by the launch mix
     # of the gradient (484 : 200 : 200 : 380); the working set is L2-resident, so this is the
     # cold-cache fill ncu sees after its cache flush
-    ("rayleigh_benard2d_256x64_Ra1e6_rk222_2000steps", "x_fft"): 1.67e6,
+    ("rayleigh_benard2d_256x64_Ra1e6_rk222_2000steps", "x_fft"): 1.68e6,
     # evp_iter_kernel, full bench launch (608 pencils, 100 iterations): 32.07 GB read + 7.4 MB
     # written, against 35.9 GB of operator rows streamed by the algorithm (the rest hits in L2)
     ("poiseuille_evp_N64_608pencils_Re8000_100iter", "pencil_solve"): 3.2075e10,
-    # Burgers trajectory + adjoint kernels, captured at 50 steps (forward: 37 MB read + 1.66 GB of
-    # trajectory written; adjoint: 1.715 GB of trajectory read + 31 MB written), trajectory bytes
+    # Burgers trajectory + adjoint kernels, captured at 50 steps (forward: 36 MB read + 1.650 GB of
+    # trajectory written; adjoint: 1.715 GB of trajectory read + 44 MB written), trajectory bytes
     # scaled to 1000 steps by (1001 / 51), averaged over the two launches of a gradient
-    ("burgers1d_N256_sbdf2_1000steps", "fused_trajectory"): 3.32e10,
-    # kol_persistent, captured at 40 steps: 6.78 GB read + 4.87 GB written per sweep (trajectory
+    ("burgers1d_N256_sbdf2_1000steps", "fused_trajectory"): 3.31e10,
+    # kol_persistent, captured at 40 steps: 6.76 GB read + 4.88 GB written per sweep (trajectory
     # and checkpoint traffic of the 64 members), scaled to 2000 steps by 50
-    ("kolmogorov2d_batch64_mixed128-512_Re100_sbdf2_2000steps_4dvar8", "fused_trajectory"): 5.83e11,
+    ("kolmogorov2d_batch64_mixed128-512_Re100_sbdf2_2000steps_4dvar8", "fused_trajectory"): 5.82e11,
 }
 
 
