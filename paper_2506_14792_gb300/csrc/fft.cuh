@@ -41,15 +41,23 @@ __host__ __device__ constexpr int sc_rec(int R) { return R == 2 ? 2 : 6; }
 // a pass's records start after those of the earlier passes
 __host__ __device__ constexpr int sc_pass_entries(int R, int Ns) { return Ns > 1 ? Ns * sc_rec(R) : 0; }
 
-// Factor n = 2^a 3^b into radix-4 passes, then one radix-2 if a is odd, then radix-3.
+// Factor n = 2^a 3^b into radix-4 passes, then one radix-2 if a is odd, then radix-3; nrad = -1
+// for any other n and for more than 8 passes.
 inline FFTPlan make_plan(int n) {
   FFTPlan p{};
   p.n = n;
   int m = n;
-  while (m % 4 == 0) { p.rad[p.nrad++] = 4; m /= 4; }
-  if (m % 2 == 0) { p.rad[p.nrad++] = 2; m /= 2; }
-  while (m % 3 == 0) { p.rad[p.nrad++] = 3; m /= 3; }
-  if (m != 1) p.nrad = -1;  // unsupported length
+  auto push = [&](int r) {
+    if (p.nrad >= 8) return false;
+    p.rad[p.nrad++] = (unsigned char)r;
+    m /= r;
+    return true;
+  };
+  bool ok = n >= 1;
+  while (ok && m % 4 == 0) ok = push(4);
+  if (ok && m % 2 == 0) ok = push(2);
+  while (ok && m % 3 == 0) ok = push(3);
+  if (!ok || m != 1) p.nrad = -1;  // unsupported length
   return p;
 }
 

@@ -190,6 +190,33 @@ def _stockham(x, rad, passes, sign):
     return a
 
 
+PLANS = r'''
+#include <cstdio>
+#include <cstdlib>
+#include "fft.cuh"
+int main(int argc, char** argv) {
+  for (int a = 1; a < argc; ++a) std::printf("%d\n", spadj::make_plan(std::atoi(argv[a])).nrad);
+  return 0;
+}
+'''
+
+
+def test_plan_rejects_unsupported_lengths(tmp_path):
+    """Lengths that are not 2^a 3^b, or that would need more than the plan's eight passes, are
+    refused (nrad = -1) instead of overrunning the radix list."""
+    if shutil.which("nvcc") is None:
+        pytest.skip("nvcc not available")
+    (tmp_path / "plans.cu").write_text(PLANS)
+    exe = tmp_path / "plans"
+    subprocess.run(["nvcc", "-std=c++17", "-I", CSRC, "-o", str(exe), str(tmp_path / "plans.cu")], check=True,
+                   capture_output=True)
+    ns = [1, 192, 1536, 4 * 3 ** 7, 4 * 3 ** 8, 3 ** 9, 5, 0, -4]
+    out = subprocess.run([str(exe)] + [str(n) for n in ns], check=True, capture_output=True, text=True).stdout.split()
+    nrad = dict(zip(ns, (int(v) for v in out)))
+    assert nrad[1] == 0 and nrad[192] == 4 and nrad[1536] == 6 and nrad[4 * 3 ** 7] == 8
+    assert all(nrad[n] == -1 for n in (4 * 3 ** 8, 3 ** 9, 5, 0, -4))
+
+
 @pytest.mark.parametrize("n", [6, 12, 48, 96, 192, 384])
 def test_record_butterflies_equal_numpy_fft(tables, n):
     rad, ent, recs = tables[n]
