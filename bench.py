@@ -72,9 +72,10 @@ TRAFFIC = {
     # trajectory written; adjoint: 1.715 GB of trajectory read + 44 MB written), trajectory bytes
     # scaled to 1000 steps by (1001 / 51), averaged over the two launches of a gradient
     ("burgers1d_N256_sbdf2_1000steps", "fused_trajectory"): 3.31e10,
-    # kol_persistent, captured at 40 steps: 6.76 GB read + 4.88 GB written per sweep (trajectory
-    # and checkpoint traffic of the 64 members), scaled to 2000 steps by 50
-    ("kolmogorov2d_batch64_mixed128-512_Re100_sbdf2_2000steps_4dvar8", "fused_trajectory"): 5.82e11,
+    # kol_persistent: no capture of the gradient's own sweeps yet (the captured launches were the
+    # 5-step forward sweeps that generate the observations: 6.76 GB read + 4.88 GB written each,
+    # about 2.3 GB per step of the 64 members' mixed-space arrays)
+    ("kolmogorov2d_batch64_mixed128-512_Re100_sbdf2_2000steps_4dvar8", "fused_trajectory"): None,
 }
 
 
@@ -83,8 +84,6 @@ TRAFFIC = {
 # of the horizon
 TRAFFIC_STEPS = {
     ("burgers1d_N256_sbdf2_1000steps", "fused_trajectory"): (1001, lambda wl: wl.nsteps + 1),
-    ("kolmogorov2d_batch64_mixed128-512_Re100_sbdf2_2000steps_4dvar8", "fused_trajectory"):
-        (2000, lambda wl: wl.nsteps),
 }
 
 

@@ -24,10 +24,6 @@ def test_trajectory_traffic_scales_with_stored_steps(bench):
     assert full == bench.TRAFFIC[(w.name, "fused_trajectory")]
     w.nsteps = 50
     assert bench.traffic_for(w, "fused_trajectory") == pytest.approx(full * 51 / 1001, rel=1e-15)
-    k = bench.KolmogorovBatch()
-    fk = bench.traffic_for(k, "fused_trajectory")
-    k.nsteps = 40
-    assert bench.traffic_for(k, "fused_trajectory") == pytest.approx(fk * 40 / 2000, rel=1e-15)
 
 
 def test_per_launch_traffic_is_horizon_independent(bench):
@@ -36,6 +32,8 @@ def test_per_launch_traffic_is_horizon_independent(bench):
     r.nsteps = 4
     assert bench.traffic_for(r, "x_fft") == t == bench.TRAFFIC[(r.name, "x_fft")]
     assert bench.traffic_for(r, "no_such_kernel") is None
+    k = bench.KolmogorovBatch()  # not captured on the gradient's sweeps: reported as null
+    assert bench.traffic_for(k, "fused_trajectory") is None
 
 
 def test_hbm_fraction(bench):
