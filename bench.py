@@ -110,14 +110,19 @@ class Burgers:
     """1D viscous Burgers, N=256, nu=0.01, SBDF2 dt=1e-3, 1000 steps, 16384 members."""
     name = "burgers1d_N256_sbdf2_1000steps"
 
-    def __init__(self, batch=16384, N=256, nsteps=1000, dt=1e-3, nu=0.01, seed=1):
+    ORDERS = {"sbdf1": 1, "sbdf2": 2, "sbdf3": 3, "sbdf4": 4}
+
+    def __init__(self, batch=16384, N=256, nsteps=1000, dt=1e-3, nu=0.01, seed=1, scheme="sbdf2"):
         self.B, self.N, self.nsteps, self.dt, self.nu, self.seed = batch, N, nsteps, dt, nu, seed
         self.dof = N
         self.K, self.M = N // 2, 3 * N // 2
+        self.scheme = scheme
+        if scheme != "sbdf2":
+            self.name = "burgers1d_N%d_%s_%dsteps" % (N, scheme, nsteps)
 
     def config(self):
         return {"workload": self.name, "N": self.N, "nu": self.nu, "dt": self.dt, "steps": self.nsteps,
-                "batch": self.B, "scheme": "SBDF2", "objective": "0.5||u(T)||^2",
+                "batch": self.B, "scheme": self.scheme.upper(), "objective": "0.5||u(T)||^2",
                 "l2": "working set > L2 (stored trajectory %.1f GB)" % (self.traj_bytes() / 1e9)}
 
     def traj_bytes(self):
@@ -132,8 +137,9 @@ class Burgers:
         from paper_2506_14792_gb300 import spadj
         self.torch = torch
         self.sp = spadj
-        self.p = spadj.Problem(spadj.SPADJ_BURGERS1D, spadj.SPADJ_SBDF2, [self.N], [2 * np.pi], [self.nu], self.dt,
-                               batch=self.B)
+        sch = {"sbdf1": spadj.SPADJ_SBDF1, "sbdf2": spadj.SPADJ_SBDF2, "sbdf3": spadj.SPADJ_SBDF3,
+               "sbdf4": spadj.SPADJ_SBDF4}[self.scheme]
+        self.p = spadj.Problem(spadj.SPADJ_BURGERS1D, sch, [self.N], [2 * np.pi], [self.nu], self.dt, batch=self.B)
         self.X0_host = synthetic.burgers_ic(self.N, batch=self.B, seed=self.seed)
         self.x0 = torch.from_numpy(self.X0_host).to(device)
         self.traj = torch.empty((self.nsteps + 1, self.B, self.K), dtype=torch.complex128, device=device)
@@ -174,7 +180,7 @@ class Burgers:
         Bs = 256
         X0 = self.X0_host[:Bs] if hasattr(self, "X0_host") else synthetic.burgers_ic(self.N, batch=Bs, seed=self.seed)
         t = time.perf_counter()
-        ob.gradient(o, X0, self.nsteps, self.dt)
+        ob.gradient(o, X0, self.nsteps, self.dt, order=self.ORDERS[self.scheme])
         el = time.perf_counter() - t
         return Bs * self.dof * self.nsteps / el, "%d members x %d steps (gradient, numpy FP64)" % (Bs, self.nsteps), el
 
@@ -184,16 +190,21 @@ class RayleighBenard:
     RK222 dt=1e-3, 2000 steps, kinetic energy at T, binomial checkpointing (64 slots)."""
     name = "rayleigh_benard2d_256x64_Ra1e6_rk222_2000steps"
 
-    def __init__(self, Nx=256, Nz=64, Ra=1e6, Pr=1.0, dt=1e-3, nsteps=2000, slots=64, seed=2, amp=1e-3):
+    def __init__(self, Nx=256, Nz=64, Ra=1e6, Pr=1.0, dt=1e-3, nsteps=2000, slots=64, seed=2, amp=1e-3,
+                 scheme="rk222"):
         self.Nx, self.Nz, self.Ra, self.Pr, self.dt, self.nsteps = Nx, Nz, Ra, Pr, dt, nsteps
         self.slots, self.seed, self.amp = slots, seed, amp
         self.dof = 3 * Nx * Nz
         self.B = 1
         self.flush_l2 = True
+        self.scheme = scheme
+        if scheme != "rk222":
+            self.name = "rayleigh_benard2d_%dx%d_Ra1e6_%s_%dsteps" % (Nx, Nz, scheme, nsteps)
 
     def config(self):
         return {"workload": self.name, "Nx": self.Nx, "Nz": self.Nz, "Ra": self.Ra, "Pr": self.Pr, "dt": self.dt,
-                "steps": self.nsteps, "scheme": "RK222 (ARS222)", "objective": "kinetic energy at T",
+                "steps": self.nsteps, "scheme": {"rk222": "RK222 (ARS222)", "rk443": "RK443 (ARS443)"}[self.scheme],
+                "objective": "kinetic energy at T",
                 "checkpoint_slots": self.slots, "dof": self.dof,
                 "l2": "L2 flushed between timed iterations (256 MB write); working set ~60 MB fits L2"}
 
@@ -204,8 +215,8 @@ class RayleighBenard:
         import torch
         from paper_2506_14792_gb300 import spadj
         self.torch = torch
-        self.p = spadj.Problem(spadj.SPADJ_RB2D, spadj.SPADJ_RK222, [self.Nx, self.Nz], [4.0], [self.Ra, self.Pr],
-                               self.dt)
+        sch = {"rk222": spadj.SPADJ_RK222, "rk443": spadj.SPADJ_RK443}[self.scheme]
+        self.p = spadj.Problem(spadj.SPADJ_RB2D, sch, [self.Nx, self.Nz], [4.0], [self.Ra, self.Pr], self.dt)
         self.s0 = synthetic.rb_ic(self.Nx, self.Nz, seed=self.seed, amp=self.amp)
         shape = (3, self.Nx // 2, self.Nz)
         self.x0 = torch.from_numpy(self.s0).to(device)
@@ -233,15 +244,17 @@ class RayleighBenard:
 
     def cpu_sample(self, nsteps=6):
         """Oracle gradient (store-all) over the first `nsteps` steps of the same workload."""
+        from oracle import imex
         from oracle import rayleigh_benard as orb
+        tab = imex.rk443_tableaux() if self.scheme == "rk443" else None
         if not hasattr(self, "_oracle"):
             self._oracle = orb.RayleighBenard(self.Nx, self.Nz, self.Ra, self.Pr)
             orb.gradient(self._oracle, self._oracle.pencils(synthetic.rb_ic(self.Nx, self.Nz, seed=self.seed,
-                                                                                amp=self.amp)), 1, self.dt)
+                                                                                amp=self.amp)), 1, self.dt, tab)
         o = self._oracle
         X0 = o.pencils(synthetic.rb_ic(self.Nx, self.Nz, seed=self.seed, amp=self.amp))
         t = time.perf_counter()
-        orb.gradient(o, X0, nsteps, self.dt)
+        orb.gradient(o, X0, nsteps, self.dt, tab)
         el = time.perf_counter() - t
         return (self.dof * nsteps / el,
                 "%d of %d steps of the same gradient (forward+adjoint, store-all, numpy/scipy FP64, "
@@ -341,13 +354,24 @@ class Couette:
     checkpoint slots sized to a 180 GB HBM budget."""
     name = "couette3d_128x64x64_Re1000_sbdf2_4000steps_gain"
 
-    def __init__(self, Nx=128, Ny=64, Nz=64, Re=1000.0, dt=5e-3, nsteps=4000, seed=5, norm=1e-4, budget=180e9):
+    def __init__(self, Nx=128, Ny=64, Nz=64, Re=1000.0, dt=5e-3, nsteps=4000, seed=5, norm=1e-4, budget=180e9,
+                 op="gain"):
         self.Nx, self.Ny, self.Nz, self.Re, self.dt, self.nsteps = Nx, Ny, Nz, Re, dt, nsteps
         self.seed, self.norm, self.budget = seed, norm, budget
         self.dof = 3 * Nx * Ny * Nz
         self.B = 1
         self.flush_l2 = False
         self.slot_bytes = 3 * 16 * 3 * (Nx // 2) * Ny * Nz  # (x_n, x_{n-1}, f_{n-1})
+        # op: "gain" (gradient of E(T)/E(0)), "integral" (gradient of the time integral of E,
+        # carried as an extra equation) or "hvp" (Hessian of E(X_N) applied to a direction,
+        # tangent over adjoint, trajectory and tangent stored)
+        self.op = op
+        if op != "gain":
+            self.name = "couette3d_%dx%dx%d_Re1000_sbdf2_%dsteps_%s" % (Nx, Ny, Nz, nsteps, op)
+            self.metric = {"integral": "forward+adjoint gradient of the time-integrated energy dof*steps/s at 1e-10 "
+                                       "rel vs FP64 oracle",
+                           "hvp": "Hessian-vector product (tangent over adjoint) dof*steps/s at 1e-10 rel vs FP64 "
+                                  "oracle"}[op]
 
     @property
     def slots(self):
@@ -355,8 +379,11 @@ class Couette:
 
     def config(self):
         return {"workload": self.name, "Nx": self.Nx, "Ny": self.Ny, "Nz": self.Nz, "Re": self.Re, "dt": self.dt,
-                "steps": self.nsteps, "scheme": "SBDF1 -> SBDF2", "objective": "energy gain E(T)/E(0)",
-                "checkpoint_slots": self.slots, "dof": self.dof,
+                "steps": self.nsteps, "scheme": "SBDF1 -> SBDF2",
+                "objective": {"gain": "energy gain E(T)/E(0)", "integral": "time integral of E (extra equation)",
+                              "hvp": "E(X_N), Hessian-vector product"}[self.op],
+                "checkpoint_slots": self.slots if self.op != "hvp" else "store-all (trajectory and tangent)",
+                "dof": self.dof,
                 "l2": "working set > L2 (pencil operators 4.8 GB read every step)"}
 
     def units_per_step(self):
@@ -378,9 +405,18 @@ class Couette:
         self.x0_pin = torch.from_numpy(self.s0).pin_memory()
         self.grad_pin = torch.empty(self.x0.shape, dtype=torch.complex128).pin_memory()
         self.x0_dev2 = torch.empty_like(self.x0)
+        if self.op == "hvp":
+            v = synthetic.couette_ic(self.Nx, self.Ny, self.Nz, seed=self.seed + 86, norm=self.norm)
+            self.v = torch.from_numpy(np.ascontiguousarray(np.transpose(v, (0, 2, 1, 3)))).to(device)
+
+    def _objective(self):
+        return self.sp.SPADJ_OBJ_ENERGY_INTEGRAL if self.op == "integral" else self.sp.SPADJ_OBJ_GAIN
 
     def step(self, ev=None):
-        self.p.gradient(self.x0, self.nsteps, self.grad, objective=self.sp.SPADJ_OBJ_GAIN, ckpt_slots=self.slots,
+        if self.op == "hvp":
+            self.p.hvp(self.x0, self.v, self.nsteps, self.grad)
+            return
+        self.p.gradient(self.x0, self.nsteps, self.grad, objective=self._objective(), ckpt_slots=self.slots,
                         want_J=False)
 
     def forward_step(self):
@@ -388,7 +424,11 @@ class Couette:
 
     def e2e_step(self):
         self.x0_dev2.copy_(self.x0_pin, non_blocking=True)
-        J = self.p.gradient(self.x0_dev2, self.nsteps, self.grad, objective=self.sp.SPADJ_OBJ_GAIN,
+        if self.op == "hvp":
+            self.p.hvp(self.x0_dev2, self.v, self.nsteps, self.grad)
+            self.grad_pin.copy_(self.grad, non_blocking=True)
+            return None
+        J = self.p.gradient(self.x0_dev2, self.nsteps, self.grad, objective=self._objective(),
                             ckpt_slots=self.slots)
         self.grad_pin.copy_(self.grad, non_blocking=True)
         return J
@@ -401,16 +441,28 @@ class Couette:
         """Oracle gain gradient (store-all) on a reduced grid of the same equations: the dense
         per-pencil LU oracle cannot factor the 4096 full-size pencils within the sample budget."""
         from oracle import couette as oco
+        from oracle import imex
         o = oco.Couette(*size, self.Re)
         X0 = o.pencils(synthetic.couette_ic(*size, seed=self.seed, norm=self.norm))
         oco.gain_gradient(o, X0, 1, self.dt)  # factorisations cached outside the timed sample
         t = time.perf_counter()
-        oco.gain_gradient(o, X0, nsteps, self.dt)
+        if self.op == "integral":
+            imex.integral_gradient(o, X0, nsteps, self.dt, o.energy, o.energy_grad)
+        elif self.op == "hvp":
+            X = imex.multistep_forward(o, X0, nsteps, self.dt)
+            dX = imex.multistep_tangent(o, X, o.pencils(synthetic.couette_ic(*size, seed=self.seed + 86,
+                                                                             norm=self.norm)), self.dt)
+            imex.multistep_hvp(o, X, dX, lambda k: o.energy_grad(X[k]) if k == nsteps else None,
+                               lambda k: o.energy_grad(dX[k]) if k == nsteps else None, self.dt)
+        else:
+            oco.gain_gradient(o, X0, nsteps, self.dt)
         el = time.perf_counter() - t
         dof = 3 * size[0] * size[1] * size[2]
+        what = {"gain": "the gain gradient (forward+adjoint", "integral": "the time-integrated energy gradient "
+                "(forward+adjoint", "hvp": "the Hessian-vector product (forward, tangent, adjoint and its tangent"}
         return (dof * nsteps / el,
-                "reduced grid %dx%dx%d, %d steps of the gain gradient (forward+adjoint, store-all, numpy/scipy "
-                "FP64, factorisations cached)" % (size + (nsteps,)), el)
+                "reduced grid %dx%dx%d, %d steps of %s, store-all, numpy/scipy FP64, factorisations cached)"
+                % (size + (nsteps, what[self.op])), el)
 
 
 class PoiseuilleEvp:
@@ -686,7 +738,8 @@ def run_gpu(args, wl):
         v, sample, el = wl.cpu_sample()
         cpu = {"value": v, "unit": "dof*steps/s", "cores": int(os.environ.get("OPENBLAS_NUM_THREADS", "1")),
                "kind": "oracle", "sample": sample}
-    line = {"metric": "forward+adjoint gradient dof*steps/s at 1e-10 rel vs FP64 oracle", "value": value,
+    line = {"metric": getattr(wl, "metric", "forward+adjoint gradient dof*steps/s at 1e-10 rel vs FP64 oracle"),
+            "value": value,
             "unit": "dof*steps/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic",
@@ -799,8 +852,24 @@ def main():
     ap.add_argument("--size", default=None,
                     help="override the grid of the rb (Nx,Nz) or couette (Nx,Ny,Nz) workload, or the pencil "
                          "grid (n_alpha,n_beta) of poiseuille_evp (profiling runs)")
+    ap.add_argument("--scheme", default=None,
+                    help="rb: rk222 (default) or rk443; burgers: sbdf1..sbdf4 (default sbdf2)")
+    ap.add_argument("--op", default=None, choices=["gain", "integral", "hvp"],
+                    help="couette: gain gradient (default), time-integrated energy gradient, or Hessian-vector product")
     args = ap.parse_args()
-    wl = WORKLOADS[args.workload]()
+    kw = {}
+    if args.scheme is not None:
+        ok = {"rb": ("rk222", "rk443"), "burgers": tuple(Burgers.ORDERS)}.get(args.workload, ())
+        if args.scheme not in ok:
+            ap.error("--scheme %s does not apply to the %s workload" % (args.scheme, args.workload))
+        kw["scheme"] = args.scheme
+    if args.op is not None:
+        if args.workload != "couette":
+            ap.error("--op applies to the couette workload")
+        kw["op"] = args.op
+    if args.nsteps is not None and args.workload != "poiseuille_evp":
+        kw["nsteps"] = args.nsteps
+    wl = WORKLOADS[args.workload](**kw)
     if args.nsteps is not None:
         wl.nsteps = args.nsteps
     if args.workload == "poiseuille_evp" and (args.nsteps is not None or args.size):
@@ -813,11 +882,11 @@ def main():
     elif args.size:
         dims = [int(v) for v in args.size.split(",")]
         if args.workload == "couette" and len(dims) == 3:
-            wl = Couette(*dims, nsteps=wl.nsteps)
-            wl.name = "couette3d_%dx%dx%d_Re1000_sbdf2_%dsteps_gain" % (dims[0], dims[1], dims[2], wl.nsteps)
+            wl = Couette(*dims, **kw)
+            wl.name = "couette3d_%dx%dx%d_Re1000_sbdf2_%dsteps_%s" % (dims[0], dims[1], dims[2], wl.nsteps, wl.op)
         elif args.workload == "rb" and len(dims) == 2:
-            wl = RayleighBenard(*dims, nsteps=wl.nsteps)
-            wl.name = "rayleigh_benard2d_%dx%d_Ra1e6_rk222_%dsteps" % (dims[0], dims[1], wl.nsteps)
+            wl = RayleighBenard(*dims, **kw)
+            wl.name = "rayleigh_benard2d_%dx%d_Ra1e6_%s_%dsteps" % (dims[0], dims[1], wl.scheme, wl.nsteps)
         else:
             ap.error("--size takes Nx,Nz for rb and Nx,Ny,Nz for couette")
     if args.hbm_gb is not None:
