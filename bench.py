@@ -7,7 +7,8 @@ reference arm (``--impl reference``) times the FP64 CPU oracle on a bounded samp
 the same workload.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
-                       [--workload rb|burgers|kolmogorov|couette|poiseuille_evp]
+                       [--workload rb|burgers|kolmogorov|couette|poiseuille_evp|couette_resolvent]
+                       [--scheme rk443|sbdf1..sbdf4] [--op integral|hvp] [--dt-blocks B] [--omega W]
 Under torchrun (N > 1) each rank runs an independent replica / shard; the time is the
 max over ranks and the value counts the units of all ranks.
 """
@@ -191,20 +192,29 @@ class RayleighBenard:
     name = "rayleigh_benard2d_256x64_Ra1e6_rk222_2000steps"
 
     def __init__(self, Nx=256, Nz=64, Ra=1e6, Pr=1.0, dt=1e-3, nsteps=2000, slots=64, seed=2, amp=1e-3,
-                 scheme="rk222"):
+                 scheme="rk222", dt_blocks=0):
         self.Nx, self.Nz, self.Ra, self.Pr, self.dt, self.nsteps = Nx, Nz, Ra, Pr, dt, nsteps
         self.slots, self.seed, self.amp = slots, seed, amp
         self.dof = 3 * Nx * Nz
         self.B = 1
         self.flush_l2 = True
         self.scheme = scheme
-        if scheme != "rk222":
-            self.name = "rayleigh_benard2d_%dx%d_Ra1e6_%s_%dsteps" % (Nx, Nz, scheme, nsteps)
+        # dt_blocks > 0: step-size schedule alternating dt and dt/2 every dt_blocks steps (two
+        # stage-operator sets, each factorised once and kept)
+        self.dt_blocks = dt_blocks
+        if scheme != "rk222" or dt_blocks:
+            self.name = "rayleigh_benard2d_%dx%d_Ra1e6_%s_%dsteps%s" % (
+                Nx, Nz, scheme, nsteps, "_dtblocks%d" % dt_blocks if dt_blocks else "")
+
+    def schedule(self):
+        return [self.dt * (0.5 if (n // self.dt_blocks) % 2 else 1.0) for n in range(self.nsteps)]
 
     def config(self):
         return {"workload": self.name, "Nx": self.Nx, "Nz": self.Nz, "Ra": self.Ra, "Pr": self.Pr, "dt": self.dt,
                 "steps": self.nsteps, "scheme": {"rk222": "RK222 (ARS222)", "rk443": "RK443 (ARS443)"}[self.scheme],
                 "objective": "kinetic energy at T",
+                **({"dt_schedule": "dt and dt/2 alternating every %d steps" % self.dt_blocks}
+                   if self.dt_blocks else {}),
                 "checkpoint_slots": self.slots, "dof": self.dof,
                 "l2": "L2 flushed between timed iterations (256 MB write); working set ~60 MB fits L2"}
 
@@ -217,6 +227,8 @@ class RayleighBenard:
         self.torch = torch
         sch = {"rk222": spadj.SPADJ_RK222, "rk443": spadj.SPADJ_RK443}[self.scheme]
         self.p = spadj.Problem(spadj.SPADJ_RB2D, sch, [self.Nx, self.Nz], [4.0], [self.Ra, self.Pr], self.dt)
+        if self.dt_blocks:
+            self.p.set_dt_schedule(self.schedule())
         self.s0 = synthetic.rb_ic(self.Nx, self.Nz, seed=self.seed, amp=self.amp)
         shape = (3, self.Nx // 2, self.Nz)
         self.x0 = torch.from_numpy(self.s0).to(device)
@@ -253,8 +265,9 @@ class RayleighBenard:
                                                                                 amp=self.amp)), 1, self.dt, tab)
         o = self._oracle
         X0 = o.pencils(synthetic.rb_ic(self.Nx, self.Nz, seed=self.seed, amp=self.amp))
+        dt = self.schedule()[:nsteps] if self.dt_blocks else self.dt
         t = time.perf_counter()
-        orb.gradient(o, X0, nsteps, self.dt, tab)
+        orb.gradient(o, X0, nsteps, dt, tab)
         el = time.perf_counter() - t
         return (self.dof * nsteps / el,
                 "%d of %d steps of the same gradient (forward+adjoint, store-all, numpy/scipy FP64, "
@@ -533,8 +546,63 @@ class PoiseuilleEvp:
             n, self.P, self.N), el
 
 
+class CouetteResolvent:
+    """Leading energy-norm resolvent gain of every (kx, ky) pencil of plane Couette flow at one
+    frequency (the LBVP adjoint: the transposed pencil solves supply R^H), Re = 1000, by a batched
+    power iteration on R^H G R f = sigma^2 G f.  One step = one spadj_resolvent call of n_iter
+    iterations; the complex-shift pencil factorisations are built on the host at the first call
+    for a frequency and kept (outside the timed region)."""
+    metric = "resolvent gain power iterations (pencil*iterations/s, forward and adjoint pencil solves)"
+    unit = "pencil*iterations/s"
+
+    def __init__(self, Nx=64, Ny=32, Nz=32, Re=1000.0, omega=0.0, n_iter=50, seed=61):
+        self.Nx, self.Ny, self.Nz, self.Re, self.omega, self.n_iter, self.seed = Nx, Ny, Nz, Re, omega, n_iter, seed
+        self.P = (Nx // 2) * Ny
+        self.name = "couette3d_%dx%dx%d_Re1000_resolvent_omega%g_%diter" % (Nx, Ny, Nz, omega, n_iter)
+        self.flush_l2 = False
+
+    def config(self):
+        return {"workload": self.name, "Nx": self.Nx, "Ny": self.Ny, "Nz": self.Nz, "Re": self.Re,
+                "omega": self.omega, "pencils": self.P, "iterations": self.n_iter,
+                "l2": "pencil operators %.0f MB" % (2 * self.P * (3 * self.Nz) ** 2 * 16 / 1e6)}
+
+    def units_per_step(self):
+        return self.P * self.n_iter
+
+    def setup(self, device):
+        import torch
+        from paper_2506_14792_gb300 import spadj
+        self.p = spadj.Problem(spadj.SPADJ_COUETTE3D, spadj.SPADJ_SBDF2, [self.Nx, self.Ny, self.Nz],
+                               [4 * np.pi, 2 * np.pi], [self.Re], 5e-3)
+        shape = (3, self.Ny, self.Nx // 2, self.Nz)
+        self.f_init = torch.from_numpy(synthetic.random_coeffs(shape, seed=self.seed))
+        self.f = self.f_init.to(device)
+        self.gains = torch.zeros((self.Ny, self.Nx // 2), dtype=torch.float64, device=device)
+        self.gains_host = torch.zeros((self.Ny, self.Nx // 2), dtype=torch.float64).pin_memory()
+
+    def step(self):
+        self.f.copy_(self.f_init, non_blocking=True)
+        self.p.resolvent(self.omega, self.n_iter, self.f, self.gains)
+        self.gains_host.copy_(self.gains)
+
+    def e2e_bytes(self):
+        return self.f_init.numel() * 16, self.P * 8
+
+    def cpu_sample(self, n=64):
+        """Oracle: dense R^H G R versus G eigenproblem of the first n pencils (numpy/scipy FP64)."""
+        from oracle import couette as oco
+        o = oco.Couette(self.Nx, self.Ny, self.Nz, self.Re, pencils=False)
+        pairs = [(m, j) for j in range(self.Ny) if j != self.Ny // 2 for m in range(self.Nx // 2)][:n]
+        t = time.perf_counter()
+        for m, j in pairs:
+            oco.resolvent_gain(o, o.alpha[m], o.beta[j], self.omega)
+        el = time.perf_counter() - t
+        return n * self.n_iter / el, "%d pencils by the dense generalised eigenproblem, counted as %d iterations " \
+            "each" % (n, self.n_iter), el
+
+
 WORKLOADS = {"burgers": Burgers, "rb": RayleighBenard, "kolmogorov": KolmogorovBatch, "couette": Couette,
-             "poiseuille_evp": PoiseuilleEvp}
+             "poiseuille_evp": PoiseuilleEvp, "couette_resolvent": CouetteResolvent}
 DEFAULT_WORKLOAD = "rb"
 
 
@@ -798,20 +866,28 @@ def run_gpu_evp(args, wl):
     e2e_ms = reduce_max(e0.elapsed_time(e1), dev)
     units = wl.units_per_step() * args.steps * ws
     value = job_value(wl.units_per_step(), args.steps, ws, dev_ms)
-    o = wl.out.cpu().numpy()
-    converged = float(np.mean(np.max(o[:, 8:10], axis=1) <= 1e-11))
-    dom = "pencil_solve"
+    evp = isinstance(wl, PoiseuilleEvp)
+    extra = {}
+    if evp:
+        o = wl.out.cpu().numpy()
+        extra["converged_fraction"] = float(np.mean(np.max(o[:, 8:10], axis=1) <= 1e-11))
+        dom = "pencil_solve"
+    else:
+        g = wl.gains_host.numpy()
+        extra["gain_range"] = [float(g[g > 0].min()), float(g.max())]
+        dom = max(rep, key=lambda k: rep[k][0])
     dms, dfl, dn = rep[dom]
     achieved = dfl / (dms / 1e3) / 1e9
     per_kernel = {k: {"ms_total": v[0], "launches": v[2], "share": v[0] / sum(x[0] for x in rep.values()),
                       "gflops": v[1] / (v[0] / 1e3) / 1e9 if v[0] > 0 else None} for k, v in rep.items()}
-    roof = {"kernel": "evp_iter_kernel (pencil_solve)", "bound": "alu", "achieved": achieved,
+    roof = {"kernel": "evp_iter_kernel (pencil_solve)" if evp else dom, "bound": "alu", "achieved": achieved,
             "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s", "frac": achieved / FP64_PEAK_GFLOPS,
             "traffic": traffic_for(wl, dom), "hbm": hbm_fraction(traffic_for(wl, dom), dms / dn / 1e3),
             "avg_launch_us": 1e3 * dms / dn, "flops_per_launch": dfl / dn,
             "per_kernel": per_kernel,
-            "peak_note": "FP64 FMA peak 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz; 16 flops per operator entry "
-                         "and iteration (forward and adjoint complex matvecs)"}
+            "peak_note": "FP64 FMA peak 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz; "
+                         + ("16 flops per operator entry and iteration (forward and adjoint complex matvecs)" if evp
+                            else "8 flops per operator entry and pencil solve (complex matvec)")}
     launches = int(sum(v[2] for v in rep.values()))
     if rank != 0:
         return 0
@@ -824,10 +900,12 @@ def run_gpu_evp(args, wl):
     line = {"metric": wl.metric, "value": value, "unit": wl.unit, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": dev_ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": dict(wl.config(), parallelism="replicas%d" % ws, converged_fraction=converged),
+            "config": dict(wl.config(), parallelism="replicas%d" % ws, **extra),
             "gpu_launches": launches,
             "e2e": {"value": units / (e2e_ms / 1e3), "unit": wl.unit, "h2d_bytes_per_step": bi,
-                    "d2h_bytes_per_step": bo, "note": "includes the host LU of every shifted pencil"},
+                    "d2h_bytes_per_step": bo,
+                    "note": "includes the host LU of every shifted pencil" if evp else
+                            "the frequency's pencil factorisations are built at the first call and kept"},
             "roofline": roof, "cpu_baseline": cpu, "clocks": clocks}
     print(json.dumps(line))
     return 0
@@ -856,6 +934,9 @@ def main():
                     help="rb: rk222 (default) or rk443; burgers: sbdf1..sbdf4 (default sbdf2)")
     ap.add_argument("--op", default=None, choices=["gain", "integral", "hvp"],
                     help="couette: gain gradient (default), time-integrated energy gradient, or Hessian-vector product")
+    ap.add_argument("--omega", type=float, default=None, help="couette_resolvent: forcing frequency (default 0)")
+    ap.add_argument("--dt-blocks", type=int, default=0,
+                    help="rb: step-size schedule alternating dt and dt/2 every this many steps (0: constant dt)")
     args = ap.parse_args()
     kw = {}
     if args.scheme is not None:
@@ -867,8 +948,19 @@ def main():
         if args.workload != "couette":
             ap.error("--op applies to the couette workload")
         kw["op"] = args.op
-    if args.nsteps is not None and args.workload != "poiseuille_evp":
-        kw["nsteps"] = args.nsteps
+    if args.nsteps is not None:
+        if args.workload == "couette_resolvent":
+            kw["n_iter"] = args.nsteps
+        elif args.workload != "poiseuille_evp":
+            kw["nsteps"] = args.nsteps
+    if args.dt_blocks:
+        if args.workload != "rb":
+            ap.error("--dt-blocks applies to the rb workload")
+        kw["dt_blocks"] = args.dt_blocks
+    if args.omega is not None:
+        if args.workload != "couette_resolvent":
+            ap.error("--omega applies to the couette_resolvent workload")
+        kw["omega"] = args.omega
     wl = WORKLOADS[args.workload](**kw)
     if args.nsteps is not None:
         wl.nsteps = args.nsteps
@@ -884,18 +976,20 @@ def main():
         if args.workload == "couette" and len(dims) == 3:
             wl = Couette(*dims, **kw)
             wl.name = "couette3d_%dx%dx%d_Re1000_sbdf2_%dsteps_%s" % (dims[0], dims[1], dims[2], wl.nsteps, wl.op)
+        elif args.workload == "couette_resolvent" and len(dims) == 3:
+            wl = CouetteResolvent(*dims, **kw)
         elif args.workload == "rb" and len(dims) == 2:
             wl = RayleighBenard(*dims, **kw)
             wl.name = "rayleigh_benard2d_%dx%d_Ra1e6_%s_%dsteps" % (dims[0], dims[1], wl.scheme, wl.nsteps)
         else:
-            ap.error("--size takes Nx,Nz for rb and Nx,Ny,Nz for couette")
+            ap.error("--size takes Nx,Nz for rb and Nx,Ny,Nz for couette and couette_resolvent")
     if args.hbm_gb is not None:
         if not isinstance(wl, Couette):
             ap.error("--hbm-gb applies to the couette workload")
         wl.budget = args.hbm_gb * 1e9
     if args.impl == "reference":
         return run_reference(args, wl)
-    if isinstance(wl, PoiseuilleEvp):
+    if isinstance(wl, (PoiseuilleEvp, CouetteResolvent)):
         return run_gpu_evp(args, wl)
     return run_gpu(args, wl)
 
