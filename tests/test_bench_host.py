@@ -41,3 +41,44 @@ def test_hbm_fraction(bench):
     assert h["achieved_gbs"] == pytest.approx(3000.0)
     assert h["frac"] == pytest.approx(3000.0 / h["peak_gbs"])
     assert bench.hbm_fraction(None, 2.0e-3) is None
+
+
+@pytest.mark.parametrize("argv,name,check", [
+    (["--workload", "rb", "--scheme", "rk443", "--nsteps", "200"], "rayleigh_benard2d_256x64_Ra1e6_rk443_200steps",
+     lambda w: w.scheme == "rk443" and w.nsteps == 200),
+    (["--workload", "rb", "--dt-blocks", "50", "--nsteps", "200"],
+     "rayleigh_benard2d_256x64_Ra1e6_rk222_200steps_dtblocks50",
+     lambda w: w.schedule()[49] == w.dt and w.schedule()[50] == 0.5 * w.dt and len(w.schedule()) == 200),
+    (["--workload", "burgers", "--scheme", "sbdf4"], "burgers1d_N256_sbdf4_1000steps",
+     lambda w: w.ORDERS[w.scheme] == 4),
+    (["--workload", "couette", "--op", "hvp", "--size", "64,32,32", "--nsteps", "100"],
+     "couette3d_64x32x32_Re1000_sbdf2_100steps_hvp", lambda w: w.op == "hvp" and "Hessian" in w.metric),
+    (["--workload", "couette_resolvent", "--nsteps", "20", "--omega", "0.3"],
+     "couette3d_64x32x32_Re1000_resolvent_omega0.3_20iter", lambda w: w.units_per_step() == 1024 * 20),
+    ([], "rayleigh_benard2d_256x64_Ra1e6_rk222_2000steps", lambda w: w.scheme == "rk222" and not w.dt_blocks),
+])
+def test_workload_variants_from_the_command_line(bench, argv, name, check):
+    """The variant flags build the workload they name (the run itself is replaced by a probe)."""
+    got = []
+    run_gpu, run_gpu_evp, saved = bench.run_gpu, bench.run_gpu_evp, sys.argv
+    bench.run_gpu = bench.run_gpu_evp = lambda args, wl: got.append(wl) or 0
+    sys.argv = ["bench.py"] + argv
+    try:
+        assert bench.main() == 0
+    finally:
+        bench.run_gpu, bench.run_gpu_evp, sys.argv = run_gpu, run_gpu_evp, saved
+    assert got[0].name == name and check(got[0])
+
+
+@pytest.mark.parametrize("argv", [["--workload", "burgers", "--dt-blocks", "5"],
+                                  ["--workload", "rb", "--scheme", "sbdf2"],
+                                  ["--workload", "rb", "--op", "hvp"],
+                                  ["--workload", "couette", "--omega", "1.0"]])
+def test_variant_flags_refused_where_they_do_not_apply(bench, argv):
+    saved = sys.argv
+    sys.argv = ["bench.py"] + argv
+    try:
+        with pytest.raises(SystemExit):
+            bench.main()
+    finally:
+        sys.argv = saved
