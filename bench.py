@@ -31,8 +31,25 @@ sys.path.insert(0, ROOT)
 import synthetic  # noqa: E402
 
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
-# FP64 peak: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.07 GHz (nominal GB300 FP64 1.25 TFLOP/s).
-FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
+# Nominal FP64 peak, for context: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.07 GHz (GB300 FP64 1.25 TFLOP/s).
+# The roofline uses the peak measured on the run's own GPU (measure_fp64_peak).
+FP64_NOMINAL_GFLOPS = 152 * 2 * 2 * 2.07
+
+
+def measure_fp64_peak(gpu_index, iters=100000):
+    """FP64 FMA throughput of this GPU from the library's probe kernel (independent FMA chains,
+    occupancy-sized grid, CUDA events), best of three launches, with the SM clocks sampled while it
+    runs."""
+    from paper_2506_14792_gb300 import spadj
+    clk = ClockSampler(gpu_index)
+    clk.start()
+    time.sleep(0.3)
+    runs = [spadj.fp64_peak(iters=iters) for _ in range(3)]
+    clocks = clk.stop()
+    g, ms = max(runs)
+    return {"gflops": g, "ms": ms, "runs_gflops": [r[0] for r in runs], "clocks": clocks,
+            "how": "spadj_fp64_peak: 8 independent FMA chains per thread, %d FMAs each, occupancy-sized grid, "
+                   "best of 3" % iters}
 
 
 def hbm_peak_gbs():
@@ -202,9 +219,8 @@ class RayleighBenard:
         # dt_blocks > 0: step-size schedule alternating dt and dt/2 every dt_blocks steps (two
         # stage-operator sets, each factorised once and kept)
         self.dt_blocks = dt_blocks
-        if scheme != "rk222" or dt_blocks:
-            self.name = "rayleigh_benard2d_%dx%d_Ra1e6_%s_%dsteps%s" % (
-                Nx, Nz, scheme, nsteps, "_dtblocks%d" % dt_blocks if dt_blocks else "")
+        self.name = "rayleigh_benard2d_%dx%d_Ra1e6_%s_%dsteps%s" % (
+            Nx, Nz, scheme, nsteps, "_dtblocks%d" % dt_blocks if dt_blocks else "")
 
     def schedule(self):
         return [self.dt * (0.5 if (n // self.dt_blocks) % 2 else 1.0) for n in range(self.nsteps)]
@@ -594,8 +610,7 @@ class CouetteResolvent:
         o = oco.Couette(self.Nx, self.Ny, self.Nz, self.Re, pencils=False)
         pairs = [(m, j) for j in range(self.Ny) if j != self.Ny // 2 for m in range(self.Nx // 2)][:n]
         t = time.perf_counter()
-        for m, j in pairs:
-            oco.resolvent_gain(o, o.alpha[m], o.beta[j], self.omega)
+        self.oracle_gains = {(m, j): oco.resolvent_gain(o, o.alpha[m], o.beta[j], self.omega) for m, j in pairs}
         el = time.perf_counter() - t
         return n * self.n_iter / el, "%d pencils by the dense generalised eigenproblem, counted as %d iterations " \
             "each" % (n, self.n_iter), el
@@ -653,6 +668,44 @@ class ClockSampler:
 # ---------------------------------------------------------------------------------------
 # arms
 # ---------------------------------------------------------------------------------------
+
+def cpu_model():
+    """Host CPU model and core count (for the CPU-baseline record)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return model, os.cpu_count()
+
+
+def _cpu_replica(ctor):
+    """One single-threaded oracle sample in a worker process (a fresh workload object)."""
+    cls, args, kw = ctor
+    wl = cls(*args, **kw)
+    v, sample, el = wl.cpu_sample()
+    return v, el
+
+
+def cpu_all_cores(wl):
+    """The oracle's throughput on every host core: one independent single-threaded replica of the
+    bounded sample per core, run concurrently in spawned processes (the GPU context is never
+    forked); value = the replicas' summed units per second."""
+    import multiprocessing as mp
+    model, n = cpu_model()
+    ctor = getattr(wl, "_ctor", (type(wl), (), {}))
+    t = time.perf_counter()
+    with mp.get_context("spawn").Pool(n) as pool:
+        res = pool.map(_cpu_replica, [ctor] * n)
+    wall = time.perf_counter() - t
+    return {"value": float(sum(v for v, _ in res)), "cores": n, "threads_per_replica": 1, "cpu_model": model,
+            "replica_seconds": [round(el, 3) for _, el in res], "wall_s": round(wall, 1),
+            "note": "%d concurrent single-threaded oracle replicas of the bounded sample" % n}
+
 
 def reduce_max(x, device=None):
     """Max of a float over all ranks (identity without torch.distributed); gloo or nccl."""
@@ -786,26 +839,40 @@ def run_gpu(args, wl):
     e2e_ms = reduce_max(e0.elapsed_time(e1), dev)
     bi, bo = wl.e2e_bytes()
 
-    # roofline of the dominant kernel class (FP64 ALU bound on GB300)
+    # roofline of the dominant kernel class (FP64 ALU bound on GB300) against the measured FP64 peak
+    fp64 = measure_fp64_peak(local)
+    peak = fp64["gflops"]
     dom = max(rep, key=lambda k: rep[k][0])
     dms, dfl, dn = rep[dom]
     achieved = dfl / (dms / 1e3) / 1e9
     per_kernel = {k: {"ms_total": v[0], "launches": v[2], "share": v[0] / sum(x[0] for x in rep.values()),
                       "gflops": v[1] / (v[0] / 1e3) / 1e9 if v[0] > 0 else None} for k, v in rep.items()}
-    roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
-            "frac": achieved / FP64_PEAK_GFLOPS, "traffic": traffic_for(wl, dom),
+    total_flops = sum(v[1] for v in rep.values())
+    roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "GFLOP/s",
+            "frac": achieved / peak, "traffic": traffic_for(wl, dom),
             "hbm": hbm_fraction(traffic_for(wl, dom), dms / dn / 1e3),
             "avg_launch_us": 1e3 * dms / dn, "flops_per_launch": dfl / dn, "per_kernel": per_kernel,
-            "peak_note": "FP64 FMA peak 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s); "
-                         "no tensor-core FP64 path (GB300 FP64 tensor rate is the same)"}
+            "whole_step": {"algorithmic_gflop": total_flops / 1e9,
+                           "achieved": total_flops / (ms / args.steps / 1e3) / 1e9,
+                           "frac": total_flops / (ms / args.steps / 1e3) / 1e9 / peak,
+                           "note": "all kernel classes' algorithmic FP64 flops of one step over the timed step"},
+            "peak_source": "measured", "peak_measurement": fp64,
+            "peak_note": "FP64 peak measured by the library's FMA-chain probe on this GPU (nominal %.0f GFLOP/s = "
+                         "152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz); no tensor-core FP64 path (GB300's FP64 "
+                         "tensor rate is the same). Per-class times come from one instrumented step in which "
+                         "the reverse sweep's lanes overlap, so each class's GFLOP/s is a lower bound"
+                         % FP64_NOMINAL_GFLOPS}
     launches = int(sum(v[2] for v in rep.values())) * args.steps
     if rank != 0:
         return 0
     cpu = None
     if ws == 1 and not args.no_cpu:
         v, sample, el = wl.cpu_sample()
+        model, _ = cpu_model()
         cpu = {"value": v, "unit": "dof*steps/s", "cores": int(os.environ.get("OPENBLAS_NUM_THREADS", "1")),
-               "kind": "oracle", "sample": sample}
+               "kind": "oracle", "sample": sample, "cpu_model": model}
+        if not args.no_cpu_all:
+            cpu["all_cores"] = cpu_all_cores(wl)
     line = {"metric": getattr(wl, "metric", "forward+adjoint gradient dof*steps/s at 1e-10 rel vs FP64 oracle"),
             "value": value,
             "unit": "dof*steps/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
@@ -876,26 +943,45 @@ def run_gpu_evp(args, wl):
         g = wl.gains_host.numpy()
         extra["gain_range"] = [float(g[g > 0].min()), float(g.max())]
         dom = max(rep, key=lambda k: rep[k][0])
+        # the GPU gains of the pencils the CPU oracle solves (dense generalised eigenproblem)
+        if rank == 0:
+            if ws == 1 and not args.no_cpu:
+                wl.cpu_result = wl.cpu_sample()  # the CPU baseline leg (reported below)
+            else:
+                wl.cpu_sample(n=16)
+            err = np.array([abs(g[j, m] - v) / v for (m, j), v in wl.oracle_gains.items()])
+            extra["vs_oracle"] = {"pencils": int(err.size), "max_rel_err": float(err.max()),
+                                  "within_1e-10": float(np.mean(err <= 1e-10)),
+                                  "within_1e-6": float(np.mean(err <= 1e-6)),
+                                  "note": "%d power iterations from a random forcing; the oracle is the converged "
+                                          "leading gain" % wl.n_iter}
     dms, dfl, dn = rep[dom]
     achieved = dfl / (dms / 1e3) / 1e9
+    fp64 = measure_fp64_peak(local)
+    peak = fp64["gflops"]
     per_kernel = {k: {"ms_total": v[0], "launches": v[2], "share": v[0] / sum(x[0] for x in rep.values()),
                       "gflops": v[1] / (v[0] / 1e3) / 1e9 if v[0] > 0 else None} for k, v in rep.items()}
     roof = {"kernel": "evp_iter_kernel (pencil_solve)" if evp else dom, "bound": "alu", "achieved": achieved,
-            "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s", "frac": achieved / FP64_PEAK_GFLOPS,
+            "peak": peak, "unit": "GFLOP/s", "frac": achieved / peak, "peak_source": "measured",
+            "peak_measurement": fp64,
             "traffic": traffic_for(wl, dom), "hbm": hbm_fraction(traffic_for(wl, dom), dms / dn / 1e3),
             "avg_launch_us": 1e3 * dms / dn, "flops_per_launch": dfl / dn,
             "per_kernel": per_kernel,
-            "peak_note": "FP64 FMA peak 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz; "
+            "peak_note": "FP64 peak measured by the library's FMA-chain probe on this GPU; "
                          + ("16 flops per operator entry and iteration (forward and adjoint complex matvecs)" if evp
-                            else "8 flops per operator entry and pencil solve (complex matvec)")}
+                            else "8 flops per operator entry and pencil solve (complex matvec), 4 per entry of "
+                                 "the real Gram products")}
     launches = int(sum(v[2] for v in rep.values()))
     if rank != 0:
         return 0
     cpu = None
     if ws == 1 and not args.no_cpu:
-        v, sample, el = wl.cpu_sample()
+        v, sample, el = getattr(wl, "cpu_result", None) or wl.cpu_sample()
+        model, _ = cpu_model()
         cpu = {"value": v, "unit": wl.unit, "cores": int(os.environ.get("OPENBLAS_NUM_THREADS", "1")),
-               "kind": "oracle", "sample": sample}
+               "kind": "oracle", "sample": sample, "cpu_model": model}
+        if not args.no_cpu_all:
+            cpu["all_cores"] = cpu_all_cores(wl)
     bi, bo = wl.e2e_bytes()
     line = {"metric": wl.metric, "value": value, "unit": wl.unit, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": dev_ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -919,6 +1005,7 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
+    ap.add_argument("--no-cpu-all", action="store_true", help="skip the all-cores CPU-oracle replicas")
     ap.add_argument("--pdl", action="store_true", help="programmatic dependent launch of consecutive kernels")
     ap.add_argument("--no-fuse", action="store_true", help="RB: separate fold / solve / expand kernels")
     ap.add_argument("--x-rows", type=int, default=0, help="x-FFT rows per CTA (1, 2, 4; 0 = tuned)")
@@ -962,6 +1049,7 @@ def main():
             ap.error("--omega applies to the couette_resolvent workload")
         kw["omega"] = args.omega
     wl = WORKLOADS[args.workload](**kw)
+    wl._ctor = (type(wl), (), dict(kw))
     if args.nsteps is not None:
         wl.nsteps = args.nsteps
     if args.workload == "poiseuille_evp" and (args.nsteps is not None or args.size):
@@ -971,16 +1059,19 @@ def main():
         it = args.nsteps if args.nsteps is not None else wl.n_iter
         wl = PoiseuilleEvp(n_alpha=dims[0], n_beta=dims[1], n_iter=it)
         wl.name = "poiseuille_evp_N64_%dpencils_Re8000_%diter" % (wl.P, it)
+        wl._ctor = (PoiseuilleEvp, (), {"n_alpha": dims[0], "n_beta": dims[1], "n_iter": it})
     elif args.size:
         dims = [int(v) for v in args.size.split(",")]
         if args.workload == "couette" and len(dims) == 3:
             wl = Couette(*dims, **kw)
+            wl._ctor = (Couette, tuple(dims), dict(kw))
             wl.name = "couette3d_%dx%dx%d_Re1000_sbdf2_%dsteps_%s" % (dims[0], dims[1], dims[2], wl.nsteps, wl.op)
         elif args.workload == "couette_resolvent" and len(dims) == 3:
             wl = CouetteResolvent(*dims, **kw)
+            wl._ctor = (CouetteResolvent, tuple(dims), dict(kw))
         elif args.workload == "rb" and len(dims) == 2:
             wl = RayleighBenard(*dims, **kw)
-            wl.name = "rayleigh_benard2d_%dx%d_Ra1e6_%s_%dsteps" % (dims[0], dims[1], wl.scheme, wl.nsteps)
+            wl._ctor = (RayleighBenard, tuple(dims), dict(kw))
         else:
             ap.error("--size takes Nx,Nz for rb and Nx,Ny,Nz for couette and couette_resolvent")
     if args.hbm_gb is not None:

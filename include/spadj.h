@@ -139,7 +139,10 @@ spadj_status spadj_destroy(spadj_problem* prob);
 /* Lengths in float64 elements for the whole batch:
  * which = 0: coefficient state (the vector the gradient is taken with respect to);
  * which = 1: one real grid field;  which = 2: parameter vector p;
- * which = 3: one scalar coefficient field (the input/output of spadj_transform). */
+ * which = 3: one scalar coefficient field (the input/output of spadj_transform);
+ * which = 4: restart state of one step (spadj_step_forward / spadj_step_tangent);
+ * which = 5: adjoint state of one step (spadj_step_adjoint).
+ * 4 and 5 are 0 where the step entry points are not provided. */
 size_t spadj_state_len(const spadj_problem* prob, int which);
 
 /* Collocation transforms (Methods, "Spectral transforms"): kind
@@ -208,9 +211,55 @@ spadj_status spadj_tangent(spadj_problem* prob, int n_steps, const double* x0, c
 
 /* Adjoint sweep over a stored trajectory traj (= X_0..X_N from spadj_forward):
  * seeds the cotangent y_final = dJ/dX_N and returns grad_x0 = dJ/dX_0 by the
- * discrete adjoint recurrence (eq. IMEX_adjoint / RK adjoint, Supplementary A.4). */
+ * discrete adjoint recurrence (eq. IMEX_adjoint / RK adjoint, Supplementary A.4).
+ * grad_p (device, nullable; spadj_state_len(prob, 2) values) receives the parameter
+ * gradient sum_n (dF(X_n)/dp)^dagger (sum_i c_i^{n+i} Y_{n+i}) (eq. 6 with p entering F); it
+ * must be NULL for problems without parameters (SPADJ_ERR_INVALID / SPADJ_ERR_UNSUPPORTED). */
 spadj_status spadj_adjoint(spadj_problem* prob, int n_steps, const double* traj,
-                           const double* y_final, double* grad_x0);
+                           const double* y_final, double* grad_x0, double* grad_p);
+
+/* One timestep at a time: the forward step, its tangent and its adjoint as separate calls, so a
+ * caller can drive its own schedule (the problem statement's "step forward" and "step adjoint";
+ * eq. imex / the RK stage equation and their adjoints eq. IMEX_adjoint / RK adjoint,
+ * Supplementary A.4; eqs. 5-6, "Efficiently calculating gradients").  Defined for SPADJ_RB2D
+ * (RK222, RK443), SPADJ_COUETTE3D (SBDF1, SBDF2) and SPADJ_BURGERS1D (SBDF1-4); other equation
+ * sets return SPADJ_ERR_UNSUPPORTED.  Step n (n >= 0) maps X_n to X_{n+1}; with a step-size
+ * schedule it uses dts[n], and a multistep scheme of order s uses order min(n + 1, s) as the
+ * sweeps do.  All arrays are caller-owned device memory on the problem's stream; input and output
+ * arrays must be distinct.  Chained from X_0, the forward and adjoint steps reproduce the sweeps
+ * (spadj_forward, spadj_gradient, spadj_vjp) bit for bit: the same kernels run on the same data;
+ * so does the tangent (spadj_tangent), except for SPADJ_RB2D with RK222, whose tangent sweep
+ * recomputes the primal stages with the unfused column kernels (agreement to rounding).
+ *
+ * Restart state s_n (spadj_state_len(prob, 4) doubles): the data step n needs.
+ *   Runge-Kutta: X_n.
+ *   Multistep of order s: blocks of one state each,
+ *   [X_n, X_{n-1}, ..., X_{n-s+1}, F(X_{n-1}), ..., F(X_{n-s+1})] (2s - 1 blocks); blocks that do
+ *   not exist yet (n < s - 1) are not read by the lower-order first steps.  For n = 0 set X_0 and
+ *   zeros.
+ * spadj_step_forward writes s_{n+1}; spadj_step_tangent writes ds_{n+1}, the tangent (JVP) of
+ * s_{n+1} along ds_n (same layout), for the primal restart state s_n. */
+spadj_status spadj_step_forward(spadj_problem* prob, int n, const double* s_n, double* s_np1);
+spadj_status spadj_step_tangent(spadj_problem* prob, int n, const double* s_n, const double* ds_n,
+                                double* ds_np1);
+
+/* Adjoint of step n.  Adjoint state y (spadj_state_len(prob, 5) doubles):
+ *   Runge-Kutta: y_n = Y_n, the cotangent of X_n: y_n = (dX_{n+1}/dX_n)^dagger y_{n+1} + src.
+ *   Multistep of order s: y_n = [Y_n, Y_{n+1}, ..., Y_{n+s-1}], the adjoint variables of
+ *   eq. IMEX_adjoint (for SPADJ_COUETTE3D in prognostic form): the right-hand side
+ *   R_n = sum_{i=1..s} (c_i^{n+i} dF/dX(X_n) - a_i^{n+i} M - b_i^{n+i} L)^dagger Y_{n+i} + src is
+ *   formed and, for n >= 1, (a_0^n M + b_0^n L)^dagger Y_n = R_n solved; for n = 0 the first block
+ *   of y_0 is R_0 = dJ/dX_0 (the gradient with respect to the initial state: no solve).
+ * x_n: the primal state X_n (one state, not the restart state).  y_np1 = NULL stands for zero
+ * adjoint variables.  src (nullable) is dJ/dX_n, the objective's explicit dependence on X_n.
+ * The chain that gives dJ/dX_0 is the same for every scheme:
+ *   y = NULL;  for n = N, N-1, ..., 0:  y = step_adjoint(n, X_n, y, dJ/dX_n);  dJ/dX_0 = y[0 : state]
+ * (at n = N a Runge-Kutta step returns src; a multistep step solves for Y_N).
+ * gp_accum (nullable): for problems with parameters, the step's parameter cotangent is added
+ * to it; problems without parameters (all equation sets that provide the step calls) require
+ * NULL and return SPADJ_ERR_INVALID otherwise. */
+spadj_status spadj_step_adjoint(spadj_problem* prob, int n, const double* x_n, const double* y_np1,
+                                const double* src, double* y_n, double* gp_accum);
 
 /* Objectives for spadj_gradient. */
 typedef enum {
@@ -282,10 +331,18 @@ spadj_status spadj_gradient(spadj_problem* prob, const double* x0, int n_steps, 
  * returns, per kernel class, the summed device time (ms), the summed algorithmic FP64
  * flop count and the number of launches since timing was (re)enabled.  Classes:
  * 0 z (Chebyshev) transforms, 1 x (Fourier) FFTs, 2 grid-point products, 3 pencil solves,
- * 4 objective, 5 fused persistent trajectory kernels, 6 y (Fourier) FFTs.  spadj_timing
+ * 4 objective, 5 fused persistent trajectory kernels, 6 y (Fourier) FFTs, 7 energy-norm (Gram)
+ * products of the resolvent iteration.  spadj_timing
  * synchronises the stream and resets the counters. */
 spadj_status spadj_timing(spadj_problem* prob, int enable);
 spadj_status spadj_timing_report(spadj_problem* prob, int kernel_class, double* ms, double* flops, long* launches);
+
+/* Measurement support (not part of the method): FP64 fused-multiply-add throughput of the current
+ * device, the denominator of the FP64-bound kernels' roofline fractions.  Runs a kernel of
+ * independent FMA chains (iters FMAs per chain, an occupancy-sized grid) on cuda_stream, timed with
+ * CUDA events after a warm-up launch; *gflops_host receives 2 x FMAs / time (GFLOP/s) and *ms_host
+ * (nullable) the timed duration.  Synchronises the stream; allocates and frees a small buffer. */
+spadj_status spadj_fp64_peak(void* cuda_stream, int iters, double* gflops_host, double* ms_host);
 
 /* Vector-Jacobian product of the trajectory map (the reverse-mode building block behind
  * spadj_gradient and the torch.autograd binding): grad_x0 = sum_i (dX_{n_i}/dX_0)^T seed_i for

@@ -90,6 +90,51 @@ def dense_g2c(K, M):
     return out
 
 
+# ---- the same four maps as direct sums over explicit exponentials ----------------------
+# Exact in exact arithmetic and equal to the FFT forms above, but with a different order of
+# summation (a dense complex matrix product instead of numpy's FFT factorisation).  Used to
+# measure how far rounding-order differences alone move a long trajectory and its gradient.
+
+def _expmat(K, M):
+    """E[j, k] = exp(2 pi i k j / M), j < M, k < K."""
+    j = np.arange(M)[:, None]
+    k = np.arange(K)[None, :]
+    return np.exp(2j * np.pi * ((j * k) % M) / M)
+
+
+def c2g_direct(c, M, axis=-1):
+    c = np.moveaxis(np.asarray(c, dtype=np.complex128), axis, -1)
+    K = c.shape[-1]
+    w = np.full(K, 2.0)
+    w[0] = 1.0
+    g = np.real((c * w) @ _expmat(K, M).T)
+    return np.moveaxis(g, -1, axis)
+
+
+def g2c_direct(g, K, axis=-1):
+    g = np.moveaxis(np.asarray(g, dtype=np.float64), axis, -1)
+    M = g.shape[-1]
+    c = (g @ np.conj(_expmat(K, M))) / M
+    return np.moveaxis(c, -1, axis)
+
+
+def c2g_adj_direct(g, K, axis=-1):
+    g = np.moveaxis(np.asarray(g, dtype=np.float64), axis, -1)
+    M = g.shape[-1]
+    c = g @ np.conj(_expmat(K, M))
+    c[..., 1:] *= 2.0
+    c[..., 0] = c[..., 0].real
+    return np.moveaxis(c, -1, axis)
+
+
+def g2c_adj_direct(c, M, axis=-1):
+    c = np.moveaxis(np.asarray(c, dtype=np.complex128), axis, -1).copy()
+    K = c.shape[-1]
+    c[..., 0] = c[..., 0].real
+    g = np.real(c @ _expmat(K, M).T) / M
+    return np.moveaxis(g, -1, axis)
+
+
 def to_real(c):
     """View a complex coefficient array as the interleaved real state vector."""
     return np.ascontiguousarray(c).view(np.float64)

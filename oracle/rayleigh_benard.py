@@ -45,8 +45,16 @@ from . import fourier
 class RayleighBenard:
     NTAU = 7
 
-    def __init__(self, Nx, Nz, Ra, Pr=1.0, Lx=4.0, dealias=1.5, nonlinear=True):
+    def __init__(self, Nx, Nz, Ra, Pr=1.0, Lx=4.0, dealias=1.5, nonlinear=True, x_sums="fft"):
+        """x_sums = "direct" evaluates the x transforms as direct sums over explicit
+        exponentials instead of numpy's FFT: the same maps, summed in another order (used to
+        measure the rounding-order spread of long trajectories)."""
         assert Nx % 2 == 0 and Nz >= 4
+        assert x_sums in ("fft", "direct")
+        if x_sums == "fft":
+            self._fx = (fourier.c2g, fourier.g2c, fourier.c2g_adj, fourier.g2c_adj)
+        else:
+            self._fx = (fourier.c2g_direct, fourier.g2c_direct, fourier.c2g_adj_direct, fourier.g2c_adj_direct)
         self.Nx, self.Nz = Nx, Nz
         self.Kx = Nx // 2
         self.Mx = int(round(dealias * Nx))
@@ -169,16 +177,16 @@ class RayleighBenard:
 
     # ---- 2D transforms of one field: coefficients (Kx, N) <-> grid (Mz, Mx) -----------------
     def c2g(self, c):
-        return fourier.c2g((c @ self.Cz.T).T, self.Mx)
+        return self._fx[0]((c @ self.Cz.T).T, self.Mx)
 
     def g2c(self, g):
-        return fourier.g2c(g, self.Kx).T @ self.Gz.T
+        return self._fx[1](g, self.Kx).T @ self.Gz.T
 
     def c2g_adj(self, g):
-        return fourier.c2g_adj(g, self.Kx).T @ self.Cz
+        return self._fx[2](g, self.Kx).T @ self.Cz
 
     def g2c_adj(self, c):
-        return fourier.g2c_adj((c @ self.Gz).T, self.Mx)
+        return self._fx[3]((c @ self.Gz).T, self.Mx)
 
     def dx(self, c):
         return 1j * self.kx[:, None] * c

@@ -64,6 +64,7 @@ spadj_status spadj_destroy(spadj_problem* p) {
 
 size_t spadj_state_len(const spadj_problem* p, int which) {
   if (!p || !p->impl) return 0;
+  if (which == 4 || which == 5) return (size_t)p->impl->step_blocks(which - 4) * p->impl->state_len(0);
   return p->impl->state_len(which);
 }
 
@@ -243,11 +244,33 @@ spadj_status spadj_tangent(spadj_problem* p, int n_steps, const double* x0, cons
 }
 
 spadj_status spadj_adjoint(spadj_problem* p, int n_steps, const double* traj, const double* y_final,
-                           double* grad_x0) {
+                           double* grad_x0, double* grad_p) {
   if (!p) return SPADJ_ERR_INVALID;
   if (bad_ptr(traj) || bad_ptr(y_final) || bad_ptr(grad_x0))
     return p->fail(SPADJ_ERR_INVALID, "adjoint: NULL array");
-  return p->impl->adjoint(p, n_steps, traj, y_final, grad_x0);
+  return p->impl->adjoint(p, n_steps, traj, y_final, grad_x0, grad_p);
+}
+
+spadj_status spadj_step_forward(spadj_problem* p, int n, const double* s_n, double* s_np1) {
+  if (!p) return SPADJ_ERR_INVALID;
+  if (bad_ptr(s_n) || bad_ptr(s_np1)) return p->fail(SPADJ_ERR_INVALID, "step_forward: NULL array");
+  if (s_n == s_np1) return p->fail(SPADJ_ERR_INVALID, "step_forward: s_n and s_np1 must not be the same array");
+  return p->impl->step_forward(p, n, s_n, s_np1);
+}
+
+spadj_status spadj_step_tangent(spadj_problem* p, int n, const double* s_n, const double* ds_n, double* ds_np1) {
+  if (!p) return SPADJ_ERR_INVALID;
+  if (bad_ptr(s_n) || bad_ptr(ds_n) || bad_ptr(ds_np1)) return p->fail(SPADJ_ERR_INVALID, "step_tangent: NULL array");
+  if (ds_n == ds_np1) return p->fail(SPADJ_ERR_INVALID, "step_tangent: ds_n and ds_np1 must not be the same array");
+  return p->impl->step_tangent(p, n, s_n, ds_n, ds_np1);
+}
+
+spadj_status spadj_step_adjoint(spadj_problem* p, int n, const double* x_n, const double* y_np1, const double* src,
+                                double* y_n, double* gp_accum) {
+  if (!p) return SPADJ_ERR_INVALID;
+  if (bad_ptr(x_n) || bad_ptr(y_n)) return p->fail(SPADJ_ERR_INVALID, "step_adjoint: NULL array");
+  if (y_np1 == y_n) return p->fail(SPADJ_ERR_INVALID, "step_adjoint: y_np1 and y_n must not be the same array");
+  return p->impl->step_adjoint(p, n, x_n, y_np1, src, y_n, gp_accum);
 }
 
 spadj_status spadj_objective(spadj_problem* p, int objective, const double* obj_data, const double* x,

@@ -15,6 +15,7 @@
 
 #include "fft.cuh"
 #include "problem.h"
+#include "revolve.h"
 
 namespace spadj {
 namespace {
@@ -271,28 +272,47 @@ __device__ __forceinline__ double2 hist_rhs(const Coef& c, const double2 (&hf)[O
   return r;
 }
 
-// mode 0: forward (optionally storing traj), mode 1: tangent.  ORD = the history length kept
-// in registers (2 for SBDF1/2, 4 for SBDF3/4): X_{n-1..n-ORD}, F_{n-1..n-ORD} (and their tangents).
+// Forward (tangent = 0) or tangent (tangent = 1) segment of n_steps steps after step n_first,
+// i.e. X_{n_first} -> X_{n_first + n_steps}.  ORD = the history length kept in registers (2 for
+// SBDF1/2, 4 for SBDF3/4): X_{n-1..n-ORD}, F_{n-1..n-ORD} (and their tangents).
+// Restart states (blocks of [B][K] complex): s = [X_n, ..., X_{n-s+1}, F(X_{n-1}), ..., F(X_{n-s+1})],
+// s = P.order.  s_in holds in_blocks blocks: 1 (X_0 alone, a sweep from the initial state) or 2s-1
+// (a full restart state); ds_in the same blocks of the tangent.  Outputs (each nullable): x_out the
+// final state (or tangent), s_out the final restart state (or its tangent), traj the states
+// X_{n_first}..X_{n_first+n_steps}.
 template <int Q, int ORD>
-__global__ void __launch_bounds__(64) trajectory_kernel(BurgersParams P, int n_steps, const double* __restrict__ x0,
-                                                        const double* __restrict__ dx0, double* __restrict__ x_out,
-                                                        double* __restrict__ traj, int tangent) {
+__global__ void __launch_bounds__(64) trajectory_kernel(BurgersParams P, int n_first, int n_steps,
+                                                        const double* __restrict__ s_in, int in_blocks,
+                                                        const double* __restrict__ ds_in, double* __restrict__ x_out,
+                                                        double* __restrict__ s_out, double* __restrict__ traj,
+                                                        int tangent) {
   Smem s = carve(P);
   extern __shared__ double2 sm[];
   double2* S2 = sm + 4 * P.L + 2 * P.K;
   double2* O2 = S2 + P.K;
   const int b = blockIdx.x, K = P.K, G = blockDim.x, tid = threadIdx.x;
   const int nb = gridDim.x;
+  const size_t blk = (size_t)nb * 2 * K;
+  const int so = P.order;
+  const int nx = in_blocks > 1 ? so : 1;  // X blocks present in s_in
   double2 X[Q][ORD], F[Q][ORD], D[Q][ORD], GJ[Q][ORD];
-  const double2* xr = row(x0, b, K);
   for (int q = 0; q < Q; ++q) {
     int k = tid + q * G;
     double2 z = make_double2(0.0, 0.0);
 #pragma unroll
     for (int i = 0; i < ORD; ++i) X[q][i] = F[q][i] = D[q][i] = GJ[q][i] = z;
-    X[q][0] = (k < K) ? xr[k] : z;
-    if (tangent && k < K) D[q][0] = row(dx0, b, K)[k];
     if (k < K) {
+#pragma unroll
+      for (int i = 0; i < ORD; ++i) {
+        if (i < nx) {
+          X[q][i] = row(s_in + i * blk, b, K)[k];
+          if (tangent) D[q][i] = row(ds_in + i * blk, b, K)[k];
+        }
+        if (i >= 1 && i < so && in_blocks > 1) {
+          F[q][i] = row(s_in + (so + i - 1) * blk, b, K)[k];
+          if (tangent) GJ[q][i] = row(ds_in + (so + i - 1) * blk, b, K)[k];
+        }
+      }
       s.S[k] = X[q][0];
       if (tangent) S2[k] = D[q][0];
       if (traj) row(traj, b, K)[k] = X[q][0];
@@ -315,7 +335,8 @@ __global__ void __launch_bounds__(64) trajectory_kernel(BurgersParams P, int n_s
     inv_m[q] = 0.0;
   }
   int s_prev = 0;
-  for (int n = 1; n <= n_steps; ++n) {
+  for (int j = 1; j <= n_steps; ++j) {
+    const int n = n_first + j;
     Coef c = step_coef(P, n);
     const int s_n = step_order(P, n);
     if (s_n != s_prev) {
@@ -332,7 +353,7 @@ __global__ void __launch_bounds__(64) trajectory_kernel(BurgersParams P, int n_s
       for (int i = ORD - 1; i > 0; --i) { X[q][i] = X[q][i - 1]; F[q][i] = F[q][i - 1]; }
       X[q][0] = xn;
       s.S[k] = xn;
-      if (traj) row(traj + (size_t)n * nb * 2 * K, b, K)[k] = xn;
+      if (traj) row(traj + (size_t)j * blk, b, K)[k] = xn;
       if (tangent) {
         double2 dn = cscale(hist_rhs<ORD>(c, GJ[q], D[q]), inv);
         if (k == 0) dn.y = 0.0;
@@ -343,7 +364,7 @@ __global__ void __launch_bounds__(64) trajectory_kernel(BurgersParams P, int n_s
       }
     }
     __syncthreads();
-    if (n < n_steps && P.nonlinear) {
+    if (j < n_steps && P.nonlinear) {
       if (tangent) eval_F_and_jvp(P, s, S2, O2, true);
       else eval_F(P, s);
       for (int q = 0; q < Q; ++q) {
@@ -352,26 +373,41 @@ __global__ void __launch_bounds__(64) trajectory_kernel(BurgersParams P, int n_s
       }
     }
   }
-  double2* o = row(x_out, b, K);
   for (int q = 0; q < Q; ++q) {
     int k = tid + q * G;
-    if (k < K) o[k] = tangent ? D[q][0] : X[q][0];
+    if (k >= K) continue;
+    if (x_out) row(x_out, b, K)[k] = tangent ? D[q][0] : X[q][0];
+    if (s_out) {
+#pragma unroll
+      for (int i = 0; i < ORD; ++i) {
+        if (i < so) row(s_out + i * blk, b, K)[k] = tangent ? D[q][i] : X[q][i];
+        if (i >= 1 && i < so) row(s_out + (so + i - 1) * blk, b, K)[k] = tangent ? GJ[q][i] : F[q][i];
+      }
+    }
   }
 }
 
-// Adjoint sweep (eq. IMEX_adjoint) over traj = X_0..X_N, seeded by y_final = dJ/dX_N.
-// seed_at (nullable, device, n_steps+1 ints): index into seeds ([n][member][k]) of the
-// cotangent injected at X_n, or -1; when seed_at is NULL the only seed is y_final at X_N.
+// Adjoint sweep (eq. IMEX_adjoint) over indices n = n_hi down to n_lo of a horizon of n_steps steps.
+// traj holds X_{n_lo}..X_{n_hi} (X_n at traj + (n - n_lo) * state).  At n = n_steps the cotangent is
+// seeded with y_final (NULL: zero) and no vector-Jacobian product is formed.  The adjoint variables
+// Y_{n+1}, ..., Y_{n+s} (s = P.order) are carried between launches as blocks of [B][K] complex:
+// carry_in (nullable = zero) holds Y_{n_hi+1}, ..., Y_{n_hi+s}; out receives Y_{n_lo}, ..., Y_{n_lo+s-1}
+// (out_blocks = s) or, when n_lo = 0, dJ/dX_0 in its first block (the right-hand side at n = 0, with no
+// solve) followed by Y_1, ..., Y_{s-1} when out_blocks = s.  Cotangents injected at X_n: seeds
+// (indexed by seed_at[n], nullable) and src (nullable, at n = n_hi).
 template <int Q, int ORD>
-__global__ void __launch_bounds__(64) adjoint_kernel(BurgersParams P, int n_steps, const double* __restrict__ traj,
-                                                     const double* __restrict__ y_final, double* __restrict__ grad,
-                                                     const int* __restrict__ seed_at, const double* __restrict__ seeds) {
+__global__ void __launch_bounds__(64) adjoint_kernel(BurgersParams P, int n_steps, int n_hi, int n_lo,
+                                                     const double* __restrict__ traj, const double* __restrict__ y_final,
+                                                     const double* __restrict__ carry_in, double* __restrict__ out,
+                                                     int out_blocks, const int* __restrict__ seed_at,
+                                                     const double* __restrict__ seeds, const double* __restrict__ src) {
   Smem s = carve(P);
   extern __shared__ double2 sm[];
   double2* S2 = sm + 4 * P.L + 2 * P.K;
   const int b = blockIdx.x, K = P.K, G = blockDim.x, tid = threadIdx.x;
   const int nb = gridDim.x;
   const size_t stride = (size_t)nb * 2 * K;
+  const int so = P.order;
   double2 Y[Q][ORD];  // Y_{n+1}, ..., Y_{n+ORD}
   const double2 z = make_double2(0.0, 0.0);
   // nu k^2 per mode and 1 / (a_0 + nu k^2) of the current step order (steps run backward, so the
@@ -383,10 +419,12 @@ __global__ void __launch_bounds__(64) adjoint_kernel(BurgersParams P, int n_step
     inv_m[q] = 0.0;
   }
   int s_prev = 0;
-  for (int q = 0; q < Q; ++q)
+  for (int q = 0; q < Q; ++q) {
+    const int k = tid + q * G;
 #pragma unroll
-    for (int i = 0; i < ORD; ++i) Y[q][i] = z;
-  for (int n = n_steps; n >= 0; --n) {
+    for (int i = 0; i < ORD; ++i) Y[q][i] = (carry_in && i < so && k < K) ? row(carry_in + i * stride, b, K)[k] : z;
+  }
+  for (int n = n_hi; n >= n_lo; --n) {
     double2 lam[Q];
     if (n == n_steps) {
       for (int q = 0; q < Q; ++q) {
@@ -402,7 +440,7 @@ __global__ void __launch_bounds__(64) adjoint_kernel(BurgersParams P, int n_step
         wc[i] = ci.c[i];
         wa[i] = ci.a[i];
       }
-      const double2* xn = row(traj + (size_t)n * stride, b, K);
+      const double2* xn = row(traj + (size_t)(n - n_lo) * stride, b, K);
       for (int q = 0; q < Q; ++q) {
         int k = tid + q * G;
         if (k >= K) continue;
@@ -432,11 +470,20 @@ __global__ void __launch_bounds__(64) adjoint_kernel(BurgersParams P, int n_step
         if (k < K) lam[q] = cadd(lam[q], row(sv, b, K)[k]);
       }
     }
-    if (n == 0) {
-      double2* g = row(grad, b, K);
+    if (src && n == n_hi) {
       for (int q = 0; q < Q; ++q) {
         int k = tid + q * G;
-        if (k < K) g[k] = lam[q];
+        if (k < K) lam[q] = cadd(lam[q], row(src, b, K)[k]);
+      }
+    }
+    if (n == 0) {
+      for (int q = 0; q < Q; ++q) {
+        int k = tid + q * G;
+        if (k >= K) continue;
+        row(out, b, K)[k] = lam[q];
+#pragma unroll
+        for (int i = 1; i < ORD; ++i)
+          if (i < so && i < out_blocks) row(out + i * stride, b, K)[k] = Y[q][i - 1];
       }
       return;
     }
@@ -455,6 +502,13 @@ __global__ void __launch_bounds__(64) adjoint_kernel(BurgersParams P, int n_step
       for (int i = ORD - 1; i > 0; --i) Y[q][i] = Y[q][i - 1];
       Y[q][0] = y;
     }
+  }
+  for (int q = 0; q < Q; ++q) {
+    int k = tid + q * G;
+    if (k >= K) continue;
+#pragma unroll
+    for (int i = 0; i < ORD; ++i)
+      if (i < so && i < out_blocks) row(out + i * stride, b, K)[k] = Y[q][i];
   }
 }
 
@@ -575,60 +629,182 @@ struct Burgers : EqImpl {
   // the pointwise product and the per-mode combine.
   double fft_flops() const { return 2.5 * P.M * std::log2((double)P.M); }
 
-  spadj_status forward(Problem* p, int n_steps, const double* x0, double* x_out, double* trj) override {
-    if (n_steps < 0) return p->fail(SPADJ_ERR_INVALID, "forward: n_steps < 0");
+  // launches of the segment kernels (forward / tangent segment; adjoint over n_hi..n_lo)
+  spadj_status launch_traj(Problem* p, int n_first, int n_steps, const double* s_in, int in_blocks, const double* ds_in,
+                           double* x_out, double* s_out, double* trj, int tangent) {
     cudaEvent_t t = p->tic();
     spadj_status s = dispatchQ(p, [&](auto q, auto o) {
-      trajectory_kernel<decltype(q)::value, decltype(o)::value><<<B, G, smem, p->stream>>>(P, n_steps, x0, nullptr,
-                                                                                         x_out, trj, 0);
+      trajectory_kernel<decltype(q)::value, decltype(o)::value><<<B, G, smem, p->stream>>>(
+          P, n_first, n_steps, s_in, in_blocks, ds_in, x_out, s_out, trj, tangent);
     });
-    p->toc(t, KC_FUSED, (double)B * n_steps * (2 * fft_flops() + P.M + 10.0 * P.K));
+    p->toc(t, KC_FUSED, (double)B * n_steps * ((tangent ? 3 : 2) * fft_flops() + P.M + 10.0 * P.K));
     return s;
+  }
+  spadj_status launch_adj(Problem* p, int n_steps, int n_hi, int n_lo, const double* trj, const double* y_final,
+                          const double* carry_in, double* out, int out_blocks, const int* seed_at, const double* seeds,
+                          const double* src) {
+    cudaEvent_t t = p->tic();
+    spadj_status s = dispatchQ(p, [&](auto q, auto o) {
+      adjoint_kernel<decltype(q)::value, decltype(o)::value><<<B, G, smem, p->stream>>>(
+          P, n_steps, n_hi, n_lo, trj, y_final, carry_in, out, out_blocks, seed_at, seeds, src);
+    });
+    p->toc(t, KC_FUSED, (double)B * (n_hi - n_lo + 1) * (3 * fft_flops() + 2.0 * P.M + 12.0 * P.K));
+    return s;
+  }
+
+  spadj_status forward(Problem* p, int n_steps, const double* x0, double* x_out, double* trj) override {
+    if (n_steps < 0) return p->fail(SPADJ_ERR_INVALID, "forward: n_steps < 0");
+    return launch_traj(p, 0, n_steps, x0, 1, nullptr, x_out, nullptr, trj, 0);
   }
 
   spadj_status tangent(Problem* p, int n_steps, const double* x0, const double* dx0, double* dx_out) override {
     if (n_steps < 0) return p->fail(SPADJ_ERR_INVALID, "tangent: n_steps < 0");
-    return dispatchQ(p, [&](auto q, auto o) {
-      trajectory_kernel<decltype(q)::value, decltype(o)::value><<<B, G, smem, p->stream>>>(P, n_steps, x0, dx0, dx_out,
-                                                                                         nullptr, 1);
-    });
+    return launch_traj(p, 0, n_steps, x0, 1, dx0, dx_out, nullptr, nullptr, 1);
   }
 
-  const int* seed_dev = nullptr;     // set only during vjp()
-  const double* seeds_dev = nullptr;
-  DevBuf seedmap;
+  // ---- one step at a time ----------------------------------------------------------------------
+  // restart state: 2s - 1 blocks [X_n..X_{n-s+1}, F(X_{n-1})..F(X_{n-s+1})]; adjoint state: s blocks
+  // [Y_n..Y_{n+s-1}] (the adjoint variables of eq. IMEX_adjoint), s = the scheme's order
+  int step_blocks(int which) const override { return which == 0 ? 2 * P.order - 1 : P.order; }
 
-  spadj_status vjp(Problem* p, const double* x0, int n_steps, int ckpt_slots, const std::vector<int>& seed_at,
-                   const double* seeds, double* grad) override {
-    (void)ckpt_slots;  // the per-member persistent kernels keep the whole trajectory (store-all)
-    if (n_steps < 1) return p->fail(SPADJ_ERR_INVALID, "vjp: n_steps < 1");
+  spadj_status step_forward(Problem* p, int n, const double* s_n, double* s_np1) override {
+    if (n < 0) return p->fail(SPADJ_ERR_INVALID, "step: n < 0");
+    return launch_traj(p, n, 1, s_n, 2 * P.order - 1, nullptr, nullptr, s_np1, nullptr, 0);
+  }
+
+  spadj_status step_tangent(Problem* p, int n, const double* s_n, const double* ds_n, double* ds_np1) override {
+    if (n < 0) return p->fail(SPADJ_ERR_INVALID, "step: n < 0");
+    return launch_traj(p, n, 1, s_n, 2 * P.order - 1, ds_n, nullptr, ds_np1, nullptr, 1);
+  }
+
+  spadj_status step_adjoint(Problem* p, int n, const double* x_n, const double* y_np1, const double* src, double* y_n,
+                            double* gp_accum) override {
+    if (gp_accum) return p->fail(SPADJ_ERR_INVALID, "burgers: the problem has no parameters (gp_accum must be NULL)");
+    if (n < 0) return p->fail(SPADJ_ERR_INVALID, "step: n < 0");
+    // y_np1 = NULL: the seed step (no later adjoint variables); otherwise every later step exists and
+    // the adjoint variables past the horizon are the caller's zeros
+    const int horizon = y_np1 ? (1 << 29) : n;
+    return launch_adj(p, horizon, n, n, x_n, nullptr, y_np1, y_n, P.order, nullptr, nullptr, src);
+  }
+
+  // ---- reverse sweeps ------------------------------------------------------------------------------
+  DevBuf rs, ys, slots, seedmap;  // restart-state ping-pong, adjoint-state ping-pong, checkpoint slots
+  HostBuf hslots;
+  int last_recompute = 0;
+
+  // Reverse sweep of n_steps steps.  y_final (nullable) seeds dJ/dX_N; seed_at[n] (nullable, host)
+  // indexes `seeds` for cotangents injected at X_n.  ckpt_slots <= 0 or > n_steps: the whole trajectory
+  // is stored and reversed in one launch; otherwise the binomial schedule (two-level with host slots,
+  // spadj_set_option 9) over device slots that hold full restart states, each forward segment and each
+  // adjoint step one launch over all members, the adjoint state carried between launches.
+  spadj_status reverse(Problem* p, const double* x0, int n_steps, int ckpt_slots, const double* y_final_dev,
+                       const std::vector<int>* seed_at, const double* seeds, double* grad, double* J_dev,
+                       double* seed_buf) {
     const size_t sl = state_len(0);
-    SPADJ_CUDA_TRY(p, traj.ensure(sizeof(double) * sl * (size_t)(n_steps + 1)));
-    SPADJ_CUDA_TRY(p, seedmap.ensure(sizeof(int) * (size_t)(n_steps + 1)));
-    SPADJ_CUDA_TRY(p, cudaMemcpyAsync(seedmap.ptr, seed_at.data(), sizeof(int) * (n_steps + 1), cudaMemcpyHostToDevice,
-                                      p->stream));
-    double* T = traj.as<double>();
-    spadj_status st = forward(p, n_steps, x0, T + (size_t)n_steps * sl, T);
-    if (st != SPADJ_OK) return st;
-    seed_dev = seedmap.as<int>();
-    seeds_dev = seeds;
-    st = adjoint(p, n_steps, T, nullptr, grad);
-    seed_dev = nullptr;
-    seeds_dev = nullptr;
-    if (st != SPADJ_OK) return st;
-    SPADJ_CUDA_TRY(p, cudaStreamSynchronize(p->stream));  // seed_at host staging is pageable
+    const int* sm_dev = nullptr;
+    if (seed_at) {
+      SPADJ_CUDA_TRY(p, seedmap.ensure(sizeof(int) * (size_t)(n_steps + 1)));
+      SPADJ_CUDA_TRY(p, cudaMemcpyAsync(seedmap.ptr, seed_at->data(), sizeof(int) * (n_steps + 1),
+                                        cudaMemcpyHostToDevice, p->stream));
+      sm_dev = seedmap.as<int>();
+    }
+    spadj_status st;
+    const int S = (ckpt_slots <= 0 || ckpt_slots > n_steps) ? n_steps + 1 : ckpt_slots;
+    if (S == n_steps + 1) {  // store-all: one forward launch, one adjoint launch
+      SPADJ_CUDA_TRY(p, traj.ensure(sizeof(double) * sl * (size_t)(n_steps + 1)));
+      double* T = traj.as<double>();
+      double* xN = T + (size_t)n_steps * sl;
+      if ((st = forward(p, n_steps, x0, xN, T)) != SPADJ_OK) return st;
+      const double* yf = y_final_dev;
+      if (J_dev) {
+        if ((st = this->objective(p, SPADJ_OBJ_ENERGY, nullptr, xN, J_dev, seed_buf)) != SPADJ_OK) return st;
+        yf = seed_buf;
+      }
+      st = launch_adj(p, n_steps, n_steps, 0, T, yf, nullptr, grad, 1, sm_dev, seeds, nullptr);
+      if (st == SPADJ_OK && seed_at) SPADJ_CUDA_TRY(p, cudaStreamSynchronize(p->stream));  // pageable staging
+      return st;
+    }
+    const int so = P.order, rb = 2 * so - 1;
+    const size_t rbytes = sizeof(double) * sl * rb, ybytes = sizeof(double) * sl * so;
+    SPADJ_CUDA_TRY(p, rs.ensure(2 * rbytes));
+    SPADJ_CUDA_TRY(p, ys.ensure(2 * ybytes));
+    SPADJ_CUDA_TRY(p, slots.ensure(rbytes * (size_t)S));
+    CkptPlanner planner;
+    const int H = std::min(p->host_slots, n_steps);
+    std::vector<CkptOp> ops = H > 0 ? planner.plan2(n_steps, S, H) : planner.plan(n_steps, S);
+    if (H > 0) SPADJ_CUDA_TRY(p, hslots.ensure(rbytes * (size_t)H));
+    auto slot_ptr = [&](int k) {
+      return k < S ? slots.as<char>() + (size_t)k * rbytes : hslots.as<char>() + (size_t)(k - S) * rbytes;
+    };
+    double* R[2] = {rs.as<double>(), rs.as<double>() + sl * rb};
+    double* Yc[2] = {ys.as<double>(), ys.as<double>() + sl * so};
+    int ri = 0, yi = 0, recompute = 0, cur_step = 0;
+    bool have_seed = false;
+    // the restart state of X_0: X_0 and zero history
+    SPADJ_CUDA_TRY(p, cudaMemsetAsync(R[ri], 0, rbytes, p->stream));
+    SPADJ_CUDA_TRY(p, cudaMemcpyAsync(R[ri], x0, sizeof(double) * sl, cudaMemcpyDeviceToDevice, p->stream));
+    for (const CkptOp& op : ops) {
+      switch (op.type) {
+        case CK_STORE:
+          SPADJ_CUDA_TRY(p, cudaMemcpyAsync(slot_ptr(op.slot), R[ri], rbytes,
+                                            op.slot < S ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, p->stream));
+          break;
+        case CK_RESTORE:
+          if (cur_step != op.a) {
+            SPADJ_CUDA_TRY(p, cudaMemcpyAsync(R[ri], slot_ptr(op.slot), rbytes,
+                                              op.slot < S ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                              p->stream));
+            cur_step = op.a;
+          }
+          break;
+        case CK_ADVANCE:
+          if ((st = launch_traj(p, op.a, op.b - op.a, R[ri], rb, nullptr, nullptr, R[1 - ri], nullptr, 0)) != SPADJ_OK)
+            return st;
+          ri = 1 - ri;
+          recompute += op.b - op.a;
+          cur_step = op.b;
+          break;
+        case CK_OBJECTIVE: {
+          const double* yf = y_final_dev;
+          if (J_dev) {
+            if ((st = this->objective(p, SPADJ_OBJ_ENERGY, nullptr, R[ri], J_dev, seed_buf)) != SPADJ_OK) return st;
+            yf = seed_buf;
+          }
+          if ((st = launch_adj(p, n_steps, n_steps, n_steps, R[ri], yf, nullptr, Yc[yi], so, sm_dev, seeds, nullptr)) !=
+              SPADJ_OK)
+            return st;
+          have_seed = true;
+          break;
+        }
+        case CK_ADJOINT: {
+          if (!have_seed) return p->fail(SPADJ_ERR_INVALID, "gradient: schedule reached an adjoint step before the objective");
+          double* out = op.a == 0 ? grad : Yc[1 - yi];
+          if ((st = launch_adj(p, n_steps, op.a, op.a, R[ri], nullptr, Yc[yi], out, op.a == 0 ? 1 : so, sm_dev, seeds,
+                               nullptr)) != SPADJ_OK)
+            return st;
+          yi = 1 - yi;
+          break;
+        }
+        default:
+          break;
+      }
+    }
+    last_recompute = recompute;
+    if (seed_at || H > 0) SPADJ_CUDA_TRY(p, cudaStreamSynchronize(p->stream));  // pageable staging, host slots
     return SPADJ_OK;
   }
 
-  spadj_status adjoint(Problem* p, int n_steps, const double* trj, const double* y_final, double* grad) override {
+  spadj_status vjp(Problem* p, const double* x0, int n_steps, int ckpt_slots, const std::vector<int>& seed_at,
+                   const double* seeds, double* grad) override {
+    if (n_steps < 1) return p->fail(SPADJ_ERR_INVALID, "vjp: n_steps < 1");
+    return reverse(p, x0, n_steps, ckpt_slots, nullptr, &seed_at, seeds, grad, nullptr, nullptr);
+  }
+
+  spadj_status adjoint(Problem* p, int n_steps, const double* trj, const double* y_final, double* grad,
+                       double* grad_p) override {
     if (n_steps < 1) return p->fail(SPADJ_ERR_INVALID, "adjoint: n_steps < 1");
-    cudaEvent_t t = p->tic();
-    spadj_status s = dispatchQ(p, [&](auto q, auto o) {
-      adjoint_kernel<decltype(q)::value, decltype(o)::value><<<B, G, smem, p->stream>>>(P, n_steps, trj, y_final, grad,
-                                                                                      seed_dev, seeds_dev);
-    });
-    p->toc(t, KC_FUSED, (double)B * n_steps * (3 * fft_flops() + 2.0 * P.M + 12.0 * P.K));
-    return s;
+    if (grad_p) return p->fail(SPADJ_ERR_INVALID, "burgers: the problem has no parameters (grad_p must be NULL)");
+    return launch_adj(p, n_steps, n_steps, 0, trj, y_final, nullptr, grad, 1, nullptr, nullptr, nullptr);
   }
 
   spadj_status objective(Problem* p, int objective, const double* obj_data, const double* x, double* J_dev,
@@ -641,19 +817,15 @@ struct Burgers : EqImpl {
 
   spadj_status gradient(Problem* p, const double* x0, int n_steps, int objective, const double* obj_data,
                         int ckpt_slots, double* J_host, double* grad, double* grad_p) override {
-    (void)obj_data; (void)ckpt_slots; (void)grad_p;
+    (void)obj_data;
+    if (grad_p) return p->fail(SPADJ_ERR_INVALID, "burgers: the problem has no parameters (grad_p must be NULL)");
     if (objective != SPADJ_OBJ_ENERGY) return p->fail(SPADJ_ERR_UNSUPPORTED, "burgers: objective must be ENERGY");
     if (n_steps < 1) return p->fail(SPADJ_ERR_INVALID, "gradient: n_steps < 1");
     const size_t sl = state_len(0);
-    SPADJ_CUDA_TRY(p, traj.ensure(sizeof(double) * sl * (size_t)(n_steps + 1)));
     SPADJ_CUDA_TRY(p, seed.ensure(sizeof(double) * sl));
     SPADJ_CUDA_TRY(p, Jd.ensure(sizeof(double) * B));
-    double* T = traj.as<double>();
-    double* xN = T + (size_t)n_steps * sl;
-    spadj_status st = forward(p, n_steps, x0, xN, T);
-    if (st != SPADJ_OK) return st;
-    if ((st = this->objective(p, objective, obj_data, xN, Jd.as<double>(), seed.as<double>())) != SPADJ_OK) return st;
-    st = adjoint(p, n_steps, T, seed.as<double>(), grad);
+    spadj_status st = reverse(p, x0, n_steps, ckpt_slots, nullptr, nullptr, nullptr, grad, Jd.as<double>(),
+                              seed.as<double>());
     if (st != SPADJ_OK) return st;
     if (J_host) {
       SPADJ_CUDA_TRY(p, cudaMemcpyAsync(J_host, Jd.ptr, sizeof(double) * B, cudaMemcpyDeviceToHost, p->stream));
@@ -667,6 +839,10 @@ struct Burgers : EqImpl {
   ~Burgers() override {
     wm.release();
     seedmap.release();
+    rs.release();
+    ys.release();
+    slots.release();
+    hslots.release();
     traj.release();
     seed.release();
     Jd.release();

@@ -577,7 +577,7 @@ struct Couette : EqImpl {
   spadj_status energy(Problem* p, const double2* x, double* e_out, const double* scale, double2* seed) {
     cudaEvent_t t = p->tic();
     cou_energy_kernel<<<P, 128, 0, p->stream>>>(x, gmat.as<double>(), Kx, Ny, N, partial.as<double>(), scale, seed);
-    p->toc(t, KC_OBJECTIVE, 8.0 * (double)P * 3 * N * N);
+    p->toc(t, KC_OBJECTIVE, 4.0 * (double)P * 3 * N * N);  // real N x N matrix times complex vector: 2 FMA per entry
     spadj_status s = check_launch(p, "couette energy");
     if (s != SPADJ_OK) return s;
     sum_kernel<<<1, 128, 0, p->stream>>>(partial.as<double>(), P, e_out);
@@ -746,8 +746,10 @@ struct Couette : EqImpl {
     return SPADJ_OK;
   }
 
-  spadj_status adjoint(Problem* p, int n_steps, const double* traj, const double* y_final, double* grad) override {
+  spadj_status adjoint(Problem* p, int n_steps, const double* traj, const double* y_final, double* grad,
+                       double* grad_p) override {
     if (n_steps < 1) return p->fail(SPADJ_ERR_INVALID, "adjoint: n_steps < 1");
+    if (grad_p) return p->fail(SPADJ_ERR_UNSUPPORTED, "couette: the problem has no parameters (grad_p must be NULL)");
     const size_t sb = sizeof(double2) * ns;
     const double2* tr = reinterpret_cast<const double2*>(traj);
     SPADJ_CUDA_TRY(p, cudaMemcpyAsync(xbar.ptr, y_final, sb, cudaMemcpyDeviceToDevice, p->stream));
@@ -775,6 +777,99 @@ struct Couette : EqImpl {
   spadj_status vjp(Problem* p, const double* x0, int n_steps, int ckpt_slots, const std::vector<int>& seed_at,
                    const double* seeds, double* grad) override {
     return reverse(p, x0, n_steps, ckpt_slots, -1, seed_at, seeds, nullptr, grad);
+  }
+
+  // ---- one step at a time ----------------------------------------------------------------------
+  // Restart state of step n (X_n -> X_{n+1}): [x_n, x_{n-1}, f_{n-1}] (SBDF2; [x_n] for SBDF1), the
+  // augmented state the checkpoint slots hold.  Adjoint state: [Y_n, Y_{n+1}] (SBDF2; [Y_n] for
+  // SBDF1), the adjoint variables of eq. IMEX_adjoint in prognostic form (Y_m = Phi_m^H P xbar_m),
+  // the same vectors the reverse sweep keeps in its W ring.
+  int step_blocks(int which) const override { return which == 0 ? 2 * order - 1 : order; }
+
+  spadj_status step_forward(Problem* p, int n, const double* s_n, double* s_np1) override {
+    if (n < 0) return p->fail(SPADJ_ERR_INVALID, "step: n < 0");
+    const size_t sb = sizeof(double2) * ns;
+    const double2* in = reinterpret_cast<const double2*>(s_n);
+    double2* out = reinterpret_cast<double2*>(s_np1);
+    Ring r;
+    SPADJ_CUDA_TRY(p, cudaMemcpyAsync(st(Xr, r.xc), in, sb, cudaMemcpyDeviceToDevice, p->stream));
+    if (order == 2) {
+      SPADJ_CUDA_TRY(p, cudaMemcpyAsync(st(Xr, r.xp), in + ns, sb, cudaMemcpyDeviceToDevice, p->stream));
+      SPADJ_CUDA_TRY(p, cudaMemcpyAsync(st(Fr, r.fp), in + 2 * ns, sb, cudaMemcpyDeviceToDevice, p->stream));
+    }
+    spadj_status s = advance(p, r, n + 1);
+    if (s != SPADJ_OK) return s;
+    SPADJ_CUDA_TRY(p, cudaMemcpyAsync(out, st(Xr, r.xc), sb, cudaMemcpyDeviceToDevice, p->stream));
+    if (order == 2) {
+      SPADJ_CUDA_TRY(p, cudaMemcpyAsync(out + ns, st(Xr, r.xp), sb, cudaMemcpyDeviceToDevice, p->stream));
+      SPADJ_CUDA_TRY(p, cudaMemcpyAsync(out + 2 * ns, st(Fr, r.fp), sb, cudaMemcpyDeviceToDevice, p->stream));
+    }
+    return SPADJ_OK;
+  }
+
+  spadj_status step_tangent(Problem* p, int n, const double* s_n, const double* ds_n, double* ds_np1) override {
+    if (n < 0) return p->fail(SPADJ_ERR_INVALID, "step: n < 0");
+    const size_t sb = sizeof(double2) * ns;
+    SPADJ_CUDA_TRY(p, dXr.ensure(3 * sb));
+    SPADJ_CUDA_TRY(p, dFr.ensure(2 * sb));
+    const double2* in = reinterpret_cast<const double2*>(s_n);
+    const double2* din = reinterpret_cast<const double2*>(ds_n);
+    double2* dout = reinterpret_cast<double2*>(ds_np1);
+    Ring r;
+    SPADJ_CUDA_TRY(p, cudaMemcpyAsync(st(Xr, r.xc), in, sb, cudaMemcpyDeviceToDevice, p->stream));
+    SPADJ_CUDA_TRY(p, cudaMemcpyAsync(st(dXr, r.xc), din, sb, cudaMemcpyDeviceToDevice, p->stream));
+    if (order == 2) {
+      SPADJ_CUDA_TRY(p, cudaMemcpyAsync(st(Xr, r.xp), in + ns, sb, cudaMemcpyDeviceToDevice, p->stream));
+      SPADJ_CUDA_TRY(p, cudaMemcpyAsync(st(Fr, r.fp), in + 2 * ns, sb, cudaMemcpyDeviceToDevice, p->stream));
+      SPADJ_CUDA_TRY(p, cudaMemcpyAsync(st(dXr, r.xp), din + ns, sb, cudaMemcpyDeviceToDevice, p->stream));
+      SPADJ_CUDA_TRY(p, cudaMemcpyAsync(st(dFr, r.fp), din + 2 * ns, sb, cudaMemcpyDeviceToDevice, p->stream));
+    }
+    spadj_status s;
+    if ((s = evalF(p, st(Xr, r.xc), st(Fr, r.fc), Gf)) != SPADJ_OK) return s;
+    if ((s = evalJvp(p, Gf, st(dXr, r.xc), st(dFr, r.fc))) != SPADJ_OK) return s;
+    if ((s = step(p, n + 1, st(dXr, r.xc), st(dXr, r.xp), st(dFr, r.fc), st(dFr, r.fp), st(dXr, r.xn))) != SPADJ_OK)
+      return s;
+    r.advance();
+    SPADJ_CUDA_TRY(p, cudaMemcpyAsync(dout, st(dXr, r.xc), sb, cudaMemcpyDeviceToDevice, p->stream));
+    if (order == 2) {
+      SPADJ_CUDA_TRY(p, cudaMemcpyAsync(dout + ns, st(dXr, r.xp), sb, cudaMemcpyDeviceToDevice, p->stream));
+      SPADJ_CUDA_TRY(p, cudaMemcpyAsync(dout + 2 * ns, st(dFr, r.fp), sb, cudaMemcpyDeviceToDevice, p->stream));
+    }
+    return SPADJ_OK;
+  }
+
+  // eq. IMEX_adjoint at index n: xbar_n = sum_i (c_i^{n+i} J(X_n) - a_i^{n+i} M)^dagger Y_{n+i} + src,
+  // then Y_n = Phi_n^H P xbar_n (n >= 1); at n = 0 the first block of y_n is xbar_0 = dJ/dX_0.
+  // y_np1 = NULL stands for zero adjoint variables (the seed step at n = N with src = dJ/dX_N).
+  spadj_status step_adjoint(Problem* p, int n, const double* x_n, const double* y_np1, const double* src, double* y_n,
+                            double* gp_accum) override {
+    if (gp_accum) return p->fail(SPADJ_ERR_INVALID, "couette: the problem has no parameters (gp_accum must be NULL)");
+    if (n < 0) return p->fail(SPADJ_ERR_INVALID, "step: n < 0");
+    const size_t sb = sizeof(double2) * ns;
+    const double2* yin = reinterpret_cast<const double2*>(y_np1);
+    double2* yout = reinterpret_cast<double2*>(y_n);
+    double2* xb = xbar.as<double2>();
+    spadj_status s;
+    if (!yin) {
+      if (src) SPADJ_CUDA_TRY(p, cudaMemcpyAsync(xb, src, sb, cudaMemcpyDeviceToDevice, p->stream));
+      else SPADJ_CUDA_TRY(p, cudaMemsetAsync(xb, 0, sb, p->stream));
+      if (order == 2) SPADJ_CUDA_TRY(p, cudaMemsetAsync(W(n + 1), 0, sb, p->stream));
+    } else {
+      SPADJ_CUDA_TRY(p, cudaMemcpyAsync(W(n + 1), yin, sb, cudaMemcpyDeviceToDevice, p->stream));
+      if (order == 2) SPADJ_CUDA_TRY(p, cudaMemcpyAsync(W(n + 2), yin + ns, sb, cudaMemcpyDeviceToDevice, p->stream));
+      // every later step exists: the adjoint variables past the horizon are the caller's zeros
+      if ((s = reverse_index(p, n, 1 << 29, reinterpret_cast<const double2*>(x_n),
+                             reinterpret_cast<const double2*>(src), xb)) != SPADJ_OK)
+        return s;
+    }
+    if (n >= 1 && !yin) {
+      const double2* in[1] = {xb};
+      double w[1] = {1.0};
+      if ((s = solve(p, 1, step_order(n), 1, in, w, W(n))) != SPADJ_OK) return s;
+    }
+    SPADJ_CUDA_TRY(p, cudaMemcpyAsync(yout, n >= 1 ? W(n) : xb, sb, cudaMemcpyDeviceToDevice, p->stream));
+    if (order == 2) SPADJ_CUDA_TRY(p, cudaMemcpyAsync(yout + ns, W(n + 1), sb, cudaMemcpyDeviceToDevice, p->stream));
+    return SPADJ_OK;
   }
 
   // ---- Hessian-vector product ----------------------------------------------------------------
@@ -907,8 +1002,11 @@ struct Couette : EqImpl {
           for (int j = 0; j < N; ++j) { A[(size_t)i * N + j] -= l * A[(size_t)k * N + j]; I[(size_t)i * N + j] -= l * I[(size_t)k * N + j]; }
         }
       }
-      SPADJ_CUDA_TRY(p, ginv.ensure(sizeof(double) * I.size()));
-      SPADJ_CUDA_TRY(p, cudaMemcpy(ginv.ptr, I.data(), sizeof(double) * I.size(), cudaMemcpyHostToDevice));
+      std::vector<double> IT(I.size());  // stored transposed for cou_gram_kernel (G itself is symmetric)
+      for (int i = 0; i < N; ++i)
+        for (int j = 0; j < N; ++j) IT[(size_t)j * N + i] = I[(size_t)i * N + j];
+      SPADJ_CUDA_TRY(p, ginv.ensure(sizeof(double) * IT.size()));
+      SPADJ_CUDA_TRY(p, cudaMemcpy(ginv.ptr, IT.data(), sizeof(double) * IT.size(), cudaMemcpyHostToDevice));
     }
     SPADJ_CUDA_TRY(p, nrm.ensure(sizeof(double) * P));
     SPADJ_CUDA_TRY(p, g2.ensure(sizeof(double) * P));
@@ -920,7 +1018,7 @@ struct Couette : EqImpl {
     auto gram = [&](const double2* in, const DevBuf& mat, double2* out, double* nr) -> spadj_status {
       cudaEvent_t ev = p->tic();
       cou_gram_kernel<<<P, 128, 0, p->stream>>>(in, mat.as<double>(), Kx, Ny, N, out, nr);
-      p->toc(ev, KC_OBJECTIVE, 8.0 * (double)P * 3 * N * N);
+      p->toc(ev, KC_GRAM, 4.0 * (double)P * 3 * N * N);  // real N x N matrix times complex vector: 2 FMA per entry
       return check_launch(p, "couette gram");
     };
     auto normalise = [&](double* gout) -> spadj_status {

@@ -269,7 +269,7 @@ __global__ void cou_energy_kernel(const double2* __restrict__ x, const double* _
     double2 g = make_double2(0.0, 0.0);
     for (int k = 0; k < N; ++k) {
       const double2 c = x[base + k];
-      const double gv = __ldg(&Gm[i * N + k]);
+      const double gv = __ldg(&Gm[k * N + i]);  // G is symmetric: its [k][i] entry, read coalesced
       g.x = fma(gv, c.x, g.x);
       g.y = fma(gv, c.y, g.y);
     }
@@ -295,7 +295,9 @@ __global__ void integral_accum_kernel(const double* __restrict__ e, const double
 // Per-pencil energy-norm algebra of the resolvent power iteration (Mat = the Gram matrix
 // G = int T_m T_n dz or its inverse, N x N, applied to each of the three fields):
 //   out = Mat in, and nrm[p] = Re(in^H out) when nrm is set.
-__global__ void cou_gram_kernel(const double2* __restrict__ in, const double* __restrict__ Mat, int Kx, int Ny, int N,
+// MatT holds the matrix transposed ([k][i]), so that at a fixed k the threads of a warp (rows i)
+// read consecutive entries.
+__global__ void cou_gram_kernel(const double2* __restrict__ in, const double* __restrict__ MatT, int Kx, int Ny, int N,
                                 double2* __restrict__ out, double* __restrict__ nrm) {
   const int p = blockIdx.x;
   const int j = p / Kx, m = p % Kx;
@@ -306,7 +308,7 @@ __global__ void cou_gram_kernel(const double2* __restrict__ in, const double* __
     double2 g = make_double2(0.0, 0.0);
     for (int k = 0; k < N; ++k) {
       const double2 c = in[base + k];
-      const double mv = __ldg(&Mat[i * N + k]);
+      const double mv = __ldg(&MatT[k * N + i]);
       g.x = fma(mv, c.x, g.x);
       g.y = fma(mv, c.y, g.y);
     }

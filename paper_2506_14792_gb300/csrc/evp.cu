@@ -448,7 +448,7 @@ struct ShearEvp : EqImpl {
   spadj_status tangent(Problem* p, int, const double*, const double*, double*) override {
     return unsupported(p, "tangent");
   }
-  spadj_status adjoint(Problem* p, int, const double*, const double*, double*) override {
+  spadj_status adjoint(Problem* p, int, const double*, const double*, double*, double*) override {
     return unsupported(p, "adjoint");
   }
   spadj_status objective(Problem* p, int, const double*, const double*, double*, double*) override {

@@ -1112,12 +1112,20 @@ struct Kol : EqImpl {
     return SPADJ_OK;
   }
 
-  spadj_status adjoint(Problem* p, int n_steps, const double* traj, const double* y_final, double* grad) override {
+  spadj_status adjoint(Problem* p, int n_steps, const double* traj, const double* y_final, double* grad,
+                       double* grad_p) override {
     if (n_steps < 1) return p->fail(SPADJ_ERR_INVALID, "adjoint: n_steps < 1");
+    if (grad_p && !closure) return p->fail(SPADJ_ERR_INVALID, "adjoint: grad_p requested but the problem has no parameters");
     std::vector<int> seed_at(n_steps + 1, -1);
     seed_at[n_steps] = 0;
-    return run_adjoint(p, n_steps, const_cast<double2*>(reinterpret_cast<const double2*>(traj)), seed_at,
-                       reinterpret_cast<const double2*>(y_final), grad);
+    if (closure) SPADJ_CUDA_TRY(p, cudaMemsetAsync(gp.ptr, 0, sizeof(double) * cnn::n_params(), p->stream));
+    spadj_status s = run_adjoint(p, n_steps, const_cast<double2*>(reinterpret_cast<const double2*>(traj)), seed_at,
+                                 reinterpret_cast<const double2*>(y_final), grad);
+    if (s != SPADJ_OK) return s;
+    if (grad_p)
+      SPADJ_CUDA_TRY(p, cudaMemcpyAsync(grad_p, gp.ptr, sizeof(double) * cnn::n_params(), cudaMemcpyDeviceToDevice,
+                                        p->stream));
+    return SPADJ_OK;
   }
 
   spadj_status vjp(Problem* p, const double* x0, int n_steps, int, const std::vector<int>& seed_at,

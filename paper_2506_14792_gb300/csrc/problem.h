@@ -76,7 +76,7 @@ struct EqImpl {
   virtual spadj_status forward(Problem* p, int n_steps, const double* x0, double* x_out, double* traj) = 0;
   virtual spadj_status tangent(Problem* p, int n_steps, const double* x0, const double* dx0, double* dx_out) = 0;
   virtual spadj_status adjoint(Problem* p, int n_steps, const double* traj, const double* y_final,
-                               double* grad_x0) = 0;
+                               double* grad_x0, double* grad_p) = 0;
   virtual spadj_status objective(Problem* p, int objective, const double* obj_data, const double* x,
                                  double* J_dev, double* seed) = 0;
   virtual spadj_status gradient(Problem* p, const double* x0, int n_steps, int objective,
@@ -85,12 +85,29 @@ struct EqImpl {
   // Reverse sweep seeded by caller cotangents: seed_at[n] indexes `seeds` for X_n (or -1).
   virtual spadj_status vjp(Problem* p, const double* x0, int n_steps, int ckpt_slots,
                            const std::vector<int>& seed_at, const double* seeds, double* grad_x0) = 0;
+  // One step at a time (spadj_step_forward / _tangent / _adjoint).  step_blocks(0): state vectors
+  // in the restart state of one step, step_blocks(1): in the adjoint state; 0 = not provided.
+  virtual int step_blocks(int which) const { (void)which; return 0; }
+  virtual spadj_status step_forward(Problem* p, int n, const double* s_n, double* s_np1) {
+    (void)n; (void)s_n; (void)s_np1;
+    return step_unsupported(p);
+  }
+  virtual spadj_status step_tangent(Problem* p, int n, const double* s_n, const double* ds_n, double* ds_np1) {
+    (void)n; (void)s_n; (void)ds_n; (void)ds_np1;
+    return step_unsupported(p);
+  }
+  virtual spadj_status step_adjoint(Problem* p, int n, const double* x_n, const double* y_np1, const double* src,
+                                    double* y_n, double* gp_accum) {
+    (void)n; (void)x_n; (void)y_np1; (void)src; (void)y_n; (void)gp_accum;
+    return step_unsupported(p);
+  }
+  static spadj_status step_unsupported(Problem* p);
 };
 
 // Optional per-kernel-class timing: CUDA events recorded on the problem's stream around
 // every launch of the library, with the algorithmic FP64 flop count of that launch.
 enum KernelClass { KC_ZTRANSFORM = 0, KC_XFFT = 1, KC_POINTWISE = 2, KC_SOLVE = 3, KC_OBJECTIVE = 4, KC_FUSED = 5,
-                   KC_YFFT = 6, KC_COUNT = 7 };
+                   KC_YFFT = 6, KC_GRAM = 7, KC_COUNT = 8 };
 
 struct Timing {
   bool enabled = false;
@@ -157,6 +174,10 @@ struct Problem {
     return st;
   }
 };
+
+inline spadj_status EqImpl::step_unsupported(Problem* p) {
+  return p->fail(SPADJ_ERR_UNSUPPORTED, "step entry points are not provided for this equation set");
+}
 
 // Launch-error check after a kernel launch.
 inline spadj_status check_launch(Problem* p, const char* what) {

@@ -56,6 +56,8 @@ struct RB : EqImpl {
     cudaGraphExec_t gFwd[2] = {nullptr, nullptr};
     cudaGraphExec_t gFwdB[2] = {nullptr, nullptr};  // lane 1 forward step graphs
     cudaGraphExec_t gAdj[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    cudaGraphExec_t gStage[2] = {nullptr, nullptr};                           // lane 2 stage-1 graphs
+    cudaGraphExec_t gAdjS[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // lane 0 staged adjoint
   };
   std::vector<std::unique_ptr<OpSet>> opsets;
   OpSet* ops_cur = nullptr;
@@ -67,23 +69,26 @@ struct RB : EqImpl {
       seedbuf, slots, traj_tmp;
   HostBuf hslots;  // host tier of the two-level checkpoint schedule
   // Buffers of one forward step.  Lane 0 runs the forward sweep and the adjoint steps, lane 1
-  // the recomputation of checkpointed segments, concurrently on its own stream.
+  // the recomputation of checkpointed segments, concurrently on its own stream; in the reverse
+  // sweep of the fused scheme lane 2 computes the stage-1 grid fields of the next adjoint steps
+  // into ws[2], ws[3] (alternating by step parity).
   struct WS {
     DevBuf Z, Y, G0, G1, f0, f1, x1;
     DevBuf rx[4], rv[4], rf[4];  // generic scheme: stage values x_i, pre-solve vectors v_i, F(x_{i-1})
   };
   // generic scheme, lane 0: tangent stages and adjoint cotangents
   DevBuf tdx[4], tdv[4], tdf[4], axb[4], avb[4], afb[4], aacc, atmp, axs;
-  WS ws[2];
+  WS ws[4];
   WS* w = &ws[0];
   size_t zsmem = 0, xsmem = 0, ssmem = 0, csmem = 0, ctsmem = 0;
   bool fused = false;  // fused column stage (rb_colstep_kernel) usable for these sizes
   int xnb = 1;         // x-FFT launch variant, xvar(rows per CTA, threads) (tuned at creation)
   // internal streams (joined to the caller's stream by events) and captured step graphs
-  cudaStream_t gs = nullptr, gs2 = nullptr, gsB = nullptr;
+  cudaStream_t gs = nullptr, gs2 = nullptr, gsB = nullptr, gsC = nullptr;
   cudaEvent_t evIn = nullptr, evOut = nullptr, evFork = nullptr, evJoin = nullptr;
   cudaEvent_t evReady = nullptr, evFree = nullptr, evBdone = nullptr;  // lane handoffs
   cudaEvent_t evAdj[2] = {nullptr, nullptr}, evCopied[2] = {nullptr, nullptr};
+  cudaEvent_t evStaged[2] = {nullptr, nullptr}, evCdone = nullptr;  // lane 2 handoffs
   double2* Sb[2] = {nullptr, nullptr};  // state ping-pong buffers
   double2* SbB[2] = {nullptr, nullptr};  // lane 1 state ping-pong buffers
   double2* Yb[2] = {nullptr, nullptr};  // cotangent ping-pong buffers
@@ -205,9 +210,9 @@ struct RB : EqImpl {
       for (DevBuf* b : {&l.f0, &l.f1, &l.x1}) SPADJ_CUDA_TRY(p, b->ensure(sb));
     }
     if (generic) {
-      for (WS& l : ws)
+      for (WS* l : {&ws[0], &ws[1]})
         for (int i = 0; i < 4; ++i)
-          for (DevBuf* b : {&l.rx[i], &l.rv[i], &l.rf[i]}) SPADJ_CUDA_TRY(p, b->ensure(sb));
+          for (DevBuf* b : {&l->rx[i], &l->rv[i], &l->rf[i]}) SPADJ_CUDA_TRY(p, b->ensure(sb));
       for (int i = 0; i < 4; ++i)
         for (DevBuf* b : {&tdx[i], &tdv[i], &tdf[i], &axb[i], &avb[i], &afb[i]}) SPADJ_CUDA_TRY(p, b->ensure(sb));
       for (DevBuf* b : {&aacc, &atmp, &axs}) SPADJ_CUDA_TRY(p, b->ensure(sb));
@@ -223,8 +228,9 @@ struct RB : EqImpl {
     SPADJ_CUDA_TRY(p, cudaStreamCreateWithFlags(&gs, cudaStreamNonBlocking));
     SPADJ_CUDA_TRY(p, cudaStreamCreateWithFlags(&gs2, cudaStreamNonBlocking));
     SPADJ_CUDA_TRY(p, cudaStreamCreateWithFlags(&gsB, cudaStreamNonBlocking));
+    SPADJ_CUDA_TRY(p, cudaStreamCreateWithFlags(&gsC, cudaStreamNonBlocking));
     for (cudaEvent_t* e : {&evIn, &evOut, &evFork, &evJoin, &evReady, &evFree, &evBdone, &evAdj[0], &evAdj[1],
-                           &evCopied[0], &evCopied[1]})
+                           &evCopied[0], &evCopied[1], &evStaged[0], &evStaged[1], &evCdone})
       SPADJ_CUDA_TRY(p, cudaEventCreateWithFlags(e, cudaEventDisableTiming));
     SPADJ_CUDA_TRY(p, partial.ensure(sizeof(double) * Kx));
     SPADJ_CUDA_TRY(p, Jdev.ensure(sizeof(double)));
@@ -852,6 +858,24 @@ struct RB : EqImpl {
     return evalVjp(p, w->G0, 2, fb, al, 2, ad, be, xb0);
   }
 
+  // The fused adjoint step with its stage-1 grid fields (G0 of X_n, G1 of the stage value x1)
+  // already computed into sg by stage1_fused on another lane: the same kernels on the same data as
+  // step_adj, without the recomputation on the critical path.
+  spadj_status step_adj_staged(Problem* p, WS& sg, const double2* xb2, double2* xb0) {
+    spadj_status s;
+    { const double2* in[1] = {xb2}; double a[1] = {1.0};
+      if ((s = solve(p, 1, 1, in, a, st(vb2))) != SPADJ_OK) return s; }
+    { const double2* fb[1] = {st(vb2)}; double al[1] = {dt * A21};
+      if ((s = vjp_expand(p, 1, fb, al)) != SPADJ_OK) return s; }
+    if ((s = vjp_middle(p, sg.G1)) != SPADJ_OK) return s;
+    { const double2* ad[1] = {st(vb2)}; double be[1] = {cc};
+      if ((s = colstepT(p, 1, ad, be, st(vb1), st(vb2), dt * (A20 - cc * A10), dt * A10)) != SPADJ_OK) return s; }
+    if ((s = vjp_middle(p, sg.G0)) != SPADJ_OK) return s;
+    const double2* ad[2] = {st(vb2), st(vb1)};
+    double be[2] = {1.0 - cc, 1.0};
+    return vjp_fold(p, 2, ad, be, xb0);
+  }
+
   // ---- C-ABI operations ----------------------------------------------------------------------
   spadj_status transform(Problem* p, int kind, const double* in, double* out) override {
     // one scalar field: coefficients [Kx][N] <-> grid [Mz][Mx]
@@ -1021,6 +1045,42 @@ struct RB : EqImpl {
     return SPADJ_OK;
   }
 
+  // lane 2 (stream gsC, workspace ws[2 + c]): stage 1 of the step from Sb[c] (grid fields for the
+  // staged adjoint step)
+  spadj_status run_stage_lane2(Problem* p, int c) {
+    cudaStream_t main = p->stream;
+    p->stream = gsC;
+    w = &ws[2 + c];
+    spadj_status s = SPADJ_OK;
+    const double2* x0 = Sb[c];
+    if (!use_graphs(p)) {
+      s = stage1_fused(p, x0);
+    } else {
+      if (!ops_cur->gStage[c]) s = capture(p, &ops_cur->gStage[c], [&] { return stage1_fused(p, x0); });
+      if (s == SPADJ_OK) {
+        cudaError_t e = cudaGraphLaunch(ops_cur->gStage[c], p->stream);
+        if (e != cudaSuccess) s = p->fail(SPADJ_ERR_CUDA, std::string("rb: graph launch: ") + cudaGetErrorString(e));
+      }
+    }
+    w = &ws[0];
+    p->stream = main;
+    return s;
+  }
+
+  // lane 0: staged adjoint step with the grid fields of ws[2 + c]: Yb[yi] -> Yb[1 - yi]
+  spadj_status run_adj_staged(Problem* p, int c, int yi) {
+    WS& sg = ws[2 + c];
+    const double2* xb2 = Yb[yi];
+    double2* xb0 = Yb[1 - yi];
+    if (!use_graphs(p)) return step_adj_staged(p, sg, xb2, xb0);
+    if (!ops_cur->gAdjS[c][yi]) {
+      spadj_status s = capture(p, &ops_cur->gAdjS[c][yi], [&] { return step_adj_staged(p, sg, xb2, xb0); });
+      if (s != SPADJ_OK) return s;
+    }
+    SPADJ_CUDA_TRY(p, cudaGraphLaunch(ops_cur->gAdjS[c][yi], p->stream));
+    return SPADJ_OK;
+  }
+
   spadj_status forward(Problem* p, int n_steps, const double* x0, double* x_out, double* traj) override {
     if (n_steps < 0) return p->fail(SPADJ_ERR_INVALID, "forward: n_steps < 0");
     spadj_status ps = prepare_steps(p, n_steps);
@@ -1064,8 +1124,10 @@ struct RB : EqImpl {
     return SPADJ_OK;
   }
 
-  spadj_status adjoint(Problem* p, int n_steps, const double* traj, const double* y_final, double* grad) override {
+  spadj_status adjoint(Problem* p, int n_steps, const double* traj, const double* y_final, double* grad,
+                       double* grad_p) override {
     if (n_steps < 1) return p->fail(SPADJ_ERR_INVALID, "adjoint: n_steps < 1");
+    if (grad_p) return p->fail(SPADJ_ERR_INVALID, "rb: the problem has no parameters (grad_p must be NULL)");
     spadj_status ps = prepare_steps(p, n_steps);
     if (ps != SPADJ_OK) return ps;
     const size_t sb = sizeof(double2) * ns;
@@ -1082,6 +1144,78 @@ struct RB : EqImpl {
       yi = 1 - yi;
     }
     SPADJ_CUDA_TRY(p, cudaMemcpyAsync(grad, Yb[yi], sb, cudaMemcpyDeviceToDevice, p->stream));
+    return SPADJ_OK;
+  }
+
+  // ---- one step at a time (the same step graphs as the sweeps) -------------------------------
+  // Runge-Kutta schemes restart from X_n alone, and the adjoint state is the cotangent of X_n.
+  int step_blocks(int which) const override { (void)which; return 1; }
+
+  // operators of step n's size (built on first use)
+  spadj_status prepare_step(Problem* p, int n) {
+    if (n < 0) return p->fail(SPADJ_ERR_INVALID, "step: n < 0");
+    if (sched.empty()) return SPADJ_OK;
+    if (n >= (int)sched.size()) return p->fail(SPADJ_ERR_INVALID, "rb: step index beyond the step-size schedule");
+    OpSet* os = nullptr;
+    return opset_for(p, sched[n], &os);
+  }
+
+  spadj_status step_forward(Problem* p, int n, const double* s_n, double* s_np1) override {
+    spadj_status s = prepare_step(p, n);
+    if (s != SPADJ_OK) return s;
+    const size_t sb = sizeof(double2) * ns;
+    StreamScope scope(this, p);
+    SPADJ_CUDA_TRY(p, cudaMemcpyAsync(Sb[0], s_n, sb, cudaMemcpyDeviceToDevice, p->stream));
+    s = select_step(p, n);
+    if (s == SPADJ_OK) s = run_fwd(p, 0);
+    select_base();
+    if (s != SPADJ_OK) return s;
+    SPADJ_CUDA_TRY(p, cudaMemcpyAsync(s_np1, Sb[1], sb, cudaMemcpyDeviceToDevice, p->stream));
+    return SPADJ_OK;
+  }
+
+  spadj_status step_tangent(Problem* p, int n, const double* s_n, const double* ds_n, double* ds_np1) override {
+    spadj_status s = prepare_step(p, n);
+    if (s != SPADJ_OK) return s;
+    const size_t sb = sizeof(double2) * ns;
+    StreamScope scope(this, p);
+    double2* T[2] = {tmpx.as<double2>(), tmpy.as<double2>()};
+    SPADJ_CUDA_TRY(p, cudaMemcpyAsync(Sb[0], s_n, sb, cudaMemcpyDeviceToDevice, p->stream));
+    SPADJ_CUDA_TRY(p, cudaMemcpyAsync(T[0], ds_n, sb, cudaMemcpyDeviceToDevice, p->stream));
+    s = select_step(p, n);
+    if (s == SPADJ_OK) s = step_tan(p, Sb[0], T[0], Sb[1], T[1]);
+    select_base();
+    if (s != SPADJ_OK) return s;
+    SPADJ_CUDA_TRY(p, cudaMemcpyAsync(ds_np1, T[1], sb, cudaMemcpyDeviceToDevice, p->stream));
+    return SPADJ_OK;
+  }
+
+  // y_n = (dX_{n+1}/dX_n)^dagger y_{n+1} + src; y_{n+1} = NULL stands for a zero cotangent (then
+  // y_n = src, the seed of a reverse sweep at the final state).
+  spadj_status step_adjoint(Problem* p, int n, const double* x_n, const double* y_np1, const double* src, double* y_n,
+                            double* gp_accum) override {
+    if (gp_accum) return p->fail(SPADJ_ERR_INVALID, "rb: the problem has no parameters (gp_accum must be NULL)");
+    const size_t sb = sizeof(double2) * ns;
+    if (!y_np1) {
+      if (src) SPADJ_CUDA_TRY(p, cudaMemcpyAsync(y_n, src, sb, cudaMemcpyDeviceToDevice, p->stream));
+      else SPADJ_CUDA_TRY(p, cudaMemsetAsync(y_n, 0, sb, p->stream));
+      return SPADJ_OK;
+    }
+    spadj_status s = prepare_step(p, n);
+    if (s != SPADJ_OK) return s;
+    StreamScope scope(this, p);
+    SPADJ_CUDA_TRY(p, cudaMemcpyAsync(Sb[0], x_n, sb, cudaMemcpyDeviceToDevice, p->stream));
+    SPADJ_CUDA_TRY(p, cudaMemcpyAsync(Yb[0], y_np1, sb, cudaMemcpyDeviceToDevice, p->stream));
+    s = select_step(p, n);
+    if (s == SPADJ_OK) s = run_adj(p, 0, 0);
+    select_base();
+    if (s != SPADJ_OK) return s;
+    if (src) {  // the injection of the checkpointed sweep
+      axpy_kernel<<<64, 256, 0, p->stream>>>(Yb[1], Yb[1], 1.0, reinterpret_cast<const double2*>(src), 1.0, nullptr,
+                                             0.0, ns);
+      if ((s = check_launch(p, "rb step src")) != SPADJ_OK) return s;
+    }
+    SPADJ_CUDA_TRY(p, cudaMemcpyAsync(y_n, Yb[1], sb, cudaMemcpyDeviceToDevice, p->stream));
     return SPADJ_OK;
   }
 
@@ -1105,11 +1239,16 @@ struct RB : EqImpl {
   // (J to J_host).  objective_kind < 0: seeds supplied by the caller, seed_at[n] = index into
   // `seeds` ([n_seeds][state], device) of the cotangent injected at X_n, or -1.
   //
-  // Two lanes run the binomial schedule concurrently: lane 1 (stream gsB, workspace ws[1])
-  // executes the forward sweep, every recomputation and the checkpoint copies; lane 0 (the
-  // problem's internal stream) the objective and the adjoint steps.  The state X_k for the
-  // adjoint step k moves from lane 1 into the staging buffer Sb[k % 2], so lane 1 recomputes
-  // the states of the next adjoint step while lane 0 is still reversing step k.
+  // Lanes run the binomial schedule concurrently: lane 1 (stream gsB, workspace ws[1]) executes
+  // the forward sweep, every recomputation and the checkpoint copies; lane 0 (the problem's
+  // internal stream) the objective and the adjoint steps.  The state X_k for the adjoint step k
+  // moves from lane 1 into the staging buffer Sb[k % 2], so lane 1 recomputes the states of the
+  // next adjoint step while lane 0 is still reversing step k.  With the fused scheme a third lane
+  // (stream gsC) takes X_k from Sb[k % 2] and recomputes the stage-1 grid fields of step k into
+  // ws[2 + k % 2], and lane 0 runs only the rest of the adjoint step (step_adj_staged): the
+  // recomputation leaves the critical path.  Events: evCopied[c] (X_k in Sb[c]), evStaged[c]
+  // (grid fields in ws[2 + c], Sb[c] free), evAdj[c] (the adjoint step that read ws[2 + c] or
+  // Sb[c] is done).
   spadj_status reverse(Problem* p, const double* x0, int n_steps, int ckpt_slots, int objective_kind,
                        const double* obj_data, const std::vector<int>& seed_at, const double* seeds, double* J_host,
                        double* grad) {
@@ -1128,8 +1267,10 @@ struct RB : EqImpl {
     std::vector<CkptOp> ops = H > 0 ? planner.plan2(n_steps, S, H) : planner.plan(n_steps, S);
     if (H > 0) SPADJ_CUDA_TRY(p, hslots.ensure(sb * (size_t)H));
     StreamScope scope(this, p);
+    const bool staged = use_fused(p);
     SPADJ_CUDA_TRY(p, cudaEventRecord(evFree, p->stream));
     SPADJ_CUDA_TRY(p, cudaStreamWaitEvent(gsB, evFree, 0));
+    SPADJ_CUDA_TRY(p, cudaStreamWaitEvent(gsC, evFree, 0));
     int ciB = 0, yi = 0;
     SPADJ_CUDA_TRY(p, cudaMemcpyAsync(SbB[ciB], x0, sb, cudaMemcpyDeviceToDevice, gsB));
     int cur_step = 0;
@@ -1143,13 +1284,14 @@ struct RB : EqImpl {
       if (objective_kind >= 0 || n < 0 || n >= (int)seed_at.size() || seed_at[n] < 0) return nullptr;
       return reinterpret_cast<const double2*>(seeds) + (size_t)seed_at[n] * ns;
     };
-    // X_k (current state of lane 1) -> Sb[k % 2] for lane 0
-    auto handoff = [&](int k) -> spadj_status {
+    // X_k (current state of lane 1) -> Sb[k % 2] for lane 0 (main_reads) or lane 2
+    auto handoff = [&](int k, bool main_reads) -> spadj_status {
       const int c = k & 1;
       SPADJ_CUDA_TRY(p, cudaStreamWaitEvent(gsB, evAdj[c], 0));  // the step that last read Sb[c] is done
+      if (staged) SPADJ_CUDA_TRY(p, cudaStreamWaitEvent(gsB, evStaged[c], 0));  // lane 2 has read Sb[c]
       SPADJ_CUDA_TRY(p, cudaMemcpyAsync(Sb[c], SbB[ciB], sb, cudaMemcpyDeviceToDevice, gsB));
       SPADJ_CUDA_TRY(p, cudaEventRecord(evCopied[c], gsB));
-      SPADJ_CUDA_TRY(p, cudaStreamWaitEvent(p->stream, evCopied[c], 0));
+      if (main_reads) SPADJ_CUDA_TRY(p, cudaStreamWaitEvent(p->stream, evCopied[c], 0));
       return SPADJ_OK;
     };
     for (const CkptOp& op : ops) {
@@ -1178,7 +1320,7 @@ struct RB : EqImpl {
           cur_step = op.b;
           break;
         case CK_OBJECTIVE:
-          if ((s = handoff(n_steps)) != SPADJ_OK) return s;
+          if ((s = handoff(n_steps, true)) != SPADJ_OK) return s;
           if (objective_kind >= 0) {
             if ((s = objective(p, objective_kind, obj_data, reinterpret_cast<const double*>(Sb[n_steps & 1]),
                                Jdev.as<double>(), reinterpret_cast<double*>(Yb[yi]))) != SPADJ_OK)
@@ -1194,9 +1336,24 @@ struct RB : EqImpl {
         case CK_ADJOINT: {
           if (!have_seed) return p->fail(SPADJ_ERR_INVALID, "gradient: schedule reached an adjoint step before the objective");
           const int c = op.a & 1;
-          if ((s = handoff(op.a)) != SPADJ_OK) return s;
+          if ((s = handoff(op.a, !staged)) != SPADJ_OK) return s;
           s = select_step(p, op.a);
-          if (s == SPADJ_OK) s = run_adj(p, c, yi);
+          if (s == SPADJ_OK && staged) {
+            // lane 2: stage 1 of step a from Sb[c] into ws[2 + c], once lane 0 has finished the
+            // adjoint step that last read ws[2 + c]
+            cudaError_t e = cudaStreamWaitEvent(gsC, evCopied[c], 0);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(gsC, evAdj[c], 0);
+            if (e != cudaSuccess) s = p->fail(SPADJ_ERR_CUDA, std::string("rb: lane 2 wait: ") + cudaGetErrorString(e));
+            if (s == SPADJ_OK) s = run_stage_lane2(p, c);
+            if (s == SPADJ_OK) {
+              e = cudaEventRecord(evStaged[c], gsC);
+              if (e == cudaSuccess) e = cudaStreamWaitEvent(p->stream, evStaged[c], 0);
+              if (e != cudaSuccess) s = p->fail(SPADJ_ERR_CUDA, std::string("rb: lane 2 event: ") + cudaGetErrorString(e));
+            }
+            if (s == SPADJ_OK) s = run_adj_staged(p, c, yi);
+          } else if (s == SPADJ_OK) {
+            s = run_adj(p, c, yi);
+          }
           select_base();
           if (s != SPADJ_OK) return s;
           SPADJ_CUDA_TRY(p, cudaEventRecord(evAdj[c], p->stream));
@@ -1214,6 +1371,8 @@ struct RB : EqImpl {
     last_recompute = recompute;
     SPADJ_CUDA_TRY(p, cudaEventRecord(evBdone, gsB));
     SPADJ_CUDA_TRY(p, cudaStreamWaitEvent(p->stream, evBdone, 0));
+    SPADJ_CUDA_TRY(p, cudaEventRecord(evCdone, gsC));
+    SPADJ_CUDA_TRY(p, cudaStreamWaitEvent(p->stream, evCdone, 0));
     SPADJ_CUDA_TRY(p, cudaMemcpyAsync(grad, Yb[yi], sb, cudaMemcpyDeviceToDevice, p->stream));
     if (J_host && objective_kind >= 0) {
       SPADJ_CUDA_TRY(p, cudaMemcpyAsync(J_host, Jdev.ptr, sizeof(double), cudaMemcpyDeviceToHost, p->stream));
@@ -1236,19 +1395,20 @@ struct RB : EqImpl {
   }
 
   ~RB() override {
-    for (cudaStream_t st : {gs, gs2, gsB})
+    for (cudaStream_t st : {gs, gs2, gsB, gsC})
       if (st) cudaStreamSynchronize(st);
     for (auto& os : opsets) {
       for (cudaGraphExec_t g : {os->gFwd[0], os->gFwd[1], os->gFwdB[0], os->gFwdB[1], os->gAdj[0][0], os->gAdj[0][1],
-                                os->gAdj[1][0], os->gAdj[1][1]})
+                                os->gAdj[1][0], os->gAdj[1][1], os->gStage[0], os->gStage[1], os->gAdjS[0][0],
+                                os->gAdjS[0][1], os->gAdjS[1][0], os->gAdjS[1][1]})
         if (g) cudaGraphExecDestroy(g);
       os->phi.release();
       os->phiT.release();
     }
     for (cudaEvent_t e : {evIn, evOut, evFork, evJoin, evReady, evFree, evBdone, evAdj[0], evAdj[1], evCopied[0],
-                          evCopied[1]})
+                          evCopied[1], evStaged[0], evStaged[1], evCdone})
       if (e) cudaEventDestroy(e);
-    for (cudaStream_t st : {gs, gs2, gsB})
+    for (cudaStream_t st : {gs, gs2, gsB, gsC})
       if (st) cudaStreamDestroy(st);
     for (WS& l : ws) {
       for (DevBuf* b : {&l.Z, &l.Y, &l.G0, &l.G1, &l.f0, &l.f1, &l.x1}) b->release();

@@ -81,14 +81,28 @@ _SIGS = {
     "spadj_checkpoint_schedule": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "spadj_forward": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp]),
     "spadj_tangent": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp]),
-    "spadj_adjoint": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp]),
+    "spadj_adjoint": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp, _vp]),
+    "spadj_step_forward": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp]),
+    "spadj_step_tangent": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp]),
+    "spadj_step_adjoint": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp, _vp, _vp]),
     "spadj_objective": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp, _vp]),
     "spadj_gradient": (ctypes.c_int, [_vp, _vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int, _vp, _vp, _vp]),
     "spadj_timing": (ctypes.c_int, [_vp, ctypes.c_int]),
     "spadj_timing_report": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                             ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_long)]),
     "spadj_last_error": (ctypes.c_char_p, [_vp]),
+    "spadj_fp64_peak": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_double)]),
 }
+
+
+def fp64_peak(stream=None, iters=200000):
+    """Measured FP64 FMA throughput of the current device (GFLOP/s, timed duration in ms)."""
+    import torch
+    st = torch.cuda.current_stream() if stream is None else stream
+    g, ms = ctypes.c_double(), ctypes.c_double()
+    _chk(None, lib().spadj_fp64_peak(ctypes.c_void_p(st.cuda_stream), int(iters), ctypes.byref(g), ctypes.byref(ms)))
+    return g.value, ms.value
 
 
 def lib():
@@ -227,11 +241,36 @@ class Problem:
                                           _ptr(_as_f64(dx_out, n, "dx_out"))))
         return dx_out
 
-    def adjoint(self, n_steps, traj, y_final, grad_x0):
+    def adjoint(self, n_steps, traj, y_final, grad_x0, grad_p=None):
         n = self.state_len(0)
+        gp = None if grad_p is None else _ptr(_as_f64(grad_p, self.state_len(2), "grad_p"))
         _chk(self.h, lib().spadj_adjoint(self.h, n_steps, _ptr(_as_f64(traj, n * (n_steps + 1), "traj")),
-                                          _ptr(_as_f64(y_final, n, "y_final")), _ptr(_as_f64(grad_x0, n, "grad_x0"))))
+                                          _ptr(_as_f64(y_final, n, "y_final")), _ptr(_as_f64(grad_x0, n, "grad_x0")),
+                                          gp))
         return grad_x0
+
+    def step_forward(self, n, s_n, s_np1):
+        """Restart state s_{n+1} from s_n (spadj_state_len(4) float64 each)."""
+        m = self.state_len(4)
+        _chk(self.h, lib().spadj_step_forward(self.h, int(n), _ptr(_as_f64(s_n, m, "s_n")),
+                                               _ptr(_as_f64(s_np1, m, "s_np1"))))
+        return s_np1
+
+    def step_tangent(self, n, s_n, ds_n, ds_np1):
+        m = self.state_len(4)
+        _chk(self.h, lib().spadj_step_tangent(self.h, int(n), _ptr(_as_f64(s_n, m, "s_n")),
+                                               _ptr(_as_f64(ds_n, m, "ds_n")), _ptr(_as_f64(ds_np1, m, "ds_np1"))))
+        return ds_np1
+
+    def step_adjoint(self, n, x_n, y_np1, y_n, src=None, gp_accum=None):
+        """Adjoint state y_n from y_{n+1} (None = zero) at the primal state x_n; src = dJ/dX_n."""
+        n0, m = self.state_len(0), self.state_len(5)
+        yp = None if y_np1 is None else _ptr(_as_f64(y_np1, m, "y_np1"))
+        sp = None if src is None else _ptr(_as_f64(src, n0, "src"))
+        gp = None if gp_accum is None else _ptr(_as_f64(gp_accum, self.state_len(2), "gp_accum"))
+        _chk(self.h, lib().spadj_step_adjoint(self.h, int(n), _ptr(_as_f64(x_n, n0, "x_n")), yp, sp,
+                                               _ptr(_as_f64(y_n, m, "y_n")), gp))
+        return y_n
 
     def objective(self, x, J_dev, seed, objective=SPADJ_OBJ_ENERGY, obj_data=None):
         n = self.state_len(0)
@@ -315,7 +354,8 @@ class Problem:
                                             _ptr(_as_f64(gains, self.desc.n[1] * (self.desc.n[0] // 2), "gains"))))
         return gains
 
-    KERNEL_CLASSES = ("z_transform", "x_fft", "pointwise", "pencil_solve", "objective", "fused_trajectory", "y_fft")
+    KERNEL_CLASSES = ("z_transform", "x_fft", "pointwise", "pencil_solve", "objective", "fused_trajectory", "y_fft",
+                      "gram")
 
     def timing(self, enable=True):
         _chk(self.h, lib().spadj_timing(self.h, int(bool(enable))))

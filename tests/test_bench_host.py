@@ -49,6 +49,9 @@ def test_hbm_fraction(bench):
     (["--workload", "rb", "--dt-blocks", "50", "--nsteps", "200"],
      "rayleigh_benard2d_256x64_Ra1e6_rk222_200steps_dtblocks50",
      lambda w: w.schedule()[49] == w.dt and w.schedule()[50] == 0.5 * w.dt and len(w.schedule()) == 200),
+    (["--workload", "rb", "--size", "128,32", "--dt-blocks", "50", "--nsteps", "200"],
+     "rayleigh_benard2d_128x32_Ra1e6_rk222_200steps_dtblocks50",
+     lambda w: w.Nx == 128 and w.Nz == 32 and w.dt_blocks == 50 and len(w.schedule()) == 200),
     (["--workload", "burgers", "--scheme", "sbdf4"], "burgers1d_N256_sbdf4_1000steps",
      lambda w: w.ORDERS[w.scheme] == 4),
     (["--workload", "couette", "--op", "hvp", "--size", "64,32,32", "--nsteps", "100"],

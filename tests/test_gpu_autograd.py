@@ -56,3 +56,35 @@ def test_burgers_autograd_observation_misfit():
     assert rel_err(host(x0.grad), g) < TOL
     lv = float(loss.detach())
     assert abs(lv - 0.5 * sum(np.sum(np.abs(X[n] - ob[i]) ** 2) for i, n in enumerate(obs))) < 1e-10 * lv
+
+
+@pytest.mark.parametrize("scheme", [2, 4])
+def test_autograd_forward_keeps_only_requested_states(scheme):
+    """Several observation steps on a long multistep horizon: the forward pass advances the restart
+    state one step at a time and stores only the observed states (no (n+1)-state trajectory), the
+    gradient (checkpointed backward) equals the store-all one bitwise, and the states equal
+    spadj_forward's."""
+    from paper_2506_14792_gb300 import spadj
+    from paper_2506_14792_gb300.autograd import trajectory
+    N, B, dt, n = 256, 64, 1e-3, 400
+    obs = (0, 50, 399, 400, 7)
+    p = spadj.Problem(spadj.SPADJ_BURGERS1D, scheme, [N], [2 * np.pi], [0.01], dt, batch=B)
+    X0 = dev(synthetic.burgers_ic(N, batch=B, seed=4))
+    W = dev(synthetic.random_coeffs((len(obs), B, N // 2), seed=6))
+    state_bytes = X0.numel() * 16
+    grads = []
+    for slots in (0, 6):
+        x0 = X0.clone().requires_grad_(True)
+        torch.cuda.synchronize()
+        torch.cuda.reset_peak_memory_stats()
+        base = torch.cuda.memory_allocated()
+        outs = trajectory(p, x0, obs, ckpt_slots=slots)
+        torch.cuda.synchronize()
+        assert torch.cuda.max_memory_allocated() - base < 40 * state_bytes  # O(observations), not O(n) = 401
+        for i, m in enumerate(obs):
+            ref = torch.empty_like(X0)
+            p.forward(m, X0, ref)
+            assert torch.equal(outs[i], ref)
+        (W.conj() * outs).real.sum().backward()
+        grads.append(x0.grad)
+    assert torch.equal(grads[0], grads[1])
