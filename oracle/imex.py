@@ -39,7 +39,22 @@ def sbdf_coeffs(n, order, dt):
     The scheme falls back to a lower order while fewer than ``order`` past steps
     exist (the paper: "revert to lower order multistep IMEX schemes for early
     iterations").  c[0] is unused and set to 0.
+
+    dt is a scalar (constant step) or a sequence of step sizes (step n spans dt[n-1]); with a
+    sequence the weights come from the scheme's definition on the actual nodes
+    t_n, t_{n-1}, ..., t_{n-s} (sbdf_weights_nodes): variable-step SBDF, which the paper's
+    timesteppers need when the timestep changes (Supplementary A.4).
     """
+    if np.ndim(dt):
+        s = min(n, order)
+        h = [float(dt[n - 1 - i]) for i in range(s)]  # h_n, h_{n-1}, ...: t_{n-i} - t_{n-i-1}
+        nodes = [0.0]
+        for i in range(s):
+            nodes.append(nodes[-1] - h[i])
+        a, c = sbdf_weights_nodes(nodes)
+        b = np.zeros(s + 1)
+        b[0] = 1.0
+        return np.array(a), b, np.array(c)
     s = min(n, order)
     if s == 1:  # backward/forward Euler
         return (np.array([1.0 / dt, -1.0 / dt]), np.array([1.0, 0.0]), np.array([0.0, 1.0]))
@@ -83,6 +98,38 @@ def sbdf_weights(s):
         for j in range(1, s + 1):
             if j != i:
                 v *= (0 - nodes[j]) / (nodes[i] - nodes[j])
+        c.append(v)
+    return a, c
+
+
+def sbdf_weights_nodes(nodes):
+    """SBDF weights from the scheme's definition on arbitrary nodes: nodes[i] = t_{n-i} - t_n
+    (nodes[0] = 0, decreasing).  a_i = d/dt at t_n of the Lagrange basis polynomial of t_{n-i}
+    through all the nodes (backward differentiation, in units of 1/time); c_i (i >= 1) = the
+    Lagrange basis polynomial of t_{n-i} through t_{n-1}, ..., t_{n-s}, evaluated at t_n
+    (extrapolation of F); c_0 = 0.  Floats in, floats out (sbdf_weights is the rational,
+    constant-step form)."""
+    s = len(nodes) - 1
+    a = []
+    for i in range(s + 1):
+        others = [nodes[j] for j in range(s + 1) if j != i]
+        den = 1.0
+        for o in others:
+            den *= nodes[i] - o
+        num = 0.0
+        for k in range(len(others)):
+            term = 1.0
+            for m, o in enumerate(others):
+                if m != k:
+                    term *= -o
+            num += term
+        a.append(num / den)
+    c = [0.0]
+    for i in range(1, s + 1):
+        v = 1.0
+        for j in range(1, s + 1):
+            if j != i:
+                v *= (0.0 - nodes[j]) / (nodes[i] - nodes[j])
         c.append(v)
     return a, c
 
