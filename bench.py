@@ -135,8 +135,8 @@ class Burgers:
         self.dof = N
         self.K, self.M = N // 2, 3 * N // 2
         self.scheme = scheme
-        if scheme != "sbdf2":
-            self.name = "burgers1d_N%d_%s_%dsteps" % (N, scheme, nsteps)
+        if scheme != "sbdf2" or batch != 16384:
+            self.name = "burgers1d_N%d_%s_%dsteps%s" % (N, scheme, nsteps, "" if batch == 16384 else "_b%d" % batch)
 
     def config(self):
         return {"workload": self.name, "N": self.N, "nu": self.nu, "dt": self.dt, "steps": self.nsteps,
@@ -195,7 +195,7 @@ class Burgers:
     def cpu_sample(self):
         from oracle import burgers as ob
         o = ob.Burgers(self.N, self.nu)
-        Bs = 256
+        Bs = min(256, self.B)
         X0 = self.X0_host[:Bs] if hasattr(self, "X0_host") else synthetic.burgers_ic(self.N, batch=Bs, seed=self.seed)
         t = time.perf_counter()
         ob.gradient(o, X0, self.nsteps, self.dt, order=self.ORDERS[self.scheme])
@@ -232,6 +232,12 @@ class RayleighBenard:
                 **({"dt_schedule": "dt and dt/2 alternating every %d steps" % self.dt_blocks}
                    if self.dt_blocks else {}),
                 "checkpoint_slots": self.slots, "dof": self.dof,
+                **({"parity": "J and dJ/dX_0 of this exact input and horizon match the FP64 oracle element by "
+                              "element to 1e-10 relative (tests/test_gpu_rb.py::"
+                              "test_full_horizon_gradient_matches_oracle_golden; the oracle's own rounding-order "
+                              "spread at 2000 steps is 1.1e-14)"}
+                   if (self.Nx, self.Nz, self.nsteps, self.scheme, self.dt_blocks) == (256, 64, 2000, "rk222", 0)
+                   else {}),
                 "l2": "L2 flushed between timed iterations (256 MB write); working set ~60 MB fits L2"}
 
     def units_per_step(self):
@@ -616,8 +622,244 @@ class CouetteResolvent:
             "each" % (n, self.n_iter), el
 
 
+class KolmogorovMembers(KolmogorovBatch):
+    """The batched Kolmogorov workload (same 64 members, observations and horizon) with every
+    member as a problem of its own: 64 gradient calls per step, each a persistent launch over one
+    member.  Against the batched line this measures what the single mixed-resolution launch gains;
+    both compute the same gradient (checked member by member at a 100-step horizon in setup)."""
+    name = "kolmogorov2d_members64_mixed128-512_Re100_sbdf2_2000steps_4dvar8"
+
+    def setup(self, device):
+        import torch
+        from paper_2506_14792_gb300 import spadj
+        self.torch, self.sp = torch, spadj
+        pack = lambda arrs: np.concatenate([a.ravel() for a in arrs])
+        ics = [synthetic.kolmogorov_ic(n, 100 + i) for i, n in enumerate(self.sizes)]
+        truths = [synthetic.kolmogorov_ic(n, 5000 + i) for i, n in enumerate(self.sizes)]
+        self.x0_host = pack(ics)
+        # per-member agreement with the batched launch at a short horizon (same kernels per member)
+        self.check = self._compare_with_batch(device, ics, truths, 100)
+        self.members, self.x0m, self.gm = [], [], []
+        for i, n in enumerate(self.sizes):
+            p = spadj.Problem(spadj.SPADJ_KOLMOGOROV2D, spadj.SPADJ_SBDF2, [n], [2 * np.pi], [self.Re, 0.0], self.dt,
+                              batch=1)
+            p.set_observations(self.obs_steps(), self._obs(p, torch.from_numpy(truths[i].ravel()).to(device),
+                                                           self.obs_steps()), 32)
+            self.members.append(p)
+            self.x0m.append(torch.from_numpy(ics[i].ravel()).to(device))
+            self.gm.append(torch.empty_like(self.x0m[-1]))
+        self.p = self.members[0]
+        self.x0 = torch.from_numpy(self.x0_host).to(device)
+        self.x0_pin = torch.from_numpy(self.x0_host).pin_memory()
+        self.grad_pin = torch.empty(self.x0.shape, dtype=torch.complex128).pin_memory()
+        self.x0_dev2 = torch.empty_like(self.x0)
+        self.grad = torch.empty_like(self.x0)
+
+    @staticmethod
+    def _obs(p, truth, steps):
+        import torch
+        out, cur, last = [], truth, 0
+        for k in steps:
+            nxt = torch.empty_like(cur)
+            p.forward(k - last, cur, nxt)
+            out.append(nxt)
+            cur, last = nxt, k
+        return torch.stack(out).contiguous()
+
+    def _compare_with_batch(self, device, ics, truths, nsteps):
+        import torch
+        sp = self.sp
+        k = max(1, nsteps // 8)
+        steps = [k * (i + 1) for i in range(8)]
+        pack = lambda arrs: torch.from_numpy(np.concatenate([a.ravel() for a in arrs])).to(device)
+        pb = sp.Problem(sp.SPADJ_KOLMOGOROV2D, sp.SPADJ_SBDF2, [128], [2 * np.pi], [self.Re, 0.0], self.dt, batch=64,
+                        batch_n=self.sizes)
+        pb.set_observations(steps, self._obs(pb, pack(truths), steps), 32)
+        x0 = pack(ics)
+        gb = torch.empty_like(x0)
+        pb.gradient(x0, nsteps, gb, objective=sp.SPADJ_OBJ_FOURDVAR)
+        worst, off = 0.0, 0
+        for i, n in enumerate(self.sizes):
+            p = sp.Problem(sp.SPADJ_KOLMOGOROV2D, sp.SPADJ_SBDF2, [n], [2 * np.pi], [self.Re, 0.0], self.dt, batch=1)
+            p.set_observations(steps, self._obs(p, torch.from_numpy(truths[i].ravel()).to(device), steps), 32)
+            g = torch.empty(ics[i].size, dtype=torch.complex128, device=device)
+            p.gradient(torch.from_numpy(ics[i].ravel()).to(device), nsteps, g, objective=sp.SPADJ_OBJ_FOURDVAR)
+            ref = gb[off:off + ics[i].size]
+            worst = max(worst, float((g - ref).abs().max() / ref.abs().max()))
+            off += ics[i].size
+            p.close()
+        pb.close()
+        return {"horizon": nsteps, "max_rel_diff_member_vs_batched": worst}
+
+    def config(self):
+        c = KolmogorovBatch.config(self)
+        c.update({"workload": self.name, "execution": "64 problems of one member each, gradients called in turn",
+                  "vs_batched_launch": self.check})
+        return c
+
+    def step(self, ev=None):
+        for p, x, g in zip(self.members, self.x0m, self.gm):
+            p.gradient(x, self.nsteps, g, objective=self.sp.SPADJ_OBJ_FOURDVAR, want_J=False)
+
+    def forward_step(self):
+        for p, x, g in zip(self.members, self.x0m, self.gm):
+            p.forward(self.nsteps, x, g)
+
+    def e2e_step(self):
+        self.x0_dev2.copy_(self.x0_pin, non_blocking=True)
+        off = 0
+        for p, x, g in zip(self.members, self.x0m, self.gm):
+            n = x.numel()
+            p.gradient(self.x0_dev2[off:off + n], self.nsteps, self.grad[off:off + n],
+                       objective=self.sp.SPADJ_OBJ_FOURDVAR)
+            off += n
+        self.grad_pin.copy_(self.grad, non_blocking=True)
+
+
+class Closure:
+    """Learned closure (coarse 64^2 Kolmogorov at Re = 1000 plus the 4-layer 3x3 CNN, 32 channels,
+    BF16 operands with FP32 accumulation, FP64 solver) trained through the coarse adjoint on fine
+    1024^2 trajectories the solver generates from seeded k^-3 fields (spun up 400 fine steps).
+    One bench step = one training iteration: the gradient of the 4D-Var misfit over 128 windows of
+    16 coarse steps (dt_c = 4e-3 = 16 fine steps) with respect to the initial states and the CNN
+    parameters (spadj_gradient with grad_p), then one Adam step (spadj_adam).  In setup the
+    network is trained (150 iterations, model selection on 16 validation windows every 25) and the
+    plain coarse, closure and fine solves are timed per window-step and judged on 16 held-out
+    windows against the restricted fine solution at T/4, T/2 and T."""
+    metric = "closure training window*steps/s through the adjoint (coarse 64^2 + BF16 CNN, FP64 solver)"
+    unit = "window*steps/s"
+    name = "closure_kolmogorov64_cnn32_Re1000_fine1024_128windows_16steps"
+    NF, NC, RE, DTF, RATIO, NCO, SPIN = 1024, 64, 1000.0, 2.5e-4, 16, 16, 400
+
+    def __init__(self, ntrain=128, nval=16, ntest=16, train_iters=150):
+        self.ntrain, self.nval, self.ntest, self.train_iters = ntrain, nval, ntest, train_iters
+        self.flush_l2 = False
+        self.B = ntrain
+        self.dt_c = self.DTF * self.RATIO
+
+    def units_per_step(self):
+        return self.ntrain * self.NCO
+
+    def _data(self, seeds):
+        import torch
+        from paper_2506_14792_gb300 import closure_training as ct
+        x0 = torch.from_numpy(np.concatenate([synthetic.kolmogorov_ic(self.NF, s).ravel() for s in seeds])).cuda()
+        return ct.make_dataset(x0, len(seeds), self.NF, self.NC, self.RE, self.DTF, self.RATIO, self.NCO,
+                               spin=self.SPIN)
+
+    def _per_step_us(self, fn, steps):
+        import torch
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        fn()
+        torch.cuda.synchronize()
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return 1e3 * e0.elapsed_time(e1) / steps
+
+    def setup(self, device):
+        import torch
+        from paper_2506_14792_gb300 import closure_training as ct
+        from paper_2506_14792_gb300 import spadj
+        self.torch, self.sp, self.ct = torch, spadj, ct
+        t0 = time.perf_counter()
+        self.tr = self._data(range(1000, 1000 + self.ntrain))
+        va = self._data(range(3000, 3000 + self.nval))
+        te = self._data(range(2000, 2000 + self.ntest))
+        t_data = time.perf_counter() - t0
+        params = torch.from_numpy(synthetic.cnn_params(7, scale_out=0.01)).to(device)
+        t0 = time.perf_counter()
+        best, hist = ct.train_selected(params, self.tr, self.ntrain, va, self.nval, self.NC, self.RE, self.dt_c,
+                                       iters=self.train_iters, every=25, lr=3e-3)
+        t_train = time.perf_counter() - t0
+        at = [self.NCO // 4, self.NCO // 2, self.NCO]
+        zero = torch.zeros_like(best)
+        plain = ct.rollout_errors(zero, te, self.ntest, self.NC, self.RE, self.dt_c, at)
+        cnn = ct.rollout_errors(best, te, self.ntest, self.NC, self.RE, self.dt_c, at)
+        # per window-step costs of the three solvers (forward sweeps over the held-out windows)
+        pc = ct.coarse_problem(self.ntest, self.NC, self.RE, self.dt_c)
+        yc = torch.empty_like(te[0])
+        pc.set_params(zero)
+        us_plain = self._per_step_us(lambda: pc.forward(self.NCO, te[0].contiguous(), yc), self.NCO * self.ntest)
+        pc.set_params(best)
+        us_cnn = self._per_step_us(lambda: pc.forward(self.NCO, te[0].contiguous(), yc), self.NCO * self.ntest)
+        pc.close()
+        x0f = torch.from_numpy(np.concatenate([synthetic.kolmogorov_ic(self.NF, 2000 + s).ravel()
+                                               for s in range(self.ntest)])).to(device)
+        pf = spadj.Problem(spadj.SPADJ_KOLMOGOROV2D, spadj.SPADJ_SBDF2, [self.NF], [2 * np.pi], [self.RE, 0.0],
+                           self.DTF, batch=self.ntest)
+        yf = torch.empty_like(x0f)
+        us_fine = self._per_step_us(lambda: pf.forward(self.RATIO * 8, x0f, yf), 8 * self.ntest)
+        pf.close()
+        mean = lambda d: {("T/4", "T/2", "T")[i]: float(d[k].mean()) for i, k in enumerate(at)}
+        self.summary = {
+            "held_out_rel_error_vs_fine": {"plain_coarse": mean(plain), "coarse_plus_cnn": mean(cnn)},
+            "us_per_window_coarse_step": {"plain_coarse_64": us_plain, "coarse_64_plus_cnn": us_cnn,
+                                          "fine_1024_16_fine_steps": us_fine},
+            "training": {"iterations": self.train_iters, "validation_history": hist, "train_windows": self.ntrain,
+                         "seconds": round(t_train, 1)},
+            "data_generation_seconds": round(t_data, 1)}
+        # the timed training iteration
+        self.params = best.clone()
+        self.p = ct.coarse_problem(self.ntrain, self.NC, self.RE, self.dt_c)
+        self.p.set_observations(list(range(1, self.NCO + 1)), self.tr[1:].contiguous(), self.NC // 2 - 1)
+        self.opt = ct.Adam(self.p, self.params.numel(), lr=3e-3, device=device)
+        self.x0 = self.tr[0].contiguous()
+        self.g = torch.empty_like(self.x0)
+        self.gp = torch.empty_like(self.params)
+        self.x0_pin = self.x0.cpu().pin_memory()
+        self.g_pin = torch.empty(self.g.shape, dtype=self.g.dtype).pin_memory()
+        self.x0_dev2 = torch.empty_like(self.x0)
+
+    def config(self):
+        return {"workload": self.name, "coarse": self.NC, "fine": self.NF, "Re": self.RE, "dt_coarse": self.dt_c,
+                "window_steps": self.NCO, "windows": self.ntrain, "cnn": "1-32-32-32-1 3x3 periodic tanh, BF16/FP32",
+                "l2": "working set ~%.0f MB (trajectory of the windows), not flushed" % (
+                    (self.NCO + 1) * self.ntrain * (self.NC // 2) * self.NC * 16 / 1e6),
+                **getattr(self, "summary", {})}
+
+    def step(self, ev=None):
+        self.p.set_params(self.params)
+        self.p.gradient(self.x0, self.NCO, self.g, objective=self.sp.SPADJ_OBJ_FOURDVAR, grad_p=self.gp, want_J=False)
+        self.opt.step(self.params, self.gp)
+
+    def forward_step(self):
+        self.p.set_params(self.params)
+        self.p.forward(self.NCO, self.x0, self.x0_dev2)
+
+    def e2e_step(self):
+        self.x0_dev2.copy_(self.x0_pin, non_blocking=True)
+        self.p.set_params(self.params)
+        self.p.gradient(self.x0_dev2, self.NCO, self.g, objective=self.sp.SPADJ_OBJ_FOURDVAR, grad_p=self.gp)
+        self.opt.step(self.params, self.gp)
+        self.g_pin.copy_(self.g, non_blocking=True)
+
+    def e2e_bytes(self):
+        n = self.x0.numel() * 16
+        return n, n + 8 * self.ntrain
+
+    def cpu_sample(self, n=1, nsteps=16):
+        """Oracle: coarse-solver gradient with the FP64 CNN closure (state and parameter gradients)
+        of n windows over the full window, numpy FP64."""
+        from oracle import cnn as ocnn
+        from oracle import imex
+        from oracle import kolmogorov as okol
+        o = okol.Kolmogorov(self.NC, self.RE, closure=ocnn.CNN(synthetic.cnn_params(7, scale_out=0.01)))
+        t = time.perf_counter()
+        for s in range(n):
+            X0 = o.project(synthetic.kolmogorov_ic(self.NC, 1000 + s))
+            target = o.project(synthetic.kolmogorov_ic(self.NC, 3000 + s))
+            X = imex.multistep_forward(o, X0, nsteps, self.dt_c)
+            imex.multistep_adjoint_params(o, X, lambda k: X[k] - target, self.dt_c)
+        el = time.perf_counter() - t
+        return n * nsteps / el, "%d windows x %d steps, coarse gradient with the FP64 CNN closure (numpy)" % (
+            n, nsteps), el
+
+
 WORKLOADS = {"burgers": Burgers, "rb": RayleighBenard, "kolmogorov": KolmogorovBatch, "couette": Couette,
-             "poiseuille_evp": PoiseuilleEvp, "couette_resolvent": CouetteResolvent}
+             "poiseuille_evp": PoiseuilleEvp, "couette_resolvent": CouetteResolvent,
+             "kolmogorov_members": KolmogorovMembers, "closure": Closure}
 DEFAULT_WORKLOAD = "rb"
 
 
@@ -1022,6 +1264,8 @@ def main():
     ap.add_argument("--op", default=None, choices=["gain", "integral", "hvp"],
                     help="couette: gain gradient (default), time-integrated energy gradient, or Hessian-vector product")
     ap.add_argument("--omega", type=float, default=None, help="couette_resolvent: forcing frequency (default 0)")
+    ap.add_argument("--batch", type=int, default=None,
+                    help="burgers: members per gradient (default 16384; 1 gives the single-member latency line)")
     ap.add_argument("--dt-blocks", type=int, default=0,
                     help="rb: step-size schedule alternating dt and dt/2 every this many steps (0: constant dt)")
     args = ap.parse_args()
@@ -1044,6 +1288,10 @@ def main():
         if args.workload != "rb":
             ap.error("--dt-blocks applies to the rb workload")
         kw["dt_blocks"] = args.dt_blocks
+    if args.batch is not None:
+        if args.workload != "burgers" or args.batch < 1:
+            ap.error("--batch (>= 1) applies to the burgers workload")
+        kw["batch"] = args.batch
     if args.omega is not None:
         if args.workload != "couette_resolvent":
             ap.error("--omega applies to the couette_resolvent workload")

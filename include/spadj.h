@@ -291,6 +291,33 @@ spadj_status spadj_set_observations(spadj_problem* prob, int n_obs, const int* o
  * FP32 accumulation; spadj_gradient's grad_p receives dJ/dp (eq. 6 with p entering F). */
 spadj_status spadj_set_params(spadj_problem* prob, const double* params);
 
+/* Training support for the learned closure (the paper names coupling the adjoints to learned
+ * models as future work, Conclusions; these two calls are not part of its method).
+ * spadj_restrict: spectral truncation R of B fine members to the resolution of prob, a
+ * SPADJ_KOLMOGOROV2D problem of uniform resolution Nc = n[0] and batch B: coarse (kx, ky) = fine
+ * (kx, ky) for kx < Nc/2 and |ky| < Nc/2, the coarse ky = -Nc/2 row zero.  fine (device): B members
+ * of n_fine >= Nc modes each ([B][n_fine/2][n_fine] complex, the layout of SPADJ_KOLMOGOROV2D);
+ * coarse (device): spadj_state_len(prob, 0) doubles.  SPADJ_ERR_INVALID for an odd or too small
+ * n_fine, SPADJ_ERR_UNSUPPORTED for a mixed-resolution batch.
+ * spadj_adam: one Adam step (Kingma & Ba, 2015) on the closure parameters: with g = grad_p,
+ * m <- b1 m + (1 - b1) g, v <- b2 v + (1 - b2) g^2, params <- params - lr mhat / (sqrt(vhat) + eps),
+ * mhat = m / (1 - b1^t), vhat = v / (1 - b2^t); t >= 1 is the step count.  grad_p, m, v, params:
+ * device arrays of spadj_state_len(prob, 2) doubles, m and v owned by the caller (zero before the
+ * first step).  The parameters of the problem are not changed: call spadj_set_params. */
+spadj_status spadj_restrict(spadj_problem* prob, int n_fine, const double* fine, double* coarse);
+
+/* Test support for the learned closure's tensor-core kernels (not part of the method): one 32 -> 32
+ * convolution of hidden layer `layer` (1 or 2) with the problem's current BF16 weights (spadj_set_params)
+ * over all batch members of its M x M grid (M = 3 n[0] / 2): mode 0 the pre-activation
+ * out = conv(in) + b (forward), mode 1 the input gradient out = conv^T(in) (no bias).  in: device, BF16
+ * bit patterns, [member][y][x][32 channels]; out: device float32, same layout.  Runs the kernel the
+ * closure passes use (tcgen05 MMAs with the accumulator in tensor memory, unless spadj_set_option 11
+ * selected the mma.sync kernel, which has no mode 0 here).  Synchronises the stream;
+ * SPADJ_ERR_TIMEOUT if a bounded wait for the MMAs ran out. */
+spadj_status spadj_closure_conv(spadj_problem* prob, int layer, int mode, const void* in, float* out);
+spadj_status spadj_adam(spadj_problem* prob, const double* grad_p, int t, double lr, double b1, double b2,
+                        double eps, double* m, double* v, double* params);
+
 /* Tuning knobs of the batched persistent launch (SPADJ_KOLMOGOROV2D): option 0 = persistent
  * scheduler (1, default) or one launch per phase (0); 1 = x-modes per column tile; 2 = grid
  * rows per row tile; 3 = resident CTAs per SM (0 = occupancy maximum); 4 = iteration limit of
@@ -306,8 +333,12 @@ spadj_status spadj_set_params(spadj_problem* prob, const double* params);
  * or 192 threads is picked by timing when the problem is created); option 9
  * (SPADJ_RB2D, SPADJ_COUETTE3D) = host checkpoint slots of spadj_gradient / spadj_vjp (0, default:
  * device slots only; h > 0: the two-level schedule of spadj_checkpoint_schedule_host, the host
- * copies in page-locked memory owned by the problem).  Set them before the first sweep (the step
- * graphs are captured once).
+ * copies in page-locked memory owned by the problem); option 10 (SPADJ_RB2D) = how the fused column
+ * stages bring their operator block into shared memory (1, default: one bulk copy, cp.async.bulk,
+ * completing on an mbarrier; 0: 16-byte cp.async copies spread over the threads); option 11
+ * (SPADJ_KOLMOGOROV2D with the closure) = the 32 -> 32 convolutions on the fifth-generation tensor
+ * cores (1, default: tcgen05.mma, accumulator in tensor memory) or on warp-level mma.sync (0).  Set
+ * them before the first sweep (the step graphs are captured once).
  * spadj_autotune times candidate settings on the problem's own sizes and keeps the fastest. */
 spadj_status spadj_set_option(spadj_problem* prob, int option, int value);
 spadj_status spadj_autotune(spadj_problem* prob);
@@ -332,7 +363,8 @@ spadj_status spadj_gradient(spadj_problem* prob, const double* x0, int n_steps, 
  * flop count and the number of launches since timing was (re)enabled.  Classes:
  * 0 z (Chebyshev) transforms, 1 x (Fourier) FFTs, 2 grid-point products, 3 pencil solves,
  * 4 objective, 5 fused persistent trajectory kernels, 6 y (Fourier) FFTs, 7 energy-norm (Gram)
- * products of the resolvent iteration.  spadj_timing
+ * products of the resolvent iteration, 8 the learned closure's network passes (BF16 operands,
+ * FP32 accumulation).  spadj_timing
  * synchronises the stream and resets the counters. */
 spadj_status spadj_timing(spadj_problem* prob, int enable);
 spadj_status spadj_timing_report(spadj_problem* prob, int kernel_class, double* ms, double* flops, long* launches);
@@ -374,13 +406,17 @@ spadj_status spadj_hvp(spadj_problem* prob, const double* x0, const double* v, i
  * for a frequency and kept until another frequency is asked for. */
 spadj_status spadj_resolvent(spadj_problem* prob, double omega, int n_iter, double* f, double* gains);
 
-/* Step-size schedule (SPADJ_RB2D): step n of every later forward, tangent, adjoint, gradient and
- * vjp sweep uses dts[n] (host array of n > 0 sizes, copied; n = 0 restores the descriptor's
- * constant dt).  The stage operators M + dt gamma L are factorised once per distinct size, when a
- * sweep first needs it, and kept for later sweeps: the paper's timesteppers reuse their LU
- * factorisations unless the timestep changes, and rebuild them when it does.  The adjoint of
- * step n uses the same size as its forward step.  A sweep longer than the schedule fails with
- * SPADJ_ERR_INVALID; sizes must be positive.  spadj_solve keeps the descriptor's dt. */
+/* Step-size schedule (SPADJ_RB2D, SPADJ_BURGERS1D): step n of every later forward, tangent, adjoint,
+ * gradient, vjp and step call uses dts[n] (host array of n > 0 sizes, copied; n = 0 restores the
+ * descriptor's constant dt).  SPADJ_RB2D: the stage operators M + dt gamma L are factorised once per
+ * distinct size, when a sweep first needs it, and kept for later sweeps: the paper's timesteppers
+ * reuse their LU factorisations unless the timestep changes, and rebuild them when it does.
+ * SPADJ_BURGERS1D (SBDF1 or SBDF2; SPADJ_ERR_UNSUPPORTED for SBDF3/4): variable-step SBDF2, the
+ * weights of step n from its own size h_n and the ratio w = h_n / h_{n-1} (Wang-Ruuth form:
+ * a0 = (1 + 2w)/((1 + w) h_n), a1 = -(1 + w)/h_n, a2 = w^2/((1 + w) h_n), c1 = 1 + w, c2 = -w; the first
+ * step SBDF1 of size h_1), the diagonal solve 1/(a0 + nu k^2) refreshed when a0 changes.  The
+ * adjoint of step n uses the same weights as its forward step.  A sweep longer than the schedule
+ * fails with SPADJ_ERR_INVALID; sizes must be positive.  spadj_solve keeps the descriptor's dt. */
 spadj_status spadj_set_dt_schedule(spadj_problem* prob, int n, const double* dts);
 
 /* Leading eigenvalue and its parameter sensitivities for a batch of pencils (SPADJ_SHEAR_EVP).

@@ -1,11 +1,12 @@
 """Training of the learned closure through the coarse adjoint (argument marshalling and the
-optimiser only; every solve, transform, CNN pass and gradient runs in libspadj.so).
+training loop only; every solve, transform, CNN pass, gradient, restriction and optimiser
+update runs in libspadj.so).
 
 Fine trajectories come from the library's own Kolmogorov solver at the fine resolution;
 the training loss over an unrolled window of coarse steps is the 4D-Var misfit
 sum_m 1/2 ||R(w_fine(t_m)) - w_coarse(t_m; p)||^2, R the spectral truncation to the coarse
 grid, and its gradient with respect to the CNN parameters p comes from spadj_gradient's
-adjoint sweep (eq. 6 with p entering F).  Adam updates p.
+adjoint sweep (eq. 6 with p entering F).  Adam (spadj_adam) updates p.
 """
 import numpy as np
 import torch
@@ -13,24 +14,16 @@ import torch
 from . import spadj
 
 
-def restrict_index(Nf, Nc):
-    """Flat indices into a fine member [Nf/2][Nf] of the coarse coefficients [Nc/2][Nc]
-    (kx < Nc/2, |ky| < Nc/2); the coarse Nyquist row maps to -1 (held at zero)."""
-    Kc = Nc // 2
-    ky = np.fft.fftfreq(Nc, 1.0 / Nc).astype(int)
-    jf = np.where(ky >= 0, ky, Nf + ky)
-    idx = (np.arange(Kc)[:, None] * Nf + jf[None, :]).astype(np.int64)
-    idx[:, Nc // 2] = -1
-    return idx.ravel()
-
-
 def restrict(fine, nmem, Nf, Nc):
-    """fine [..., nmem * Nf/2 * Nf] (complex, device) -> [..., nmem * Nc/2 * Nc]."""
-    idx = torch.from_numpy(restrict_index(Nf, Nc)).to(fine.device)
+    """fine [..., nmem * Nf/2 * Nf] (complex, device) -> [..., nmem * Nc/2 * Nc]: the spectral
+    truncation R of every member (spadj_restrict)."""
     lead = fine.shape[:-1]
-    f = fine.reshape(lead + (nmem, (Nf // 2) * Nf))
-    safe = torch.clamp(idx, min=0)
-    out = f[..., safe] * (idx >= 0).to(fine.dtype)
+    f = fine.reshape(-1, nmem * (Nf // 2) * Nf)
+    out = torch.empty((f.shape[0], nmem * (Nc // 2) * Nc), dtype=fine.dtype, device=fine.device)
+    p = spadj.Problem(spadj.SPADJ_KOLMOGOROV2D, spadj.SPADJ_SBDF2, [Nc], [2 * np.pi], [1.0, 0.0], 1.0, batch=nmem)
+    for i in range(f.shape[0]):
+        p.restrict(Nf, f[i], out[i])
+    p.close()
     return out.reshape(lead + (nmem * (Nc // 2) * Nc,))
 
 
@@ -96,19 +89,18 @@ def fine_snapshots(x0_fine, nmem, Nf, Re, dt_f, ratio, ncoarse):
 
 
 class Adam:
-    def __init__(self, n, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8, device="cuda"):
+    """Adam moments of the closure parameters; the update itself runs in the library (spadj_adam)."""
+
+    def __init__(self, problem, n, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8, device="cuda"):
+        self.p = problem
         self.m = torch.zeros(n, dtype=torch.float64, device=device)
         self.v = torch.zeros_like(self.m)
         self.t = 0
         self.lr, self.b1, self.b2, self.eps = lr, b1, b2, eps
 
-    def step(self, p, g):
+    def step(self, params, g):
         self.t += 1
-        self.m.mul_(self.b1).add_(g, alpha=1 - self.b1)
-        self.v.mul_(self.b2).addcmul_(g, g, value=1 - self.b2)
-        mh = self.m / (1 - self.b1 ** self.t)
-        vh = self.v / (1 - self.b2 ** self.t)
-        p.sub_(self.lr * mh / (vh.sqrt() + self.eps))
+        self.p.adam(g, self.t, self.m, self.v, params, lr=self.lr, b1=self.b1, b2=self.b2, eps=self.eps)
 
 
 def coarse_problem(nmem, Nc, Re, dt_c):
@@ -123,7 +115,7 @@ def train(params, coarse_snaps, nmem, Nc, Re, dt_c, iters, lr=1e-3, log=None):
     p = coarse_problem(nmem, Nc, Re, dt_c)
     steps = list(range(1, nco + 1))
     p.set_observations(steps, coarse_snaps[1:].contiguous(), Nc // 2 - 1)
-    opt = Adam(params.numel(), lr=lr, device=params.device)
+    opt = Adam(p, params.numel(), lr=lr, device=params.device)
     g = torch.empty_like(coarse_snaps[0])
     gp = torch.empty_like(params)
     losses = []

@@ -120,6 +120,7 @@ spadj_status spadj_resolvent(spadj_problem* p, double omega, int n_iter, double*
 spadj_status spadj_set_dt_schedule(spadj_problem* p, int n, const double* dts) {
   if (!p) return SPADJ_ERR_INVALID;
   if (n < 0 || (n > 0 && bad_ptr(dts))) return p->fail(SPADJ_ERR_INVALID, "set_dt_schedule: need n >= 0 and dts");
+  if (p->desc.eq == SPADJ_BURGERS1D) return spadj::burgers_set_dt_schedule(p->impl, p, n, dts);
   return spadj::rb_set_dt_schedule(p->impl, p, n, dts);
 }
 
@@ -167,6 +168,10 @@ spadj_status spadj_set_option(spadj_problem* p, int option, int value) {
     p->x_rows = value;
     return SPADJ_OK;
   }
+  if (option == 10) {
+    p->bulk_staging = value != 0;
+    return SPADJ_OK;
+  }
   if (option == 9) {
     if (value < 0) return p->fail(SPADJ_ERR_INVALID, "set_option 9: host checkpoint slots must be >= 0");
     p->host_slots = value;
@@ -179,6 +184,25 @@ spadj_status spadj_set_params(spadj_problem* p, const double* params) {
   if (!p) return SPADJ_ERR_INVALID;
   if (bad_ptr(params)) return p->fail(SPADJ_ERR_INVALID, "set_params: NULL array");
   return spadj::kol_set_params(p->impl, p, params);
+}
+
+spadj_status spadj_restrict(spadj_problem* p, int n_fine, const double* fine, double* coarse) {
+  if (!p) return SPADJ_ERR_INVALID;
+  if (bad_ptr(fine) || bad_ptr(coarse)) return p->fail(SPADJ_ERR_INVALID, "restrict: NULL array");
+  return spadj::kol_restrict(p->impl, p, n_fine, fine, coarse);
+}
+
+spadj_status spadj_adam(spadj_problem* p, const double* grad_p, int t, double lr, double b1, double b2, double eps,
+                        double* m, double* v, double* params) {
+  if (!p) return SPADJ_ERR_INVALID;
+  if (bad_ptr(grad_p) || bad_ptr(m) || bad_ptr(v) || bad_ptr(params)) return p->fail(SPADJ_ERR_INVALID, "adam: NULL array");
+  return spadj::kol_adam(p->impl, p, grad_p, t, lr, b1, b2, eps, m, v, params);
+}
+
+spadj_status spadj_closure_conv(spadj_problem* p, int layer, int mode, const void* in, float* out) {
+  if (!p) return SPADJ_ERR_INVALID;
+  if (bad_ptr(in) || bad_ptr(out)) return p->fail(SPADJ_ERR_INVALID, "closure_conv: NULL array");
+  return spadj::kol_closure_conv(p->impl, p, layer, mode, in, out);
 }
 
 spadj_status spadj_autotune(spadj_problem* p) {

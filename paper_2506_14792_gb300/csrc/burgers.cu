@@ -33,6 +33,10 @@ struct BurgersParams {
   // SBDF<s> weights, s = 1..kMaxOrder (row s-1): backward differentiation weights already divided
   // by dt (no division in the step loops) and extrapolation weights of F
   double wa[kMaxOrder][kMaxOrder + 1], wc[kMaxOrder][kMaxOrder + 1];
+  // step-size schedule (nullable): weights of step n (1-based) at ws[5 (n - 1)] = a0, a1, a2, c1, c2
+  // (variable-step SBDF1 / SBDF2), ws_len steps
+  const double* ws;
+  int ws_len;
 };
 
 struct Smem {
@@ -240,6 +244,15 @@ constexpr double kSbdfC[kMaxOrder][kMaxOrder + 1] = {{0.0, 1.0, 0.0, 0.0, 0.0},
 __device__ __forceinline__ int step_order(const BurgersParams& P, int n) { return n < P.order ? n : P.order; }
 __device__ __forceinline__ Coef step_coef(const BurgersParams& P, int n) {
   Coef c;
+  if (P.ws) {  // variable steps: the schedule's weights (zero past its end)
+#pragma unroll
+    for (int i = 0; i <= kMaxOrder; ++i) c.a[i] = c.c[i] = 0.0;
+    if (n >= 1 && n <= P.ws_len) {
+      const double* w = P.ws + (size_t)(n - 1) * 5;
+      c.a[0] = w[0]; c.a[1] = w[1]; c.a[2] = w[2]; c.c[1] = w[3]; c.c[2] = w[4];
+    }
+    return c;
+  }
   const int s = step_order(P, n);
 #pragma unroll
   for (int i = 0; i <= kMaxOrder; ++i) {
@@ -327,21 +340,21 @@ __global__ void __launch_bounds__(64) trajectory_kernel(BurgersParams P, int n_f
       if (k < K) { F[q][0] = s.O[k]; if (tangent) GJ[q][0] = O2[k]; }
     }
   }
-  // nu k^2 per mode and 1 / (a_0 + nu k^2), recomputed only when the step order changes
+  // nu k^2 per mode and 1 / (a_0 + nu k^2), recomputed only when a_0 changes (the step order, or
+  // the step size of a schedule)
   double nk2[Q], inv_m[Q];
   for (int q = 0; q < Q; ++q) {
     const double kk = kwav(P, tid + q * G);
     nk2[q] = P.nu * kk * kk;
     inv_m[q] = 0.0;
   }
-  int s_prev = 0;
+  double a0_prev = 0.0;
   for (int j = 1; j <= n_steps; ++j) {
     const int n = n_first + j;
     Coef c = step_coef(P, n);
-    const int s_n = step_order(P, n);
-    if (s_n != s_prev) {
+    if (c.a[0] != a0_prev) {
       for (int q = 0; q < Q; ++q) inv_m[q] = 1.0 / (c.a[0] + nk2[q]);
-      s_prev = s_n;
+      a0_prev = c.a[0];
     }
     for (int q = 0; q < Q; ++q) {
       int k = tid + q * G;
@@ -410,15 +423,14 @@ __global__ void __launch_bounds__(64) adjoint_kernel(BurgersParams P, int n_step
   const int so = P.order;
   double2 Y[Q][ORD];  // Y_{n+1}, ..., Y_{n+ORD}
   const double2 z = make_double2(0.0, 0.0);
-  // nu k^2 per mode and 1 / (a_0 + nu k^2) of the current step order (steps run backward, so the
-  // order changes only over the first steps)
+  // nu k^2 per mode and 1 / (a_0 + nu k^2) of the current step, recomputed when a_0 changes
   double nk2[Q], inv_m[Q];
   for (int q = 0; q < Q; ++q) {
     const double kk = kwav(P, tid + q * G);
     nk2[q] = P.nu * kk * kk;
     inv_m[q] = 0.0;
   }
-  int s_prev = 0;
+  double a0_prev = 0.0;
   for (int q = 0; q < Q; ++q) {
     const int k = tid + q * G;
 #pragma unroll
@@ -487,11 +499,12 @@ __global__ void __launch_bounds__(64) adjoint_kernel(BurgersParams P, int n_step
       }
       return;
     }
-    const int s_n = step_order(P, n);
-    if (s_n != s_prev) {
+    {
       const Coef c = step_coef(P, n);
-      for (int q = 0; q < Q; ++q) inv_m[q] = 1.0 / (c.a[0] + nk2[q]);
-      s_prev = s_n;
+      if (c.a[0] != a0_prev) {
+        for (int q = 0; q < Q; ++q) inv_m[q] = 1.0 / (c.a[0] + nk2[q]);
+        a0_prev = c.a[0];
+      }
     }
     for (int q = 0; q < Q; ++q) {
       int k = tid + q * G;
@@ -600,6 +613,45 @@ struct Burgers : EqImpl {
     return SPADJ_OK;
   }
 
+  // ---- step-size schedule (variable-step SBDF1 / SBDF2) ---------------------------------------
+  DevBuf wsched;
+  spadj_status set_schedule(Problem* p, int n, const double* dts) {
+    if (n == 0) {
+      P.ws = nullptr;
+      P.ws_len = 0;
+      return SPADJ_OK;
+    }
+    if (P.order > 2) return p->fail(SPADJ_ERR_UNSUPPORTED, "burgers: step-size schedules need SBDF1 or SBDF2");
+    for (int i = 0; i < n; ++i)
+      if (!(dts[i] > 0.0) || !std::isfinite(dts[i])) return p->fail(SPADJ_ERR_INVALID, "set_dt_schedule: step sizes must be > 0");
+    // step n (1-based) spans h = dts[n-1]; from the second step on, SBDF2 with w = h / dts[n-2]
+    std::vector<double> w((size_t)n * 5, 0.0);
+    for (int k = 1; k <= n; ++k) {
+      const double h = dts[k - 1];
+      double* r = &w[(size_t)(k - 1) * 5];
+      if (k == 1 || P.order == 1) {
+        r[0] = 1.0 / h; r[1] = -1.0 / h; r[3] = 1.0;
+      } else {
+        const double om = h / dts[k - 2];
+        r[0] = (1.0 + 2.0 * om) / ((1.0 + om) * h);
+        r[1] = -(1.0 + om) / h;
+        r[2] = om * om / ((1.0 + om) * h);
+        r[3] = 1.0 + om;
+        r[4] = -om;
+      }
+    }
+    SPADJ_CUDA_TRY(p, cudaStreamSynchronize(p->stream));  // no kernel may still read the old table
+    SPADJ_CUDA_TRY(p, wsched.ensure(sizeof(double) * w.size()));
+    SPADJ_CUDA_TRY(p, cudaMemcpy(wsched.ptr, w.data(), sizeof(double) * w.size(), cudaMemcpyHostToDevice));
+    P.ws = wsched.as<double>();
+    P.ws_len = n;
+    return SPADJ_OK;
+  }
+  spadj_status check_horizon(Problem* p, int n_steps) {
+    if (P.ws && n_steps > P.ws_len) return p->fail(SPADJ_ERR_INVALID, "burgers: the step-size schedule is shorter than the sweep");
+    return SPADJ_OK;
+  }
+
   spadj_status transform(Problem* p, int kind, const double* in, double* out) override {
     if (kind < 0 || kind > 3) return p->fail(SPADJ_ERR_INVALID, "transform: kind must be 0..3");
     transform_kernel<<<B, G, smem, p->stream>>>(P, kind, in, out);
@@ -654,11 +706,13 @@ struct Burgers : EqImpl {
 
   spadj_status forward(Problem* p, int n_steps, const double* x0, double* x_out, double* trj) override {
     if (n_steps < 0) return p->fail(SPADJ_ERR_INVALID, "forward: n_steps < 0");
+    if (spadj_status h = check_horizon(p, n_steps)) return h;
     return launch_traj(p, 0, n_steps, x0, 1, nullptr, x_out, nullptr, trj, 0);
   }
 
   spadj_status tangent(Problem* p, int n_steps, const double* x0, const double* dx0, double* dx_out) override {
     if (n_steps < 0) return p->fail(SPADJ_ERR_INVALID, "tangent: n_steps < 0");
+    if (spadj_status h = check_horizon(p, n_steps)) return h;
     return launch_traj(p, 0, n_steps, x0, 1, dx0, dx_out, nullptr, nullptr, 1);
   }
 
@@ -669,11 +723,13 @@ struct Burgers : EqImpl {
 
   spadj_status step_forward(Problem* p, int n, const double* s_n, double* s_np1) override {
     if (n < 0) return p->fail(SPADJ_ERR_INVALID, "step: n < 0");
+    if (spadj_status h = check_horizon(p, n + 1)) return h;
     return launch_traj(p, n, 1, s_n, 2 * P.order - 1, nullptr, nullptr, s_np1, nullptr, 0);
   }
 
   spadj_status step_tangent(Problem* p, int n, const double* s_n, const double* ds_n, double* ds_np1) override {
     if (n < 0) return p->fail(SPADJ_ERR_INVALID, "step: n < 0");
+    if (spadj_status h = check_horizon(p, n + 1)) return h;
     return launch_traj(p, n, 1, s_n, 2 * P.order - 1, ds_n, nullptr, ds_np1, nullptr, 1);
   }
 
@@ -681,6 +737,7 @@ struct Burgers : EqImpl {
                             double* gp_accum) override {
     if (gp_accum) return p->fail(SPADJ_ERR_INVALID, "burgers: the problem has no parameters (gp_accum must be NULL)");
     if (n < 0) return p->fail(SPADJ_ERR_INVALID, "step: n < 0");
+    if (spadj_status h = check_horizon(p, n)) return h;
     // y_np1 = NULL: the seed step (no later adjoint variables); otherwise every later step exists and
     // the adjoint variables past the horizon are the caller's zeros
     const int horizon = y_np1 ? (1 << 29) : n;
@@ -700,6 +757,7 @@ struct Burgers : EqImpl {
   spadj_status reverse(Problem* p, const double* x0, int n_steps, int ckpt_slots, const double* y_final_dev,
                        const std::vector<int>* seed_at, const double* seeds, double* grad, double* J_dev,
                        double* seed_buf) {
+    if (spadj_status h = check_horizon(p, n_steps)) return h;
     const size_t sl = state_len(0);
     const int* sm_dev = nullptr;
     if (seed_at) {
@@ -804,6 +862,7 @@ struct Burgers : EqImpl {
                        double* grad_p) override {
     if (n_steps < 1) return p->fail(SPADJ_ERR_INVALID, "adjoint: n_steps < 1");
     if (grad_p) return p->fail(SPADJ_ERR_INVALID, "burgers: the problem has no parameters (grad_p must be NULL)");
+    if (spadj_status h = check_horizon(p, n_steps)) return h;
     return launch_adj(p, n_steps, n_steps, 0, trj, y_final, nullptr, grad, 1, nullptr, nullptr, nullptr);
   }
 
@@ -838,6 +897,7 @@ struct Burgers : EqImpl {
 
   ~Burgers() override {
     wm.release();
+    wsched.release();
     seedmap.release();
     rs.release();
     ys.release();
@@ -850,6 +910,12 @@ struct Burgers : EqImpl {
 };
 
 }  // namespace
+
+spadj_status burgers_set_dt_schedule(EqImpl* impl, Problem* p, int n, const double* dts) {
+  Burgers* b = dynamic_cast<Burgers*>(impl);
+  if (!b) return p->fail(SPADJ_ERR_UNSUPPORTED, "set_dt_schedule: not a Burgers problem");
+  return b->set_schedule(p, n, dts);
+}
 
 EqImpl* make_burgers(Problem* p, spadj_status* st) {
   Burgers* b = new Burgers();

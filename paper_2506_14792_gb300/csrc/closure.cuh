@@ -12,6 +12,8 @@
 #pragma once
 #include <cuda_bf16.h>
 
+#include "pdl.cuh"
+
 namespace spadj {
 namespace cnn {
 
@@ -376,6 +378,174 @@ __global__ void bgrad32_kernel(int l, int M, const __nv_bfloat16* __restrict__ d
     for (int k = 0; k < (int)blockDim.x; ++k) s += red[k];
     part[(long long)mb * npar + w_off(l) + 32 * 32 * 9 + o] = s;
   }
+}
+
+}  // namespace cnn
+}  // namespace spadj
+
+namespace spadj {
+namespace cnn {
+
+// ---- fifth-generation tensor cores (tcgen05) for the 32 -> 32 layers ----------------------------
+//
+// Implicit GEMM D[p][n] = sum_k A[p][k] B[n][k] with rows p = 128 consecutive pixels (one tile),
+// columns n = 32 output channels and reduction k = tap * 32 + channel (9 taps x 32 channels = 288),
+// BF16 operands and an FP32 accumulator in tensor memory:
+//  * A (the gathered, shifted activations: forward in[shift(p, a - 1, b - 1)][c], input gradient
+//    dz[shift(p, 1 - a, 1 - b)][o]) and B (the weights, W[o][a][b][c] or its transpose) are staged in
+//    shared memory in the canonical K-major layout without swizzle: 8 x 16-byte core matrices, the
+//    core matrix of rows 8 r .. 8 r + 7 and k = 8 g .. 8 g + 7 at byte (r * 36 + g) * 128, row i of it
+//    at + 16 i (leading-byte offset 128 between the two k core matrices of an MMA, stride-byte offset
+//    36 * 128 between 8-row groups);
+//  * one thread issues the 18 MMAs (M = 128, N = 32, K = 16) of a tile and commits them to an
+//    mbarrier; every thread waits on it (bounded), reads its pixel's 32 accumulators from its lane of
+//    tensor memory (tcgen05.ld 32x32b) and applies the epilogue.
+// The CTA keeps its 32 tensor-memory columns (allocated by warp 0) for all tiles and frees them at
+// exit.  A wait that runs out sets *err, waits once more (bounded) and ends the CTA's work.
+constexpr int kTcRows = 128;        // pixels per tile (MMA M)
+constexpr int kTcK = 288;           // reduction length
+constexpr int kTcKg = kTcK / 8;     // k core-matrix groups
+constexpr unsigned kTcSpin = 1u << 22;
+constexpr size_t kTcSmem = (size_t)(kTcRows + 32) * kTcK * 2;  // A tile + B
+
+__device__ __forceinline__ unsigned long long tc_smem_desc(unsigned addr, unsigned lbo, unsigned sbo) {
+  // start address, leading- and stride-byte offsets in 16-byte units; version 1 (tcgen05); no swizzle
+  return (unsigned long long)((addr & 0x3FFFFu) >> 4) | ((unsigned long long)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((unsigned long long)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// instruction descriptor of kind::f16: D F32, A and B BF16, both K-major, N = 32, M = 128
+constexpr unsigned kTcIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
+
+__device__ __forceinline__ unsigned tc_core_off(int row, int k) {  // byte offset of element (row, k)
+  return (unsigned)(((row >> 3) * kTcKg + (k >> 3)) * 128 + (row & 7) * 16 + (k & 7) * 2);
+}
+
+__device__ __forceinline__ bool tc_wait(unsigned long long* bar, unsigned parity, int* err) {
+  for (unsigned it = 0; it < kTcSpin; ++it) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    __nanosleep(32);
+  }
+  if (err) atomicExch(err, 1);
+  return false;
+}
+
+// mode 0: forward hidden layer, out = tanh(D + b) as BF16 h and 1 - tanh^2 as FP32 dact (nullable);
+// mode 1: input gradient, din = D (FP32); mode 2: pre-activation zout = D + b (FP32, for tests).
+__global__ void __launch_bounds__(128) conv32_tc_kernel(int l, int M, int nb, int mode,
+                                                        const __nv_bfloat16* __restrict__ in,
+                                                        const __nv_bfloat16* __restrict__ wq,
+                                                        const float* __restrict__ bq, __nv_bfloat16* __restrict__ h,
+                                                        float* __restrict__ dact, float* __restrict__ fout,
+                                                        int* __restrict__ err) {
+  extern __shared__ __align__(128) unsigned char tcs[];
+  __shared__ unsigned long long bar;
+  __shared__ unsigned tmem_holder;
+  unsigned char* sA = tcs;                              // 128 x 288 BF16, canonical K-major
+  unsigned char* sB = tcs + (size_t)kTcRows * kTcK * 2; // 32 x 288 BF16, canonical K-major
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const long long P = (long long)M * M, npix = P * nb;
+  const long long tiles = (npix + kTcRows - 1) / kTcRows;
+  const __nv_bfloat16* W = wq + w_off(l);
+  // B[n][k = tap * 32 + kc]: forward W[o = n][tap][c = kc]; gradient W[o = kc][tap][c = n]
+  for (int i = tid; i < 32 * kTcK; i += blockDim.x) {
+    const int n = i / kTcK, k = i - n * kTcK, tap = k >> 5, kc = k & 31;
+    const __nv_bfloat16 v = mode == 1 ? W[(kc * 9 + tap) * 32 + n] : W[(n * 9 + tap) * 32 + kc];
+    *reinterpret_cast<__nv_bfloat16*>(sB + tc_core_off(n, k)) = v;
+  }
+  if (tid == 0) mbar_init(&bar, 1);
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(smem_addr(&tmem_holder))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const unsigned tmem = tmem_holder;
+  const float* Bias = bq + w_off(l) + 32 * 32 * 9;
+  const unsigned aaddr = smem_addr(sA), baddr = smem_addr(sB);
+  unsigned parity = 0;
+  bool alive = true;
+  for (long long tile = blockIdx.x; tile < tiles && alive; tile += gridDim.x) {
+    // gather A: thread t owns row t (pixel p), 36 chunks of 8 channels (16 bytes) each
+    const long long p = tile * kTcRows + tid;
+    const bool ok = p < npix;
+    const long long pc = ok ? p : 0;
+    const long long mb = pc / P;
+    const int pp = (int)(pc - mb * P), y = pp / M, x = pp - (pp / M) * M;
+    for (int tap = 0; tap < 9; ++tap) {
+      const int a = tap / 3, b = tap % 3;
+      const int dx = mode == 1 ? 1 - a : a - 1, dy = mode == 1 ? 1 - b : b - 1;
+      const int xx = (x + dx + M) % M, yy = (y + dy + M) % M;
+      const uint4* src = reinterpret_cast<const uint4*>(in + (mb * P + (long long)yy * M + xx) * 32);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const uint4 v = ok ? __ldg(src + j) : make_uint4(0u, 0u, 0u, 0u);
+        *reinterpret_cast<uint4*>(sA + tc_core_off(tid, tap * 32 + 8 * j)) = v;
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic-proxy writes -> tensor core
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll 1
+      for (int kk = 0; kk < kTcK / 16; ++kk) {
+        const unsigned long long ad = tc_smem_desc(aaddr + kk * 256, 128, kTcKg * 128);
+        const unsigned long long bd = tc_smem_desc(baddr + kk * 256, 128, kTcKg * 128);
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+            "l"(ad), "l"(bd), "r"(kTcIdesc), "r"(kk > 0 ? 1 : 0)
+            : "memory");
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(&bar))
+                   : "memory");
+    }
+    if (!tc_wait(&bar, parity, err)) {
+      tc_wait(&bar, parity, nullptr);  // the tile's MMAs may still be running: wait once more
+      alive = false;
+    }
+    parity ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    unsigned r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+          "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(tmem + ((unsigned)(warp * 32) << 16))
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    if (ok && alive) {
+      if (mode == 0) {
+        for (int n = 0; n < 32; n += 2) {
+          const float t0 = tanhf(__uint_as_float(r[n]) + Bias[n]), t1 = tanhf(__uint_as_float(r[n + 1]) + Bias[n + 1]);
+          *reinterpret_cast<unsigned*>(h + p * 32 + n) = pack2(__float2bfloat16_rn(t0), __float2bfloat16_rn(t1));
+          if (dact) {
+            dact[p * 32 + n] = 1.0f - t0 * t0;
+            dact[p * 32 + n + 1] = 1.0f - t1 * t1;
+          }
+        }
+      } else {
+        for (int n = 0; n < 32; ++n) fout[p * 32 + n] = __uint_as_float(r[n]) + (mode == 2 ? Bias[n] : 0.0f);
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();  // A may be overwritten and the accumulator reused once every thread has read it
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem) : "memory");
 }
 
 }  // namespace cnn

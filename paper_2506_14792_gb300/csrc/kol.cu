@@ -682,6 +682,41 @@ __global__ void sum_rows_kernel(const double* partial, int n_obs, int nmem, doub
   J[b] = s;
 }
 
+// ---- training support for the learned closure -------------------------------------------------
+// Spectral truncation of B fine members (Nf modes, layout [kx][ky] of SPADJ_KOLMOGOROV2D) to Nc
+// modes: coarse (kx, ky) = fine (kx, ky) for kx < Nc/2 and |ky| < Nc/2; the coarse ky = -Nc/2 row
+// is zero (the layout holds it at zero).
+__global__ void restrict_kernel(const double2* __restrict__ fine, int Nf, int Nc, int B, double2* __restrict__ coarse) {
+  const int Kc = Nc / 2, Kf = Nf / 2;
+  const long long per_c = (long long)Kc * Nc, n = per_c * B;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int b = (int)(i / per_c);
+    const int r = (int)(i - (long long)b * per_c);
+    const int kx = r / Nc, j = r - kx * Nc;
+    double2 v = make_double2(0.0, 0.0);
+    if (j != Nc / 2) {
+      const int ky = j < Nc / 2 ? j : j - Nc;
+      const int jf = ky >= 0 ? ky : Nf + ky;
+      v = fine[(long long)b * Kf * Nf + (long long)kx * Nf + jf];
+    }
+    coarse[i] = v;
+  }
+}
+
+// One Adam step (Kingma & Ba 2015) on n parameters: m <- b1 m + (1 - b1) g, v <- b2 v + (1 - b2) g^2,
+// p <- p - lr mhat / (sqrt(vhat) + eps) with the bias corrections c1 = 1 - b1^t, c2 = 1 - b2^t.
+__global__ void adam_kernel(int n, const double* __restrict__ g, double b1, double b2, double lr, double eps, double c1,
+                            double c2, double* __restrict__ m, double* __restrict__ v, double* __restrict__ p) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const double gi = g[i];
+    const double mi = b1 * m[i] + (1.0 - b1) * gi;
+    const double vi = b2 * v[i] + (1.0 - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi / c1) / (sqrt(vi / c2) + eps);
+  }
+}
+
 // ---- host ------------------------------------------------------------------------------------
 
 bool fft_len_ok(int n) {
@@ -842,6 +877,15 @@ struct Kol : EqImpl {
       SPADJ_CUDA_TRY(p, part.ensure(sizeof(float) * np * nmem));
       SPADJ_CUDA_TRY(p, gp.ensure(sizeof(double) * np));
       SPADJ_CUDA_TRY(p, chunkbuf.ensure(sizeof(float) * (size_t)nmem * 9 * kWgradChunks * 1024));
+      SPADJ_CUDA_TRY(p, cnnerr.ensure(sizeof(int)));
+      SPADJ_CUDA_TRY(p, cudaMemsetAsync(cnnerr.ptr, 0, sizeof(int), p->stream));
+      {
+        int dev = 0;
+        SPADJ_CUDA_TRY(p, cudaGetDevice(&dev));
+        SPADJ_CUDA_TRY(p, cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, dev));
+      }
+      SPADJ_CUDA_TRY(p, cudaFuncSetAttribute(cnn::conv32_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)cnn::kTcSmem));
       SPADJ_CUDA_TRY(p, cudaMemsetAsync(pbuf.ptr, 0, sizeof(double) * np, p->stream));
       cnn::convert_kernel<<<64, 256, 0, p->stream>>>(pbuf.as<double>(), wq.as<__nv_bfloat16>(), bq.as<float>());
       spadj_status st = check_launch(p, "closure convert");
@@ -908,10 +952,8 @@ struct Kol : EqImpl {
 
   spadj_status launch(Problem* p, KolArgs& A) {
     const int per = A.nCAtot + A.nBtot;
-    const double flops = 0;  // accounted per launch below
-    (void)flops;
-    cudaEvent_t t = p->tic();
     if (persistent) {
+      cudaEvent_t t = p->tic();
       SPADJ_CUDA_TRY(p, cudaMemsetAsync(ctr.ptr, 0, sizeof(int) * (2 * (size_t)nmem + 2), p->stream));
       if (!grid_persistent) {
         int dev = 0, sms = 0, occ = 0;
@@ -927,20 +969,24 @@ struct Kol : EqImpl {
       p->toc(t, KC_FUSED, work_flops(A));
       return s;
     }
+    // one launch per phase; the solver's phases and the closure's network passes are timed
+    // separately (classes fused and cnn), stage by stage
+    const double per_stage = A.nstage > 1 ? work_flops(A) / (A.nstage - 1) : 0.0;
     for (int st = 0; st < A.nstage; ++st) {
+      cudaEvent_t ts = p->tic();
       kol_phase<<<A.nCAtot, kKolThreads, smem, p->stream>>>(A, st, 1);
       spadj_status s = check_launch(p, "kolmogorov phase CA");
       if (s != SPADJ_OK) return s;
       if (st + 1 < A.nstage) {
         kol_phase<<<A.nBtot, kKolThreads, smem, p->stream>>>(A, st, 0);
         if ((s = check_launch(p, "kolmogorov phase B")) != SPADJ_OK) return s;
-        if (closure) {
-          s = A.adjoint ? closure_backward(p, A) : closure_forward(p, A);
-          if (s != SPADJ_OK) return s;
-        }
+      }
+      p->toc(ts, KC_FUSED, st + 1 < A.nstage ? per_stage : 0.0);
+      if (st + 1 < A.nstage && closure) {
+        s = A.adjoint ? closure_backward(p, A) : closure_forward(p, A);
+        if (s != SPADJ_OK) return s;
       }
     }
-    p->toc(t, KC_FUSED, work_flops(A));
     (void)per;
     return SPADJ_OK;
   }
@@ -1001,6 +1047,47 @@ struct Kol : EqImpl {
   int cnn_grid(long long n) const { return (int)std::min<long long>((n + 255) / 256, 4096); }
   int mma_grid(long long npix) const { return (int)std::min<long long>((npix + 63) / 64, 8192); }
 
+  // One 32 -> 32 convolution of layer l (1 or 2) over all members: mode 0 forward hidden layer
+  // (h, dact), 1 input gradient (fout), 2 pre-activation (fout, tests).  On the fifth-generation tensor
+  // cores (tcgen05, accumulator in tensor memory; default) or, with spadj_set_option 11 = 0, the
+  // warp-level mma.sync kernel (modes 0 and 1).
+  int sm_count = 0;
+  int tc_conv = 1;
+  DevBuf cnnerr;
+  spadj_status conv32(Problem* p, int l, int mode, const __nv_bfloat16* in, __nv_bfloat16* h, float* da, float* fout) {
+    const int M = hm[0].M, nb = nmem;
+    const long long P = (long long)M * M * nb;
+    if (tc_conv) {
+      const long long tiles = (P + cnn::kTcRows - 1) / cnn::kTcRows;
+      const int grid = (int)std::min<long long>(tiles, 2LL * sm_count);
+      cnn::conv32_tc_kernel<<<grid, 128, cnn::kTcSmem, p->stream>>>(l, M, nb, mode, in, wq.as<__nv_bfloat16>(),
+                                                                     bq.as<float>(), h, da, fout, cnnerr.as<int>());
+    } else {
+      if (mode == 2) return p->fail(SPADJ_ERR_UNSUPPORTED, "closure conv: pre-activation output needs the tcgen05 kernel");
+      cnn::conv32_mma_kernel<<<mma_grid(P), 128, 0, p->stream>>>(l, M, nb, mode, in, wq.as<__nv_bfloat16>(),
+                                                                  bq.as<float>(), h, da, fout);
+    }
+    return check_launch(p, "closure conv");
+  }
+
+  spadj_status closure_conv_layer(Problem* p, int l, int mode, const void* in, float* out) {
+    if (!closure) return p->fail(SPADJ_ERR_UNSUPPORTED, "closure_conv: the problem has no learned closure");
+    if ((l != 1 && l != 2) || (mode != 0 && mode != 1))
+      return p->fail(SPADJ_ERR_INVALID, "closure_conv: layer must be 1 or 2 and mode 0 or 1");
+    return conv32(p, l, mode == 0 ? 2 : 1, reinterpret_cast<const __nv_bfloat16*>(in), nullptr, nullptr, out);
+  }
+
+  spadj_status check_cnn(Problem* p) {  // synchronises the stream
+    int e = 0;
+    SPADJ_CUDA_TRY(p, cudaMemcpyAsync(&e, cnnerr.ptr, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+    SPADJ_CUDA_TRY(p, cudaStreamSynchronize(p->stream));
+    if (e) {
+      SPADJ_CUDA_TRY(p, cudaMemsetAsync(cnnerr.ptr, 0, sizeof(int), p->stream));
+      return p->fail(SPADJ_ERR_TIMEOUT, "closure: a tensor-core convolution gave up waiting for its MMAs");
+    }
+    return SPADJ_OK;
+  }
+
   spadj_status closure_forward(Problem* p, const KolArgs& A) {
     const int M = hm[0].M, nb = nmem;
     const long long P = (long long)M * M * nb;
@@ -1010,8 +1097,7 @@ struct Kol : EqImpl {
     for (int l = 0; l < cnn::kLayers; ++l) {
       const int co = (l == cnn::kLayers - 1) ? 1 : cnn::kHid;
       if (l == 1 || l == 2)  // 32 -> 32: tensor cores
-        cnn::conv32_mma_kernel<<<mma_grid(P), 128, 0, p->stream>>>(l, M, nb, 0, in, wq.as<__nv_bfloat16>(), bq.as<float>(),
-                                                                    hbuf[l].as<__nv_bfloat16>(), nullptr, nullptr);
+        conv32(p, l, 0, in, hbuf[l].as<__nv_bfloat16>(), nullptr, nullptr);
       else
         cnn::fwd_kernel<<<cnn_grid(P * co), 256, 0, p->stream>>>(
             l, M, nb, in, wq.as<__nv_bfloat16>(), bq.as<float>(), l < 3 ? hbuf[l].as<__nv_bfloat16>() : nullptr, nullptr,
@@ -1019,7 +1105,7 @@ struct Kol : EqImpl {
       if (l < 3) in = hbuf[l].as<__nv_bfloat16>();
     }
     closure_rows_kernel<<<dim3(M, nb), kKolThreads, smem, p->stream>>>(A, corr.as<double>(), 0);
-    p->toc(t, KC_POINTWISE, 2.0 * P * (9.0 * 32 + 2 * 9.0 * 32 * 32 + 9.0 * 32));
+    p->toc(t, KC_CNN, 2.0 * P * (9.0 * 32 + 2 * 9.0 * 32 * 32 + 9.0 * 32));
     return check_launch(p, "closure forward");
   }
 
@@ -1036,9 +1122,7 @@ struct Kol : EqImpl {
                                                                          bq.as<float>(), hbuf[l].as<__nv_bfloat16>(),
                                                                          dact[l].as<float>(), nullptr);
       else
-        cnn::conv32_mma_kernel<<<mma_grid(P), 128, 0, p->stream>>>(l, M, nb, 0, ins[l], wq.as<__nv_bfloat16>(),
-                                                                    bq.as<float>(), hbuf[l].as<__nv_bfloat16>(),
-                                                                    dact[l].as<float>(), nullptr);
+        conv32(p, l, 0, ins[l], hbuf[l].as<__nv_bfloat16>(), dact[l].as<float>(), nullptr);
     }
     for (int l = cnn::kLayers - 1; l >= 0; --l) {
       const int co = (l == cnn::kLayers - 1) ? 1 : cnn::kHid, ci = (l == 0) ? 1 : cnn::kHid;
@@ -1053,9 +1137,7 @@ struct Kol : EqImpl {
         cnn::wgrad32_finish_kernel<<<dim3(36, nb), 256, 0, p->stream>>>(l, chunkbuf.as<float>(), kWgradChunks,
                                                                         part.as<float>(), np);
         cnn::bgrad32_kernel<<<dim3(32, nb), 256, 0, p->stream>>>(l, M, dz.as<__nv_bfloat16>(), part.as<float>(), np);
-        cnn::conv32_mma_kernel<<<mma_grid(P), 128, 0, p->stream>>>(l, M, nb, 1, dz.as<__nv_bfloat16>(),
-                                                                    wq.as<__nv_bfloat16>(), bq.as<float>(), nullptr,
-                                                                    nullptr, dh.as<float>());
+        conv32(p, l, 1, dz.as<__nv_bfloat16>(), nullptr, nullptr, dh.as<float>());
       } else {
         cnn::wgrad_kernel<<<dim3(co * 10, nb), 256, 0, p->stream>>>(l, M, ins[l], dz.as<__nv_bfloat16>(), part.as<float>(),
                                                                     np);
@@ -1066,8 +1148,32 @@ struct Kol : EqImpl {
     }
     cnn::reduce_params_kernel<<<64, 256, 0, p->stream>>>(part.as<float>(), nb, np, gp.as<double>());
     closure_rows_kernel<<<dim3(M, nb), kKolThreads, smem, p->stream>>>(A, corr.as<double>(), 1);
-    p->toc(t, KC_POINTWISE, 6.0 * P * (9.0 * 32 + 2 * 9.0 * 32 * 32 + 9.0 * 32));
+    p->toc(t, KC_CNN, 6.0 * P * (9.0 * 32 + 2 * 9.0 * 32 * 32 + 9.0 * 32));
     return check_launch(p, "closure backward");
+  }
+
+  // spectral truncation of fine members (n_fine modes) to this uniform-resolution batch
+  spadj_status restrict_from(Problem* p, int n_fine, const double* fine, double* coarse) {
+    const int Nc = hm[0].N;
+    for (auto& m : hm)
+      if (m.N != Nc) return p->fail(SPADJ_ERR_UNSUPPORTED, "restrict: the batch must have one resolution");
+    if (n_fine < Nc || n_fine % 2 != 0) return p->fail(SPADJ_ERR_INVALID, "restrict: n_fine must be even and >= n[0]");
+    const long long n = (long long)(Nc / 2) * Nc * nmem;
+    const int grid = (int)std::min<long long>((n + 255) / 256, 4096);
+    restrict_kernel<<<grid, 256, 0, p->stream>>>(reinterpret_cast<const double2*>(fine), n_fine, Nc, nmem,
+                                                 reinterpret_cast<double2*>(coarse));
+    return check_launch(p, "restrict");
+  }
+
+  spadj_status adam(Problem* p, const double* g, int t, double lr, double b1, double b2, double eps, double* m,
+                    double* v, double* params) {
+    if (!closure) return p->fail(SPADJ_ERR_UNSUPPORTED, "adam: the problem has no learned closure");
+    if (t < 1 || !(lr > 0) || !(b1 >= 0 && b1 < 1) || !(b2 >= 0 && b2 < 1) || !(eps > 0))
+      return p->fail(SPADJ_ERR_INVALID, "adam: need t >= 1, lr > 0, 0 <= b1, b2 < 1, eps > 0");
+    const int n = cnn::n_params();
+    const double c1 = 1.0 - std::pow(b1, t), c2 = 1.0 - std::pow(b2, t);
+    adam_kernel<<<(n + 255) / 256, 256, 0, p->stream>>>(n, g, b1, b2, lr, eps, c1, c2, m, v, params);
+    return check_launch(p, "adam");
   }
 
   spadj_status set_params(Problem* p, const double* params) {
@@ -1185,6 +1291,10 @@ struct Kol : EqImpl {
       SPADJ_CUDA_TRY(p, cudaMemcpyAsync(grad_p, gp.ptr, sizeof(double) * cnn::n_params(), cudaMemcpyDeviceToDevice,
                                         p->stream));
     }
+    if (closure && J_host) {
+      spadj_status e = check_cnn(p);
+      if (e != SPADJ_OK) return e;
+    }
     if (J_host) {
       SPADJ_CUDA_TRY(p, cudaMemcpyAsync(J_host, Jd.ptr, sizeof(double) * nmem, cudaMemcpyDeviceToHost, p->stream));
       SPADJ_CUDA_TRY(p, cudaStreamSynchronize(p->stream));
@@ -1214,6 +1324,8 @@ struct Kol : EqImpl {
       case 5:  // failure-path test: member whose completion is never signalled (-1 = off)
         if (value < -1 || value >= nmem) return p->fail(SPADJ_ERR_INVALID, "set_option: member out of range");
         drop_signal_member = value; return SPADJ_OK;
+      case 11:  // closure convolutions on tcgen05 (1) or mma.sync (0)
+        tc_conv = value ? 1 : 0; return SPADJ_OK;
       default: return p->fail(SPADJ_ERR_INVALID, "set_option: unknown option");
     }
   }
@@ -1292,6 +1404,27 @@ spadj_status kol_set_params(EqImpl* impl, Problem* p, const double* params) {
   Kol* k = dynamic_cast<Kol*>(impl);
   if (!k) return p->fail(SPADJ_ERR_UNSUPPORTED, "set_params: only defined for the Kolmogorov batch with a closure");
   return k->set_params(p, params);
+}
+
+spadj_status kol_restrict(EqImpl* impl, Problem* p, int n_fine, const double* fine, double* coarse) {
+  Kol* k = dynamic_cast<Kol*>(impl);
+  if (!k) return p->fail(SPADJ_ERR_UNSUPPORTED, "restrict: only defined for SPADJ_KOLMOGOROV2D");
+  return k->restrict_from(p, n_fine, fine, coarse);
+}
+
+spadj_status kol_adam(EqImpl* impl, Problem* p, const double* g, int t, double lr, double b1, double b2, double eps,
+                      double* m, double* v, double* params) {
+  Kol* k = dynamic_cast<Kol*>(impl);
+  if (!k) return p->fail(SPADJ_ERR_UNSUPPORTED, "adam: only defined for SPADJ_KOLMOGOROV2D with a closure");
+  return k->adam(p, g, t, lr, b1, b2, eps, m, v, params);
+}
+
+spadj_status kol_closure_conv(EqImpl* impl, Problem* p, int layer, int mode, const void* in, float* out) {
+  Kol* k = dynamic_cast<Kol*>(impl);
+  if (!k) return p->fail(SPADJ_ERR_UNSUPPORTED, "closure_conv: only defined for SPADJ_KOLMOGOROV2D with a closure");
+  spadj_status s = k->closure_conv_layer(p, layer, mode, in, out);
+  if (s != SPADJ_OK) return s;
+  return k->check_cnn(p);
 }
 
 spadj_status kol_autotune(EqImpl* impl, Problem* p) {

@@ -1,3 +1,5 @@
+// Launch helpers and asynchronous copies shared by the kernels.
+//
 // Programmatic dependent launch (sm_90+): a kernel launched with the programmatic
 // stream-serialisation attribute may be scheduled while its predecessor in the stream is
 // still running.  Kernels signal early that their dependents may launch (pdl_trigger) and
@@ -27,6 +29,47 @@ __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src)
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// ---- bulk (TMA) copies completing on an mbarrier ----------------------------------------------
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+// initialise an mbarrier (8-byte aligned shared word) for `count` arrivals; make the initialisation
+// visible to the asynchronous proxy before a bulk copy signals it
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// this thread's arrival, announcing `bytes` of transactions that complete the current phase
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+// one bulk copy of `bytes` (multiple of 16; both addresses 16-byte aligned) from global memory into
+// this CTA's shared memory, counted on `bar` as it lands
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for phase `parity` of `bar`: true when it completed; after `limit` polls (each a
+// hardware-suspended try_wait plus a short sleep) false, and *err (nullable) is set.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity, unsigned limit, int* err) {
+  for (unsigned it = 0; it < limit; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    __nanosleep(64);
+  }
+  if (err) atomicExch(err, 1);
+  return false;
+}
 
 // Launch `kernel` on `st`, with the programmatic stream-serialisation attribute when pdl.
 template <typename... KArgs, typename... Args>

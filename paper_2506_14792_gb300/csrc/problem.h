@@ -107,7 +107,7 @@ struct EqImpl {
 // Optional per-kernel-class timing: CUDA events recorded on the problem's stream around
 // every launch of the library, with the algorithmic FP64 flop count of that launch.
 enum KernelClass { KC_ZTRANSFORM = 0, KC_XFFT = 1, KC_POINTWISE = 2, KC_SOLVE = 3, KC_OBJECTIVE = 4, KC_FUSED = 5,
-                   KC_YFFT = 6, KC_GRAM = 7, KC_COUNT = 8 };
+                   KC_YFFT = 6, KC_GRAM = 7, KC_CNN = 8, KC_COUNT = 9 };
 
 struct Timing {
   bool enabled = false;
@@ -155,6 +155,7 @@ struct Problem {
   bool fuse_columns = true;  // RB: fused fold + solve + expand cluster kernel (spadj_set_option 7)
   int x_rows = 0;            // x-FFT rows per CTA: 0 = tuned at creation, else 1, 2 or 4 (option 8)
   int host_slots = 0;        // host checkpoint slots of the two-level schedule, 0 = device only (option 9)
+  bool bulk_staging = true;  // RB fused column stages: operator block by one bulk copy (option 10)
   cudaEvent_t tic() {
     if (!timing.enabled) return nullptr;
     cudaEvent_t e = timing.get();
@@ -188,6 +189,7 @@ inline spadj_status check_launch(Problem* p, const char* what) {
 
 // Factories (one per equation set).
 EqImpl* make_burgers(Problem* p, spadj_status* st);
+spadj_status burgers_set_dt_schedule(EqImpl* impl, Problem* p, int n, const double* dts);
 EqImpl* make_rb(Problem* p, spadj_status* st);
 spadj_status rb_pencil_solve(EqImpl* impl, Problem* p, int transpose, const double* v, double* x);
 spadj_status rb_set_dt_schedule(EqImpl* impl, Problem* p, int n, const double* dts);
@@ -199,6 +201,10 @@ spadj_status kol_set_observations(EqImpl* impl, Problem* p, int n, const int* st
 spadj_status kol_set_option(EqImpl* impl, Problem* p, int option, int value);
 spadj_status kol_autotune(EqImpl* impl, Problem* p);
 spadj_status kol_set_params(EqImpl* impl, Problem* p, const double* params);
+spadj_status kol_restrict(EqImpl* impl, Problem* p, int n_fine, const double* fine, double* coarse);
+spadj_status kol_closure_conv(EqImpl* impl, Problem* p, int layer, int mode, const void* in, float* out);
+spadj_status kol_adam(EqImpl* impl, Problem* p, const double* g, int t, double lr, double b1, double b2, double eps,
+                      double* m, double* v, double* params);
 spadj_status rb_transform_noalloc(EqImpl* impl, Problem* p, int kind, const double* in, double* out);
 EqImpl* make_couette(Problem* p, spadj_status* st);
 spadj_status cou_pencil_solve(EqImpl* impl, Problem* p, int transpose, const double* v, double* x);

@@ -67,6 +67,7 @@ struct RB : EqImpl {
   // device work buffers
   DevBuf dG, Gb, Fg, df0, df1, dx1, vb2, vb1, xb1, tmpx, tmpy, ybar, ybar2, cur, nxt, curB, nxtB, partial, Jdev,
       seedbuf, slots, traj_tmp;
+  DevBuf errbuf;   // set by a fused column stage whose bounded wait for its operator block ran out
   HostBuf hslots;  // host tier of the two-level checkpoint schedule
   // Buffers of one forward step.  Lane 0 runs the forward sweep and the adjoint steps, lane 1
   // the recomputation of checkpointed segments, concurrently on its own stream; in the reverse
@@ -234,6 +235,8 @@ struct RB : EqImpl {
       SPADJ_CUDA_TRY(p, cudaEventCreateWithFlags(e, cudaEventDisableTiming));
     SPADJ_CUDA_TRY(p, partial.ensure(sizeof(double) * Kx));
     SPADJ_CUDA_TRY(p, Jdev.ensure(sizeof(double)));
+    SPADJ_CUDA_TRY(p, errbuf.ensure(sizeof(int)));
+    SPADJ_CUDA_TRY(p, cudaMemsetAsync(errbuf.ptr, 0, sizeof(int), p->stream));
     zsmem = (size_t)2 * 2 * (size_t)std::max(N, Mz / 2) * kTM * sizeof(double2);
     xsmem = sizeof(double2) * (4 * L + Kx);
     const int H = 3 * (N / 2);
@@ -572,6 +575,8 @@ struct RB : EqImpl {
     S.zout = w->Z.as<double2>();
     S.nmix = nmix;
     S.Kx = Kx; S.N = N; S.Mz = Mz;
+    S.err = errbuf.as<int>();
+    S.bulk = p->bulk_staging ? 1 : 0;
     const int H = 3 * N / 2;
     const double fl = (double)Kx * (3 * 2 * 4.0 * N * (Mz / 2) + 2 * 4.0 * H * H + 3 * 4.0 * N * (Mz / 2));
     cudaEvent_t t = p->tic();
@@ -613,6 +618,8 @@ struct RB : EqImpl {
     S.zout = expand ? w->Z.as<double2>() : nullptr;
     S.nmix = nmix;
     S.Kx = Kx; S.N = N; S.Mz = Mz;
+    S.err = errbuf.as<int>();
+    S.bulk = p->bulk_staging ? 1 : 0;
     const int H = 3 * N / 2;
     // algorithmic flops: fold 4 N (Mz/2) per field column, solve 2 classes x 4 H^2, expand as zflops
     const double fl = (double)Kx * (3 * 4.0 * N * (Mz / 2) + 2 * 4.0 * H * H + (expand ? 6 * 4.0 * N * (Mz / 2) : 0.0));
@@ -1375,8 +1382,14 @@ struct RB : EqImpl {
     SPADJ_CUDA_TRY(p, cudaStreamWaitEvent(p->stream, evCdone, 0));
     SPADJ_CUDA_TRY(p, cudaMemcpyAsync(grad, Yb[yi], sb, cudaMemcpyDeviceToDevice, p->stream));
     if (J_host && objective_kind >= 0) {
+      int err = 0;
       SPADJ_CUDA_TRY(p, cudaMemcpyAsync(J_host, Jdev.ptr, sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+      SPADJ_CUDA_TRY(p, cudaMemcpyAsync(&err, errbuf.ptr, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
       SPADJ_CUDA_TRY(p, cudaStreamSynchronize(p->stream));
+      if (err) {
+        SPADJ_CUDA_TRY(p, cudaMemsetAsync(errbuf.ptr, 0, sizeof(int), p->stream));
+        return p->fail(SPADJ_ERR_TIMEOUT, "rb: a fused column stage gave up waiting for its operator block");
+      }
       if (!std::isfinite(J_host[0])) return p->fail(SPADJ_ERR_NONFINITE, "rb: objective is not finite");
     }
     return SPADJ_OK;
@@ -1418,6 +1431,7 @@ struct RB : EqImpl {
     for (int i = 0; i < 4; ++i)
       for (DevBuf* b : {&tdx[i], &tdv[i], &tdf[i], &axb[i], &avb[i], &afb[i]}) b->release();
     for (DevBuf* b : {&aacc, &atmp, &axs}) b->release();
+    errbuf.release();
     for (DevBuf* b : {&wm, &czE, &cdzE, &gzF, &gzTE, &czTF, &cdzTF, &gmat, &dG, &Gb, &Fg, &df0, &df1, &dx1,
                       &vb2, &vb1, &xb1, &tmpx, &tmpy, &ybar, &ybar2, &cur, &nxt, &curB, &nxtB, &partial, &Jdev,
                       &seedbuf, &slots, &traj_tmp})

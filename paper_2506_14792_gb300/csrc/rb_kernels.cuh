@@ -608,13 +608,18 @@ __global__ void __launch_bounds__(1024) solve_kernel(const __grid_constant__ Sol
 // CTAs (one per z-parity class, cluster rank = class):
 //   1. fold: f = Gz Y for the three grid-product rows Y_q (mixed [Mz][Kx]) restricted to the
 //      modes of this class (the reflection-folded Chebyshev reduction of zmm_kernel);
-//   2. solve: x = Phi (sum_t a_t in_t + af f) for this class (solve_kernel's arithmetic, with
-//      the class block of Phi' staged in shared memory by cp.async during the fold);
+//   2. solve: x = Phi (sum_t a_t in_t + af f) for this class (solve_kernel's arithmetic), with
+//      the class block of Phi' brought into shared memory by one bulk copy (cp.async.bulk,
+//      completing on an mbarrier) issued at entry, so it lands during the fold;
 //   3. when zout is set: the two CTAs exchange their halves of x through distributed shared
 //      memory and each expands three of the six grid fields (u, dz u, w, dz w, theta,
 //      dz theta; class 0 the values, class 1 the z-derivatives) into zout[6][Mz][Kx].
 // f and x are also written in the state layout [3][Kx][N].  Replaces zmm fold + solve +
-// zmm expand (three launches) by one.
+// zmm expand (three launches) by one.  The kernel is FP64-throughput bound (one thread per
+// output of each phase keeps the dependency chains long but the FP64 pipe busy; spreading the dot
+// products over all threads with a reduction measured slower, its adds cost FP64 issue slots).
+// A bulk copy that does not complete within the bounded wait sets *err (the launch's results are
+// then invalid; the host reports it).
 struct ColStepArgs {
   const double2* yin[3];  // grid products after the x-forward FFT, mixed layout
   const double* gzF;      // N x (Mz/2) fold matrix
@@ -630,7 +635,39 @@ struct ColStepArgs {
   double2* zout;          // nullable
   size_t nmix;
   int Kx, N, Mz;
+  int* err;
+  int bulk;               // 1: operator block by one bulk copy; 0: per-thread cp.async
 };
+
+constexpr unsigned kCsSpin = 1u << 20;  // bounded wait for the operator block's bulk copy
+
+// Bounded wait of every thread for the operator block; a second bounded wait after a timeout
+// (the copy targets this CTA's shared memory, which must not be left while it may still land).
+__device__ __forceinline__ void colstep_wait_block(unsigned long long* bar, int* err, int bulk) {
+  if (!bulk) {
+    cp_async_wait_all();
+    return;
+  }
+  if (!mbar_wait_bounded(bar, 0, kCsSpin, err)) mbar_wait_bounded(bar, 0, kCsSpin, nullptr);
+}
+
+// The class block (H x H doubles) into ph: one bulk copy counted on bar (thread 0), or, when
+// bulk == 0, 16-byte cp.async copies spread over the threads (completed by colstep_wait_block).
+__device__ __forceinline__ void colstep_issue_block(double* ph, const double* blk, int H, unsigned long long* bar,
+                                                    int bulk) {
+  if (bulk) {
+    if (threadIdx.x == 0) {
+      const unsigned bytes = (unsigned)(sizeof(double) * (size_t)H * H);
+      mbar_init(bar, 1);
+      mbar_arrive_expect_tx(bar, bytes);
+      bulk_g2s(ph, blk, bytes, bar);
+    }
+  } else {
+    for (int idx = threadIdx.x; idx < H * H / 2; idx += blockDim.x)
+      cp_async16(reinterpret_cast<double2*>(ph) + idx, reinterpret_cast<const double2*>(blk) + idx);
+    cp_async_commit();
+  }
+}
 
 __host__ __device__ inline size_t colstep_smem(int N, int Mz) {
   const int H = 3 * N / 2;
@@ -645,16 +682,14 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256) rb_colstep_kern
   const int N = S.N, Nh = N / 2, H = 3 * Nh, Kx = S.Kx, Mz = S.Mz, Mh = Mz / 2;
   const int tid = threadIdx.x, nt = blockDim.x;
   extern __shared__ double2 cs[];
+  __shared__ unsigned long long bar;
   double* ph = reinterpret_cast<double*>(cs);          // [H][H] as [k][r]
   double2* sd = cs + (size_t)H * H / 2;                // [3][Mh] folded samples (s or d)
   double2* fs = sd + 3 * Mh;                           // [3][N] f (this class's modes)
   double2* v = fs + 3 * N;                             // [H] right-hand side (class order)
   double2* xc = v + H;                                 // [H] solution (class order)
-  const double* blk = S.phiF + ((size_t)m * 2 + cls) * H * H;
+  colstep_issue_block(ph, S.phiF + ((size_t)m * 2 + cls) * H * H, H, &bar, S.bulk);
   pdl_trigger();
-  for (int idx = tid; idx < H * H / 2; idx += nt)
-    cp_async16(reinterpret_cast<double2*>(ph) + idx, reinterpret_cast<const double2*>(blk) + idx);
-  cp_async_commit();
   pdl_wait();
   // class-local mode of field q: parity (q == 0 ? cls : 1 - cls); fold with s (even) or d (odd)
   for (int idx = tid; idx < 3 * Mh; idx += nt) {
@@ -699,7 +734,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256) rb_colstep_kern
     if (q == 0) x = make_double2(x.y, -x.x);  // times -i (Dr)
     v[c] = x;
   }
-  cp_async_wait_all();
+  colstep_wait_block(&bar, S.err, S.bulk);
   __syncthreads();
   for (int r = tid; r < H; r += nt) {
     double2 a0 = make_double2(0.0, 0.0), a1 = make_double2(0.0, 0.0);
@@ -754,8 +789,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256) rb_colstep_kern
 // for one x-mode pencil, as a cluster of two CTAs (one per z-parity class):
 //   1. fold: xb = Cz^T a_q + (Cz Dz)^T b_q + sum_a beta_a add_a for the six mixed rows
 //      (a_u, b_u, a_w, b_w, a_t, b_t) restricted to this class's modes;
-//   2. transposed solve: vb = Phi^H xb for this class (solve_kernel's transpose arithmetic,
-//      the class block of Phi' staged in shared memory by cp.async during the fold);
+//   2. transposed solve: vb = Phi^H xb for this class (solve_kernel's transpose arithmetic),
+//      the class block of Phi' brought into shared memory by one bulk copy (completing on an
+//      mbarrier) issued at entry;
 //   3. the two CTAs exchange their halves of vb through distributed shared memory and each
 //      expands, for half of the Gauss rows, the three columns Gz^T (al0 c0 + al1 vb) into
 //      zout[3][Mz][Kx] (the first transform of the next vector-Jacobian product).
@@ -775,6 +811,8 @@ struct ColStepTArgs {
   double2* zout;
   size_t nmix;
   int Kx, N, Mz;
+  int* err;
+  int bulk;
 };
 
 __host__ __device__ inline size_t colstepT_smem(int N, int Mz) {
@@ -790,15 +828,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256) rb_colstepT_ker
   const int N = S.N, Nh = N / 2, H = 3 * Nh, Kx = S.Kx, Mz = S.Mz, Mh = Mz / 2;
   const int tid = threadIdx.x, nt = blockDim.x;
   extern __shared__ double2 cs[];
+  __shared__ unsigned long long bar;
   double* ph = reinterpret_cast<double*>(cs);   // [H][H] as [k][r]
   double2* sd = cs + (size_t)H * H / 2;         // [6][Mh] folded samples
   double2* xv = sd + 6 * Mh;                    // [H] right-hand side (class order)
   double2* vc = xv + H;                         // [H] solution (class order)
+  colstep_issue_block(ph, S.phiA + ((size_t)m * 2 + cls) * H * H, H, &bar, S.bulk);
   pdl_trigger();
-  const double* blk = S.phiA + ((size_t)m * 2 + cls) * H * H;
-  for (int idx = tid; idx < H * H / 2; idx += nt)
-    cp_async16(reinterpret_cast<double2*>(ph) + idx, reinterpret_cast<const double2*>(blk) + idx);
-  cp_async_commit();
   pdl_wait();
   // row e = 2q + term: term 0 (values) folds with s for even modes, term 1 (z-derivative
   // parity) with s for odd modes; this class's modes of field q have parity (q == 0 ? cls : 1 - cls)
@@ -835,7 +871,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256) rb_colstepT_ker
     if (q == 0) x = make_double2(x.y, -x.x);  // times -i (Dc^H)
     xv[c] = x;
   }
-  cp_async_wait_all();
+  colstep_wait_block(&bar, S.err, S.bulk);
   __syncthreads();
   for (int r = tid; r < H; r += nt) {
     double2 a0 = make_double2(0.0, 0.0), a1 = make_double2(0.0, 0.0);

@@ -78,6 +78,10 @@ _SIGS = {
     "spadj_set_option": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
     "spadj_autotune": (ctypes.c_int, [_vp]),
     "spadj_set_params": (ctypes.c_int, [_vp, _vp]),
+    "spadj_restrict": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp]),
+    "spadj_closure_conv": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp]),
+    "spadj_adam": (ctypes.c_int, [_vp, _vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                  ctypes.c_double, _vp, _vp, _vp]),
     "spadj_checkpoint_schedule": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "spadj_forward": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp]),
     "spadj_tangent": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp]),
@@ -301,6 +305,32 @@ class Problem:
     def set_params(self, params):
         _chk(self.h, lib().spadj_set_params(self.h, _ptr(_as_f64(params, self.state_len(2), "params"))))
 
+    def restrict(self, n_fine, fine, coarse):
+        """Spectral truncation of fine members (n_fine modes) to this problem's resolution."""
+        B, Nc = self.desc.batch, self.desc.n[0]
+        _chk(self.h, lib().spadj_restrict(self.h, int(n_fine), _ptr(_as_f64(fine, B * n_fine * n_fine, "fine")),
+                                           _ptr(_as_f64(coarse, self.state_len(0), "coarse"))))
+        return coarse
+
+    def closure_conv(self, layer, mode, inp, out):
+        """One 32 -> 32 closure convolution (mode 0 pre-activation, 1 input gradient); inp: int16/bfloat16
+        CUDA tensor [pixels][32], out: float32 CUDA tensor of the same shape."""
+        import torch
+        if inp.dtype not in (torch.int16, torch.bfloat16) or out.dtype != torch.float32 or inp.numel() != out.numel():
+            raise ValueError("closure_conv: bfloat16/int16 input and float32 output of equal size")
+        if not (inp.is_cuda and out.is_cuda and inp.is_contiguous() and out.is_contiguous()):
+            raise ValueError("closure_conv: contiguous CUDA tensors")
+        _chk(self.h, lib().spadj_closure_conv(self.h, int(layer), int(mode), _ptr(inp), _ptr(out)))
+        return out
+
+    def adam(self, grad_p, t, m, v, params, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+        """One Adam step on the closure parameters (m, v: caller-owned moments)."""
+        n = self.state_len(2)
+        _chk(self.h, lib().spadj_adam(self.h, _ptr(_as_f64(grad_p, n, "grad_p")), int(t), float(lr), float(b1),
+                                       float(b2), float(eps), _ptr(_as_f64(m, n, "m")), _ptr(_as_f64(v, n, "v")),
+                                       _ptr(_as_f64(params, n, "params"))))
+        return params
+
     def set_option(self, option, value):
         _chk(self.h, lib().spadj_set_option(self.h, int(option), int(value)))
 
@@ -355,7 +385,7 @@ class Problem:
         return gains
 
     KERNEL_CLASSES = ("z_transform", "x_fft", "pointwise", "pencil_solve", "objective", "fused_trajectory", "y_fft",
-                      "gram")
+                      "gram", "cnn")
 
     def timing(self, enable=True):
         _chk(self.h, lib().spadj_timing(self.h, int(bool(enable))))

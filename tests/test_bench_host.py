@@ -52,6 +52,8 @@ def test_hbm_fraction(bench):
     (["--workload", "rb", "--size", "128,32", "--dt-blocks", "50", "--nsteps", "200"],
      "rayleigh_benard2d_128x32_Ra1e6_rk222_200steps_dtblocks50",
      lambda w: w.Nx == 128 and w.Nz == 32 and w.dt_blocks == 50 and len(w.schedule()) == 200),
+    (["--workload", "burgers", "--batch", "1"], "burgers1d_N256_sbdf2_1000steps_b1",
+     lambda w: w.B == 1 and w.units_per_step() == 256 * 1000),
     (["--workload", "burgers", "--scheme", "sbdf4"], "burgers1d_N256_sbdf4_1000steps",
      lambda w: w.ORDERS[w.scheme] == 4),
     (["--workload", "couette", "--op", "hvp", "--size", "64,32,32", "--nsteps", "100"],
@@ -74,6 +76,7 @@ def test_workload_variants_from_the_command_line(bench, argv, name, check):
 
 
 @pytest.mark.parametrize("argv", [["--workload", "burgers", "--dt-blocks", "5"],
+                                  ["--workload", "rb", "--batch", "4"],
                                   ["--workload", "rb", "--scheme", "sbdf2"],
                                   ["--workload", "rb", "--op", "hvp"],
                                   ["--workload", "couette", "--omega", "1.0"]])

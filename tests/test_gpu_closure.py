@@ -1,10 +1,13 @@
 """GPU closure (BF16-operand / FP32-accumulate CNN inside the Kolmogorov F) against the FP64
-oracle.  Stated tolerances: the closure correction and the gradients carry the BF16 operand
-rounding of four stacked layers (about 2^-8 per operand), so they are compared at the
-percent level, while the FP64 parts stay exact:
-  * correction C(w; p) on the grid: max-norm relative error <= 3e-2
-  * trajectory gradients w.r.t. the initial state and the 19105 parameters: <= 5e-2
-  * zero parameters: the closure problem reproduces the plain solver bitwise."""
+oracle.  The closure correction and the gradients carry the BF16 operand rounding of four stacked
+layers (2^-9 relative per operand); measured on the GB300: correction 1.4-1.9e-3, J 1e-5,
+dJ/dX_0 1e-5, dJ/dp 3.7e-3 (max-norm relative).  Bars (about 2.5-10x the measured errors, so a
+dropped tap, channel block or reduction chunk, an error of several percent, fails):
+  * correction C(w; p) on the grid: <= 5e-3
+  * J and dJ/dX_0 of a trajectory objective: <= 1e-4; dJ/dp (19105 parameters): <= 1e-2
+  * zero parameters: the closure problem reproduces the plain solver bitwise
+  * each 32 -> 32 tensor-core convolution alone against the oracle's convolution of the same BF16
+    operands (exact products and sums): <= 1e-5 (FP32 accumulation only)."""
 import numpy as np
 import pytest
 
@@ -44,9 +47,12 @@ def test_closure_correction_matches_fp64():
     C = host(f1 - f0).reshape(B, N // 2, N)
     o = okol.Kolmogorov(N, RE)
     net = cnn.CNN(params)
+    errs = []
     for b in range(B):
         want = o.g2c(net.forward(o.c2g(X[b])))
-        assert rel_err(C[b], want) < 3e-2
+        errs.append(rel_err(C[b], want))
+        assert errs[-1] < 5e-3
+    print("closure correction vs FP64 oracle, max-norm relative error per member:", errs)
 
 
 def test_zero_params_bitwise_plain():
@@ -88,6 +94,57 @@ def test_closure_gradients_vs_fp64_oracle():
     J = p.gradient(dev(np.concatenate([a.ravel() for a in X0])), nsteps, g, objective=spadj.SPADJ_OBJ_FOURDVAR, grad_p=gp)
     gh = host(g).reshape(B, N // 2, N)
     for b in range(B):
-        assert abs(J[b] - J_ref[b]) <= 1e-2 * abs(J_ref[b])
-        assert rel_err(gh[b], gx_ref[b]) < 5e-2
-    assert rel_err(host(gp), gp_ref) < 5e-2
+        assert abs(J[b] - J_ref[b]) <= 1e-4 * abs(J_ref[b])
+        assert rel_err(gh[b], gx_ref[b]) < 1e-4
+    assert rel_err(host(gp), gp_ref) < 1e-2
+    print("closure gradients vs FP64 oracle: J", [abs(J[b] - J_ref[b]) / abs(J_ref[b]) for b in range(B)],
+          "dJ/dX0", [rel_err(gh[b], gx_ref[b]) for b in range(B)], "dJ/dp", rel_err(host(gp), gp_ref))
+
+
+def _bf16(x):
+    """float32 -> the nearest bfloat16 (round to nearest even), as float32 values and bit patterns."""
+    u = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32)
+    r = (((u >> 16) & 1) + 0x7FFF).astype(np.uint32)
+    v = ((u + r) & np.uint32(0xFFFF0000)).view(np.float32)
+    return v, (v.view(np.uint32) >> 16).astype(np.uint16)
+
+
+@pytest.mark.parametrize("layer", [1, 2])
+def test_tensor_core_convolution_vs_bf16_restated_oracle(layer):
+    """The 32 -> 32 layers on the fifth-generation tensor cores (tcgen05.mma, FP32 accumulator in tensor
+    memory), called alone through spadj_closure_conv: the pre-activation conv(x) + b and the input
+    gradient conv^T(g) against the oracle's direct-sum convolution (oracle/cnn.py) applied to the same
+    BF16-rounded operands with exact (FP64) products and sums: the only difference left is the FP32
+    accumulation, so the bar is 1e-5 relative.  Three members of a 24 x 24 grid: 1728 pixels, 13.5
+    tiles of 128 (a ragged last tile)."""
+    from oracle import cnn as ocnn
+    from paper_2506_14792_gb300 import spadj
+    N, nb = 16, 3
+    M = 3 * N // 2
+    p = spadj.Problem(spadj.SPADJ_KOLMOGOROV2D, spadj.SPADJ_SBDF2, [N], [2 * np.pi], [RE, 0.0], 4e-3, batch=nb,
+                      closure=True)
+    prm = synthetic.cnn_params(11, scale_out=0.5)
+    p.set_params(dev(prm))
+    W, b = ocnn.unpack(prm)[layer]
+    Wq = _bf16(W.astype(np.float32))[0].astype(np.float64)  # the library's FP64 -> FP32 -> BF16 rounding
+    bq = b.astype(np.float32).astype(np.float64)
+    rng = np.random.default_rng(layer)
+    x = rng.uniform(-1.0, 1.0, (nb, 32, M, M)).astype(np.float32)  # oracle layout [member][c][x][y]
+    xv, xbits = _bf16(x)
+    inp = torch.from_numpy(np.ascontiguousarray(xbits.view(np.int16).transpose(0, 3, 2, 1))).cuda()  # [m][y][x][c]
+    out = torch.zeros((nb, M, M, 32), dtype=torch.float32, device="cuda")
+    for mode in (0, 1):
+        p.closure_conv(layer, mode, inp, out)
+        got = host(out).transpose(0, 3, 2, 1)  # -> [m][o][x][y]
+        for m in range(nb):
+            xm = xv[m].astype(np.float64)
+            ref = ocnn.conv(xm, Wq, bq) if mode == 0 else ocnn.conv_t(xm, Wq)
+            err = np.max(np.abs(got[m] - ref)) / np.max(np.abs(ref))
+            assert err < 1e-5, (layer, mode, m, err)
+    # the warp-level mma.sync kernel computes the same input gradient
+    p.set_option(11, 0)
+    ref_tc = host(out).copy()
+    out.zero_()
+    p.closure_conv(layer, 1, inp, out)
+    assert np.max(np.abs(host(out) - ref_tc)) <= 1e-5 * np.max(np.abs(ref_tc))
+    p.set_option(11, 1)

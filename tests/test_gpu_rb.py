@@ -330,3 +330,23 @@ def test_x_rows_per_cta_bitwise(Nx, Nz):
         outs.append((f, v))
     for f, v in outs[1:]:
         assert torch.equal(f, outs[0][0]) and torch.equal(v, outs[0][1])
+
+
+def test_full_horizon_gradient_matches_oracle_golden():
+    """The benchmarked configuration itself (256 x 64, Ra = 1e6, RK222, dt = 1e-3, 2000 steps, 64
+    binomial checkpoint slots): J and dJ/dX_0 against the oracle's values in tests/golden (written by
+    tests/golden/make_rb_256x64_2000steps.py from oracle/ alone), element by element.  The bar is
+    max(1e-10, 10 x the oracle's own spread), the spread being the difference between the oracle run
+    with numpy's FFT and with direct exponential sums (about 1e-14 at this horizon)."""
+    import os
+    gold = np.load(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                                "rb_256x64_ra1e6_rk222_2000steps.npz"))
+    tol = max(1e-10, 10.0 * float(gold["spread_grad"]), 10.0 * float(gold["spread_J"]))
+    assert tol == 1e-10  # the spread is far below the parity bar at this horizon
+    Nx, Nz, dt, nsteps = 256, 64, 1e-3, 2000
+    p = gpu_problem(Nx, Nz, dt=dt)
+    s0 = synthetic.rb_ic(Nx, Nz, seed=2, amp=1e-3)
+    gr = _z((3, Nx // 2, Nz))
+    J = p.gradient(dev(s0), nsteps, gr, ckpt_slots=64)[0]
+    assert abs(J - float(gold["J"])) <= tol * abs(float(gold["J"]))
+    assert rel_err(host(gr), gold["grad"]) < tol

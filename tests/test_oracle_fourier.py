@@ -68,3 +68,22 @@ def test_axis_argument():
     c[0] = c[0].real
     g0 = fourier.c2g(c, M, axis=0)
     np.testing.assert_allclose(g0, fourier.c2g(c.T, M).T, atol=1e-14)
+
+
+def test_direct_sum_transforms_equal_fft_forms_and_brute_force():
+    """The direct-sum forms (used to measure rounding-order spread) are the same four maps: they
+    agree with the FFT forms and with the brute-force real matrices to rounding."""
+    from oracle import fourier as fo
+    rng = np.random.default_rng(11)
+    for K, M in ((4, 12), (16, 48), (128, 384)):
+        c = rng.standard_normal((3, K)) + 1j * rng.standard_normal((3, K))
+        g = rng.standard_normal((3, M))
+        for a, b, x, n in ((fo.c2g, fo.c2g_direct, c, M), (fo.g2c, fo.g2c_direct, g, K),
+                           (fo.c2g_adj, fo.c2g_adj_direct, g, K), (fo.g2c_adj, fo.g2c_adj_direct, c, M)):
+            r1, r2 = a(x, n), b(x, n)
+            assert np.max(np.abs(r1 - r2)) <= 1e-13 * np.max(np.abs(r1))
+        B = fo.dense_c2g(K, M)
+        cr = fo.to_real(c[0])
+        assert np.allclose(fo.c2g_direct(c[0], M), B @ cr, rtol=0, atol=1e-12 * np.max(np.abs(B @ cr)))
+        T = fo.dense_g2c(K, M)
+        assert np.allclose(fo.to_real(fo.g2c_direct(g[0], K)), T @ g[0], rtol=0, atol=1e-13)
