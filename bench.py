@@ -61,6 +61,15 @@ def hbm_peak_gbs():
         return 6800.0, "fallback"
 
 
+def bf16_peak_gflops():
+    """Measured dense BF16 tensor rate (burst, GFLOP/s) and its source, or the recipe's fallback."""
+    try:
+        with open(PEAKS_PATH) as f:
+            return 1e3 * float(json.load(f)["bf16_tflops"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return 1.9e6, "fallback"
+
+
 def hbm_fraction(traffic, avg_launch_s):
     """DRAM bytes of one launch of the dominant kernel over its CUDA-event duration, against the
     measured HBM roof (the metric's "% HBM roofline"); None without an ncu traffic figure."""
@@ -778,10 +787,12 @@ class Closure:
         plain = ct.rollout_errors(zero, te, self.ntest, self.NC, self.RE, self.dt_c, at)
         cnn = ct.rollout_errors(best, te, self.ntest, self.NC, self.RE, self.dt_c, at)
         # per window-step costs of the three solvers (forward sweeps over the held-out windows)
-        pc = ct.coarse_problem(self.ntest, self.NC, self.RE, self.dt_c)
         yc = torch.empty_like(te[0])
-        pc.set_params(zero)
-        us_plain = self._per_step_us(lambda: pc.forward(self.NCO, te[0].contiguous(), yc), self.NCO * self.ntest)
+        pp = spadj.Problem(spadj.SPADJ_KOLMOGOROV2D, spadj.SPADJ_SBDF2, [self.NC], [2 * np.pi], [self.RE, 0.0],
+                           self.dt_c, batch=self.ntest)  # the plain coarse solver (no network)
+        us_plain = self._per_step_us(lambda: pp.forward(self.NCO, te[0].contiguous(), yc), self.NCO * self.ntest)
+        pp.close()
+        pc = ct.coarse_problem(self.ntest, self.NC, self.RE, self.dt_c)
         pc.set_params(best)
         us_cnn = self._per_step_us(lambda: pc.forward(self.NCO, te[0].contiguous(), yc), self.NCO * self.ntest)
         pc.close()
@@ -1014,6 +1025,9 @@ def run_gpu(args, wl):
         wl.p.set_option(8, args.x_rows)
     if args.host_slots:
         wl.p.set_option(9, args.host_slots)
+    for kv in args.set_option:
+        k, v = kv.split("=")
+        wl.p.set_option(int(k), int(v))
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev) if wl.flush_l2 else None
 
@@ -1090,15 +1104,18 @@ def run_gpu(args, wl):
     per_kernel = {k: {"ms_total": v[0], "launches": v[2], "share": v[0] / sum(x[0] for x in rep.values()),
                       "gflops": v[1] / (v[0] / 1e3) / 1e9 if v[0] > 0 else None} for k, v in rep.items()}
     total_flops = sum(v[1] for v in rep.values())
-    roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "GFLOP/s",
-            "frac": achieved / peak, "traffic": traffic_for(wl, dom),
+    bound, dpeak, psrc = "alu", peak, "measured"
+    if dom == "cnn":  # BF16 operands on the tensor cores: the measured dense BF16 rate
+        bound, dpeak, psrc = "tensor", bf16_peak_gflops()
+    roof = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": dpeak, "unit": "GFLOP/s",
+            "frac": achieved / dpeak, "traffic": traffic_for(wl, dom),
             "hbm": hbm_fraction(traffic_for(wl, dom), dms / dn / 1e3),
             "avg_launch_us": 1e3 * dms / dn, "flops_per_launch": dfl / dn, "per_kernel": per_kernel,
             "whole_step": {"algorithmic_gflop": total_flops / 1e9,
                            "achieved": total_flops / (ms / args.steps / 1e3) / 1e9,
                            "frac": total_flops / (ms / args.steps / 1e3) / 1e9 / peak,
                            "note": "all kernel classes' algorithmic FP64 flops of one step over the timed step"},
-            "peak_source": "measured", "peak_measurement": fp64,
+            "peak_source": psrc, "peak_measurement": fp64 if bound == "alu" else "MEASURED_PEAKS.json bf16_tflops",
             "peak_note": "FP64 peak measured by the library's FMA-chain probe on this GPU (nominal %.0f GFLOP/s = "
                          "152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz); no tensor-core FP64 path (GB300's FP64 "
                          "tensor rate is the same). Per-class times come from one instrumented step in which "
@@ -1111,20 +1128,21 @@ def run_gpu(args, wl):
     if ws == 1 and not args.no_cpu:
         v, sample, el = wl.cpu_sample()
         model, _ = cpu_model()
-        cpu = {"value": v, "unit": "dof*steps/s", "cores": int(os.environ.get("OPENBLAS_NUM_THREADS", "1")),
+        cpu = {"value": v, "unit": getattr(wl, "unit", "dof*steps/s"), "cores": int(os.environ.get("OPENBLAS_NUM_THREADS", "1")),
                "kind": "oracle", "sample": sample, "cpu_model": model}
         if not args.no_cpu_all:
             cpu["all_cores"] = cpu_all_cores(wl)
     line = {"metric": getattr(wl, "metric", "forward+adjoint gradient dof*steps/s at 1e-10 rel vs FP64 oracle"),
             "value": value,
-            "unit": "dof*steps/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "unit": getattr(wl, "unit", "dof*steps/s"), "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic",
             "config": dict(wl.config(), parallelism="replicas%d" % ws,
-                           **({"host_checkpoint_slots": args.host_slots} if args.host_slots else {})),
+                           **({"host_checkpoint_slots": args.host_slots} if args.host_slots else {}),
+                           **({"options": args.set_option} if args.set_option else {})),
             "gpu_launches": launches,
-            "e2e": {"value": units / (e2e_ms / 1e3), "unit": "dof*steps/s", "h2d_bytes_per_step": bi,
-                    "d2h_bytes_per_step": bo},
+            "e2e": {"value": units / (e2e_ms / 1e3), "unit": getattr(wl, "unit", "dof*steps/s"),
+                    "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo},
             "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
             "adjoint_forward_ratio": {"value": adj_ratio, "forward_ms": fwd_ms,
                                       "definition": "(gradient - forward sweep) / forward sweep, same workload"}}
@@ -1254,6 +1272,8 @@ def main():
     ap.add_argument("--host-slots", type=int, default=0,
                     help="rb/couette: host checkpoint slots (two-level schedule; device slots then from --hbm-gb)")
     ap.add_argument("--hbm-gb", type=float, default=None, help="couette: device checkpoint budget in GB")
+    ap.add_argument("--set-option", action="append", default=[], metavar="K=V",
+                    help="spadj_set_option(K, V) on the workload's problem before the run (repeatable)")
     ap.add_argument("--nsteps", type=int, default=None,
                     help="override the workload's time steps, or the iterations of poiseuille_evp (profiling runs)")
     ap.add_argument("--size", default=None,

@@ -222,8 +222,9 @@ spadj_status spadj_adjoint(spadj_problem* prob, int n_steps, const double* traj,
  * caller can drive its own schedule (the problem statement's "step forward" and "step adjoint";
  * eq. imex / the RK stage equation and their adjoints eq. IMEX_adjoint / RK adjoint,
  * Supplementary A.4; eqs. 5-6, "Efficiently calculating gradients").  Defined for SPADJ_RB2D
- * (RK222, RK443), SPADJ_COUETTE3D (SBDF1, SBDF2) and SPADJ_BURGERS1D (SBDF1-4); other equation
- * sets return SPADJ_ERR_UNSUPPORTED.  Step n (n >= 0) maps X_n to X_{n+1}; with a step-size
+ * (RK222, RK443), SPADJ_COUETTE3D (SBDF1, SBDF2), SPADJ_BURGERS1D (SBDF1-4) and SPADJ_KOLMOGOROV2D
+ * (SBDF2; forward and adjoint steps, no tangent; with the closure the adjoint step adds the step's
+ * parameter cotangent to gp_accum); other equation sets return SPADJ_ERR_UNSUPPORTED.  Step n (n >= 0) maps X_n to X_{n+1}; with a step-size
  * schedule it uses dts[n], and a multistep scheme of order s uses order min(n + 1, s) as the
  * sweeps do.  All arrays are caller-owned device memory on the problem's stream; input and output
  * arrays must be distinct.  Chained from X_0, the forward and adjoint steps reproduce the sweeps
@@ -255,9 +256,10 @@ spadj_status spadj_step_tangent(spadj_problem* prob, int n, const double* s_n, c
  * The chain that gives dJ/dX_0 is the same for every scheme:
  *   y = NULL;  for n = N, N-1, ..., 0:  y = step_adjoint(n, X_n, y, dJ/dX_n);  dJ/dX_0 = y[0 : state]
  * (at n = N a Runge-Kutta step returns src; a multistep step solves for Y_N).
- * gp_accum (nullable): for problems with parameters, the step's parameter cotangent is added
- * to it; problems without parameters (all equation sets that provide the step calls) require
- * NULL and return SPADJ_ERR_INVALID otherwise. */
+ * gp_accum (nullable): for problems with parameters (SPADJ_KOLMOGOROV2D with the learned closure),
+ * the step's parameter cotangent (dF(X_n)/dp)^dagger (sum_i c_i^{n+i} Y_{n+i}) is added to it
+ * (spadj_state_len(prob, 2) doubles), so the chain accumulates dJ/dp; problems without parameters
+ * require NULL and return SPADJ_ERR_INVALID otherwise. */
 spadj_status spadj_step_adjoint(spadj_problem* prob, int n, const double* x_n, const double* y_np1,
                                 const double* src, double* y_n, double* gp_accum);
 
@@ -350,8 +352,8 @@ spadj_status spadj_objective(spadj_problem* prob, int objective, const double* o
                              double* J_dev, double* seed);
 
 /* Gradient of an objective with respect to the initial condition (eqs. 1-6):
- * forward sweep with checkpoints (ckpt_slots <= 0: store every step), objective,
- * adjoint sweep with recomputation.  J_host receives J per batch member (host
+ * forward sweep with checkpoints (ckpt_slots <= 0: store every step; the schedules per equation
+ * set are those of spadj_vjp), objective, adjoint sweep with recomputation.  J_host receives J per batch member (host
  * memory, B doubles); grad_x0 receives dJ/dX_0.  obj_data and grad_p may be NULL. */
 spadj_status spadj_gradient(spadj_problem* prob, const double* x0, int n_steps, int objective,
                             const double* obj_data, int ckpt_slots, double* J_host,
@@ -379,9 +381,13 @@ spadj_status spadj_fp64_peak(void* cuda_stream, int iters, double* gflops_host, 
 /* Vector-Jacobian product of the trajectory map (the reverse-mode building block behind
  * spadj_gradient and the torch.autograd binding): grad_x0 = sum_i (dX_{n_i}/dX_0)^T seed_i for
  * cotangents seeds[i] (device, layout [n_seeds][state]) injected at steps seed_steps[i]
- * (host ints in 0..n_steps, distinct).  The Burgers and Kolmogorov problems keep the whole
- * trajectory; SPADJ_RB2D and SPADJ_COUETTE3D use ckpt_slots binomial checkpoint slots (<= 0:
- * store every step).  This is the
+ * (host ints in 0..n_steps, distinct).  Checkpointing (as in spadj_gradient): ckpt_slots <= 0 stores
+ * every step; SPADJ_RB2D, SPADJ_COUETTE3D and SPADJ_BURGERS1D run the binomial schedule on ckpt_slots
+ * device slots (two-level with host slots, spadj_set_option 9); SPADJ_KOLMOGOROV2D keeps the restart
+ * state [X_a, X_{a-1}, F(X_{a-1})] of each of ckpt_slots segments (device memory, or page-locked host
+ * memory for the option 9 count of segments), recomputes one segment's trajectory at a time and
+ * reverses it in one persistent launch (the adjoint variables of eq. IMEX_adjoint carried from one
+ * segment's launch to the next).  This is the
  * adjoint sweep of Supplementary A.4 with the objective's partial derivatives replaced by the
  * given cotangents (4D-Var style injection at intermediate steps included). */
 spadj_status spadj_vjp(spadj_problem* prob, const double* x0, int n_steps, int ckpt_slots, int n_seeds,

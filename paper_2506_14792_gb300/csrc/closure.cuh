@@ -53,6 +53,26 @@ __global__ void quantize_kernel(const double* __restrict__ g, __nv_bfloat16* __r
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) x[i] = __float2bfloat16_rn((float)g[i]);
 }
 
+// acc + sum_c x[c] w[c] over 32 BF16 channels (both 16-byte aligned; either may be in global or
+// shared memory, so the loads are generic), FP32 products and sums in channel order
+__device__ __forceinline__ float dot32_bf16(const __nv_bfloat16* x, const __nv_bfloat16* w, float acc) {
+  const uint4* xv = reinterpret_cast<const uint4*>(x);
+  const uint4* wv = reinterpret_cast<const uint4*>(w);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const uint4 a = xv[j], b = wv[j];
+    const unsigned au[4] = {a.x, a.y, a.z, a.w}, bu[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const float2 af = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&au[k]));
+      const float2 bf = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&bu[k]));
+      acc = fmaf(bf.x, af.x, acc);
+      acc = fmaf(bf.y, af.y, acc);
+    }
+  }
+  return acc;
+}
+
 // forward of layer l for `nb` members of an M x M grid (member stride M*M pixels):
 // z = conv(in) + b; hidden layers store h = bf16(tanh z) and dact = 1 - tanh^2 (if non-null);
 // the last layer writes the FP64 output.
@@ -77,7 +97,8 @@ __global__ void fwd_kernel(int l, int M, int nb, const __nv_bfloat16* __restrict
         const int ys = (y + b - 1 + M) % M;
         const __nv_bfloat16* src = in + (mb * P + (long long)ys * M + xs) * ci;
         const __nv_bfloat16* w = W + ((o * 3 + a) * 3 + b) * ci;
-        for (int c = 0; c < ci; ++c) acc = fmaf(__bfloat162float(w[c]), __bfloat162float(src[c]), acc);
+        if (ci == kHid) acc = dot32_bf16(src, w, acc);
+        else acc = fmaf(__bfloat162float(w[0]), __bfloat162float(src[0]), acc);
       }
     }
     if (l < kLayers - 1) {
@@ -105,6 +126,12 @@ __global__ void dgrad_kernel(int l, int M, int nb, const __nv_bfloat16* __restri
   const long long P = (long long)M * M;
   const long long total = P * nb * ci;
   const __nv_bfloat16* W = wq + w_off(l);
+  // for ci = 1 the weights of a tap, W[o][0][a][b] over o, as a contiguous 32-vector
+  __shared__ __align__(16) __nv_bfloat16 wt[9 * kHid];
+  if (ci == 1) {
+    for (int i = threadIdx.x; i < 9 * co; i += blockDim.x) wt[i] = W[(i % co) * 9 + i / co];
+    __syncthreads();
+  }
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
     const int c = (int)(t % ci);
     const long long pix = t / ci;
@@ -117,8 +144,12 @@ __global__ void dgrad_kernel(int l, int M, int nb, const __nv_bfloat16* __restri
       for (int b = 0; b < 3; ++b) {
         const int ys = (y - b + 1 + M) % M;
         const __nv_bfloat16* src = dz + (mb * P + (long long)ys * M + xs) * co;
-        for (int o = 0; o < co; ++o)
-          acc = fmaf(__bfloat162float(W[((o * 3 + a) * 3 + b) * ci + c]), __bfloat162float(src[o]), acc);
+        if (ci == 1 && co == kHid) {
+          acc = dot32_bf16(src, wt + (a * 3 + b) * kHid, acc);
+        } else {
+          for (int o = 0; o < co; ++o)
+            acc = fmaf(__bfloat162float(W[((o * 3 + a) * 3 + b) * ci + c]), __bfloat162float(src[o]), acc);
+        }
       }
     }
     if (dout) dout[pix] = (double)acc;
@@ -126,46 +157,57 @@ __global__ void dgrad_kernel(int l, int M, int nb, const __nv_bfloat16* __restri
   }
 }
 
-// weight gradient of layer l for each member: part[mb][w_off(l) + r] (flat FP64-vector order),
-// dW[o,c,a,b] = sum_pixels in[c](x + a - 1, y + b - 1) dz[o](x, y), db[o] = sum dz[o].
-// One CTA per (member, o, a, b) plus one per (member, o) for the bias; fixed reduction order.
-__global__ void wgrad_kernel(int l, int M, const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict__ dz,
-                             float* __restrict__ part, int npar) {
+// weight gradient of a thin layer (l = 0: 1 -> 32, l = 3: 32 -> 1) for each member:
+// part[mb][w_off(l) + r] (flat FP64-vector order), dW[o,c,a,b] = sum_pixels in[c](x + a - 1, y + b - 1)
+// dz[o](x, y), db[o] = sum dz[o].  One CTA per (member, tap) plus one per member for the bias; thread
+// t = (pixel lane t / 32, wide channel w = t % 32), the wide channel being o for layer 0 and c for
+// layer 3, so the reads of the 32-channel tensor are coalesced; the pixel lanes' partial sums are
+// reduced in shared memory in a fixed order.
+__global__ void __launch_bounds__(256) wgrad_kernel(int l, int M, const __nv_bfloat16* __restrict__ in,
+                                                    const __nv_bfloat16* __restrict__ dz, float* __restrict__ part,
+                                                    int npar) {
   const int ci = (l == 0) ? 1 : kHid, co = (l == kLayers - 1) ? 1 : kHid;
   const long long P = (long long)M * M;
-  const int mb = blockIdx.y;
-  const int item = blockIdx.x;  // 0 .. co*9 - 1: weights; co*9 .. co*10 - 1: biases
+  const int mb = blockIdx.y, item = blockIdx.x;  // 0..8: taps, 9: bias
+  const int w = threadIdx.x & 31, lane = threadIdx.x >> 5, nl = blockDim.x >> 5;
   __shared__ float red[256];
   float* dst = part + (long long)mb * npar + w_off(l);
-  if (item < co * 9) {
-    const int o = item / 9, a = (item % 9) / 3, b = item % 3;
-    // thread t owns channel c = t % ci and a strided share of the pixels
-    const int c = threadIdx.x % ci, lane = threadIdx.x / ci, nl = blockDim.x / ci;
-    float acc = 0.0f;
+  const __nv_bfloat16* inm = in + (long long)mb * P * ci;
+  const __nv_bfloat16* dzm = dz + (long long)mb * P * co;
+  float acc = 0.0f;
+  if (item < 9) {
+    const int a = item / 3, b = item % 3;
     for (long long pp = lane; pp < P; pp += nl) {
-      const int y = (int)(pp / M), x = (int)(pp % M);
+      const int y = (int)(pp / M), x = (int)(pp - (long long)y * M);
       const int xs = (x + a - 1 + M) % M, ys = (y + b - 1 + M) % M;
-      const float iv = __bfloat162float(in[((long long)mb * P + (long long)ys * M + xs) * ci + c]);
-      const float dv = __bfloat162float(dz[((long long)mb * P + pp) * co + o]);
+      const long long sp = (long long)ys * M + xs;
+      const float iv = __bfloat162float(ci == 1 ? inm[sp] : inm[sp * ci + w]);
+      const float dv = __bfloat162float(co == 1 ? dzm[pp] : dzm[pp * co + w]);
       acc = fmaf(iv, dv, acc);
     }
-    red[threadIdx.x] = acc;
-    __syncthreads();
-    if (threadIdx.x < ci) {
-      float s = 0.0f;
-      for (int k = 0; k < nl; ++k) s += red[k * ci + threadIdx.x];
-      dst[((o * ci + threadIdx.x) * 3 + a) * 3 + b] = s;
-    }
-  } else {
-    const int o = item - co * 9;
-    float acc = 0.0f;
-    for (long long pp = threadIdx.x; pp < P; pp += blockDim.x) acc += __bfloat162float(dz[((long long)mb * P + pp) * co + o]);
-    red[threadIdx.x] = acc;
-    __syncthreads();
+  } else if (co > 1) {  // bias of layer 0: db[o = w]
+    for (long long pp = lane; pp < P; pp += nl) acc += __bfloat162float(dzm[pp * co + w]);
+  } else {  // bias of layer 3: every thread takes a strided share of the pixels
+    for (long long pp = threadIdx.x; pp < P; pp += blockDim.x) acc += __bfloat162float(dzm[pp]);
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  if (item == 9 && co == 1) {
     if (threadIdx.x == 0) {
       float s = 0.0f;
       for (int k = 0; k < (int)blockDim.x; ++k) s += red[k];
-      dst[co * ci * 9 + o] = s;
+      dst[co * ci * 9] = s;
+    }
+    return;
+  }
+  if (threadIdx.x < 32) {
+    float s = 0.0f;
+    for (int k = 0; k < nl; ++k) s += red[k * 32 + w];
+    if (item == 9) {
+      dst[co * ci * 9 + w] = s;
+    } else {
+      const int o = (co == 1) ? 0 : w, c = (ci == 1) ? 0 : w;
+      dst[((o * ci + c) * 3 + item / 3) * 3 + item % 3] = s;
     }
   }
 }

@@ -65,7 +65,16 @@ struct KolArgs {
   int adjoint;      // 0 forward, 1 adjoint
   int fonly;        // forward: stage-0 F evaluation only (writes F(x0) to out)
   int nstage;       // number of stages in this launch
-  int S;            // n_steps
+  int S;            // n_steps of the sweep (adjoint: the horizon N, which fixes the weights and the seed)
+  // Segments (checkpointed sweeps).  Forward: stage s is step n0 + s (x0 = X_{n0}, with X_{n0-1} and
+  // F(X_{n0-1}) preset in the rings when n0 >= 1), traj (nullable) holds the launch's states relative
+  // to n0.  Adjoint: stage k processes index n0 - k; prologue = 1: stage 0 only forms the transforms
+  // of W_{n0-1} from Y_{n0}, Y_{n0+1} in the Y ring (the second half of index n0, whose first half ran
+  // in the previous launch); lo: lowest index of the launch (its second half is skipped when lo > 0),
+  // traj holds X_lo .. (relative to lo).
+  int n0;
+  int prologue;
+  int lo;
   int forcing, nonlinear;
   const double2* x0;
   double2* Xr[2];
@@ -151,6 +160,8 @@ struct KSmem {
 __device__ void ca_forward(const KolArgs& A, const KMember& m, int tile, int s) {
   extern __shared__ double2 ks[];
   const int N = m.N, Kx = m.Kx, M = m.M;
+  const int n = A.n0 + s;           // absolute step of this stage
+  const int last = A.nstage - 1;    // the launch's last stage
   const KRes& R = A.res[m.res];
   double2* ca = ks;          // M
   double2* cb = ca + M;      // M
@@ -168,7 +179,7 @@ __device__ void ca_forward(const KolArgs& A, const KMember& m, int tile, int s) 
         for (int j = threadIdx.x; j < M; j += blockDim.x) ca[j] = ldcg2(&A.mixB[0][m.off_mix + (long long)j * Kx + kx]);
         r = col_fft<-1>(ca, cb, R);
       }
-      const Coef c = kcoef(s, A.kc);
+      const Coef c = kcoef(n, A.kc);
       const double invM = 1.0 / M;
       for (int q = threadIdx.x; q < N; q += blockDim.x) {
         const int idx = yidx(q, N, M);
@@ -180,15 +191,15 @@ __device__ void ca_forward(const KolArgs& A, const KMember& m, int tile, int s) 
           A.out[col + q] = F;
           continue;
         }
-        const double2 X1 = ldcg2(&A.Xr[(s - 1) & 1][col + q]);
+        const double2 X1 = ldcg2(&A.Xr[(n - 1) & 1][col + q]);
         double2 num = make_double2(c.c1 * F.x - c.a1 * X1.x, c.c1 * F.y - c.a1 * X1.y);
-        if (s >= 2) {
-          const double2 X2 = ldcg2(&A.Xr[s & 1][col + q]);
-          const double2 F2 = ldcg2(&A.Fr[s & 1][col + q]);
+        if (n >= 2) {
+          const double2 X2 = ldcg2(&A.Xr[n & 1][col + q]);
+          const double2 F2 = ldcg2(&A.Fr[n & 1][col + q]);
           num.x += c.c2 * F2.x - c.a2 * X2.x;
           num.y += c.c2 * F2.y - c.a2 * X2.y;
         }
-        A.Fr[(s - 1) & 1][col + q] = F;
+        A.Fr[(n - 1) & 1][col + q] = F;
         const double inv = 1.0 / (c.a0 + ((double)kx * kx + ky * ky) * A.invRe);
         xc[q] = make_double2(num.x * inv, num.y * inv);
       }
@@ -197,16 +208,16 @@ __device__ void ca_forward(const KolArgs& A, const KMember& m, int tile, int s) 
       project_col(xc, N, kx);
     }
     for (int q = threadIdx.x; q < N; q += blockDim.x) {
-      A.Xr[s & 1][col + q] = xc[q];
+      A.Xr[n & 1][col + q] = xc[q];
       if (A.traj) A.traj[(long long)s * S + col + q] = xc[q];
-      if (s == A.S) A.out[col + q] = xc[q];
+      if (s == last) A.out[col + q] = xc[q];
     }
-    if (s < A.S && (A.nonlinear || A.closure)) {
+    if (s < last && (A.nonlinear || A.closure)) {
       // the fields' inverse y transforms two at a time, sharing their passes: set p at
       // ks + 2 p M (scratch + M); the column is read back from the state just written, its
       // shared slot being reused
       const int nf = A.closure ? 5 : 4;
-      const double2* xs = A.Xr[s & 1] + col;
+      const double2* xs = A.Xr[n & 1] + col;
       for (int f0 = 0; f0 < nf; f0 += 2) {
         const int np = min(2, nf - f0);
         __syncthreads();
@@ -336,7 +347,9 @@ __device__ void b_forward(const KolArgs& A, const KMember& m, int tile) {
 }
 
 // ---- adjoint C'A' tile ------------------------------------------------------------------------
-__device__ void ca_adjoint(const KolArgs& A, const KMember& m, int tile, int n) {
+// first: the first half (finish the VJP at X_n, inject the cotangent, solve for Y_n); otherwise Y_n is
+// read from the Y ring.  second: the second half (W_{n-1} and the fields of X_{n-1} for the next VJP).
+__device__ void ca_adjoint(const KolArgs& A, const KMember& m, int tile, int n, bool first, bool second) {
   extern __shared__ double2 ks[];
   const int N = m.N, Kx = m.Kx, M = m.M;
   const KRes& R = A.res[m.res];
@@ -352,6 +365,10 @@ __device__ void ca_adjoint(const KolArgs& A, const KMember& m, int tile, int n) 
   const int SN = A.S;
   for (int kx = kx0; kx < kx1; ++kx) {
     const long long col = m.off_state + (long long)kx * N;
+    if (!first) {  // Y_n from the ring (computed by the previous launch)
+      for (int q = threadIdx.x; q < N; q += blockDim.x) yc[q] = ldcg2(&A.Yr[n & 1][col + q]);
+      __syncthreads();
+    } else {
     for (int q = threadIdx.x; q < N; q += blockDim.x) lam[q] = make_double2(0.0, 0.0);
     __syncthreads();
     if (n < SN && (A.nonlinear || A.closure)) {
@@ -422,6 +439,12 @@ __device__ void ca_adjoint(const KolArgs& A, const KMember& m, int tile, int n) 
       yc[q] = make_double2(lam[q].x * inv, lam[q].y * inv);
     }
     __syncthreads();
+    }  // first half
+    if (!second) {  // the launch ends at Y_n: store it for the next launch
+      for (int q = threadIdx.x; q < N; q += blockDim.x) A.Yr[n & 1][col + q] = yc[q];
+      __syncthreads();
+      continue;
+    }
     // W_{n-1} = c1^n Y_n + c2^{n+1} Y_{n+1}, read Y_{n+1} before Y_n overwrites Y_{n+2}
     const Coef cw1 = kcoef(n, A.kc);
     const Coef cw2 = (n + 1 <= SN) ? kcoef(n + 1, A.kc) : Coef{0, 0, 0, 0, 0};
@@ -451,7 +474,7 @@ __device__ void ca_adjoint(const KolArgs& A, const KMember& m, int tile, int n) 
     }
     // fields of X_{n-1} from the trajectory, their inverse y transforms two at a time (sets at
     // ks + 2 p M, scratch + M; 4M <= the CTA's shared memory for every member)
-    const double2* xs = A.traj + (long long)(n - 1) * S + col;
+    const double2* xs = A.traj + (long long)(n - 1 - A.lo) * S + col;
     const int fa = A.nonlinear ? 0 : 4, fb = A.closure ? 5 : 4;
     for (int f0 = fa; f0 < fb; f0 += 2) {
       const int np = min(2, fb - f0);
@@ -548,8 +571,8 @@ __device__ void run_item(const KolArgs& A, int stage, bool isCA, int b, int tile
     if (isCA) ca_forward(A, m, tile, stage);
     else b_forward(A, m, tile);
   } else {
-    const int n = A.S - stage;
-    if (isCA) ca_adjoint(A, m, tile, n);
+    const int n = A.n0 - stage;
+    if (isCA) ca_adjoint(A, m, tile, n, !(A.prologue && stage == 0), !(A.lo > 0 && n == A.lo));
     else b_adjoint(A, m, tile);
   }
 }
@@ -680,6 +703,11 @@ __global__ void sum_rows_kernel(const double* partial, int n_obs, int nmem, doub
   double s = 0.0;
   for (int o = 0; o < n_obs; ++o) s += partial[(long long)b * n_obs + o];
   J[b] = s;
+}
+
+// y += x (n values)
+__global__ void add_kernel(double* __restrict__ y, const double* __restrict__ x, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) y[i] += x[i];
 }
 
 // ---- training support for the learned closure -------------------------------------------------
@@ -1033,6 +1061,7 @@ struct Kol : EqImpl {
     A.adjoint = 1;
     A.nstage = n_steps + 1;
     A.S = n_steps;
+    A.n0 = n_steps;
     A.traj = traj;
     A.out = reinterpret_cast<double2*>(grad);
     A.seed_at = seedmap.as<int>();
@@ -1041,6 +1070,196 @@ struct Kol : EqImpl {
     if (s != SPADJ_OK) return s;
     return persistent ? check_err(p) : cudaStreamSynchronize(p->stream) == cudaSuccess ? SPADJ_OK
                                                                                        : p->fail(SPADJ_ERR_CUDA, "sync");
+  }
+
+  // ---- segments: checkpointed sweeps and the step entry points ----------------------------------
+  // Restart state of step n (three states, the augmented state of the two-step scheme):
+  // [X_n, X_{n-1}, F(X_{n-1})]; for n = 0 only X_0 is read.
+  size_t sbytes() const { return sizeof(double2) * (size_t)state_size; }
+
+  // k steps n0 -> n0 + k from the restart state rs (device); traj (nullable): X_{n0}..X_{n0+k};
+  // x_out: X_{n0+k}; rs_out (nullable, may equal rs): the restart state of n0 + k
+  spadj_status run_forward_seg(Problem* p, int n0, int k, const double2* rs, double2* traj, double2* x_out,
+                               double2* rs_out) {
+    const size_t sb = sbytes();
+    const long long S = state_size;
+    if (n0 >= 1) {
+      SPADJ_CUDA_TRY(p, cudaMemcpyAsync(Xr[(n0 - 1) & 1].ptr, rs + S, sb, cudaMemcpyDeviceToDevice, p->stream));
+      SPADJ_CUDA_TRY(p, cudaMemcpyAsync(Fr[(n0 - 1) & 1].ptr, rs + 2 * S, sb, cudaMemcpyDeviceToDevice, p->stream));
+    }
+    SPADJ_CUDA_TRY(p, segx0.ensure(sb));
+    SPADJ_CUDA_TRY(p, cudaMemcpyAsync(segx0.ptr, rs, sb, cudaMemcpyDeviceToDevice, p->stream));
+    KolArgs A = base_args();
+    A.adjoint = 0;
+    A.nstage = k + 1;
+    A.S = k;
+    A.n0 = n0;
+    A.x0 = segx0.as<double2>();
+    A.traj = traj;
+    A.out = x_out;
+    spadj_status st = launch(p, A);
+    if (st != SPADJ_OK) return st;
+    if (persistent && (st = check_err(p)) != SPADJ_OK) return st;
+    if (rs_out && k >= 1) {
+      const int n1 = n0 + k;
+      if (rs_out != x_out) SPADJ_CUDA_TRY(p, cudaMemcpyAsync(rs_out, x_out, sb, cudaMemcpyDeviceToDevice, p->stream));
+      SPADJ_CUDA_TRY(p, cudaMemcpyAsync(rs_out + S, Xr[(n1 - 1) & 1].ptr, sb, cudaMemcpyDeviceToDevice, p->stream));
+      SPADJ_CUDA_TRY(p, cudaMemcpyAsync(rs_out + 2 * S, Fr[(n1 - 1) & 1].ptr, sb, cudaMemcpyDeviceToDevice, p->stream));
+    }
+    return SPADJ_OK;
+  }
+
+  // adjoint indices hi .. lo of a horizon N over the segment trajectory seg = X_lo .. X_hi (prologue at
+  // hi + 1 when hi < N: the adjoint variables Y_{hi+1}, Y_{hi+2} are in the Y ring); horizon = N for
+  // the weights and the seed (or larger in step mode).  grad (nullable unless lo = 0) receives dJ/dX_0.
+  spadj_status run_adjoint_seg(Problem* p, int N, int lo, int hi, const double2* seg, const int* seedmap_dev,
+                               const double2* seeds, double* grad, int horizon) {
+    KolArgs A = base_args();
+    A.adjoint = 1;
+    A.S = horizon;
+    A.prologue = hi < N ? 1 : 0;
+    A.n0 = hi + A.prologue;
+    A.lo = lo;
+    A.nstage = hi - lo + 1 + A.prologue;
+    A.traj = const_cast<double2*>(seg);
+    A.out = reinterpret_cast<double2*>(grad);
+    A.seed_at = seedmap_dev;
+    A.seeds = seeds;
+    spadj_status st = launch(p, A);
+    if (st != SPADJ_OK) return st;
+    return persistent ? check_err(p) : SPADJ_OK;
+  }
+
+  // Checkpointed reverse sweep: H segments of K = ceil(N / H) steps; the restart state at each segment
+  // start is kept (device slots, or page-locked host slots with host = true); each segment's
+  // trajectory (K + 1 states) is recomputed before it is reversed, last segment first, and the
+  // adjoint variables pass from one segment's launch to the next through the Y ring.  Observation
+  // states (4D-Var) are kept from the first forward sweep.  seed_at[n] indexes seeds (device) for the
+  // cotangent injected at X_n (objective_kind < 0), or the objective's seeds are formed here.
+  DevBuf segx0, segbuf, rsbuf, cslots, obsstates, obsidx;
+  HostBuf hcslots;
+  spadj_status reverse_seg(Problem* p, const double* x0, int N, int H, bool host, bool objective,
+                           const std::vector<int>& seed_at_in, const double2* seeds_in, double* grad, double* J_host) {
+    H = std::max(1, std::min(H, N));
+    const int K = (N + H - 1) / H;
+    H = (N + K - 1) / K;
+    const size_t sb = sbytes();
+    const long long S = state_size;
+    SPADJ_CUDA_TRY(p, segbuf.ensure(sb * (size_t)(K + 1)));
+    SPADJ_CUDA_TRY(p, rsbuf.ensure(3 * sb));
+    if (host) SPADJ_CUDA_TRY(p, hcslots.ensure(3 * sb * (size_t)H));
+    else SPADJ_CUDA_TRY(p, cslots.ensure(3 * sb * (size_t)H));
+    auto slot = [&](int j) {
+      return host ? hcslots.as<char>() + (size_t)j * 3 * sb : cslots.as<char>() + (size_t)j * 3 * sb;
+    };
+    const cudaMemcpyKind to_slot = host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    const cudaMemcpyKind from_slot = host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    double2* rs = rsbuf.as<double2>();
+    double2* seg = segbuf.as<double2>();
+    std::vector<int> seed_at = seed_at_in;
+    const double2* seeds = seeds_in;
+    if (objective) {
+      SPADJ_CUDA_TRY(p, obsstates.ensure(sb * (size_t)n_obs));
+      SPADJ_CUDA_TRY(p, obsidx.ensure(sizeof(int) * (size_t)n_obs));
+      std::vector<int> idx(n_obs);
+      for (int i = 0; i < n_obs; ++i) idx[i] = i;
+      SPADJ_CUDA_TRY(p, cudaMemcpyAsync(obsidx.ptr, idx.data(), sizeof(int) * n_obs, cudaMemcpyHostToDevice, p->stream));
+      SPADJ_CUDA_TRY(p, cudaStreamSynchronize(p->stream));
+    }
+    // first forward sweep: segment starts into the slots, observation states kept
+    SPADJ_CUDA_TRY(p, cudaMemsetAsync(rs, 0, 3 * sb, p->stream));
+    SPADJ_CUDA_TRY(p, cudaMemcpyAsync(rs, x0, sb, cudaMemcpyDeviceToDevice, p->stream));
+    for (int j = 0; j < H; ++j) {
+      const int a = j * K, b = std::min(N, a + K);
+      SPADJ_CUDA_TRY(p, cudaMemcpyAsync(slot(j), rs, 3 * sb, to_slot, p->stream));
+      spadj_status st = run_forward_seg(p, a, b - a, rs, objective ? seg : nullptr, tmp.as<double2>(), rs);
+      if (st != SPADJ_OK) return st;
+      if (objective)
+        for (int i = 0; i < n_obs; ++i)
+          if (obs_steps_h[i] > a && obs_steps_h[i] <= b)
+            SPADJ_CUDA_TRY(p, cudaMemcpyAsync(obsstates.as<double2>() + (size_t)i * S, seg + (size_t)(obs_steps_h[i] - a) * S,
+                                              sb, cudaMemcpyDeviceToDevice, p->stream));
+    }
+    if (objective) {
+      SPADJ_CUDA_TRY(p, seedbuf.ensure(sb * (size_t)n_obs));
+      SPADJ_CUDA_TRY(p, partial.ensure(sizeof(double) * (size_t)nmem * n_obs));
+      SPADJ_CUDA_TRY(p, Jd.ensure(sizeof(double) * nmem));
+      cudaEvent_t t = p->tic();
+      fourdvar_kernel<<<dim3(nmem, n_obs), kKolThreads, 0, p->stream>>>(dmem.as<KMember>(), obsstates.as<double2>(),
+                                                                        obsidx.as<int>(), obsbuf.as<double2>(), S,
+                                                                        obs_kmax, seedbuf.as<double2>(),
+                                                                        partial.as<double>(), n_obs);
+      sum_rows_kernel<<<(nmem + 127) / 128, 128, 0, p->stream>>>(partial.as<double>(), n_obs, nmem, Jd.as<double>());
+      p->toc(t, KC_OBJECTIVE, 4.0 * state_size * n_obs);
+      spadj_status st = check_launch(p, "kolmogorov 4dvar");
+      if (st != SPADJ_OK) return st;
+      seed_at.assign(N + 1, -1);
+      for (int i = 0; i < n_obs; ++i) seed_at[obs_steps_h[i]] = i;
+      seeds = seedbuf.as<double2>();
+    }
+    SPADJ_CUDA_TRY(p, seedmap.ensure(sizeof(int) * (N + 1)));
+    SPADJ_CUDA_TRY(p, cudaMemcpyAsync(seedmap.ptr, seed_at.data(), sizeof(int) * (N + 1), cudaMemcpyHostToDevice, p->stream));
+    // reverse, last segment first
+    for (int j = H - 1; j >= 0; --j) {
+      const int a = j * K, b = std::min(N, a + K);
+      SPADJ_CUDA_TRY(p, cudaMemcpyAsync(rs, slot(j), 3 * sb, from_slot, p->stream));
+      spadj_status st = run_forward_seg(p, a, b - a, rs, seg, tmp.as<double2>(), nullptr);
+      if (st != SPADJ_OK) return st;
+      const int hi = (b == N) ? N : b - 1;
+      if ((st = run_adjoint_seg(p, N, a, hi, seg, seedmap.as<int>(), seeds, grad, N)) != SPADJ_OK) return st;
+    }
+    SPADJ_CUDA_TRY(p, cudaStreamSynchronize(p->stream));  // host staging (seed map, host slots)
+    if (objective && J_host) {
+      SPADJ_CUDA_TRY(p, cudaMemcpy(J_host, Jd.ptr, sizeof(double) * nmem, cudaMemcpyDeviceToHost));
+    }
+    return SPADJ_OK;
+  }
+
+  int step_blocks(int which) const override { return which == 0 ? 3 : 2; }
+
+  spadj_status step_forward(Problem* p, int n, const double* s_n, double* s_np1) override {
+    if (n < 0) return p->fail(SPADJ_ERR_INVALID, "step: n < 0");
+    SPADJ_CUDA_TRY(p, rsbuf.ensure(3 * sbytes()));
+    SPADJ_CUDA_TRY(p, segbuf.ensure(2 * sbytes()));
+    double2* out = reinterpret_cast<double2*>(s_np1);
+    return run_forward_seg(p, n, 1, reinterpret_cast<const double2*>(s_n), nullptr, out, out);
+  }
+
+  // adjoint state [Y_n, Y_{n+1}] (eq. IMEX_adjoint), kept in the Y ring during the call
+  spadj_status step_adjoint(Problem* p, int n, const double* x_n, const double* y_np1, const double* src, double* y_n,
+                            double* gp_accum) override {
+    if (n < 0) return p->fail(SPADJ_ERR_INVALID, "step: n < 0");
+    if (gp_accum && !closure) return p->fail(SPADJ_ERR_INVALID, "step_adjoint: gp_accum but the problem has no parameters");
+    const size_t sb = sbytes();
+    const long long S = state_size;
+    const double2* yin = reinterpret_cast<const double2*>(y_np1);
+    double2* yout = reinterpret_cast<double2*>(y_n);
+    // the seed map for index n: src (if any) as seed 0
+    std::vector<int> sm(n + 1, -1);
+    if (src) sm[n] = 0;
+    SPADJ_CUDA_TRY(p, seedmap.ensure(sizeof(int) * (n + 1)));
+    SPADJ_CUDA_TRY(p, cudaMemcpyAsync(seedmap.ptr, sm.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, p->stream));
+    if (closure && gp_accum) SPADJ_CUDA_TRY(p, cudaMemsetAsync(gp.ptr, 0, sizeof(double) * cnn::n_params(), p->stream));
+    spadj_status st;
+    if (!yin) {  // the seed step: no later adjoint variables, no vector-Jacobian product
+      for (int i = 0; i < 2; ++i) SPADJ_CUDA_TRY(p, cudaMemsetAsync(Yr[i].ptr, 0, sb, p->stream));
+      st = run_adjoint_seg(p, n, n, n, reinterpret_cast<const double2*>(x_n), seedmap.as<int>(),
+                           reinterpret_cast<const double2*>(src), n == 0 ? y_n : nullptr, n);
+    } else {
+      SPADJ_CUDA_TRY(p, cudaMemcpyAsync(Yr[(n + 1) & 1].ptr, yin, sb, cudaMemcpyDeviceToDevice, p->stream));
+      SPADJ_CUDA_TRY(p, cudaMemcpyAsync(Yr[n & 1].ptr, yin + S, sb, cudaMemcpyDeviceToDevice, p->stream));
+      st = run_adjoint_seg(p, 1 << 29, n, n, reinterpret_cast<const double2*>(x_n), seedmap.as<int>(),
+                           reinterpret_cast<const double2*>(src), n == 0 ? y_n : nullptr, 1 << 29);
+    }
+    if (st != SPADJ_OK) return st;
+    if (n >= 1) SPADJ_CUDA_TRY(p, cudaMemcpyAsync(yout, Yr[n & 1].ptr, sb, cudaMemcpyDeviceToDevice, p->stream));
+    SPADJ_CUDA_TRY(p, cudaMemcpyAsync(yout + S, yin ? Yr[(n + 1) & 1].ptr : Yr[(n + 1) & 1].ptr, sb,
+                                      cudaMemcpyDeviceToDevice, p->stream));
+    if (closure && gp_accum) {
+      add_kernel<<<64, 256, 0, p->stream>>>(gp_accum, gp.as<double>(), cnn::n_params());
+      if ((st = check_launch(p, "gp accumulate")) != SPADJ_OK) return st;
+    }
+    return cudaStreamSynchronize(p->stream) == cudaSuccess ? SPADJ_OK : p->fail(SPADJ_ERR_CUDA, "sync");
   }
 
   // ---- learned closure ---------------------------------------------------------------------
@@ -1139,8 +1358,7 @@ struct Kol : EqImpl {
         cnn::bgrad32_kernel<<<dim3(32, nb), 256, 0, p->stream>>>(l, M, dz.as<__nv_bfloat16>(), part.as<float>(), np);
         conv32(p, l, 1, dz.as<__nv_bfloat16>(), nullptr, nullptr, dh.as<float>());
       } else {
-        cnn::wgrad_kernel<<<dim3(co * 10, nb), 256, 0, p->stream>>>(l, M, ins[l], dz.as<__nv_bfloat16>(), part.as<float>(),
-                                                                    np);
+        cnn::wgrad_kernel<<<dim3(10, nb), 256, 0, p->stream>>>(l, M, ins[l], dz.as<__nv_bfloat16>(), part.as<float>(), np);
         cnn::dgrad_kernel<<<cnn_grid(P * ci), 256, 0, p->stream>>>(l, M, nb, dz.as<__nv_bfloat16>(),
                                                                     wq.as<__nv_bfloat16>(), l > 0 ? dh.as<float>() : nullptr,
                                                                     l == 0 ? corr.as<double>() : nullptr);
@@ -1234,8 +1452,21 @@ struct Kol : EqImpl {
     return SPADJ_OK;
   }
 
-  spadj_status vjp(Problem* p, const double* x0, int n_steps, int, const std::vector<int>& seed_at,
+  // checkpointed sweeps: ckpt_slots in 1..n_steps-1 segments with device-resident starts, or the
+  // host slots of spadj_set_option 9 (page-locked segment starts)
+  bool segmented(Problem* p, int n_steps, int ckpt_slots) const {
+    return p->host_slots > 0 || (ckpt_slots > 0 && ckpt_slots < n_steps);
+  }
+
+  spadj_status vjp(Problem* p, const double* x0, int n_steps, int ckpt_slots, const std::vector<int>& seed_at,
                    const double* seeds, double* grad) override {
+    if (n_steps < 1) return p->fail(SPADJ_ERR_INVALID, "vjp: n_steps < 1");
+    if (segmented(p, n_steps, ckpt_slots)) {
+      if (closure) SPADJ_CUDA_TRY(p, cudaMemsetAsync(gp.ptr, 0, sizeof(double) * cnn::n_params(), p->stream));
+      const bool host = p->host_slots > 0;
+      return reverse_seg(p, x0, n_steps, host ? p->host_slots : ckpt_slots, host, false, seed_at,
+                         reinterpret_cast<const double2*>(seeds), grad, nullptr);
+    }
     spadj_status s = ensure_traj(p, n_steps);
     if (s != SPADJ_OK) return s;
     if ((s = run_forward(p, n_steps, x0, tmp.as<double>(), trajbuf.as<double2>())) != SPADJ_OK) return s;
@@ -1263,11 +1494,31 @@ struct Kol : EqImpl {
     return p->fail(SPADJ_ERR_UNSUPPORTED, "kolmogorov: the 4D-Var objective is evaluated inside spadj_gradient");
   }
 
-  spadj_status gradient(Problem* p, const double* x0, int n_steps, int objective_kind, const double*, int,
+  spadj_status gradient(Problem* p, const double* x0, int n_steps, int objective_kind, const double*, int ckpt_slots,
                         double* J_host, double* grad, double* grad_p) override {
     if (objective_kind != SPADJ_OBJ_FOURDVAR) return p->fail(SPADJ_ERR_UNSUPPORTED, "kolmogorov: objective must be FOURDVAR");
     if (n_obs < 1) return p->fail(SPADJ_ERR_INVALID, "kolmogorov: call spadj_set_observations first");
     if (obs_steps_h.back() > n_steps) return p->fail(SPADJ_ERR_INVALID, "kolmogorov: observation step beyond n_steps");
+    if (grad_p && !closure) return p->fail(SPADJ_ERR_INVALID, "gradient: grad_p requested but the problem has no parameters");
+    if (segmented(p, n_steps, ckpt_slots)) {
+      if (closure) SPADJ_CUDA_TRY(p, cudaMemsetAsync(gp.ptr, 0, sizeof(double) * cnn::n_params(), p->stream));
+      const bool host = p->host_slots > 0;
+      std::vector<double> Jl(nmem, 0.0);
+      spadj_status s = reverse_seg(p, x0, n_steps, host ? p->host_slots : ckpt_slots, host, true, {}, nullptr, grad,
+                                   Jl.data());
+      if (s != SPADJ_OK) return s;
+      if (grad_p)
+        SPADJ_CUDA_TRY(p, cudaMemcpyAsync(grad_p, gp.ptr, sizeof(double) * cnn::n_params(), cudaMemcpyDeviceToDevice,
+                                          p->stream));
+      if (closure && J_host && (s = check_cnn(p)) != SPADJ_OK) return s;
+      if (J_host) {
+        for (int b = 0; b < nmem; ++b) {
+          J_host[b] = Jl[b];
+          if (!std::isfinite(J_host[b])) return p->fail(SPADJ_ERR_NONFINITE, "kolmogorov: objective is not finite");
+        }
+      }
+      return SPADJ_OK;
+    }
     spadj_status s = ensure_traj(p, n_steps);
     if (s != SPADJ_OK) return s;
     if ((s = run_forward(p, n_steps, x0, tmp.as<double>(), trajbuf.as<double2>())) != SPADJ_OK) return s;
@@ -1371,8 +1622,10 @@ struct Kol : EqImpl {
                       &pbuf, &wq, &bq, &part, &gp, &chunkbuf})
       b->release();
     for (DevBuf* b : {&dmem, &tables, &Xr[0], &Xr[1], &Fr[0], &Fr[1], &Yr[0], &Yr[1], &mixA, &mixB, &ctr, &trajbuf,
-                      &seedbuf, &seedmap, &obsbuf, &obsteps, &partial, &Jd, &tmp})
+                      &seedbuf, &seedmap, &obsbuf, &obsteps, &partial, &Jd, &tmp, &segx0, &segbuf, &rsbuf, &cslots,
+                      &obsstates, &obsidx, &cnnerr})
       b->release();
+    hcslots.release();
   }
 };
 

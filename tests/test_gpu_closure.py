@@ -148,3 +148,33 @@ def test_tensor_core_convolution_vs_bf16_restated_oracle(layer):
     p.closure_conv(layer, 1, inp, out)
     assert np.max(np.abs(host(out) - ref_tc)) <= 1e-5 * np.max(np.abs(ref_tc))
     p.set_option(11, 1)
+
+
+def test_step_adjoint_accumulates_the_parameter_gradient():
+    """With the learned closure, the chained spadj_step_adjoint calls add each step's parameter
+    cotangent to gp_accum: the sum equals spadj_adjoint's grad_p over the stored trajectory (and the
+    state gradient its grad_x0), bit for bit."""
+    from paper_2506_14792_gb300 import spadj
+    B, n = 2, 6
+    p = gpu_problem(B)
+    p.set_params(dev(synthetic.cnn_params(8, scale_out=1.0)))
+    ns = p.state_len(0)
+    X0 = dev(np.concatenate([okol.Kolmogorov(N, RE).project(synthetic.kolmogorov_ic(N, 700 + i)).ravel()
+                             for i in range(B)]))
+    traj = torch.zeros((n + 1, X0.numel()), dtype=torch.complex128, device="cuda")
+    xN = torch.zeros_like(X0)
+    p.forward(n, X0, xN, traj)
+    yN = dev(np.concatenate([okol.Kolmogorov(N, RE).project(synthetic.kolmogorov_ic(N, 800 + i)).ravel()
+                             for i in range(B)]))
+    g_ref = torch.zeros_like(X0)
+    gp_ref = torch.zeros(p.state_len(2), dtype=torch.float64, device="cuda")
+    p.adjoint(n, traj, yN, g_ref, gp_ref)
+    gp = torch.zeros_like(gp_ref)
+    y = None
+    for k in range(n, -1, -1):
+        out = torch.zeros(p.state_len(5), dtype=torch.float64, device="cuda")
+        p.step_adjoint(k, torch.view_as_real(traj[k]).reshape(-1).contiguous(), y, out,
+                       src=torch.view_as_real(yN).reshape(-1) if k == n else None, gp_accum=gp)
+        y = out
+    assert torch.equal(y[:ns], torch.view_as_real(g_ref).reshape(-1))
+    assert torch.equal(gp, gp_ref)

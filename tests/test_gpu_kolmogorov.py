@@ -184,3 +184,66 @@ def test_full_batch_sampled_members():
     for i in check:
         assert abs(J[i] - ref[i][0]) <= TOL * abs(ref[i][0])
         assert rel_err(got[i], ref[i][1]) < TOL
+
+
+@pytest.mark.parametrize("persistent", [1, 0])
+def test_segmented_checkpointing_equals_store_all(persistent):
+    """Checkpointed 4D-Var gradient: restart states [X_a, X_{a-1}, F(X_{a-1})] at segment starts (device
+    slots, or page-locked host slots with option 9), each segment recomputed and reversed in one
+    launch, the adjoint variables carried through the Y ring: bitwise equal to the store-all sweep,
+    for J, dJ/dX_0 and spadj_vjp with cotangents injected at several steps."""
+    from paper_2506_14792_gb300 import spadj
+    sizes, dt, n = [16, 24, 32, 16], 5e-3, 40
+    p = gpu_problem(sizes, dt=dt)
+    p.set_option(0, persistent)
+    X0 = dev(pack(ics(sizes, 30)))
+    obs_steps = [7, 20, 33, 40]
+    truth = dev(pack(ics(sizes, 70)))
+    obs = torch.stack([truth * (0.5 + 0.1 * i) for i in range(len(obs_steps))]).contiguous()
+    p.set_observations(obs_steps, obs, 5)
+    ref = torch.zeros_like(X0)
+    J = p.gradient(X0, n, ref, objective=spadj.SPADJ_OBJ_FOURDVAR, ckpt_slots=0)
+    for slots, hs in ((3, 0), (5, 0), (39, 0), (0, 6)):
+        p.set_option(9, hs)
+        g = torch.zeros_like(X0)
+        Jc = p.gradient(X0, n, g, objective=spadj.SPADJ_OBJ_FOURDVAR, ckpt_slots=slots)
+        assert np.array_equal(Jc, J), (slots, hs)
+        assert torch.equal(g, ref), (slots, hs)
+    p.set_option(9, 0)
+    seeds = torch.stack([dev(pack(ics(sizes, 90 + i))) for i in range(3)]).contiguous()
+    ga, gb = torch.zeros_like(X0), torch.zeros_like(X0)
+    p.vjp(X0, n, [n, 25, 3], seeds, ga, ckpt_slots=0)
+    p.vjp(X0, n, [n, 25, 3], seeds, gb, ckpt_slots=4)
+    assert torch.equal(ga, gb)
+
+
+def test_step_entry_points_equal_sweeps():
+    """spadj_step_forward on the restart state [X_n, X_{n-1}, F(X_{n-1})] reproduces spadj_forward, and
+    the adjoint chain (seed step at N, then steps N-1..0 with cotangents injected as sources)
+    reproduces spadj_vjp, bit for bit."""
+    sizes, dt, n = [16, 24], 5e-3, 12
+    p = gpu_problem(sizes, dt=dt)
+    ns = p.state_len(0)
+    assert p.state_len(4) == 3 * ns and p.state_len(5) == 2 * ns
+    X0 = dev(pack(ics(sizes, 50)))
+    s = torch.zeros(3 * ns, dtype=torch.float64, device="cuda")
+    s[:ns] = torch.view_as_real(X0).reshape(-1)
+    X = [s[:ns].clone()]
+    for k in range(n):
+        t = torch.zeros_like(s)
+        p.step_forward(k, s, t)
+        s = t
+        X.append(s[:ns].clone())
+    ref = torch.zeros_like(X0)
+    p.forward(n, X0, ref)
+    assert torch.equal(X[-1], torch.view_as_real(ref).reshape(-1))
+    seeds = torch.stack([torch.view_as_real(dev(pack(ics(sizes, 60 + i)))).reshape(-1) for i in range(3)])
+    at = {n: 0, 7: 1, 2: 2}
+    y = None
+    for k in range(n, -1, -1):
+        out = torch.zeros(2 * ns, dtype=torch.float64, device="cuda")
+        p.step_adjoint(k, X[k], y, out, src=seeds[at[k]].contiguous() if k in at else None)
+        y = out
+    g = torch.zeros_like(X0)
+    p.vjp(X0, n, [n, 7, 2], torch.view_as_complex(seeds.reshape(3, -1, 2)).contiguous(), g)
+    assert torch.equal(y[:ns], torch.view_as_real(g).reshape(-1))

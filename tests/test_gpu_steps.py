@@ -202,6 +202,12 @@ def test_step_argument_errors():
                               ctypes.c_void_p(b.data_ptr()))
     assert st == spadj.SPADJ_ERR_INVALID  # gp_accum on a problem without parameters
     k = spadj.Problem(spadj.SPADJ_KOLMOGOROV2D, spadj.SPADJ_SBDF2, [16], [2 * np.pi], [100.0], 1e-3)
-    assert k.state_len(4) == 0
-    st = L.spadj_step_forward(k.h, 0, ctypes.c_void_p(a.data_ptr()), ctypes.c_void_p(b.data_ptr()))
+    assert k.state_len(4) == 3 * k.state_len(0) and k.state_len(5) == 2 * k.state_len(0)
+    ka, kb = _zeros(k.state_len(4)), _zeros(k.state_len(4))
+    st = L.spadj_step_tangent(k.h, 0, ctypes.c_void_p(ka.data_ptr()), ctypes.c_void_p(ka.data_ptr()),
+                              ctypes.c_void_p(kb.data_ptr()))
+    assert st == spadj.SPADJ_ERR_UNSUPPORTED  # the Kolmogorov batch has no tangent sweep
+    e = spadj.Problem(spadj.SPADJ_SHEAR_EVP, 0, [0, 0, 16], [0.0], [1.0], 0.0, batch=2)
+    assert e.state_len(4) == 0
+    st = L.spadj_step_forward(e.h, 0, ctypes.c_void_p(a.data_ptr()), ctypes.c_void_p(b.data_ptr()))
     assert st == spadj.SPADJ_ERR_UNSUPPORTED
