@@ -139,18 +139,27 @@ class Burgers:
 
     ORDERS = {"sbdf1": 1, "sbdf2": 2, "sbdf3": 3, "sbdf4": 4}
 
-    def __init__(self, batch=16384, N=256, nsteps=1000, dt=1e-3, nu=0.01, seed=1, scheme="sbdf2"):
+    def __init__(self, batch=16384, N=256, nsteps=1000, dt=1e-3, nu=0.01, seed=1, scheme="sbdf2", slots=0):
         self.B, self.N, self.nsteps, self.dt, self.nu, self.seed = batch, N, nsteps, dt, nu, seed
         self.dof = N
         self.K, self.M = N // 2, 3 * N // 2
         self.scheme = scheme
-        if scheme != "sbdf2" or batch != 16384:
-            self.name = "burgers1d_N%d_%s_%dsteps%s" % (N, scheme, nsteps, "" if batch == 16384 else "_b%d" % batch)
+        self.slots = slots
+        if scheme != "sbdf2" or batch != 16384 or slots:
+            self.name = "burgers1d_N%d_%s_%dsteps%s%s" % (N, scheme, nsteps, "" if batch == 16384 else "_b%d" % batch,
+                                                          "_ckpt%d" % slots if slots else "")
 
     def config(self):
         return {"workload": self.name, "N": self.N, "nu": self.nu, "dt": self.dt, "steps": self.nsteps,
                 "batch": self.B, "scheme": self.scheme.upper(), "objective": "0.5||u(T)||^2",
-                "l2": "working set > L2 (stored trajectory %.1f GB)" % (self.traj_bytes() / 1e9)}
+                "checkpointing": ("binomial, %d restart-state slots" % self.slots) if self.slots else "store-all",
+                "l2": "working set > L2 (%s %.1f GB)" % (
+                    ("checkpoint slots", self.slots * self.ckpt_state_bytes()) if self.slots
+                    else ("stored trajectory", self.traj_bytes() / 1e9))}
+
+    def ckpt_state_bytes(self):
+        """GB of one restart state (the (2s - 1) state blocks of an order-s SBDF step)."""
+        return (2 * self.ORDERS[self.scheme] - 1) * self.B * self.K * 16 / 1e9
 
     def traj_bytes(self):
         return (self.nsteps + 1) * self.B * self.K * 16
@@ -169,8 +178,12 @@ class Burgers:
         self.p = spadj.Problem(spadj.SPADJ_BURGERS1D, sch, [self.N], [2 * np.pi], [self.nu], self.dt, batch=self.B)
         self.X0_host = synthetic.burgers_ic(self.N, batch=self.B, seed=self.seed)
         self.x0 = torch.from_numpy(self.X0_host).to(device)
-        self.traj = torch.empty((self.nsteps + 1, self.B, self.K), dtype=torch.complex128, device=device)
-        self.xN = self.traj[-1]
+        if self.slots:
+            self.traj = None
+            self.xN = torch.empty((self.B, self.K), dtype=torch.complex128, device=device)
+        else:
+            self.traj = torch.empty((self.nsteps + 1, self.B, self.K), dtype=torch.complex128, device=device)
+            self.xN = self.traj[-1]
         self.J = torch.empty(self.B, dtype=torch.float64, device=device)
         self.seedv = torch.empty((self.B, self.K), dtype=torch.complex128, device=device)
         self.grad = torch.empty((self.B, self.K), dtype=torch.complex128, device=device)
@@ -182,7 +195,12 @@ class Burgers:
     flush_l2 = False
 
     def step(self, ev=None):
-        """Device-resident step: forward (trajectory stored), objective, adjoint sweep."""
+        """Device-resident step: forward (trajectory stored), objective, adjoint sweep; with
+        checkpoint slots the library's checkpointed gradient (forward to the slots, reverse sweep
+        with recomputation)."""
+        if self.slots:
+            self.p.gradient(self.x0, self.nsteps, self.grad, ckpt_slots=self.slots, want_J=False)
+            return
         self.p.forward(self.nsteps, self.x0, self.xN, self.traj)
         self.p.objective(self.xN, self.J, self.seedv)
         self.p.adjoint(self.nsteps, self.traj, self.seedv, self.grad)
@@ -193,7 +211,7 @@ class Burgers:
     def e2e_step(self):
         """Public API call with host buffers: pinned H2D of x0, spadj_gradient (J to host), D2H of grad."""
         self.x0_dev2.copy_(self.x0_pin, non_blocking=True)
-        J = self.p.gradient(self.x0_dev2, self.nsteps, self.grad)
+        J = self.p.gradient(self.x0_dev2, self.nsteps, self.grad, ckpt_slots=self.slots)
         self.grad_pin.copy_(self.grad, non_blocking=True)
         return J
 
@@ -312,7 +330,10 @@ class KolmogorovBatch:
     truth run of the same solver (synthetic data)."""
     name = "kolmogorov2d_batch64_mixed128-512_Re100_sbdf2_2000steps_4dvar8"
 
-    def __init__(self, nsteps=2000, dt=5e-4, Re=100.0):
+    def __init__(self, nsteps=2000, dt=5e-4, Re=100.0, slots=0):
+        self.slots = slots
+        if slots:
+            self.name = self.name + "_seg%d" % slots
         self.res = [128, 256, 384, 512]
         self.sizes = [self.res[i // 16] for i in range(64)]
         self.nsteps, self.dt, self.Re = nsteps, dt, Re
@@ -323,8 +344,12 @@ class KolmogorovBatch:
     def config(self):
         return {"workload": self.name, "members": 64, "resolutions": self.res, "Re": self.Re, "dt": self.dt,
                 "steps": self.nsteps, "observations": self.obs_steps(), "dof_per_step": self.dof,
-                "l2": "working set > L2 (stored trajectory %.0f GB)" % (16 * sum((n // 2) * n for n in self.sizes)
-                                                                        * (self.nsteps + 1) / 1e9)}
+                "checkpointing": ("%d segments (restart state at each segment start, one segment recomputed "
+                                  "per reverse launch)" % self.slots) if self.slots else "store-all",
+                "l2": "working set > L2 (%s %.0f GB)" % (
+                    "segment buffer and restart states" if self.slots else "stored trajectory",
+                    16 * sum((n // 2) * n for n in self.sizes) * (
+                        (-(-self.nsteps // self.slots) + 1 + 3 * self.slots) if self.slots else (self.nsteps + 1)) / 1e9)}
 
     def obs_steps(self):
         k = max(1, self.nsteps // 8)
@@ -360,14 +385,16 @@ class KolmogorovBatch:
         self.x0_dev2 = torch.empty_like(self.x0)
 
     def step(self, ev=None):
-        self.p.gradient(self.x0, self.nsteps, self.grad, objective=self.sp.SPADJ_OBJ_FOURDVAR, want_J=False)
+        self.p.gradient(self.x0, self.nsteps, self.grad, objective=self.sp.SPADJ_OBJ_FOURDVAR, ckpt_slots=self.slots,
+                        want_J=False)
 
     def forward_step(self):
         self.p.forward(self.nsteps, self.x0, self.x0_dev2)
 
     def e2e_step(self):
         self.x0_dev2.copy_(self.x0_pin, non_blocking=True)
-        J = self.p.gradient(self.x0_dev2, self.nsteps, self.grad, objective=self.sp.SPADJ_OBJ_FOURDVAR)
+        J = self.p.gradient(self.x0_dev2, self.nsteps, self.grad, objective=self.sp.SPADJ_OBJ_FOURDVAR,
+                            ckpt_slots=self.slots)
         self.grad_pin.copy_(self.grad, non_blocking=True)
         return J
 
@@ -740,8 +767,11 @@ class Closure:
     name = "closure_kolmogorov64_cnn32_Re1000_fine1024_128windows_16steps"
     NF, NC, RE, DTF, RATIO, NCO, SPIN = 1024, 64, 1000.0, 2.5e-4, 16, 16, 400
 
-    def __init__(self, ntrain=128, nval=16, ntest=16, train_iters=150):
+    def __init__(self, ntrain=128, nval=16, ntest=16, train_iters=150, quick=False):
         self.ntrain, self.nval, self.ntest, self.train_iters = ntrain, nval, ntest, train_iters
+        self.quick = quick
+        if quick:  # profiling runs: coarse windows of the plain solver, untrained network, no held-out judgement
+            self.name = self.name + "_quick"
         self.flush_l2 = False
         self.B = ntrain
         self.dt_c = self.DTF * self.RATIO
@@ -772,6 +802,17 @@ class Closure:
         from paper_2506_14792_gb300 import closure_training as ct
         from paper_2506_14792_gb300 import spadj
         self.torch, self.sp, self.ct = torch, spadj, ct
+        if self.quick:
+            x0 = torch.from_numpy(np.concatenate([synthetic.kolmogorov_ic(self.NC, 1000 + s).ravel()
+                                                  for s in range(self.ntrain)])).to(device)
+            pp = spadj.Problem(spadj.SPADJ_KOLMOGOROV2D, spadj.SPADJ_SBDF2, [self.NC], [2 * np.pi], [self.RE, 0.0],
+                               self.dt_c, batch=self.ntrain)
+            self.tr = torch.empty((self.NCO + 1,) + tuple(x0.shape), dtype=x0.dtype, device=device)
+            pp.forward(self.NCO, x0, self.tr[-1], self.tr)
+            pp.close()
+            self.summary = {"setup": "quick: windows of the plain coarse solver as observations, network untrained"}
+            self._timed_setup(torch.from_numpy(synthetic.cnn_params(7, scale_out=0.01)).to(device), device)
+            return
         t0 = time.perf_counter()
         self.tr = self._data(range(1000, 1000 + self.ntrain))
         va = self._data(range(3000, 3000 + self.nval))
@@ -811,8 +852,12 @@ class Closure:
             "training": {"iterations": self.train_iters, "validation_history": hist, "train_windows": self.ntrain,
                          "seconds": round(t_train, 1)},
             "data_generation_seconds": round(t_data, 1)}
-        # the timed training iteration
-        self.params = best.clone()
+        self._timed_setup(best, device)
+
+    def _timed_setup(self, params, device):
+        """The timed training iteration's problem, optimiser and buffers."""
+        torch, ct = self.torch, self.ct
+        self.params = params.clone()
         self.p = ct.coarse_problem(self.ntrain, self.NC, self.RE, self.dt_c)
         self.p.set_observations(list(range(1, self.NCO + 1)), self.tr[1:].contiguous(), self.NC // 2 - 1)
         self.opt = ct.Adam(self.p, self.params.numel(), lr=3e-3, device=device)
@@ -1286,6 +1331,11 @@ def main():
     ap.add_argument("--omega", type=float, default=None, help="couette_resolvent: forcing frequency (default 0)")
     ap.add_argument("--batch", type=int, default=None,
                     help="burgers: members per gradient (default 16384; 1 gives the single-member latency line)")
+    ap.add_argument("--quick", action="store_true",
+                    help="closure: skip the fine data and the training (profiling runs; same timed iteration)")
+    ap.add_argument("--slots", type=int, default=0,
+                    help="burgers: binomial checkpointing with this many restart-state slots; kolmogorov: this many "
+                         "checkpointed segments (0: store-all)")
     ap.add_argument("--dt-blocks", type=int, default=0,
                     help="rb: step-size schedule alternating dt and dt/2 every this many steps (0: constant dt)")
     args = ap.parse_args()
@@ -1312,6 +1362,14 @@ def main():
         if args.workload != "burgers" or args.batch < 1:
             ap.error("--batch (>= 1) applies to the burgers workload")
         kw["batch"] = args.batch
+    if args.quick:
+        if args.workload != "closure":
+            ap.error("--quick applies to the closure workload")
+        kw["quick"] = True
+    if args.slots:
+        if args.workload not in ("burgers", "kolmogorov") or args.slots < 1:
+            ap.error("--slots (>= 1) applies to the burgers and kolmogorov workloads")
+        kw["slots"] = args.slots
     if args.omega is not None:
         if args.workload != "couette_resolvent":
             ap.error("--omega applies to the couette_resolvent workload")

@@ -172,6 +172,10 @@ spadj_status spadj_set_option(spadj_problem* p, int option, int value) {
     p->bulk_staging = value != 0;
     return SPADJ_OK;
   }
+  if (option == 12) {
+    p->cou_band = value != 0;
+    return SPADJ_OK;
+  }
   if (option == 9) {
     if (value < 0) return p->fail(SPADJ_ERR_INVALID, "set_option 9: host checkpoint slots must be >= 0");
     p->host_slots = value;

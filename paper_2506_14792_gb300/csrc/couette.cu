@@ -41,6 +41,13 @@ struct Couette : EqImpl {
   XParams xp{};
   YParams yp{};
   DevBuf wmx, w2y, czE, cdzE, gzF, gzTE, czTF, cdzTF, gmat, phi1F, phi1A, phi2F, phi2A, one;
+  // banded factors of the step solves: [scheme order - 1][0 forward, 1 adjoint]
+  struct BandDev {
+    DevBuf L, U, dinv, piv, ssb;
+    int kl = 0, ku = 0, nv = 0;
+  };
+  BandDev band[2][2];
+  bool band_ok = false, dense_ok = false;
   DevBuf Zm, Ym, Gf, dGf, Gb, Fg, Xr, Fr, dXr, dFr, Wr, xbar, src0, partial, edev, sdev, Jdev, slots, wts;
   DevBuf phiRF, phiRA, ginv, nrm, g2;  // resolvent operators of the last frequency, G^-1, per-pencil norms
   DevBuf htraj, hdtraj, dWr, dxbar, htmp;  // Hessian-vector product: trajectories and second-order cotangents
@@ -110,12 +117,6 @@ struct Couette : EqImpl {
 
     rbhost::Operators o = rbhost::build_operators(N, Mz, 1.0);
     ops = o;
-    std::vector<double> f1, a1, f2, a2;
-    std::string err;
-    if (!couhost::build_phi(o, Kx, Ny, Lx, Ly, nu, 1.0 / dt, f1, a1, &err, base))
-      return p->fail(SPADJ_ERR_INVALID, err);
-    if (order == 2 && !couhost::build_phi(o, Kx, Ny, Lx, Ly, nu, 1.5 / dt, f2, a2, &err, base))
-      return p->fail(SPADJ_ERR_INVALID, err);
     const int Mh = Mz / 2;
     std::vector<double> hczE((size_t)Mh * N), hcdzE((size_t)Mh * N), hgzF((size_t)N * Mh), hgzTE((size_t)Mh * N),
         hczTF((size_t)N * Mh), hcdzTF((size_t)N * Mh);
@@ -157,12 +158,6 @@ struct Couette : EqImpl {
     SPADJ_CUDA_TRY(p, up(czTF, hczTF.data(), sizeof(double) * hczTF.size()));
     SPADJ_CUDA_TRY(p, up(cdzTF, hcdzTF.data(), sizeof(double) * hcdzTF.size()));
     SPADJ_CUDA_TRY(p, up(gmat, o.G.data(), sizeof(double) * o.G.size()));
-    SPADJ_CUDA_TRY(p, up(phi1F, f1.data(), sizeof(double) * f1.size()));
-    SPADJ_CUDA_TRY(p, up(phi1A, a1.data(), sizeof(double) * a1.size()));
-    if (order == 2) {
-      SPADJ_CUDA_TRY(p, up(phi2F, f2.data(), sizeof(double) * f2.size()));
-      SPADJ_CUDA_TRY(p, up(phi2A, a2.data(), sizeof(double) * a2.size()));
-    }
     SPADJ_CUDA_TRY(p, up(one, &hone, sizeof(double)));
     SPADJ_CUDA_TRY(p, cudaStreamSynchronize(p->stream));
     xp.WM = wmx.as<double2>();
@@ -188,6 +183,10 @@ struct Couette : EqImpl {
     zsmem = (size_t)2 * 2 * (size_t)std::max(N, Mz / 2) * kTM * sizeof(double2);
     xsmem = sizeof(double2) * (4 * L + Kx);
     ysmem = sizeof(double2) * 2 * (size_t)My * yp.TK;
+    {  // the step-solve operators of the selected form (the other one is built on first use)
+      spadj_status s = p->cou_band ? ensure_band(p) : ensure_dense(p);
+      if (s != SPADJ_OK) return s;
+    }
     {  // x-FFT rows per CTA, timed on the six inverse transforms of one F evaluation
       SPADJ_CUDA_TRY(p, cudaMemsetAsync(Ym.ptr, 0, Ym.bytes, p->stream));
       XJobs xj{};
@@ -420,12 +419,103 @@ struct Couette : EqImpl {
     return launch_z(p, zf);
   }
 
+  // The dense step operators Phi of both scheme orders (couette_setup.h, build_phi).
+  spadj_status ensure_dense(Problem* p) {
+    if (dense_ok) return SPADJ_OK;
+    std::string err;
+    for (int ord = 1; ord <= order; ++ord) {
+      std::vector<double> f, a;
+      if (!couhost::build_phi(ops, Kx, Ny, Lx, Ly, nu, ord == 1 ? 1.0 / dt : 1.5 / dt, f, a, &err, base))
+        return p->fail(SPADJ_ERR_INVALID, err);
+      DevBuf& F = ord == 1 ? phi1F : phi2F;
+      DevBuf& A = ord == 1 ? phi1A : phi2A;
+      SPADJ_CUDA_TRY(p, F.ensure(sizeof(double) * f.size()));
+      SPADJ_CUDA_TRY(p, A.ensure(sizeof(double) * a.size()));
+      SPADJ_CUDA_TRY(p, cudaMemcpyAsync(F.ptr, f.data(), sizeof(double) * f.size(), cudaMemcpyHostToDevice, p->stream));
+      SPADJ_CUDA_TRY(p, cudaMemcpyAsync(A.ptr, a.data(), sizeof(double) * a.size(), cudaMemcpyHostToDevice, p->stream));
+      SPADJ_CUDA_TRY(p, cudaStreamSynchronize(p->stream));
+    }
+    dense_ok = true;
+    return SPADJ_OK;
+  }
+
+  // The banded factors of both scheme orders and directions (couette_setup.h, build_band).
+  // Widths beyond the kernel's rounds (kl > 32, ku > 64) leave the banded form off: the dense
+  // operators serve the solves instead.
+  spadj_status ensure_band(Problem* p) {
+    if (band_ok) return SPADJ_OK;
+    std::string err;
+    for (int ord = 1; ord <= order; ++ord)
+      for (int dir = 0; dir < 2; ++dir) {
+        couhost::BandFactors F;
+        if (!couhost::build_band(ops, Kx, Ny, Lx, Ly, nu, ord == 1 ? 1.0 / dt : 1.5 / dt, base, dir == 1, F, &err))
+          return p->fail(SPADJ_ERR_INVALID, err);
+        if (F.kl > 32 || F.ku > 64) return ensure_dense(p);
+        BandDev& B = band[ord - 1][dir];
+        B.kl = F.kl;
+        B.ku = F.ku;
+        B.nv = F.nv;
+        auto put = [&](DevBuf& b, const void* h, size_t bytes) -> cudaError_t {
+          cudaError_t e = b.ensure(bytes);
+          if (e != cudaSuccess) return e;
+          return cudaMemcpyAsync(b.ptr, h, bytes, cudaMemcpyHostToDevice, p->stream);
+        };
+        SPADJ_CUDA_TRY(p, put(B.L, F.L.data(), sizeof(double) * F.L.size()));
+        SPADJ_CUDA_TRY(p, put(B.U, F.U.data(), sizeof(double) * F.U.size()));
+        SPADJ_CUDA_TRY(p, put(B.dinv, F.dinv.data(), sizeof(double) * F.dinv.size()));
+        SPADJ_CUDA_TRY(p, put(B.piv, F.piv.data(), F.piv.size()));
+        SPADJ_CUDA_TRY(p, put(B.ssb, F.ssb.data(), sizeof(double) * F.ssb.size()));
+        SPADJ_CUDA_TRY(p, cudaStreamSynchronize(p->stream));
+      }
+    band_ok = true;
+    return SPADJ_OK;
+  }
+
   // x = P Phi v (transpose = 0) or v = Phi^H P x (transpose = 1), v = sum_t a_t in_t;
-  // scheme order 1 or 2 selects the SBDF1 or SBDF2 operator.
+  // scheme order 1 or 2 selects the SBDF1 or SBDF2 operator.  The banded factors serve the
+  // solve unless option 12 selects the dense Phi (or the band is too wide for the kernel).
   spadj_status solve(Problem* p, int transpose, int ord, int nin, const double2* const* in, const double* a,
                      double2* out) {
+    if (p->cou_band) {
+      spadj_status s = ensure_band(p);
+      if (s != SPADJ_OK) return s;
+      if (band_ok) return solve_band(p, transpose, ord, nin, in, a, out);
+    }
+    spadj_status s = ensure_dense(p);
+    if (s != SPADJ_OK) return s;
     return solve_with(p, transpose, (ord == 1 ? phi1F : phi2F).as<double2>(), (ord == 1 ? phi1A : phi2A).as<double2>(),
                       1, nin, in, a, out);
+  }
+
+  template <int RL, int RU>
+  cudaError_t launch_band(Problem* p, size_t smem, const CouBandArgs& S) {
+    return launch_kernel(p->pdl, cou_band_kernel<RL, RU>, dim3(Kx * (Ny / 2 + 1)), dim3(32), smem, p->stream, S);
+  }
+  spadj_status solve_band(Problem* p, int transpose, int ord, int nin, const double2* const* in, const double* a,
+                          double2* out) {
+    const BandDev& B = band[ord - 1][transpose ? 1 : 0];
+    CouBandArgs S{};
+    for (int t = 0; t < nin; ++t) { S.in[t] = in[t]; S.a[t] = a[t]; }
+    S.nin = nin; S.out = out; S.transpose = transpose;
+    S.L = B.L.as<double2>(); S.U = B.U.as<double2>(); S.dinv = B.dinv.as<double2>();
+    S.piv = B.piv.as<unsigned char>(); S.ssb = B.ssb.as<double>();
+    S.kl = B.kl; S.ku = B.ku; S.nv = B.nv;
+    S.Kx = Kx; S.Ny = Ny; S.N = N;
+    const size_t smem = sizeof(double2) * (2 * (size_t)B.nv + 6 * (size_t)N);
+    const int rl = (2 * B.kl + 31) / 32, ru = (2 * B.ku + 31) / 32;
+    cudaEvent_t t = p->tic();
+    cudaError_t e;
+    if (rl <= 1) {
+      e = ru <= 1 ? launch_band<1, 1>(p, smem, S) : ru == 2 ? launch_band<1, 2>(p, smem, S)
+        : ru == 3 ? launch_band<1, 3>(p, smem, S) : launch_band<1, 4>(p, smem, S);
+    } else {
+      e = ru <= 1 ? launch_band<2, 1>(p, smem, S) : ru == 2 ? launch_band<2, 2>(p, smem, S)
+        : ru == 3 ? launch_band<2, 3>(p, smem, S) : launch_band<2, 4>(p, smem, S);
+    }
+    SPADJ_CUDA_TRY(p, e);
+    // complex multiply-adds of the two sweeps and the scaling, per right-hand side
+    p->toc(t, KC_SOLVE, (8.0 * (B.kl + B.ku) + 6.0) * B.nv * (double)Kx * (Ny - 1));
+    return check_launch(p, "couette banded solve");
   }
   spadj_status solve_with(Problem* p, int transpose, const double2* phiF_, const double2* phiA_, int project, int nin,
                           const double2* const* in, const double* a, double2* out) {
@@ -1097,6 +1187,9 @@ struct Couette : EqImpl {
   }
 
   ~Couette() override {
+    for (auto& o2 : band)
+      for (BandDev& B : o2)
+        for (DevBuf* b : {&B.L, &B.U, &B.dinv, &B.piv, &B.ssb}) b->release();
     for (DevBuf* b : {&wmx, &w2y, &czE, &cdzE, &gzF, &gzTE, &czTF, &cdzTF, &gmat, &phi1F, &phi1A, &phi2F, &phi2A, &one,
                       &Zm, &Ym, &Gf, &dGf, &Gb, &Fg, &Xr, &Fr, &dXr, &dFr, &Wr, &xbar, &src0, &partial, &edev, &sdev,
                       &Jdev, &slots, &wts, &phiRF, &phiRA, &ginv, &nrm, &g2, &htraj, &hdtraj, &dWr, &dxbar, &htmp})

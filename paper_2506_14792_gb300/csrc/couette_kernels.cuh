@@ -233,6 +233,229 @@ __global__ void __launch_bounds__(1024) cou_solve_kernel(const __grid_constant__
   }
 }
 
+// Banded step solve of the pencil pair (kx m, ky +jh), (kx m, ky -jh): the same map as
+// cou_solve_kernel (x = P Phi v, or v = Phi^H P x), computed from the band LU factors of the
+// recombined, reordered pencil matrix A' (couette_setup.h) instead of the dense Phi.  One warp
+// (the CTA) per pair; its two right-hand sides sit in shared memory.
+//   forward:  y = [S1S0 v on the momentum rows of A'], solve A' y' = y, x = R y' (u_n = y'_n - y'_{n-2})
+//   adjoint:  y = J [R^T x on the velocity columns of A'], solve (J A'^H J) y' = y,
+//             v = S1S0^T [momentum rows of J y']
+// A sweep step updates up to 32 * R entries (R rounds of one entry per lane, both right-hand
+// sides side by side); the factors of step j + 1 are loaded while step j computes.
+struct CouBandArgs {
+  const double2* in[4];
+  double a[4];
+  int nin;
+  double2* out;
+  int transpose;
+  const double2* L;          // [pencil][j][kl]
+  const double2* U;          // [pencil][j][ku]
+  const double2* dinv;       // [pencil][j]
+  const unsigned char* piv;  // [pencil][j]: pivot row - j
+  const double* ssb;         // [N][5]: S1S0[n][n + d]
+  int kl, ku, nv;
+  int Kx, Ny, N;
+};
+
+__device__ __forceinline__ void cmac_sub(double2& y, double2 f, double2 x) {  // y -= f x
+  y.x = fma(-f.x, x.x, fma(f.y, x.y, y.x));
+  y.y = fma(-f.x, x.y, fma(-f.y, x.x, y.y));
+}
+
+template <int RL, int RU>
+__global__ void __launch_bounds__(32) cou_band_kernel(const __grid_constant__ CouBandArgs S) {
+  pdl_trigger();
+  pdl_wait();
+  const int lane = threadIdx.x;
+  const int Kx = S.Kx, Ny = S.Ny, N = S.N, H = 3 * N, nv = S.nv, kl = S.kl, ku = S.ku;
+  const int m = blockIdx.x % Kx, jh = blockIdx.x / Kx;
+  auto off = [&](int c, int j) { return (((size_t)(c / N) * Ny + j) * Kx + m) * N + (c % N); };
+  if (jh == Ny / 2) {  // the ky = -Ny/2 row is not stored: held at zero
+    for (int c = lane; c < H; c += 32) S.out[off(c, jh)] = make_double2(0.0, 0.0);
+    return;
+  }
+  const int j1 = jh, j2 = (Ny - jh) % Ny;
+  const bool two = j2 != j1;
+  const int nr = two ? 2 : 1;
+  const bool mean = m == 0 && jh == 0;
+  const size_t pp = (size_t)jh * Kx + m;
+  extern __shared__ double2 sband[];
+  double2* y = sband;           // [2][nv]
+  double2* t = sband + 2 * nv;  // [2][H]
+  // right-hand side combination, projection of the adjoint input, D on the -ky member
+  for (int c = lane; c < H; c += 32) {
+    double2 x1 = make_double2(0.0, 0.0), x2 = make_double2(0.0, 0.0);
+    for (int q = 0; q < S.nin; ++q) {
+      const double2 y1 = S.in[q][off(c, j1)];
+      x1.x = fma(S.a[q], y1.x, x1.x);
+      x1.y = fma(S.a[q], y1.y, x1.y);
+      if (two) {
+        const double2 y2 = S.in[q][off(c, j2)];
+        x2.x = fma(S.a[q], y2.x, x2.x);
+        x2.y = fma(S.a[q], y2.y, x2.y);
+      }
+    }
+    if (S.transpose && m == 0) {
+      if (two) {
+        const double2 h = make_double2(0.5 * (x1.x + x2.x), 0.5 * (x1.y - x2.y));
+        x1 = h;
+        x2 = cconj(h);
+      } else {
+        x1.y = 0.0;
+      }
+    }
+    if (c / N == 1) x2 = make_double2(-x2.x, -x2.y);
+    t[c] = x1;
+    t[H + c] = x2;
+  }
+  for (int i = lane; i < 2 * nv; i += 32) y[i] = make_double2(0.0, 0.0);
+  __syncwarp();
+  for (int c = lane; c < H; c += 32) {
+    const int f = c / N, n = c - f * N;
+    for (int r = 0; r < nr; ++r) {
+      const double2* tr = t + r * H;
+      double2 b = make_double2(0.0, 0.0);
+      int pos;
+      if (!S.transpose) {
+        for (int d = 0; d < 5 && n + d < N; ++d) {
+          const double w = __ldg(S.ssb + n * 5 + d);
+          b.x = fma(w, tr[c + d].x, b.x);
+          b.y = fma(w, tr[c + d].y, b.y);
+        }
+        pos = (mean ? 0 : 1) + 4 * n + f;
+      } else {
+        b = tr[c];
+        if (n + 2 < N) b = make_double2(b.x - tr[c + 2].x, b.y - tr[c + 2].y);
+        pos = nv - 1 - (1 + 4 * n + f);
+      }
+      y[r * nv + pos] = b;
+    }
+  }
+  __syncwarp();
+  const double2 zero = make_double2(0.0, 0.0);
+  {  // forward sweep: interchange, then the multipliers of column j
+    const double2* Lp = S.L + pp * nv * kl;
+    const unsigned char* pv = S.piv + pp * nv;
+    int kq[RL], rq[RL];
+    bool vq[RL];
+    double2 fc[RL], fn[RL];
+#pragma unroll
+    for (int q = 0; q < RL; ++q) {
+      const int tk = q * 32 + lane;
+      vq[q] = tk < nr * kl;
+      rq[q] = vq[q] ? tk / kl : 0;
+      kq[q] = vq[q] ? tk - rq[q] * kl : 0;
+      fc[q] = vq[q] ? __ldg(Lp + kq[q]) : zero;
+    }
+    int pc = __ldg(pv);
+    for (int j = 0; j < nv; ++j) {
+      int pn = 0;
+      if (j + 1 < nv) {
+#pragma unroll
+        for (int q = 0; q < RL; ++q) fn[q] = vq[q] ? __ldg(Lp + (size_t)(j + 1) * kl + kq[q]) : zero;
+        pn = __ldg(pv + j + 1);
+      }
+      if (pc && lane < nr) {
+        double2* yr = y + lane * nv;
+        const double2 a = yr[j];
+        yr[j] = yr[j + pc];
+        yr[j + pc] = a;
+      }
+      __syncwarp();
+#pragma unroll
+      for (int q = 0; q < RL; ++q) {
+        const int i = j + 1 + kq[q];
+        if (vq[q] && i < nv) {
+          double2* yr = y + rq[q] * nv;
+          double2 yi = yr[i];
+          cmac_sub(yi, fc[q], yr[j]);
+          yr[i] = yi;
+        }
+      }
+      __syncwarp();
+#pragma unroll
+      for (int q = 0; q < RL; ++q) fc[q] = fn[q];
+      pc = pn;
+    }
+  }
+  {  // the unit-diagonal scaling
+    const double2* Dp = S.dinv + pp * nv;
+    for (int i = lane; i < nr * nv; i += 32) {
+      const int r = i >= nv, j = i - r * nv;
+      y[i] = cmul(y[i], __ldg(Dp + j));
+    }
+    __syncwarp();
+  }
+  {  // back sweep, column-oriented on the row-scaled U
+    const double2* Up = S.U + pp * nv * ku;
+    int kq[RU], rq[RU];
+    bool vq[RU];
+    double2 fc[RU], fn[RU];
+#pragma unroll
+    for (int q = 0; q < RU; ++q) {
+      const int tk = q * 32 + lane;
+      vq[q] = tk < nr * ku;
+      rq[q] = vq[q] ? tk / ku : 0;
+      kq[q] = vq[q] ? tk - rq[q] * ku : 0;
+      fc[q] = vq[q] ? __ldg(Up + (size_t)(nv - 1) * ku + kq[q]) : zero;
+    }
+    for (int j = nv - 1; j >= 0; --j) {
+      if (j > 0) {
+#pragma unroll
+        for (int q = 0; q < RU; ++q) fn[q] = vq[q] ? __ldg(Up + (size_t)(j - 1) * ku + kq[q]) : zero;
+      }
+#pragma unroll
+      for (int q = 0; q < RU; ++q) {
+        const int i = j - 1 - kq[q];
+        if (vq[q] && i >= 0) {
+          double2* yr = y + rq[q] * nv;
+          double2 yi = yr[i];
+          cmac_sub(yi, fc[q], yr[j]);
+          yr[i] = yi;
+        }
+      }
+      __syncwarp();
+#pragma unroll
+      for (int q = 0; q < RU; ++q) fc[q] = fn[q];
+    }
+  }
+  for (int c = lane; c < H; c += 32) {
+    const int f = c / N, n = c - f * N;
+    double2 xo[2];
+    for (int r = 0; r < nr; ++r) {
+      const double2* yr = y + r * nv;
+      double2 v;
+      if (!S.transpose) {
+        v = yr[1 + 4 * n + f];
+        if (n >= 2) v = make_double2(v.x - yr[1 + 4 * (n - 2) + f].x, v.y - yr[1 + 4 * (n - 2) + f].y);
+      } else {
+        const int o0 = mean ? 0 : 1;
+        v = zero;
+        for (int d = 0; d < 5 && n - d >= 0; ++d) {
+          const double w = __ldg(S.ssb + (n - d) * 5 + d);
+          const double2 z = yr[nv - 1 - (o0 + 4 * (n - d) + f)];
+          v.x = fma(w, z.x, v.x);
+          v.y = fma(w, z.y, v.y);
+        }
+      }
+      xo[r] = v;
+    }
+    double2 x1 = xo[0], x2 = two ? xo[1] : zero;
+    if (f == 1) x2 = make_double2(-x2.x, -x2.y);
+    if (!S.transpose && m == 0) {
+      if (two) {
+        const double2 h = make_double2(0.5 * (x1.x + x2.x), 0.5 * (x1.y - x2.y));
+        x1 = h;
+        x2 = cconj(h);
+      } else {
+        x1.y = 0.0;
+      }
+    }
+    S.out[off(c, j1)] = x1;
+    if (two) S.out[off(c, j2)] = x2;
+  }
+}
+
 // Reverse of the products F = u x omega on the grid (slots 0 u, 1 v, 2 w, 3 omega_x,
 // 4 omega_y, 5 omega_z; cotangents gF of (F_x, F_y, F_z)) -> cotangents Gb of the six fields.
 __global__ void cou_prod_vjp_kernel(const double* __restrict__ G, const double* __restrict__ gF,

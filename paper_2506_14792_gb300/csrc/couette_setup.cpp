@@ -15,13 +15,17 @@
 // solve is the linear map Phi (3N x 3N per pencil).  The pencil matrix is complex (the
 // advection term is imaginary), so Phi is complex; it is computed here by LU with partial
 // pivoting (one factorisation per pencil and scheme, reused every step: Methods "Linear
-// system solves") and applied on the GPU as a dense matvec.
+// system solves") and applied on the GPU as a dense matvec.  The banded form (build_band)
+// keeps the factors instead: the pencil matrix, recombined so that its boundary rows become
+// local and ordered by Chebyshev mode, is narrowly banded (Sparse spectral methods section), and
+// the GPU runs its forward and back sweeps.
 #include "couette_setup.h"
 
 #include <algorithm>
 #include <cmath>
 #include <complex>
 #include <thread>
+#include <tuple>
 
 namespace spadj {
 namespace couhost {
@@ -291,6 +295,215 @@ bool build_phi(const rbhost::Operators& o, int Kx, int Ny, double Lx, double Ly,
                       std::to_string(pp / Kx) + ")";
       return false;
     }
+  return true;
+}
+
+namespace {
+
+// Row and column orders of the banded form (couette_setup.h): perm_r[i] / perm_c[i] is the row /
+// column of the assembled pencil matrix at position i.
+void band_orders(int N, bool mean, std::vector<int>& perm_r, std::vector<int>& perm_c) {
+  const int nv = 4 * N + 7;
+  perm_r.clear();
+  perm_c.clear();
+  if (!mean) perm_r.push_back(4 * N + 6);
+  perm_c.push_back(4 * N + 6);
+  for (int n = 0; n < N; ++n)
+    for (int f = 0; f < 4; ++f) {
+      perm_r.push_back(f * N + n);
+      perm_c.push_back(f * N + n);
+    }
+  for (int b = 0; b < 6; ++b) {
+    perm_r.push_back(4 * N + b);
+    perm_c.push_back(4 * N + b);
+  }
+  if (mean) perm_r.push_back(4 * N + 6);
+  (void)nv;
+}
+
+// The recombined, reordered pencil matrix A' (row-major nv x nv) and, for the adjoint direction,
+// J A'^H J in its place.
+void band_matrix(const rbhost::Operators& o, const std::vector<double>& ZS, const std::vector<double>& UP, double al,
+                 double be, bool mean, double nu, double a0, bool hermitian, std::vector<cd>& A, std::vector<cd>& B) {
+  const int N = o.N, nv = 4 * N + 7;
+  assemble_pencil(o, ZS, UP, al, be, mean, nu, cd(a0, 0.0), A);
+  auto col_sub = [&](int c, int c2, double w) {  // column c -= w * column c2
+    for (int r = 0; r < nv; ++r) A[(size_t)r * nv + c] -= w * A[(size_t)r * nv + c2];
+  };
+  // ascending j: column j + 2 is still the plain Chebyshev column when column j takes it
+  for (int f = 0; f < 3; ++f)
+    for (int j = 0; j + 2 < N; ++j) col_sub(f * N + j, f * N + j + 2, 1.0);
+  // the pressure columns only where the gauge row reads them (the mean pencil): elsewhere the
+  // recombination would raise the condition number of A' by four orders of magnitude
+  for (int j = 0; mean && j + 2 < N; j += 2) {
+    const double wj = 2.0 / (1.0 - (double)j * j), wj2 = 2.0 / (1.0 - (double)(j + 2) * (j + 2));
+    col_sub(3 * N + j, 3 * N + j + 2, wj / wj2);
+    // int psi_j dz = 0 exactly; the gauge row's rounding residue is dropped
+    A[(size_t)(4 * N + 6) * nv + 3 * N + j] = 0.0;
+  }
+  std::vector<int> pr, pc;
+  band_orders(N, mean, pr, pc);
+  B.assign((size_t)nv * nv, cd(0.0, 0.0));
+  for (int i = 0; i < nv; ++i)
+    for (int k = 0; k < nv; ++k) {
+      const cd v = A[(size_t)pr[i] * nv + pc[k]];
+      if (!hermitian)
+        B[(size_t)i * nv + k] = v;
+      else
+        B[(size_t)(nv - 1 - k) * nv + (nv - 1 - i)] = std::conj(v);
+    }
+}
+
+void band_widths(const std::vector<cd>& B, int nv, int& kl, int& ku) {
+  kl = ku = 0;
+  for (int i = 0; i < nv; ++i)
+    for (int k = 0; k < nv; ++k)
+      if (B[(size_t)i * nv + k] != 0.0) {
+        kl = std::max(kl, i - k);
+        ku = std::max(ku, k - i);
+      }
+}
+
+// Band LU with partial pivoting of B (row-major nv x nv, lower width kl, upper width ku) in place;
+// interchanges touch only the columns from j on.  piv[j] = pivot row - j.  False if singular.
+bool band_lu(std::vector<cd>& B, int nv, int kl, int ku, std::vector<int>& piv) {
+  piv.assign(nv, 0);
+  for (int j = 0; j < nv; ++j) {
+    const int imax = std::min(nv - 1, j + kl), cmax = std::min(nv - 1, j + kl + ku);
+    int p = j;
+    double best = std::norm(B[(size_t)j * nv + j]);
+    for (int i = j + 1; i <= imax; ++i) {
+      const double v = std::norm(B[(size_t)i * nv + j]);
+      if (v > best) { best = v; p = i; }
+    }
+    if (best == 0.0) return false;
+    piv[j] = p - j;
+    if (p != j)
+      for (int c = j; c <= cmax; ++c) std::swap(B[(size_t)j * nv + c], B[(size_t)p * nv + c]);
+    const cd inv = 1.0 / B[(size_t)j * nv + j];
+    for (int i = j + 1; i <= imax; ++i) {
+      const cd l = B[(size_t)i * nv + j] * inv;
+      B[(size_t)i * nv + j] = l;
+      if (l == 0.0) continue;
+      caxpy_sub(&B[(size_t)i * nv + j + 1], &B[(size_t)j * nv + j + 1], l, cmax - j);
+    }
+  }
+  return true;
+}
+
+}  // namespace
+
+bool build_band(const rbhost::Operators& o, int Kx, int Ny, double Lx, double Ly, double nu, double a0, int base,
+                bool hermitian, BandFactors& F, std::string* err) {
+  const int N = o.N, nv = 4 * N + 7, Nyh = Ny / 2, npen = Kx * Nyh;
+  std::vector<double> ZS, UP;
+  base_flow(o, base, ZS, UP);
+  F.ssb.assign((size_t)N * 5, 0.0);
+  for (int r = 0; r < N; ++r)
+    for (int c = 0; c < N; ++c) {
+      const double v = o.SS[(size_t)r * N + c];
+      if (v == 0.0) continue;
+      if (c < r || c > r + 4) {
+        if (err) *err = "couette: the conversion S1S0 is not banded as the banded solve assumes";
+        return false;
+      }
+      F.ssb[(size_t)r * 5 + (c - r)] = v;
+    }
+  unsigned nt = std::thread::hardware_concurrency();
+  if (nt == 0) nt = 1;
+  if (nt > 64) nt = 64;
+  if ((int)nt > npen) nt = npen;
+  const int chunk = (npen + nt - 1) / nt;
+  auto pencil = [&](int pp) {
+    const int jh = pp / Kx, m = pp % Kx;
+    return std::make_tuple(2.0 * M_PI / Lx * m, 2.0 * M_PI / Ly * jh, m == 0 && jh == 0);
+  };
+  auto run = [&](auto&& body) {
+    std::vector<std::thread> th;
+    for (unsigned t = 0; t < nt; ++t) {
+      const int p0 = t * chunk, p1 = std::min(npen, p0 + chunk);
+      if (p0 < p1) th.emplace_back([&, p0, p1] { body(p0, p1); });
+    }
+    for (auto& t : th) t.join();
+  };
+  // pass 1: the band widths (maximum over the pencils)
+  std::vector<int> wl(npen, 0), wu(npen, 0);
+  run([&](int p0, int p1) {
+    std::vector<cd> A, B;
+    for (int pp = p0; pp < p1; ++pp) {
+      auto [al, be, mean] = pencil(pp);
+      band_matrix(o, ZS, UP, al, be, mean, nu, a0, hermitian, A, B);
+      band_widths(B, nv, wl[pp], wu[pp]);
+    }
+  });
+  const int kl = *std::max_element(wl.begin(), wl.end()), kus = *std::max_element(wu.begin(), wu.end());
+  if (kl > 255) {
+    if (err) *err = "couette: banded pencil lower width above 255";
+    return false;
+  }
+  const int kuf = kl + kus;  // U width with the fill of the interchanges
+  // pass 2: factorise; U stored at the full width, then trimmed to the widest actual U
+  F.nv = nv;
+  F.kl = kl;
+  F.npen = npen;
+  F.L.assign((size_t)npen * nv * kl * 2, 0.0);
+  F.U.assign((size_t)npen * nv * kuf * 2, 0.0);
+  F.dinv.assign((size_t)npen * nv * 2, 0.0);
+  F.piv.assign((size_t)npen * nv, 0);
+  std::vector<int> bad(npen, 0), wact(npen, 0);
+  run([&](int p0, int p1) {
+    std::vector<cd> A, B;
+    std::vector<int> piv;
+    for (int pp = p0; pp < p1; ++pp) {
+      auto [al, be, mean] = pencil(pp);
+      band_matrix(o, ZS, UP, al, be, mean, nu, a0, hermitian, A, B);
+      if (!band_lu(B, nv, kl, kus, piv)) {
+        bad[pp] = 1;
+        continue;
+      }
+      double* Lp = &F.L[(size_t)pp * nv * kl * 2];
+      double* Up = &F.U[(size_t)pp * nv * kuf * 2];
+      double* Dp = &F.dinv[(size_t)pp * nv * 2];
+      for (int j = 0; j < nv; ++j) {
+        F.piv[(size_t)pp * nv + j] = (unsigned char)piv[j];
+        const cd d = 1.0 / B[(size_t)j * nv + j];
+        Dp[2 * j] = d.real();
+        Dp[2 * j + 1] = d.imag();
+        for (int k = 0; k < kl && j + 1 + k < nv; ++k) {
+          const cd l = B[(size_t)(j + 1 + k) * nv + j];
+          Lp[((size_t)j * kl + k) * 2] = l.real();
+          Lp[((size_t)j * kl + k) * 2 + 1] = l.imag();
+        }
+      }
+      for (int j = 0; j < nv; ++j)
+        for (int k = 0; k < kuf && j - 1 - k >= 0; ++k) {
+          const int i = j - 1 - k;
+          const cd u = B[(size_t)i * nv + j];
+          if (u == 0.0) continue;
+          wact[pp] = std::max(wact[pp], k + 1);
+          const cd us = u / B[(size_t)i * nv + i];
+          Up[((size_t)j * kuf + k) * 2] = us.real();
+          Up[((size_t)j * kuf + k) * 2 + 1] = us.imag();
+        }
+    }
+  });
+  for (int pp = 0; pp < npen; ++pp)
+    if (bad[pp]) {
+      if (err)
+        *err = "couette: singular banded pencil matrix at (kx, ky) index (" + std::to_string(pp % Kx) + ", " +
+               std::to_string(pp / Kx) + ")";
+      return false;
+    }
+  const int ku = std::max(1, *std::max_element(wact.begin(), wact.end()));
+  if (ku < kuf) {  // trim every U row to the widest actual one (in place: rows only move down)
+    for (size_t r = 0; r < (size_t)npen * nv; ++r)
+      for (int k = 0; k < ku; ++k) {
+        F.U[(r * ku + k) * 2] = F.U[(r * kuf + k) * 2];
+        F.U[(r * ku + k) * 2 + 1] = F.U[(r * kuf + k) * 2 + 1];
+      }
+    F.U.resize((size_t)npen * nv * ku * 2);
+  }
+  F.ku = ku;
   return true;
 }
 

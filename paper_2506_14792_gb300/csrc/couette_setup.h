@@ -43,6 +43,43 @@ void assemble_pencil(const rbhost::Operators& o, const std::vector<double>& Umat
 bool build_phi(const rbhost::Operators& o, int Kx, int Ny, double Lx, double Ly, double nu, std::complex<double> a0,
                std::vector<double>& phiF, std::vector<double>& phiA, std::string* err, int base = 0);
 
+// Banded factors of the step solves (the alternative to the dense Phi; same linear map up to
+// rounding).  The pencil matrix A = a0 M + L is right-preconditioned by a recombination R of the
+// Chebyshev columns (velocity: phi_j = T_j - T_{j+2} for j <= N-3, which vanish at z = +-1; on
+// the mean pencil also pressure: psi_j = T_j - (int T_j / int T_{j+2}) T_{j+2} for even j <= N-3,
+// which integrate to zero), so the boundary rows and the gauge row touch only the last two
+// modes; rows and columns
+// are then ordered by Chebyshev mode (the four equations / variables of a mode together), with
+//   rows    [gauge, modes 0..N-1 (u-eq, v-eq, w-eq, continuity), u(-1), u(1), v(-1), v(1), w(-1), w(1)]
+//           (the mean pencil puts the gauge row last),
+//   columns [tau_p, modes 0..N-1 (u, v, w, p), tau_u1, tau_u2, tau_v1, tau_v2, tau_w1, tau_w2],
+// which makes A' = Pr A R Pc^T banded (kl = 12, ku = 20 at N = 64).  A' is factorised by band
+// LU with partial pivoting (row interchanges confined to the band, LAPACK's band convention:
+// the multipliers of column j are not moved by later interchanges).  The adjoint direction
+// factorises J A'^H J (J the order reversal, so its lower band is A's and the forward sweep of
+// both directions is the short one) instead of reusing A's factors transposed: the same
+// operator A^-H, with the solve in the same column-oriented form.
+// Solve semantics of one factor set (n = nv unknowns), as the GPU kernel runs it:
+//   for j = 0..n-1: y_j <-> y_{j + piv[j]}; y_{j+1+k} -= L[j][k] y_j (k < kl)
+//   y_j *= dinv[j]
+//   for j = n-1..0: y_{j-1-k} -= U[j][k] y_j (k < ku)
+// with dinv[j] = 1 / U_jj and U[j][k] = U_{j-1-k, j} / U_{j-1-k, j-1-k} (the rows of U scaled to a
+// unit diagonal, so the back sweep needs no division).
+struct BandFactors {
+  int nv = 0, kl = 0, ku = 0, npen = 0;
+  std::vector<double> L;           // [pencil][j][kl] complex, interleaved (re, im)
+  std::vector<double> U;           // [pencil][j][ku] complex
+  std::vector<double> dinv;        // [pencil][j] complex
+  std::vector<unsigned char> piv;  // [pencil][j]: pivot row - j (0..kl)
+  std::vector<double> ssb;         // [N][5]: S1S0[n][n + d] (the conversion's band)
+};
+
+// The banded factors of every pencil (pencil index jh * Kx + m, ky = jh >= 0, as build_phi) at
+// a0 (real); hermitian selects the adjoint direction.  False (and err) if a pencil is singular,
+// the conversion S1S0 is not banded as assumed, or kl exceeds 255.
+bool build_band(const rbhost::Operators& o, int Kx, int Ny, double Lx, double Ly, double nu, double a0, int base,
+                bool hermitian, BandFactors& F, std::string* err);
+
 // Shift-invert operators of P eigenvalue pencils (prm[p] = alpha, beta, Re; shift[p] = sigma as
 // (re, im)) of the base flow `base`: with A_p = sigma_p M + L_p (one LU per pencil),
 //   T[p]  = A_p^-1 [S1S0 on the u, v, w momentum rows]   ((4N + 7) x 3N),

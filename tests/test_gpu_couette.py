@@ -389,3 +389,36 @@ def test_channel_flow_gain_gradient():
     gc = _zc(x0.shape)
     p.gradient(x0, n, gc, objective=spadj.SPADJ_OBJ_GAIN, ckpt_slots=3)
     assert torch.equal(gc, gr)
+
+
+@pytest.mark.parametrize("Nx,Ny,Nz,base", [(16, 6, 12, "couette"), (32, 8, 16, "couette"), (16, 8, 16, "poiseuille")])
+def test_banded_and_dense_step_solves(Nx, Ny, Nz, base):
+    """The two forms of the step solve (option 12: banded factors of the recombined pencil
+    matrix, or the dense Phi) agree to rounding in both directions, the banded adjoint is the
+    adjoint of the banded forward (dot test in the real inner product of the stored
+    coefficients; P is an orthogonal projection for it), and a gain gradient agrees across the
+    forms."""
+    from paper_2506_14792_gb300 import spadj
+    o = oco.Couette(Nx, Ny, Nz, RE, pencils=False)
+    v = rand_fields(o, 31, project=False)
+    w = rand_fields(o, 32, project=False)
+    u0 = synthetic.couette_ic(Nx, Ny, Nz, seed=5, norm=0.05)
+    res = {}
+    for form in (1, 0):
+        p = gpu_problem(Nx, Ny, Nz, base=base)
+        p.set_option(12, form)
+        a, b = _zc((3, o.Ny, o.Kx, o.N)), _zc((3, o.Ny, o.Kx, o.N))
+        p.solve(dev(to_gpu(v)), a)
+        p.solve(dev(to_gpu(w)), b, transpose=True)
+        g = _zc((3, o.Ny, o.Kx, o.N))
+        J = p.gradient(dev(to_gpu(u0)), 8, g, objective=spadj.SPADJ_OBJ_GAIN)
+        res[form] = (host(a), host(b), host(g), J[0])
+    assert rel_err(res[1][0], res[0][0]) < 1e-12
+    assert rel_err(res[1][1], res[0][1]) < 1e-12
+    # P (kx = 0 plane Hermitian in ky) is real-linear, not complex-linear: the identity holds for
+    # the real inner product Re <a, b>
+    lhs = np.vdot(to_gpu(w), res[1][0]).real
+    rhs = np.vdot(res[1][1], to_gpu(v)).real
+    assert abs(lhs - rhs) < 1e-12 * np.linalg.norm(to_gpu(w)) * np.linalg.norm(res[1][0])
+    assert abs(res[1][3] - res[0][3]) < 1e-12 * abs(res[0][3])
+    assert rel_err(res[1][2], res[0][2]) < 1e-11
