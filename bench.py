@@ -1151,7 +1151,8 @@ def run_gpu(args, wl):
     total_flops = sum(v[1] for v in rep.values())
     bound, dpeak, psrc = "alu", peak, "measured"
     if dom == "cnn":  # BF16 operands on the tensor cores: the measured dense BF16 rate
-        bound, dpeak, psrc = "tensor", bf16_peak_gflops()
+        bound = "tensor"
+        dpeak, psrc = bf16_peak_gflops()
     roof = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": dpeak, "unit": "GFLOP/s",
             "frac": achieved / dpeak, "traffic": traffic_for(wl, dom),
             "hbm": hbm_fraction(traffic_for(wl, dom), dms / dn / 1e3),

@@ -73,41 +73,52 @@ __device__ __forceinline__ float dot32_bf16(const __nv_bfloat16* x, const __nv_b
   return acc;
 }
 
-// forward of layer l for `nb` members of an M x M grid (member stride M*M pixels):
-// z = conv(in) + b; hidden layers store h = bf16(tanh z) and dact = 1 - tanh^2 (if non-null);
-// the last layer writes the FP64 output.
-__global__ void fwd_kernel(int l, int M, int nb, const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict__ wq,
-                           const float* __restrict__ bq, __nv_bfloat16* __restrict__ h, float* __restrict__ dact,
-                           double* __restrict__ out) {
-  const int ci = (l == 0) ? 1 : kHid, co = (l == kLayers - 1) ? 1 : kHid;
-  const long long P = (long long)M * M;
-  const long long total = P * nb * co;
+// periodic neighbour index of a coordinate in [-1, M]
+__device__ __forceinline__ int wrap1(int v, int M) { return v < 0 ? v + M : (v >= M ? v - M : v); }
+
+// Thin layers (l = 0: 1 -> 32, l = 3: 32 -> 1).  Thread = (pixel q of a member, channel k) with
+// the 32-wide channel fastest, so the 32-channel tensor is read and written coalesced; grid =
+// (pixel-channel tiles of 256, member); 32-bit index arithmetic (a member has M^2 < 2^31 pixels).
+template <int C>
+__device__ __forceinline__ bool thin_index(int M, int& y, int& x, int& k) {
+  const int tq = blockIdx.x * blockDim.x + threadIdx.x;
+  const int q = C == 1 ? tq : (tq >> 5);
+  k = C == 1 ? 0 : (tq & 31);
+  if (q >= M * M) return false;
+  y = q / M;
+  x = q - y * M;
+  return true;
+}
+
+// forward of a thin layer: z = conv(in) + b; layer 0 stores h = bf16(tanh z) and
+// dact = 1 - tanh^2 (if non-null); layer 3 writes the FP64 output.
+template <int CI, int CO>
+__global__ void __launch_bounds__(256) fwd_kernel(int l, int M, const __nv_bfloat16* __restrict__ in,
+                                                  const __nv_bfloat16* __restrict__ wq, const float* __restrict__ bq,
+                                                  __nv_bfloat16* __restrict__ h, float* __restrict__ dact,
+                                                  double* __restrict__ out) {
+  int y, x, o;
+  if (!thin_index<CO>(M, y, x, o)) return;
+  const long long base = (long long)blockIdx.y * M * M;
+  const long long pix = base + (long long)y * M + x;
   const __nv_bfloat16* W = wq + w_off(l);
-  const float* B = bq + w_off(l) + co * ci * 9;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
-    const int o = (int)(t % co);
-    const long long pix = t / co;
-    const long long mb = pix / P;
-    const int pp = (int)(pix % P);
-    const int y = pp / M, x = pp % M;
-    float acc = B[o];
-    for (int a = 0; a < 3; ++a) {
-      const int xs = (x + a - 1 + M) % M;
-      for (int b = 0; b < 3; ++b) {
-        const int ys = (y + b - 1 + M) % M;
-        const __nv_bfloat16* src = in + (mb * P + (long long)ys * M + xs) * ci;
-        const __nv_bfloat16* w = W + ((o * 3 + a) * 3 + b) * ci;
-        if (ci == kHid) acc = dot32_bf16(src, w, acc);
-        else acc = fmaf(__bfloat162float(w[0]), __bfloat162float(src[0]), acc);
-      }
+  float acc = bq[w_off(l) + CO * CI * 9 + o];
+  for (int a = 0; a < 3; ++a) {
+    const int xs = wrap1(x + a - 1, M);
+    for (int b = 0; b < 3; ++b) {
+      const int ys = wrap1(y + b - 1, M);
+      const __nv_bfloat16* src = in + (base + (long long)ys * M + xs) * CI;
+      const __nv_bfloat16* w = W + ((o * 3 + a) * 3 + b) * CI;
+      if (CI == kHid) acc = dot32_bf16(src, w, acc);
+      else acc = fmaf(__bfloat162float(w[0]), __bfloat162float(src[0]), acc);
     }
-    if (l < kLayers - 1) {
-      const float th = tanhf(acc);
-      h[pix * co + o] = __float2bfloat16_rn(th);
-      if (dact) dact[pix * co + o] = 1.0f - th * th;
-    } else {
-      out[pix] = (double)acc;
-    }
+  }
+  if (CO == kHid) {
+    const float th = tanhf(acc);
+    h[pix * CO + o] = __float2bfloat16_rn(th);
+    if (dact) dact[pix * CO + o] = 1.0f - th * th;
+  } else {
+    out[pix] = (double)acc;
   }
 }
 
@@ -118,85 +129,85 @@ __global__ void dz_kernel(long long n, const float* __restrict__ dh, const float
     dz[i] = __float2bfloat16_rn(g ? (float)g[i] : dh[i] * dact[i]);
 }
 
-// input gradient of layer l: din[c](x', y') = sum_{o,a,b} W[o,c,a,b] dz[o](x' - a + 1, y' - b + 1)
-// (FP32 into din, or FP64 into dout for the first layer)
-__global__ void dgrad_kernel(int l, int M, int nb, const __nv_bfloat16* __restrict__ dz, const __nv_bfloat16* __restrict__ wq,
-                             float* __restrict__ din, double* __restrict__ dout) {
-  const int ci = (l == 0) ? 1 : kHid, co = (l == kLayers - 1) ? 1 : kHid;
-  const long long P = (long long)M * M;
-  const long long total = P * nb * ci;
+// input gradient of a thin layer: din[c](x', y') = sum_{o,a,b} W[o,c,a,b] dz[o](x' - a + 1, y' - b + 1)
+// (FP32 into din for layer 3, FP64 into dout for layer 0)
+template <int CI, int CO>
+__global__ void __launch_bounds__(256) dgrad_kernel(int l, int M, const __nv_bfloat16* __restrict__ dz,
+                                                    const __nv_bfloat16* __restrict__ wq, float* __restrict__ din,
+                                                    double* __restrict__ dout) {
   const __nv_bfloat16* W = wq + w_off(l);
-  // for ci = 1 the weights of a tap, W[o][0][a][b] over o, as a contiguous 32-vector
+  // for CI = 1 the weights of a tap, W[o][0][a][b] over o, as a contiguous 32-vector
   __shared__ __align__(16) __nv_bfloat16 wt[9 * kHid];
-  if (ci == 1) {
-    for (int i = threadIdx.x; i < 9 * co; i += blockDim.x) wt[i] = W[(i % co) * 9 + i / co];
+  if (CI == 1) {
+    for (int i = threadIdx.x; i < 9 * CO; i += blockDim.x) wt[i] = W[(i % CO) * 9 + i / CO];
     __syncthreads();
   }
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
-    const int c = (int)(t % ci);
-    const long long pix = t / ci;
-    const long long mb = pix / P;
-    const int pp = (int)(pix % P);
-    const int y = pp / M, x = pp % M;
-    float acc = 0.0f;
-    for (int a = 0; a < 3; ++a) {
-      const int xs = (x - a + 1 + M) % M;
-      for (int b = 0; b < 3; ++b) {
-        const int ys = (y - b + 1 + M) % M;
-        const __nv_bfloat16* src = dz + (mb * P + (long long)ys * M + xs) * co;
-        if (ci == 1 && co == kHid) {
-          acc = dot32_bf16(src, wt + (a * 3 + b) * kHid, acc);
-        } else {
-          for (int o = 0; o < co; ++o)
-            acc = fmaf(__bfloat162float(W[((o * 3 + a) * 3 + b) * ci + c]), __bfloat162float(src[o]), acc);
-        }
+  int y, x, c;
+  if (!thin_index<CI>(M, y, x, c)) return;
+  const long long base = (long long)blockIdx.y * M * M;
+  const long long pix = base + (long long)y * M + x;
+  float acc = 0.0f;
+  for (int a = 0; a < 3; ++a) {
+    const int xs = wrap1(x - a + 1, M);
+    for (int b = 0; b < 3; ++b) {
+      const int ys = wrap1(y - b + 1, M);
+      const __nv_bfloat16* src = dz + (base + (long long)ys * M + xs) * CO;
+      if (CI == 1 && CO == kHid) {
+        acc = dot32_bf16(src, wt + (a * 3 + b) * kHid, acc);
+      } else {
+        for (int o = 0; o < CO; ++o)
+          acc = fmaf(__bfloat162float(W[((o * 3 + a) * 3 + b) * CI + c]), __bfloat162float(src[o]), acc);
       }
     }
-    if (dout) dout[pix] = (double)acc;
-    else din[pix * ci + c] = acc;
   }
+  if (CI == 1) dout[pix] = (double)acc;
+  else din[pix * CI + c] = acc;
 }
 
-// weight gradient of a thin layer (l = 0: 1 -> 32, l = 3: 32 -> 1) for each member:
+// weight gradient of a thin layer for each member:
 // part[mb][w_off(l) + r] (flat FP64-vector order), dW[o,c,a,b] = sum_pixels in[c](x + a - 1, y + b - 1)
 // dz[o](x, y), db[o] = sum dz[o].  One CTA per (member, tap) plus one per member for the bias; thread
 // t = (pixel lane t / 32, wide channel w = t % 32), the wide channel being o for layer 0 and c for
-// layer 3, so the reads of the 32-channel tensor are coalesced; the pixel lanes' partial sums are
-// reduced in shared memory in a fixed order.
+// layer 3, so the reads of the 32-channel tensor are coalesced; a pixel lane takes the pixels of a
+// row with x = lane (mod lanes), row after row (independent loads unrolled), and the lanes'
+// partial sums are reduced in shared memory in a fixed order.
+template <int CI, int CO>
 __global__ void __launch_bounds__(256) wgrad_kernel(int l, int M, const __nv_bfloat16* __restrict__ in,
                                                     const __nv_bfloat16* __restrict__ dz, float* __restrict__ part,
                                                     int npar) {
-  const int ci = (l == 0) ? 1 : kHid, co = (l == kLayers - 1) ? 1 : kHid;
-  const long long P = (long long)M * M;
   const int mb = blockIdx.y, item = blockIdx.x;  // 0..8: taps, 9: bias
   const int w = threadIdx.x & 31, lane = threadIdx.x >> 5, nl = blockDim.x >> 5;
   __shared__ float red[256];
   float* dst = part + (long long)mb * npar + w_off(l);
-  const __nv_bfloat16* inm = in + (long long)mb * P * ci;
-  const __nv_bfloat16* dzm = dz + (long long)mb * P * co;
+  const __nv_bfloat16* inm = in + (long long)mb * M * M * CI;
+  const __nv_bfloat16* dzm = dz + (long long)mb * M * M * CO;
   float acc = 0.0f;
   if (item < 9) {
     const int a = item / 3, b = item % 3;
-    for (long long pp = lane; pp < P; pp += nl) {
-      const int y = (int)(pp / M), x = (int)(pp - (long long)y * M);
-      const int xs = (x + a - 1 + M) % M, ys = (y + b - 1 + M) % M;
-      const long long sp = (long long)ys * M + xs;
-      const float iv = __bfloat162float(ci == 1 ? inm[sp] : inm[sp * ci + w]);
-      const float dv = __bfloat162float(co == 1 ? dzm[pp] : dzm[pp * co + w]);
-      acc = fmaf(iv, dv, acc);
+    for (int y = 0; y < M; ++y) {
+      const int ys = wrap1(y + b - 1, M);
+      const __nv_bfloat16* irow = inm + (long long)ys * M * CI;
+      const __nv_bfloat16* drow = dzm + (long long)y * M * CO;
+#pragma unroll 4
+      for (int x = lane; x < M; x += nl) {
+        const int xs = wrap1(x + a - 1, M);
+        const float iv = __bfloat162float(CI == 1 ? irow[xs] : irow[xs * CI + w]);
+        const float dv = __bfloat162float(CO == 1 ? drow[x] : drow[x * CO + w]);
+        acc = fmaf(iv, dv, acc);
+      }
     }
-  } else if (co > 1) {  // bias of layer 0: db[o = w]
-    for (long long pp = lane; pp < P; pp += nl) acc += __bfloat162float(dzm[pp * co + w]);
+  } else if (CO > 1) {  // bias of layer 0: db[o = w]
+    for (int q = lane; q < M * M; q += nl) acc += __bfloat162float(dzm[(long long)q * CO + w]);
   } else {  // bias of layer 3: every thread takes a strided share of the pixels
-    for (long long pp = threadIdx.x; pp < P; pp += blockDim.x) acc += __bfloat162float(dzm[pp]);
+    for (int q = threadIdx.x; q < M * M; q += blockDim.x) acc += __bfloat162float(dzm[q]);
   }
   red[threadIdx.x] = acc;
   __syncthreads();
-  if (item == 9 && co == 1) {
+  if (item == 9 && CO == 1) {
     if (threadIdx.x == 0) {
       float s = 0.0f;
       for (int k = 0; k < (int)blockDim.x; ++k) s += red[k];
-      dst[co * ci * 9] = s;
+      dst[CO * CI * 9] = s;
     }
     return;
   }
@@ -204,10 +215,10 @@ __global__ void __launch_bounds__(256) wgrad_kernel(int l, int M, const __nv_bfl
     float s = 0.0f;
     for (int k = 0; k < nl; ++k) s += red[k * 32 + w];
     if (item == 9) {
-      dst[co * ci * 9 + w] = s;
+      dst[CO * CI * 9 + w] = s;
     } else {
-      const int o = (co == 1) ? 0 : w, c = (ci == 1) ? 0 : w;
-      dst[((o * ci + c) * 3 + item / 3) * 3 + item % 3] = s;
+      const int o = (CO == 1) ? 0 : w, c = (CI == 1) ? 0 : w;
+      dst[((o * CI + c) * 3 + item / 3) * 3 + item % 3] = s;
     }
   }
 }
@@ -243,6 +254,13 @@ __device__ __forceinline__ void mma_bf16(float* c, const unsigned* a, const unsi
       "{%0,%1,%2,%3};\n"
       : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// 16-byte asynchronous copy global -> shared, zero-filled (nothing read) when valid is false
+__device__ __forceinline__ void cp_async16_zfill(void* smem_dst, const void* gmem_src, bool valid) {
+  const unsigned s = smem_addr(smem_dst);
+  const int n = valid ? 16 : 0;
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(s), "l"(gmem_src), "r"(n) : "memory");
 }
 
 __device__ __forceinline__ unsigned pack2(__nv_bfloat16 lo, __nv_bfloat16 hi) {
@@ -515,26 +533,32 @@ __global__ void __launch_bounds__(128) conv32_tc_kernel(int l, int M, int nb, in
   const unsigned aaddr = smem_addr(sA), baddr = smem_addr(sB);
   unsigned parity = 0;
   bool alive = true;
-  for (long long tile = blockIdx.x; tile < tiles && alive; tile += gridDim.x) {
-    // gather A: thread t owns row t (pixel p), 36 chunks of 8 channels (16 bytes) each
+  // A gather of a tile: thread t owns row t (pixel p), 36 asynchronous 16-byte copies (8 channels
+  // each) into the canonical layout; rows past the last pixel are zero-filled
+  auto gather = [&](long long tile) {
     const long long p = tile * kTcRows + tid;
     const bool ok = p < npix;
     const long long pc = ok ? p : 0;
     const long long mb = pc / P;
-    const int pp = (int)(pc - mb * P), y = pp / M, x = pp - (pp / M) * M;
+    const int pp = (int)(pc - mb * P), y = pp / M, x = pp - y * M;
+#pragma unroll
     for (int tap = 0; tap < 9; ++tap) {
       const int a = tap / 3, b = tap % 3;
       const int dx = mode == 1 ? 1 - a : a - 1, dy = mode == 1 ? 1 - b : b - 1;
-      const int xx = (x + dx + M) % M, yy = (y + dy + M) % M;
-      const uint4* src = reinterpret_cast<const uint4*>(in + (mb * P + (long long)yy * M + xx) * 32);
+      const int xx = wrap1(x + dx, M), yy = wrap1(y + dy, M);
+      const __nv_bfloat16* src = in + (mb * P + (long long)yy * M + xx) * 32;
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const uint4 v = ok ? __ldg(src + j) : make_uint4(0u, 0u, 0u, 0u);
-        *reinterpret_cast<uint4*>(sA + tc_core_off(tid, tap * 32 + 8 * j)) = v;
-      }
+      for (int j = 0; j < 4; ++j) cp_async16_zfill(sA + tc_core_off(tid, tap * 32 + 8 * j), src + 8 * j, ok);
     }
+    cp_async_commit();
+  };
+  long long tile = blockIdx.x;
+  if (tile < tiles) gather(tile);
+  for (; tile < tiles && alive; tile += gridDim.x) {
+    cp_async_wait_all();
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic-proxy writes -> tensor core
-    __syncthreads();
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();  // A complete, and every thread has read the previous tile's accumulator
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll 1
@@ -567,23 +591,40 @@ __global__ void __launch_bounds__(128) conv32_tc_kernel(int l, int M, int nb, in
         : "r"(tmem + ((unsigned)(warp * 32) << 16))
         : "memory");
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-    if (ok && alive) {
+    // the MMAs have consumed A: the next tile's gather runs under this tile's epilogue
+    if (alive && tile + gridDim.x < tiles) gather(tile + gridDim.x);
+    const long long p = tile * kTcRows + tid;
+    if (p < npix && alive) {
       if (mode == 0) {
-        for (int n = 0; n < 32; n += 2) {
-          const float t0 = tanhf(__uint_as_float(r[n]) + Bias[n]), t1 = tanhf(__uint_as_float(r[n + 1]) + Bias[n + 1]);
-          *reinterpret_cast<unsigned*>(h + p * 32 + n) = pack2(__float2bfloat16_rn(t0), __float2bfloat16_rn(t1));
+#pragma unroll
+        for (int n = 0; n < 32; n += 8) {
+          float t[8];
+#pragma unroll
+          for (int e = 0; e < 8; ++e) t[e] = tanhf(__uint_as_float(r[n + e]) + Bias[n + e]);
+          uint4 hv;
+          hv.x = pack2(__float2bfloat16_rn(t[0]), __float2bfloat16_rn(t[1]));
+          hv.y = pack2(__float2bfloat16_rn(t[2]), __float2bfloat16_rn(t[3]));
+          hv.z = pack2(__float2bfloat16_rn(t[4]), __float2bfloat16_rn(t[5]));
+          hv.w = pack2(__float2bfloat16_rn(t[6]), __float2bfloat16_rn(t[7]));
+          *reinterpret_cast<uint4*>(h + p * 32 + n) = hv;
           if (dact) {
-            dact[p * 32 + n] = 1.0f - t0 * t0;
-            dact[p * 32 + n + 1] = 1.0f - t1 * t1;
+            *reinterpret_cast<float4*>(dact + p * 32 + n) =
+                make_float4(1.0f - t[0] * t[0], 1.0f - t[1] * t[1], 1.0f - t[2] * t[2], 1.0f - t[3] * t[3]);
+            *reinterpret_cast<float4*>(dact + p * 32 + n + 4) =
+                make_float4(1.0f - t[4] * t[4], 1.0f - t[5] * t[5], 1.0f - t[6] * t[6], 1.0f - t[7] * t[7]);
           }
         }
       } else {
-        for (int n = 0; n < 32; ++n) fout[p * 32 + n] = __uint_as_float(r[n]) + (mode == 2 ? Bias[n] : 0.0f);
+        const float bs = mode == 2 ? 1.0f : 0.0f;
+#pragma unroll
+        for (int n = 0; n < 32; n += 4)
+          *reinterpret_cast<float4*>(fout + p * 32 + n) =
+              make_float4(__uint_as_float(r[n]) + bs * Bias[n], __uint_as_float(r[n + 1]) + bs * Bias[n + 1],
+                          __uint_as_float(r[n + 2]) + bs * Bias[n + 2], __uint_as_float(r[n + 3]) + bs * Bias[n + 3]);
       }
     }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();  // A may be overwritten and the accumulator reused once every thread has read it
   }
+  cp_async_wait_all();  // no copy outstanding at exit (a run cut short by a timeout)
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");

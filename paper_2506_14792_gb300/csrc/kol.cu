@@ -1264,6 +1264,8 @@ struct Kol : EqImpl {
 
   // ---- learned closure ---------------------------------------------------------------------
   int cnn_grid(long long n) const { return (int)std::min<long long>((n + 255) / 256, 4096); }
+  // thin-layer kernels: (pixel-channel tiles of 256 over one member's M^2 x C, members)
+  dim3 thin_grid(int M, int C) const { return dim3((unsigned)(((long long)M * M * C + 255) / 256), (unsigned)nmem); }
   int mma_grid(long long npix) const { return (int)std::min<long long>((npix + 63) / 64, 8192); }
 
   // One 32 -> 32 convolution of layer l (1 or 2) over all members: mode 0 forward hidden layer
@@ -1317,10 +1319,12 @@ struct Kol : EqImpl {
       const int co = (l == cnn::kLayers - 1) ? 1 : cnn::kHid;
       if (l == 1 || l == 2)  // 32 -> 32: tensor cores
         conv32(p, l, 0, in, hbuf[l].as<__nv_bfloat16>(), nullptr, nullptr);
+      else if (l == 0)
+        cnn::fwd_kernel<1, cnn::kHid><<<thin_grid(M, co), 256, 0, p->stream>>>(
+            l, M, in, wq.as<__nv_bfloat16>(), bq.as<float>(), hbuf[l].as<__nv_bfloat16>(), nullptr, nullptr);
       else
-        cnn::fwd_kernel<<<cnn_grid(P * co), 256, 0, p->stream>>>(
-            l, M, nb, in, wq.as<__nv_bfloat16>(), bq.as<float>(), l < 3 ? hbuf[l].as<__nv_bfloat16>() : nullptr, nullptr,
-            l == 3 ? corr.as<double>() : nullptr);
+        cnn::fwd_kernel<cnn::kHid, 1><<<thin_grid(M, co), 256, 0, p->stream>>>(
+            l, M, in, wq.as<__nv_bfloat16>(), bq.as<float>(), nullptr, nullptr, corr.as<double>());
       if (l < 3) in = hbuf[l].as<__nv_bfloat16>();
     }
     closure_rows_kernel<<<dim3(M, nb), kKolThreads, smem, p->stream>>>(A, corr.as<double>(), 0);
@@ -1337,9 +1341,9 @@ struct Kol : EqImpl {
                                    hbuf[2].as<__nv_bfloat16>()};
     for (int l = 0; l < 3; ++l) {
       if (l == 0)
-        cnn::fwd_kernel<<<cnn_grid(P * cnn::kHid), 256, 0, p->stream>>>(l, M, nb, ins[l], wq.as<__nv_bfloat16>(),
-                                                                         bq.as<float>(), hbuf[l].as<__nv_bfloat16>(),
-                                                                         dact[l].as<float>(), nullptr);
+        cnn::fwd_kernel<1, cnn::kHid><<<thin_grid(M, cnn::kHid), 256, 0, p->stream>>>(
+            l, M, ins[l], wq.as<__nv_bfloat16>(), bq.as<float>(), hbuf[l].as<__nv_bfloat16>(), dact[l].as<float>(),
+            nullptr);
       else
         conv32(p, l, 0, ins[l], hbuf[l].as<__nv_bfloat16>(), dact[l].as<float>(), nullptr);
     }
@@ -1358,10 +1362,17 @@ struct Kol : EqImpl {
         cnn::bgrad32_kernel<<<dim3(32, nb), 256, 0, p->stream>>>(l, M, dz.as<__nv_bfloat16>(), part.as<float>(), np);
         conv32(p, l, 1, dz.as<__nv_bfloat16>(), nullptr, nullptr, dh.as<float>());
       } else {
-        cnn::wgrad_kernel<<<dim3(10, nb), 256, 0, p->stream>>>(l, M, ins[l], dz.as<__nv_bfloat16>(), part.as<float>(), np);
-        cnn::dgrad_kernel<<<cnn_grid(P * ci), 256, 0, p->stream>>>(l, M, nb, dz.as<__nv_bfloat16>(),
-                                                                    wq.as<__nv_bfloat16>(), l > 0 ? dh.as<float>() : nullptr,
-                                                                    l == 0 ? corr.as<double>() : nullptr);
+        if (l == 0) {
+          cnn::wgrad_kernel<1, cnn::kHid><<<dim3(10, nb), 256, 0, p->stream>>>(l, M, ins[l], dz.as<__nv_bfloat16>(),
+                                                                                part.as<float>(), np);
+          cnn::dgrad_kernel<1, cnn::kHid><<<thin_grid(M, ci), 256, 0, p->stream>>>(
+              l, M, dz.as<__nv_bfloat16>(), wq.as<__nv_bfloat16>(), nullptr, corr.as<double>());
+        } else {
+          cnn::wgrad_kernel<cnn::kHid, 1><<<dim3(10, nb), 256, 0, p->stream>>>(l, M, ins[l], dz.as<__nv_bfloat16>(),
+                                                                                part.as<float>(), np);
+          cnn::dgrad_kernel<cnn::kHid, 1><<<thin_grid(M, ci), 256, 0, p->stream>>>(
+              l, M, dz.as<__nv_bfloat16>(), wq.as<__nv_bfloat16>(), dh.as<float>(), nullptr);
+        }
       }
     }
     cnn::reduce_params_kernel<<<64, 256, 0, p->stream>>>(part.as<float>(), nb, np, gp.as<double>());
