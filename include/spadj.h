@@ -339,11 +339,14 @@ spadj_status spadj_adam(spadj_problem* prob, const double* grad_p, int t, double
  * stages bring their operator block into shared memory (1, default: one bulk copy, cp.async.bulk,
  * completing on an mbarrier; 0: 16-byte cp.async copies spread over the threads); option 11
  * (SPADJ_KOLMOGOROV2D with the closure) = the 32 -> 32 convolutions on the fifth-generation tensor
- * cores (1, default: tcgen05.mma, accumulator in tensor memory) or on warp-level mma.sync (0);
- * option 12 (SPADJ_COUETTE3D) = form of the step solves (1, default: forward and back sweeps with
- * the banded LU factors of each recombined, mode-ordered pencil matrix, one warp per pencil pair;
- * 0: the dense prognostic operator Phi applied as a matvec; both compute the same map up to
- * rounding, and the form not built at creation is built on its first use).  Set them before the
+ * cores (tcgen05.mma, accumulator in tensor memory) with the operand staged once per tile and the
+ * nine taps read through shifted descriptors (1, default), the same with the operand gathered once
+ * per tap (2), or on warp-level mma.sync (0);
+ * option 12 (SPADJ_COUETTE3D) = form of the step solves (1: forward and back sweeps with the
+ * banded LU factors of each recombined, mode-ordered pencil matrix, one warp per pencil pair;
+ * 0: the dense prognostic operator Phi applied as a matvec; -1, default: banded when there are at
+ * least 8 pencil pairs per SM, else dense; both compute the same map up to rounding, and the form
+ * not built at creation is built on its first use).  Set them before the
  * first sweep (the step graphs are captured once).
  * spadj_autotune times candidate settings on the problem's own sizes and keeps the fastest. */
 spadj_status spadj_set_option(spadj_problem* prob, int option, int value);

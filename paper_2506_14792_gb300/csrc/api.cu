@@ -173,7 +173,8 @@ spadj_status spadj_set_option(spadj_problem* p, int option, int value) {
     return SPADJ_OK;
   }
   if (option == 12) {
-    p->cou_band = value != 0;
+    if (value < -1 || value > 1) return p->fail(SPADJ_ERR_INVALID, "set_option 12: -1, 0 or 1");
+    p->cou_band = value;
     return SPADJ_OK;
   }
   if (option == 9) {

@@ -73,6 +73,11 @@ __device__ __forceinline__ float dot32_bf16(const __nv_bfloat16* x, const __nv_b
   return acc;
 }
 
+// two BF16 values as one 32-bit word (lo in the low half)
+__device__ __forceinline__ unsigned pack2(__nv_bfloat16 lo, __nv_bfloat16 hi) {
+  return (unsigned)__bfloat16_as_ushort(lo) | ((unsigned)__bfloat16_as_ushort(hi) << 16);
+}
+
 // periodic neighbour index of a coordinate in [-1, M]
 __device__ __forceinline__ int wrap1(int v, int M) { return v < 0 ? v + M : (v >= M ? v - M : v); }
 
@@ -164,9 +169,95 @@ __global__ void __launch_bounds__(256) dgrad_kernel(int l, int M, const __nv_bfl
   else din[pix * CI + c] = acc;
 }
 
+// Layer 0 forward with one thread per pixel (all 32 output channels): the pixel's nine inputs are
+// read once and the 288 weights come from shared memory; the same sums in the same order as
+// fwd_kernel<1, 32> (bias, then the taps a-major), written as four 16-byte BF16 stores of h and
+// eight of dact.  Grid = (pixel tiles of 128, member).
+__global__ void __launch_bounds__(128) fwd0_kernel(int M, const __nv_bfloat16* __restrict__ in,
+                                                   const __nv_bfloat16* __restrict__ wq, const float* __restrict__ bq,
+                                                   __nv_bfloat16* __restrict__ h, float* __restrict__ dact) {
+  __shared__ float ws[9][kHid];
+  __shared__ float bs[kHid];
+  for (int i = threadIdx.x; i < 9 * kHid; i += blockDim.x) {
+    const int o = i / 9, t = i - o * 9;  // W[o][0][a][b] at o * 9 + a * 3 + b
+    ws[t][o] = __bfloat162float(wq[w_off(0) + i]);
+  }
+  if (threadIdx.x < kHid) bs[threadIdx.x] = bq[w_off(0) + kHid * 9 + threadIdx.x];
+  __syncthreads();
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= M * M) return;
+  const int y = q / M, x = q - y * M;
+  const long long base = (long long)blockIdx.y * M * M;
+  const long long pix = base + q;
+  float v[9];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+      v[a * 3 + b] = __bfloat162float(in[base + (long long)wrap1(y + b - 1, M) * M + wrap1(x + a - 1, M)]);
+#pragma unroll
+  for (int o0 = 0; o0 < kHid; o0 += 8) {
+    float acc[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) acc[e] = bs[o0 + e];
+#pragma unroll
+    for (int t = 0; t < 9; ++t)
+#pragma unroll
+      for (int e = 0; e < 8; ++e) acc[e] = fmaf(ws[t][o0 + e], v[t], acc[e]);
+    float th[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) th[e] = tanhf(acc[e]);
+    uint4 hv;
+    hv.x = pack2(__float2bfloat16_rn(th[0]), __float2bfloat16_rn(th[1]));
+    hv.y = pack2(__float2bfloat16_rn(th[2]), __float2bfloat16_rn(th[3]));
+    hv.z = pack2(__float2bfloat16_rn(th[4]), __float2bfloat16_rn(th[5]));
+    hv.w = pack2(__float2bfloat16_rn(th[6]), __float2bfloat16_rn(th[7]));
+    *reinterpret_cast<uint4*>(h + pix * kHid + o0) = hv;
+    if (dact) {
+      *reinterpret_cast<float4*>(dact + pix * kHid + o0) =
+          make_float4(1.0f - th[0] * th[0], 1.0f - th[1] * th[1], 1.0f - th[2] * th[2], 1.0f - th[3] * th[3]);
+      *reinterpret_cast<float4*>(dact + pix * kHid + o0 + 4) =
+          make_float4(1.0f - th[4] * th[4], 1.0f - th[5] * th[5], 1.0f - th[6] * th[6], 1.0f - th[7] * th[7]);
+    }
+  }
+}
+
+// Layer 3 input gradient with one thread per pixel (all 32 input channels): din[c] = sum over taps
+// of W[0][c][a][b] dz(x - a + 1, y - b + 1), the nine dz values read once, the same sums in the
+// same order as dgrad_kernel<32, 1>, written as eight 16-byte stores.
+__global__ void __launch_bounds__(128) dgrad3_kernel(int M, const __nv_bfloat16* __restrict__ dz,
+                                                     const __nv_bfloat16* __restrict__ wq, float* __restrict__ din) {
+  __shared__ float ws[9][kHid];
+  for (int i = threadIdx.x; i < 9 * kHid; i += blockDim.x) {
+    const int t = i / kHid, c = i - t * kHid;  // W[0][a][b][c] at (a * 3 + b) * 32 + c
+    ws[t][c] = __bfloat162float(wq[w_off(kLayers - 1) + i]);
+  }
+  __syncthreads();
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= M * M) return;
+  const int y = q / M, x = q - y * M;
+  const long long base = (long long)blockIdx.y * M * M;
+  float v[9];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+      v[a * 3 + b] = __bfloat162float(dz[base + (long long)wrap1(y - b + 1, M) * M + wrap1(x - a + 1, M)]);
+  float* dst = din + (base + q) * kHid;
+#pragma unroll
+  for (int c0 = 0; c0 < kHid; c0 += 4) {
+    float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+    for (int t = 0; t < 9; ++t)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) acc[e] = fmaf(ws[t][c0 + e], v[t], acc[e]);
+    *reinterpret_cast<float4*>(dst + c0) = make_float4(acc[0], acc[1], acc[2], acc[3]);
+  }
+}
+
 // weight gradient of a thin layer for each member:
 // part[mb][w_off(l) + r] (flat FP64-vector order), dW[o,c,a,b] = sum_pixels in[c](x + a - 1, y + b - 1)
-// dz[o](x, y), db[o] = sum dz[o].  One CTA per (member, tap) plus one per member for the bias; thread
+// dz[o](x, y), db[o] = sum dz[o].  One CTA per (member, x offset a) plus one per member for the bias; thread
 // t = (pixel lane t / 32, wide channel w = t % 32), the wide channel being o for layer 0 and c for
 // layer 3, so the reads of the 32-channel tensor are coalesced; a pixel lane takes the pixels of a
 // row with x = lane (mod lanes), row after row (independent loads unrolled), and the lanes'
@@ -175,50 +266,58 @@ template <int CI, int CO>
 __global__ void __launch_bounds__(256) wgrad_kernel(int l, int M, const __nv_bfloat16* __restrict__ in,
                                                     const __nv_bfloat16* __restrict__ dz, float* __restrict__ part,
                                                     int npar) {
-  const int mb = blockIdx.y, item = blockIdx.x;  // 0..8: taps, 9: bias
+  const int mb = blockIdx.y, item = blockIdx.x;  // 0..2: the taps of x offset a = item, 3: bias
   const int w = threadIdx.x & 31, lane = threadIdx.x >> 5, nl = blockDim.x >> 5;
-  __shared__ float red[256];
+  __shared__ float red[3][256];
   float* dst = part + (long long)mb * npar + w_off(l);
   const __nv_bfloat16* inm = in + (long long)mb * M * M * CI;
   const __nv_bfloat16* dzm = dz + (long long)mb * M * M * CO;
-  float acc = 0.0f;
-  if (item < 9) {
-    const int a = item / 3, b = item % 3;
+  float acc[3] = {0.0f, 0.0f, 0.0f};  // taps (a, b = 0, 1, 2): one dz load serves the three
+  if (item < 3) {
+    const int a = item;
     for (int y = 0; y < M; ++y) {
-      const int ys = wrap1(y + b - 1, M);
-      const __nv_bfloat16* irow = inm + (long long)ys * M * CI;
+      const __nv_bfloat16* irow[3];
+#pragma unroll
+      for (int b = 0; b < 3; ++b) irow[b] = inm + (long long)wrap1(y + b - 1, M) * M * CI;
       const __nv_bfloat16* drow = dzm + (long long)y * M * CO;
 #pragma unroll 4
       for (int x = lane; x < M; x += nl) {
         const int xs = wrap1(x + a - 1, M);
-        const float iv = __bfloat162float(CI == 1 ? irow[xs] : irow[xs * CI + w]);
         const float dv = __bfloat162float(CO == 1 ? drow[x] : drow[x * CO + w]);
-        acc = fmaf(iv, dv, acc);
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+          acc[b] = fmaf(__bfloat162float(CI == 1 ? irow[b][xs] : irow[b][xs * CI + w]), dv, acc[b]);
       }
     }
   } else if (CO > 1) {  // bias of layer 0: db[o = w]
-    for (int q = lane; q < M * M; q += nl) acc += __bfloat162float(dzm[(long long)q * CO + w]);
+    for (int q = lane; q < M * M; q += nl) acc[0] += __bfloat162float(dzm[(long long)q * CO + w]);
   } else {  // bias of layer 3: every thread takes a strided share of the pixels
-    for (int q = threadIdx.x; q < M * M; q += blockDim.x) acc += __bfloat162float(dzm[q]);
+    for (int q = threadIdx.x; q < M * M; q += blockDim.x) acc[0] += __bfloat162float(dzm[q]);
   }
-  red[threadIdx.x] = acc;
+#pragma unroll
+  for (int b = 0; b < 3; ++b) red[b][threadIdx.x] = acc[b];
   __syncthreads();
-  if (item == 9 && CO == 1) {
+  if (item == 3 && CO == 1) {
     if (threadIdx.x == 0) {
       float s = 0.0f;
-      for (int k = 0; k < (int)blockDim.x; ++k) s += red[k];
+      for (int k = 0; k < (int)blockDim.x; ++k) s += red[0][k];
       dst[CO * CI * 9] = s;
     }
     return;
   }
   if (threadIdx.x < 32) {
-    float s = 0.0f;
-    for (int k = 0; k < nl; ++k) s += red[k * 32 + w];
-    if (item == 9) {
+    if (item == 3) {
+      float s = 0.0f;
+      for (int k = 0; k < nl; ++k) s += red[0][k * 32 + w];
       dst[CO * CI * 9 + w] = s;
     } else {
       const int o = (CO == 1) ? 0 : w, c = (CI == 1) ? 0 : w;
-      dst[((o * CI + c) * 3 + item / 3) * 3 + item % 3] = s;
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        float s = 0.0f;
+        for (int k = 0; k < nl; ++k) s += red[b][k * 32 + w];
+        dst[((o * CI + c) * 3 + item) * 3 + b] = s;
+      }
     }
   }
 }
@@ -261,10 +360,6 @@ __device__ __forceinline__ void cp_async16_zfill(void* smem_dst, const void* gme
   const unsigned s = smem_addr(smem_dst);
   const int n = valid ? 16 : 0;
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(s), "l"(gmem_src), "r"(n) : "memory");
-}
-
-__device__ __forceinline__ unsigned pack2(__nv_bfloat16 lo, __nv_bfloat16 hi) {
-  return (unsigned)__bfloat16_as_ushort(lo) | ((unsigned)__bfloat16_as_ushort(hi) << 16);
 }
 
 // out[p][n] = sum_{a,b,c} Wt[n][a][b][c] * in[shift(p, a, b)][c]  (+ bias, tanh for dir = +1)
@@ -354,33 +449,35 @@ __global__ void __launch_bounds__(128) conv32_mma_kernel(int l, int M, int nb, i
 __global__ void __launch_bounds__(128) wgrad32_mma_kernel(int l, int M, const __nv_bfloat16* __restrict__ in,
                                                           const __nv_bfloat16* __restrict__ dz,
                                                           float* __restrict__ chunkbuf, int nchunk) {
-  const long long P = (long long)M * M;
+  const int P = M * M;  // pixels of a member (< 2^31): 32-bit index arithmetic
   const int tap = blockIdx.y, mb = blockIdx.z, chunk = blockIdx.x;
   const int a = tap / 3, b = tap % 3;
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int g = lane / 4, t4 = lane % 4;
-  const long long per = (P + nchunk - 1) / nchunk;
-  const long long pbeg = chunk * per, pend = min(P, pbeg + per);
+  const int per = (P + nchunk - 1) / nchunk;
+  const int pbeg = chunk * per, pend = min(P, pbeg + per);
+  const __nv_bfloat16* inm = in + (long long)mb * P * 32;
+  const __nv_bfloat16* dzm = dz + (long long)mb * P * 32;
   float acc[2][4][4];
   for (int mt = 0; mt < 2; ++mt)
     for (int nt = 0; nt < 4; ++nt)
       for (int q = 0; q < 4; ++q) acc[mt][nt][q] = 0.0f;
   const __nv_bfloat16 z = __float2bfloat16_rn(0.0f);
   // k-steps of 16 pixels, interleaved over the 4 warps
-  for (long long k0 = pbeg + warp * 16; k0 < pend; k0 += 64) {
+  for (int k0 = pbeg + warp * 16; k0 < pend; k0 += 64) {
     // pixels of this lane's k pairs: k0 + 2 t4 + {0, 1} and + 8
-    long long pk[4] = {k0 + 2 * t4, k0 + 2 * t4 + 1, k0 + 2 * t4 + 8, k0 + 2 * t4 + 9};
+    const int pk[4] = {k0 + 2 * t4, k0 + 2 * t4 + 1, k0 + 2 * t4 + 8, k0 + 2 * t4 + 9};
     const __nv_bfloat16* sh[4];
+    const __nv_bfloat16* dzr[4];
     bool okk[4];
+#pragma unroll
     for (int i = 0; i < 4; ++i) {
       okk[i] = pk[i] < pend;
-      const long long pc = okk[i] ? pk[i] : pbeg;
-      const int y = (int)(pc / M), x = (int)(pc % M);
-      const int xx = (x + a - 1 + M) % M, yy = (y + b - 1 + M) % M;
-      sh[i] = in + ((long long)mb * P + (long long)yy * M + xx) * 32;
+      const int pc = okk[i] ? pk[i] : pbeg;
+      const int y = pc / M, x = pc - y * M;
+      sh[i] = inm + ((long long)wrap1(y + b - 1, M) * M + wrap1(x + a - 1, M)) * 32;
+      dzr[i] = dzm + (long long)pc * 32;
     }
-    const __nv_bfloat16* dzr[4];
-    for (int i = 0; i < 4; ++i) dzr[i] = dz + ((long long)mb * P + (okk[i] ? pk[i] : pbeg)) * 32;
     for (int mt = 0; mt < 2; ++mt) {
       // A[o][p] = dz[p][o]: rows o = 16 mt + g (+8), k pairs = pixels
       const int o0 = mt * 16 + g, o1 = o0 + 8;
@@ -625,6 +722,170 @@ __global__ void __launch_bounds__(128) conv32_tc_kernel(int l, int M, int nb, in
     }
   }
   cp_async_wait_all();  // no copy outstanding at exit (a run cut short by a timeout)
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem) : "memory");
+}
+
+// The same convolutions with the operand staged once per tile instead of once per tap.  The
+// member's grid is addressed through a staged index s = ys * W + xs with W = M + 2 (xs = 0 holds
+// column M - 1, xs = 1..M columns 0..M-1, xs = M + 1 column 0: the periodic halo), so that every
+// tap is a uniform shift of s: (b - 1) W + (a - 1) in the forward (mode 0/2), its negative for the
+// input gradient (mode 1).  A tile is 128 consecutive staged indices of one member (rows at a halo
+// column or past the member are computed and discarded); its operand is the staged range
+// [s0 - W - 1, s0 + 128 + W + 1) of R = 2 W + 130 pixels, copied once by cp.async into
+//   [chunk g = c / 8][staged pixel i] x 16 bytes,
+// which is the canonical K-major layout without swizzle with rows 16 bytes apart (stride-byte
+// offset 128 between 8-row groups) and the chunks R * 16 bytes apart (leading-byte offset): the
+// MMA of tap t and channel half h reads A from chunk 2h at the tap's shifted first row, so the
+// nine taps need no copies of their own.  The staged range of the next tile is copied into the
+// other of two buffers while the current tile's MMAs and epilogue run.  Each input pixel is read
+// about R / 128 = 2.5 times instead of nine.
+__host__ __device__ constexpr int halo_range(int M) { return 2 * (M + 2) + 130; }
+__host__ __device__ constexpr size_t halo_smem(int M) {
+  return (size_t)2 * 4 * halo_range(M) * 16 + (size_t)32 * kTcK * 2;
+}
+
+__global__ void __launch_bounds__(128) conv32_halo_kernel(int l, int M, int nb, int mode,
+                                                          const __nv_bfloat16* __restrict__ in,
+                                                          const __nv_bfloat16* __restrict__ wq,
+                                                          const float* __restrict__ bq, __nv_bfloat16* __restrict__ h,
+                                                          float* __restrict__ dact, float* __restrict__ fout,
+                                                          int* __restrict__ err) {
+  extern __shared__ __align__(128) unsigned char hs[];
+  __shared__ unsigned long long bar;
+  __shared__ unsigned tmem_holder;
+  const int W = M + 2, R = halo_range(M);
+  const size_t abytes = (size_t)4 * R * 16;
+  unsigned char* sA[2] = {hs, hs + abytes};
+  unsigned char* sB = hs + 2 * abytes;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const long long P = (long long)M * M;
+  const int tpm = (M * W + kTcRows - 1) / kTcRows;  // tiles per member
+  const long long tiles = (long long)tpm * nb;
+  const __nv_bfloat16* Wt = wq + w_off(l);
+  for (int i = tid; i < 32 * kTcK; i += blockDim.x) {
+    const int n = i / kTcK, k = i - n * kTcK, tap = k >> 5, kc = k & 31;
+    const __nv_bfloat16 v = mode == 1 ? Wt[(kc * 9 + tap) * 32 + n] : Wt[(n * 9 + tap) * 32 + kc];
+    *reinterpret_cast<__nv_bfloat16*>(sB + tc_core_off(n, k)) = v;
+  }
+  if (tid == 0) mbar_init(&bar, 1);
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(smem_addr(&tmem_holder))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const unsigned tmem = tmem_holder;
+  const float* Bias = bq + w_off(l) + 32 * 32 * 9;
+  const unsigned baddr = smem_addr(sB);
+  // staged range of a tile into buffer buf: entry (g, i) <- channels 8g..8g+7 of the pixel at
+  // staged index s0 - W - 1 + i (rows wrap periodically)
+  auto stage = [&](long long tile, int buf) {
+    const long long mb = tile / tpm;
+    const int s0 = (int)(tile - mb * tpm) * kTcRows;
+    const __nv_bfloat16* src = in + mb * P * 32;
+    for (int idx = tid; idx < 4 * R; idx += blockDim.x) {
+      const int i = idx >> 2, g = idx & 3;
+      const int r = s0 - W - 1 + i;
+      int ys = r >= 0 ? r / W : -((W - 1 - r) / W);  // floor division (r >= -W - 1)
+      const int xs = r - ys * W;                      // 0 .. W - 1
+      ys = ((ys % M) + M) % M;  // rows past the member (read only by discarded outputs) wrap too
+      int x = xs - 1;
+      x = x < 0 ? x + M : (x >= M ? x - M : x);
+      cp_async16_zfill(sA[buf] + ((size_t)g * R + i) * 16, src + ((long long)ys * M + x) * 32 + g * 8, true);
+    }
+    cp_async_commit();
+  };
+  unsigned parity = 0;
+  bool alive = true;
+  long long tile = blockIdx.x;
+  int buf = 0;
+  if (tile < tiles) stage(tile, 0);
+  for (; tile < tiles && alive; tile += gridDim.x, buf ^= 1) {
+    // the next tile's range into the other buffer (its last reader, the MMAs of the previous
+    // tile, completed before that tile's epilogue); then wait for this tile's range only
+    if (tile + gridDim.x < tiles) stage(tile + gridDim.x, buf ^ 1);
+    else cp_async_commit();
+    asm volatile("cp.async.wait_group 1;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic-proxy writes -> tensor core
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();  // the range complete, and every thread has read the previous accumulator
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const unsigned aaddr = smem_addr(sA[buf]);
+#pragma unroll 1
+      for (int kk = 0; kk < kTcK / 16; ++kk) {
+        const int tap = kk >> 1, half = kk & 1, a = tap / 3, b = tap % 3;
+        const int sh = (b - 1) * W + (a - 1);
+        const int i0 = W + 1 + (mode == 1 ? -sh : sh);
+        const unsigned long long ad = tc_smem_desc(aaddr + (unsigned)((2 * half * R + i0) * 16), (unsigned)R * 16, 128);
+        const unsigned long long bd = tc_smem_desc(baddr + kk * 256, 128, kTcKg * 128);
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+            "l"(ad), "l"(bd), "r"(kTcIdesc), "r"(kk > 0 ? 1 : 0)
+            : "memory");
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(&bar))
+                   : "memory");
+    }
+    if (!tc_wait(&bar, parity, err)) {
+      tc_wait(&bar, parity, nullptr);  // the tile's MMAs may still be running: wait once more
+      alive = false;
+    }
+    parity ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    unsigned r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+          "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(tmem + ((unsigned)(warp * 32) << 16))
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    // this thread's output row: staged index s0 + tid, a pixel unless at a halo column or past the member
+    const long long mb = tile / tpm;
+    const int so = (int)(tile - mb * tpm) * kTcRows + tid;
+    const int ys = so / W, xs = so - ys * W;
+    if (alive && ys < M && xs >= 1 && xs <= M) {
+      const long long p = mb * P + (long long)ys * M + (xs - 1);
+      if (mode == 0) {
+#pragma unroll
+        for (int n = 0; n < 32; n += 8) {
+          float t[8];
+#pragma unroll
+          for (int e = 0; e < 8; ++e) t[e] = tanhf(__uint_as_float(r[n + e]) + Bias[n + e]);
+          uint4 hv;
+          hv.x = pack2(__float2bfloat16_rn(t[0]), __float2bfloat16_rn(t[1]));
+          hv.y = pack2(__float2bfloat16_rn(t[2]), __float2bfloat16_rn(t[3]));
+          hv.z = pack2(__float2bfloat16_rn(t[4]), __float2bfloat16_rn(t[5]));
+          hv.w = pack2(__float2bfloat16_rn(t[6]), __float2bfloat16_rn(t[7]));
+          *reinterpret_cast<uint4*>(h + p * 32 + n) = hv;
+          if (dact) {
+            *reinterpret_cast<float4*>(dact + p * 32 + n) =
+                make_float4(1.0f - t[0] * t[0], 1.0f - t[1] * t[1], 1.0f - t[2] * t[2], 1.0f - t[3] * t[3]);
+            *reinterpret_cast<float4*>(dact + p * 32 + n + 4) =
+                make_float4(1.0f - t[4] * t[4], 1.0f - t[5] * t[5], 1.0f - t[6] * t[6], 1.0f - t[7] * t[7]);
+          }
+        }
+      } else {
+        const float bs = mode == 2 ? 1.0f : 0.0f;
+#pragma unroll
+        for (int n = 0; n < 32; n += 4)
+          *reinterpret_cast<float4*>(fout + p * 32 + n) =
+              make_float4(__uint_as_float(r[n]) + bs * Bias[n], __uint_as_float(r[n + 1]) + bs * Bias[n + 1],
+                          __uint_as_float(r[n + 2]) + bs * Bias[n + 2], __uint_as_float(r[n + 3]) + bs * Bias[n + 3]);
+      }
+    }
+  }
+  cp_async_wait_all();  // no copy outstanding at exit
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");

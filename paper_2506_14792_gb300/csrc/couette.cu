@@ -48,6 +48,7 @@ struct Couette : EqImpl {
   };
   BandDev band[2][2];
   bool band_ok = false, dense_ok = false;
+  bool band_auto = true;  // the form option 12 = -1 selects: banded when the pencil pairs fill the GPU
   DevBuf Zm, Ym, Gf, dGf, Gb, Fg, Xr, Fr, dXr, dFr, Wr, xbar, src0, partial, edev, sdev, Jdev, slots, wts;
   DevBuf phiRF, phiRA, ginv, nrm, g2;  // resolvent operators of the last frequency, G^-1, per-pencil norms
   DevBuf htraj, hdtraj, dWr, dxbar, htmp;  // Hessian-vector product: trajectories and second-order cotangents
@@ -184,7 +185,14 @@ struct Couette : EqImpl {
     xsmem = sizeof(double2) * (4 * L + Kx);
     ysmem = sizeof(double2) * 2 * (size_t)My * yp.TK;
     {  // the step-solve operators of the selected form (the other one is built on first use)
-      spadj_status s = p->cou_band ? ensure_band(p) : ensure_dense(p);
+      // One warp per pencil pair runs the band sweeps: with fewer than 8 pairs per SM the warps
+      // cannot keep the FP64 pipe busy and the dense Phi (a CTA per pair) is faster (measured:
+      // 2112 pairs on 152 SMs 2.3x faster banded, 544 pairs 2x slower).
+      int dev = 0, sms = 0;
+      SPADJ_CUDA_TRY(p, cudaGetDevice(&dev));
+      SPADJ_CUDA_TRY(p, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+      band_auto = (long long)Kx * (Ny / 2 + 1) >= 8LL * sms;
+      spadj_status s = use_band(p) ? ensure_band(p) : ensure_dense(p);
       if (s != SPADJ_OK) return s;
     }
     {  // x-FFT rows per CTA, timed on the six inverse transforms of one F evaluation
@@ -471,12 +479,14 @@ struct Couette : EqImpl {
     return SPADJ_OK;
   }
 
+  bool use_band(const Problem* p) const { return p->cou_band < 0 ? band_auto : p->cou_band != 0; }
+
   // x = P Phi v (transpose = 0) or v = Phi^H P x (transpose = 1), v = sum_t a_t in_t;
   // scheme order 1 or 2 selects the SBDF1 or SBDF2 operator.  The banded factors serve the
   // solve unless option 12 selects the dense Phi (or the band is too wide for the kernel).
   spadj_status solve(Problem* p, int transpose, int ord, int nin, const double2* const* in, const double* a,
                      double2* out) {
-    if (p->cou_band) {
+    if (use_band(p)) {
       spadj_status s = ensure_band(p);
       if (s != SPADJ_OK) return s;
       if (band_ok) return solve_band(p, transpose, ord, nin, in, a, out);

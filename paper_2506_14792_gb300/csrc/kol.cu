@@ -914,6 +914,8 @@ struct Kol : EqImpl {
       }
       SPADJ_CUDA_TRY(p, cudaFuncSetAttribute(cnn::conv32_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)cnn::kTcSmem));
+      SPADJ_CUDA_TRY(p, cudaFuncSetAttribute(cnn::conv32_halo_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)cnn::halo_smem(hm[0].M)));
       SPADJ_CUDA_TRY(p, cudaMemsetAsync(pbuf.ptr, 0, sizeof(double) * np, p->stream));
       cnn::convert_kernel<<<64, 256, 0, p->stream>>>(pbuf.as<double>(), wq.as<__nv_bfloat16>(), bq.as<float>());
       spadj_status st = check_launch(p, "closure convert");
@@ -1266,6 +1268,8 @@ struct Kol : EqImpl {
   int cnn_grid(long long n) const { return (int)std::min<long long>((n + 255) / 256, 4096); }
   // thin-layer kernels: (pixel-channel tiles of 256 over one member's M^2 x C, members)
   dim3 thin_grid(int M, int C) const { return dim3((unsigned)(((long long)M * M * C + 255) / 256), (unsigned)nmem); }
+  // one thread per pixel: (pixel tiles of 128, members)
+  dim3 pixel_grid(int M) const { return dim3((unsigned)(((long long)M * M + 127) / 128), (unsigned)nmem); }
   int mma_grid(long long npix) const { return (int)std::min<long long>((npix + 63) / 64, 8192); }
 
   // One 32 -> 32 convolution of layer l (1 or 2) over all members: mode 0 forward hidden layer
@@ -1278,7 +1282,12 @@ struct Kol : EqImpl {
   spadj_status conv32(Problem* p, int l, int mode, const __nv_bfloat16* in, __nv_bfloat16* h, float* da, float* fout) {
     const int M = hm[0].M, nb = nmem;
     const long long P = (long long)M * M * nb;
-    if (tc_conv) {
+    if (tc_conv == 1) {  // operand staged once per tile (halo), nine shifted descriptors
+      const long long tiles = (long long)((M * (M + 2) + cnn::kTcRows - 1) / cnn::kTcRows) * nb;
+      const int grid = (int)std::min<long long>(tiles, 3LL * sm_count);
+      cnn::conv32_halo_kernel<<<grid, 128, cnn::halo_smem(M), p->stream>>>(
+          l, M, nb, mode, in, wq.as<__nv_bfloat16>(), bq.as<float>(), h, da, fout, cnnerr.as<int>());
+    } else if (tc_conv == 2) {  // operand gathered per tap
       const long long tiles = (P + cnn::kTcRows - 1) / cnn::kTcRows;
       const int grid = (int)std::min<long long>(tiles, 2LL * sm_count);
       cnn::conv32_tc_kernel<<<grid, 128, cnn::kTcSmem, p->stream>>>(l, M, nb, mode, in, wq.as<__nv_bfloat16>(),
@@ -1320,8 +1329,8 @@ struct Kol : EqImpl {
       if (l == 1 || l == 2)  // 32 -> 32: tensor cores
         conv32(p, l, 0, in, hbuf[l].as<__nv_bfloat16>(), nullptr, nullptr);
       else if (l == 0)
-        cnn::fwd_kernel<1, cnn::kHid><<<thin_grid(M, co), 256, 0, p->stream>>>(
-            l, M, in, wq.as<__nv_bfloat16>(), bq.as<float>(), hbuf[l].as<__nv_bfloat16>(), nullptr, nullptr);
+        cnn::fwd0_kernel<<<pixel_grid(M), 128, 0, p->stream>>>(M, in, wq.as<__nv_bfloat16>(), bq.as<float>(),
+                                                                hbuf[l].as<__nv_bfloat16>(), nullptr);
       else
         cnn::fwd_kernel<cnn::kHid, 1><<<thin_grid(M, co), 256, 0, p->stream>>>(
             l, M, in, wq.as<__nv_bfloat16>(), bq.as<float>(), nullptr, nullptr, corr.as<double>());
@@ -1341,9 +1350,8 @@ struct Kol : EqImpl {
                                    hbuf[2].as<__nv_bfloat16>()};
     for (int l = 0; l < 3; ++l) {
       if (l == 0)
-        cnn::fwd_kernel<1, cnn::kHid><<<thin_grid(M, cnn::kHid), 256, 0, p->stream>>>(
-            l, M, ins[l], wq.as<__nv_bfloat16>(), bq.as<float>(), hbuf[l].as<__nv_bfloat16>(), dact[l].as<float>(),
-            nullptr);
+        cnn::fwd0_kernel<<<pixel_grid(M), 128, 0, p->stream>>>(M, ins[l], wq.as<__nv_bfloat16>(), bq.as<float>(),
+                                                                hbuf[l].as<__nv_bfloat16>(), dact[l].as<float>());
       else
         conv32(p, l, 0, ins[l], hbuf[l].as<__nv_bfloat16>(), dact[l].as<float>(), nullptr);
     }
@@ -1363,15 +1371,15 @@ struct Kol : EqImpl {
         conv32(p, l, 1, dz.as<__nv_bfloat16>(), nullptr, nullptr, dh.as<float>());
       } else {
         if (l == 0) {
-          cnn::wgrad_kernel<1, cnn::kHid><<<dim3(10, nb), 256, 0, p->stream>>>(l, M, ins[l], dz.as<__nv_bfloat16>(),
+          cnn::wgrad_kernel<1, cnn::kHid><<<dim3(4, nb), 256, 0, p->stream>>>(l, M, ins[l], dz.as<__nv_bfloat16>(),
                                                                                 part.as<float>(), np);
           cnn::dgrad_kernel<1, cnn::kHid><<<thin_grid(M, ci), 256, 0, p->stream>>>(
               l, M, dz.as<__nv_bfloat16>(), wq.as<__nv_bfloat16>(), nullptr, corr.as<double>());
         } else {
-          cnn::wgrad_kernel<cnn::kHid, 1><<<dim3(10, nb), 256, 0, p->stream>>>(l, M, ins[l], dz.as<__nv_bfloat16>(),
+          cnn::wgrad_kernel<cnn::kHid, 1><<<dim3(4, nb), 256, 0, p->stream>>>(l, M, ins[l], dz.as<__nv_bfloat16>(),
                                                                                 part.as<float>(), np);
-          cnn::dgrad_kernel<cnn::kHid, 1><<<thin_grid(M, ci), 256, 0, p->stream>>>(
-              l, M, dz.as<__nv_bfloat16>(), wq.as<__nv_bfloat16>(), dh.as<float>(), nullptr);
+          cnn::dgrad3_kernel<<<pixel_grid(M), 128, 0, p->stream>>>(M, dz.as<__nv_bfloat16>(), wq.as<__nv_bfloat16>(),
+                                                                    dh.as<float>());
         }
       }
     }
@@ -1586,8 +1594,10 @@ struct Kol : EqImpl {
       case 5:  // failure-path test: member whose completion is never signalled (-1 = off)
         if (value < -1 || value >= nmem) return p->fail(SPADJ_ERR_INVALID, "set_option: member out of range");
         drop_signal_member = value; return SPADJ_OK;
-      case 11:  // closure convolutions on tcgen05 (1) or mma.sync (0)
-        tc_conv = value ? 1 : 0; return SPADJ_OK;
+      case 11:  // closure convolutions: tcgen05 with a halo-staged operand (1), tcgen05 with the operand
+                // gathered per tap (2), or mma.sync (0)
+        if (value < 0 || value > 2) return p->fail(SPADJ_ERR_INVALID, "set_option 11: 0, 1 or 2");
+        tc_conv = value; return SPADJ_OK;
       default: return p->fail(SPADJ_ERR_INVALID, "set_option: unknown option");
     }
   }

@@ -156,7 +156,7 @@ struct Problem {
   int x_rows = 0;            // x-FFT rows per CTA: 0 = tuned at creation, else 1, 2 or 4 (option 8)
   int host_slots = 0;        // host checkpoint slots of the two-level schedule, 0 = device only (option 9)
   bool bulk_staging = true;  // RB fused column stages: operator block by one bulk copy (option 10)
-  bool cou_band = true;      // Couette step solves: banded factors (1) or dense Phi (0) (option 12)
+  int cou_band = -1;         // Couette step solves: banded (1), dense Phi (0), by size (-1) (option 12)
   cudaEvent_t tic() {
     if (!timing.enabled) return nullptr;
     cudaEvent_t e = timing.get();

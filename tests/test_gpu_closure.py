@@ -112,8 +112,9 @@ def _bf16(x):
 @pytest.mark.parametrize("layer", [1, 2])
 def test_tensor_core_convolution_vs_bf16_restated_oracle(layer):
     """The 32 -> 32 layers on the fifth-generation tensor cores (tcgen05.mma, FP32 accumulator in tensor
-    memory), called alone through spadj_closure_conv: the pre-activation conv(x) + b and the input
-    gradient conv^T(g) against the oracle's direct-sum convolution (oracle/cnn.py) applied to the same
+    memory), called alone through spadj_closure_conv in both operand-staging forms (halo tile with
+    shifted descriptors, gather per tap): the pre-activation conv(x) + b and the input gradient
+    conv^T(g) against the oracle's direct-sum convolution (oracle/cnn.py) applied to the same
     BF16-rounded operands with exact (FP64) products and sums: the only difference left is the FP32
     accumulation, so the bar is 1e-5 relative.  Three members of a 24 x 24 grid: 1728 pixels, 13.5
     tiles of 128 (a ragged last tile)."""
@@ -133,14 +134,21 @@ def test_tensor_core_convolution_vs_bf16_restated_oracle(layer):
     xv, xbits = _bf16(x)
     inp = torch.from_numpy(np.ascontiguousarray(xbits.view(np.int16).transpose(0, 3, 2, 1))).cuda()  # [m][y][x][c]
     out = torch.zeros((nb, M, M, 32), dtype=torch.float32, device="cuda")
-    for mode in (0, 1):
-        p.closure_conv(layer, mode, inp, out)
-        got = host(out).transpose(0, 3, 2, 1)  # -> [m][o][x][y]
-        for m in range(nb):
-            xm = xv[m].astype(np.float64)
-            ref = ocnn.conv(xm, Wq, bq) if mode == 0 else ocnn.conv_t(xm, Wq)
-            err = np.max(np.abs(got[m] - ref)) / np.max(np.abs(ref))
-            assert err < 1e-5, (layer, mode, m, err)
+    res = {}
+    for form in (2, 1):  # operand gathered per tap; operand staged once per tile (halo, the default)
+        p.set_option(11, form)
+        for mode in (0, 1):
+            out.zero_()
+            p.closure_conv(layer, mode, inp, out)
+            res[(form, mode)] = host(out).copy()
+            got = res[(form, mode)].transpose(0, 3, 2, 1)  # -> [m][o][x][y]
+            for m in range(nb):
+                xm = xv[m].astype(np.float64)
+                ref = ocnn.conv(xm, Wq, bq) if mode == 0 else ocnn.conv_t(xm, Wq)
+                err = np.max(np.abs(got[m] - ref)) / np.max(np.abs(ref))
+                assert err < 1e-5, (layer, form, mode, m, err)
+    for mode in (0, 1):  # the two staging forms issue the same MMAs in the same order
+        assert np.max(np.abs(res[(1, mode)] - res[(2, mode)])) <= 1e-6 * np.max(np.abs(res[(2, mode)]))
     # the warp-level mma.sync kernel computes the same input gradient
     p.set_option(11, 0)
     ref_tc = host(out).copy()
