@@ -255,27 +255,31 @@ __global__ void __launch_bounds__(128) dgrad3_kernel(int M, const __nv_bfloat16*
   }
 }
 
-// weight gradient of a thin layer for each member:
-// part[mb][w_off(l) + r] (flat FP64-vector order), dW[o,c,a,b] = sum_pixels in[c](x + a - 1, y + b - 1)
-// dz[o](x, y), db[o] = sum dz[o].  One CTA per (member, x offset a) plus one per member for the bias; thread
-// t = (pixel lane t / 32, wide channel w = t % 32), the wide channel being o for layer 0 and c for
-// layer 3, so the reads of the 32-channel tensor are coalesced; a pixel lane takes the pixels of a
-// row with x = lane (mod lanes), row after row (independent loads unrolled), and the lanes'
-// partial sums are reduced in shared memory in a fixed order.
+// weight gradient of a thin layer for each member: dW[o,c,a,b] = sum_pixels in[c](x + a - 1, y + b - 1)
+// dz[o](x, y), db[o] = sum dz[o], in kThinSplits row bands per member whose partials
+// (scratch[member][band][r], r the flat FP64-vector index within the layer) wgrad_finish_kernel sums
+// in order.  CTA = (x offset a with its three taps b, or the bias; member; band); thread t = (pixel
+// lane t / 32, wide channel w = t % 32), the wide channel being o for layer 0 and c for layer 3, so
+// the reads of the 32-channel tensor are coalesced and one dz load serves the three taps; a pixel
+// lane takes the pixels x = lane (mod lanes) of the band's rows, and the lanes' partial sums are
+// reduced in shared memory in a fixed order.
+constexpr int kThinSplits = 4;
+constexpr int kThinOut = 9 * kHid + kHid;  // 320 partial slots per (member, band)
 template <int CI, int CO>
 __global__ void __launch_bounds__(256) wgrad_kernel(int l, int M, const __nv_bfloat16* __restrict__ in,
-                                                    const __nv_bfloat16* __restrict__ dz, float* __restrict__ part,
-                                                    int npar) {
-  const int mb = blockIdx.y, item = blockIdx.x;  // 0..2: the taps of x offset a = item, 3: bias
+                                                    const __nv_bfloat16* __restrict__ dz,
+                                                    float* __restrict__ scratch) {
+  const int mb = blockIdx.y, item = blockIdx.x, band = blockIdx.z;  // item 0..2: x offset a, 3: bias
   const int w = threadIdx.x & 31, lane = threadIdx.x >> 5, nl = blockDim.x >> 5;
+  const int y0 = band * M / kThinSplits, y1 = (band + 1) * M / kThinSplits;
   __shared__ float red[3][256];
-  float* dst = part + (long long)mb * npar + w_off(l);
+  float* dst = scratch + ((long long)mb * kThinSplits + band) * kThinOut;
   const __nv_bfloat16* inm = in + (long long)mb * M * M * CI;
   const __nv_bfloat16* dzm = dz + (long long)mb * M * M * CO;
-  float acc[3] = {0.0f, 0.0f, 0.0f};  // taps (a, b = 0, 1, 2): one dz load serves the three
+  float acc[3] = {0.0f, 0.0f, 0.0f};  // taps (a, b = 0, 1, 2)
   if (item < 3) {
     const int a = item;
-    for (int y = 0; y < M; ++y) {
+    for (int y = y0; y < y1; ++y) {
       const __nv_bfloat16* irow[3];
 #pragma unroll
       for (int b = 0; b < 3; ++b) irow[b] = inm + (long long)wrap1(y + b - 1, M) * M * CI;
@@ -290,9 +294,9 @@ __global__ void __launch_bounds__(256) wgrad_kernel(int l, int M, const __nv_bfl
       }
     }
   } else if (CO > 1) {  // bias of layer 0: db[o = w]
-    for (int q = lane; q < M * M; q += nl) acc[0] += __bfloat162float(dzm[(long long)q * CO + w]);
-  } else {  // bias of layer 3: every thread takes a strided share of the pixels
-    for (int q = threadIdx.x; q < M * M; q += blockDim.x) acc[0] += __bfloat162float(dzm[q]);
+    for (int q = y0 * M + lane; q < y1 * M; q += nl) acc[0] += __bfloat162float(dzm[(long long)q * CO + w]);
+  } else {  // bias of layer 3: every thread takes a strided share of the band's pixels
+    for (int q = y0 * M + threadIdx.x; q < y1 * M; q += blockDim.x) acc[0] += __bfloat162float(dzm[q]);
   }
 #pragma unroll
   for (int b = 0; b < 3; ++b) red[b][threadIdx.x] = acc[b];
@@ -319,6 +323,16 @@ __global__ void __launch_bounds__(256) wgrad_kernel(int l, int M, const __nv_bfl
         dst[((o * CI + c) * 3 + item) * 3 + b] = s;
       }
     }
+  }
+}
+
+// part[mb][w_off(l) + r] = sum over the bands of scratch[mb][band][r], in band order
+__global__ void wgrad_finish_kernel(int l, const float* __restrict__ scratch, float* __restrict__ part, int npar) {
+  const int mb = blockIdx.x, nr = kThinOut - (l == 0 ? 0 : kHid - 1);  // 9 * 32 weights + 32 or 1 biases
+  for (int r = threadIdx.x; r < nr; r += blockDim.x) {
+    float s = 0.0f;
+    for (int band = 0; band < kThinSplits; ++band) s += scratch[((long long)mb * kThinSplits + band) * kThinOut + r];
+    part[(long long)mb * npar + w_off(l) + r] = s;
   }
 }
 

@@ -1371,13 +1371,15 @@ struct Kol : EqImpl {
         conv32(p, l, 1, dz.as<__nv_bfloat16>(), nullptr, nullptr, dh.as<float>());
       } else {
         if (l == 0) {
-          cnn::wgrad_kernel<1, cnn::kHid><<<dim3(4, nb), 256, 0, p->stream>>>(l, M, ins[l], dz.as<__nv_bfloat16>(),
-                                                                                part.as<float>(), np);
+          cnn::wgrad_kernel<1, cnn::kHid><<<dim3(4, nb, cnn::kThinSplits), 256, 0, p->stream>>>(
+              l, M, ins[l], dz.as<__nv_bfloat16>(), chunkbuf.as<float>());
+          cnn::wgrad_finish_kernel<<<nb, 320, 0, p->stream>>>(l, chunkbuf.as<float>(), part.as<float>(), np);
           cnn::dgrad_kernel<1, cnn::kHid><<<thin_grid(M, ci), 256, 0, p->stream>>>(
               l, M, dz.as<__nv_bfloat16>(), wq.as<__nv_bfloat16>(), nullptr, corr.as<double>());
         } else {
-          cnn::wgrad_kernel<cnn::kHid, 1><<<dim3(4, nb), 256, 0, p->stream>>>(l, M, ins[l], dz.as<__nv_bfloat16>(),
-                                                                                part.as<float>(), np);
+          cnn::wgrad_kernel<cnn::kHid, 1><<<dim3(4, nb, cnn::kThinSplits), 256, 0, p->stream>>>(
+              l, M, ins[l], dz.as<__nv_bfloat16>(), chunkbuf.as<float>());
+          cnn::wgrad_finish_kernel<<<nb, 320, 0, p->stream>>>(l, chunkbuf.as<float>(), part.as<float>(), np);
           cnn::dgrad3_kernel<<<pixel_grid(M), 128, 0, p->stream>>>(M, dz.as<__nv_bfloat16>(), wq.as<__nv_bfloat16>(),
                                                                     dh.as<float>());
         }
