@@ -906,5 +906,122 @@ __global__ void __launch_bounds__(128) conv32_halo_kernel(int l, int M, int nb, 
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem) : "memory");
 }
 
+// Weight gradient of a 32 -> 32 layer from halo-staged operands: dW[o][c][tap] =
+// sum_p dz[p][o] in[p + shift(tap)][c] as warp-level BF16 MMAs (m16n8k16, FP32 accumulation) whose
+// fragments are read from shared memory by ldmatrix.trans.  A tile is 128 consecutive staged
+// indices of one member (the staged index space of conv32_halo_kernel); its dz rows (zero at the
+// halo columns and past the member, so they add nothing) and the halo range of the input are
+// copied once by cp.async as [8-channel chunk][pixel] x 16 bytes, double-buffered.  Warp t owns
+// tap t: per 16 pixels it loads the A fragments (o x pixel) from the dz chunks and the B fragments
+// (pixel x c) from the input chunks at the tap's shifted rows, and keeps its 32 x 32 accumulators
+// in registers over the CTA's tiles.  CTA = (pixel chunk of the member's tiles, member); each warp
+// writes its tap's partial block to chunkbuf[member][tap][chunk], summed by wgrad32_finish_kernel.
+__device__ __forceinline__ void ldsm_x4_t(unsigned* r, const void* row_addr) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0, %1, %2, %3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(smem_addr(row_addr)));
+}
+__host__ __device__ constexpr size_t wgrad_halo_smem(int M) {
+  return (size_t)2 * 4 * (halo_range(M) + kTcRows) * 16;
+}
+
+__global__ void __launch_bounds__(288) wgrad32_halo_kernel(int M, const __nv_bfloat16* __restrict__ in,
+                                                           const __nv_bfloat16* __restrict__ dz,
+                                                           float* __restrict__ chunkbuf, int nchunk) {
+  extern __shared__ __align__(128) unsigned char ws[];
+  const int W = M + 2, R = halo_range(M);
+  const size_t buf_bytes = (size_t)4 * (R + kTcRows) * 16;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int chunk = blockIdx.x, mb = blockIdx.y;
+  const long long P = (long long)M * M;
+  const int tpm = (M * W + kTcRows - 1) / kTcRows;
+  const int t0 = chunk * tpm / nchunk, t1 = (chunk + 1) * tpm / nchunk;
+  const __nv_bfloat16* inm = in + mb * P * 32;
+  const __nv_bfloat16* dzm = dz + mb * P * 32;
+  // buffer b: input range [g][i] (4 x R rows), then dz [g][k] (4 x 128 rows), 16 bytes each
+  auto sin = [&](int b) { return ws + b * buf_bytes; };
+  auto sdz = [&](int b) { return ws + b * buf_bytes + (size_t)4 * R * 16; };
+  auto stage = [&](int tile, int b) {
+    const int s0 = tile * kTcRows;
+    for (int idx = tid; idx < 4 * R; idx += blockDim.x) {
+      const int i = idx >> 2, g = idx & 3;
+      const int r = s0 - W - 1 + i;
+      int ys = r >= 0 ? r / W : -((W - 1 - r) / W);
+      const int xs = r - ys * W;
+      ys = ((ys % M) + M) % M;
+      int x = xs - 1;
+      x = x < 0 ? x + M : (x >= M ? x - M : x);
+      cp_async16_zfill(sin(b) + ((size_t)g * R + i) * 16, inm + ((long long)ys * M + x) * 32 + g * 8, true);
+    }
+    for (int idx = tid; idx < 4 * kTcRows; idx += blockDim.x) {
+      const int i = idx >> 2, g = idx & 3;
+      const int so = s0 + i, ys = so / W, xs = so - ys * W;
+      const bool ok = ys < M && xs >= 1 && xs <= M;
+      const long long pix = ok ? (long long)ys * M + (xs - 1) : 0;
+      cp_async16_zfill(sdz(b) + ((size_t)g * kTcRows + i) * 16, dzm + pix * 32 + g * 8, ok);
+    }
+    cp_async_commit();
+  };
+  const int tap = warp, a = tap / 3, bb = tap % 3;
+  const int i0 = W + 1 + (bb - 1) * W + (a - 1);  // the tap's first input row of a tile
+  float acc[2][4][4];
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[mt][nt][q] = 0.0f;
+  // ldmatrix row of this lane: matrix lane / 8, row lane % 8
+  const int lm = lane >> 3, lr = lane & 7;
+  int b = 0;
+  if (t0 < t1) stage(t0, 0);
+  for (int tile = t0; tile < t1; ++tile, b ^= 1) {
+    if (tile + 1 < t1) stage(tile + 1, b ^ 1);
+    else cp_async_commit();
+    asm volatile("cp.async.wait_group 1;" ::: "memory");
+    __syncthreads();
+    const unsigned char* si = sin(b);
+    const unsigned char* sd = sdz(b);
+#pragma unroll 1
+    for (int ks = 0; ks < kTcRows / 16; ++ks) {
+      unsigned af[2][4], bf[4][2];
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt) {
+        // matrices: (o 0-7, k 0-7), (o 8-15, k 0-7), (o 0-7, k 8-15), (o 8-15, k 8-15) of chunks 2mt, 2mt+1
+        const int g = 2 * mt + (lm & 1), k = ks * 16 + (lm >> 1) * 8 + lr;
+        ldsm_x4_t(af[mt], sd + ((size_t)g * kTcRows + k) * 16);
+      }
+#pragma unroll
+      for (int np = 0; np < 2; ++np) {
+        // matrices: (c chunk 2np, k 0-7), (2np, k 8-15), (2np+1, k 0-7), (2np+1, k 8-15)
+        const int g = 2 * np + (lm >> 1), k = ks * 16 + (lm & 1) * 8 + lr;
+        unsigned r4[4];
+        ldsm_x4_t(r4, si + ((size_t)g * R + i0 + k) * 16);
+        bf[2 * np][0] = r4[0];
+        bf[2 * np][1] = r4[1];
+        bf[2 * np + 1][0] = r4[2];
+        bf[2 * np + 1][1] = r4[3];
+      }
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt) mma_bf16(acc[mt][nt], af[mt], bf[nt]);
+    }
+    __syncthreads();  // every warp is done with buffer b before the next stage overwrites it
+  }
+  cp_async_wait_all();
+  const int g = lane >> 2, t4 = lane & 3;
+  float* dst = chunkbuf + (((long long)mb * 9 + tap) * nchunk + chunk) * 1024;
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int o = mt * 16 + g + 8 * (q / 2), c = nt * 8 + 2 * t4 + (q % 2);
+        dst[o * 32 + c] = acc[mt][nt][q];
+      }
+}
+
 }  // namespace cnn
 }  // namespace spadj

@@ -916,6 +916,8 @@ struct Kol : EqImpl {
                                              (int)cnn::kTcSmem));
       SPADJ_CUDA_TRY(p, cudaFuncSetAttribute(cnn::conv32_halo_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)cnn::halo_smem(hm[0].M)));
+      SPADJ_CUDA_TRY(p, cudaFuncSetAttribute(cnn::wgrad32_halo_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)cnn::wgrad_halo_smem(hm[0].M)));
       SPADJ_CUDA_TRY(p, cudaMemsetAsync(pbuf.ptr, 0, sizeof(double) * np, p->stream));
       cnn::convert_kernel<<<64, 256, 0, p->stream>>>(pbuf.as<double>(), wq.as<__nv_bfloat16>(), bq.as<float>());
       spadj_status st = check_launch(p, "closure convert");
@@ -1363,8 +1365,12 @@ struct Kol : EqImpl {
         cnn::dz_kernel<<<cnn_grid(P * co), 256, 0, p->stream>>>(P * co, dh.as<float>(), dact[l].as<float>(), nullptr,
                                                                  dz.as<__nv_bfloat16>());
       if (l == 1 || l == 2) {  // 32 -> 32: tensor cores
-        cnn::wgrad32_mma_kernel<<<dim3(kWgradChunks, 9, nb), 128, 0, p->stream>>>(l, M, ins[l], dz.as<__nv_bfloat16>(),
-                                                                                 chunkbuf.as<float>(), kWgradChunks);
+        if (tc_conv == 1)  // halo-staged operands, ldmatrix fragments, one warp per tap
+          cnn::wgrad32_halo_kernel<<<dim3(kWgradChunks, nb), 288, cnn::wgrad_halo_smem(M), p->stream>>>(
+              M, ins[l], dz.as<__nv_bfloat16>(), chunkbuf.as<float>(), kWgradChunks);
+        else
+          cnn::wgrad32_mma_kernel<<<dim3(kWgradChunks, 9, nb), 128, 0, p->stream>>>(
+              l, M, ins[l], dz.as<__nv_bfloat16>(), chunkbuf.as<float>(), kWgradChunks);
         cnn::wgrad32_finish_kernel<<<dim3(36, nb), 256, 0, p->stream>>>(l, chunkbuf.as<float>(), kWgradChunks,
                                                                         part.as<float>(), np);
         cnn::bgrad32_kernel<<<dim3(32, nb), 256, 0, p->stream>>>(l, M, dz.as<__nv_bfloat16>(), part.as<float>(), np);

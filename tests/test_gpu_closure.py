@@ -186,3 +186,30 @@ def test_step_adjoint_accumulates_the_parameter_gradient():
         y = out
     assert torch.equal(y[:ns], torch.view_as_real(g_ref).reshape(-1))
     assert torch.equal(gp, gp_ref)
+
+
+def test_weight_gradient_forms_agree():
+    """The parameter gradient with the halo-staged ldmatrix weight gradient of the 32 -> 32 layers
+    (default) equals the one with the per-tap mma.sync weight gradient (option 11 = 2, whose
+    convolutions issue the same MMAs as the default ones) up to the FP32 summation order: 1e-5
+    relative in max norm; the state gradient and J, which do not involve the weight gradient,
+    agree to 1e-6 (the two convolution forms agree to that bar or better)."""
+    from paper_2506_14792_gb300 import spadj
+    B, n = 2, 4
+    X0 = dev(np.concatenate([okol.Kolmogorov(N, RE).project(synthetic.kolmogorov_ic(N, 910 + i)).ravel()
+                             for i in range(B)]))
+    obs = torch.stack([X0 * (0.8 ** k) for k in range(1, n + 1)]).contiguous()
+    out = {}
+    for form in (1, 2):
+        p = gpu_problem(B)
+        p.set_option(11, form)
+        p.set_params(dev(synthetic.cnn_params(9, scale_out=1.0)))
+        p.set_observations(list(range(1, n + 1)), obs, N // 2 - 1)
+        g = torch.zeros_like(X0)
+        gp = torch.zeros(p.state_len(2), dtype=torch.float64, device="cuda")
+        J = p.gradient(X0, n, g, objective=spadj.SPADJ_OBJ_FOURDVAR, grad_p=gp)
+        out[form] = (J, host(g), host(gp))
+    assert np.max(np.abs(out[1][0] - out[2][0]) / np.abs(out[2][0])) < 1e-6
+    assert rel_err(out[1][1], out[2][1]) < 1e-6
+    assert rel_err(out[1][2], out[2][2]) < 1e-5
+    print("weight-gradient forms: dJ/dp relative difference", rel_err(out[1][2], out[2][2]))
