@@ -47,7 +47,7 @@ struct Couette : EqImpl {
     int kl = 0, ku = 0, nv = 0;
   };
   BandDev band[2][2];
-  bool band_ok = false, dense_ok = false;
+  bool band_ok = false, dense_ok = false, band_too_wide = false;
   bool band_auto = true;  // the form option 12 = -1 selects: banded when the pencil pairs fill the GPU
   DevBuf Zm, Ym, Gf, dGf, Gb, Fg, Xr, Fr, dXr, dFr, Wr, xbar, src0, partial, edev, sdev, Jdev, slots, wts;
   DevBuf phiRF, phiRA, ginv, nrm, g2;  // resolvent operators of the last frequency, G^-1, per-pencil norms
@@ -452,13 +452,17 @@ struct Couette : EqImpl {
   // operators serve the solves instead.
   spadj_status ensure_band(Problem* p) {
     if (band_ok) return SPADJ_OK;
+    if (band_too_wide) return ensure_dense(p);
     std::string err;
     for (int ord = 1; ord <= order; ++ord)
       for (int dir = 0; dir < 2; ++dir) {
         couhost::BandFactors F;
         if (!couhost::build_band(ops, Kx, Ny, Lx, Ly, nu, ord == 1 ? 1.0 / dt : 1.5 / dt, base, dir == 1, F, &err))
           return p->fail(SPADJ_ERR_INVALID, err);
-        if (F.kl > 32 || F.ku > 64) return ensure_dense(p);
+        if (F.kl > 32 || F.ku > 64) {  // remembered: the factorisation is not repeated on every solve
+          band_too_wide = true;
+          return ensure_dense(p);
+        }
         BandDev& B = band[ord - 1][dir];
         B.kl = F.kl;
         B.ku = F.ku;

@@ -914,10 +914,15 @@ struct Kol : EqImpl {
       }
       SPADJ_CUDA_TRY(p, cudaFuncSetAttribute(cnn::conv32_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)cnn::kTcSmem));
-      SPADJ_CUDA_TRY(p, cudaFuncSetAttribute(cnn::conv32_halo_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)cnn::halo_smem(hm[0].M)));
-      SPADJ_CUDA_TRY(p, cudaFuncSetAttribute(cnn::wgrad32_halo_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)cnn::wgrad_halo_smem(hm[0].M)));
+      // the halo-staged forms need two staging buffers of the grid's halo range: up to a 764-point
+      // grid they fit one CTA; larger grids use the per-tap forms
+      halo_fits = cnn::wgrad_halo_smem(hm[0].M) <= kHaloSmemMax && cnn::halo_smem(hm[0].M) <= kHaloSmemMax;
+      if (halo_fits) {
+        SPADJ_CUDA_TRY(p, cudaFuncSetAttribute(cnn::conv32_halo_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)cnn::halo_smem(hm[0].M)));
+        SPADJ_CUDA_TRY(p, cudaFuncSetAttribute(cnn::wgrad32_halo_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)cnn::wgrad_halo_smem(hm[0].M)));
+      }
       SPADJ_CUDA_TRY(p, cudaMemsetAsync(pbuf.ptr, 0, sizeof(double) * np, p->stream));
       cnn::convert_kernel<<<64, 256, 0, p->stream>>>(pbuf.as<double>(), wq.as<__nv_bfloat16>(), bq.as<float>());
       spadj_status st = check_launch(p, "closure convert");
@@ -1280,16 +1285,18 @@ struct Kol : EqImpl {
   // warp-level mma.sync kernel (modes 0 and 1).
   int sm_count = 0;
   int tc_conv = 1;
+  bool halo_fits = true;                           // the halo-staged network kernels fit this grid
+  static constexpr size_t kHaloSmemMax = 226 * 1024;  // opt-in shared memory per CTA less the static part
   DevBuf cnnerr;
   spadj_status conv32(Problem* p, int l, int mode, const __nv_bfloat16* in, __nv_bfloat16* h, float* da, float* fout) {
     const int M = hm[0].M, nb = nmem;
     const long long P = (long long)M * M * nb;
-    if (tc_conv == 1) {  // operand staged once per tile (halo), nine shifted descriptors
+    if (tc_conv == 1 && halo_fits) {  // operand staged once per tile (halo), nine shifted descriptors
       const long long tiles = (long long)((M * (M + 2) + cnn::kTcRows - 1) / cnn::kTcRows) * nb;
       const int grid = (int)std::min<long long>(tiles, 3LL * sm_count);
       cnn::conv32_halo_kernel<<<grid, 128, cnn::halo_smem(M), p->stream>>>(
           l, M, nb, mode, in, wq.as<__nv_bfloat16>(), bq.as<float>(), h, da, fout, cnnerr.as<int>());
-    } else if (tc_conv == 2) {  // operand gathered per tap
+    } else if (tc_conv != 0) {  // operand gathered per tap
       const long long tiles = (P + cnn::kTcRows - 1) / cnn::kTcRows;
       const int grid = (int)std::min<long long>(tiles, 2LL * sm_count);
       cnn::conv32_tc_kernel<<<grid, 128, cnn::kTcSmem, p->stream>>>(l, M, nb, mode, in, wq.as<__nv_bfloat16>(),
@@ -1365,7 +1372,7 @@ struct Kol : EqImpl {
         cnn::dz_kernel<<<cnn_grid(P * co), 256, 0, p->stream>>>(P * co, dh.as<float>(), dact[l].as<float>(), nullptr,
                                                                  dz.as<__nv_bfloat16>());
       if (l == 1 || l == 2) {  // 32 -> 32: tensor cores
-        if (tc_conv == 1)  // halo-staged operands, ldmatrix fragments, one warp per tap
+        if (tc_conv == 1 && halo_fits)  // halo-staged operands, ldmatrix fragments, one warp per tap
           cnn::wgrad32_halo_kernel<<<dim3(kWgradChunks, nb), 288, cnn::wgrad_halo_smem(M), p->stream>>>(
               M, ins[l], dz.as<__nv_bfloat16>(), chunkbuf.as<float>(), kWgradChunks);
         else
