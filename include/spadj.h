@@ -311,7 +311,9 @@ spadj_status spadj_restrict(spadj_problem* prob, int n_fine, const double* fine,
 /* Test support for the learned closure's tensor-core kernels (not part of the method): one 32 -> 32
  * convolution of hidden layer `layer` (1 or 2) with the problem's current BF16 weights (spadj_set_params)
  * over all batch members of its M x M grid (M = 3 n[0] / 2): mode 0 the pre-activation
- * out = conv(in) + b (forward), mode 1 the input gradient out = conv^T(in) (no bias).  in: device, BF16
+ * out = conv(in) + b (forward), mode 1 the input gradient out = conv^T(in) (no bias), mode 2 the
+ * derivative of the activation the forward epilogue stores, out = 1 - tanh(conv(in) + b)^2 (the
+ * layer's BF16 activations are overwritten in the problem's own buffer).  in: device, BF16
  * bit patterns, [member][y][x][32 channels]; out: device float32, same layout.  Runs the kernel the
  * closure passes use (tcgen05 MMAs with the accumulator in tensor memory, unless spadj_set_option 11
  * selected the mma.sync kernel, which has no mode 0 here).  Synchronises the stream;

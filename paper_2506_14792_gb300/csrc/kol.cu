@@ -1311,9 +1311,12 @@ struct Kol : EqImpl {
 
   spadj_status closure_conv_layer(Problem* p, int l, int mode, const void* in, float* out) {
     if (!closure) return p->fail(SPADJ_ERR_UNSUPPORTED, "closure_conv: the problem has no learned closure");
-    if ((l != 1 && l != 2) || (mode != 0 && mode != 1))
-      return p->fail(SPADJ_ERR_INVALID, "closure_conv: layer must be 1 or 2 and mode 0 or 1");
-    return conv32(p, l, mode == 0 ? 2 : 1, reinterpret_cast<const __nv_bfloat16*>(in), nullptr, nullptr, out);
+    if ((l != 1 && l != 2) || mode < 0 || mode > 2)
+      return p->fail(SPADJ_ERR_INVALID, "closure_conv: layer must be 1 or 2 and mode 0, 1 or 2");
+    const __nv_bfloat16* x = reinterpret_cast<const __nv_bfloat16*>(in);
+    if (mode == 2)  // the forward epilogue: h into the layer's own activation buffer, 1 - tanh^2 into out
+      return conv32(p, l, 0, x, hbuf[l].as<__nv_bfloat16>(), out, nullptr);
+    return conv32(p, l, mode == 0 ? 2 : 1, x, nullptr, nullptr, out);
   }
 
   spadj_status check_cnn(Problem* p) {  // synchronises the stream

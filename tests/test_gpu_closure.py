@@ -149,9 +149,17 @@ def test_tensor_core_convolution_vs_bf16_restated_oracle(layer):
                 assert err < 1e-5, (layer, form, mode, m, err)
     for mode in (0, 1):  # the two staging forms issue the same MMAs in the same order
         assert np.max(np.abs(res[(1, mode)] - res[(2, mode)])) <= 1e-6 * np.max(np.abs(res[(2, mode)]))
+    # the forward epilogue's activation (the exp-based tanh in FP32): 1 - tanh^2 of the kernel's own
+    # FP32 pre-activations, against the FP64 tanh of the same values
+    p.set_option(11, 1)
+    out.zero_()
+    p.closure_conv(layer, 2, inp, out)
+    pre = res[(1, 0)].astype(np.float64)
+    dact_err = np.max(np.abs(host(out) - (1.0 - np.tanh(pre) ** 2)))
+    assert dact_err < 4e-6, dact_err
     # the warp-level mma.sync kernel computes the same input gradient
     p.set_option(11, 0)
-    ref_tc = host(out).copy()
+    ref_tc = res[(1, 1)]
     out.zero_()
     p.closure_conv(layer, 1, inp, out)
     assert np.max(np.abs(host(out) - ref_tc)) <= 1e-5 * np.max(np.abs(ref_tc))
