@@ -387,6 +387,19 @@ spadj_status spadj_timing_report(spadj_problem* prob, int kernel_class, double* 
  * (nullable) the timed duration.  Synchronises the stream; allocates and frees a small buffer. */
 spadj_status spadj_fp64_peak(void* cuda_stream, int iters, double* gflops_host, double* ms_host);
 
+/* Test support (host only, no GPU; not part of the method): the banded step solve of one plane-
+ * Couette pencil computed on the host with the factors and the sweep order the GPU kernel uses
+ * (option 12 = 1), so that the factorisation can be checked against a dense solve without a GPU.
+ * Pencil (kx, ky) = (alpha, beta) >= 0 of the z discretisation with n_z Chebyshev modes (a multiple
+ * of 4 in 8..128), Re = re, base flow `base` (0 plane Couette, 1 plane Poiseuille), shift a0 > 0
+ * (1/dt for SBDF1, 1.5/dt for SBDF2).  transpose = 0: out = [(a0 M + L)^-1 (S1S0 in on the momentum
+ * rows)] restricted to the u, v, w coefficients; transpose = 1: out = S1S0^T [momentum rows of
+ * (a0 M + L)^-H (in on the u, v, w rows)] (the adjoint map).  in, out: host arrays of 3 n_z complex
+ * values (u, v, w blocks; interleaved re, im).  SPADJ_ERR_INVALID for bad arguments or a singular
+ * pencil (spadj_last_error(NULL) says which). */
+spadj_status spadj_couette_pencil_solve_host(int n_z, double alpha, double beta, double re, double a0, int base,
+                                             int transpose, const double* in, double* out);
+
 /* Vector-Jacobian product of the trajectory map (the reverse-mode building block behind
  * spadj_gradient and the torch.autograd binding): grad_x0 = sum_i (dX_{n_i}/dX_0)^T seed_i for
  * cotangents seeds[i] (device, layout [n_seeds][state]) injected at steps seed_steps[i]

@@ -5,6 +5,7 @@
 #include <string>
 #include <vector>
 
+#include "couette_setup.h"
 #include "problem.h"
 #include "revolve.h"
 
@@ -333,6 +334,29 @@ spadj_status spadj_timing_report(spadj_problem* p, int kernel_class, double* ms,
   *ms = p->timing.ms[kernel_class];
   *flops = p->timing.flops[kernel_class];
   *launches = p->timing.launches[kernel_class];
+  return SPADJ_OK;
+}
+
+spadj_status spadj_couette_pencil_solve_host(int n_z, double alpha, double beta, double re, double a0, int base,
+                                             int transpose, const double* in, double* out) {
+  if (n_z < 8 || n_z % 4 != 0 || n_z > 128 || !(re > 0) || !(a0 > 0) || (base != 0 && base != 1) || bad_ptr(in) ||
+      bad_ptr(out) || alpha < 0 || beta < 0) {
+    g_create_error = "couette_pencil_solve_host: n_z a multiple of 4 in 8..128, re > 0, a0 > 0, base 0 or 1, "
+                     "alpha, beta >= 0 and non-NULL arrays";
+    return SPADJ_ERR_INVALID;
+  }
+  try {
+    const spadj::rbhost::Operators o = spadj::rbhost::build_operators(n_z, 3 * n_z / 2, 1.0);
+    std::string err;
+    if (!spadj::couhost::band_solve_host(o, alpha, beta, 1.0 / re, a0, base, transpose != 0,
+                                         reinterpret_cast<const std::complex<double>*>(in),
+                                         reinterpret_cast<std::complex<double>*>(out), &err)) {
+      g_create_error = err;
+      return SPADJ_ERR_INVALID;
+    }
+  } catch (const std::bad_alloc&) {
+    return SPADJ_ERR_NOMEM;
+  }
   return SPADJ_OK;
 }
 

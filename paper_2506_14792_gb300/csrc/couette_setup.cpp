@@ -507,6 +507,58 @@ bool build_band(const rbhost::Operators& o, int Kx, int Ny, double Lx, double Ly
   return true;
 }
 
+bool band_solve_host(const rbhost::Operators& o, double al, double be, double nu, double a0, int base, bool transpose,
+                     const cd* in, cd* out, std::string* err) {
+  const int N = o.N, nv = 4 * N + 7;
+  const bool mean = al == 0.0 && be == 0.0;
+  std::vector<double> ZS, UP;
+  base_flow(o, base, ZS, UP);
+  std::vector<cd> A, B;
+  band_matrix(o, ZS, UP, al, be, mean, nu, a0, transpose, A, B);
+  int kl = 0, ku = 0;
+  band_widths(B, nv, kl, ku);
+  std::vector<int> piv;
+  if (!band_lu(B, nv, kl, ku, piv)) {
+    if (err) *err = "couette: singular banded pencil matrix";
+    return false;
+  }
+  std::vector<double> ssb((size_t)N * 5, 0.0);
+  for (int r = 0; r < N; ++r)
+    for (int d = 0; d < 5 && r + d < N; ++d) ssb[(size_t)r * 5 + d] = o.SS[(size_t)r * N + r + d];
+  std::vector<cd> y(nv, cd(0.0, 0.0));
+  const int o_rows = mean ? 0 : 1;  // position of mode 0's momentum rows in A'
+  for (int f = 0; f < 3; ++f)
+    for (int n = 0; n < N; ++n) {
+      if (!transpose) {
+        cd b = 0.0;
+        for (int d = 0; d < 5 && n + d < N; ++d) b += ssb[(size_t)n * 5 + d] * in[f * N + n + d];
+        y[o_rows + 4 * n + f] = b;
+      } else {
+        y[nv - 1 - (1 + 4 * n + f)] = in[f * N + n] - (n + 2 < N ? in[f * N + n + 2] : cd(0.0, 0.0));
+      }
+    }
+  // the sweeps of the GPU kernel: interchange and multipliers, 1/U_jj, row-scaled U by columns
+  for (int j = 0; j < nv; ++j) {
+    if (piv[j]) std::swap(y[j], y[j + piv[j]]);
+    for (int i = j + 1; i <= std::min(nv - 1, j + kl); ++i) y[i] -= B[(size_t)i * nv + j] * y[j];
+  }
+  for (int j = 0; j < nv; ++j) y[j] *= 1.0 / B[(size_t)j * nv + j];
+  for (int j = nv - 1; j >= 0; --j)
+    for (int i = std::max(0, j - kl - ku); i < j; ++i)
+      y[i] -= (B[(size_t)i * nv + j] / B[(size_t)i * nv + i]) * y[j];
+  for (int f = 0; f < 3; ++f)
+    for (int n = 0; n < N; ++n) {
+      if (!transpose) {
+        out[f * N + n] = y[1 + 4 * n + f] - (n >= 2 ? y[1 + 4 * (n - 2) + f] : cd(0.0, 0.0));
+      } else {
+        cd v = 0.0;
+        for (int d = 0; d < 5 && n - d >= 0; ++d) v += ssb[(size_t)(n - d) * 5 + d] * y[nv - 1 - (o_rows + 4 * (n - d) + f)];
+        out[f * N + n] = v;
+      }
+    }
+  return true;
+}
+
 bool build_evp(const rbhost::Operators& o, int base, int P, const double* prm, const double* shift,
                std::vector<double>& T, std::vector<double>& RH, std::string* err) {
   const int N = o.N, nv = 4 * N + 7, H = 3 * N;

@@ -80,6 +80,14 @@ struct BandFactors {
 bool build_band(const rbhost::Operators& o, int Kx, int Ny, double Lx, double Ly, double nu, double a0, int base,
                 bool hermitian, BandFactors& F, std::string* err);
 
+// One pencil's banded solve on the host with the arithmetic of the GPU kernel (test support):
+// x = [A'^-1 (S1S0 v on the momentum rows)] recombined to the prognostic coefficients (transpose = 0),
+// or v = S1S0^T [momentum rows of (J A'^H J)^-1 J (R^T x)] (transpose = 1), for the pencil
+// (alpha, beta) at a0 (real); v, x: 3N complex (u, v, w coefficients), the ky >= 0 member (no
+// projection).  False (and err) if the pencil is singular.
+bool band_solve_host(const rbhost::Operators& o, double al, double be, double nu, double a0, int base, bool transpose,
+                     const std::complex<double>* in, std::complex<double>* out, std::string* err);
+
 // Shift-invert operators of P eigenvalue pencils (prm[p] = alpha, beta, Re; shift[p] = sigma as
 // (re, im)) of the base flow `base`: with A_p = sigma_p M + L_p (one LU per pencil),
 //   T[p]  = A_p^-1 [S1S0 on the u, v, w momentum rows]   ((4N + 7) x 3N),

@@ -80,6 +80,8 @@ _SIGS = {
     "spadj_set_params": (ctypes.c_int, [_vp, _vp]),
     "spadj_restrict": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp]),
     "spadj_closure_conv": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp]),
+    "spadj_couette_pencil_solve_host": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                                        ctypes.c_double, ctypes.c_int, ctypes.c_int, _vp, _vp]),
     "spadj_adam": (ctypes.c_int, [_vp, _vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                   ctypes.c_double, _vp, _vp, _vp]),
     "spadj_checkpoint_schedule": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
@@ -158,6 +160,22 @@ def checkpoint_schedule(n_steps, slots, host_slots=0):
     buf = (ctypes.c_int * (4 * n.value))()
     _chk(None, call(buf, n.value))
     return [tuple(buf[4 * i:4 * i + 4]) for i in range(n.value)]
+
+
+def couette_pencil_solve_host(n_z, alpha, beta, re, a0, v, transpose=False, base=0):
+    """Host banded step solve of one plane-Couette pencil (test support; no GPU): v is a numpy
+    complex array of 3 n_z values (u, v, w blocks); returns the solution (or the adjoint map's
+    result) as a new numpy array."""
+    import numpy as np
+    src = np.ascontiguousarray(v, dtype=np.complex128)
+    if src.size != 3 * n_z:
+        raise ValueError("couette_pencil_solve_host: v must hold 3 n_z complex values")
+    out = np.zeros_like(src)
+    _chk(None, lib().spadj_couette_pencil_solve_host(int(n_z), float(alpha), float(beta), float(re), float(a0),
+                                                      int(base), int(bool(transpose)),
+                                                      src.ctypes.data_as(ctypes.c_void_p),
+                                                      out.ctypes.data_as(ctypes.c_void_p)))
+    return out
 
 
 CK_ADVANCE, CK_STORE, CK_RESTORE, CK_ADJOINT, CK_FREE, CK_OBJECTIVE = range(6)
