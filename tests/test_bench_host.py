@@ -61,6 +61,12 @@ def test_hbm_fraction(bench):
     (["--workload", "couette_resolvent", "--nsteps", "20", "--omega", "0.3"],
      "couette3d_64x32x32_Re1000_resolvent_omega0.3_20iter", lambda w: w.units_per_step() == 1024 * 20),
     ([], "rayleigh_benard2d_256x64_Ra1e6_rk222_2000steps", lambda w: w.scheme == "rk222" and not w.dt_blocks),
+    (["--workload", "burgers", "--slots", "32"], "burgers1d_N256_sbdf2_1000steps_ckpt32",
+     lambda w: w.slots == 32 and "binomial" in w.config()["checkpointing"]),
+    (["--workload", "kolmogorov", "--slots", "40"], "kolmogorov2d_batch64_mixed128-512_Re100_sbdf2_2000steps_4dvar8_seg40",
+     lambda w: w.slots == 40 and "segments" in w.config()["checkpointing"]),
+    (["--workload", "closure", "--quick"], "closure_kolmogorov64_cnn32_Re1000_fine1024_128windows_16steps_quick",
+     lambda w: w.quick and w.units_per_step() == 128 * 16),
 ])
 def test_workload_variants_from_the_command_line(bench, argv, name, check):
     """The variant flags build the workload they name (the run itself is replaced by a probe)."""
@@ -79,7 +85,9 @@ def test_workload_variants_from_the_command_line(bench, argv, name, check):
                                   ["--workload", "rb", "--batch", "4"],
                                   ["--workload", "rb", "--scheme", "sbdf2"],
                                   ["--workload", "rb", "--op", "hvp"],
-                                  ["--workload", "couette", "--omega", "1.0"]])
+                                  ["--workload", "couette", "--omega", "1.0"],
+                                  ["--workload", "rb", "--slots", "8"],
+                                  ["--workload", "burgers", "--quick"]])
 def test_variant_flags_refused_where_they_do_not_apply(bench, argv):
     saved = sys.argv
     sys.argv = ["bench.py"] + argv
