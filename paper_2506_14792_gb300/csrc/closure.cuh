@@ -226,7 +226,8 @@ __global__ void __launch_bounds__(128) fwd0_kernel(int M, const __nv_bfloat16* _
 // of W[0][c][a][b] dz(x - a + 1, y - b + 1), the nine dz values read once, the same sums in the
 // same order as dgrad_kernel<32, 1>, written as eight 16-byte stores.
 __global__ void __launch_bounds__(128) dgrad3_kernel(int M, const __nv_bfloat16* __restrict__ dz,
-                                                     const __nv_bfloat16* __restrict__ wq, float* __restrict__ din) {
+                                                     const __nv_bfloat16* __restrict__ wq, float* __restrict__ din,
+                                                     const float* __restrict__ dact, __nv_bfloat16* __restrict__ dzo) {
   __shared__ float ws[9][kHid];
   for (int i = threadIdx.x; i < 9 * kHid; i += blockDim.x) {
     const int t = i / kHid, c = i - t * kHid;  // W[0][a][b][c] at (a * 3 + b) * 32 + c
@@ -243,7 +244,7 @@ __global__ void __launch_bounds__(128) dgrad3_kernel(int M, const __nv_bfloat16*
 #pragma unroll
     for (int b = 0; b < 3; ++b)
       v[a * 3 + b] = __bfloat162float(dz[base + (long long)wrap1(y - b + 1, M) * M + wrap1(x - a + 1, M)]);
-  float* dst = din + (base + q) * kHid;
+  const long long o = (base + q) * kHid;
 #pragma unroll
   for (int c0 = 0; c0 < kHid; c0 += 4) {
     float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
@@ -251,7 +252,15 @@ __global__ void __launch_bounds__(128) dgrad3_kernel(int M, const __nv_bfloat16*
     for (int t = 0; t < 9; ++t)
 #pragma unroll
       for (int e = 0; e < 4; ++e) acc[e] = fmaf(ws[t][c0 + e], v[t], acc[e]);
-    *reinterpret_cast<float4*>(dst + c0) = make_float4(acc[0], acc[1], acc[2], acc[3]);
+    if (dzo) {  // the previous layer's BF16 cotangent bf16(din * dact), the separate dz pass fused in
+      const float4 d = *reinterpret_cast<const float4*>(dact + o + c0);
+      uint2 zv;
+      zv.x = pack2(__float2bfloat16_rn(acc[0] * d.x), __float2bfloat16_rn(acc[1] * d.y));
+      zv.y = pack2(__float2bfloat16_rn(acc[2] * d.z), __float2bfloat16_rn(acc[3] * d.w));
+      *reinterpret_cast<uint2*>(dzo + o + c0) = zv;
+    } else {
+      *reinterpret_cast<float4*>(din + o + c0) = make_float4(acc[0], acc[1], acc[2], acc[3]);
+    }
   }
 }
 
@@ -608,7 +617,9 @@ __device__ __forceinline__ bool tc_wait(unsigned long long* bar, unsigned parity
 }
 
 // mode 0: forward hidden layer, out = tanh(D + b) as BF16 h and 1 - tanh^2 as FP32 dact (nullable);
-// mode 1: input gradient, din = D (FP32); mode 2: pre-activation zout = D + b (FP32, for tests).
+// mode 1: input gradient, din = D (FP32); mode 2: pre-activation zout = D + b (FP32, for tests);
+// mode 3: input gradient times the previous layer's activation derivative, written as that
+// layer's BF16 cotangent h = bf16(D * dact) (dact read): the separate dz pass fused into the epilogue.
 __global__ void __launch_bounds__(128) conv32_tc_kernel(int l, int M, int nb, int mode,
                                                         const __nv_bfloat16* __restrict__ in,
                                                         const __nv_bfloat16* __restrict__ wq,
@@ -627,7 +638,7 @@ __global__ void __launch_bounds__(128) conv32_tc_kernel(int l, int M, int nb, in
   // B[n][k = tap * 32 + kc]: forward W[o = n][tap][c = kc]; gradient W[o = kc][tap][c = n]
   for (int i = tid; i < 32 * kTcK; i += blockDim.x) {
     const int n = i / kTcK, k = i - n * kTcK, tap = k >> 5, kc = k & 31;
-    const __nv_bfloat16 v = mode == 1 ? W[(kc * 9 + tap) * 32 + n] : W[(n * 9 + tap) * 32 + kc];
+    const __nv_bfloat16 v = (mode & 1) ? W[(kc * 9 + tap) * 32 + n] : W[(n * 9 + tap) * 32 + kc];
     *reinterpret_cast<__nv_bfloat16*>(sB + tc_core_off(n, k)) = v;
   }
   if (tid == 0) mbar_init(&bar, 1);
@@ -655,7 +666,7 @@ __global__ void __launch_bounds__(128) conv32_tc_kernel(int l, int M, int nb, in
 #pragma unroll
     for (int tap = 0; tap < 9; ++tap) {
       const int a = tap / 3, b = tap % 3;
-      const int dx = mode == 1 ? 1 - a : a - 1, dy = mode == 1 ? 1 - b : b - 1;
+      const int dx = (mode & 1) ? 1 - a : a - 1, dy = (mode & 1) ? 1 - b : b - 1;
       const int xx = wrap1(x + dx, M), yy = wrap1(y + dy, M);
       const __nv_bfloat16* src = in + (mb * P + (long long)yy * M + xx) * 32;
 #pragma unroll
@@ -725,6 +736,18 @@ __global__ void __launch_bounds__(128) conv32_tc_kernel(int l, int M, int nb, in
                 make_float4(1.0f - t[4] * t[4], 1.0f - t[5] * t[5], 1.0f - t[6] * t[6], 1.0f - t[7] * t[7]);
           }
         }
+      } else if (mode == 3) {  // the next layer's BF16 cotangent dz = din * dact, dact read from `dact`
+#pragma unroll
+        for (int n = 0; n < 32; n += 8) {
+          const float4 d0 = *reinterpret_cast<const float4*>(dact + p * 32 + n);
+          const float4 d1 = *reinterpret_cast<const float4*>(dact + p * 32 + n + 4);
+          uint4 zv;
+          zv.x = pack2(__float2bfloat16_rn(__uint_as_float(r[n]) * d0.x), __float2bfloat16_rn(__uint_as_float(r[n + 1]) * d0.y));
+          zv.y = pack2(__float2bfloat16_rn(__uint_as_float(r[n + 2]) * d0.z), __float2bfloat16_rn(__uint_as_float(r[n + 3]) * d0.w));
+          zv.z = pack2(__float2bfloat16_rn(__uint_as_float(r[n + 4]) * d1.x), __float2bfloat16_rn(__uint_as_float(r[n + 5]) * d1.y));
+          zv.w = pack2(__float2bfloat16_rn(__uint_as_float(r[n + 6]) * d1.z), __float2bfloat16_rn(__uint_as_float(r[n + 7]) * d1.w));
+          *reinterpret_cast<uint4*>(h + p * 32 + n) = zv;
+        }
       } else {
         const float bs = mode == 2 ? 1.0f : 0.0f;
 #pragma unroll
@@ -781,7 +804,7 @@ __global__ void __launch_bounds__(128) conv32_halo_kernel(int l, int M, int nb, 
   const __nv_bfloat16* Wt = wq + w_off(l);
   for (int i = tid; i < 32 * kTcK; i += blockDim.x) {
     const int n = i / kTcK, k = i - n * kTcK, tap = k >> 5, kc = k & 31;
-    const __nv_bfloat16 v = mode == 1 ? Wt[(kc * 9 + tap) * 32 + n] : Wt[(n * 9 + tap) * 32 + kc];
+    const __nv_bfloat16 v = (mode & 1) ? Wt[(kc * 9 + tap) * 32 + n] : Wt[(n * 9 + tap) * 32 + kc];
     *reinterpret_cast<__nv_bfloat16*>(sB + tc_core_off(n, k)) = v;
   }
   if (tid == 0) mbar_init(&bar, 1);
@@ -835,7 +858,7 @@ __global__ void __launch_bounds__(128) conv32_halo_kernel(int l, int M, int nb, 
       for (int kk = 0; kk < kTcK / 16; ++kk) {
         const int tap = kk >> 1, half = kk & 1, a = tap / 3, b = tap % 3;
         const int sh = (b - 1) * W + (a - 1);
-        const int i0 = W + 1 + (mode == 1 ? -sh : sh);
+        const int i0 = W + 1 + ((mode & 1) ? -sh : sh);
         const unsigned long long ad = tc_smem_desc(aaddr + (unsigned)((2 * half * R + i0) * 16), (unsigned)R * 16, 128);
         const unsigned long long bd = tc_smem_desc(baddr + kk * 256, 128, kTcKg * 128);
         asm volatile(
@@ -888,6 +911,18 @@ __global__ void __launch_bounds__(128) conv32_halo_kernel(int l, int M, int nb, 
             *reinterpret_cast<float4*>(dact + p * 32 + n + 4) =
                 make_float4(1.0f - t[4] * t[4], 1.0f - t[5] * t[5], 1.0f - t[6] * t[6], 1.0f - t[7] * t[7]);
           }
+        }
+      } else if (mode == 3) {  // the next layer's BF16 cotangent dz = din * dact, dact read from `dact`
+#pragma unroll
+        for (int n = 0; n < 32; n += 8) {
+          const float4 d0 = *reinterpret_cast<const float4*>(dact + p * 32 + n);
+          const float4 d1 = *reinterpret_cast<const float4*>(dact + p * 32 + n + 4);
+          uint4 zv;
+          zv.x = pack2(__float2bfloat16_rn(__uint_as_float(r[n]) * d0.x), __float2bfloat16_rn(__uint_as_float(r[n + 1]) * d0.y));
+          zv.y = pack2(__float2bfloat16_rn(__uint_as_float(r[n + 2]) * d0.z), __float2bfloat16_rn(__uint_as_float(r[n + 3]) * d0.w));
+          zv.z = pack2(__float2bfloat16_rn(__uint_as_float(r[n + 4]) * d1.x), __float2bfloat16_rn(__uint_as_float(r[n + 5]) * d1.y));
+          zv.w = pack2(__float2bfloat16_rn(__uint_as_float(r[n + 6]) * d1.z), __float2bfloat16_rn(__uint_as_float(r[n + 7]) * d1.w));
+          *reinterpret_cast<uint4*>(h + p * 32 + n) = zv;
         }
       } else {
         const float bs = mode == 2 ? 1.0f : 0.0f;

@@ -760,7 +760,7 @@ struct Kol : EqImpl {
   int nmem = 0;
   long long state_size = 0, mix_size = 0, grid_size = 0;
   int closure = 0;
-  DevBuf gridW, gridG, corr, xq, hbuf[3], dact[3], dh, dz, pbuf, wq, bq, part, gp, chunkbuf;
+  DevBuf gridW, gridG, corr, xq, hbuf[3], dact[3], dh, dz, dz2, pbuf, wq, bq, part, gp, chunkbuf;
   static constexpr int kWgradChunks = 8;
   int Lmax = 0, Mmax = 0, Nmax = 0, Kxmax = 0;
   double Re = 100.0, dt = 0;
@@ -899,6 +899,7 @@ struct Kol : EqImpl {
       }
       SPADJ_CUDA_TRY(p, dh.ensure(sizeof(float) * act));
       SPADJ_CUDA_TRY(p, dz.ensure(sizeof(__nv_bfloat16) * act));
+      SPADJ_CUDA_TRY(p, dz2.ensure(sizeof(__nv_bfloat16) * act));
       SPADJ_CUDA_TRY(p, pbuf.ensure(sizeof(double) * np));
       SPADJ_CUDA_TRY(p, wq.ensure(sizeof(__nv_bfloat16) * np));
       SPADJ_CUDA_TRY(p, bq.ensure(sizeof(float) * np));
@@ -1367,39 +1368,49 @@ struct Kol : EqImpl {
       else
         conv32(p, l, 0, ins[l], hbuf[l].as<__nv_bfloat16>(), dact[l].as<float>(), nullptr);
     }
+    // The tensor-core convolutions and the layer-3 input gradient write the next layer's BF16
+    // cotangent dz = bf16(din * dact) from their epilogue (two dz buffers in turn); the mma.sync form
+    // writes din in FP32 and a separate pass forms dz.
+    const bool fuse = tc_conv != 0;
+    __nv_bfloat16* dzb[2] = {dz.as<__nv_bfloat16>(), dz2.as<__nv_bfloat16>()};
+    int cur = 0;
     for (int l = cnn::kLayers - 1; l >= 0; --l) {
       const int co = (l == cnn::kLayers - 1) ? 1 : cnn::kHid, ci = (l == 0) ? 1 : cnn::kHid;
+      __nv_bfloat16* dzc = dzb[cur];
       if (l == cnn::kLayers - 1)
-        cnn::dz_kernel<<<cnn_grid(P), 256, 0, p->stream>>>(P, nullptr, nullptr, gridG.as<double>(), dz.as<__nv_bfloat16>());
-      else
+        cnn::dz_kernel<<<cnn_grid(P), 256, 0, p->stream>>>(P, nullptr, nullptr, gridG.as<double>(), dzc);
+      else if (!fuse)
         cnn::dz_kernel<<<cnn_grid(P * co), 256, 0, p->stream>>>(P * co, dh.as<float>(), dact[l].as<float>(), nullptr,
-                                                                 dz.as<__nv_bfloat16>());
+                                                                 dzc);
       if (l == 1 || l == 2) {  // 32 -> 32: tensor cores
         if (tc_conv == 1 && halo_fits)  // halo-staged operands, ldmatrix fragments, one warp per tap
           cnn::wgrad32_halo_kernel<<<dim3(kWgradChunks, nb), 288, cnn::wgrad_halo_smem(M), p->stream>>>(
-              M, ins[l], dz.as<__nv_bfloat16>(), chunkbuf.as<float>(), kWgradChunks);
+              M, ins[l], dzc, chunkbuf.as<float>(), kWgradChunks);
         else
           cnn::wgrad32_mma_kernel<<<dim3(kWgradChunks, 9, nb), 128, 0, p->stream>>>(
-              l, M, ins[l], dz.as<__nv_bfloat16>(), chunkbuf.as<float>(), kWgradChunks);
+              l, M, ins[l], dzc, chunkbuf.as<float>(), kWgradChunks);
         cnn::wgrad32_finish_kernel<<<dim3(36, nb), 256, 0, p->stream>>>(l, chunkbuf.as<float>(), kWgradChunks,
                                                                         part.as<float>(), np);
-        cnn::bgrad32_kernel<<<dim3(32, nb), 256, 0, p->stream>>>(l, M, dz.as<__nv_bfloat16>(), part.as<float>(), np);
-        conv32(p, l, 1, dz.as<__nv_bfloat16>(), nullptr, nullptr, dh.as<float>());
+        cnn::bgrad32_kernel<<<dim3(32, nb), 256, 0, p->stream>>>(l, M, dzc, part.as<float>(), np);
+        if (fuse)
+          conv32(p, l, 3, dzc, dzb[cur ^ 1], dact[l - 1].as<float>(), nullptr);
+        else
+          conv32(p, l, 1, dzc, nullptr, nullptr, dh.as<float>());
+      } else if (l == 0) {
+        cnn::wgrad_kernel<1, cnn::kHid><<<dim3(4, nb, cnn::kThinSplits), 256, 0, p->stream>>>(
+            l, M, ins[l], dzc, chunkbuf.as<float>());
+        cnn::wgrad_finish_kernel<<<nb, 320, 0, p->stream>>>(l, chunkbuf.as<float>(), part.as<float>(), np);
+        cnn::dgrad_kernel<1, cnn::kHid><<<thin_grid(M, ci), 256, 0, p->stream>>>(
+            l, M, dzc, wq.as<__nv_bfloat16>(), nullptr, corr.as<double>());
       } else {
-        if (l == 0) {
-          cnn::wgrad_kernel<1, cnn::kHid><<<dim3(4, nb, cnn::kThinSplits), 256, 0, p->stream>>>(
-              l, M, ins[l], dz.as<__nv_bfloat16>(), chunkbuf.as<float>());
-          cnn::wgrad_finish_kernel<<<nb, 320, 0, p->stream>>>(l, chunkbuf.as<float>(), part.as<float>(), np);
-          cnn::dgrad_kernel<1, cnn::kHid><<<thin_grid(M, ci), 256, 0, p->stream>>>(
-              l, M, dz.as<__nv_bfloat16>(), wq.as<__nv_bfloat16>(), nullptr, corr.as<double>());
-        } else {
-          cnn::wgrad_kernel<cnn::kHid, 1><<<dim3(4, nb, cnn::kThinSplits), 256, 0, p->stream>>>(
-              l, M, ins[l], dz.as<__nv_bfloat16>(), chunkbuf.as<float>());
-          cnn::wgrad_finish_kernel<<<nb, 320, 0, p->stream>>>(l, chunkbuf.as<float>(), part.as<float>(), np);
-          cnn::dgrad3_kernel<<<pixel_grid(M), 128, 0, p->stream>>>(M, dz.as<__nv_bfloat16>(), wq.as<__nv_bfloat16>(),
-                                                                    dh.as<float>());
-        }
+        cnn::wgrad_kernel<cnn::kHid, 1><<<dim3(4, nb, cnn::kThinSplits), 256, 0, p->stream>>>(
+            l, M, ins[l], dzc, chunkbuf.as<float>());
+        cnn::wgrad_finish_kernel<<<nb, 320, 0, p->stream>>>(l, chunkbuf.as<float>(), part.as<float>(), np);
+        cnn::dgrad3_kernel<<<pixel_grid(M), 128, 0, p->stream>>>(
+            M, dzc, wq.as<__nv_bfloat16>(), fuse ? nullptr : dh.as<float>(), fuse ? dact[l - 1].as<float>() : nullptr,
+            fuse ? dzb[cur ^ 1] : nullptr);
       }
+      if (fuse) cur ^= 1;
     }
     cnn::reduce_params_kernel<<<64, 256, 0, p->stream>>>(part.as<float>(), nb, np, gp.as<double>());
     closure_rows_kernel<<<dim3(M, nb), kKolThreads, smem, p->stream>>>(A, corr.as<double>(), 1);
@@ -1657,7 +1668,7 @@ struct Kol : EqImpl {
   }
 
   ~Kol() override {
-    for (DevBuf* b : {&gridW, &gridG, &corr, &xq, &hbuf[0], &hbuf[1], &hbuf[2], &dact[0], &dact[1], &dact[2], &dh, &dz,
+    for (DevBuf* b : {&gridW, &gridG, &corr, &xq, &hbuf[0], &hbuf[1], &hbuf[2], &dact[0], &dact[1], &dact[2], &dh, &dz, &dz2,
                       &pbuf, &wq, &bq, &part, &gp, &chunkbuf})
       b->release();
     for (DevBuf* b : {&dmem, &tables, &Xr[0], &Xr[1], &Fr[0], &Fr[1], &Yr[0], &Yr[1], &mixA, &mixB, &ctr, &trajbuf,
