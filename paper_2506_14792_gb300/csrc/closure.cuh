@@ -531,10 +531,16 @@ __global__ void __launch_bounds__(128) wgrad32_mma_kernel(int l, int M, const __
   for (int i = threadIdx.x; i < 1024; i += blockDim.x) dst[i] = ((red[0][i] + red[1][i]) + red[2][i]) + red[3][i];
 }
 
-// sum the chunks of wgrad32_mma_kernel in order into part[mb][w_off(l) + flat W index]
+// sum the chunks of wgrad32_mma_kernel / wgrad32_halo_kernel in order into part[mb][w_off(l) + flat W
+// index]; with bpart (the halo kernel's partial bias sums [mb][chunk][32]) the bias gradient too
 __global__ void wgrad32_finish_kernel(int l, const float* __restrict__ chunkbuf, int nchunk, float* __restrict__ part,
-                                      int npar) {
+                                      int npar, const float* __restrict__ bpart) {
   const int mb = blockIdx.y;
+  if (bpart && blockIdx.x == 0 && threadIdx.x < 32) {
+    float s = 0.0f;
+    for (int k = 0; k < nchunk; ++k) s += bpart[((long long)mb * nchunk + k) * 32 + threadIdx.x];
+    part[(long long)mb * npar + w_off(l) + 32 * 32 * 9 + threadIdx.x] = s;
+  }
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 9 * 1024; i += gridDim.x * blockDim.x) {
     const int tap = i / 1024, oc = i % 1024, o = oc / 32, c = oc % 32;
     const float* src = chunkbuf + (((long long)mb * 9 + tap) * nchunk) * 1024 + oc;
@@ -960,9 +966,10 @@ __host__ __device__ constexpr size_t wgrad_halo_smem(int M) {
   return (size_t)2 * 4 * (halo_range(M) + kTcRows) * 16;
 }
 
-__global__ void __launch_bounds__(288) wgrad32_halo_kernel(int M, const __nv_bfloat16* __restrict__ in,
+__global__ void __launch_bounds__(288, 3) wgrad32_halo_kernel(int M, const __nv_bfloat16* __restrict__ in,
                                                            const __nv_bfloat16* __restrict__ dz,
-                                                           float* __restrict__ chunkbuf, int nchunk) {
+                                                           float* __restrict__ chunkbuf, int nchunk,
+                                                           float* __restrict__ bpart) {
   extern __shared__ __align__(128) unsigned char ws[];
   const int W = M + 2, R = halo_range(M);
   const size_t buf_bytes = (size_t)4 * (R + kTcRows) * 16;
@@ -1008,6 +1015,9 @@ __global__ void __launch_bounds__(288) wgrad32_halo_kernel(int M, const __nv_bfl
       for (int q = 0; q < 4; ++q) acc[mt][nt][q] = 0.0f;
   // ldmatrix row of this lane: matrix lane / 8, row lane % 8
   const int lm = lane >> 3, lr = lane & 7;
+  // bias gradient db[o = lane] = sum_p dz[p][o] from the same staged rows: warp w takes rows
+  // w, w + 9, ... of every tile
+  float bacc = 0.0f;
   int b = 0;
   if (t0 < t1) stage(t0, 0);
   for (int tile = t0; tile < t1; ++tile, b ^= 1) {
@@ -1042,9 +1052,20 @@ __global__ void __launch_bounds__(288) wgrad32_halo_kernel(int M, const __nv_bfl
 #pragma unroll
         for (int nt = 0; nt < 4; ++nt) mma_bf16(acc[mt][nt], af[mt], bf[nt]);
     }
+    for (int k = warp; k < kTcRows; k += 9)
+      bacc += __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(sd + ((size_t)(lane >> 3) * kTcRows + k) * 16 +
+                                                                         (lane & 7) * 2));
     __syncthreads();  // every warp is done with buffer b before the next stage overwrites it
   }
   cp_async_wait_all();
+  __shared__ float bred[9][32];
+  bred[warp][lane] = bacc;
+  __syncthreads();
+  if (warp == 0) {  // the warps' partial bias sums in warp order
+    float sb = 0.0f;
+    for (int w = 0; w < 9; ++w) sb += bred[w][lane];
+    bpart[((long long)mb * nchunk + chunk) * 32 + lane] = sb;
+  }
   const int g = lane >> 2, t4 = lane & 3;
   float* dst = chunkbuf + (((long long)mb * 9 + tap) * nchunk + chunk) * 1024;
 #pragma unroll

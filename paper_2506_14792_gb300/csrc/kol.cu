@@ -905,7 +905,8 @@ struct Kol : EqImpl {
       SPADJ_CUDA_TRY(p, bq.ensure(sizeof(float) * np));
       SPADJ_CUDA_TRY(p, part.ensure(sizeof(float) * np * nmem));
       SPADJ_CUDA_TRY(p, gp.ensure(sizeof(double) * np));
-      SPADJ_CUDA_TRY(p, chunkbuf.ensure(sizeof(float) * (size_t)nmem * 9 * kWgradChunks * 1024));
+      // weight partials [member][tap][chunk][32 x 32], then the bias partials [member][chunk][32]
+      SPADJ_CUDA_TRY(p, chunkbuf.ensure(sizeof(float) * (size_t)nmem * kWgradChunks * (9 * 1024 + 32)));
       SPADJ_CUDA_TRY(p, cnnerr.ensure(sizeof(int)));
       SPADJ_CUDA_TRY(p, cudaMemsetAsync(cnnerr.ptr, 0, sizeof(int), p->stream));
       {
@@ -1383,15 +1384,18 @@ struct Kol : EqImpl {
         cnn::dz_kernel<<<cnn_grid(P * co), 256, 0, p->stream>>>(P * co, dh.as<float>(), dact[l].as<float>(), nullptr,
                                                                  dzc);
       if (l == 1 || l == 2) {  // 32 -> 32: tensor cores
-        if (tc_conv == 1 && halo_fits)  // halo-staged operands, ldmatrix fragments, one warp per tap
+        // the halo kernel also sums the bias gradient from its staged dz rows
+        float* bpart = chunkbuf.as<float>() + (size_t)nb * 9 * kWgradChunks * 1024;
+        const bool halo = tc_conv == 1 && halo_fits;
+        if (halo)  // halo-staged operands, ldmatrix fragments, one warp per tap
           cnn::wgrad32_halo_kernel<<<dim3(kWgradChunks, nb), 288, cnn::wgrad_halo_smem(M), p->stream>>>(
-              M, ins[l], dzc, chunkbuf.as<float>(), kWgradChunks);
+              M, ins[l], dzc, chunkbuf.as<float>(), kWgradChunks, bpart);
         else
           cnn::wgrad32_mma_kernel<<<dim3(kWgradChunks, 9, nb), 128, 0, p->stream>>>(
               l, M, ins[l], dzc, chunkbuf.as<float>(), kWgradChunks);
         cnn::wgrad32_finish_kernel<<<dim3(36, nb), 256, 0, p->stream>>>(l, chunkbuf.as<float>(), kWgradChunks,
-                                                                        part.as<float>(), np);
-        cnn::bgrad32_kernel<<<dim3(32, nb), 256, 0, p->stream>>>(l, M, dzc, part.as<float>(), np);
+                                                                        part.as<float>(), np, halo ? bpart : nullptr);
+        if (!halo) cnn::bgrad32_kernel<<<dim3(32, nb), 256, 0, p->stream>>>(l, M, dzc, part.as<float>(), np);
         if (fuse)
           conv32(p, l, 3, dzc, dzb[cur ^ 1], dact[l - 1].as<float>(), nullptr);
         else
