@@ -648,7 +648,21 @@ struct RB : EqImpl {
   //   f_i = F(x_i) (i < S),  X_{n+1} = x_S.
 
   // out = sum_t a_t in_t (n >= 1); in[0] may be out itself (accumulation)
+  int comb_grid() const { return (int)std::min<size_t>((ns + 255) / 256, 1024); }
+
+  // out = sum_t a_t in_t (in[0] may be out): one launch for up to kCombMax terms
   spadj_status lincomb(Problem* p, double2* out, int n, const double2* const* in, const double* a) {
+    if (n >= 1 && n <= kCombMax) {
+      CombArgs A{};
+      for (int t = 0; t < n; ++t) { A.in[t] = in[t]; A.a[t] = a[t]; }
+      A.n = n;
+      A.out = out;
+      A.count = ns;
+      cudaEvent_t ev = p->tic();
+      SPADJ_CUDA_TRY(p, launch_kernel(p->pdl, combine_kernel, dim3(comb_grid()), dim3(256), 0, p->stream, A));
+      p->toc(ev, KC_POINTWISE, 4.0 * (double)ns * (n - 1) + 2.0 * (double)ns);
+      return check_launch(p, "rb combine");
+    }
     int t = 0;
     bool first = true;
     while (first || t < n) {
@@ -677,6 +691,20 @@ struct RB : EqImpl {
 
   // terms of v_i (pointers, weights) over x_0, f_j and (v_j, x_j); the tangent's stage vectors
   // (dx_0, df_j, dv_j, dx_j) when tangent
+  // out_k += c_k src for n distinct outputs (none is src), one launch
+  spadj_status scatter(Problem* p, const double2* src, int n, double2* const* out, const double* c) {
+    if (n == 0) return SPADJ_OK;
+    ScatArgs A{};
+    for (int k = 0; k < n; ++k) { A.out[k] = out[k]; A.c[k] = c[k]; }
+    A.n = n;
+    A.src = src;
+    A.count = ns;
+    cudaEvent_t ev = p->tic();
+    SPADJ_CUDA_TRY(p, launch_kernel(p->pdl, scatter_kernel, dim3(comb_grid()), dim3(256), 0, p->stream, A));
+    p->toc(ev, KC_POINTWISE, 4.0 * (double)ns * n);
+    return check_launch(p, "rb scatter");
+  }
+
   int stage_terms(int i, const double2* x0, const double2** in, double* a, bool tangent) {
     int n = 0;
     in[n] = x0; a[n++] = 1.0;
@@ -745,22 +773,22 @@ struct RB : EqImpl {
         if ((s = solve(p, 1, 1, v, one, st(atmp))) != SPADJ_OK) return s; }
       { const double2* in[2] = {vbi, st(atmp)}; const double a[2] = {1.0, 1.0};
         if ((s = lincomb(p, vbi, 2, in, a)) != SPADJ_OK) return s; }
-      // v_i = x_0 + sum_j dt A_ij f_j - sum_j h_ij (v_j - x_j): distribute vbar_i
-      { const double2* in[2] = {st(aacc), vbi}; const double a[2] = {1.0, 1.0};
-        if ((s = lincomb(p, st(aacc), 2, in, a)) != SPADJ_OK) return s; }
-      for (int j = 0; j < i; ++j)
-        if (tA[i][j] != 0.0) {
-          const double2* in[2] = {st(afb[j]), vbi};
-          const double a[2] = {1.0, dt * tA[i][j]};
-          if ((s = lincomb(p, st(afb[j]), 2, in, a)) != SPADJ_OK) return s;
+      // v_i = x_0 + sum_j dt A_ij f_j - sum_j h_ij (v_j - x_j): distribute vbar_i, every cotangent
+      // it reaches in one launch
+      {
+        double2* outs[kCombMax];
+        double cs[kCombMax];
+        int no = 0;
+        outs[no] = st(aacc); cs[no++] = 1.0;
+        for (int j = 0; j < i; ++j)
+          if (tA[i][j] != 0.0) { outs[no] = st(afb[j]); cs[no++] = dt * tA[i][j]; }
+        for (int j = 1; j < i; ++j) {
+          const double h = tH[i][j] / gam;
+          if (h == 0.0) continue;
+          outs[no] = st(avb[j - 1]); cs[no++] = -h;
+          outs[no] = st(axb[j - 1]); cs[no++] = h;
         }
-      for (int j = 1; j < i; ++j) {
-        const double h = tH[i][j] / gam;
-        if (h == 0.0) continue;
-        { const double2* in[2] = {st(avb[j - 1]), vbi}; const double a[2] = {1.0, -h};
-          if ((s = lincomb(p, st(avb[j - 1]), 2, in, a)) != SPADJ_OK) return s; }
-        { const double2* in[2] = {st(axb[j - 1]), vbi}; const double a[2] = {1.0, h};
-          if ((s = lincomb(p, st(axb[j - 1]), 2, in, a)) != SPADJ_OK) return s; }
+        if ((s = scatter(p, vbi, no, outs, cs)) != SPADJ_OK) return s;
       }
     }
     // xbar_0 = acc + (dF/dx)(x_0)^H fbar_0

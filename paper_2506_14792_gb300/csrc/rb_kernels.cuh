@@ -975,6 +975,53 @@ __global__ void sum_kernel(const double* __restrict__ partial, int n, double* __
 }
 
 // y = sum_t a_t x_t over n complex entries (state combinations).
+// Linear combinations of state vectors in one launch.  combine: out = a_0 in_0 + a_1 in_1 + ...
+// (in_0 may be out; the terms are added by multiply-adds in term order, the same sums as a chain
+// of axpy_kernel launches); scatter: out_k += c_k src for several distinct outputs (none equal to
+// src).
+constexpr int kCombMax = 16;
+struct CombArgs {
+  const double2* in[kCombMax];
+  double a[kCombMax];
+  int n;
+  double2* out;
+  size_t count;
+};
+__global__ void combine_kernel(const __grid_constant__ CombArgs A) {
+  pdl_trigger();
+  pdl_wait();
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < A.count; i += (size_t)gridDim.x * blockDim.x) {
+    double2 v = A.in[0][i];
+    double2 r = make_double2(A.a[0] * v.x, A.a[0] * v.y);
+    for (int t = 1; t < A.n; ++t) {
+      v = A.in[t][i];
+      r.x = fma(A.a[t], v.x, r.x);
+      r.y = fma(A.a[t], v.y, r.y);
+    }
+    A.out[i] = r;
+  }
+}
+struct ScatArgs {
+  double2* out[kCombMax];
+  double c[kCombMax];
+  int n;
+  const double2* src;
+  size_t count;
+};
+__global__ void scatter_kernel(const __grid_constant__ ScatArgs A) {
+  pdl_trigger();
+  pdl_wait();
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < A.count; i += (size_t)gridDim.x * blockDim.x) {
+    const double2 s = A.src[i];
+    for (int k = 0; k < A.n; ++k) {
+      double2 y = A.out[k][i];
+      y.x = fma(A.c[k], s.x, y.x);
+      y.y = fma(A.c[k], s.y, y.y);
+      A.out[k][i] = y;
+    }
+  }
+}
+
 __global__ void axpy_kernel(double2* __restrict__ y, const double2* __restrict__ x0, double a0,
                             const double2* __restrict__ x1, double a1, const double2* __restrict__ x2, double a2,
                             size_t n) {
