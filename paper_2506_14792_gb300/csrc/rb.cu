@@ -585,9 +585,14 @@ struct RB : EqImpl {
     return check_launch(p, "rb colstepT");
   }
 
-  spadj_status solve(Problem* p, int transpose, int nin, const double2* const* in, const double* a, double2* out) {
+  // out = Phi (sum_t a_t in_t) (transpose 0) or Phi^H ... (transpose 1), up to 16 terms combined on
+  // the operand load; vout (nullable, forward) receives the combined operand.
+  spadj_status solve(Problem* p, int transpose, int nin, const double2* const* in, const double* a, double2* out,
+                     double2* vout = nullptr) {
+    if (nin < 1 || nin > 16) return p->fail(SPADJ_ERR_INVALID, "rb solve: 1..16 operand terms");
     SolveArgs S{};
     for (int t = 0; t < nin; ++t) { S.in[t] = in[t]; S.a[t] = a[t]; }
+    S.vout = transpose ? nullptr : vout;
     S.nin = nin; S.out = out; S.transpose = transpose; S.phiF = ops_cur->phiT.as<double>(); S.phiA = ops_cur->phi.as<double>();
     S.Kx = Kx; S.N = N;
     const int H = 3 * N / 2;
@@ -729,10 +734,9 @@ struct RB : EqImpl {
       const double2* in[16];
       double a[16];
       int n = stage_terms(i, x0, in, a, false);
-      if ((s = lincomb(p, gv(i), n, in, a)) != SPADJ_OK) return s;
       double2* xi = i == S ? x_out : gx(i);
-      { const double2* v[1] = {gv(i)};
-        if ((s = solve(p, 0, 1, v, one, xi)) != SPADJ_OK) return s; }
+      // v_i combined on the solve's operand load (and stored for the later stages and the adjoint)
+      if ((s = solve(p, 0, n, in, a, xi, gv(i))) != SPADJ_OK) return s;
       if (dx0) {
         n = stage_terms(i, dx0, in, a, true);
         if ((s = lincomb(p, st(tdv[i - 1]), n, in, a)) != SPADJ_OK) return s;

@@ -522,10 +522,11 @@ __global__ void prod_vjp_kernel(const double* __restrict__ G, const double* __re
 // CTA's rows of the operator are staged in shared memory by cp.async before the kernel waits
 // for its predecessor (programmatic dependent launch), so the staging overlaps that kernel.
 struct SolveArgs {
-  const double2* in[4];
-  double a[4];
+  const double2* in[16];
+  double a[16];
   int nin;
   double2* out;
+  double2* vout;  // nullable: the combined operand sum_t a_t in_t is also stored here (forward only)
   int transpose;
   const double* phiF;  // [Kx][2][H][H] as [k][r] = Phi'[r][k]
   const double* phiA;  // [Kx][2][H][H] as [k][r] = Phi'[k][r]
@@ -565,6 +566,7 @@ __global__ void __launch_bounds__(1024) solve_kernel(const __grid_constant__ Sol
       x.x = fma(S.a[t], y.x, x.x);
       x.y = fma(S.a[t], y.y, x.y);
     }
+    if (S.vout && blockIdx.z == 0) S.vout[off] = x;  // one row block of each (pencil, class) stores it
     if (S.transpose && m == 0) x.y = 0.0;          // projection (self-adjoint)
     if (f == 0) x = make_double2(x.y, -x.x);        // times -i (Dr, or Dc^H)
     v[c] = x;
