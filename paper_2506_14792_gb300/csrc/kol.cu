@@ -65,6 +65,9 @@ struct KolArgs {
   int adjoint;      // 0 forward, 1 adjoint
   int fonly;        // forward: stage-0 F evaluation only (writes F(x0) to out)
   int nstage;       // number of stages in this launch
+  // persistent launch over stages stage0 .. stage0 + nrun - 1 of the sweep only (nrun = 0: all); the
+  // completion counters count from the sweep's first stage, so a later launch waits on the same targets
+  int stage0, nrun;
   int S;            // n_steps of the sweep (adjoint: the horizon N, which fixes the weights and the seed)
   // Segments (checkpointed sweeps).  Forward: stage s is step n0 + s (x0 = X_{n0}, with X_{n0-1} and
   // F(X_{n0-1}) preset in the rings when n0 >= 1), traj (nullable) holds the launch's states relative
@@ -602,14 +605,15 @@ __device__ bool wait_ge(int* ctr, int target, int* err, unsigned limit) {
 __global__ void __launch_bounds__(kKolThreads) kol_persistent(const __grid_constant__ KolArgs A) {
   __shared__ int item;
   const int per = A.nCAtot + A.nBtot;
-  const int total = A.nstage * per - A.nBtot;  // the last stage has no B phase
+  const int nrun = A.nrun > 0 ? A.nrun : A.nstage;
+  const int total = nrun * per - (A.stage0 + nrun == A.nstage ? A.nBtot : 0);  // the last stage has no B phase
   while (true) {
     if (threadIdx.x == 0) item = (*(volatile int*)A.err) ? total : atomicAdd(A.queue, 1);
     __syncthreads();
     const int it = item;
     __syncthreads();
     if (it >= total) break;
-    const int stage = it / per, r = it % per;
+    const int stage = A.stage0 + it / per, r = it % per;
     const bool isCA = r < A.nCAtot;
     const int rr = isCA ? r : r - A.nCAtot;
     const int b = find_member(A, rr, isCA);
@@ -885,7 +889,8 @@ struct Kol : EqImpl {
     SPADJ_CUDA_TRY(p, mixA.ensure(6 * mb));
     SPADJ_CUDA_TRY(p, mixB.ensure(5 * mb));
     if (closure) {
-      persistent = 0;  // the CNN needs whole-member grid phases between the row and column phases
+      // the CNN needs whole-member grids between the steps: the persistent scheduler runs one
+      // launch per step (option 0 = 0: one launch per phase)
       const size_t gb = sizeof(double) * grid_size;
       const size_t np = (size_t)cnn::n_params();
       const size_t act = (size_t)grid_size * cnn::kHid;
@@ -992,7 +997,7 @@ struct Kol : EqImpl {
   spadj_status launch(Problem* p, KolArgs& A) {
     const int per = A.nCAtot + A.nBtot;
     if (persistent) {
-      cudaEvent_t t = p->tic();
+      cudaEvent_t t = closure ? nullptr : p->tic();
       SPADJ_CUDA_TRY(p, cudaMemsetAsync(ctr.ptr, 0, sizeof(int) * (2 * (size_t)nmem + 2), p->stream));
       if (!grid_persistent) {
         int dev = 0, sms = 0, occ = 0;
@@ -1003,10 +1008,30 @@ struct Kol : EqImpl {
         const int per_sm = ctas_per_sm > 0 ? std::min(ctas_per_sm, occ) : occ;
         grid_persistent = sms * per_sm;
       }
-      kol_persistent<<<grid_persistent, kKolThreads, smem, p->stream>>>(A);
-      spadj_status s = check_launch(p, "kolmogorov persistent");
-      p->toc(t, KC_FUSED, work_flops(A));
-      return s;
+      if (!closure) {
+        kol_persistent<<<grid_persistent, kKolThreads, smem, p->stream>>>(A);
+        spadj_status s = check_launch(p, "kolmogorov persistent");
+        p->toc(t, KC_FUSED, work_flops(A));
+        return s;
+      }
+      // closure: one persistent launch per step over that step's phases of all members (a member's
+      // B tiles start as soon as its own CA tiles are done), the network passes between the launches
+      const double per_stage = A.nstage > 1 ? work_flops(A) / (A.nstage - 1) : 0.0;
+      for (int st = 0; st < A.nstage; ++st) {
+        cudaEvent_t ts = p->tic();
+        if (st > 0) SPADJ_CUDA_TRY(p, cudaMemsetAsync(ctr.ptr, 0, sizeof(int), p->stream));  // the item queue only
+        A.stage0 = st;
+        A.nrun = 1;
+        kol_persistent<<<grid_persistent, kKolThreads, smem, p->stream>>>(A);
+        spadj_status s = check_launch(p, "kolmogorov persistent step");
+        if (s != SPADJ_OK) return s;
+        p->toc(ts, KC_FUSED, st + 1 < A.nstage ? per_stage : 0.0);
+        if (st + 1 < A.nstage) {
+          s = A.adjoint ? closure_backward(p, A) : closure_forward(p, A);
+          if (s != SPADJ_OK) return s;
+        }
+      }
+      return SPADJ_OK;
     }
     // one launch per phase; the solver's phases and the closure's network passes are timed
     // separately (classes fused and cnn), stage by stage
@@ -1610,7 +1635,6 @@ struct Kol : EqImpl {
   spadj_status set_option(Problem* p, int option, int value) {
     switch (option) {
       case 0:
-        if (value && closure) return p->fail(SPADJ_ERR_UNSUPPORTED, "set_option: the closure runs with per-phase launches");
         persistent = value ? 1 : 0;
         return SPADJ_OK;
       case 1:

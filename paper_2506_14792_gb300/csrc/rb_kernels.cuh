@@ -9,6 +9,7 @@
 // so every output pair (j, Mz-1-j) costs one half-length dot product ("expand"), and
 // every grid-to-coefficient reduction runs over Mz/2 folded samples ("fold").
 #pragma once
+#include <algorithm>
 #include <cooperative_groups.h>
 
 #include "fft.cuh"
@@ -469,16 +470,24 @@ inline int tune_xfft_rows(const XJobs& js, const XParams& xp, int nrows, cudaStr
   int best_xv = xvar(1, 64);
   float best = 1e30f;
   constexpr int cand[] = {xvar(1, 64), xvar(2, 64), xvar(4, 64), xvar(2, 96), xvar(4, 96), xvar(4, 128), xvar(4, 192)};
+  // each candidate: one untimed launch, then the median of 7 timed ones (a lucky or unlucky single
+  // launch does not decide the variant)
   for (int xv : cand) {
     if (!ok[xvar_rows(xv)]) continue;
-    for (int rep = 0; rep < 4 && *err == cudaSuccess; ++rep) {
+    float t[7];
+    int nt = 0;
+    for (int rep = 0; rep < 8 && *err == cudaSuccess; ++rep) {
       cudaEventRecord(a, st);
       *err = launch_xfft(false, xv, js, xp, nrows, st);
       cudaEventRecord(b, st);
       if (*err == cudaSuccess) *err = cudaEventSynchronize(b);
       float ms = 0.f;
       if (*err == cudaSuccess) cudaEventElapsedTime(&ms, a, b);
-      if (rep > 0 && ms < best) { best = ms; best_xv = xv; }
+      if (rep > 0) t[nt++] = ms;
+    }
+    if (nt == 7) {
+      std::sort(t, t + 7);
+      if (t[3] < best) { best = t[3]; best_xv = xv; }
     }
   }
   cudaEventDestroy(a);

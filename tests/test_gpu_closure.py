@@ -101,6 +101,39 @@ def test_closure_gradients_vs_fp64_oracle():
           "dJ/dX0", [rel_err(gh[b], gx_ref[b]) for b in range(B)], "dJ/dp", rel_err(host(gp), gp_ref))
 
 
+def test_persistent_step_launches_equal_per_phase_launches():
+    """The solver phases of a closure step as one persistent launch per step (option 0 = 1, the
+    default: a member's B tiles start as soon as its own CA tiles are done) and as one launch per
+    phase (option 0 = 0): the same arithmetic on every tile, so the forward states and the whole
+    gradient (J, dJ/dX_0, dJ/dp) are bitwise equal."""
+    from paper_2506_14792_gb300 import spadj
+    B, nsteps, obs_steps = 3, 6, [3, 6]
+    params = synthetic.cnn_params(7, scale_out=1.0)
+    X0 = dev(np.concatenate([okol.Kolmogorov(N, RE).project(synthetic.kolmogorov_ic(N, 700 + i)).ravel()
+                             for i in range(B)]))
+    kmax = N // 2 - 1
+    obs = np.stack([np.concatenate([(okol.Kolmogorov(N, RE).lowpass_mask(kmax) *
+                                     okol.Kolmogorov(N, RE).project(synthetic.kolmogorov_ic(N, 800 + b + 10 * o))).ravel()
+                                    for b in range(B)]) for o in range(len(obs_steps))])
+    res = []
+    for mode in (1, 0):
+        p = gpu_problem(B)
+        p.set_option(0, mode)
+        p.set_params(dev(params))
+        p.set_observations(obs_steps, dev(obs), kmax)
+        xo = torch.zeros_like(X0)
+        p.forward(nsteps, X0, xo)
+        g = torch.zeros_like(X0)
+        gp = torch.zeros(cnn.n_params(), dtype=torch.float64, device="cuda")
+        J = p.gradient(X0, nsteps, g, objective=spadj.SPADJ_OBJ_FOURDVAR, grad_p=gp)
+        res.append((xo, np.asarray(J), g, gp))
+    (xa, Ja, ga, pa), (xb, Jb, gb, pb) = res
+    assert torch.equal(xa, xb)
+    assert np.array_equal(Ja, Jb)
+    assert torch.equal(ga, gb)
+    assert torch.equal(pa, pb)
+
+
 def _bf16(x):
     """float32 -> the nearest bfloat16 (round to nearest even), as float32 values and bit patterns."""
     u = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32)
