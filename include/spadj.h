@@ -323,12 +323,13 @@ spadj_status spadj_adam(spadj_problem* prob, const double* grad_p, int t, double
                         double eps, double* m, double* v, double* params);
 
 /* Tuning knobs of the batched persistent launch (SPADJ_KOLMOGOROV2D): option 0 = persistent
- * scheduler (1, default; with the closure, one persistent launch per step, the network's
- * whole-grid passes running between the launches) or one launch per phase (0); 1 = x-modes per
- * column tile; 2 = grid rows per row tile; 3 = resident CTAs per SM (0 = occupancy maximum);
- * 4 = iteration limit of the scheduler's bounded waits (0 = default, several seconds);
- * 5 = failure-path test: the completion of this member (-1 = none) is never signalled, so a
- * bounded wait runs out and the call returns SPADJ_ERR_TIMEOUT with the context intact.  Option 6 (SPADJ_RB2D,
+ * scheduler (1, default) or one launch per phase (0); with the closure the persistent scheduler
+ * runs one launch per step (the network's whole-grid passes run between the launches) and is the
+ * default only for batches of at least 64 grid rows per SM; 1 = x-modes per column tile;
+ * 2 = grid rows per row tile; 3 = resident CTAs per SM (0 = occupancy maximum); 4 = iteration
+ * limit of the scheduler's bounded waits (0 = default, several seconds); 5 = failure-path test:
+ * the completion of this member (-1 = none) is never signalled, so a bounded wait runs out and
+ * the call returns SPADJ_ERR_TIMEOUT with the context intact.  Option 6 (SPADJ_RB2D,
  * SPADJ_COUETTE3D) = programmatic dependent launch of consecutive kernels (1: the next kernel
  * is scheduled while its predecessor drains and waits for it on the device; 0, default: plain
  * stream order); option 7 (SPADJ_RB2D) = fused column stage (1, default: the z fold, the stage

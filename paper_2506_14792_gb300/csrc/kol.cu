@@ -889,8 +889,23 @@ struct Kol : EqImpl {
     SPADJ_CUDA_TRY(p, mixA.ensure(6 * mb));
     SPADJ_CUDA_TRY(p, mixB.ensure(5 * mb));
     if (closure) {
-      // the CNN needs whole-member grids between the steps: the persistent scheduler runs one
-      // launch per step (option 0 = 0: one launch per phase)
+      // The CNN needs whole-member grids between the steps, so the persistent scheduler runs one
+      // launch per step.  It pays off only when the batch has enough grid rows to keep every CTA
+      // busy while the members' row tiles wait on their column tiles; measured with 64-mode
+      // windows (forward sweep, us per window-step, per-step persistent with 4 rows per row tile
+      // against one launch per phase with 2): 128 windows 7.8 against 8.1 (training iteration
+      // 57.3 against 59.8 ms), 64 windows 9.4 against 8.9, 16 windows 19.1 against 15.4.  Hence:
+      // at least 64 grid rows per SM -> per-step persistent launches with 4 rows per row tile,
+      // else one launch per phase with 2 (option 0 overrides the launch form).
+      {
+        int dev = 0, sms = 0;
+        SPADJ_CUDA_TRY(p, cudaGetDevice(&dev));
+        SPADJ_CUDA_TRY(p, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        long long rows = 0;
+        for (auto& m : hm) rows += m.M;
+        persistent = rows >= 64LL * sms ? 1 : 0;
+        RW = persistent ? 4 : 2;
+      }
       const size_t gb = sizeof(double) * grid_size;
       const size_t np = (size_t)cnn::n_params();
       const size_t act = (size_t)grid_size * cnn::kHid;

@@ -74,6 +74,32 @@ def test_persistent_equals_phased_bitwise():
     assert torch.equal(outs[0], outs[1])
 
 
+def test_tilings_bitwise():
+    """The tile sizes only group the same row and column transforms differently (x-modes per
+    column tile, option 1; grid rows per row tile, option 2; resident CTAs per SM, option 3), so
+    the forward states and the 4D-Var gradient are bitwise equal for every tiling, including tiles
+    that do not divide the member (ragged last tiles)."""
+    from paper_2506_14792_gb300 import spadj
+    sizes, dt, nsteps, obs_steps, kmax = [16, 32, 48], 5e-3, 10, [5, 10], 6
+    X0, obs, _, _ = _fourdvar_case(sizes, dt, nsteps, obs_steps, kmax, 40)
+    X = dev(pack(X0))
+    ref = None
+    for cw, rw, cps in [(4, 2, 0), (2, 1, 0), (8, 4, 0), (3, 5, 0), (64, 64, 1), (1, 7, 2)]:
+        p = gpu_problem(sizes, dt=dt)
+        p.set_option(1, cw)
+        p.set_option(2, rw)
+        p.set_option(3, cps)
+        p.set_observations(obs_steps, dev(obs), kmax)
+        o = torch.zeros_like(X)
+        p.forward(nsteps, X, o)
+        g = torch.zeros_like(X)
+        J = np.asarray(p.gradient(X, nsteps, g, objective=spadj.SPADJ_OBJ_FOURDVAR))
+        if ref is None:
+            ref = (o, g, J)
+        else:
+            assert torch.equal(o, ref[0]) and torch.equal(g, ref[1]) and np.array_equal(J, ref[2]), (cw, rw, cps)
+
+
 def _fourdvar_case(sizes, dt, nsteps, obs_steps, kmax, seed0):
     X0 = ics(sizes, seed0)
     obs, Js, gs = [], [], []
