@@ -790,6 +790,28 @@ __host__ __device__ constexpr size_t halo_smem(int M) {
   return (size_t)2 * 4 * halo_range(M) * 16 + (size_t)32 * kTcK * 2;
 }
 
+// One thread's entries of a staged halo range: i = i0, i0 + step, ... < R, entry i holding the
+// pixel at staged index r0 + i (row ys = floor(s / W) taken modulo M, column xs - 1 with the halo
+// columns xs = 0 and M + 1 wrapped).  One floor division at the start; then the column advances by
+// step and carries into the row, so the loop needs no division.  f(i, pixel) per entry.
+template <class F>
+__device__ __forceinline__ void halo_walk(int r0, int i, int step, int R, int W, int M, F&& f) {
+  const int r = r0 + i;
+  const int ys = r >= 0 ? r / W : -((W - 1 - r) / W);  // floor division (r >= -W - 1)
+  int xs = r - ys * W;                                 // 0 .. W - 1
+  int ym = ((ys % M) + M) % M;  // rows past the member (read only by discarded outputs) wrap too
+  for (; i < R; i += step) {
+    int x = xs - 1;
+    x = x < 0 ? x + M : (x >= M ? x - M : x);
+    f(i, ym * M + x);
+    xs += step;
+    while (xs >= W) {
+      xs -= W;
+      if (++ym == M) ym = 0;
+    }
+  }
+}
+
 __global__ void __launch_bounds__(128) conv32_halo_kernel(int l, int M, int nb, int mode,
                                                           const __nv_bfloat16* __restrict__ in,
                                                           const __nv_bfloat16* __restrict__ wq,
@@ -830,17 +852,12 @@ __global__ void __launch_bounds__(128) conv32_halo_kernel(int l, int M, int nb, 
   auto stage = [&](long long tile, int buf) {
     const long long mb = tile / tpm;
     const int s0 = (int)(tile - mb * tpm) * kTcRows;
-    const __nv_bfloat16* src = in + mb * P * 32;
-    for (int idx = tid; idx < 4 * R; idx += blockDim.x) {
-      const int i = idx >> 2, g = idx & 3;
-      const int r = s0 - W - 1 + i;
-      int ys = r >= 0 ? r / W : -((W - 1 - r) / W);  // floor division (r >= -W - 1)
-      const int xs = r - ys * W;                      // 0 .. W - 1
-      ys = ((ys % M) + M) % M;  // rows past the member (read only by discarded outputs) wrap too
-      int x = xs - 1;
-      x = x < 0 ? x + M : (x >= M ? x - M : x);
-      cp_async16_zfill(sA[buf] + ((size_t)g * R + i) * 16, src + ((long long)ys * M + x) * 32 + g * 8, true);
-    }
+    const __nv_bfloat16* src = in + mb * P * 32 + (tid & 3) * 8;
+    unsigned char* dst = sA[buf] + (size_t)(tid & 3) * R * 16;
+    // entry (g, i) for idx = 4 i + g = tid, tid + 128, ...: g = tid & 3 fixed, i steps by 32
+    halo_walk(s0 - W - 1, tid >> 2, blockDim.x >> 2, R, W, M, [&](int i, int pix) {
+      cp_async16_zfill(dst + (size_t)i * 16, src + (long long)pix * 32, true);
+    });
     cp_async_commit();
   };
   unsigned parity = 0;
@@ -985,15 +1002,12 @@ __global__ void __launch_bounds__(288, 3) wgrad32_halo_kernel(int M, const __nv_
   auto sdz = [&](int b) { return ws + b * buf_bytes + (size_t)4 * R * 16; };
   auto stage = [&](int tile, int b) {
     const int s0 = tile * kTcRows;
-    for (int idx = tid; idx < 4 * R; idx += blockDim.x) {
-      const int i = idx >> 2, g = idx & 3;
-      const int r = s0 - W - 1 + i;
-      int ys = r >= 0 ? r / W : -((W - 1 - r) / W);
-      const int xs = r - ys * W;
-      ys = ((ys % M) + M) % M;
-      int x = xs - 1;
-      x = x < 0 ? x + M : (x >= M ? x - M : x);
-      cp_async16_zfill(sin(b) + ((size_t)g * R + i) * 16, inm + ((long long)ys * M + x) * 32 + g * 8, true);
+    {
+      const __nv_bfloat16* src = inm + (tid & 3) * 8;
+      unsigned char* dst = sin(b) + (size_t)(tid & 3) * R * 16;
+      halo_walk(s0 - W - 1, tid >> 2, blockDim.x >> 2, R, W, M, [&](int i, int pix) {
+        cp_async16_zfill(dst + (size_t)i * 16, src + (long long)pix * 32, true);
+      });
     }
     for (int idx = tid; idx < 4 * kTcRows; idx += blockDim.x) {
       const int i = idx >> 2, g = idx & 3;
