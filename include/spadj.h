@@ -345,7 +345,9 @@ spadj_status spadj_adam(spadj_problem* prob, const double* grad_p, int t, double
  * (SPADJ_KOLMOGOROV2D with the closure) = the 32 -> 32 convolutions on the fifth-generation tensor
  * cores (tcgen05.mma, accumulator in tensor memory) with the operand staged once per tile and the
  * nine taps read through shifted descriptors (1, default), the same with the operand gathered once
- * per tap (2), or on warp-level mma.sync (0);
+ * per tap (2), or on warp-level mma.sync (0); option 13 (SPADJ_KOLMOGOROV2D with the closure) =
+ * how the thin layers' (1 -> 32, 32 -> 1) weight gradients are summed (1, default: all nine taps
+ * in one CTA per row band and member, the input window in registers; 0: one CTA per x offset);
  * option 12 (SPADJ_COUETTE3D) = form of the step solves (1: forward and back sweeps with the
  * banded LU factors of each recombined, mode-ordered pencil matrix, one warp per pencil pair;
  * 0: the dense prognostic operator Phi applied as a matvec; -1, default: banded when there are at

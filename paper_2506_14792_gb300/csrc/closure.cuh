@@ -335,6 +335,95 @@ __global__ void __launch_bounds__(256) wgrad_kernel(int l, int M, const __nv_bfl
   }
 }
 
+// The same weight and bias gradients with all nine taps in one CTA per (band, member): thread =
+// (pixel lane = t / 16, channel pair p = t % 16: wide channels 2p, 2p + 1, read as one BF16 pair).
+// A lane walks a contiguous segment of each row of the band with the 3 x 3 input window in
+// registers (three new input loads and one dz load per pixel, against four loads per tap triple
+// in wgrad_kernel, whose three x offsets are separate CTAs), accumulating the 9 x 2 tap sums and
+// the bias sums; the lanes' partials are then summed in shared memory in lane order into the same
+// scratch slots as wgrad_kernel (weight r = k * 9 + a * 3 + b, k the wide channel; then the
+// biases).  The narrow side (one channel) is loaded as a scalar by every thread of a pixel.
+template <int CI, int CO>
+__global__ void __launch_bounds__(256) wgrad_win_kernel(int M, const __nv_bfloat16* __restrict__ in,
+                                                        const __nv_bfloat16* __restrict__ dz,
+                                                        float* __restrict__ scratch) {
+  static_assert((CI == 1) != (CO == 1) && CI * CO == kHid, "a thin layer: one side 1, the other 32 wide");
+  constexpr bool kWideIn = CI > 1;
+  const int band = blockIdx.x, mb = blockIdx.y;
+  const int cp = threadIdx.x & 15, lane = threadIdx.x >> 4;
+  const int y0 = band * M / kThinSplits, y1 = (band + 1) * M / kThinSplits;
+  const int S = (M + 15) >> 4, x0 = lane * S, x1 = min(M, x0 + S);
+  const __nv_bfloat16* inm = in + (long long)mb * M * M * CI;
+  const __nv_bfloat16* dzm = dz + (long long)mb * M * M * CO;
+  // value pair at pixel q of a tensor: the thread's two wide channels, or the narrow value twice
+  auto ld = [&](const __nv_bfloat16* t, bool wide, int q) -> float2 {
+    if (wide) return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(t + (long long)q * kHid + 2 * cp));
+    const float v = __bfloat162float(t[q]);
+    return make_float2(v, v);
+  };
+  float acc[9][2], bacc[2] = {0.0f, 0.0f};
+#pragma unroll
+  for (int t = 0; t < 9; ++t) acc[t][0] = acc[t][1] = 0.0f;
+  if (x0 < x1) {
+    for (int y = y0; y < y1; ++y) {
+      const int yr[3] = {wrap1(y - 1, M) * M, y * M, wrap1(y + 1, M) * M};
+      float2 w[3][3];  // w[b][j]: input at row y + b - 1, column x + j - 1
+      const int xl = wrap1(x0 - 1, M);
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        w[b][0] = ld(inm, kWideIn, yr[b] + xl);
+        w[b][1] = ld(inm, kWideIn, yr[b] + x0);
+      }
+      for (int x = x0; x < x1; ++x) {
+        const int xn = wrap1(x + 1, M);
+#pragma unroll
+        for (int b = 0; b < 3; ++b) w[b][2] = ld(inm, kWideIn, yr[b] + xn);
+        const float2 d = ld(dzm, !kWideIn, yr[1] + x);
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+          for (int b = 0; b < 3; ++b) {
+            acc[a * 3 + b][0] = fmaf(w[b][a].x, d.x, acc[a * 3 + b][0]);
+            acc[a * 3 + b][1] = fmaf(w[b][a].y, d.y, acc[a * 3 + b][1]);
+          }
+        bacc[0] += d.x;
+        bacc[1] += d.y;
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+          w[b][0] = w[b][1];
+          w[b][1] = w[b][2];
+        }
+      }
+    }
+  }
+  __shared__ float red[16][16][20];
+#pragma unroll
+  for (int t = 0; t < 9; ++t) {
+    red[lane][cp][2 * t] = acc[t][0];
+    red[lane][cp][2 * t + 1] = acc[t][1];
+  }
+  red[lane][cp][18] = bacc[0];
+  red[lane][cp][19] = bacc[1];
+  __syncthreads();
+  float* dst = scratch + ((long long)mb * kThinSplits + band) * kThinOut;
+  const int nout = 9 * kHid + CO;  // CO biases (a narrow output has one, summed once: channel 0)
+  for (int r = threadIdx.x; r < nout; r += blockDim.x) {
+    int p, e;
+    if (r < 9 * kHid) {
+      const int k = r / 9, t = r - k * 9;
+      p = k >> 1;
+      e = 2 * t + (k & 1);
+    } else {
+      const int k = r - 9 * kHid;
+      p = k >> 1;
+      e = 18 + (k & 1);
+    }
+    float sum = 0.0f;
+    for (int q = 0; q < 16; ++q) sum += red[q][p][e];
+    dst[r] = sum;
+  }
+}
+
 // part[mb][w_off(l) + r] = sum over the bands of scratch[mb][band][r], in band order
 __global__ void wgrad_finish_kernel(int l, const float* __restrict__ scratch, float* __restrict__ part, int npar) {
   const int mb = blockIdx.x, nr = kThinOut - (l == 0 ? 0 : kHid - 1);  // 9 * 32 weights + 32 or 1 biases

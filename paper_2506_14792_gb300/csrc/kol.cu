@@ -1327,6 +1327,7 @@ struct Kol : EqImpl {
   // warp-level mma.sync kernel (modes 0 and 1).
   int sm_count = 0;
   int tc_conv = 1;
+  int thin_wgrad = 1;  // thin layers' weight gradients: 1 windowed (all taps per CTA), 0 one CTA per tap triple
   bool halo_fits = true;                           // the halo-staged network kernels fit this grid
   static constexpr size_t kHaloSmemMax = 226 * 1024;  // opt-in shared memory per CTA less the static part
   DevBuf cnnerr;
@@ -1441,14 +1442,22 @@ struct Kol : EqImpl {
         else
           conv32(p, l, 1, dzc, nullptr, nullptr, dh.as<float>());
       } else if (l == 0) {
-        cnn::wgrad_kernel<1, cnn::kHid><<<dim3(4, nb, cnn::kThinSplits), 256, 0, p->stream>>>(
-            l, M, ins[l], dzc, chunkbuf.as<float>());
+        if (thin_wgrad)
+          cnn::wgrad_win_kernel<1, cnn::kHid><<<dim3(cnn::kThinSplits, nb), 256, 0, p->stream>>>(
+              M, ins[l], dzc, chunkbuf.as<float>());
+        else
+          cnn::wgrad_kernel<1, cnn::kHid><<<dim3(4, nb, cnn::kThinSplits), 256, 0, p->stream>>>(
+              l, M, ins[l], dzc, chunkbuf.as<float>());
         cnn::wgrad_finish_kernel<<<nb, 320, 0, p->stream>>>(l, chunkbuf.as<float>(), part.as<float>(), np);
         cnn::dgrad_kernel<1, cnn::kHid><<<thin_grid(M, ci), 256, 0, p->stream>>>(
             l, M, dzc, wq.as<__nv_bfloat16>(), nullptr, corr.as<double>());
       } else {
-        cnn::wgrad_kernel<cnn::kHid, 1><<<dim3(4, nb, cnn::kThinSplits), 256, 0, p->stream>>>(
-            l, M, ins[l], dzc, chunkbuf.as<float>());
+        if (thin_wgrad)
+          cnn::wgrad_win_kernel<cnn::kHid, 1><<<dim3(cnn::kThinSplits, nb), 256, 0, p->stream>>>(
+              M, ins[l], dzc, chunkbuf.as<float>());
+        else
+          cnn::wgrad_kernel<cnn::kHid, 1><<<dim3(4, nb, cnn::kThinSplits), 256, 0, p->stream>>>(
+              l, M, ins[l], dzc, chunkbuf.as<float>());
         cnn::wgrad_finish_kernel<<<nb, 320, 0, p->stream>>>(l, chunkbuf.as<float>(), part.as<float>(), np);
         cnn::dgrad3_kernel<<<pixel_grid(M), 128, 0, p->stream>>>(
             M, dzc, wq.as<__nv_bfloat16>(), fuse ? nullptr : dh.as<float>(), fuse ? dact[l - 1].as<float>() : nullptr,
@@ -1670,6 +1679,9 @@ struct Kol : EqImpl {
                 // gathered per tap (2), or mma.sync (0)
         if (value < 0 || value > 2) return p->fail(SPADJ_ERR_INVALID, "set_option 11: 0, 1 or 2");
         tc_conv = value; return SPADJ_OK;
+      case 13:  // thin layers' weight gradients: windowed (1) or one CTA per tap triple (0)
+        if (value < 0 || value > 1) return p->fail(SPADJ_ERR_INVALID, "set_option 13: 0 or 1");
+        thin_wgrad = value; return SPADJ_OK;
       default: return p->fail(SPADJ_ERR_INVALID, "set_option: unknown option");
     }
   }

@@ -134,6 +134,40 @@ def test_persistent_step_launches_equal_per_phase_launches():
     assert torch.equal(pa, pb)
 
 
+def test_thin_weight_gradient_forms_agree():
+    """The thin layers' weight and bias gradients (1 -> 32 and 32 -> 1) by the windowed kernel (all
+    nine taps per CTA, the input window in registers; option 13 = 1, the default) and by one CTA
+    per x offset (option 13 = 0): the same FP32 products summed in another order, so dJ/dp agrees to
+    1e-5 (max-norm relative) and J and dJ/dX_0, which do not depend on them, are bitwise equal.  36
+    modes on a 54 x 54 grid: row segments of 4 pixels with a ragged last lane of 2, bands of 13
+    and 14 rows."""
+    from paper_2506_14792_gb300 import spadj
+    B, n, nsteps, obs_steps = 2, 36, 4, [2, 4]
+    kmax = n // 2 - 1
+    params = synthetic.cnn_params(9, scale_out=1.0)
+    X0 = dev(np.concatenate([okol.Kolmogorov(n, RE).project(synthetic.kolmogorov_ic(n, 900 + i)).ravel()
+                             for i in range(B)]))
+    obs = np.stack([np.concatenate([(okol.Kolmogorov(n, RE).lowpass_mask(kmax) *
+                                     okol.Kolmogorov(n, RE).project(synthetic.kolmogorov_ic(n, 950 + b + 10 * o))).ravel()
+                                    for b in range(B)]) for o in range(len(obs_steps))])
+    res = []
+    for form in (1, 0):
+        p = spadj.Problem(spadj.SPADJ_KOLMOGOROV2D, spadj.SPADJ_SBDF2, [n], [2 * np.pi], [RE, 0.0], DT, batch=B,
+                          closure=True)
+        p.set_option(13, form)
+        p.set_params(dev(params))
+        p.set_observations(obs_steps, dev(obs), kmax)
+        g = torch.zeros_like(X0)
+        gp = torch.zeros(cnn.n_params(), dtype=torch.float64, device="cuda")
+        J = p.gradient(X0, nsteps, g, objective=spadj.SPADJ_OBJ_FOURDVAR, grad_p=gp)
+        res.append((np.asarray(J), g, host(gp)))
+    (Ja, ga, pa), (Jb, gb, pb) = res
+    assert np.array_equal(Ja, Jb) and torch.equal(ga, gb)
+    err = rel_err(pa, pb)
+    print("thin weight-gradient forms: dJ/dp max-norm relative difference", err)
+    assert err < 1e-5
+
+
 def _bf16(x):
     """float32 -> the nearest bfloat16 (round to nearest even), as float32 values and bit patterns."""
     u = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32)
