@@ -348,6 +348,10 @@ spadj_status spadj_adam(spadj_problem* prob, const double* grad_p, int t, double
  * per tap (2), or on warp-level mma.sync (0); option 13 (SPADJ_KOLMOGOROV2D with the closure) =
  * how the thin layers' (1 -> 32, 32 -> 1) weight gradients are summed (1, default: all nine taps
  * in one CTA per row band and member, the input window in registers; 0: one CTA per x offset);
+ * option 14 (SPADJ_KOLMOGOROV2D with the closure) = how the thin layers' single-channel outputs
+ * (the 32 -> 1 forward, the 1 -> 32 input gradient) are summed (1, default: row segments with the
+ * 32-channel window in registers, channel pairs added across the half-warp; 0: one thread per
+ * pixel);
  * option 12 (SPADJ_COUETTE3D) = form of the step solves (1: forward and back sweeps with the
  * banded LU factors of each recombined, mode-ordered pencil matrix, one warp per pencil pair;
  * 0: the dense prognostic operator Phi applied as a matvec; -1, default: banded when there are at

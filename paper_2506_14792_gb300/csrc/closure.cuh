@@ -424,6 +424,76 @@ __global__ void __launch_bounds__(256) wgrad_win_kernel(int M, const __nv_bfloat
   }
 }
 
+// The thin layers' single-channel FP64 outputs with the 32-channel side read in windows: the
+// 32 -> 1 forward (kAdj = false: out = b + sum_{a,b,c} W[0][a][b][c] in[c](x + a - 1, y + b - 1))
+// and the 1 -> 32 input gradient (kAdj = true: out = sum_{o,a,b} W[o][0][a][b] dz[o](x - a + 1,
+// y - b + 1)).  CTA = (row band, member); thread = (pixel lane, channel pair) as in
+// wgrad_win_kernel: a lane walks a contiguous segment of each row with the 3 x 3 window of its two
+// channels in registers (three new loads per pixel) and its 18 weights in registers; the partial
+// sums of a pixel's 16 channel pairs are added by a butterfly over the half-warp.  Every thread of
+// a warp takes the same number of steps (a lane past the row's end works on a wrapped pixel and
+// stores nothing), so the shuffles are convergent.
+constexpr int kThinBands = 8;
+template <bool kAdj>
+__global__ void __launch_bounds__(256) thin_out_win_kernel(int M, const __nv_bfloat16* __restrict__ t32,
+                                                           const __nv_bfloat16* __restrict__ wq,
+                                                           const float* __restrict__ bq, double* __restrict__ out) {
+  const int band = blockIdx.x, mb = blockIdx.y;
+  const int cp = threadIdx.x & 15, lane = threadIdx.x >> 4;
+  const int y0 = band * M / kThinBands, y1 = (band + 1) * M / kThinBands;
+  const int S = (M + 15) >> 4, x0 = lane * S, xa = x0 % M;
+  const int l = kAdj ? 0 : kLayers - 1;
+  const __nv_bfloat16* W = wq + w_off(l);
+  float wr[9][2];
+#pragma unroll
+  for (int t = 0; t < 9; ++t)
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const int k = 2 * cp + e;  // W[0][a][b][k] (forward) or W[k][0][a][b] (input gradient), t = 3 a + b
+      wr[t][e] = __bfloat162float(kAdj ? W[k * 9 + t] : W[t * kHid + k]);
+    }
+  const float bias = kAdj ? 0.0f : bq[w_off(l) + 9 * kHid];
+  const __nv_bfloat16* tm = t32 + (long long)mb * M * M * kHid + 2 * cp;
+  double* om = out + (long long)mb * M * M;
+  auto ld = [&](int q) {
+    return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(tm + (long long)q * kHid));
+  };
+  for (int y = y0; y < y1; ++y) {
+    const int yr[3] = {wrap1(y - 1, M) * M, y * M, wrap1(y + 1, M) * M};
+    float2 w[3][3];  // w[r][j]: row y + r - 1, column xc + j - 1
+    int xc = xa;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      w[r][0] = ld(yr[r] + wrap1(xc - 1, M));
+      w[r][1] = ld(yr[r] + xc);
+    }
+    for (int s = 0; s < S; ++s) {
+      const int xn = wrap1(xc + 1, M);
+#pragma unroll
+      for (int r = 0; r < 3; ++r) w[r][2] = ld(yr[r] + xn);
+      float acc = 0.0f;
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+          const float2 v = kAdj ? w[2 - b][2 - a] : w[b][a];
+          acc = fmaf(wr[a * 3 + b][0], v.x, acc);
+          acc = fmaf(wr[a * 3 + b][1], v.y, acc);
+        }
+#pragma unroll
+      for (int off = 8; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+      const int x = x0 + s;
+      if (cp == 0 && x < M) om[yr[1] + x] = (double)(bias + acc);
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        w[r][0] = w[r][1];
+        w[r][1] = w[r][2];
+      }
+      xc = xn;
+    }
+  }
+}
+
 // part[mb][w_off(l) + r] = sum over the bands of scratch[mb][band][r], in band order
 __global__ void wgrad_finish_kernel(int l, const float* __restrict__ scratch, float* __restrict__ part, int npar) {
   const int mb = blockIdx.x, nr = kThinOut - (l == 0 ? 0 : kHid - 1);  // 9 * 32 weights + 32 or 1 biases

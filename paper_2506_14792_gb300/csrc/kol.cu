@@ -1328,6 +1328,7 @@ struct Kol : EqImpl {
   int sm_count = 0;
   int tc_conv = 1;
   int thin_wgrad = 1;  // thin layers' weight gradients: 1 windowed (all taps per CTA), 0 one CTA per tap triple
+  int thin_out = 1;    // thin layers' single-channel outputs: 1 windowed (32-channel side), 0 one thread per pixel
   bool halo_fits = true;                           // the halo-staged network kernels fit this grid
   static constexpr size_t kHaloSmemMax = 226 * 1024;  // opt-in shared memory per CTA less the static part
   DevBuf cnnerr;
@@ -1386,6 +1387,9 @@ struct Kol : EqImpl {
       else if (l == 0)
         cnn::fwd0_kernel<<<pixel_grid(M), 128, 0, p->stream>>>(M, in, wq.as<__nv_bfloat16>(), bq.as<float>(),
                                                                 hbuf[l].as<__nv_bfloat16>(), nullptr);
+      else if (thin_out)
+        cnn::thin_out_win_kernel<false><<<dim3(cnn::kThinBands, nb), 256, 0, p->stream>>>(
+            M, in, wq.as<__nv_bfloat16>(), bq.as<float>(), corr.as<double>());
       else
         cnn::fwd_kernel<cnn::kHid, 1><<<thin_grid(M, co), 256, 0, p->stream>>>(
             l, M, in, wq.as<__nv_bfloat16>(), bq.as<float>(), nullptr, nullptr, corr.as<double>());
@@ -1449,8 +1453,12 @@ struct Kol : EqImpl {
           cnn::wgrad_kernel<1, cnn::kHid><<<dim3(4, nb, cnn::kThinSplits), 256, 0, p->stream>>>(
               l, M, ins[l], dzc, chunkbuf.as<float>());
         cnn::wgrad_finish_kernel<<<nb, 320, 0, p->stream>>>(l, chunkbuf.as<float>(), part.as<float>(), np);
-        cnn::dgrad_kernel<1, cnn::kHid><<<thin_grid(M, ci), 256, 0, p->stream>>>(
-            l, M, dzc, wq.as<__nv_bfloat16>(), nullptr, corr.as<double>());
+        if (thin_out)
+          cnn::thin_out_win_kernel<true><<<dim3(cnn::kThinBands, nb), 256, 0, p->stream>>>(
+              M, dzc, wq.as<__nv_bfloat16>(), bq.as<float>(), corr.as<double>());
+        else
+          cnn::dgrad_kernel<1, cnn::kHid><<<thin_grid(M, ci), 256, 0, p->stream>>>(
+              l, M, dzc, wq.as<__nv_bfloat16>(), nullptr, corr.as<double>());
       } else {
         if (thin_wgrad)
           cnn::wgrad_win_kernel<cnn::kHid, 1><<<dim3(cnn::kThinSplits, nb), 256, 0, p->stream>>>(
@@ -1682,6 +1690,9 @@ struct Kol : EqImpl {
       case 13:  // thin layers' weight gradients: windowed (1) or one CTA per tap triple (0)
         if (value < 0 || value > 1) return p->fail(SPADJ_ERR_INVALID, "set_option 13: 0 or 1");
         thin_wgrad = value; return SPADJ_OK;
+      case 14:  // thin layers' single-channel outputs: windowed (1) or one thread per pixel (0)
+        if (value < 0 || value > 1) return p->fail(SPADJ_ERR_INVALID, "set_option 14: 0 or 1");
+        thin_out = value; return SPADJ_OK;
       default: return p->fail(SPADJ_ERR_INVALID, "set_option: unknown option");
     }
   }

@@ -168,6 +168,42 @@ def test_thin_weight_gradient_forms_agree():
     assert err < 1e-5
 
 
+def test_thin_output_forms_agree():
+    """The thin layers' single-channel outputs (the 32 -> 1 forward into the closure term, the
+    1 -> 32 input gradient into the grid cotangent) by the windowed kernel (a row segment per
+    lane, the window of two channels per thread, the channel pairs added by a half-warp butterfly;
+    option 14 = 1, the default) and by one thread per pixel with a 32-channel dot product per tap
+    (option 14 = 0): the same FP32 products summed in another order, so the closure correction,
+    J, dJ/dX_0 and dJ/dp agree to 1e-5 (max-norm relative).  36 modes on a 54 x 54 grid: row
+    segments of 4 pixels with a ragged last lane of 2, bands of 6 and 7 rows."""
+    from paper_2506_14792_gb300 import spadj
+    B, n, nsteps, obs_steps = 2, 36, 4, [2, 4]
+    kmax = n // 2 - 1
+    params = synthetic.cnn_params(10, scale_out=1.0)
+    X0 = dev(np.concatenate([okol.Kolmogorov(n, RE).project(synthetic.kolmogorov_ic(n, 960 + i)).ravel()
+                             for i in range(B)]))
+    obs = np.stack([np.concatenate([(okol.Kolmogorov(n, RE).lowpass_mask(kmax) *
+                                     okol.Kolmogorov(n, RE).project(synthetic.kolmogorov_ic(n, 970 + b + 10 * o))).ravel()
+                                    for b in range(B)]) for o in range(len(obs_steps))])
+    res = []
+    for form in (1, 0):
+        p = spadj.Problem(spadj.SPADJ_KOLMOGOROV2D, spadj.SPADJ_SBDF2, [n], [2 * np.pi], [RE, 0.0], DT, batch=B,
+                          closure=True)
+        p.set_option(14, form)
+        p.set_params(dev(params))
+        f = torch.zeros_like(X0)
+        p.eval_F(X0, f)
+        p.set_observations(obs_steps, dev(obs), kmax)
+        g = torch.zeros_like(X0)
+        gp = torch.zeros(cnn.n_params(), dtype=torch.float64, device="cuda")
+        J = p.gradient(X0, nsteps, g, objective=spadj.SPADJ_OBJ_FOURDVAR, grad_p=gp)
+        res.append((host(f), np.asarray(J), host(g), host(gp)))
+    (fa, Ja, ga, pa), (fb, Jb, gb, pb) = res
+    errs = [rel_err(fa, fb), rel_err(Ja, Jb), rel_err(ga, gb), rel_err(pa, pb)]
+    print("thin output forms: F, J, dJ/dX0, dJ/dp max-norm relative differences", errs)
+    assert max(errs) < 1e-5
+
+
 def _bf16(x):
     """float32 -> the nearest bfloat16 (round to nearest even), as float32 values and bit patterns."""
     u = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32)
